@@ -1,0 +1,503 @@
+/*
+ * fsi_oracle.c -- plain, slow FP64 CPU oracle for the immersed-FSI hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; only tests/, the smoke check and the CPU-baseline leg of
+ * bench.py use it.  It shares no code, header or table with the CUDA library.
+ *
+ * What it computes (each function cites the passage it follows):
+ *   - Q1 (trilinear) shape functions on the parent cube [-1,1]^3
+ *     (first-order Lagrange elements, Sec. 4 intro).
+ *   - The VMS-stabilised incompressible Navier-Stokes residual on a uniform
+ *     hexahedral background grid: the Galerkin weak form of Eq. (fluid_weak_form)
+ *     plus the residual-based VMS terms of Bazilevs et al. 2007 that Sec. 2.1
+ *     refers to, with tau_m, tau_c, G from Sec. 2.1 (C_I = 36, C_T = 4).
+ *   - The consistent Jacobian-vector product of that residual with respect to
+ *     the generalized-alpha unknowns (Sec. 2.4, reduced system), written out
+ *     term by term.
+ *   - Point location, the interpolation u_A = sum_B N_B(phi(X_A)) v_B of
+ *     Eq. (nodal_solid_velo) and the spreading C^lambda lambda with
+ *     C_AB = N_A(phi(X_B)) I of Eq. (fsi_constraint_matrix) (Sec. 2.3).
+ *
+ * Everything is the definition written out: loops over elements, the eight
+ * 2x2x2 Gauss points and the eight test nodes; no sum factorisation, no
+ * colouring, no blocking.  Element contributions are computed independently
+ * (optionally with OpenMP) into element-local buffers and then assembled
+ * serially in element order.
+ *
+ * Layouts: nodes are lexicographic with x fastest, node(i,j,k) =
+ * i + (Nx+1)*(j + (Ny+1)*k); elements likewise with Nx, Ny; every nodal field
+ * is [n][4] row-major (vx, vy, vz, p) for U, (ax, ay, az, s) for A.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Q1 shape functions.  Local node a = ax + 2*ay + 4*az sits at parent
+ * coordinates xi^a_k = 2*a_k - 1; N_a(xi) = 1/8 prod_k (1 + xi_k xi^a_k).   */
+void or_shape(const double xi[3], double N[8], double dNdxi[24])
+{
+    for (int a = 0; a < 8; ++a) {
+        double s0 = (a & 1) ? 1.0 : -1.0;
+        double s1 = (a & 2) ? 1.0 : -1.0;
+        double s2 = (a & 4) ? 1.0 : -1.0;
+        double l0 = 1.0 + s0 * xi[0];
+        double l1 = 1.0 + s1 * xi[1];
+        double l2 = 1.0 + s2 * xi[2];
+        N[a] = l0 * l1 * l2 / 8.0;
+        dNdxi[3 * a + 0] = s0 * l1 * l2 / 8.0;
+        dNdxi[3 * a + 1] = l0 * s1 * l2 / 8.0;
+        dNdxi[3 * a + 2] = l0 * l1 * s2 / 8.0;
+    }
+}
+
+static int64_t node_id(const int N[3], int i, int j, int k)
+{
+    return (int64_t)i + (int64_t)(N[0] + 1) * ((int64_t)j + (int64_t)(N[1] + 1) * k);
+}
+
+/* global node of local node a of element (ex,ey,ez) */
+static int64_t elem_node(const int N[3], int ex, int ey, int ez, int a)
+{
+    return node_id(N, ex + (a & 1), ey + ((a >> 1) & 1), ez + ((a >> 2) & 1));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Stabilisation parameters of Sec. 2.1:
+ *   tau_m = ( s ( C_T/dt^2 + v.G v + C_I (mu/rho)^2 G:G ) )^(-1/2)
+ *   tau_c = ( tau_m tr G )^(-1)
+ *   G_ij  = sum_k dxi_k/dx_i dxi_k/dx_j.
+ * On the axis-aligned uniform grid dxi_k/dx_k = 2/h_k, so G = diag(4/h_k^2).
+ * ct_dt2 is C_T/dt^2 (0 for a steady problem).                               */
+void or_tau(const double v[3], double s, const double h[3], double rho, double mu,
+            double ct_dt2, double C_I, double out[2])
+{
+    double G[3], trG = 0.0, GG = 0.0, vGv = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        G[k] = 4.0 / (h[k] * h[k]);
+        trG += G[k];
+        GG += G[k] * G[k];
+        vGv += v[k] * G[k] * v[k];
+    }
+    double nu = mu / rho;
+    double tau_m = 1.0 / sqrt(s * (ct_dt2 + vGv + C_I * nu * nu * GG));
+    out[0] = tau_m;
+    out[1] = 1.0 / (tau_m * trG);
+}
+
+/* Physical parameters passed as an array so that ctypes stays simple:
+ * phys[0]=rho, phys[1]=mu, phys[2]=C_T/dt^2, phys[3]=C_I, phys[4]=has_s.   */
+typedef struct {
+    double rho, mu, ct_dt2, C_I;
+    int has_s;
+} or_phys;
+
+static or_phys unpack_phys(const double phys[5])
+{
+    or_phys p;
+    p.rho = phys[0];
+    p.mu = phys[1];
+    p.ct_dt2 = phys[2];
+    p.C_I = phys[3];
+    p.has_s = phys[4] != 0.0;
+    return p;
+}
+
+/* Field values at one Gauss point of one element. */
+typedef struct {
+    double N[8], dN[8][3];  /* shape values, physical gradients dN_a/dx_j */
+    double v[3], gv[3][3];  /* v_i, gv[i][j] = d v_i / d x_j            */
+    double p, gp[3];
+    double a[3], f[3], s;
+} gp_state;
+
+static void eval_gp(const int N[3], const double h[3], int ex, int ey, int ez, int g,
+                    const double *U, const double *A, const double *f, int has_s,
+                    gp_state *st)
+{
+    const double gq = 1.0 / sqrt(3.0);
+    double xi[3] = {(g & 1) ? gq : -gq, (g & 2) ? gq : -gq, (g & 4) ? gq : -gq};
+    double dNdxi[24];
+    or_shape(xi, st->N, dNdxi);
+    for (int a = 0; a < 8; ++a)
+        for (int j = 0; j < 3; ++j)
+            st->dN[a][j] = dNdxi[3 * a + j] * (2.0 / h[j]);
+    memset(st->v, 0, sizeof st->v);
+    memset(st->gv, 0, sizeof st->gv);
+    memset(st->gp, 0, sizeof st->gp);
+    memset(st->a, 0, sizeof st->a);
+    memset(st->f, 0, sizeof st->f);
+    st->p = 0.0;
+    st->s = has_s ? 0.0 : 1.0;
+    for (int a = 0; a < 8; ++a) {
+        int64_t nd = elem_node(N, ex, ey, ez, a);
+        const double *u = U + 4 * nd;
+        const double *ac = A + 4 * nd;
+        for (int i = 0; i < 3; ++i) {
+            st->v[i] += st->N[a] * u[i];
+            st->a[i] += st->N[a] * ac[i];
+            if (f) st->f[i] += st->N[a] * f[4 * nd + i];
+            for (int j = 0; j < 3; ++j) st->gv[i][j] += st->dN[a][j] * u[i];
+        }
+        st->p += st->N[a] * u[3];
+        for (int j = 0; j < 3; ++j) st->gp[j] += st->dN[a][j] * u[3];
+        if (has_s) st->s += st->N[a] * ac[3];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Element residual.  The weak form at a Gauss point, per test node A:
+ *
+ * momentum (component i):
+ *     N_A rho (a_i + v_j d_j v_i - f_i)             Galerkin inertia+convection
+ *   + d_j N_A mu (d_j v_i + d_i v_j)                 2 mu eps(w):eps(v)
+ *   - d_i N_A p                                      -(div w, p)
+ *   - rho v_j d_j N_A u'_i                           -(rho v.grad w, u')   SUPG
+ *   - d_i N_A p'                                     -(div w, p')          LSIC
+ *   + N_A rho u'_j d_j v_i                           (w, rho u'.grad v)    cross
+ *   - rho d_j N_A u'_i u'_j                          -(grad w, rho u'(x)u') Reynolds
+ * continuity:
+ *     N_A d_j v_j                                    (q, div v)
+ *   - d_j N_A u'_j                                   -(grad q, u')         PSPG
+ *
+ * with the strong residuals r_M = rho (a + v.grad v - f) + grad p,
+ * r_C = div v, and the fine scales u' = -(tau_M/rho) r_M, p' = -rho tau_C r_C.
+ * stab = 0 drops every term carrying u' or p' (plain Galerkin).             */
+static void element_residual(const int N[3], const double h[3], const or_phys *ph,
+                             int ex, int ey, int ez, const double *U, const double *A,
+                             const double *f, int stab, double Re[8][4])
+{
+    const double detJ = h[0] * h[1] * h[2] / 8.0;
+    const double rho = ph->rho, mu = ph->mu;
+    memset(Re, 0, 8 * 4 * sizeof(double));
+    for (int g = 0; g < 8; ++g) {
+        gp_state st;
+        eval_gp(N, h, ex, ey, ez, g, U, A, f, ph->has_s, &st);
+        double conv[3], rM[3], up[3];
+        for (int i = 0; i < 3; ++i) {
+            conv[i] = 0.0;
+            for (int j = 0; j < 3; ++j) conv[i] += st.v[j] * st.gv[i][j];
+            rM[i] = rho * (st.a[i] + conv[i] - st.f[i]) + st.gp[i];
+        }
+        double rC = st.gv[0][0] + st.gv[1][1] + st.gv[2][2];
+        double tau[2];
+        or_tau(st.v, st.s, h, rho, mu, ph->ct_dt2, ph->C_I, tau);
+        double pp = 0.0;
+        for (int i = 0; i < 3; ++i) up[i] = stab ? -(tau[0] / rho) * rM[i] : 0.0;
+        if (stab) pp = -rho * tau[1] * rC;
+
+        for (int A_ = 0; A_ < 8; ++A_) {
+            const double NA = st.N[A_];
+            const double *dNA = st.dN[A_];
+            double vgradN = 0.0;
+            for (int j = 0; j < 3; ++j) vgradN += st.v[j] * dNA[j];
+            for (int i = 0; i < 3; ++i) {
+                double t = NA * rho * (st.a[i] + conv[i] - st.f[i]);
+                for (int j = 0; j < 3; ++j) t += dNA[j] * mu * (st.gv[i][j] + st.gv[j][i]);
+                t -= dNA[i] * st.p;
+                t -= rho * vgradN * up[i];
+                t -= dNA[i] * pp;
+                for (int j = 0; j < 3; ++j) t += NA * rho * up[j] * st.gv[i][j];
+                for (int j = 0; j < 3; ++j) t -= rho * dNA[j] * up[i] * up[j];
+                Re[A_][i] += detJ * t;
+            }
+            double c = NA * rC;
+            for (int j = 0; j < 3; ++j) c -= dNA[j] * up[j];
+            Re[A_][3] += detJ * c;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Element Jacobian-vector product: the directional derivative of the element
+ * residual above in the direction dU = (c_v x_v, x_p), dA = (c_a x_v, 0),
+ * i.e. the consistent linearisation with respect to (Vdot_{n+1}, P_{n+1})
+ * with the generalized-alpha chain factors c_a = alpha_m and
+ * c_v = alpha_f gamma dt (Sec. 2.4).  xe holds the 8x4 local direction.
+ * Every term of element_residual is differentiated, including the
+ * dependence of tau_M and tau_C on v.                                        */
+static void element_jacobian_apply(const int N[3], const double h[3], const or_phys *ph,
+                                   int ex, int ey, int ez, const double *U,
+                                   const double *A, const double *f,
+                                   const double xe[8][4], double c_a, double c_v,
+                                   double Je[8][4])
+{
+    const double detJ = h[0] * h[1] * h[2] / 8.0;
+    const double rho = ph->rho, mu = ph->mu;
+    double G[3], trG = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        G[k] = 4.0 / (h[k] * h[k]);
+        trG += G[k];
+    }
+    memset(Je, 0, 8 * 4 * sizeof(double));
+    for (int g = 0; g < 8; ++g) {
+        gp_state st;
+        eval_gp(N, h, ex, ey, ez, g, U, A, f, ph->has_s, &st);
+        /* direction at the Gauss point */
+        double dv[3] = {0, 0, 0}, dgv[3][3] = {{0}}, dp = 0.0, dgp[3] = {0, 0, 0};
+        double da[3] = {0, 0, 0};
+        for (int a = 0; a < 8; ++a) {
+            for (int i = 0; i < 3; ++i) {
+                dv[i] += st.N[a] * c_v * xe[a][i];
+                da[i] += st.N[a] * c_a * xe[a][i];
+                for (int j = 0; j < 3; ++j) dgv[i][j] += st.dN[a][j] * c_v * xe[a][i];
+            }
+            dp += st.N[a] * xe[a][3];
+            for (int j = 0; j < 3; ++j) dgp[j] += st.dN[a][j] * xe[a][3];
+        }
+        /* base state */
+        double conv[3], rM[3], up[3];
+        for (int i = 0; i < 3; ++i) {
+            conv[i] = 0.0;
+            for (int j = 0; j < 3; ++j) conv[i] += st.v[j] * st.gv[i][j];
+            rM[i] = rho * (st.a[i] + conv[i] - st.f[i]) + st.gp[i];
+        }
+        double rC = st.gv[0][0] + st.gv[1][1] + st.gv[2][2];
+        double tau[2];
+        or_tau(st.v, st.s, h, rho, mu, ph->ct_dt2, ph->C_I, tau);
+        double tauM = tau[0], tauC = tau[1];
+        for (int i = 0; i < 3; ++i) up[i] = -(tauM / rho) * rM[i];
+        /* derivatives */
+        double dconv[3], drM[3], dup[3];
+        for (int i = 0; i < 3; ++i) {
+            dconv[i] = 0.0;
+            for (int j = 0; j < 3; ++j) dconv[i] += dv[j] * st.gv[i][j] + st.v[j] * dgv[i][j];
+            drM[i] = rho * (da[i] + dconv[i]) + dgp[i];
+        }
+        double drC = dgv[0][0] + dgv[1][1] + dgv[2][2];
+        /* tau_M = (s Q)^(-1/2), Q = C_T/dt^2 + v.G v + C_I nu^2 G:G
+         * d tau_M = -1/2 tau_M^3 s dQ, dQ = 2 v.G dv ;
+         * tau_C = 1/(tau_M trG) -> d tau_C = -tau_C d tau_M / tau_M          */
+        double dQ = 0.0;
+        for (int k = 0; k < 3; ++k) dQ += 2.0 * st.v[k] * G[k] * dv[k];
+        double dtauM = -0.5 * tauM * tauM * tauM * st.s * dQ;
+        double dtauC = -tauC * dtauM / tauM;
+        for (int i = 0; i < 3; ++i) dup[i] = -(dtauM * rM[i] + tauM * drM[i]) / rho;
+        double dpp = -rho * (dtauC * rC + tauC * drC);
+
+        for (int A_ = 0; A_ < 8; ++A_) {
+            const double NA = st.N[A_];
+            const double *dNA = st.dN[A_];
+            double vgradN = 0.0, dvgradN = 0.0;
+            for (int j = 0; j < 3; ++j) {
+                vgradN += st.v[j] * dNA[j];
+                dvgradN += dv[j] * dNA[j];
+            }
+            for (int i = 0; i < 3; ++i) {
+                double t = NA * rho * (da[i] + dconv[i]);
+                for (int j = 0; j < 3; ++j) t += dNA[j] * mu * (dgv[i][j] + dgv[j][i]);
+                t -= dNA[i] * dp;
+                t -= rho * (dvgradN * up[i] + vgradN * dup[i]);
+                t -= dNA[i] * dpp;
+                for (int j = 0; j < 3; ++j)
+                    t += NA * rho * (dup[j] * st.gv[i][j] + up[j] * dgv[i][j]);
+                for (int j = 0; j < 3; ++j)
+                    t -= rho * dNA[j] * (dup[i] * up[j] + up[i] * dup[j]);
+                Je[A_][i] += detJ * t;
+            }
+            double c = NA * drC;
+            for (int j = 0; j < 3; ++j) c -= dNA[j] * dup[j];
+            Je[A_][3] += detJ * c;
+        }
+    }
+}
+
+static void set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+/* Assembled VMS residual R[n][4] (Sec. 2.1, Eq. fluid_weak_form + VMS).
+ * f may be NULL (no body force).                                            */
+void or_residual(const int N[3], const double h[3], const double phys[5],
+                 const double *U, const double *A, const double *f, int stab,
+                 double *R, int nthreads)
+{
+    or_phys ph = unpack_phys(phys);
+    int64_t E = (int64_t)N[0] * N[1] * N[2];
+    int64_t n = (int64_t)(N[0] + 1) * (N[1] + 1) * (N[2] + 1);
+    double *Rel = (double *)malloc((size_t)E * 32 * sizeof(double));
+    set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < E; ++e) {
+        int ex = (int)(e % N[0]), ey = (int)((e / N[0]) % N[1]), ez = (int)(e / ((int64_t)N[0] * N[1]));
+        element_residual(N, h, &ph, ex, ey, ez, U, A, f, stab, (double(*)[4])(Rel + 32 * e));
+    }
+    memset(R, 0, (size_t)n * 4 * sizeof(double));
+    for (int64_t e = 0; e < E; ++e) {
+        int ex = (int)(e % N[0]), ey = (int)((e / N[0]) % N[1]), ez = (int)(e / ((int64_t)N[0] * N[1]));
+        for (int a = 0; a < 8; ++a) {
+            int64_t nd = elem_node(N, ex, ey, ez, a);
+            for (int c = 0; c < 4; ++c) R[4 * nd + c] += Rel[32 * e + 4 * a + c];
+        }
+    }
+    free(Rel);
+}
+
+/* Assembled Jacobian-vector product Jx[n][4] of or_residual (stab = 1). */
+void or_jacobian_apply(const int N[3], const double h[3], const double phys[5],
+                       const double *U, const double *A, const double *f,
+                       const double *x, double c_a, double c_v, double *Jx, int nthreads)
+{
+    or_phys ph = unpack_phys(phys);
+    int64_t E = (int64_t)N[0] * N[1] * N[2];
+    int64_t n = (int64_t)(N[0] + 1) * (N[1] + 1) * (N[2] + 1);
+    double *Jel = (double *)malloc((size_t)E * 32 * sizeof(double));
+    set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < E; ++e) {
+        int ex = (int)(e % N[0]), ey = (int)((e / N[0]) % N[1]), ez = (int)(e / ((int64_t)N[0] * N[1]));
+        double xe[8][4];
+        for (int a = 0; a < 8; ++a) {
+            int64_t nd = elem_node(N, ex, ey, ez, a);
+            for (int c = 0; c < 4; ++c) xe[a][c] = x[4 * nd + c];
+        }
+        element_jacobian_apply(N, h, &ph, ex, ey, ez, U, A, f, (const double(*)[4])xe, c_a, c_v,
+                               (double(*)[4])(Jel + 32 * e));
+    }
+    memset(Jx, 0, (size_t)n * 4 * sizeof(double));
+    for (int64_t e = 0; e < E; ++e) {
+        int ex = (int)(e % N[0]), ey = (int)((e / N[0]) % N[1]), ez = (int)(e / ((int64_t)N[0] * N[1]));
+        for (int a = 0; a < 8; ++a) {
+            int64_t nd = elem_node(N, ex, ey, ez, a);
+            for (int c = 0; c < 4; ++c) Jx[4 * nd + c] += Jel[32 * e + 4 * a + c];
+        }
+    }
+    free(Jel);
+}
+
+/* Element tangent matrices Ke[E][32][32], column (4b+d) = element Jacobian
+ * applied to the unit direction at local node b, component d.  Used by the
+ * oracle's direct Newton solves on small grids.  conn[E][8] receives the
+ * global node of each local node.                                           */
+void or_element_jacobian(const int N[3], const double h[3], const double phys[5],
+                         const double *U, const double *A, const double *f, double c_a,
+                         double c_v, double *Ke, int64_t *conn, int nthreads)
+{
+    or_phys ph = unpack_phys(phys);
+    int64_t E = (int64_t)N[0] * N[1] * N[2];
+    set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < E; ++e) {
+        int ex = (int)(e % N[0]), ey = (int)((e / N[0]) % N[1]), ez = (int)(e / ((int64_t)N[0] * N[1]));
+        for (int a = 0; a < 8; ++a) conn[8 * e + a] = elem_node(N, ex, ey, ez, a);
+        for (int col = 0; col < 32; ++col) {
+            double xe[8][4] = {{0}};
+            double Je[8][4];
+            xe[col / 4][col % 4] = 1.0;
+            element_jacobian_apply(N, h, &ph, ex, ey, ez, U, A, f, (const double(*)[4])xe, c_a,
+                                   c_v, Je);
+            for (int row = 0; row < 32; ++row)
+                Ke[(int64_t)1024 * e + 32 * row + col] = Je[row / 4][row % 4];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Point location on the uniform grid (the role of the point search of
+ * Sec. 3 / Algorithm 1: element number and parametric position xi).
+ * t_k = (X_k - x0_k)/h_k ; a point is outside unless 0 <= t_k <= N_k for all
+ * k; e_k = min(floor(t_k), N_k - 1) ; xi_k = 2 (t_k - e_k) - 1.
+ * Outside points get elem = -1 and xi = 0.  Returns the outside count.      */
+int64_t or_locate(const int N[3], const double x0[3], const double h[3], int64_t m,
+                  const double *X, int32_t *elem, double *xi)
+{
+    int64_t outside = 0;
+    for (int64_t b = 0; b < m; ++b) {
+        double t[3];
+        int e[3], in = 1;
+        for (int k = 0; k < 3; ++k) {
+            t[k] = (X[3 * b + k] - x0[k]) / h[k];
+            if (!(t[k] >= 0.0 && t[k] <= (double)N[k])) in = 0;
+        }
+        if (!in) {
+            elem[b] = -1;
+            xi[3 * b] = xi[3 * b + 1] = xi[3 * b + 2] = 0.0;
+            ++outside;
+            continue;
+        }
+        for (int k = 0; k < 3; ++k) {
+            e[k] = (int)floor(t[k]);
+            if (e[k] > N[k] - 1) e[k] = N[k] - 1;
+            xi[3 * b + k] = 2.0 * (t[k] - (double)e[k]) - 1.0;
+        }
+        elem[b] = (int32_t)(e[0] + N[0] * (e[1] + N[1] * e[2]));
+    }
+    return outside;
+}
+
+/* Cell -> points CSR by a stable counting sort on the element number:
+ * cell_start[E+1], perm[m] lists the inside points cell by cell in
+ * increasing point index, then the outside points in increasing index.     */
+void or_cell_hash(const int N[3], int64_t m, const int32_t *elem, int32_t *cell_start,
+                  int32_t *perm)
+{
+    int64_t E = (int64_t)N[0] * N[1] * N[2];
+    memset(cell_start, 0, (size_t)(E + 1) * sizeof(int32_t));
+    for (int64_t b = 0; b < m; ++b)
+        if (elem[b] >= 0) cell_start[elem[b] + 1] += 1;
+    for (int64_t c = 0; c < E; ++c) cell_start[c + 1] += cell_start[c];
+    int32_t *cursor = (int32_t *)malloc((size_t)(E + 1) * sizeof(int32_t));
+    memcpy(cursor, cell_start, (size_t)(E + 1) * sizeof(int32_t));
+    int64_t tail = cell_start[E];
+    for (int64_t b = 0; b < m; ++b) {
+        if (elem[b] >= 0)
+            perm[cursor[elem[b]]++] = (int32_t)b;
+        else
+            perm[tail++] = (int32_t)b;
+    }
+    free(cursor);
+}
+
+/* Interpolation of Eq. (nodal_solid_velo): u_B = sum_A N_A(xi_B) v_A over
+ * the 8 nodes of the element holding point B (velocity components only).
+ * Outside points (elem < 0) get u = 0.                                      */
+void or_interp(const int N[3], int64_t m, const int32_t *elem, const double *xi,
+               const double *U, double *u)
+{
+    for (int64_t b = 0; b < m; ++b) {
+        u[3 * b] = u[3 * b + 1] = u[3 * b + 2] = 0.0;
+        if (elem[b] < 0) continue;
+        int e = elem[b];
+        int ex = e % N[0], ey = (e / N[0]) % N[1], ez = e / (N[0] * N[1]);
+        double Nv[8], dN[24];
+        or_shape(xi + 3 * b, Nv, dN);
+        for (int a = 0; a < 8; ++a) {
+            int64_t nd = elem_node(N, ex, ey, ez, a);
+            for (int i = 0; i < 3; ++i) u[3 * b + i] += Nv[a] * U[4 * nd + i];
+        }
+    }
+}
+
+/* Spreading with the FSI constraint matrix of Eq. (fsi_constraint_matrix):
+ * F_A += sum_B w_B N_A(xi_B) lambda_B into the momentum slots; the pressure
+ * slot is neither read nor written.  w may be NULL (w_B = 1).  accumulate = 0
+ * first sets the momentum slots to zero.                                    */
+void or_spread(const int N[3], int64_t m, const int32_t *elem, const double *xi,
+               const double *lam, const double *w, double *F, int accumulate)
+{
+    int64_t n = (int64_t)(N[0] + 1) * (N[1] + 1) * (N[2] + 1);
+    if (!accumulate)
+        for (int64_t a = 0; a < n; ++a) F[4 * a] = F[4 * a + 1] = F[4 * a + 2] = 0.0;
+    for (int64_t b = 0; b < m; ++b) {
+        if (elem[b] < 0) continue;
+        int e = elem[b];
+        int ex = e % N[0], ey = (e / N[0]) % N[1], ez = e / (N[0] * N[1]);
+        double Nv[8], dN[24];
+        or_shape(xi + 3 * b, Nv, dN);
+        double wb = w ? w[b] : 1.0;
+        for (int a = 0; a < 8; ++a) {
+            int64_t nd = elem_node(N, ex, ey, ez, a);
+            for (int i = 0; i < 3; ++i) F[4 * nd + i] += wb * Nv[a] * lam[3 * b + i];
+        }
+    }
+}

@@ -1,0 +1,123 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module only draws random numbers and lays out geometry; it holds none of
+the method's arithmetic (no shape functions, no residual, no time
+integration).  Everything is numpy float64 on the host.
+
+Workload shapes follow the paper's problems: a uniform background hex grid on
+the unit cube, immersed thin leaflet-like solids sampled as point clouds (the
+paper's valve leaflets are 0.015-0.0212 thick), and random multipliers.
+
+Recipes (every array is drawn from ``numpy.random.default_rng(seed)``):
+
+* ``uniform_state``   -- nodal unknown y ~ U[-1, 1] i.i.d., history zero.
+* ``fourier_field``   -- per component a sum of separable sinusoids with
+  wavenumbers 1..8 per axis and random phases/amplitudes, normalised to
+  max |v| = 1, plus N(0, 0.01^2) noise.
+* ``ball_points``     -- points uniform in a ball.
+* ``leaflet_points``  -- three cylindrical-sector shells about the x axis
+  through (0.5, 0.5): radius 0.29..0.31, x in [0.1, 0.9], arc 0.5 at radius
+  0.3 (95.5 deg), centred 120 deg apart, uniform in volume.
+* ``multipliers``     -- lambda ~ N(0, 1) per component.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(seed)
+
+
+def n_nodes(N) -> int:
+    if np.isscalar(N):
+        N = (N, N, N)
+    return (N[0] + 1) * (N[1] + 1) * (N[2] + 1)
+
+
+def uniform_state(N, seed: int, lo: float = -1.0, hi: float = 1.0):
+    """y[n,4] ~ U[lo,hi] and zero history (Vn, An) -- the one-step workload."""
+    g = rng(seed)
+    n = n_nodes(N)
+    y = g.uniform(lo, hi, size=(n, 4))
+    Vn = np.zeros((n, 4))
+    An = np.zeros((n, 4))
+    return y, Vn, An
+
+
+def uniform_nodal(N, seed: int, ncomp: int = 4, lo: float = -1.0, hi: float = 1.0):
+    g = rng(seed)
+    return g.uniform(lo, hi, size=(n_nodes(N), ncomp))
+
+
+def fourier_field(N, seed: int, modes: int = 8, noise: float = 0.01, ncomp: int = 4):
+    """Smooth random field on the nodes of an N^3 unit-cube grid, [n, ncomp]."""
+    if np.isscalar(N):
+        N = (N, N, N)
+    g = rng(seed)
+    ax = [np.arange(N[k] + 1) / N[k] for k in range(3)]
+    k = np.arange(1, modes + 1)
+    out = np.empty((n_nodes(N), ncomp))
+    for c in range(ncomp):
+        S = []
+        for d in range(3):
+            ph = g.uniform(0.0, 2.0 * math.pi, size=modes)
+            S.append(np.sin(2.0 * math.pi * np.outer(ax[d], k) + ph[None, :]))
+        amp = g.normal(size=(modes, modes, modes)) / (1.0 + k[:, None, None] ** 2
+                                                     + k[None, :, None] ** 2
+                                                     + k[None, None, :] ** 2)
+        # field[z, y, x] = sum_{kz,ky,kx} amp[kx,ky,kz] Sx[x,kx] Sy[y,ky] Sz[z,kz]
+        f = np.einsum("abc,xa,yb,zc->zyx", amp, S[0], S[1], S[2], optimize=True)
+        f /= np.abs(f).max()
+        f += g.normal(scale=noise, size=f.shape)
+        out[:, c] = f.ravel()
+    return out
+
+
+def ball_points(m: int, seed: int, center=(0.5, 0.5, 0.5), radius: float = 0.3):
+    g = rng(seed)
+    d = g.normal(size=(m, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = radius * g.uniform(0.0, 1.0, size=m) ** (1.0 / 3.0)
+    return np.asarray(center)[None, :] + r[:, None] * d
+
+
+def leaflet_points(m: int, seed: int, theta0: float | None = None, radius: float = 0.3,
+                   thickness: float = 0.02, length: float = 0.8, arc: float = 0.5,
+                   axis_center=(0.5, 0.5)):
+    """m points uniform in the volume of three thin cylindrical-sector shells."""
+    g = rng(seed)
+    if theta0 is None:
+        theta0 = g.uniform(0.0, 2.0 * math.pi)
+    which = g.integers(0, 3, size=m)
+    half = 0.5 * arc / radius
+    r0, r1 = radius - 0.5 * thickness, radius + 0.5 * thickness
+    r = np.sqrt(g.uniform(r0 * r0, r1 * r1, size=m))
+    th = theta0 + which * (2.0 * math.pi / 3.0) + g.uniform(-half, half, size=m)
+    x = g.uniform(0.5 - 0.5 * length, 0.5 + 0.5 * length, size=m)
+    y = axis_center[0] + r * np.cos(th)
+    z = axis_center[1] + r * np.sin(th)
+    return np.stack([x, y, z], axis=1)
+
+
+def multipliers(m: int, seed: int):
+    return rng(seed).normal(size=(m, 3))
+
+
+def edge_points(N, seed: int, m_random: int = 64):
+    """Points on nodes, faces, edges, corners, the far boundary and outside."""
+    if np.isscalar(N):
+        N = (N, N, N)
+    g = rng(seed)
+    pts = []
+    for i in (0, N[0] // 2, N[0]):
+        for j in (0, N[1]):
+            for k in (0, N[2] // 3, N[2]):
+                pts.append((i / N[0], j / N[1], k / N[2]))
+    pts += [(0.5, 0.5, 1.0), (1.0, 1.0, 1.0), (0.0, 0.0, 0.0), (1.0, 0.25, 0.5)]
+    pts += [(-1e-9, 0.5, 0.5), (0.5, 1.0 + 1e-9, 0.5), (0.5, 0.5, 2.0), (-3.0, -3.0, -3.0)]
+    pts += [(float("nan"), 0.5, 0.5)]
+    R = g.uniform(-0.1, 1.1, size=(m_random, 3))
+    return np.concatenate([np.asarray(pts, dtype=np.float64), R], axis=0)

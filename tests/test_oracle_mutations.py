@@ -1,0 +1,50 @@
+"""Plant plausible mistakes in a copy of the C oracle and check that the pins
+catch each one (a sign flip, a transposed gradient, a dropped term, a wrong
+index, a dropped tau derivative).  The mistakes are planted on the CPU in a
+temporary copy; the committed oracle is never modified."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = {
+    "cross_term_sign": ("t += NA * rho * up[j] * st.gv[i][j];",
+                        "t -= NA * rho * up[j] * st.gv[i][j];"),
+    "convection_transposed": ("conv[i] += st.v[j] * st.gv[i][j];\n            rM[i]",
+                              "conv[i] += st.v[j] * st.gv[j][i];\n            rM[i]"),
+    "supg_sign": ("t -= rho * vgradN * up[i];", "t += rho * vgradN * up[i];"),
+    "lsic_dropped": ("t -= dNA[i] * pp;", ";"),
+    "reynolds_index": ("t -= rho * dNA[j] * up[i] * up[j];",
+                       "t -= rho * dNA[i] * up[j] * up[j];"),
+    "pspg_sign": ("for (int j = 0; j < 3; ++j) c -= dNA[j] * up[j];\n            Re",
+                  "for (int j = 0; j < 3; ++j) c += dNA[j] * up[j];\n            Re"),
+    "viscous_not_symmetric": ("t += dNA[j] * mu * (st.gv[i][j] + st.gv[j][i]);",
+                              "t += dNA[j] * mu * (st.gv[i][j] + st.gv[i][j]);"),
+    "tau_time_term_dropped": ("sqrt(s * (ct_dt2 + vGv", "sqrt(s * (0.0 * ct_dt2 + vGv"),
+    "jacobian_dtau_dropped": ("double dtauM = -0.5 * tauM * tauM * tauM * st.s * dQ;",
+                              "double dtauM = 0.0;"),
+    "interp_node_order": ("return node_id(N, ex + (a & 1), ey + ((a >> 1) & 1), ez + ((a >> 2) & 1));",
+                          "return node_id(N, ex + ((a >> 1) & 1), ey + (a & 1), ez + ((a >> 2) & 1));"),
+    "locate_xi_sign": ("xi[3 * b + k] = 2.0 * (t[k] - (double)e[k]) - 1.0;",
+                       "xi[3 * b + k] = 1.0 - 2.0 * (t[k] - (double)e[k]);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    src = open(os.path.join(ROOT, "oracle", "fsi_oracle.c")).read()
+    old, new = MUTATIONS[name]
+    assert old in src, f"mutation anchor for {name} no longer in the oracle"
+    (tmp_path / "fsi_oracle.c").write_text(src.replace(old, new, 1))
+    lib = tmp_path / "liboracle.so"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", str(lib),
+                           str(tmp_path / "fsi_oracle.c"), "-lm"])
+    env = dict(os.environ, FSI_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        "tests/test_oracle_vms.py", "tests/test_oracle_dlm.py",
+                        "-k", "not manufactured and not quadratic"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"planted mistake {name} was not caught:\n{r.stdout[-2000:]}"
