@@ -1,0 +1,434 @@
+#!/usr/bin/env python3
+"""Benchmark of the immersed-FSI hot path on GB300.
+
+One step = one pass of the operator path over the 64^3 workload (background
+hex grid 64^3 = 262,144 elements, 274,625 nodes, 1,098,500 DOFs; smooth
+seeded Fourier velocity/pressure plus noise; three thin leaflets sampled as
+200,000 solid points):
+
+  stage (generalized alpha) -> VMS residual -> VMS Jacobian apply ->
+  locate + cell table -> interpolation C^T V -> spreading C lambda
+
+in FP64 (the plain method).  The same operators in FP32 are timed in a second
+loop and reported under "ops_f32".  value = DOFs (4 per node) passed through
+the step per second, in GDOF/s.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs its own replica (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "GDOF/s VMS Jacobian apply; s/Newton step at 1e-8 resid, mixed+learned vs FP64"
+UNIT = "GDOF/s"
+WORKLOAD = "64^3 Q1-Q1 VMS grid + 200k leaflet points (stage, residual, Jacobian apply, locate, interp, spread)"
+N_GRID = 64
+M_POINTS = 200_000
+SEED = 2026
+# Kernel launches per step issued by the library (stage 1, residual 2,
+# Jacobian 2, locate 1 + scan 3 + scatter 1 + sort 1, interp 1, spread 1).
+LAUNCHES_PER_STEP = 13
+# Algorithmic FP64/FP32 operations per element of one VMS Jacobian apply and
+# one residual (FMA = 2 flops), counted from the kernel's arithmetic.
+FLOPS_PER_ELEM = {"jacobian": 4928.0, "residual": 2992.0}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(N=N_GRID, m=M_POINTS, seed=SEED):
+    from paper_2601_08266_gb300 import inputs
+    n = inputs.n_nodes(N)
+    Vn = inputs.fourier_field(N, seed=seed)
+    An = inputs.fourier_field(N, seed=seed + 1)
+    y = inputs.fourier_field(N, seed=seed + 2)
+    x = inputs.uniform_nodal(N, seed=seed + 3)
+    X = inputs.leaflet_points(m, seed=seed + 4)
+    lam = inputs.multipliers(m, seed=seed + 5)
+    return dict(N=N, n=n, m=m, y=y, Vn=Vn, An=An, x=x, X=X, lam=lam)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------ oracle arm
+def oracle_pass(W, grid, phys, c_a, c_v, nthreads=0):
+    import oracle.core as oc
+    import oracle.timeint as ot
+    U, A = ot.stage(W["y"], W["Vn"], W["An"], phys["dt"], phys["rho_inf"])
+    oc.residual(grid, phys, U, A, nthreads=nthreads)
+    oc.jacobian_apply(grid, phys, U, A, W["x"], c_a, c_v, nthreads=nthreads)
+    elem, xi, _ = oc.locate(grid, W["X"])
+    oc.cell_hash(grid, elem)
+    oc.interp(grid, elem, xi, U)
+    oc.spread(grid, elem, xi, W["lam"])
+
+
+def cpu_oracle_rate(W, max_seconds=20.0, min_passes=1):
+    """Oracle FP64 passes over the full workload on all host cores."""
+    import oracle.core as oc
+    import oracle.timeint as ot
+    oc.build()
+    grid = oc.Grid(W["N"])
+    phys = dict(rho=1.0, mu=0.01, dt=1e-3, rho_inf=0.5)
+    c_a, c_v = ot.chain_factors(0.5, 1e-3)
+    passes, t0 = 0, time.perf_counter()
+    while passes < min_passes or time.perf_counter() - t0 < max_seconds * 0.5:
+        oracle_pass(W, grid, phys, c_a, c_v)
+        passes += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    el = time.perf_counter() - t0
+    return 4.0 * W["n"] * passes / el / 1e9, passes, el
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    W = make_workload()
+    import oracle.core as oc
+    import oracle.timeint as ot
+    oc.build()
+    grid = oc.Grid(W["N"])
+    phys = dict(rho=1.0, mu=0.01, dt=1e-3, rho_inf=0.5)
+    c_a, c_v = ot.chain_factors(0.5, 1e-3)
+    for _ in range(args.warmup):
+        oracle_pass(W, grid, phys, c_a, c_v)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_pass(W, grid, phys, c_a, c_v)
+    el = time.perf_counter() - t0
+    value = 4.0 * W["n"] * args.steps / el / 1e9
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [W["N"]] * 3, "points": W["m"],
+                   "l2": "CPU run"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full FP64 oracle passes over the workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    import paper_2601_08266_gb300 as fsi
+    from paper_2601_08266_gb300 import _binding as B
+
+    W = make_workload(seed=SEED + rank)
+    N, n, m = W["N"], W["n"], W["m"]
+    stream = torch.cuda.Stream(device=dev)
+    mesh = fsi.Mesh(N, rho=1.0, mu=0.01, dt=1e-3, rho_inf=0.5, device=local,
+                    stream=stream.cuda_stream)
+
+    def buffers(dtype):
+        b = {}
+        with torch.cuda.stream(stream):
+            for k in ("y", "Vn", "An", "x"):
+                b[k] = torch.as_tensor(W[k], device=dev).to(dtype).contiguous()
+            b["X"] = torch.as_tensor(W["X"], device=dev).contiguous()
+            b["lam"] = torch.as_tensor(W["lam"], device=dev).to(dtype).contiguous()
+            for k in ("U", "A", "R", "Jx", "F"):
+                b[k] = torch.zeros((n, 4), dtype=dtype, device=dev)
+            b["elem"] = torch.empty(m, dtype=torch.int32, device=dev)
+            b["xi"] = torch.empty((m, 3), dtype=torch.float64, device=dev)
+            b["cs"] = torch.empty(N ** 3 + 1, dtype=torch.int32, device=dev)
+            b["perm"] = torch.empty(m, dtype=torch.int32, device=dev)
+            b["u"] = torch.empty((m, 3), dtype=dtype, device=dev)
+        stream.synchronize()
+        return b
+
+    b64 = buffers(torch.float64)
+    P64 = fsi.FSI_F64
+    ops = ["stage", "residual", "jacobian", "locate", "interp", "spread"]
+
+    def step(b, P, ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        fsi.fsi_stage(mesh, P, b["y"], b["Vn"], b["An"], None, b["U"], b["A"])
+        mark(1)
+        fsi.fsi_residual(mesh, P, b["U"], b["A"], None, b["R"])
+        mark(2)
+        fsi.fsi_jacobian_apply(mesh, P, b["U"], b["A"], None, b["x"], b["Jx"])
+        mark(3)
+        fsi.fsi_locate(mesh, b["X"], b["elem"], b["xi"], b["cs"], b["perm"], want_outside=False)
+        mark(4)
+        fsi.fsi_dlm_interp(mesh, P, b["elem"], b["xi"], b["U"], b["u"])
+        mark(5)
+        fsi.fsi_dlm_spread(mesh, P, b["elem"], b["xi"], b["cs"], b["perm"], b["lam"], None,
+                           b["F"], False)
+        mark(6)
+
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device=dev)
+
+    def timed(run_step, K, Wm):
+        for _ in range(Wm):
+            run_step(None)
+        stream.synchronize()
+        per_op = np.zeros(len(ops))
+        total = 0.0
+        for _ in range(K):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)          # evict the working set from L2
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(ops) + 1)]
+            run_step(ev)
+            stream.synchronize()
+            d = [ev[i].elapsed_time(ev[i + 1]) for i in range(len(ops))]
+            per_op += d
+            total += ev[0].elapsed_time(ev[-1])
+        return total / K, per_op / K
+
+    sampler = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ms64, per64 = timed(lambda ev: step(b64, P64, ev), args.steps, args.warmup)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    # FP32 operators (xi cast once outside the timed loop)
+    b32 = buffers(torch.float32)
+    fsi.fsi_locate(mesh, b32["X"], b32["elem"], b32["xi"], b32["cs"], b32["perm"],
+                   want_outside=False)
+    xi32 = b32["xi"].to(torch.float32)
+    ops32 = ["residual", "jacobian", "interp", "spread"]
+
+    def step32(ev):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        fsi.fsi_residual(mesh, fsi.FSI_F32, b32["U"], b32["A"], None, b32["R"])
+        mark(1)
+        fsi.fsi_jacobian_apply(mesh, fsi.FSI_F32, b32["U"], b32["A"], None, b32["x"], b32["Jx"])
+        mark(2)
+        fsi.fsi_dlm_interp(mesh, fsi.FSI_F32, b32["elem"], xi32, b32["U"], b32["u"])
+        mark(3)
+        fsi.fsi_dlm_spread(mesh, fsi.FSI_F32, b32["elem"], xi32, b32["cs"], b32["perm"],
+                           b32["lam"], None, b32["F"], False)
+        mark(4)
+        for i in range(4, 7):
+            mark(i)
+
+    fsi.fsi_stage(mesh, fsi.FSI_F32, b32["y"], b32["Vn"], b32["An"], None, b32["U"], b32["A"])
+    ms32, per32 = timed(step32, args.steps, args.warmup)
+
+    # end to end through host buffers (pinned), FP64 step
+    h_in = {k: torch.as_tensor(W[k]).pin_memory() for k in ("y", "Vn", "An", "x", "X", "lam")}
+    h_out = {k: torch.empty(tuple(b64[k].shape), dtype=b64[k].dtype).pin_memory()
+             for k in ("R", "Jx", "u", "F")}
+    h2d = sum(t.numel() * t.element_size() for t in h_in.values())
+    d2h = sum(t.numel() * t.element_size() for t in h_out.values())
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            for k, t in h_in.items():
+                b64[k].copy_(t, non_blocking=True)
+        step(b64, P64)
+        with torch.cuda.stream(stream):
+            for k, t in h_out.items():
+                t.copy_(b64[k], non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    stream.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+
+    # max over ranks
+    t_step = ms64
+    if ws > 1:
+        t = torch.tensor([ms64, e2e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step, e2e_ms = float(t[0]), float(t[1])
+    value = ws * 4.0 * n / (t_step * 1e-3) / 1e9
+    e2e_val = ws * 4.0 * n / (e2e_ms * 1e-3) / 1e9
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+        return 0
+
+    # roofline of the dominant kernel (FP64 Jacobian apply: ALU bound)
+    fma64 = B.fsi_measure_fma_peak(local, fsi.FSI_F64)
+    fma32 = B.fsi_measure_fma_peak(local, fsi.FSI_F32)
+    E = N ** 3
+    jac_ms = per64[ops.index("jacobian")]
+    achieved = FLOPS_PER_ELEM["jacobian"] * E / (jac_ms * 1e-3)
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        traffic = tr.get("vms_jacobian_f64_64cubed_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+
+    def gdofs(ms):
+        return 4.0 * n / (ms * 1e-3) / 1e9
+
+    op_tab = {o: {"ms": round(float(t), 5), "gdof_s": round(gdofs(t), 4)} for o, t in zip(ops, per64)}
+    op_tab32 = {o: {"ms": round(float(t), 5), "gdof_s": round(gdofs(t), 4)}
+                for o, t in zip(ops32, per32[:4])}
+    # HBM-bound DLM operators: algorithmic bytes per launch
+    bytes_interp64 = m * (4 + 24 + 24)
+    bytes_spread64 = m * (4 + 4 + 24 + 24) + (E + 1) * 4 + n * 24
+    op_tab["interp"]["gb_s"] = round(bytes_interp64 / (per64[4] * 1e-3) / 1e9, 1)
+    op_tab["spread"]["gb_s"] = round(bytes_spread64 / (per64[5] * 1e-3) / 1e9, 1)
+    op_tab32["jacobian"]["tflop_s"] = round(FLOPS_PER_ELEM["jacobian"] * E / (per32[1] * 1e-3) / 1e12, 3)
+    op_tab32["jacobian"]["alu_frac"] = round(FLOPS_PER_ELEM["jacobian"] * E / (per32[1] * 1e-3) / fma32, 4)
+    op_tab["residual"]["tflop_s"] = round(FLOPS_PER_ELEM["residual"] * E / (per64[1] * 1e-3) / 1e12, 4)
+
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        rate, passes, el = cpu_oracle_rate(W, max_seconds=args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{passes} full FP64 oracle pass(es) of the step on the 64^3 workload "
+                         f"({el:.1f} s, OpenMP over elements)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N, N, N], "dofs": 4 * n, "points": m,
+                   "l2": "flushed between timed steps (write of a buffer > L2)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "roofline": {"bound": "alu", "kernel": "vms_jacobian f64 (brick + gather)",
+                     "achieved": achieved / 1e12, "peak": fma64 / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / fma64, "traffic": traffic,
+                     "peak_source": "measured FP64 FMA rate (fsi_measure_fma_peak, this run)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "clocks": clocks,
+        "ops_f64": op_tab,
+        "ops_f32": op_tab32,
+        "ms_per_step_f32_ops": ms32,
+        "alu_peaks_tflop_s": {"f64": fma64 / 1e12, "f32": fma32 / 1e12},
+        "hbm_peak_gbs": hbm,
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.barrier()
+    mesh.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,192 @@
+/*
+ * fsi.h -- C ABI of the GB300 immersed-FSI hot-path library (libfsi.so).
+ *
+ * The library evaluates, on one GPU, the data-parallel operators of the
+ * monolithic fictitious-domain / distributed-Lagrange-multiplier FSI method
+ * of arxiv 2601.08266 (Black et al., "An open-source computational framework
+ * for immersed fluid-structure interaction modeling using FEBio and MFEM"):
+ *
+ *   - the VMS-stabilised incompressible Navier-Stokes residual on a uniform
+ *     Q1-Q1 hexahedral background grid and its consistent Jacobian-vector
+ *     product (Sec. 2.1, Eq. fluid_weak_form, and the reduced block system of
+ *     Sec. 2.4);
+ *   - the coupling operators of Sec. 2.3: locating solid points in fluid
+ *     elements, interpolation u = C^T V (Eq. nodal_solid_velo) and spreading
+ *     F = C lambda (Eq. fsi_constraint_matrix);
+ *   - the Newton step on the reduced system (Sec. 2.4).
+ *
+ * Conventions (apply to every entry point unless its comment says otherwise):
+ *   - Every array argument is a DEVICE pointer on the mesh's device, owned by
+ *     the caller, contiguous, row-major.  Nodal fields are [n][4] with
+ *     n = (Nx+1)(Ny+1)(Nz+1) nodes numbered lexicographically, x fastest:
+ *     node(i,j,k) = i + (Nx+1)*(j + (Ny+1)*k).  Slots are (vx, vy, vz, p) for
+ *     velocity-pressure fields and (ax, ay, az, s) for the acceleration field
+ *     A, whose 4th slot carries the interface scaling s of Sec. 2.1 when the
+ *     mesh was created with has_s != 0 (it is ignored otherwise).
+ *     Elements are numbered e = ex + Nx*(ey + Ny*ez).
+ *   - fsi_prec selects the element type of the floating-point arrays of that
+ *     call: FSI_F64 = double, FSI_F32 = float.  Point coordinates X are always
+ *     double.
+ *   - Calls are asynchronous and stream-ordered on the mesh's stream, except
+ *     where a comment says the call synchronises.  Arrays must stay valid
+ *     until the stream has passed the call.
+ *   - Invalid arguments return FSI_ERR_ARG without launching anything; every
+ *     error also sets a thread-local message returned by fsi_last_error().
+ *     No C++ exception crosses this interface.
+ *   - The library allocates device memory only inside fsi_mesh objects (its
+ *     scratch); it never frees caller memory.
+ */
+#ifndef FSI_H
+#define FSI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FSI_OK = 0,
+    FSI_ERR_ARG = 1,      /* invalid argument; nothing was launched          */
+    FSI_ERR_CUDA = 2,     /* a CUDA runtime call or kernel launch failed      */
+    FSI_ERR_OOM = 3,      /* device allocation failed                         */
+    FSI_ERR_OUTSIDE = 4,  /* strict locate: some point lies outside the grid  */
+    FSI_ERR_NOCONV = 5,   /* Newton did not reach its tolerance               */
+    FSI_ERR_TIMEOUT = 6,  /* a bounded device wait gave up                    */
+    FSI_ERR_NAN = 7       /* a non-finite norm was met                        */
+} fsi_status;
+
+typedef enum { FSI_F64 = 0, FSI_F32 = 1 } fsi_prec;
+
+/* Opaque handle: grid, physics, stream, tuning and library-owned scratch. */
+typedef struct fsi_mesh fsi_mesh;
+
+/* Uniform axis-aligned hexahedral grid: N[k] elements of size h[k] along
+ * axis k starting at x0[k] (the unfitted background fluid mesh, Sec. 2). */
+typedef struct {
+    int32_t N[3];
+    double x0[3];
+    double h[3];
+} fsi_grid;
+
+/* Fluid and time-integration parameters.
+ *   rho, mu  fluid density and dynamic viscosity (Eq. fluid_weak_form);
+ *   dt       time step; rho_inf spectral radius of the generalized-alpha
+ *            method (Sec. 2.4) giving alpha_m = (3-rho_inf)/(2(1+rho_inf)),
+ *            alpha_f = 1/(1+rho_inf), gamma = 1/2 + alpha_m - alpha_f;
+ *   C_I, C_T constants of tau_m (Sec. 2.1; the paper uses 36 and 4);
+ *   has_s    nonzero: the 4th slot of A holds the nodal scaling field s of
+ *            Sec. 2.1, interpolated like the pressure; zero: s = 1.        */
+typedef struct {
+    double rho, mu, dt, rho_inf, C_I, C_T;
+    int32_t has_s;
+    int32_t reserved;
+} fsi_physics;
+
+/* Create a mesh handle on CUDA device `device`, issuing work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * Allocates the handle's scratch.  Returns FSI_ERR_ARG for N[k] < 1,
+ * h[k] <= 0, rho <= 0, mu < 0, dt <= 0, or a grid with more than 2^31-1
+ * nodes; FSI_ERR_OOM when scratch cannot be allocated.                    */
+fsi_status fsi_mesh_create(const fsi_grid *grid, const fsi_physics *phys, int device,
+                           void *cuda_stream, fsi_mesh **out);
+
+/* Release the handle and its scratch (synchronises its stream).  NULL ok. */
+void fsi_mesh_destroy(fsi_mesh *mesh);
+
+/* Change the stream subsequent calls are issued on. */
+fsi_status fsi_mesh_set_stream(fsi_mesh *mesh, void *cuda_stream);
+
+/* Replace the physics parameters (same validation as fsi_mesh_create). */
+fsi_status fsi_mesh_set_physics(fsi_mesh *mesh, const fsi_physics *phys);
+
+/* Number of nodes n and elements E of the mesh (host outputs, may be NULL). */
+fsi_status fsi_mesh_sizes(const fsi_mesh *mesh, int64_t *n_nodes, int64_t *n_elems);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char *fsi_last_error(void);
+
+/* Generalized-alpha stage values (Sec. 2.4).  From the unknown
+ * y = (Vdot_{n+1}, P_{n+1}) [n][4] and the history Vn = (V_n, -) and
+ * An = (Vdot_n, -) [n][4]:
+ *   V_{n+1}     = V_n + dt Vdot_n + gamma dt (Vdot_{n+1} - Vdot_n)
+ *   U = (V_n + alpha_f (V_{n+1} - V_n),  P_{n+1})
+ *   A = (Vdot_n + alpha_m (Vdot_{n+1} - Vdot_n),  s)
+ * s [n] (same precision) fills A's 4th slot; NULL writes 1.  Slot 4 of Vn
+ * and An is ignored.                                                       */
+fsi_status fsi_stage(fsi_mesh *mesh, fsi_prec prec, const void *y, const void *Vn,
+                     const void *An, const void *s, void *U, void *A);
+
+/* VMS residual R [n][4] (Sec. 2.1): the Galerkin form of Eq. fluid_weak_form
+ * with the residual-based VMS terms (SUPG, PSPG, LSIC, cross and Reynolds
+ * stress) of Bazilevs et al. 2007, tau_m and tau_c of Sec. 2.1, 2x2x2 Gauss
+ * quadrature.  U = (v, p) and A = (a, s) are the stage values; f [n][4]
+ * (slots 0..2) is a nodal body force or NULL.  Rows 0..2 of each node are
+ * the momentum residual R^{f,m}, row 3 the continuity residual R^{f,c}.
+ * Boundary conditions are not applied (natural traction-free boundaries).
+ * R is overwritten; it must not alias any input.  Deterministic: the same
+ * inputs give bitwise the same R.                                          */
+fsi_status fsi_residual(fsi_mesh *mesh, fsi_prec prec, const void *U, const void *A,
+                        const void *f, void *R);
+
+/* Consistent Jacobian-vector product Jx [n][4] of fsi_residual with respect
+ * to the unknown y = (Vdot_{n+1}, P_{n+1}) of the reduced system of Sec. 2.4
+ * at the stage (U, A): the exact directional derivative of R in the
+ * direction dU = (alpha_f gamma dt x_v, x_p), dA = (alpha_m x_v, 0),
+ * including the dependence of tau_m and tau_c on v.  f as in fsi_residual
+ * (the Jacobian depends on it through the strong residual inside the fine
+ * scales u').  Jx must not alias any input.  Deterministic.               */
+fsi_status fsi_jacobian_apply(fsi_mesh *mesh, fsi_prec prec, const void *U, const void *A,
+                              const void *f, const void *x, void *Jx);
+
+/* Point location on the grid plus the cell -> points table (the point search
+ * that builds C^lambda, Sec. 3 and Algorithm 1).  For each of the m points
+ * X [m][3] (double):  t_k = (X_k - x0_k)/h_k; the point is outside unless
+ * 0 <= t_k <= N_k for every k (NaN counts as outside); otherwise
+ * e_k = min(floor(t_k), N_k - 1), elem = e_x + Nx (e_y + Ny e_z) and
+ * xi_k = 2 (t_k - e_k) - 1 in [-1, 1].  Outside points get elem = -1 and
+ * xi = 0.  cell_start [E+1] and perm [m] (int32, may both be NULL to skip)
+ * receive a stable counting sort of the inside points by element:
+ * the points of element e are perm[cell_start[e] .. cell_start[e+1]) in
+ * increasing index order, followed in perm by the outside points in
+ * increasing index order.  n_outside (HOST pointer, may be NULL) receives
+ * the number of outside points; passing it makes the call synchronise.
+ * strict != 0 returns FSI_ERR_OUTSIDE (after completing all outputs) when
+ * some point is outside.  m may be 0.  m must be < 2^31.                   */
+fsi_status fsi_locate(fsi_mesh *mesh, int64_t m, const double *X, int32_t *elem, double *xi,
+                      int32_t *cell_start, int32_t *perm, int64_t *n_outside, int strict);
+
+/* Interpolation of the fluid velocity to the solid points, u = C^T V
+ * (Eq. nodal_solid_velo): u_B = sum_A N_A(xi_B) V_A over the 8 nodes of
+ * element elem[B], velocity slots only.  xi [m][3] and U [n][4] and u [m][3]
+ * are in `prec`; elem [m] int32 from fsi_locate.  Outside points (elem < 0)
+ * get u = 0; so do points whose elem is >= E (never produced by
+ * fsi_locate), which are never dereferenced.                               */
+fsi_status fsi_dlm_interp(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_t *elem,
+                          const void *xi, const void *U, void *u);
+
+/* Spreading with the FSI constraint matrix C_AB = N_A(xi_B) I
+ * (Eq. fsi_constraint_matrix): F_A += sum_B w_B N_A(xi_B) lambda_B into the
+ * momentum slots 0..2 of F [n][4]; slot 3 is neither read nor written.
+ * accumulate == 0 overwrites slots 0..2 instead of adding.  lam [m][3],
+ * w [m] (NULL: w_B = 1), xi [m][3] and F are in `prec`.  elem, cell_start
+ * and perm are the outputs of fsi_locate for the same points.  The sum for
+ * each node runs over its (up to) 8 cells in a fixed order and over each
+ * cell's points in perm order, so the result is deterministic and no atomic
+ * operation is used.                                                       */
+fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_t *elem,
+                          const void *xi, const int32_t *cell_start, const int32_t *perm,
+                          const void *lam, const void *w, void *F, int accumulate);
+
+/* Measurement helper (the paper has no counterpart): the device's sustained
+ * FMA throughput on the CUDA cores in `prec`, in FLOP/s (an FMA counts as 2),
+ * from a dependent-chain FMA kernel over all SMs timed with CUDA events
+ * (best of 3).  It is the ALU roofline of the VMS operators.  Uses its own
+ * stream and a small buffer it allocates and frees; synchronises.          */
+fsi_status fsi_measure_fma_peak(int device, fsi_prec prec, double *flops_per_second);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSI_H */

@@ -1,0 +1,216 @@
+"""Thin ctypes binding of libfsi (include/fsi.h).
+
+Argument marshalling only: every operator runs in the CUDA library.  Array
+arguments are torch tensors on the mesh's device (contiguous; float64 or
+float32 as the precision says; int32 for indices); ``None`` maps to NULL.
+There is no CPU fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+FSI_OK, FSI_ERR_ARG, FSI_ERR_CUDA, FSI_ERR_OOM, FSI_ERR_OUTSIDE = 0, 1, 2, 3, 4
+FSI_ERR_NOCONV, FSI_ERR_TIMEOUT, FSI_ERR_NAN = 5, 6, 7
+FSI_F64, FSI_F32 = 0, 1
+STATUS_NAMES = {0: "FSI_OK", 1: "FSI_ERR_ARG", 2: "FSI_ERR_CUDA", 3: "FSI_ERR_OOM",
+                4: "FSI_ERR_OUTSIDE", 5: "FSI_ERR_NOCONV", 6: "FSI_ERR_TIMEOUT",
+                7: "FSI_ERR_NAN"}
+
+
+class FsiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class fsi_grid(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32 * 3), ("x0", ctypes.c_double * 3),
+                ("h", ctypes.c_double * 3)]
+
+
+class fsi_physics(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("mu", ctypes.c_double), ("dt", ctypes.c_double),
+                ("rho_inf", ctypes.c_double), ("C_I", ctypes.c_double),
+                ("C_T", ctypes.c_double), ("has_s", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_INT = ctypes.c_int
+_SIGS = {
+    "fsi_mesh_create": ([ctypes.POINTER(fsi_grid), ctypes.POINTER(fsi_physics), _INT, _VP,
+                         ctypes.POINTER(_VP)], _INT),
+    "fsi_mesh_destroy": ([_VP], None),
+    "fsi_mesh_set_stream": ([_VP, _VP], _INT),
+    "fsi_mesh_set_physics": ([_VP, ctypes.POINTER(fsi_physics)], _INT),
+    "fsi_mesh_sizes": ([_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], _INT),
+    "fsi_last_error": ([], ctypes.c_char_p),
+    "fsi_stage": ([_VP, _INT, _VP, _VP, _VP, _VP, _VP, _VP], _INT),
+    "fsi_residual": ([_VP, _INT, _VP, _VP, _VP, _VP], _INT),
+    "fsi_jacobian_apply": ([_VP, _INT, _VP, _VP, _VP, _VP, _VP], _INT),
+    "fsi_locate": ([_VP, _I64, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_I64), _INT], _INT),
+    "fsi_dlm_interp": ([_VP, _INT, _I64, _VP, _VP, _VP, _VP], _INT),
+    "fsi_dlm_spread": ([_VP, _INT, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _INT], _INT),
+    "fsi_measure_fma_peak": ([_INT, _INT, ctypes.POINTER(ctypes.c_double)], _INT),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if needed) libfsi.so and declare its signatures."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != FSI_OK:
+        raise FsiError(st, lib().fsi_last_error().decode())
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("array arguments must be CUDA tensors (device memory)")
+    if not t.is_contiguous():
+        raise ValueError("array arguments must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _prec_dtype(prec):
+    import torch
+    return torch.float64 if prec == FSI_F64 else torch.float32
+
+
+class Mesh:
+    """Owner of an fsi_mesh handle."""
+
+    def __init__(self, N, x0=(0.0, 0.0, 0.0), h=None, rho=1.0, mu=0.01, dt=1e-3,
+                 rho_inf=0.5, C_I=36.0, C_T=4.0, has_s=False, device=0, stream=None):
+        import torch
+        if isinstance(N, int):
+            N = (N, N, N)
+        if h is None:
+            h = tuple(1.0 / v for v in N)
+        elif isinstance(h, (int, float)):
+            h = (float(h),) * 3
+        self.N, self.x0, self.h = tuple(N), tuple(x0), tuple(h)
+        self.device = device
+        g = fsi_grid((ctypes.c_int32 * 3)(*N), (ctypes.c_double * 3)(*x0),
+                     (ctypes.c_double * 3)(*h))
+        self.phys = fsi_physics(rho, mu, dt, rho_inf, C_I, C_T, 1 if has_s else 0, 0)
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self._stream = stream
+        out = ctypes.c_void_p()
+        _check(lib().fsi_mesh_create(ctypes.byref(g), ctypes.byref(self.phys), device,
+                                     ctypes.c_void_p(stream), ctypes.byref(out)))
+        self.handle = out
+
+    @property
+    def n_nodes(self):
+        return (self.N[0] + 1) * (self.N[1] + 1) * (self.N[2] + 1)
+
+    @property
+    def n_elems(self):
+        return self.N[0] * self.N[1] * self.N[2]
+
+    def set_stream(self, stream):
+        self._stream = stream
+        _check(lib().fsi_mesh_set_stream(self.handle, ctypes.c_void_p(stream)))
+
+    def set_physics(self, **kw):
+        for k, v in kw.items():
+            setattr(self.phys, k, v)
+        _check(lib().fsi_mesh_set_physics(self.handle, ctypes.byref(self.phys)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fsi_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------- C-ABI mirrors
+def fsi_stage(mesh: Mesh, prec, y, Vn, An, s, U, A):
+    dt = _prec_dtype(prec)
+    _check(lib().fsi_stage(mesh.handle, prec, _ptr(y, dt), _ptr(Vn, dt), _ptr(An, dt),
+                           _ptr(s, dt), _ptr(U, dt), _ptr(A, dt)))
+
+
+def fsi_residual(mesh: Mesh, prec, U, A, f, R):
+    dt = _prec_dtype(prec)
+    _check(lib().fsi_residual(mesh.handle, prec, _ptr(U, dt), _ptr(A, dt), _ptr(f, dt),
+                              _ptr(R, dt)))
+
+
+def fsi_jacobian_apply(mesh: Mesh, prec, U, A, f, x, Jx):
+    dt = _prec_dtype(prec)
+    _check(lib().fsi_jacobian_apply(mesh.handle, prec, _ptr(U, dt), _ptr(A, dt), _ptr(f, dt),
+                                    _ptr(x, dt), _ptr(Jx, dt)))
+
+
+def fsi_locate(mesh: Mesh, X, elem, xi, cell_start=None, perm=None, want_outside=True,
+               strict=False):
+    import torch
+    m = 0 if X is None else X.shape[0]
+    nout = _I64(0)
+    _check(lib().fsi_locate(mesh.handle, m, _ptr(X, torch.float64), _ptr(elem, torch.int32),
+                            _ptr(xi, torch.float64), _ptr(cell_start, torch.int32),
+                            _ptr(perm, torch.int32),
+                            ctypes.byref(nout) if want_outside else None,
+                            1 if strict else 0))
+    return int(nout.value) if want_outside else None
+
+
+def fsi_dlm_interp(mesh: Mesh, prec, elem, xi, U, u):
+    import torch
+    dt = _prec_dtype(prec)
+    _check(lib().fsi_dlm_interp(mesh.handle, prec, elem.shape[0], _ptr(elem, torch.int32),
+                                _ptr(xi, dt), _ptr(U, dt), _ptr(u, dt)))
+
+
+def fsi_dlm_spread(mesh: Mesh, prec, elem, xi, cell_start, perm, lam, w, F, accumulate):
+    import torch
+    dt = _prec_dtype(prec)
+    m = elem.shape[0] if elem is not None else lam.shape[0]
+    _check(lib().fsi_dlm_spread(mesh.handle, prec, m, _ptr(elem, torch.int32), _ptr(xi, dt),
+                                _ptr(cell_start, torch.int32), _ptr(perm, torch.int32),
+                                _ptr(lam, dt), _ptr(w, dt), _ptr(F, dt),
+                                1 if accumulate else 0))
+
+
+def fsi_measure_fma_peak(device, prec):
+    out = ctypes.c_double(0.0)
+    _check(lib().fsi_measure_fma_peak(device, prec, ctypes.byref(out)))
+    return out.value

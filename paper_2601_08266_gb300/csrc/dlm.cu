@@ -1,0 +1,405 @@
+// dlm.cu -- fictitious-domain coupling operators (Sec. 2.3 of the paper):
+// point location with a cell -> points table, interpolation u = C^T V
+// (Eq. nodal_solid_velo) and spreading F = C lambda (Eq. fsi_constraint_matrix).
+//
+// Location is closed-form on the uniform grid.  The cell table is a stable
+// counting sort: histogram (integer atomics, order-free), a three-kernel
+// exclusive scan, a scatter through per-cell cursors, and a per-cell sort of
+// each cell's slice by point index, which restores the stable order exactly.
+// Spreading is node-centric: every node pulls from the points of its (up to)
+// eight cells in a fixed order, so there are no atomics and no races, and the
+// result does not depend on scheduling.
+#include <cmath>
+
+#include "fsi_internal.cuh"
+
+namespace fsi {
+namespace {
+
+struct GridArgs {
+    int Nx, Ny, Nz;
+    double x0, y0, z0, hx, hy, hz;
+};
+
+GridArgs grid_args(const fsi_mesh *m)
+{
+    GridArgs g;
+    g.Nx = m->grid.N[0];
+    g.Ny = m->grid.N[1];
+    g.Nz = m->grid.N[2];
+    g.x0 = m->grid.x0[0];
+    g.y0 = m->grid.x0[1];
+    g.z0 = m->grid.x0[2];
+    g.hx = m->grid.h[0];
+    g.hy = m->grid.h[1];
+    g.hz = m->grid.h[2];
+    return g;
+}
+
+int blocks_for(int64_t n, int threads, int cap = 152 * 16)
+{
+    int64_t b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+// --------------------------------------------------------------- locate
+__global__ void locate_kernel(int64_t m, GridArgs g, const double *__restrict__ X,
+                              int32_t *__restrict__ elem, double *__restrict__ xi,
+                              int32_t *__restrict__ count, unsigned long long *n_out)
+{
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const double tx = (X[3 * b + 0] - g.x0) / g.hx;
+        const double ty = (X[3 * b + 1] - g.y0) / g.hy;
+        const double tz = (X[3 * b + 2] - g.z0) / g.hz;
+        const bool in = (tx >= 0.0 && tx <= (double)g.Nx) && (ty >= 0.0 && ty <= (double)g.Ny) &&
+                        (tz >= 0.0 && tz <= (double)g.Nz);
+        if (!in) {
+            elem[b] = -1;
+            xi[3 * b + 0] = 0.0;
+            xi[3 * b + 1] = 0.0;
+            xi[3 * b + 2] = 0.0;
+            atomicAdd(n_out, 1ull);
+            continue;
+        }
+        const int ex = min((int)floor(tx), g.Nx - 1);
+        const int ey = min((int)floor(ty), g.Ny - 1);
+        const int ez = min((int)floor(tz), g.Nz - 1);
+        xi[3 * b + 0] = 2.0 * (tx - (double)ex) - 1.0;
+        xi[3 * b + 1] = 2.0 * (ty - (double)ey) - 1.0;
+        xi[3 * b + 2] = 2.0 * (tz - (double)ez) - 1.0;
+        const int e = ex + g.Nx * (ey + g.Ny * ez);
+        elem[b] = e;
+        if (count) atomicAdd(count + e, 1);
+    }
+}
+
+// --------------------------------------------------------------- scan
+// Exclusive scan of count[0..E) into start[0..E] (start[E] = total) with
+// 2048-entry tiles: (1) tile-local inclusive scan + tile totals, (2) one CTA
+// scans the tile totals, (3) tiles add their offset.
+constexpr int kScanTile = 2048;
+
+__device__ __forceinline__ int block_inclusive_scan(int v, int *warp_sums)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) warp_sums[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    if (wid > 0) v += warp_sums[wid - 1];
+    return v;
+}
+
+__global__ void __launch_bounds__(1024) scan_tiles_kernel(int64_t E, const int32_t *count,
+                                                          int32_t *start, int32_t *tile_sum)
+{
+    __shared__ int warp_sums[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + 2 * threadIdx.x;
+    const int a = base < E ? count[base] : 0;
+    const int b = base + 1 < E ? count[base + 1] : 0;
+    const int incl = block_inclusive_scan(a + b, warp_sums);
+    if (base < E) start[base + 1] = incl - b;
+    if (base + 1 < E) start[base + 2] = incl;
+    if (threadIdx.x == blockDim.x - 1) tile_sum[blockIdx.x] = incl;
+}
+
+__global__ void __launch_bounds__(1024) scan_totals_kernel(int64_t ntiles, int32_t *tile_sum)
+{
+    __shared__ int warp_sums[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < ntiles; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const int v = i < ntiles ? tile_sum[i] : 0;
+        const int incl = block_inclusive_scan(v, warp_sums);
+        const int c = carry;
+        __syncthreads();
+        if (i < ntiles) tile_sum[i] = c + incl - v;  // exclusive
+        if (threadIdx.x == blockDim.x - 1) carry = c + incl;
+        __syncthreads();
+    }
+}
+
+__global__ void scan_add_kernel(int64_t E, int32_t *start, const int32_t *tile_sum)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    const int off = tile_sum[blockIdx.x];
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+        const int64_t k = base + i;
+        if (k < E) start[k + 1] += off;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) start[0] = 0;
+}
+
+// --------------------------------------------------------------- scatter + sort
+__global__ void scatter_kernel(int64_t m, int64_t E, const int32_t *__restrict__ elem,
+                               const int32_t *__restrict__ start, int32_t *fill,
+                               int32_t *__restrict__ perm)
+{
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int e = elem[b];
+        const int64_t cell = e >= 0 ? e : E;  // outside points form the tail "cell" E
+        const int pos = start[cell] + atomicAdd(fill + cell, 1);
+        perm[pos] = (int32_t)b;
+    }
+}
+
+// Sort every cell's slice of perm ascending (restores the stable order).
+// Cell E is the tail of outside points [start[E], m).
+__global__ void cell_sort_kernel(int64_t E, int64_t m, const int32_t *__restrict__ start,
+                                 int32_t *__restrict__ perm)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= E;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int lo = start[c];
+        const int hi = (c < E) ? start[c + 1] : (int)m;
+        const int len = hi - lo;
+        if (len < 2) continue;
+        int32_t *s = perm + lo;
+        if (len <= 32) {
+            for (int i = 1; i < len; ++i) {
+                const int v = s[i];
+                int j = i - 1;
+                while (j >= 0 && s[j] > v) {
+                    s[j + 1] = s[j];
+                    --j;
+                }
+                s[j + 1] = v;
+            }
+        } else {
+            // Shell sort with Ciura's gap sequence (extended by x2.25).
+            int gap = 1;
+            while (gap * 9 / 4 + 1 < len) gap = gap * 9 / 4 + 1;
+            const int ciura[8] = {701, 301, 132, 57, 23, 10, 4, 1};
+            for (;;) {
+                for (int i = gap; i < len; ++i) {
+                    const int v = s[i];
+                    int j = i;
+                    while (j >= gap && s[j - gap] > v) {
+                        s[j] = s[j - gap];
+                        j -= gap;
+                    }
+                    s[j] = v;
+                }
+                if (gap == 1) break;
+                int next = 1;
+                if (gap > 701) {
+                    next = gap * 4 / 9;
+                    if (next < 701) next = 701;
+                } else {
+                    for (int k = 0; k < 8; ++k)
+                        if (ciura[k] < gap) {
+                            next = ciura[k];
+                            break;
+                        }
+                }
+                gap = next;
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------- interp / spread
+template <typename T> __device__ __forceinline__ T shape_1d(T xi, int side)
+{
+    return side ? (T(1) + xi) : (T(1) - xi);
+}
+
+template <typename T>
+__global__ void interp_kernel(int64_t m, GridArgs g, const int32_t *__restrict__ elem,
+                              const T *__restrict__ xi, const vec4<T> *__restrict__ U,
+                              T *__restrict__ u)
+{
+    const int NX1 = g.Nx + 1, NXY1 = (g.Nx + 1) * (g.Ny + 1);
+    const int E = g.Nx * g.Ny * g.Nz;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int e = elem[b];
+        T ux = T(0), uy = T(0), uz = T(0);
+        if (e >= 0 && e < E) {
+            const int ex = e % g.Nx, ey = (e / g.Nx) % g.Ny, ez = e / (g.Nx * g.Ny);
+            const T x0 = xi[3 * b], x1 = xi[3 * b + 1], x2 = xi[3 * b + 2];
+            const int n0 = ex + NX1 * ey + NXY1 * ez;
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+                const T Na = shape_1d(x0, ax) * shape_1d(x1, ay) * shape_1d(x2, az) * T(0.125);
+                const vec4<T> v = ld4(U + n0 + ax + NX1 * ay + NXY1 * az);
+                ux += Na * v.x;
+                uy += Na * v.y;
+                uz += Na * v.z;
+            }
+        }
+        u[3 * b] = ux;
+        u[3 * b + 1] = uy;
+        u[3 * b + 2] = uz;
+    }
+}
+
+template <typename T>
+__global__ void spread_kernel(GridArgs g, const T *__restrict__ xi,
+                              const int32_t *__restrict__ start,
+                              const int32_t *__restrict__ perm, const T *__restrict__ lam,
+                              const T *__restrict__ w, T *__restrict__ F, int accumulate)
+{
+    const int NX1 = g.Nx + 1, NY1 = g.Ny + 1;
+    const int n = NX1 * NY1 * (g.Nz + 1);
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < n;
+         node += gridDim.x * blockDim.x) {
+        const int i = node % NX1, j = (node / NX1) % NY1, k = node / (NX1 * NY1);
+        T fx = T(0), fy = T(0), fz = T(0);
+        bool touched = false;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            // this node is local corner (cx,cy,cz) of cell (i-cx, j-cy, k-cz)
+            const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+            const int ex = i - cx, ey = j - cy, ez = k - cz;
+            if (ex < 0 || ey < 0 || ez < 0 || ex >= g.Nx || ey >= g.Ny || ez >= g.Nz) continue;
+            const int cell = ex + g.Nx * (ey + g.Ny * ez);
+            const int lo = start[cell], hi = start[cell + 1];
+            for (int p = lo; p < hi; ++p) {
+                const int b = perm[p];
+                const T Na = shape_1d(xi[3 * b], cx) * shape_1d(xi[3 * b + 1], cy) *
+                             shape_1d(xi[3 * b + 2], cz) * T(0.125);
+                const T s = w ? Na * w[b] : Na;
+                fx += s * lam[3 * b];
+                fy += s * lam[3 * b + 1];
+                fz += s * lam[3 * b + 2];
+                touched = true;
+            }
+        }
+        T *o = F + 4 * (size_t)node;
+        if (accumulate) {
+            if (touched) {
+                o[0] += fx;
+                o[1] += fy;
+                o[2] += fz;
+            }
+        } else {
+            o[0] = fx;
+            o[1] = fy;
+            o[2] = fz;
+        }
+    }
+}
+
+}  // namespace
+}  // namespace fsi
+
+using namespace fsi;
+
+extern "C" {
+
+fsi_status fsi_locate(fsi_mesh *mesh, int64_t m, const double *X, int32_t *elem, double *xi,
+                      int32_t *cell_start, int32_t *perm, int64_t *n_outside, int strict)
+{
+    FSI_TRY(validate_mesh(mesh));
+    if (m < 0 || m >= INT32_MAX) return set_error(FSI_ERR_ARG, "fsi_locate: m out of range");
+    if (m > 0 && (!X || !elem || !xi))
+        return set_error(FSI_ERR_ARG, "fsi_locate: NULL X, elem or xi");
+    if ((cell_start == nullptr) != (perm == nullptr))
+        return set_error(FSI_ERR_ARG, "fsi_locate: pass both cell_start and perm, or neither");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    const int64_t E = mesh->n_elems;
+    cudaStream_t s = mesh->stream;
+    unsigned long long *nout = (unsigned long long *)mesh->dev_counters;
+    FSI_CUDA(cudaMemsetAsync(nout, 0, sizeof(unsigned long long), s), "memset");
+    const bool table = cell_start != nullptr;
+    if (table) FSI_CUDA(cudaMemsetAsync(mesh->hash_fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
+    GridArgs g = grid_args(mesh);
+    if (m > 0) {
+        locate_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, g, X, elem, xi,
+                                                         table ? mesh->hash_fill : nullptr, nout);
+        FSI_TRY(check_launch("locate kernel"));
+    }
+    if (table) {
+        const int64_t ntiles = (E + kScanTile - 1) / kScanTile;
+        scan_tiles_kernel<<<(int)ntiles, 1024, 0, s>>>(E, mesh->hash_fill, cell_start,
+                                                       mesh->scan_tmp);
+        FSI_TRY(check_launch("scan tiles kernel"));
+        scan_totals_kernel<<<1, 1024, 0, s>>>(ntiles, mesh->scan_tmp);
+        FSI_TRY(check_launch("scan totals kernel"));
+        scan_add_kernel<<<(int)ntiles, 256, 0, s>>>(E, cell_start, mesh->scan_tmp);
+        FSI_TRY(check_launch("scan add kernel"));
+        if (m > 0) {
+            FSI_CUDA(cudaMemsetAsync(mesh->hash_fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
+            scatter_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, E, elem, cell_start,
+                                                              mesh->hash_fill, perm);
+            FSI_TRY(check_launch("scatter kernel"));
+            cell_sort_kernel<<<blocks_for(E + 1, 256, 152 * 64), 256, 0, s>>>(E, m, cell_start,
+                                                                            perm);
+            FSI_TRY(check_launch("cell sort kernel"));
+        }
+    }
+    if (n_outside || strict) {
+        unsigned long long h = 0;
+        FSI_CUDA(cudaMemcpyAsync(&h, nout, sizeof h, cudaMemcpyDeviceToHost, s), "memcpy");
+        FSI_CUDA(cudaStreamSynchronize(s), "stream sync");
+        if (n_outside) *n_outside = (int64_t)h;
+        if (strict && h > 0)
+            return set_error(FSI_ERR_OUTSIDE, "fsi_locate: %llu points outside the grid", h);
+    }
+    return FSI_OK;
+}
+
+fsi_status fsi_dlm_interp(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_t *elem,
+                          const void *xi, const void *U, void *u)
+{
+    FSI_TRY(validate_mesh(mesh));
+    if (m < 0 || m >= INT32_MAX) return set_error(FSI_ERR_ARG, "fsi_dlm_interp: m out of range");
+    if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
+    if (m == 0) return FSI_OK;
+    if (!elem || !xi || !U || !u) return set_error(FSI_ERR_ARG, "fsi_dlm_interp: NULL argument");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    GridArgs g = grid_args(mesh);
+    if (prec == FSI_F64)
+        interp_kernel<double><<<blocks_for(m, 256), 256, 0, mesh->stream>>>(
+            m, g, elem, (const double *)xi, (const vec4<double> *)U, (double *)u);
+    else
+        interp_kernel<float><<<blocks_for(m, 256), 256, 0, mesh->stream>>>(
+            m, g, elem, (const float *)xi, (const vec4<float> *)U, (float *)u);
+    return check_launch("interp kernel");
+}
+
+fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_t *elem,
+                          const void *xi, const int32_t *cell_start, const int32_t *perm,
+                          const void *lam, const void *w, void *F, int accumulate)
+{
+    (void)elem;
+    FSI_TRY(validate_mesh(mesh));
+    if (m < 0 || m >= INT32_MAX) return set_error(FSI_ERR_ARG, "fsi_dlm_spread: m out of range");
+    if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
+    if (!F || !cell_start) return set_error(FSI_ERR_ARG, "fsi_dlm_spread: NULL F or cell_start");
+    if (m > 0 && (!xi || !perm || !lam))
+        return set_error(FSI_ERR_ARG, "fsi_dlm_spread: NULL xi, perm or lam");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    GridArgs g = grid_args(mesh);
+    const int grid = blocks_for(mesh->n_nodes, 256, 152 * 32);
+    if (prec == FSI_F64)
+        spread_kernel<double><<<grid, 256, 0, mesh->stream>>>(
+            g, (const double *)xi, cell_start, perm, (const double *)lam, (const double *)w,
+            (double *)F, accumulate);
+    else
+        spread_kernel<float><<<grid, 256, 0, mesh->stream>>>(
+            g, (const float *)xi, cell_start, perm, (const float *)lam, (const float *)w,
+            (float *)F, accumulate);
+    return check_launch("spread kernel");
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// fsi_internal.cuh -- definitions shared by the translation units of libfsi.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "fsi.h"
+
+namespace fsi {
+
+// ---------------------------------------------------------------- errors
+fsi_status set_error(fsi_status st, const char *fmt, ...);
+fsi_status check_cuda(cudaError_t e, const char *what);
+fsi_status check_launch(const char *what);
+
+#define FSI_TRY(expr)                       \
+    do {                                    \
+        fsi_status _st = (expr);            \
+        if (_st != FSI_OK) return _st;      \
+    } while (0)
+
+#define FSI_CUDA(expr, what) FSI_TRY(::fsi::check_cuda((expr), (what)))
+
+// ---------------------------------------------------------------- 4-vectors
+// 16/32-byte aligned node records so that one node is one vector load.
+template <typename T> struct alignas(4 * sizeof(T)) vec4 {
+    T x, y, z, w;
+};
+
+template <typename T> __device__ __forceinline__ vec4<T> ld4(const vec4<T> *p);
+template <> __device__ __forceinline__ vec4<float> ld4(const vec4<float> *p)
+{
+    float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return {v.x, v.y, v.z, v.w};
+}
+template <> __device__ __forceinline__ vec4<double> ld4(const vec4<double> *p)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 a = __ldg(q), b = __ldg(q + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+
+template <typename T> __device__ __forceinline__ void st4(vec4<T> *p, vec4<T> v) { *p = v; }
+
+// ---------------------------------------------------------------- tuning
+struct Brick {
+    int bx, by, bz;  // elements per CTA along each axis
+    int threads;     // CTA size (multiple of 32; 8 lanes per element)
+};
+
+// ---------------------------------------------------------------- mesh
+}  // namespace fsi
+
+struct fsi_mesh {
+    fsi_grid grid;
+    fsi_physics phys;
+    int device;
+    cudaStream_t stream;
+    int64_t n_nodes, n_elems;
+    double alpha_m, alpha_f, gamma;
+    // VMS brick schedule per [op: 0 residual, 1 jacobian][prec]
+    fsi::Brick brick[2][2];
+    // scratch: per-brick node-block partial sums of the VMS operators
+    void *vms_scratch;
+    size_t vms_scratch_bytes;
+    // scratch: cell fill counters [E+1] + scan block sums + misc counters
+    int32_t *hash_fill;
+    int32_t *scan_tmp;
+    int64_t scan_tmp_len;
+    int64_t *dev_counters;  // [0] outside count, [1] error flag
+};
+
+namespace fsi {
+
+fsi_status validate_mesh(const fsi_mesh *m);
+fsi_status ensure_vms_scratch(fsi_mesh *m, const Brick &b, size_t elem_bytes);
+size_t vms_scratch_bytes_for(const fsi_mesh *m, const Brick &b, size_t elem_bytes);
+
+// VMS operators (vms.cu)
+fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
+                        const void *f, void *R);
+fsi_status vms_jacobian(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
+                        const void *f, const void *x, void *Jx);
+
+}  // namespace fsi
