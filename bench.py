@@ -42,8 +42,8 @@ N_GRID = 64
 M_POINTS = 200_000
 SEED = 2026
 # Kernel launches per step issued by the library (stage 1, residual 2,
-# Jacobian 2, locate 1 + scan 3 + scatter 1 + sort 1, interp 1, spread 1).
-LAUNCHES_PER_STEP = 13
+# Jacobian 2, locate 1 + scan 3 + scatter 1 + sort 1, interp 1, spread 2).
+LAUNCHES_PER_STEP = 14
 # Algorithmic FP64/FP32 operations per element of one VMS Jacobian apply and
 # one residual (FMA = 2 flops), counted from the kernel's arithmetic.
 FLOPS_PER_ELEM = {"jacobian": 4928.0, "residual": 2992.0}
@@ -84,7 +84,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -206,7 +206,7 @@ def run_ours(args):
     import paper_2601_08266_gb300 as fsi
     from paper_2601_08266_gb300 import _binding as B
 
-    W = make_workload(seed=SEED + rank)
+    W = make_workload(N=args.grid, m=args.points, seed=SEED + rank)
     N, n, m = W["N"], W["n"], W["m"]
     stream = torch.cuda.Stream(device=dev)
     mesh = fsi.Mesh(N, rho=1.0, mu=0.01, dt=1e-3, rho_inf=0.5, device=local,
@@ -277,9 +277,9 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    time.sleep(0.3)
     ms64, per64 = timed(lambda ev: step(b64, P64, ev), args.steps, args.warmup)
     torch.cuda.synchronize()
-    clocks = sampler.stop()
     # FP32 operators (xi cast once outside the timed loop)
     b32 = buffers(torch.float32)
     fsi.fsi_locate(mesh, b32["X"], b32["elem"], b32["xi"], b32["cs"], b32["perm"],
@@ -306,6 +306,11 @@ def run_ours(args):
 
     fsi.fsi_stage(mesh, fsi.FSI_F32, b32["y"], b32["Vn"], b32["An"], None, b32["U"], b32["A"])
     ms32, per32 = timed(step32, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if args.no_e2e:
+        return finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
+                      clocks, None, 0, 0)
 
     # end to end through host buffers (pinned), FP64 step
     h_in = {k: torch.as_tensor(W[k]).pin_memory() for k in ("y", "Vn", "An", "x", "X", "lam")}
@@ -333,7 +338,19 @@ def run_ours(args):
     e1.record(stream)
     stream.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
+    return finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32, clocks,
+                  e2e_ms, h2d, d2h)
 
+
+def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32, clocks, e2e_ms,
+           h2d, d2h):
+    import torch
+    import paper_2601_08266_gb300 as fsi
+    from paper_2601_08266_gb300 import _binding as B
+    N, n, m = W["N"], W["n"], W["m"]
+    dev = torch.device(f"cuda:{local}")
+    if e2e_ms is None:
+        e2e_ms = float("nan")
     # max over ranks
     t_step = ms64
     if ws > 1:
@@ -341,7 +358,7 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_step, e2e_ms = float(t[0]), float(t[1])
     value = ws * 4.0 * n / (t_step * 1e-3) / 1e9
-    e2e_val = ws * 4.0 * n / (e2e_ms * 1e-3) / 1e9
+    e2e_val = ws * 4.0 * n / (e2e_ms * 1e-3) / 1e9 if math.isfinite(e2e_ms) else None
 
     if rank != 0:
         if ws > 1:
@@ -379,7 +396,7 @@ def run_ours(args):
     op_tab["residual"]["tflop_s"] = round(FLOPS_PER_ELEM["residual"] * E / (per64[1] * 1e-3) / 1e12, 4)
 
     cpu = None
-    if ws == 1 and not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline and N == N_GRID and m == M_POINTS:
         rate, passes, el = cpu_oracle_rate(W, max_seconds=args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{passes} full FP64 oracle pass(es) of the step on the 64^3 workload "
@@ -389,7 +406,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [N, N, N], "dofs": 4 * n, "points": m,
+        "config": {"workload": WORKLOAD if (N, m) == (N_GRID, M_POINTS) else
+                   f"{N}^3 grid + {m} leaflet points (profiling case)",
+                   "grid": [N, N, N], "dofs": 4 * n, "points": m,
                    "l2": "flushed between timed steps (write of a buffer > L2)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "kernel": "vms_jacobian f64 (brick + gather)",
@@ -397,8 +416,9 @@ def run_ours(args):
                      "frac": achieved / fma64, "traffic": traffic,
                      "peak_source": "measured FP64 FMA rate (fsi_measure_fma_peak, this run)"},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "e2e": None if e2e_val is None else {
+            "value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clocks,
         "ops_f64": op_tab,
@@ -422,6 +442,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--grid", type=int, default=N_GRID, help="elements per axis (profiling)")
+    ap.add_argument("--points", type=int, default=M_POINTS, help="solid points (profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -170,10 +170,11 @@ fsi_status fsi_dlm_interp(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
  * momentum slots 0..2 of F [n][4]; slot 3 is neither read nor written.
  * accumulate == 0 overwrites slots 0..2 instead of adding.  lam [m][3],
  * w [m] (NULL: w_B = 1), xi [m][3] and F are in `prec`.  elem, cell_start
- * and perm are the outputs of fsi_locate for the same points.  The sum for
- * each node runs over its (up to) 8 cells in a fixed order and over each
- * cell's points in perm order, so the result is deterministic and no atomic
- * operation is used.                                                       */
+ * and perm are the outputs of fsi_locate for the same points.  No atomic
+ * operation is used and the result is deterministic: each cell's corner sums
+ * are formed over its points in perm order with a fixed reduction tree (in
+ * mesh scratch), then each node adds the sums of its (up to) 8 cells in a
+ * fixed order.                                                            */
 fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_t *elem,
                           const void *xi, const int32_t *cell_start, const int32_t *perm,
                           const void *lam, const void *w, void *F, int accumulate);

@@ -6,8 +6,9 @@
 // counting sort: histogram (integer atomics, order-free), a three-kernel
 // exclusive scan, a scatter through per-cell cursors, and a per-cell sort of
 // each cell's slice by point index, which restores the stable order exactly.
-// Spreading is node-centric: every node pulls from the points of its (up to)
-// eight cells in a fixed order, so there are no atomics and no races, and the
+// Spreading is atomic-free in two passes: per-cell corner sums (one warp per
+// 32-cell segment, butterfly reductions), then a node gather over the (up to)
+// eight cells of each node in a fixed order.  No races, no atomics, and the
 // result does not depend on scheduling.
 #include <cmath>
 
@@ -252,11 +253,73 @@ __global__ void interp_kernel(int64_t m, GridArgs g, const int32_t *__restrict__
     }
 }
 
+// Spreading, pass 1: one warp per segment of 32 consecutive cells.  For each
+// occupied cell the lanes stride over its points (perm order) and accumulate the
+// 8 corner contributions w_B N_a(xi_B) lambda_B (24 values), then a butterfly
+// reduction (fixed lane order, so deterministic) gives the cell's corner sums
+// S[cell][8][3].
 template <typename T>
-__global__ void spread_kernel(GridArgs g, const T *__restrict__ xi,
-                              const int32_t *__restrict__ start,
-                              const int32_t *__restrict__ perm, const T *__restrict__ lam,
-                              const T *__restrict__ w, T *__restrict__ F, int accumulate)
+__global__ void spread_cells_kernel(int64_t E, const T *__restrict__ xi,
+                                    const int32_t *__restrict__ start,
+                                    const int32_t *__restrict__ perm, const T *__restrict__ lam,
+                                    const T *__restrict__ w, T *__restrict__ S)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c0 = warp * 32; c0 < E; c0 += nwarps * 32) {
+        const int64_t myc = c0 + lane;
+        int lo = 0, hi = 0;
+        if (myc < E) {
+            lo = start[myc];
+            hi = start[myc + 1];
+        }
+        unsigned occ = __ballot_sync(0xffffffffu, hi > lo);
+        while (occ) {
+            const int l = __ffs(occ) - 1;
+            occ &= occ - 1;
+            const int plo = __shfl_sync(0xffffffffu, lo, l);
+            const int phi = __shfl_sync(0xffffffffu, hi, l);
+            T acc[24];
+#pragma unroll
+            for (int k = 0; k < 24; ++k) acc[k] = T(0);
+            for (int p = plo + lane; p < phi; p += 32) {
+                const int b = perm[p];
+                const T x0 = xi[3 * b], x1 = xi[3 * b + 1], x2 = xi[3 * b + 2];
+                const T s = w ? w[b] * T(0.125) : T(0.125);
+                const T l0 = lam[3 * b], l1 = lam[3 * b + 1], l2 = lam[3 * b + 2];
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    const T Na = shape_1d(x0, a & 1) * shape_1d(x1, (a >> 1) & 1) *
+                                 shape_1d(x2, (a >> 2) & 1) * s;
+                    acc[3 * a] += Na * l0;
+                    acc[3 * a + 1] += Na * l1;
+                    acc[3 * a + 2] += Na * l2;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 24; ++k) {
+                T v = acc[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                acc[k] = v;
+            }
+            if (lane < 24) {
+                T v = acc[0];
+#pragma unroll
+                for (int k = 1; k < 24; ++k)
+                    if (lane == k) v = acc[k];
+                S[(c0 + l) * 24 + lane] = v;
+            }
+        }
+    }
+}
+
+// Spreading, pass 2: every node sums the corner sums of its (up to 8)
+// occupied cells in a fixed order.
+template <typename T>
+__global__ void spread_nodes_kernel(GridArgs g, const int32_t *__restrict__ start,
+                                    const T *__restrict__ S, T *__restrict__ F, int accumulate)
 {
     const int NX1 = g.Nx + 1, NY1 = g.Ny + 1;
     const int n = NX1 * NY1 * (g.Nz + 1);
@@ -272,17 +335,12 @@ __global__ void spread_kernel(GridArgs g, const T *__restrict__ xi,
             const int ex = i - cx, ey = j - cy, ez = k - cz;
             if (ex < 0 || ey < 0 || ez < 0 || ex >= g.Nx || ey >= g.Ny || ez >= g.Nz) continue;
             const int cell = ex + g.Nx * (ey + g.Ny * ez);
-            const int lo = start[cell], hi = start[cell + 1];
-            for (int p = lo; p < hi; ++p) {
-                const int b = perm[p];
-                const T Na = shape_1d(xi[3 * b], cx) * shape_1d(xi[3 * b + 1], cy) *
-                             shape_1d(xi[3 * b + 2], cz) * T(0.125);
-                const T s = w ? Na * w[b] : Na;
-                fx += s * lam[3 * b];
-                fy += s * lam[3 * b + 1];
-                fz += s * lam[3 * b + 2];
-                touched = true;
-            }
+            if (start[cell + 1] == start[cell]) continue;
+            const T *sc = S + (size_t)cell * 24 + 3 * c;
+            fx += sc[0];
+            fy += sc[1];
+            fz += sc[2];
+            touched = true;
         }
         T *o = F + 4 * (size_t)node;
         if (accumulate) {
@@ -313,8 +371,10 @@ fsi_status fsi_locate(fsi_mesh *mesh, int64_t m, const double *X, int32_t *elem,
     if (m < 0 || m >= INT32_MAX) return set_error(FSI_ERR_ARG, "fsi_locate: m out of range");
     if (m > 0 && (!X || !elem || !xi))
         return set_error(FSI_ERR_ARG, "fsi_locate: NULL X, elem or xi");
-    if ((cell_start == nullptr) != (perm == nullptr))
-        return set_error(FSI_ERR_ARG, "fsi_locate: pass both cell_start and perm, or neither");
+    if (perm != nullptr && cell_start == nullptr)
+        return set_error(FSI_ERR_ARG, "fsi_locate: perm given without cell_start");
+    if (cell_start != nullptr && perm == nullptr && m > 0)
+        return set_error(FSI_ERR_ARG, "fsi_locate: cell_start given without perm");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
     const int64_t E = mesh->n_elems;
     cudaStream_t s = mesh->stream;
@@ -390,16 +450,27 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
         return set_error(FSI_ERR_ARG, "fsi_dlm_spread: NULL xi, perm or lam");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
     GridArgs g = grid_args(mesh);
-    const int grid = blocks_for(mesh->n_nodes, 256, 152 * 32);
-    if (prec == FSI_F64)
-        spread_kernel<double><<<grid, 256, 0, mesh->stream>>>(
-            g, (const double *)xi, cell_start, perm, (const double *)lam, (const double *)w,
-            (double *)F, accumulate);
-    else
-        spread_kernel<float><<<grid, 256, 0, mesh->stream>>>(
-            g, (const float *)xi, cell_start, perm, (const float *)lam, (const float *)w,
-            (float *)F, accumulate);
-    return check_launch("spread kernel");
+    const size_t esz = prec == FSI_F64 ? sizeof(double) : sizeof(float);
+    FSI_TRY(ensure_spread_scratch(mesh, (size_t)mesh->n_elems * 24 * esz));
+    const int64_t E = mesh->n_elems;
+    const int cgrid = blocks_for((E + 31) / 32 * 32, 256, 152 * 64);
+    const int ngrid = blocks_for(mesh->n_nodes, 256, 152 * 32);
+    if (prec == FSI_F64) {
+        spread_cells_kernel<double><<<cgrid, 256, 0, mesh->stream>>>(
+            E, (const double *)xi, cell_start, perm, (const double *)lam, (const double *)w,
+            (double *)mesh->spread_scratch);
+        FSI_TRY(check_launch("spread cells kernel"));
+        spread_nodes_kernel<double><<<ngrid, 256, 0, mesh->stream>>>(
+            g, cell_start, (const double *)mesh->spread_scratch, (double *)F, accumulate);
+    } else {
+        spread_cells_kernel<float><<<cgrid, 256, 0, mesh->stream>>>(
+            E, (const float *)xi, cell_start, perm, (const float *)lam, (const float *)w,
+            (float *)mesh->spread_scratch);
+        FSI_TRY(check_launch("spread cells kernel"));
+        spread_nodes_kernel<float><<<ngrid, 256, 0, mesh->stream>>>(
+            g, cell_start, (const float *)mesh->spread_scratch, (float *)F, accumulate);
+    }
+    return check_launch("spread nodes kernel");
 }
 
 }  // extern "C"

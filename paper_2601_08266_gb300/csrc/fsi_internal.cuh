@@ -72,6 +72,9 @@ struct fsi_mesh {
     int32_t *scan_tmp;
     int64_t scan_tmp_len;
     int64_t *dev_counters;  // [0] outside count, [1] error flag
+    // scratch: per-cell corner sums of the spreading operator [E][8][3]
+    void *spread_scratch;
+    size_t spread_scratch_bytes;
 };
 
 namespace fsi {
@@ -79,6 +82,7 @@ namespace fsi {
 fsi_status validate_mesh(const fsi_mesh *m);
 fsi_status ensure_vms_scratch(fsi_mesh *m, const Brick &b, size_t elem_bytes);
 size_t vms_scratch_bytes_for(const fsi_mesh *m, const Brick &b, size_t elem_bytes);
+fsi_status ensure_spread_scratch(fsi_mesh *m, size_t bytes);
 
 // VMS operators (vms.cu)
 fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,

@@ -82,6 +82,20 @@ fsi_status ensure_vms_scratch(fsi_mesh *m, const Brick &b, size_t elem_bytes)
     return FSI_OK;
 }
 
+fsi_status ensure_spread_scratch(fsi_mesh *m, size_t need)
+{
+    if (need <= m->spread_scratch_bytes) return FSI_OK;
+    if (m->spread_scratch) {
+        FSI_CUDA(cudaStreamSynchronize(m->stream), "stream sync before scratch growth");
+        cudaFree(m->spread_scratch);
+        m->spread_scratch = nullptr;
+        m->spread_scratch_bytes = 0;
+    }
+    FSI_CUDA(cudaMalloc(&m->spread_scratch, need), "spread scratch allocation");
+    m->spread_scratch_bytes = need;
+    return FSI_OK;
+}
+
 // ------------------------------------------------------------ stage kernel
 template <typename T>
 __global__ void stage_kernel(int64_t n, T dt, T am, T af, T gamma, const vec4<T> *__restrict__ y,
@@ -168,6 +182,7 @@ fsi_status fsi_mesh_create(const fsi_grid *grid, const fsi_physics *phys, int de
     if (st == FSI_OK)
         st = check_cuda(cudaMalloc(&m->dev_counters, 8 * sizeof(int64_t)), "counter scratch");
     if (st == FSI_OK) st = ensure_vms_scratch(m, m->brick[1][0], sizeof(double));
+    if (st == FSI_OK) st = ensure_spread_scratch(m, (size_t)E * 24 * sizeof(double));
     if (st != FSI_OK) {
         fsi_mesh_destroy(m);
         return st;
@@ -185,6 +200,7 @@ void fsi_mesh_destroy(fsi_mesh *m)
     cudaFree(m->hash_fill);
     cudaFree(m->scan_tmp);
     cudaFree(m->dev_counters);
+    cudaFree(m->spread_scratch);
     delete m;
 }
 

@@ -133,7 +133,7 @@ __device__ __forceinline__ void base_state(const VmsArgs<T> &P, GP<T> &q)
 template <typename T, bool JAC>
 __global__ void __launch_bounds__(256) vms_brick_kernel(const VmsArgs<T> P)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(32) unsigned char smem_raw[];
     vec4<T> *rel = reinterpret_cast<vec4<T> *>(smem_raw);  // [bx*by*bz][8]
 
     const int g = threadIdx.x & 7;

@@ -84,9 +84,8 @@ def test_stage_matches_generalized_alpha(fsi, oracle, prec):
     mesh, grid, p = make(fsi, oracle, 5, dt=0.013)
     n = mesh.n_nodes
     rng = np.random.default_rng(0)
-    y, Vn, An, s = (cast(prec, rng.normal(size=(n, 4))) for _ in range(3)) if False else (
-        cast(prec, rng.normal(size=(n, 4))), cast(prec, rng.normal(size=(n, 4))),
-        cast(prec, rng.normal(size=(n, 4))), cast(prec, rng.uniform(1, 3, n)))
+    y, Vn, An = (cast(prec, rng.normal(size=(n, 4))) for _ in range(3))
+    s = cast(prec, rng.uniform(1, 3, n))
     dt = dtype_of(prec)
     P = fsi.FSI_F64 if prec == "f64" else fsi.FSI_F32
     U = torch.empty((n, 4), dtype=dt, device="cuda")
