@@ -179,6 +179,94 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
                           const void *xi, const int32_t *cell_start, const int32_t *perm,
                           const void *lam, const void *w, void *F, int accumulate);
 
+/* ----------------------------------------------------------------------- */
+/* One implicit step: the reduced FSI system of Sec. 2.4.                    */
+
+/* The state of one time step.  All arrays are DEVICE pointers, FP64.
+ * The unknown y = (Vdot_{n+1}, P_{n+1}) [n][4]; Vn = (V_n, -) and
+ * An = (Vdot_n, -) [n][4] are the history (slot 4 ignored); s [n] and
+ * f [n][4] are optional (NULL).  Dirichlet rows: mask [n][4] (uint8, nonzero
+ * = Dirichlet) with prescribed values yD [n][4]; both NULL for none.
+ * Immersed solid (may have m = 0): the m points located at the start of the
+ * step by fsi_locate (elem, xi [m][3] FP64, cell_start, perm), weights w [m]
+ * (NULL: 1).  The paper's solid residual R^s needs FEBio constitutive code;
+ * this library uses a point-mass stand-in per point B:
+ *   r^s_B = drho_s (a_B - g_s) + k_s dx_B,  a_B = (C^T Vdot_{n+1})_B,
+ *   dx_B = dt (C^T V_{n+1})_B,
+ * spread with the point weights: R^{f,m} += C W r^s, so that the solid block
+ * of the reduced Jacobian is C W (drho_s + k_s gamma dt^2) C^T.            */
+typedef struct {
+    double *y;
+    const double *Vn, *An, *s, *f;
+    const uint8_t *mask;
+    const double *yD;
+    int64_t m;
+    const int32_t *elem, *cell_start, *perm;
+    const double *xi, *w;
+    double drho_s, k_s;
+    double g_s[3];
+} fsi_step_state;
+
+/* Full FP64 residual of the reduced system (Sec. 2.4) at st->y:
+ * R = [R^{f,m} + C W r^s ; R^{f,c}] with Dirichlet rows replaced by y - yD.
+ * R [n][4] FP64 device, overwritten.                                       */
+fsi_status fsi_coupled_residual(fsi_mesh *mesh, const fsi_step_state *st, double *R);
+
+/* Jacobian-vector product of fsi_coupled_residual at st->y in `prec`:
+ * Jx = J_f x + C W (drho_s + k_s gamma dt^2) C^T x_v, with Dirichlet rows
+ * of Jx equal to those of x.  x and Jx [n][4] are in `prec` (the
+ * linearisation point is converted to `prec` internally).                  */
+fsi_status fsi_coupled_jacobian_apply(fsi_mesh *mesh, fsi_prec prec, const fsi_step_state *st,
+                                      const void *x, void *Jx);
+
+/* Nodal 4x4 diagonal blocks of the coupled Jacobian at st->y, by probing
+ * with the 8 node colours x 4 components (nodes of one colour share no
+ * element or cell, so each probe returns exact diagonal blocks):
+ * blocks [n][4][4] in `prec`, row-major (row = residual slot, column =
+ * unknown slot).  Dirichlet rows are unit rows.                            */
+fsi_status fsi_block_diagonal(fsi_mesh *mesh, fsi_prec prec, const fsi_step_state *st,
+                              void *blocks);
+
+/* Newton on the reduced system (Sec. 2.4) from st->y (the predictor; on
+ * return the iterate that met the tolerance, or the last one).  Each
+ * iteration: FP64 residual; right-preconditioned restarted GMRES on
+ * J dy = -R with a nodal 4x4 block-Jacobi preconditioner; y += dy in FP64.
+ *   mixed = 0: every step in FP64 (the plain method);
+ *   mixed = 1: Krylov vectors, Jacobian applies and preconditioner in FP32;
+ *              the residual, the Gram-Schmidt dot products and norms (FP64
+ *              accumulation), the Hessenberg least-squares problem and the
+ *              update stay FP64 (defect correction).
+ * Stops when ||R(y_k)||_2 <= newton_rtol * r_ref, r_ref = ||R(y_0)||_2 when
+ * opts.r_ref <= 0.  Synchronises.  Returns FSI_ERR_NOCONV when max_newton
+ * iterations did not reach the tolerance, FSI_ERR_NAN on a non-finite norm;
+ * the report is filled in every case.  Workspace is kept in the mesh.      */
+typedef struct {
+    int32_t mixed;
+    int32_t restart;       /* GMRES restart length, 1..200 (e.g. 50)          */
+    int32_t max_newton;    /* Newton iterations at most                       */
+    int32_t max_krylov;    /* Krylov iterations per Newton iteration at most  */
+    double newton_rtol;    /* e.g. 1e-8                                        */
+    double krylov_rtol;    /* inner relative tolerance, e.g. 1e-3              */
+    double r_ref;          /* > 0: reference norm of the stopping test         */
+    int32_t precond_every; /* rebuild the block-Jacobi every k Newton iterations
+                              (0: build once per call, at y_0)                */
+    int32_t reserved;
+} fsi_newton_opts;
+
+typedef struct {
+    int32_t newton_iters;  /* Newton corrections applied                      */
+    int32_t krylov_iters;  /* GMRES iterations summed over Newton iterations   */
+    double r0;             /* ||R(y_0)||_2                                     */
+    double r_final;        /* ||R(y)||_2 of the returned y                     */
+    double r_ref;          /* reference norm used by the stopping test         */
+    double seconds;        /* wall time of the call                            */
+    int32_t converged;
+    int32_t precond_builds;
+} fsi_newton_report;
+
+fsi_status fsi_newton_step(fsi_mesh *mesh, const fsi_newton_opts *opts, const fsi_step_state *st,
+                           fsi_newton_report *report);
+
 /* Measurement helper (the paper has no counterpart): the device's sustained
  * FMA throughput on the CUDA cores in `prec`, in FLOP/s (an FMA counts as 2),
  * from a dependent-chain FMA kernel over all SMs timed with CUDA events

@@ -4,6 +4,7 @@ The operators live in the CUDA library ``libfsi.so`` (C ABI: include/fsi.h);
 this package only builds it (``build.build``), binds it (``_binding``) and
 provides seeded synthetic inputs (``inputs``).
 """
-from ._binding import (FSI_F32, FSI_F64, FsiError, Mesh, fsi_dlm_interp,  # noqa: F401
-                       fsi_dlm_spread, fsi_jacobian_apply, fsi_locate, fsi_residual,
-                       fsi_stage, lib, library_path)
+from ._binding import (FSI_F32, FSI_F64, FsiError, Mesh, StepState,  # noqa: F401
+                       fsi_block_diagonal, fsi_coupled_jacobian_apply, fsi_coupled_residual,
+                       fsi_dlm_interp, fsi_dlm_spread, fsi_jacobian_apply, fsi_locate,
+                       fsi_newton_step, fsi_residual, fsi_stage, lib, library_path)

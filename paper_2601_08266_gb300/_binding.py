@@ -39,6 +39,33 @@ class fsi_physics(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class fsi_step_state(ctypes.Structure):
+    _fields_ = [("y", ctypes.c_void_p), ("Vn", ctypes.c_void_p), ("An", ctypes.c_void_p),
+                ("s", ctypes.c_void_p), ("f", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("yD", ctypes.c_void_p), ("m", ctypes.c_int64), ("elem", ctypes.c_void_p),
+                ("cell_start", ctypes.c_void_p), ("perm", ctypes.c_void_p),
+                ("xi", ctypes.c_void_p), ("w", ctypes.c_void_p), ("drho_s", ctypes.c_double),
+                ("k_s", ctypes.c_double), ("g_s", ctypes.c_double * 3)]
+
+
+class fsi_newton_opts(ctypes.Structure):
+    _fields_ = [("mixed", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("max_newton", ctypes.c_int32), ("max_krylov", ctypes.c_int32),
+                ("newton_rtol", ctypes.c_double), ("krylov_rtol", ctypes.c_double),
+                ("r_ref", ctypes.c_double), ("precond_every", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class fsi_newton_report(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int32), ("krylov_iters", ctypes.c_int32),
+                ("r0", ctypes.c_double), ("r_final", ctypes.c_double),
+                ("r_ref", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("converged", ctypes.c_int32), ("precond_builds", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -60,6 +87,11 @@ _SIGS = {
     "fsi_dlm_interp": ([_VP, _INT, _I64, _VP, _VP, _VP, _VP], _INT),
     "fsi_dlm_spread": ([_VP, _INT, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _INT], _INT),
     "fsi_measure_fma_peak": ([_INT, _INT, ctypes.POINTER(ctypes.c_double)], _INT),
+    "fsi_coupled_residual": ([_VP, ctypes.POINTER(fsi_step_state), _VP], _INT),
+    "fsi_coupled_jacobian_apply": ([_VP, _INT, ctypes.POINTER(fsi_step_state), _VP, _VP], _INT),
+    "fsi_block_diagonal": ([_VP, _INT, ctypes.POINTER(fsi_step_state), _VP], _INT),
+    "fsi_newton_step": ([_VP, ctypes.POINTER(fsi_newton_opts), ctypes.POINTER(fsi_step_state),
+                         ctypes.POINTER(fsi_newton_report)], _INT),
 }
 
 
@@ -214,3 +246,50 @@ def fsi_measure_fma_peak(device, prec):
     out = ctypes.c_double(0.0)
     _check(lib().fsi_measure_fma_peak(device, prec, ctypes.byref(out)))
     return out.value
+
+
+class StepState:
+    """Owns the torch tensors behind an fsi_step_state (all FP64 on the device)."""
+
+    def __init__(self, y, Vn, An, s=None, f=None, mask=None, yD=None, elem=None, xi=None,
+                 cell_start=None, perm=None, w=None, drho_s=0.5, k_s=0.0, g_s=(0.0, 0.0, 0.0)):
+        import torch
+        self.t = dict(y=y, Vn=Vn, An=An, s=s, f=f, mask=mask, yD=yD, elem=elem, xi=xi,
+                      cell_start=cell_start, perm=perm, w=w)
+        m = 0 if elem is None else int(elem.shape[0])
+        f64 = torch.float64
+        self.c = fsi_step_state(
+            _ptr(y, f64), _ptr(Vn, f64), _ptr(An, f64), _ptr(s, f64), _ptr(f, f64),
+            _ptr(mask, torch.uint8), _ptr(yD, f64), m, _ptr(elem, torch.int32),
+            _ptr(cell_start, torch.int32), _ptr(perm, torch.int32), _ptr(xi, f64),
+            _ptr(w, f64), float(drho_s), float(k_s), (ctypes.c_double * 3)(*g_s))
+
+
+def fsi_coupled_residual(mesh: Mesh, st: StepState, R):
+    import torch
+    _check(lib().fsi_coupled_residual(mesh.handle, ctypes.byref(st.c), _ptr(R, torch.float64)))
+
+
+def fsi_coupled_jacobian_apply(mesh: Mesh, prec, st: StepState, x, Jx):
+    dt = _prec_dtype(prec)
+    _check(lib().fsi_coupled_jacobian_apply(mesh.handle, prec, ctypes.byref(st.c), _ptr(x, dt),
+                                            _ptr(Jx, dt)))
+
+
+def fsi_block_diagonal(mesh: Mesh, prec, st: StepState, blocks):
+    dt = _prec_dtype(prec)
+    _check(lib().fsi_block_diagonal(mesh.handle, prec, ctypes.byref(st.c), _ptr(blocks, dt)))
+
+
+def fsi_newton_step(mesh: Mesh, st: StepState, mixed=True, restart=50, max_newton=10,
+                    max_krylov=1000, newton_rtol=1e-8, krylov_rtol=1e-3, r_ref=0.0,
+                    precond_every=0, check=True):
+    """Returns (status, report dict); raises on error when check is True."""
+    o = fsi_newton_opts(1 if mixed else 0, restart, max_newton, max_krylov, newton_rtol,
+                        krylov_rtol, r_ref, precond_every, 0)
+    rep = fsi_newton_report()
+    st_code = lib().fsi_newton_step(mesh.handle, ctypes.byref(o), ctypes.byref(st.c),
+                                    ctypes.byref(rep))
+    if check:
+        _check(st_code)
+    return st_code, rep.as_dict()

@@ -162,55 +162,79 @@ __global__ void scatter_kernel(int64_t m, int64_t E, const int32_t *__restrict__
 }
 
 // Sort every cell's slice of perm ascending (restores the stable order).
-// Cell E is the tail of outside points [start[E], m).
+// Cell E is the tail of outside points [start[E], m).  One warp per segment of
+// 32 consecutive cells; each slice is sorted by ranks (values are distinct
+// point indices, so rank_i = #{j : v_j < v_i} is a permutation): registers for
+// slices of up to 32, a two-phase rank pass through local arrays up to 1024,
+// and a single-lane shell sort beyond (rare: very dense cells).
+__device__ void shell_sort(int32_t *s, int len)
+{
+    int gap = 1;
+    while (gap * 9 / 4 + 1 < len) gap = gap * 9 / 4 + 1;
+    for (;;) {
+        for (int i = gap; i < len; ++i) {
+            const int v = s[i];
+            int j = i;
+            while (j >= gap && s[j - gap] > v) {
+                s[j] = s[j - gap];
+                j -= gap;
+            }
+            s[j] = v;
+        }
+        if (gap == 1) break;
+        gap = gap * 4 / 9;
+        if (gap < 1) gap = 1;
+    }
+}
+
 __global__ void cell_sort_kernel(int64_t E, int64_t m, const int32_t *__restrict__ start,
                                  int32_t *__restrict__ perm)
 {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= E;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        const int lo = start[c];
-        const int hi = (c < E) ? start[c + 1] : (int)m;
-        const int len = hi - lo;
-        if (len < 2) continue;
-        int32_t *s = perm + lo;
-        if (len <= 32) {
-            for (int i = 1; i < len; ++i) {
-                const int v = s[i];
-                int j = i - 1;
-                while (j >= 0 && s[j] > v) {
-                    s[j + 1] = s[j];
-                    --j;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c0 = warp * 32; c0 <= E; c0 += nwarps * 32) {
+        const int64_t c = c0 + lane;
+        int lo = 0, len = 0;
+        if (c <= E) {
+            lo = start[c];
+            len = (c < E ? start[c + 1] : (int)m) - lo;
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, len >= 2);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int base = __shfl_sync(0xffffffffu, lo, l);
+            const int n = __shfl_sync(0xffffffffu, len, l);
+            int32_t *sl = perm + base;
+            if (n <= 32) {
+                const int v = lane < n ? sl[lane] : INT32_MAX;
+                int rank = 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) rank += __shfl_sync(0xffffffffu, v, j) < v;
+                __syncwarp();
+                if (lane < n) sl[rank] = v;
+                __syncwarp();
+            } else if (n <= 1024) {
+                int own[32], rk[32];
+                const int nown = (n - lane + 31) / 32;  // elements lane, lane+32, ...
+                for (int i = 0; i < 32; ++i) {
+                    own[i] = (i < nown) ? sl[lane + 32 * i] : INT32_MAX;
+                    rk[i] = 0;
                 }
-                s[j + 1] = v;
-            }
-        } else {
-            // Shell sort with Ciura's gap sequence (extended by x2.25).
-            int gap = 1;
-            while (gap * 9 / 4 + 1 < len) gap = gap * 9 / 4 + 1;
-            const int ciura[8] = {701, 301, 132, 57, 23, 10, 4, 1};
-            for (;;) {
-                for (int i = gap; i < len; ++i) {
-                    const int v = s[i];
-                    int j = i;
-                    while (j >= gap && s[j - gap] > v) {
-                        s[j] = s[j - gap];
-                        j -= gap;
+                for (int k = 0; k < (n + 31) / 32; ++k) {
+                    const int w = (32 * k + lane < n) ? sl[32 * k + lane] : INT32_MAX;
+                    for (int j = 0; j < 32; ++j) {
+                        const int wj = __shfl_sync(0xffffffffu, w, j);
+                        for (int i = 0; i < nown; ++i) rk[i] += wj < own[i];
                     }
-                    s[j] = v;
                 }
-                if (gap == 1) break;
-                int next = 1;
-                if (gap > 701) {
-                    next = gap * 4 / 9;
-                    if (next < 701) next = 701;
-                } else {
-                    for (int k = 0; k < 8; ++k)
-                        if (ciura[k] < gap) {
-                            next = ciura[k];
-                            break;
-                        }
-                }
-                gap = next;
+                __syncwarp();
+                for (int i = 0; i < nown; ++i) sl[rk[i]] = own[i];
+                __syncwarp();
+            } else {
+                if (lane == 0) shell_sort(sl, n);
+                __syncwarp();
             }
         }
     }
@@ -297,19 +321,39 @@ __global__ void spread_cells_kernel(int64_t E, const T *__restrict__ xi,
                     acc[3 * a + 2] += Na * l2;
                 }
             }
+            // transpose-reduce across the warp: each level halves the values a
+            // lane carries (12, 6, 3), then a butterfly over the last two bits;
+            // the pattern is fixed, so the sums are deterministic.
+            const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
 #pragma unroll
-            for (int k = 0; k < 24; ++k) {
-                T v = acc[k];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                acc[k] = v;
+            for (int k = 0; k < 12; ++k) {
+                const T send = b4 ? acc[k] : acc[12 + k];
+                const T keep = b4 ? acc[12 + k] : acc[k];
+                acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
             }
-            if (lane < 24) {
-                T v = acc[0];
 #pragma unroll
-                for (int k = 1; k < 24; ++k)
-                    if (lane == k) v = acc[k];
-                S[(c0 + l) * 24 + lane] = v;
+            for (int k = 0; k < 6; ++k) {
+                const T send = b3 ? acc[k] : acc[6 + k];
+                const T keep = b3 ? acc[6 + k] : acc[k];
+                acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const T send = b2 ? acc[k] : acc[3 + k];
+                const T keep = b2 ? acc[3 + k] : acc[k];
+                acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 2);
+                acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 1);
+            }
+            if ((lane & 3) == 0) {
+                const int idx0 = (b4 ? 12 : 0) + (b3 ? 6 : 0) + (b2 ? 3 : 0);
+                T *dst = S + (c0 + l) * 24 + idx0;
+                dst[0] = acc[0];
+                dst[1] = acc[1];
+                dst[2] = acc[2];
             }
         }
     }
@@ -402,8 +446,8 @@ fsi_status fsi_locate(fsi_mesh *mesh, int64_t m, const double *X, int32_t *elem,
             scatter_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, E, elem, cell_start,
                                                               mesh->hash_fill, perm);
             FSI_TRY(check_launch("scatter kernel"));
-            cell_sort_kernel<<<blocks_for(E + 1, 256, 152 * 64), 256, 0, s>>>(E, m, cell_start,
-                                                                            perm);
+            cell_sort_kernel<<<blocks_for((E + 32) / 32 * 32, 256, 152 * 64), 256, 0, s>>>(
+                E, m, cell_start, perm);
             FSI_TRY(check_launch("cell sort kernel"));
         }
     }

@@ -52,6 +52,8 @@ struct Brick {
     int threads;     // CTA size (multiple of 32; 8 lanes per element)
 };
 
+struct NewtonWorkspace;
+
 // ---------------------------------------------------------------- mesh
 }  // namespace fsi
 
@@ -75,6 +77,8 @@ struct fsi_mesh {
     // scratch: per-cell corner sums of the spreading operator [E][8][3]
     void *spread_scratch;
     size_t spread_scratch_bytes;
+    // Newton / Krylov workspace (newton.cu), created on first use
+    fsi::NewtonWorkspace *newton;
 };
 
 namespace fsi {
@@ -83,6 +87,7 @@ fsi_status validate_mesh(const fsi_mesh *m);
 fsi_status ensure_vms_scratch(fsi_mesh *m, const Brick &b, size_t elem_bytes);
 size_t vms_scratch_bytes_for(const fsi_mesh *m, const Brick &b, size_t elem_bytes);
 fsi_status ensure_spread_scratch(fsi_mesh *m, size_t bytes);
+void destroy_newton_workspace(fsi_mesh *m);
 
 // VMS operators (vms.cu)
 fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,

@@ -1,0 +1,721 @@
+// newton.cu -- the implicit step on the reduced FSI system (Sec. 2.4 of the
+// paper): coupled residual and Jacobian (fluid VMS operators plus the solid
+// coupling C W D C^T through interpolation and spreading), a nodal 4x4
+// block-Jacobi preconditioner built by colour probing, restarted GMRES with
+// classical Gram-Schmidt and one reorthogonalisation (FP64 dot products), and
+// Newton with an FP64 residual and update.  In mixed mode the Krylov vectors,
+// Jacobian applies and preconditioner run in FP32 (defect correction).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fsi_internal.cuh"
+
+namespace fsi {
+namespace {
+
+constexpr int kRedGrid = 304;   // fixed partial-sum grid: deterministic dots
+constexpr int kRedThreads = 256;
+constexpr int kDotGroup = 8;    // vectors per multi-dot pass
+
+int grid1d(int64_t n, int threads = 256, int cap = 152 * 16)
+{
+    int64_t b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+#define GRID_STRIDE(i, n)                                                                  \
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n);              \
+         i += (int64_t)gridDim.x * blockDim.x)
+
+// ------------------------------------------------------------ elementwise
+template <typename Ti, typename To> __global__ void cast_kernel(int64_t n, const Ti *a, To *b)
+{
+    GRID_STRIDE(i, n) b[i] = (To)a[i];
+}
+
+template <typename T> __global__ void neg_cast_kernel(int64_t n, const double *a, T *b)
+{
+    GRID_STRIDE(i, n) b[i] = (T)(-a[i]);
+}
+
+template <typename T> __global__ void add_to_f64_kernel(int64_t n, const T *x, double *y)
+{
+    GRID_STRIDE(i, n) y[i] += (double)x[i];
+}
+
+template <typename T> __global__ void zero_kernel(int64_t n, T *x)
+{
+    GRID_STRIDE(i, n) x[i] = T(0);
+}
+
+template <typename T> __global__ void add_kernel(int64_t n, const T *x, T *y)
+{
+    GRID_STRIDE(i, n) y[i] += x[i];
+}
+
+template <typename T> __global__ void sub_kernel(int64_t n, const T *a, const T *b, T *c)
+{
+    GRID_STRIDE(i, n) c[i] = a[i] - b[i];
+}
+
+// V_{n+1} = V_n + dt Vdot_n + gamma dt (Vdot_{n+1} - Vdot_n), slot 4 = 0
+__global__ void velocity_next_kernel(int64_t n, double dt, double gamma, const double *y,
+                                     const double *Vn, const double *An, double *V1)
+{
+    GRID_STRIDE(i, n)
+    {
+        for (int c = 0; c < 3; ++c) {
+            const int64_t k = 4 * i + c;
+            V1[k] = Vn[k] + dt * An[k] + gamma * dt * (y[k] - An[k]);
+        }
+        V1[4 * i + 3] = 0.0;
+    }
+}
+
+// r^s_B = drho (a_B - g) + k dt (C^T V_{n+1})_B for inside points, 0 outside
+__global__ void solid_force_kernel(int64_t m, const int32_t *elem, const double *a,
+                                   const double *v1, double drho, double kdt, double g0,
+                                   double g1, double g2, double *rs)
+{
+    GRID_STRIDE(b, m)
+    {
+        const bool in = elem[b] >= 0;
+        const double g[3] = {g0, g1, g2};
+        for (int c = 0; c < 3; ++c)
+            rs[3 * b + c] = in ? drho * (a[3 * b + c] - g[c]) + kdt * v1[3 * b + c] : 0.0;
+    }
+}
+
+template <typename T> __global__ void scale_kernel(int64_t n, T alpha, const T *x, T *y)
+{
+    GRID_STRIDE(i, n) y[i] = alpha * x[i];
+}
+
+__global__ void dirichlet_residual_kernel(int64_t n4, const uint8_t *mask, const double *y,
+                                          const double *yD, double *R)
+{
+    GRID_STRIDE(i, n4)
+    if (mask[i]) R[i] = y[i] - yD[i];
+}
+
+template <typename T>
+__global__ void dirichlet_rows_kernel(int64_t n4, const uint8_t *mask, const T *x, T *Jx)
+{
+    GRID_STRIDE(i, n4)
+    if (mask[i]) Jx[i] = x[i];
+}
+
+// ------------------------------------------------------------ reductions
+// partial[k][block] = sum over the block's grid-stride range of V_k . w, for
+// k in [k0, k0+cnt), FP64 accumulation; fixed grid and block size.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) multi_dot_partial_kernel(
+    int k0, int cnt, int64_t len, const T *V, int64_t ld, const T *w, double *partial)
+{
+    __shared__ double red[kDotGroup][kRedThreads / 32];
+    double acc[kDotGroup];
+#pragma unroll
+    for (int j = 0; j < kDotGroup; ++j) acc[j] = 0.0;
+    GRID_STRIDE(i, len)
+    {
+        const double wi = (double)w[i];
+#pragma unroll
+        for (int j = 0; j < kDotGroup; ++j)
+            if (j < cnt) acc[j] += (double)V[(int64_t)(k0 + j) * ld + i] * wi;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kDotGroup; ++j) {
+        double v = acc[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[j][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+        double v = 0.0;
+        for (int q = 0; q < kRedThreads / 32; ++q) v += red[threadIdx.x][q];
+        partial[(int64_t)(k0 + threadIdx.x) * kRedGrid + blockIdx.x] = v;
+    }
+}
+
+// out[k] (+)= sum_b partial[k][b] for k < cnt; one block per k, fixed tree.
+// mode 0: store, 1: add, 2: store sqrt (norm)
+__global__ void multi_dot_final_kernel(int cnt, const double *partial, double *out, int mode)
+{
+    __shared__ double red[kRedThreads];
+    const int k = blockIdx.x;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < kRedGrid; b += blockDim.x) v += partial[(int64_t)k * kRedGrid + b];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (mode == 0) out[k] = red[0];
+        else if (mode == 1) out[k] += red[0];
+        else out[k] = sqrt(red[0]);
+    }
+    (void)cnt;
+}
+
+// w_i -= sum_k V_k[i] h[k], k < cnt (FP64 accumulation)
+template <typename T>
+__global__ void multi_axpy_kernel(int cnt, int64_t len, const T *V, int64_t ld, const double *h,
+                                  T *w)
+{
+    GRID_STRIDE(i, len)
+    {
+        double acc = (double)w[i];
+        for (int k = 0; k < cnt; ++k) acc -= (double)V[(int64_t)k * ld + i] * h[k];
+        w[i] = (T)acc;
+    }
+}
+
+// y = x / *den (0 when the norm vanished: lucky breakdown)
+template <typename T>
+__global__ void scale_by_inv_kernel(int64_t len, const double *den, const T *x, T *y)
+{
+    const double d = *den;
+    const double s = d > 0.0 ? 1.0 / d : 0.0;
+    GRID_STRIDE(i, len) y[i] = (T)((double)x[i] * s);
+}
+
+// ------------------------------------------------------------ block Jacobi
+__device__ __forceinline__ int node_color(int node, int NX1, int NY1)
+{
+    const int i = node % NX1, j = (node / NX1) % NY1, k = node / (NX1 * NY1);
+    return (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+}
+
+template <typename T>
+__global__ void probe_fill_kernel(int n, int NX1, int NY1, int color, int comp, T *x)
+{
+    GRID_STRIDE(node, n)
+    {
+        const bool on = node_color((int)node, NX1, NY1) == color;
+        for (int c = 0; c < 4; ++c) x[4 * node + c] = (on && c == comp) ? T(1) : T(0);
+    }
+}
+
+template <typename T>
+__global__ void probe_extract_kernel(int n, int NX1, int NY1, int color, int comp, const T *Jx,
+                                     T *blocks)
+{
+    GRID_STRIDE(node, n)
+    if (node_color((int)node, NX1, NY1) == color)
+        for (int r = 0; r < 4; ++r) blocks[16 * node + 4 * r + comp] = Jx[4 * node + r];
+}
+
+// 4x4 inverse per node, Gauss-Jordan with partial pivoting in FP64; a
+// singular block is replaced by the identity (no preconditioning there).
+template <typename T> __global__ void block_invert_kernel(int n, const T *blocks, T *inv)
+{
+    GRID_STRIDE(node, n)
+    {
+        double a[4][8];
+        for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) {
+                a[r][c] = (double)blocks[16 * node + 4 * r + c];
+                a[r][4 + c] = r == c ? 1.0 : 0.0;
+            }
+        bool ok = true;
+        for (int col = 0; col < 4 && ok; ++col) {
+            int p = col;
+            for (int r = col + 1; r < 4; ++r)
+                if (fabs(a[r][col]) > fabs(a[p][col])) p = r;
+            if (!(fabs(a[p][col]) > 0.0)) {
+                ok = false;
+                break;
+            }
+            if (p != col)
+                for (int c = 0; c < 8; ++c) {
+                    const double t = a[p][c];
+                    a[p][c] = a[col][c];
+                    a[col][c] = t;
+                }
+            const double piv = 1.0 / a[col][col];
+            for (int c = 0; c < 8; ++c) a[col][c] *= piv;
+            for (int r = 0; r < 4; ++r)
+                if (r != col) {
+                    const double f = a[r][col];
+                    for (int c = 0; c < 8; ++c) a[r][c] -= f * a[col][c];
+                }
+        }
+        for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c)
+                inv[16 * node + 4 * r + c] = ok ? (T)a[r][4 + c] : (T)(r == c ? 1.0 : 0.0);
+    }
+}
+
+template <typename T> __global__ void block_apply_kernel(int n, const T *inv, const T *x, T *y)
+{
+    GRID_STRIDE(node, n)
+    {
+        const T x0 = x[4 * node], x1 = x[4 * node + 1], x2 = x[4 * node + 2],
+                x3 = x[4 * node + 3];
+        const T *M = inv + 16 * node;
+        for (int r = 0; r < 4; ++r)
+            y[4 * node + r] = M[4 * r] * x0 + M[4 * r + 1] * x1 + M[4 * r + 2] * x2 +
+                              M[4 * r + 3] * x3;
+    }
+}
+
+// ------------------------------------------------------------ workspace
+struct Work {
+    int64_t n = 0, m = 0;
+    int restart = 0;
+    bool have = false;
+    // FP64 state
+    double *U = nullptr, *A = nullptr, *R = nullptr, *V1 = nullptr;
+    double *pa = nullptr, *pv = nullptr, *prs = nullptr;  // [m][3]
+    // working-precision buffers (8 bytes per entry so that either type fits)
+    void *Uw = nullptr, *Aw = nullptr, *fw = nullptr, *xiw = nullptr, *ww = nullptr;
+    void *pu = nullptr;                    // [m][3] point work
+    void *Vk = nullptr;                    // [restart+1][4n]
+    void *w = nullptr, *z = nullptr, *x = nullptr, *b = nullptr;
+    void *blocks = nullptr, *inv = nullptr;  // [n][16]
+    double *partial = nullptr;              // [restart+2][kRedGrid]
+    double *hcol = nullptr, *h2 = nullptr;  // [restart+2]
+    double *hhost = nullptr;                // pinned
+};
+
+void free_work(Work &W)
+{
+    void *ptrs[] = {W.U, W.A, W.R, W.V1, W.pa, W.pv, W.prs, W.Uw, W.Aw, W.fw, W.xiw, W.ww, W.pu,
+                    W.Vk, W.w, W.z, W.x, W.b, W.blocks, W.inv, W.partial, W.hcol, W.h2};
+    for (void *p : ptrs) cudaFree(p);
+    if (W.hhost) cudaFreeHost(W.hhost);
+    W = Work();
+}
+
+}  // namespace
+
+// The workspace lives in the mesh (one per mesh), behind an opaque pointer.
+struct NewtonWorkspace {
+    Work w;
+};
+
+void destroy_newton_workspace(fsi_mesh *m)
+{
+    if (m->newton) {
+        free_work(m->newton->w);
+        delete m->newton;
+        m->newton = nullptr;
+    }
+}
+
+namespace {
+
+fsi_status ensure_work(fsi_mesh *mesh, int64_t m_pts, int restart)
+{
+    if (!mesh->newton) mesh->newton = new NewtonWorkspace();
+    Work &W = mesh->newton->w;
+    const int64_t n = mesh->n_nodes;
+    if (W.have && W.n == n && W.m >= m_pts && W.restart >= restart) return FSI_OK;
+    FSI_CUDA(cudaStreamSynchronize(mesh->stream), "sync");
+    free_work(W);
+    W.n = n;
+    W.m = m_pts;
+    W.restart = restart;
+    const size_t v = (size_t)n * 4 * sizeof(double);
+    const size_t pm = (size_t)(m_pts > 0 ? m_pts : 1) * 3 * sizeof(double);
+    struct {
+        void **p;
+        size_t bytes;
+    } req[] = {
+        {(void **)&W.U, v}, {(void **)&W.A, v}, {(void **)&W.R, v}, {(void **)&W.V1, v},
+        {(void **)&W.pa, pm}, {(void **)&W.pv, pm}, {(void **)&W.prs, pm},
+        {&W.Uw, v}, {&W.Aw, v}, {&W.fw, v}, {&W.xiw, pm}, {&W.ww, pm / 3 + 8}, {&W.pu, pm},
+        {&W.Vk, v * (size_t)(restart + 1)}, {&W.w, v}, {&W.z, v}, {&W.x, v}, {&W.b, v},
+        {&W.blocks, v * 4}, {&W.inv, v * 4},
+        {(void **)&W.partial, (size_t)(restart + 2) * kRedGrid * sizeof(double)},
+        {(void **)&W.hcol, (size_t)(restart + 2) * sizeof(double)},
+        {(void **)&W.h2, (size_t)(restart + 2) * sizeof(double)},
+    };
+    for (auto &r : req) {
+        cudaError_t e = cudaMalloc(r.p, r.bytes);
+        if (e != cudaSuccess) {
+            free_work(W);
+            return check_cuda(e, "Newton workspace allocation");
+        }
+    }
+    cudaError_t e = cudaMallocHost((void **)&W.hhost, (size_t)(restart + 2) * sizeof(double));
+    if (e != cudaSuccess) {
+        free_work(W);
+        return check_cuda(e, "pinned host buffer");
+    }
+    W.have = true;
+    return FSI_OK;
+}
+
+template <typename T> fsi_prec prec_of() { return sizeof(T) == 8 ? FSI_F64 : FSI_F32; }
+
+// ------------------------------------------------------------ operators
+// FP64 coupled residual at st->y; leaves the FP64 stage in W.U, W.A.
+fsi_status coupled_residual_impl(fsi_mesh *mesh, const fsi_step_state *st, double *R)
+{
+    Work &W = mesh->newton->w;
+    cudaStream_t s = mesh->stream;
+    const int64_t n = mesh->n_nodes;
+    FSI_TRY(fsi_stage(mesh, FSI_F64, st->y, st->Vn, st->An, st->s, W.U, W.A));
+    FSI_TRY(vms_residual(mesh, FSI_F64, W.U, W.A, st->f, R));
+    if (st->m > 0) {
+        velocity_next_kernel<<<grid1d(n), 256, 0, s>>>(n, mesh->phys.dt, mesh->gamma, st->y,
+                                                      st->Vn, st->An, W.V1);
+        FSI_TRY(check_launch("velocity_next kernel"));
+        FSI_TRY(fsi_dlm_interp(mesh, FSI_F64, st->m, st->elem, st->xi, st->y, W.pa));
+        FSI_TRY(fsi_dlm_interp(mesh, FSI_F64, st->m, st->elem, st->xi, W.V1, W.pv));
+        solid_force_kernel<<<grid1d(st->m), 256, 0, s>>>(
+            st->m, st->elem, W.pa, W.pv, st->drho_s, st->k_s * mesh->phys.dt, st->g_s[0],
+            st->g_s[1], st->g_s[2], W.prs);
+        FSI_TRY(check_launch("solid force kernel"));
+        FSI_TRY(fsi_dlm_spread(mesh, FSI_F64, st->m, st->elem, st->xi, st->cell_start, st->perm,
+                               W.prs, st->w, R, 1));
+    }
+    if (st->mask) {
+        dirichlet_residual_kernel<<<grid1d(4 * n), 256, 0, s>>>(4 * n, st->mask, st->y, st->yD, R);
+        FSI_TRY(check_launch("dirichlet residual kernel"));
+    }
+    return FSI_OK;
+}
+
+// Working-precision copies of the linearisation point (after a residual).
+template <typename T> fsi_status prepare_linearisation(fsi_mesh *mesh, const fsi_step_state *st)
+{
+    Work &W = mesh->newton->w;
+    cudaStream_t s = mesh->stream;
+    const int64_t n4 = 4 * mesh->n_nodes;
+    cast_kernel<double, T><<<grid1d(n4), 256, 0, s>>>(n4, W.U, (T *)W.Uw);
+    cast_kernel<double, T><<<grid1d(n4), 256, 0, s>>>(n4, W.A, (T *)W.Aw);
+    if (st->f) cast_kernel<double, T><<<grid1d(n4), 256, 0, s>>>(n4, st->f, (T *)W.fw);
+    if (st->m > 0) {
+        cast_kernel<double, T><<<grid1d(3 * st->m), 256, 0, s>>>(3 * st->m, st->xi, (T *)W.xiw);
+        if (st->w) cast_kernel<double, T><<<grid1d(st->m), 256, 0, s>>>(st->m, st->w, (T *)W.ww);
+    }
+    return check_launch("linearisation casts");
+}
+
+template <typename T>
+fsi_status coupled_jacobian_impl(fsi_mesh *mesh, const fsi_step_state *st, const T *x, T *Jx)
+{
+    Work &W = mesh->newton->w;
+    cudaStream_t s = mesh->stream;
+    const int64_t n = mesh->n_nodes;
+    const fsi_prec P = prec_of<T>();
+    FSI_TRY(vms_jacobian(mesh, P, W.Uw, W.Aw, st->f ? W.fw : nullptr, x, Jx));
+    if (st->m > 0) {
+        FSI_TRY(fsi_dlm_interp(mesh, P, st->m, st->elem, W.xiw, x, W.pu));
+        const double D = st->drho_s + st->k_s * mesh->gamma * mesh->phys.dt * mesh->phys.dt;
+        scale_kernel<T><<<grid1d(3 * st->m), 256, 0, s>>>(3 * st->m, (T)D, (const T *)W.pu,
+                                                        (T *)W.pu);
+        FSI_TRY(check_launch("scale kernel"));
+        FSI_TRY(fsi_dlm_spread(mesh, P, st->m, st->elem, W.xiw, st->cell_start, st->perm, W.pu,
+                               st->w ? W.ww : nullptr, Jx, 1));
+    }
+    if (st->mask) {
+        dirichlet_rows_kernel<T><<<grid1d(4 * n), 256, 0, s>>>(4 * n, st->mask, x, Jx);
+        FSI_TRY(check_launch("dirichlet rows kernel"));
+    }
+    return FSI_OK;
+}
+
+template <typename T> fsi_status build_block_jacobi(fsi_mesh *mesh, const fsi_step_state *st)
+{
+    Work &W = mesh->newton->w;
+    cudaStream_t s = mesh->stream;
+    const int n = (int)mesh->n_nodes;
+    const int NX1 = mesh->grid.N[0] + 1, NY1 = mesh->grid.N[1] + 1;
+    T *px = (T *)W.z, *pj = (T *)W.w;
+    for (int color = 0; color < 8; ++color)
+        for (int comp = 0; comp < 4; ++comp) {
+            probe_fill_kernel<T><<<grid1d(n), 256, 0, s>>>(n, NX1, NY1, color, comp, px);
+            FSI_TRY(check_launch("probe fill"));
+            FSI_TRY(coupled_jacobian_impl<T>(mesh, st, px, pj));
+            probe_extract_kernel<T><<<grid1d(n), 256, 0, s>>>(n, NX1, NY1, color, comp, pj,
+                                                             (T *)W.blocks);
+            FSI_TRY(check_launch("probe extract"));
+        }
+    block_invert_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.blocks, (T *)W.inv);
+    return check_launch("block invert");
+}
+
+// ------------------------------------------------------------ Krylov helpers
+template <typename T>
+fsi_status multi_dot(fsi_mesh *mesh, int cnt, const T *V, int64_t ld, const T *w, double *out,
+                     int mode)
+{
+    Work &W = mesh->newton->w;
+    cudaStream_t s = mesh->stream;
+    const int64_t len = 4 * mesh->n_nodes;
+    for (int k0 = 0; k0 < cnt; k0 += kDotGroup) {
+        const int c = cnt - k0 < kDotGroup ? cnt - k0 : kDotGroup;
+        multi_dot_partial_kernel<T><<<kRedGrid, kRedThreads, 0, s>>>(k0, c, len, V, ld, w,
+                                                                    W.partial);
+    }
+    FSI_TRY(check_launch("multi-dot partial"));
+    multi_dot_final_kernel<<<cnt, kRedThreads, 0, s>>>(cnt, W.partial, out, mode);
+    return check_launch("multi-dot final");
+}
+
+template <typename T> fsi_status norm2(fsi_mesh *mesh, const T *x, double *dev_out)
+{
+    return multi_dot<T>(mesh, 1, x, 0, x, dev_out, 2);
+}
+
+fsi_status host_scalar(fsi_mesh *mesh, const double *dev, double *out)
+{
+    Work &W = mesh->newton->w;
+    FSI_CUDA(cudaMemcpyAsync(W.hhost, dev, sizeof(double), cudaMemcpyDeviceToHost, mesh->stream),
+             "memcpy");
+    FSI_CUDA(cudaStreamSynchronize(mesh->stream), "sync");
+    *out = W.hhost[0];
+    return FSI_OK;
+}
+
+// GMRES(restart) with right preconditioning M^{-1} (block Jacobi) on
+// J x = b, x0 = 0, to ||b - J x|| <= rtol ||b||.  Result in W.x.
+template <typename T>
+fsi_status gmres(fsi_mesh *mesh, const fsi_step_state *st, int restart, int max_its, double rtol,
+                 int *its_out)
+{
+    Work &W = mesh->newton->w;
+    cudaStream_t s = mesh->stream;
+    const int64_t len = 4 * mesh->n_nodes;
+    const int n = (int)mesh->n_nodes;
+    T *V = (T *)W.Vk, *w = (T *)W.w, *z = (T *)W.z, *x = (T *)W.x, *b = (T *)W.b;
+    const int64_t ld = len;
+    std::vector<double> H((size_t)(restart + 1) * restart, 0.0), cs(restart), sn(restart),
+        g(restart + 1), y(restart);
+    zero_kernel<T><<<grid1d(len), 256, 0, s>>>(len, x);
+    FSI_TRY(check_launch("zero"));
+    // r = b (x0 = 0)
+    cudaMemcpyAsync(w, b, len * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    double beta = 0.0, beta0 = 0.0;
+    FSI_TRY(norm2<T>(mesh, w, W.hcol));
+    FSI_TRY(host_scalar(mesh, W.hcol, &beta));
+    beta0 = beta;
+    int its = 0;
+    if (!(beta > 0.0)) {
+        *its_out = 0;
+        return std::isfinite(beta) ? FSI_OK : set_error(FSI_ERR_NAN, "GMRES: non-finite rhs");
+    }
+    const double target = rtol * beta0;
+    while (true) {
+        scale_by_inv_kernel<T><<<grid1d(len), 256, 0, s>>>(len, W.hcol, w, V);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jj = 0;
+        bool done = false;
+        for (int j = 0; j < restart && its < max_its; ++j) {
+            T *Vj = V + (int64_t)j * ld;
+            block_apply_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, Vj, z);
+            FSI_TRY(coupled_jacobian_impl<T>(mesh, st, z, w));
+            // classical Gram-Schmidt with one reorthogonalisation
+            FSI_TRY(multi_dot<T>(mesh, j + 1, V, ld, w, W.hcol, 0));
+            multi_axpy_kernel<T><<<grid1d(len), 256, 0, s>>>(j + 1, len, V, ld, W.hcol, w);
+            FSI_TRY(multi_dot<T>(mesh, j + 1, V, ld, w, W.h2, 0));
+            multi_axpy_kernel<T><<<grid1d(len), 256, 0, s>>>(j + 1, len, V, ld, W.h2, w);
+            add_kernel<double><<<1, 64, 0, s>>>(j + 1, W.h2, W.hcol);
+            FSI_TRY(norm2<T>(mesh, w, W.hcol + j + 1));
+            scale_by_inv_kernel<T><<<grid1d(len), 256, 0, s>>>(len, W.hcol + j + 1, w,
+                                                              V + (int64_t)(j + 1) * ld);
+            FSI_CUDA(cudaMemcpyAsync(W.hhost, W.hcol, (j + 2) * sizeof(double),
+                                     cudaMemcpyDeviceToHost, s),
+                     "memcpy");
+            FSI_CUDA(cudaStreamSynchronize(s), "GMRES sync");
+            ++its;
+            double *h = &H[(size_t)j * (restart + 1)];
+            for (int i = 0; i <= j + 1; ++i) h[i] = W.hhost[i];
+            if (!std::isfinite(h[j + 1]))
+                return set_error(FSI_ERR_NAN, "GMRES: non-finite Arnoldi coefficient");
+            for (int i = 0; i < j; ++i) {
+                const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+                h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+                h[i] = t;
+            }
+            const double r = std::hypot(h[j], h[j + 1]);
+            cs[j] = r > 0.0 ? h[j] / r : 1.0;
+            sn[j] = r > 0.0 ? h[j + 1] / r : 0.0;
+            h[j] = r;
+            h[j + 1] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            jj = j + 1;
+            if (std::fabs(g[j + 1]) <= target || W.hhost[j + 1] == 0.0) {
+                done = true;
+                break;
+            }
+        }
+        // back substitution and x += M^{-1} V y
+        for (int i = jj - 1; i >= 0; --i) {
+            double t = g[i];
+            for (int k = i + 1; k < jj; ++k) t -= H[(size_t)k * (restart + 1) + i] * y[k];
+            const double d = H[(size_t)i * (restart + 1) + i];
+            y[i] = d != 0.0 ? t / d : 0.0;
+        }
+        for (int i = 0; i < jj; ++i) W.hhost[i] = -y[i];
+        FSI_CUDA(cudaMemcpyAsync(W.h2, W.hhost, jj * sizeof(double), cudaMemcpyHostToDevice, s),
+                 "memcpy");
+        zero_kernel<T><<<grid1d(len), 256, 0, s>>>(len, w);
+        multi_axpy_kernel<T><<<grid1d(len), 256, 0, s>>>(jj, len, V, ld, W.h2, w);  // w = V y
+        block_apply_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, w, z);
+        add_kernel<T><<<grid1d(len), 256, 0, s>>>(len, z, x);
+        FSI_TRY(check_launch("GMRES update"));
+        if (done || its >= max_its) break;
+        // restart: r = b - J x
+        FSI_TRY(coupled_jacobian_impl<T>(mesh, st, x, z));
+        sub_kernel<T><<<grid1d(len), 256, 0, s>>>(len, b, z, w);
+        FSI_TRY(norm2<T>(mesh, w, W.hcol));
+        FSI_TRY(host_scalar(mesh, W.hcol, &beta));
+        if (!std::isfinite(beta)) return set_error(FSI_ERR_NAN, "GMRES: non-finite residual");
+        if (beta <= target) break;
+    }
+    *its_out = its;
+    return FSI_OK;
+}
+
+template <typename T>
+fsi_status newton_impl(fsi_mesh *mesh, const fsi_newton_opts *o, const fsi_step_state *st,
+                       fsi_newton_report *rep)
+{
+    Work &W = mesh->newton->w;
+    cudaStream_t s = mesh->stream;
+    const int64_t len = 4 * mesh->n_nodes;
+    FSI_TRY(coupled_residual_impl(mesh, st, W.R));
+    double r = 0.0;
+    FSI_TRY(norm2<double>(mesh, W.R, W.hcol));
+    FSI_TRY(host_scalar(mesh, W.hcol, &r));
+    rep->r0 = r;
+    rep->r_ref = o->r_ref > 0.0 ? o->r_ref : r;
+    rep->r_final = r;
+    if (!std::isfinite(r)) return set_error(FSI_ERR_NAN, "Newton: non-finite initial residual");
+    const double target = o->newton_rtol * rep->r_ref;
+    int it = 0;
+    while (r > target && it < o->max_newton) {
+        FSI_TRY(prepare_linearisation<T>(mesh, st));
+        if (rep->precond_builds == 0 || (o->precond_every > 0 && it % o->precond_every == 0)) {
+            FSI_TRY(build_block_jacobi<T>(mesh, st));
+            rep->precond_builds++;
+        }
+        neg_cast_kernel<T><<<grid1d(len), 256, 0, s>>>(len, W.R, (T *)W.b);
+        int its = 0;
+        FSI_TRY(gmres<T>(mesh, st, o->restart, o->max_krylov, o->krylov_rtol, &its));
+        rep->krylov_iters += its;
+        add_to_f64_kernel<T><<<grid1d(len), 256, 0, s>>>(len, (const T *)W.x, st->y);
+        FSI_TRY(check_launch("Newton update"));
+        ++it;
+        FSI_TRY(coupled_residual_impl(mesh, st, W.R));
+        FSI_TRY(norm2<double>(mesh, W.R, W.hcol));
+        FSI_TRY(host_scalar(mesh, W.hcol, &r));
+        rep->r_final = r;
+        rep->newton_iters = it;
+        if (!std::isfinite(r)) return set_error(FSI_ERR_NAN, "Newton: non-finite residual");
+    }
+    rep->converged = r <= target;
+    if (!rep->converged)
+        return set_error(FSI_ERR_NOCONV, "Newton: ||R|| = %.3e > %.3e after %d iterations", r,
+                         target, it);
+    return FSI_OK;
+}
+
+fsi_status validate_state(const fsi_mesh *mesh, const fsi_step_state *st)
+{
+    if (!st) return set_error(FSI_ERR_ARG, "state is NULL");
+    if (!st->y || !st->Vn || !st->An) return set_error(FSI_ERR_ARG, "state: NULL y, Vn or An");
+    if ((st->mask == nullptr) != (st->yD == nullptr))
+        return set_error(FSI_ERR_ARG, "state: pass both mask and yD, or neither");
+    if (st->m < 0 || st->m >= INT32_MAX) return set_error(FSI_ERR_ARG, "state: m out of range");
+    if (st->m > 0 && (!st->elem || !st->xi || !st->cell_start || !st->perm))
+        return set_error(FSI_ERR_ARG, "state: points need elem, xi, cell_start and perm");
+    (void)mesh;
+    return FSI_OK;
+}
+
+}  // namespace
+}  // namespace fsi
+
+using namespace fsi;
+
+extern "C" {
+
+fsi_status fsi_coupled_residual(fsi_mesh *mesh, const fsi_step_state *st, double *R)
+{
+    FSI_TRY(validate_mesh(mesh));
+    FSI_TRY(validate_state(mesh, st));
+    if (!R) return set_error(FSI_ERR_ARG, "R is NULL");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_TRY(ensure_work(mesh, st->m, 1));
+    return coupled_residual_impl(mesh, st, R);
+}
+
+fsi_status fsi_coupled_jacobian_apply(fsi_mesh *mesh, fsi_prec prec, const fsi_step_state *st,
+                                      const void *x, void *Jx)
+{
+    FSI_TRY(validate_mesh(mesh));
+    FSI_TRY(validate_state(mesh, st));
+    if (!x || !Jx || x == Jx) return set_error(FSI_ERR_ARG, "bad x / Jx");
+    if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_TRY(ensure_work(mesh, st->m, 1));
+    Work &W = mesh->newton->w;
+    FSI_TRY(coupled_residual_impl(mesh, st, W.R));
+    if (prec == FSI_F64) {
+        FSI_TRY(prepare_linearisation<double>(mesh, st));
+        return coupled_jacobian_impl<double>(mesh, st, (const double *)x, (double *)Jx);
+    }
+    FSI_TRY(prepare_linearisation<float>(mesh, st));
+    return coupled_jacobian_impl<float>(mesh, st, (const float *)x, (float *)Jx);
+}
+
+fsi_status fsi_block_diagonal(fsi_mesh *mesh, fsi_prec prec, const fsi_step_state *st,
+                              void *blocks)
+{
+    FSI_TRY(validate_mesh(mesh));
+    FSI_TRY(validate_state(mesh, st));
+    if (!blocks) return set_error(FSI_ERR_ARG, "blocks is NULL");
+    if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_TRY(ensure_work(mesh, st->m, 1));
+    Work &W = mesh->newton->w;
+    FSI_TRY(coupled_residual_impl(mesh, st, W.R));
+    const size_t bytes = (size_t)mesh->n_nodes * 16 * (prec == FSI_F64 ? 8 : 4);
+    if (prec == FSI_F64) {
+        FSI_TRY(prepare_linearisation<double>(mesh, st));
+        FSI_TRY(build_block_jacobi<double>(mesh, st));
+    } else {
+        FSI_TRY(prepare_linearisation<float>(mesh, st));
+        FSI_TRY(build_block_jacobi<float>(mesh, st));
+    }
+    FSI_CUDA(cudaMemcpyAsync(blocks, W.blocks, bytes, cudaMemcpyDeviceToDevice, mesh->stream),
+             "memcpy");
+    return FSI_OK;
+}
+
+fsi_status fsi_newton_step(fsi_mesh *mesh, const fsi_newton_opts *opts, const fsi_step_state *st,
+                           fsi_newton_report *report)
+{
+    FSI_TRY(validate_mesh(mesh));
+    FSI_TRY(validate_state(mesh, st));
+    if (!opts || !report) return set_error(FSI_ERR_ARG, "opts or report is NULL");
+    if (opts->restart < 1 || opts->restart > 200 || opts->max_newton < 0 ||
+        opts->max_krylov < 1 || !(opts->newton_rtol > 0.0) || !(opts->krylov_rtol > 0.0))
+        return set_error(FSI_ERR_ARG, "invalid Newton options");
+    std::memset(report, 0, sizeof *report);
+    const auto t0 = std::chrono::steady_clock::now();
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_TRY(ensure_work(mesh, st->m, opts->restart));
+    fsi_status stt = opts->mixed ? newton_impl<float>(mesh, opts, st, report)
+                                 : newton_impl<double>(mesh, opts, st, report);
+    cudaStreamSynchronize(mesh->stream);
+    report->seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return stt;
+}
+
+}  // extern "C"

@@ -201,6 +201,7 @@ void fsi_mesh_destroy(fsi_mesh *m)
     cudaFree(m->scan_tmp);
     cudaFree(m->dev_counters);
     cudaFree(m->spread_scratch);
+    destroy_newton_workspace(m);
     delete m;
 }
 

@@ -1,0 +1,138 @@
+"""GPU parity of the implicit step (Sec. 2.4): coupled residual, coupled
+Jacobian apply, nodal diagonal blocks and the Newton step (plain FP64 and
+mixed FP32/FP64) against the oracle's coupled problem with direct solves."""
+import numpy as np
+import pytest
+
+from paper_2601_08266_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fsi():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2601_08266_gb300 as pkg
+    return pkg
+
+
+def T(a, dtype=None):
+    import torch
+    t = torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    return t.to(dtype) if dtype is not None else t
+
+
+def H(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def setup(fsi, oracle, N=8, m=300, seed=0, dt=0.01, k_s=2.0, mu=0.05, y_scale=1.0):
+    import torch
+    from oracle import newton
+    core = oracle.core
+    grid = core.Grid(N)
+    n = grid.n_nodes
+    rng = np.random.default_rng(seed)
+    phys = dict(rho=1.0, mu=mu, dt=dt, rho_inf=0.5, has_s=True)
+    Vn = 0.5 * rng.normal(size=(n, 4))
+    An = 0.5 * rng.normal(size=(n, 4))
+    s = rng.uniform(1.0, 3.0, n)
+    f = rng.normal(size=(n, 4))
+    X = inputs.ball_points(m, seed=seed + 1, radius=0.3)
+    elem, xi, _ = core.locate(grid, X)
+    w = rng.uniform(0.5, 1.5, m)
+    Xn = grid.node_coords()
+    bnd = np.any((Xn < 1e-12) | (Xn > 1 - 1e-12), axis=1)
+    mask = np.zeros((n, 4), dtype=bool)
+    mask[bnd, :3] = True
+    mask[0, 3] = True
+    yD = np.zeros((n, 4))
+    yD[bnd, :3] = 0.3 * rng.normal(size=(bnd.sum(), 3))
+    solid = dict(drho=0.7, k=k_s, g=(0.0, 0.0, -9.81))
+    P = newton.Problem(grid, phys, Vn, An, f=f, s=s, mask=mask, yD=yD, points=(elem, xi, w),
+                       solid=solid)
+    y = y_scale * rng.normal(size=(n, 4))
+    y[mask] = yD[mask]
+
+    mesh = fsi.Mesh(N, rho=1.0, mu=mu, dt=dt, rho_inf=0.5, has_s=True, device=0)
+    e_d = torch.empty(m, dtype=torch.int32, device="cuda")
+    xi_d = torch.empty((m, 3), dtype=torch.float64, device="cuda")
+    cs_d = torch.empty(mesh.n_elems + 1, dtype=torch.int32, device="cuda")
+    pm_d = torch.empty(m, dtype=torch.int32, device="cuda")
+    fsi.fsi_locate(mesh, T(X), e_d, xi_d, cs_d, pm_d)
+    dev = dict(y=T(y), Vn=T(Vn), An=T(An), s=T(s), f=T(f), mask=T(mask.astype(np.uint8)),
+               yD=T(yD), elem=e_d, xi=xi_d, cs=cs_d, perm=pm_d, w=T(w))
+    st = fsi.StepState(dev["y"], dev["Vn"], dev["An"], s=dev["s"], f=dev["f"], mask=dev["mask"],
+                       yD=dev["yD"], elem=e_d, xi=xi_d, cell_start=cs_d, perm=pm_d, w=dev["w"],
+                       drho_s=0.7, k_s=k_s, g_s=(0.0, 0.0, -9.81))
+    return mesh, st, dev, P, y
+
+
+def test_coupled_residual_parity(fsi, oracle):
+    import torch
+    mesh, st, dev, P, y = setup(fsi, oracle)
+    R = torch.empty_like(dev["y"])
+    fsi.fsi_coupled_residual(mesh, st, R)
+    torch.cuda.synchronize()
+    assert rel(H(R), P.residual(y)) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_coupled_jacobian_parity(fsi, oracle, prec):
+    import torch
+    mesh, st, dev, P, y = setup(fsi, oracle, dt=0.05)
+    x = np.random.default_rng(9).normal(size=y.shape)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    if prec == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+    Jx = torch.empty(y.shape, dtype=dt, device="cuda")
+    fsi.fsi_coupled_jacobian_apply(mesh, fsi.FSI_F64 if prec == "f64" else fsi.FSI_F32, st,
+                                   T(x, dt), Jx)
+    torch.cuda.synchronize()
+    ref = (P.jacobian(y) @ x.ravel()).reshape(y.shape)
+    assert rel(H(Jx), ref) < (1e-12 if prec == "f64" else 1e-5)
+
+
+def test_block_diagonal_parity(fsi, oracle):
+    import torch
+    mesh, st, dev, P, y = setup(fsi, oracle, N=6, m=200, dt=0.05)
+    n = mesh.n_nodes
+    B = torch.empty((n, 4, 4), dtype=torch.float64, device="cuda")
+    fsi.fsi_block_diagonal(mesh, fsi.FSI_F64, st, B)
+    torch.cuda.synchronize()
+    J = P.jacobian(y).tocsr()
+    ref = np.zeros((n, 4, 4))
+    for a in range(n):
+        ref[a] = J[4 * a:4 * a + 4, 4 * a:4 * a + 4].toarray()
+    assert rel(H(B), ref) < 1e-12
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_newton_step_matches_direct_newton(fsi, oracle, mixed):
+    """Both the plain FP64 and the mixed step reach ||R|| <= 1e-8 ||R0|| (FP64) and
+    land on the oracle's direct-solve solution."""
+    from oracle import newton
+    mesh, st, dev, P, y0 = setup(fsi, oracle, seed=3)
+    code, rep = fsi.fsi_newton_step(mesh, st, mixed=mixed, restart=50, max_newton=12,
+                                    max_krylov=2000, newton_rtol=1e-8, krylov_rtol=1e-3)
+    assert code == 0 and rep["converged"] == 1
+    y_gpu = H(dev["y"])
+    r_check = np.linalg.norm(P.residual(y_gpu))
+    assert r_check <= 1.01e-8 * rep["r_ref"], (r_check, rep)
+    assert abs(rep["r0"] - np.linalg.norm(P.residual(y0))) <= 1e-12 * rep["r0"]
+    y_ref, hist = newton.newton(P, y0, rtol=1e-13)
+    assert rel(y_gpu, y_ref) < 1e-6, rep
+
+
+def test_newton_reports_non_convergence(fsi, oracle):
+    mesh, st, dev, P, y0 = setup(fsi, oracle, seed=4)
+    code, rep = fsi.fsi_newton_step(mesh, st, mixed=True, max_newton=1, newton_rtol=1e-14,
+                                    krylov_rtol=1e-2, check=False)
+    assert code == 5  # FSI_ERR_NOCONV
+    assert rep["converged"] == 0 and rep["newton_iters"] == 1 and rep["r_final"] < rep["r0"]
