@@ -156,6 +156,28 @@ fsi_status fsi_jacobian_apply(fsi_mesh *mesh, fsi_prec prec, const void *U, cons
 fsi_status fsi_locate(fsi_mesh *mesh, int64_t m, const double *X, int32_t *elem, double *xi,
                       int32_t *cell_start, int32_t *perm, int64_t *n_outside, int strict);
 
+/* fsi_locate without any device allocation (the paper has no counterpart).
+ * Same inputs, outputs, ordering and errors as fsi_locate, bit for bit, but
+ * it needs no fsi_mesh: the grid is passed by value and the work is issued
+ * on `cuda_stream` of CUDA device `device`.  It exists for callers that must
+ * not call cudaMalloc: code that runs inside a host application whose memory
+ * manager owns all device memory, and loops that cannot pay the implicit
+ * device-wide synchronisation of cudaMalloc/cudaFree.
+ * Its scratch (per-cell counters, scan tile sums, outside counter) lives in
+ * one static device array of about 16 MB that every device which loads the
+ * library holds until the process exits; grids with more than 4,000,000
+ * cells are rejected with FSI_ERR_ARG before anything is launched.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture
+ * begins.  All calls share the array and it keeps the last call's
+ * contents (each call clears what must start at zero): calls that overlap on
+ * the GPU (on different streams, or from different host threads) race and
+ * must be ordered by the caller.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.                                               */
+fsi_status fsi_locate_noalloc(const fsi_grid *grid, int64_t m, const double *X, int32_t *elem,
+                              double *xi, int32_t *cell_start, int32_t *perm,
+                              int64_t *n_outside, int strict, int device, void *cuda_stream);
+
 /* Interpolation of the fluid velocity to the solid points, u = C^T V
  * (Eq. nodal_solid_velo): u_B = sum_A N_A(xi_B) V_A over the 8 nodes of
  * element elem[B], velocity slots only.  xi [m][3] and U [n][4] and u [m][3]

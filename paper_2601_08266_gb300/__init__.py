@@ -7,4 +7,5 @@ provides seeded synthetic inputs (``inputs``).
 from ._binding import (FSI_F32, FSI_F64, FsiError, Mesh, StepState,  # noqa: F401
                        fsi_block_diagonal, fsi_coupled_jacobian_apply, fsi_coupled_residual,
                        fsi_dlm_interp, fsi_dlm_spread, fsi_jacobian_apply, fsi_locate,
-                       fsi_newton_step, fsi_residual, fsi_stage, lib, library_path)
+                       fsi_locate_noalloc, fsi_newton_step, fsi_residual, fsi_stage, lib,
+                       library_path)

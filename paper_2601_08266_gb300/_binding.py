@@ -92,6 +92,8 @@ _SIGS = {
     "fsi_block_diagonal": ([_VP, _INT, ctypes.POINTER(fsi_step_state), _VP], _INT),
     "fsi_newton_step": ([_VP, ctypes.POINTER(fsi_newton_opts), ctypes.POINTER(fsi_step_state),
                          ctypes.POINTER(fsi_newton_report)], _INT),
+    "fsi_locate_noalloc": ([ctypes.POINTER(fsi_grid), _I64, _VP, _VP, _VP, _VP, _VP,
+                            ctypes.POINTER(_I64), _INT, _INT, _VP], _INT),
 }
 
 
@@ -293,3 +295,22 @@ def fsi_newton_step(mesh: Mesh, st: StepState, mixed=True, restart=50, max_newto
     if check:
         _check(st_code)
     return st_code, rep.as_dict()
+
+
+def fsi_locate_noalloc(N, x0, h, X, elem, xi, cell_start=None, perm=None, want_outside=True,
+                       strict=False, device=0, stream=None):
+    """Point location that allocates no device memory (see include/fsi.h)."""
+    import torch
+    if isinstance(N, int):
+        N = (N, N, N)
+    g = fsi_grid((ctypes.c_int32 * 3)(*N), (ctypes.c_double * 3)(*x0), (ctypes.c_double * 3)(*h))
+    if stream is None:
+        stream = torch.cuda.current_stream(device).cuda_stream
+    m = 0 if X is None else X.shape[0]
+    nout = _I64(0)
+    _check(lib().fsi_locate_noalloc(ctypes.byref(g), m, _ptr(X, torch.float64),
+                                    _ptr(elem, torch.int32), _ptr(xi, torch.float64),
+                                    _ptr(cell_start, torch.int32), _ptr(perm, torch.int32),
+                                    ctypes.byref(nout) if want_outside else None,
+                                    1 if strict else 0, device, ctypes.c_void_p(stream)))
+    return int(nout.value) if want_outside else None

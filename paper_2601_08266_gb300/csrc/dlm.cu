@@ -11,6 +11,7 @@
 // eight cells of each node in a fixed order.  No races, no atomics, and the
 // result does not depend on scheduling.
 #include <cmath>
+#include <mutex>
 
 #include "fsi_internal.cuh"
 
@@ -401,6 +402,57 @@ __global__ void spread_nodes_kernel(GridArgs g, const int32_t *__restrict__ star
     }
 }
 
+// ---------------------------------------------------------------- no-allocation locate
+// fsi_locate_noalloc keeps its scratch (outside-point counter, per-cell fill
+// counters, scan tile sums) in one file-scope device array instead of mesh
+// memory, so it never allocates.  Layout in int32 slots: [0, 64) counter
+// (first 8 bytes), [64, 64 + kNoAllocMaxCells + 1 rounded up) fill counters,
+// then the tile sums.  About 16 MB per device, held until the process exits.
+constexpr int64_t kNoAllocMaxCells = 4000000;
+constexpr int64_t kNoAllocFillOffset = 64;
+constexpr int64_t kNoAllocTileOffset =
+    kNoAllocFillOffset + ((kNoAllocMaxCells + 1 + 63) / 64) * 64;
+constexpr int64_t kNoAllocInts =
+    kNoAllocTileOffset + ((kNoAllocMaxCells + kScanTile - 1) / kScanTile + 64);
+static __device__ __align__(256) int32_t g_locate_scratch[kNoAllocInts];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+int32_t *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_locate_scratch on `device` (which must be current),
+// looked up once per device.  Host code cannot use the symbol itself: its
+// host-side name is only a stand-in, not a device address.
+fsi_status noalloc_scratch(int device, int32_t **out)
+{
+    if (device < 0 || device >= kNoAllocMaxDevices)
+        return set_error(FSI_ERR_ARG, "fsi_locate_noalloc: device %d out of range", device);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        FSI_CUDA(cudaGetSymbolAddress(&p, g_locate_scratch),
+                 "fsi_locate_noalloc: cudaGetSymbolAddress of the static scratch");
+        g_noalloc_addr[device] = (int32_t *)p;
+    }
+    *out = g_noalloc_addr[device];
+    return FSI_OK;
+}
+
+GridArgs grid_args_of(const fsi_grid &gr)
+{
+    GridArgs g;
+    g.Nx = gr.N[0];
+    g.Ny = gr.N[1];
+    g.Nz = gr.N[2];
+    g.x0 = gr.x0[0];
+    g.y0 = gr.x0[1];
+    g.z0 = gr.x0[2];
+    g.hx = gr.h[0];
+    g.hy = gr.h[1];
+    g.hz = gr.h[2];
+    return g;
+}
+
 }  // namespace
 }  // namespace fsi
 
@@ -515,6 +567,76 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
             g, cell_start, (const float *)mesh->spread_scratch, (float *)F, accumulate);
     }
     return check_launch("spread nodes kernel");
+}
+
+fsi_status fsi_locate_noalloc(const fsi_grid *grid, int64_t m, const double *X, int32_t *elem,
+                              double *xi, int32_t *cell_start, int32_t *perm, int64_t *n_outside,
+                              int strict, int device, void *cuda_stream)
+{
+    if (!grid) return set_error(FSI_ERR_ARG, "fsi_locate_noalloc: grid is NULL");
+    int64_t E = 1;
+    for (int k = 0; k < 3; ++k) {
+        if (grid->N[k] < 1 || !(grid->h[k] > 0.0) || !std::isfinite(grid->h[k]) ||
+            !std::isfinite(grid->x0[k]))
+            return set_error(FSI_ERR_ARG, "fsi_locate_noalloc: invalid grid");
+        E *= grid->N[k];
+    }
+    if (E > kNoAllocMaxCells)
+        return set_error(FSI_ERR_ARG,
+                         "fsi_locate_noalloc: grid has %lld cells, more than the static "
+                         "scratch maximum of %lld; use fsi_locate with a mesh instead",
+                         (long long)E, (long long)kNoAllocMaxCells);
+    if (m < 0 || m >= INT32_MAX) return set_error(FSI_ERR_ARG, "fsi_locate_noalloc: m out of range");
+    if (m > 0 && (!X || !elem || !xi))
+        return set_error(FSI_ERR_ARG, "fsi_locate_noalloc: NULL X, elem or xi");
+    if (perm != nullptr && cell_start == nullptr)
+        return set_error(FSI_ERR_ARG, "fsi_locate_noalloc: perm given without cell_start");
+    if (cell_start != nullptr && perm == nullptr && m > 0)
+        return set_error(FSI_ERR_ARG, "fsi_locate_noalloc: cell_start given without perm");
+    FSI_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    int32_t *scratch = nullptr;
+    FSI_TRY(noalloc_scratch(device, &scratch));
+    unsigned long long *nout = (unsigned long long *)scratch;
+    int32_t *fill = scratch + kNoAllocFillOffset;
+    int32_t *tiles = scratch + kNoAllocTileOffset;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // the array keeps the previous call's contents: clear what must start at zero
+    FSI_CUDA(cudaMemsetAsync(nout, 0, sizeof(unsigned long long), s), "memset");
+    const bool table = cell_start != nullptr;
+    if (table) FSI_CUDA(cudaMemsetAsync(fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
+    GridArgs g = grid_args_of(*grid);
+    if (m > 0) {
+        locate_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, g, X, elem, xi, table ? fill : nullptr,
+                                                         nout);
+        FSI_TRY(check_launch("locate kernel"));
+    }
+    if (table) {
+        const int64_t ntiles = (E + kScanTile - 1) / kScanTile;
+        scan_tiles_kernel<<<(int)ntiles, 1024, 0, s>>>(E, fill, cell_start, tiles);
+        FSI_TRY(check_launch("scan tiles kernel"));
+        scan_totals_kernel<<<1, 1024, 0, s>>>(ntiles, tiles);
+        FSI_TRY(check_launch("scan totals kernel"));
+        scan_add_kernel<<<(int)ntiles, 256, 0, s>>>(E, cell_start, tiles);
+        FSI_TRY(check_launch("scan add kernel"));
+        if (m > 0) {
+            FSI_CUDA(cudaMemsetAsync(fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
+            scatter_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, E, elem, cell_start, fill, perm);
+            FSI_TRY(check_launch("scatter kernel"));
+            cell_sort_kernel<<<blocks_for((E + 32) / 32 * 32, 256, 152 * 64), 256, 0, s>>>(
+                E, m, cell_start, perm);
+            FSI_TRY(check_launch("cell sort kernel"));
+        }
+    }
+    if (n_outside || strict) {
+        unsigned long long h = 0;
+        FSI_CUDA(cudaMemcpyAsync(&h, nout, sizeof h, cudaMemcpyDeviceToHost, s), "memcpy");
+        FSI_CUDA(cudaStreamSynchronize(s), "stream sync");
+        if (n_outside) *n_outside = (int64_t)h;
+        if (strict && h > 0)
+            return set_error(FSI_ERR_OUTSIDE, "fsi_locate_noalloc: %llu points outside the grid",
+                             h);
+    }
+    return FSI_OK;
 }
 
 }  // extern "C"
