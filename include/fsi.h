@@ -117,6 +117,12 @@ const char *fsi_last_error(void);
 fsi_status fsi_stage(fsi_mesh *mesh, fsi_prec prec, const void *y, const void *Vn,
                      const void *An, const void *s, void *U, void *A);
 
+/* End of a time step (generalized alpha, Sec. 2.4): from the converged
+ * y = (Vdot_{n+1}, P_{n+1}) update the history in place,
+ *   Vn <- V_{n+1} = V_n + dt Vdot_n + gamma dt (Vdot_{n+1} - Vdot_n),
+ *   An <- Vdot_{n+1}  (velocity slots; slot 4 untouched).                  */
+fsi_status fsi_advance_history(fsi_mesh *mesh, fsi_prec prec, const void *y, void *Vn, void *An);
+
 /* VMS residual R [n][4] (Sec. 2.1): the Galerkin form of Eq. fluid_weak_form
  * with the residual-based VMS terms (SUPG, PSPG, LSIC, cross and Reynolds
  * stress) of Bazilevs et al. 2007, tau_m and tau_c of Sec. 2.1, 2x2x2 Gauss
@@ -288,6 +294,72 @@ typedef struct {
 
 fsi_status fsi_newton_step(fsi_mesh *mesh, const fsi_newton_opts *opts, const fsi_step_state *st,
                            fsi_newton_report *report);
+
+/* ----------------------------------------------------------------------- */
+/* Learned initial guess (an extension; the paper has no counterpart).      */
+/* A 112 -> 256 -> 256 -> 4 ReLU network predicts, per node, the correction c
+ * to the extrapolated increment e = 2 d_{n-1} - d_{n-2} (d_k = y_{k+1} - y_k)
+ * so that the Newton predictor is y^(0) = y_n + e + c.  Inputs per node: the
+ * 27-node stencil (offsets -1..1 per axis, x fastest, zero outside the grid)
+ * of (V_n velocity, P_n pressure) = 108 values, then e (4); each normalised
+ * as (x - in_mean) / in_std.  Outputs o are de-normalised as
+ * c = out_mean + out_std * o.
+ * Parameters: one FP32 device vector of fsi_mlp_num_params() values laid out
+ * W1 [112][256], b1 [256], W2 [256][256], b2 [256], W3 [256][4], b3 [4]
+ * (row = input unit).  The GEMMs run on the tensor cores with BF16 operands
+ * and FP32 accumulation.  Loss = (1/B) sum_rows 1/2 |o - t|^2.             */
+typedef struct fsi_mlp fsi_mlp;
+
+/* Handle with activation scratch for batches of up to max_batch rows. */
+fsi_status fsi_mlp_create(int device, void *cuda_stream, int64_t max_batch, fsi_mlp **out);
+void fsi_mlp_destroy(fsi_mlp *mlp);
+int64_t fsi_mlp_num_params(void);
+
+/* out [B][4] = network(X [B][112]) (normalised units). */
+fsi_status fsi_mlp_forward(fsi_mlp *mlp, const float *params, const float *X, int64_t B,
+                           float *out);
+
+/* loss (device scalar) and grad [num_params] of the batch (X [B][112], T [B][4]). */
+fsi_status fsi_mlp_loss_grad(fsi_mlp *mlp, const float *params, const float *X, const float *T,
+                             int64_t B, float *loss, float *grad);
+
+/* One Adam step (bias-corrected; step counts from 1) on params, in place. */
+fsi_status fsi_mlp_adam(fsi_mlp *mlp, float *params, const float *grad, float *m, float *v,
+                        int step, float lr, float beta1, float beta2, float eps);
+
+/* Normalised features X [k][112] of the nodes idx [k] (all n nodes when idx
+ * is NULL) from Vn [n][4] (velocity slots), y [n][4] (pressure slot) and the
+ * last two increments d1, d2 [n][4]; FP64 inputs, FP32 output.            */
+fsi_status fsi_mlp_features(fsi_mesh *mesh, const double *Vn, const double *y, const double *d1,
+                            const double *d2, const int32_t *idx, int64_t k,
+                            const float *in_mean, const float *in_std, float *X);
+
+/* Newton predictor y0 [n][4] = y + e + c for every node, in chunks of the
+ * handle's max_batch, on the mesh's stream.                                */
+fsi_status fsi_mlp_predict(fsi_mlp *mlp, fsi_mesh *mesh, const float *params,
+                           const float *in_mean, const float *in_std, const float *out_mean,
+                           const float *out_std, const double *Vn, const double *y,
+                           const double *d1, const double *d2, double *y0);
+
+/* The FP64 residual judges the network: builds the fallback predictor
+ * (fallback 0: y_n, the zero increment; 1: y_n + e) into st->y and the
+ * network's predictor into work[0 : 4n], evaluates the coupled FP64 residual
+ * of both (fsi_coupled_residual, using work[4n : 8n]) and leaves in st->y the
+ * one with the smaller norm; Dirichlet rows (st->mask) of both candidates
+ * take their prescribed values st->yD first.  work: caller-owned FP64 device
+ * array [2][n][4].
+ * yn [n][4] is y_n (must not alias st->y).  Synchronises.                  */
+typedef struct {
+    double r_fallback;  /* ||R(fallback)||_2 */
+    double r_learned;   /* ||R(network)||_2  */
+    int32_t used_learned;
+    int32_t reserved;
+} fsi_guess_report;
+
+fsi_status fsi_mlp_guess(fsi_mlp *mlp, fsi_mesh *mesh, const float *params, const float *in_mean,
+                         const float *in_std, const float *out_mean, const float *out_std,
+                         const fsi_step_state *st, const double *yn, const double *d1,
+                         const double *d2, int fallback, double *work, fsi_guess_report *rep);
 
 /* Measurement helper (the paper has no counterpart): the device's sustained
  * FMA throughput on the CUDA cores in `prec`, in FLOP/s (an FMA counts as 2),

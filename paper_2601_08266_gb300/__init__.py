@@ -4,7 +4,10 @@ The operators live in the CUDA library ``libfsi.so`` (C ABI: include/fsi.h);
 this package only builds it (``build.build``), binds it (``_binding``) and
 provides seeded synthetic inputs (``inputs``).
 """
-from ._binding import (FSI_F32, FSI_F64, FsiError, Mesh, StepState,  # noqa: F401
+from ._binding import (FSI_F32, FSI_F64, FsiError, Mesh, Mlp, StepState,  # noqa: F401
+                       fsi_mlp_adam, fsi_mlp_features, fsi_mlp_forward, fsi_mlp_loss_grad,
+                       fsi_mlp_num_params, fsi_mlp_predict, fsi_mlp_guess,
+                       fsi_advance_history,
                        fsi_block_diagonal, fsi_coupled_jacobian_apply, fsi_coupled_residual,
                        fsi_dlm_interp, fsi_dlm_spread, fsi_jacobian_apply, fsi_locate,
                        fsi_locate_noalloc, fsi_newton_step, fsi_residual, fsi_stage, lib,

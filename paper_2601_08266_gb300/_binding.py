@@ -66,6 +66,11 @@ class fsi_newton_report(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class fsi_guess_report(ctypes.Structure):
+    _fields_ = [("r_fallback", ctypes.c_double), ("r_learned", ctypes.c_double),
+                ("used_learned", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -94,6 +99,18 @@ _SIGS = {
                          ctypes.POINTER(fsi_newton_report)], _INT),
     "fsi_locate_noalloc": ([ctypes.POINTER(fsi_grid), _I64, _VP, _VP, _VP, _VP, _VP,
                             ctypes.POINTER(_I64), _INT, _INT, _VP], _INT),
+    "fsi_mlp_create": ([_INT, _VP, _I64, ctypes.POINTER(_VP)], _INT),
+    "fsi_mlp_destroy": ([_VP], None),
+    "fsi_mlp_num_params": ([], _I64),
+    "fsi_mlp_forward": ([_VP, _VP, _VP, _I64, _VP], _INT),
+    "fsi_mlp_loss_grad": ([_VP, _VP, _VP, _VP, _I64, _VP, _VP], _INT),
+    "fsi_mlp_adam": ([_VP, _VP, _VP, _VP, _VP, _INT, ctypes.c_float, ctypes.c_float,
+                      ctypes.c_float, ctypes.c_float], _INT),
+    "fsi_mlp_features": ([_VP, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP], _INT),
+    "fsi_mlp_predict": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _INT),
+    "fsi_mlp_guess": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(fsi_step_state), _VP,
+                       _VP, _VP, _INT, _VP, ctypes.POINTER(fsi_guess_report)], _INT),
+    "fsi_advance_history": ([_VP, _INT, _VP, _VP, _VP], _INT),
 }
 
 
@@ -314,3 +331,89 @@ def fsi_locate_noalloc(N, x0, h, X, elem, xi, cell_start=None, perm=None, want_o
                                     ctypes.byref(nout) if want_outside else None,
                                     1 if strict else 0, device, ctypes.c_void_p(stream)))
     return int(nout.value) if want_outside else None
+
+
+class Mlp:
+    """Owner of an fsi_mlp handle (activation scratch for max_batch rows)."""
+
+    def __init__(self, max_batch, device=0, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        out = ctypes.c_void_p()
+        _check(lib().fsi_mlp_create(device, ctypes.c_void_p(stream), int(max_batch),
+                                    ctypes.byref(out)))
+        self.handle = out
+        self.max_batch = int(max_batch)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fsi_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fsi_mlp_num_params():
+    return int(lib().fsi_mlp_num_params())
+
+
+def fsi_mlp_forward(mlp: Mlp, params, X, out):
+    import torch
+    f = torch.float32
+    _check(lib().fsi_mlp_forward(mlp.handle, _ptr(params, f), _ptr(X, f), X.shape[0],
+                                 _ptr(out, f)))
+
+
+def fsi_mlp_loss_grad(mlp: Mlp, params, X, T, loss, grad):
+    import torch
+    f = torch.float32
+    _check(lib().fsi_mlp_loss_grad(mlp.handle, _ptr(params, f), _ptr(X, f), _ptr(T, f),
+                                   X.shape[0], _ptr(loss, f), _ptr(grad, f)))
+
+
+def fsi_mlp_adam(mlp: Mlp, params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    import torch
+    f = torch.float32
+    _check(lib().fsi_mlp_adam(mlp.handle, _ptr(params, f), _ptr(grad, f), _ptr(m, f), _ptr(v, f),
+                              int(step), lr, beta1, beta2, eps))
+
+
+def fsi_mlp_features(mesh: Mesh, Vn, y, d1, d2, idx, in_mean, in_std, X):
+    import torch
+    d, f = torch.float64, torch.float32
+    k = 0 if idx is None else idx.shape[0]
+    _check(lib().fsi_mlp_features(mesh.handle, _ptr(Vn, d), _ptr(y, d), _ptr(d1, d), _ptr(d2, d),
+                                  _ptr(idx, torch.int32), k, _ptr(in_mean, f), _ptr(in_std, f),
+                                  _ptr(X, f)))
+
+
+def fsi_mlp_predict(mlp: Mlp, mesh: Mesh, params, in_mean, in_std, out_mean, out_std, Vn, y, d1,
+                    d2, y0):
+    import torch
+    d, f = torch.float64, torch.float32
+    _check(lib().fsi_mlp_predict(mlp.handle, mesh.handle, _ptr(params, f), _ptr(in_mean, f),
+                                 _ptr(in_std, f), _ptr(out_mean, f), _ptr(out_std, f),
+                                 _ptr(Vn, d), _ptr(y, d), _ptr(d1, d), _ptr(d2, d), _ptr(y0, d)))
+
+
+def fsi_advance_history(mesh: Mesh, prec, y, Vn, An):
+    dt = _prec_dtype(prec)
+    _check(lib().fsi_advance_history(mesh.handle, prec, _ptr(y, dt), _ptr(Vn, dt), _ptr(An, dt)))
+
+
+def fsi_mlp_guess(mlp: Mlp, mesh: Mesh, params, in_mean, in_std, out_mean, out_std,
+                  st: "StepState", yn, d1, d2, fallback, work):
+    import torch
+    d, f = torch.float64, torch.float32
+    rep = fsi_guess_report()
+    _check(lib().fsi_mlp_guess(mlp.handle, mesh.handle, _ptr(params, f), _ptr(in_mean, f),
+                               _ptr(in_std, f), _ptr(out_mean, f), _ptr(out_std, f),
+                               ctypes.byref(st.c), _ptr(yn, d), _ptr(d1, d), _ptr(d2, d),
+                               int(fallback), _ptr(work, d), ctypes.byref(rep)))
+    return {"r_fallback": rep.r_fallback, "r_learned": rep.r_learned,
+            "used_learned": rep.used_learned}

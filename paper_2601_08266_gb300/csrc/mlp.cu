@@ -1,0 +1,543 @@
+// mlp.cu -- the learned initial guess (an extension; the paper has no
+// counterpart): a 112 -> 256 -> 256 -> 4 ReLU network whose GEMMs run on the
+// tensor cores in BF16 with FP32 accumulation, trained on the GPU by these
+// kernels (forward, backward, Adam) and applied per node to predict the
+// Newton predictor y^(0) = y_n + e + c, e = 2 d_{n-1} - d_{n-2}.
+//
+// GEMM: C[M x N] = op(A)[M x K] op(B)[K x N] with FP32 operands in global
+// memory rounded to BF16 when staged into shared memory, mma.sync m16n8k16
+// (BF16 x BF16 -> FP32), 64x64 CTA tiles, 4 warps of 32x32, fused epilogues
+// (bias, ReLU keeping the pre-activation, multiply by a ReLU mask).
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "fsi_internal.cuh"
+
+struct fsi_mlp {
+    int device;
+    cudaStream_t stream;
+    int64_t max_batch;
+    // activations [max_batch] x {256, 256, 256, 256, 4, 4} and gradients
+    float *Z1, *H1, *Z2, *H2, *O, *dO, *dZ1, *dZ2;
+    float *X;       // features of a predict chunk [max_batch][112]
+    double *loss_partial;
+};
+
+namespace fsi {
+namespace {
+
+constexpr int NI = 112, NH = 256, NO = 4;
+constexpr int64_t OFF_W1 = 0, OFF_b1 = OFF_W1 + NI * NH, OFF_W2 = OFF_b1 + NH,
+                  OFF_b2 = OFF_W2 + NH * NH, OFF_W3 = OFF_b2 + NH, OFF_b3 = OFF_W3 + NH * NO,
+                  N_PARAMS = OFF_b3 + NO;
+
+constexpr int BM = 64, BN = 64, BK = 32, SK = BK + 8;  // SK: padded smem row (bf16)
+
+enum Epi { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_RELU = 2, EPI_MASK = 3 };
+
+struct GemmArgs {
+    int M, N, K;
+    const float *A;
+    int64_t lda;
+    int transA;
+    const float *B;
+    int64_t ldb;
+    int transB;
+    float *C;
+    int64_t ldc;
+    int epi;
+    const float *bias;  // [N] for EPI_BIAS / EPI_BIAS_RELU
+    float *Cpre;        // pre-activation output for EPI_BIAS_RELU (may be null)
+    const float *mask;  // [M x N] (ldc) for EPI_MASK: C *= (mask > 0)
+};
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[BM][SK];  // [m][k]
+    __shared__ __align__(16) __nv_bfloat16 Bs[BN][SK];  // [n][k]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int gq = lane >> 2, tq = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+        // stage A (BM x BK) and B (BK x BN) as BF16; zero outside the matrices
+        for (int e = tid; e < BM * BK; e += 128) {
+            int r, kk;
+            if (!g.transA) { r = e / BK; kk = e % BK; }   // k fastest: coalesced
+            else { kk = e / BM; r = e % BM; }             // m fastest: coalesced
+            const int gi = m0 + r, gk = k0 + kk;
+            float v = 0.f;
+            if (gi < g.M && gk < g.K)
+                v = g.transA ? g.A[(int64_t)gk * g.lda + gi] : g.A[(int64_t)gi * g.lda + gk];
+            As[r][kk] = __float2bfloat16_rn(v);
+        }
+        for (int e = tid; e < BN * BK; e += 128) {
+            int c, kk;
+            if (!g.transB) { kk = e / BN; c = e % BN; }   // n fastest
+            else { c = e / BK; kk = e % BK; }             // k fastest
+            const int gj = n0 + c, gk = k0 + kk;
+            float v = 0.f;
+            if (gj < g.N && gk < g.K)
+                v = g.transB ? g.B[(int64_t)gj * g.ldb + gk] : g.B[(int64_t)gk * g.ldb + gj];
+            Bs[c][kk] = __float2bfloat16_rn(v);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[2][4], bf[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                const int r = wm * 32 + mi * 16 + gq;
+                af[mi][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * tq]);
+                af[mi][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * tq]);
+                af[mi][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * tq + 8]);
+                af[mi][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * tq + 8]);
+            }
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) {
+                const int c = wn * 32 + ni * 8 + gq;
+                bf[ni][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + 2 * tq]);
+                bf[ni][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + 2 * tq + 8]);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bf[ni]);
+        }
+        __syncthreads();
+    }
+    // epilogue
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int i = m0 + wm * 32 + mi * 16 + gq + 8 * h;
+                    const int j = n0 + wn * 32 + ni * 8 + 2 * tq + t;
+                    if (i >= g.M || j >= g.N) continue;
+                    float v = acc[mi][ni][2 * h + t];
+                    const int64_t o = (int64_t)i * g.ldc + j;
+                    if (g.epi == EPI_BIAS || g.epi == EPI_BIAS_RELU) v += g.bias[j];
+                    if (g.epi == EPI_BIAS_RELU) {
+                        if (g.Cpre) g.Cpre[o] = v;
+                        v = v > 0.f ? v : 0.f;
+                    }
+                    if (g.epi == EPI_MASK) v = g.mask[o] > 0.f ? v : 0.f;
+                    g.C[o] = v;
+                }
+}
+
+fsi_status gemm(cudaStream_t s, GemmArgs g)
+{
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
+    gemm_bf16_kernel<<<grid, 128, 0, s>>>(g);
+    return check_launch("bf16 gemm");
+}
+
+GemmArgs ga(int M, int N, int K, const float *A, int64_t lda, int tA, const float *B, int64_t ldb,
+            int tB, float *C, int64_t ldc, int epi = EPI_STORE, const float *bias = nullptr,
+            float *Cpre = nullptr, const float *mask = nullptr)
+{
+    GemmArgs g;
+    g.M = M; g.N = N; g.K = K;
+    g.A = A; g.lda = lda; g.transA = tA;
+    g.B = B; g.ldb = ldb; g.transB = tB;
+    g.C = C; g.ldc = ldc; g.epi = epi; g.bias = bias; g.Cpre = Cpre; g.mask = mask;
+    return g;
+}
+
+// dO = (O - T)/B; per-block partial sums of 1/2 |O - T|^2 / B (FP64)
+__global__ void loss_kernel(int64_t B, const float *O, const float *T, float *dO,
+                            double *partial)
+{
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B * NO;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = O[i] - T[i];
+        dO[i] = d / (float)B;
+        acc += 0.5 * (double)d * (double)d / (double)B;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void loss_final_kernel(int nb, const double *partial, float *loss)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += partial[b];
+        *loss = (float)s;
+    }
+}
+
+// db[j] = sum_i dZ[i][j] (fixed order over i)
+__global__ void colsum_kernel(int64_t M, int N, const float *dZ, float *db)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double s = 0.0;
+    for (int64_t i = 0; i < M; ++i) s += dZ[i * N + j];
+    db[j] = (float)s;
+}
+
+__global__ void adam_kernel(int64_t n, float *p, const float *g, float *m, float *v, float lr,
+                            float b1, float b2, float eps, float c1, float c2)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// Normalised stencil features of nodes idx[0..k) (all nodes when idx == null).
+__global__ void features_kernel(int Nx, int Ny, int Nz, int64_t base, int64_t k,
+                                const int32_t *idx,
+                                const double *Vn, const double *y, const double *d1,
+                                const double *d2, const float *mean, const float *stdv, float *X)
+{
+    const int nx = Nx + 1, ny = Ny + 1, nz = Nz + 1;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < k;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int node = idx ? idx[r] : (int)(base + r);
+        const int i = node % nx, j = (node / nx) % ny, kk = node / (nx * ny);
+        float *x = X + r * NI;
+        int s = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx, ++s) {
+                    const int ii = i + dx, jj = j + dy, kz = kk + dz;
+                    const bool ok = ii >= 0 && ii < nx && jj >= 0 && jj < ny && kz >= 0 && kz < nz;
+                    const int nb = ok ? ii + nx * (jj + ny * kz) : 0;
+                    for (int c = 0; c < 4; ++c) {
+                        const double raw = ok ? (c < 3 ? Vn[4 * (int64_t)nb + c]
+                                                       : y[4 * (int64_t)nb + 3])
+                                              : 0.0;
+                        const int f = 4 * s + c;
+                        x[f] = (float)((raw - mean[f]) / stdv[f]);
+                    }
+                }
+        for (int c = 0; c < 4; ++c) {
+            const int f = 108 + c;
+            const double e = 2.0 * d1[4 * (int64_t)node + c] - d2[4 * (int64_t)node + c];
+            x[f] = (float)((e - mean[f]) / stdv[f]);
+        }
+    }
+}
+
+// y0 = y + e + (mean_c + std_c * O) for nodes [base, base + k)
+__global__ void predict_combine_kernel(int64_t base, int64_t k, const double *y, const double *d1,
+                                       const double *d2, const float *O, const float *omean,
+                                       const float *ostd, double *y0)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < k;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t node = base + r;
+        for (int c = 0; c < 4; ++c) {
+            const int64_t q = 4 * node + c;
+            const double e = 2.0 * d1[q] - d2[q];
+            y0[q] = y[q] + e + ((double)omean[c] + (double)ostd[c] * (double)O[r * NO + c]);
+        }
+    }
+}
+
+// fallback predictors: mode 0 y0 = y (zero increment), mode 1 y0 = y + e
+__global__ void fallback_kernel(int64_t n4, int mode, const double *y, const double *d1,
+                                const double *d2, double *y0)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
+         q += (int64_t)gridDim.x * blockDim.x)
+        y0[q] = mode == 1 ? y[q] + 2.0 * d1[q] - d2[q] : y[q];
+}
+
+__global__ void apply_dirichlet_kernel(int64_t n4, const uint8_t *mask, const double *yD,
+                                       double *y)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
+         q += (int64_t)gridDim.x * blockDim.x)
+        if (mask[q]) y[q] = yD[q];
+}
+
+__global__ void norm_partial_kernel(int64_t n, const double *x, double *partial)
+{
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc += x[i] * x[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+int blocks(int64_t n, int threads = 256, int cap = 152 * 16)
+{
+    int64_t b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+fsi_status forward_impl(fsi_mlp *h, const float *P, const float *X, int64_t B, bool keep)
+{
+    cudaStream_t s = h->stream;
+    FSI_TRY(gemm(s, ga((int)B, NH, NI, X, NI, 0, P + OFF_W1, NH, 0, h->H1, NH, EPI_BIAS_RELU,
+                       P + OFF_b1, keep ? h->Z1 : nullptr)));
+    FSI_TRY(gemm(s, ga((int)B, NH, NH, h->H1, NH, 0, P + OFF_W2, NH, 0, h->H2, NH, EPI_BIAS_RELU,
+                       P + OFF_b2, keep ? h->Z2 : nullptr)));
+    return gemm(s, ga((int)B, NO, NH, h->H2, NH, 0, P + OFF_W3, NO, 0, h->O, NO, EPI_BIAS,
+                      P + OFF_b3));
+}
+
+fsi_status check_mlp(const fsi_mlp *h, int64_t B)
+{
+    if (!h) return set_error(FSI_ERR_ARG, "mlp handle is NULL");
+    if (B < 1 || B > h->max_batch)
+        return set_error(FSI_ERR_ARG, "batch %lld outside [1, %lld]", (long long)B,
+                         (long long)h->max_batch);
+    return FSI_OK;
+}
+
+}  // namespace
+}  // namespace fsi
+
+using namespace fsi;
+
+extern "C" {
+
+fsi_status fsi_mlp_create(int device, void *cuda_stream, int64_t max_batch, fsi_mlp **out)
+{
+    if (!out) return set_error(FSI_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (max_batch < 1 || max_batch > (1 << 24))
+        return set_error(FSI_ERR_ARG, "max_batch must be in [1, 2^24]");
+    FSI_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    fsi_mlp *h = new (std::nothrow) fsi_mlp();
+    if (!h) return set_error(FSI_ERR_OOM, "host allocation failed");
+    h->device = device;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->max_batch = max_batch;
+    struct {
+        float **p;
+        int64_t n;
+    } req[] = {{&h->Z1, NH}, {&h->H1, NH}, {&h->Z2, NH}, {&h->H2, NH}, {&h->O, NO},
+               {&h->dO, NO}, {&h->dZ1, NH}, {&h->dZ2, NH}, {&h->X, NI}};
+    for (auto &r : req) {
+        cudaError_t e = cudaMalloc(r.p, (size_t)max_batch * r.n * sizeof(float));
+        if (e != cudaSuccess) {
+            fsi_mlp_destroy(h);
+            return check_cuda(e, "mlp activation allocation");
+        }
+    }
+    cudaError_t e = cudaMalloc(&h->loss_partial, 1024 * sizeof(double));
+    if (e != cudaSuccess) {
+        fsi_mlp_destroy(h);
+        return check_cuda(e, "mlp allocation");
+    }
+    *out = h;
+    return FSI_OK;
+}
+
+void fsi_mlp_destroy(fsi_mlp *h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    float *ptrs[] = {h->Z1, h->H1, h->Z2, h->H2, h->O, h->dO, h->dZ1, h->dZ2, h->X};
+    for (float *p : ptrs) cudaFree(p);
+    cudaFree(h->loss_partial);
+    delete h;
+}
+
+int64_t fsi_mlp_num_params(void) { return N_PARAMS; }
+
+fsi_status fsi_mlp_forward(fsi_mlp *h, const float *params, const float *X, int64_t B, float *out)
+{
+    FSI_TRY(check_mlp(h, B));
+    if (!params || !X || !out) return set_error(FSI_ERR_ARG, "NULL argument");
+    FSI_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    FSI_TRY(forward_impl(h, params, X, B, false));
+    FSI_CUDA(cudaMemcpyAsync(out, h->O, B * NO * sizeof(float), cudaMemcpyDeviceToDevice,
+                             h->stream),
+             "memcpy");
+    return FSI_OK;
+}
+
+fsi_status fsi_mlp_loss_grad(fsi_mlp *h, const float *params, const float *X, const float *T,
+                             int64_t B, float *loss, float *grad)
+{
+    FSI_TRY(check_mlp(h, B));
+    if (!params || !X || !T || !loss || !grad) return set_error(FSI_ERR_ARG, "NULL argument");
+    FSI_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t s = h->stream;
+    const float *P = params;
+    FSI_TRY(forward_impl(h, P, X, B, true));
+    const int nb = 256;
+    loss_kernel<<<nb, 256, 0, s>>>(B, h->O, T, h->dO, h->loss_partial);
+    loss_final_kernel<<<1, 32, 0, s>>>(nb, h->loss_partial, loss);
+    FSI_TRY(check_launch("loss kernels"));
+    const int M = (int)B;
+    // layer 3: dW3 = H2^T dO, db3 = colsum(dO), dZ2 = (dO W3^T) * (Z2 > 0)
+    FSI_TRY(gemm(s, ga(NH, NO, M, h->H2, NH, 1, h->dO, NO, 0, grad + OFF_W3, NO)));
+    colsum_kernel<<<1, 32, 0, s>>>(B, NO, h->dO, grad + OFF_b3);
+    FSI_TRY(gemm(s, ga(M, NH, NO, h->dO, NO, 0, P + OFF_W3, NO, 1, h->dZ2, NH, EPI_MASK,
+                       nullptr, nullptr, h->Z2)));
+    // layer 2: dW2 = H1^T dZ2, db2, dZ1 = (dZ2 W2^T) * (Z1 > 0)
+    FSI_TRY(gemm(s, ga(NH, NH, M, h->H1, NH, 1, h->dZ2, NH, 0, grad + OFF_W2, NH)));
+    colsum_kernel<<<1, 256, 0, s>>>(B, NH, h->dZ2, grad + OFF_b2);
+    FSI_TRY(gemm(s, ga(M, NH, NH, h->dZ2, NH, 0, P + OFF_W2, NH, 1, h->dZ1, NH, EPI_MASK,
+                       nullptr, nullptr, h->Z1)));
+    // layer 1: dW1 = X^T dZ1, db1
+    FSI_TRY(gemm(s, ga(NI, NH, M, X, NI, 1, h->dZ1, NH, 0, grad + OFF_W1, NH)));
+    colsum_kernel<<<1, 256, 0, s>>>(B, NH, h->dZ1, grad + OFF_b1);
+    return check_launch("bias gradients");
+}
+
+fsi_status fsi_mlp_adam(fsi_mlp *h, float *params, const float *grad, float *m, float *v,
+                        int step, float lr, float beta1, float beta2, float eps)
+{
+    if (!h) return set_error(FSI_ERR_ARG, "mlp handle is NULL");
+    if (!params || !grad || !m || !v || step < 1) return set_error(FSI_ERR_ARG, "bad argument");
+    FSI_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+    adam_kernel<<<blocks(N_PARAMS), 256, 0, h->stream>>>(N_PARAMS, params, grad, m, v, lr, beta1,
+                                                        beta2, eps, c1, c2);
+    return check_launch("adam kernel");
+}
+
+fsi_status fsi_mlp_features(fsi_mesh *mesh, const double *Vn, const double *y, const double *d1,
+                            const double *d2, const int32_t *idx, int64_t k,
+                            const float *in_mean, const float *in_std, float *X)
+{
+    FSI_TRY(validate_mesh(mesh));
+    if (!Vn || !y || !d1 || !d2 || !in_mean || !in_std || !X)
+        return set_error(FSI_ERR_ARG, "NULL argument");
+    if (!idx) k = mesh->n_nodes;
+    if (k < 0) return set_error(FSI_ERR_ARG, "k < 0");
+    if (k == 0) return FSI_OK;
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    features_kernel<<<blocks(k), 256, 0, mesh->stream>>>(mesh->grid.N[0], mesh->grid.N[1],
+                                                        mesh->grid.N[2], 0, k, idx, Vn, y, d1,
+                                                        d2, in_mean, in_std, X);
+    return check_launch("features kernel");
+}
+
+fsi_status fsi_mlp_predict(fsi_mlp *h, fsi_mesh *mesh, const float *params, const float *in_mean,
+                           const float *in_std, const float *out_mean, const float *out_std,
+                           const double *Vn, const double *y, const double *d1, const double *d2,
+                           double *y0)
+{
+    FSI_TRY(validate_mesh(mesh));
+    if (!h) return set_error(FSI_ERR_ARG, "mlp handle is NULL");
+    if (!params || !in_mean || !in_std || !out_mean || !out_std || !Vn || !y || !d1 || !d2 || !y0)
+        return set_error(FSI_ERR_ARG, "NULL argument");
+    if (h->device != mesh->device) return set_error(FSI_ERR_ARG, "mlp and mesh on other devices");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    cudaStream_t s = mesh->stream;
+    const cudaStream_t saved = h->stream;
+    h->stream = s;
+    fsi_status st = FSI_OK;
+    for (int64_t base = 0; base < mesh->n_nodes && st == FSI_OK; base += h->max_batch) {
+        const int64_t k = mesh->n_nodes - base < h->max_batch ? mesh->n_nodes - base : h->max_batch;
+        features_kernel<<<blocks(k), 256, 0, s>>>(mesh->grid.N[0], mesh->grid.N[1],
+                                                 mesh->grid.N[2], base, k, nullptr, Vn, y, d1, d2,
+                                                 in_mean, in_std, h->X);
+        st = check_launch("features kernel");
+        if (st == FSI_OK) st = forward_impl(h, params, h->X, k, false);
+        if (st == FSI_OK) {
+            predict_combine_kernel<<<blocks(k), 256, 0, s>>>(base, k, y, d1, d2, h->O, out_mean,
+                                                            out_std, y0);
+            st = check_launch("predict combine kernel");
+        }
+    }
+    h->stream = saved;
+    return st;
+}
+
+fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const float *in_mean,
+                         const float *in_std, const float *out_mean, const float *out_std,
+                         const fsi_step_state *st, const double *yn, const double *d1,
+                         const double *d2, int fallback, double *work, fsi_guess_report *rep)
+{
+    FSI_TRY(validate_mesh(mesh));
+    if (!h || !st || !st->y || !yn || !d1 || !d2 || !work || !rep)
+        return set_error(FSI_ERR_ARG, "NULL argument");
+    if (fallback != 0 && fallback != 1) return set_error(FSI_ERR_ARG, "fallback must be 0 or 1");
+    if (st->y == yn) return set_error(FSI_ERR_ARG, "st->y must not alias yn");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    cudaStream_t s = mesh->stream;
+    const int64_t n4 = 4 * mesh->n_nodes;
+    double *cand = work, *R = work + n4;
+    // candidate 0: the fallback predictor, written into st->y
+    fallback_kernel<<<blocks(n4), 256, 0, s>>>(n4, fallback, yn, d1, d2, st->y);
+    FSI_TRY(check_launch("fallback kernel"));
+    // candidate 1: the network's predictor
+    FSI_TRY(fsi_mlp_predict(h, mesh, params, in_mean, in_std, out_mean, out_std, st->Vn, yn, d1,
+                            d2, cand));
+    if (st->mask) {
+        apply_dirichlet_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->mask, st->yD, st->y);
+        apply_dirichlet_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->mask, st->yD, cand);
+        FSI_TRY(check_launch("dirichlet kernel"));
+    }
+    double r[2];
+    fsi_step_state tmp = *st;
+    const int nb = 256;
+    double host_partial[nb];
+    for (int c = 0; c < 2; ++c) {
+        tmp.y = c == 0 ? st->y : cand;
+        FSI_TRY(fsi_coupled_residual(mesh, &tmp, R));
+        norm_partial_kernel<<<nb, 256, 0, s>>>(n4, R, h->loss_partial);
+        FSI_TRY(check_launch("norm kernel"));
+        FSI_CUDA(cudaMemcpyAsync(host_partial, h->loss_partial, nb * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s),
+                 "memcpy");
+        FSI_CUDA(cudaStreamSynchronize(s), "sync");
+        double acc = 0.0;
+        for (int b = 0; b < nb; ++b) acc += host_partial[b];
+        r[c] = sqrt(acc);
+    }
+    rep->r_fallback = r[0];
+    rep->r_learned = r[1];
+    rep->used_learned = (std::isfinite(r[1]) && r[1] < r[0]) ? 1 : 0;
+    if (rep->used_learned)
+        FSI_CUDA(cudaMemcpyAsync(st->y, cand, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s),
+                 "memcpy");
+    return FSI_OK;
+}
+
+}  // extern "C"

@@ -124,6 +124,25 @@ __global__ void stage_kernel(int64_t n, T dt, T am, T af, T gamma, const vec4<T>
     }
 }
 
+// V_n <- V_{n+1} = V_n + dt Vdot_n + gamma dt (Vdot_{n+1} - Vdot_n), Vdot_n <- Vdot_{n+1}
+template <typename T>
+__global__ void advance_kernel(int64_t n, T dt, T gamma, const vec4<T> *__restrict__ y,
+                               vec4<T> *__restrict__ Vn, vec4<T> *__restrict__ An)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        vec4<T> yy = ld4(y + i), v = Vn[i], a = An[i];
+        v.x = v.x + dt * a.x + gamma * dt * (yy.x - a.x);
+        v.y = v.y + dt * a.y + gamma * dt * (yy.y - a.y);
+        v.z = v.z + dt * a.z + gamma * dt * (yy.z - a.z);
+        a.x = yy.x;
+        a.y = yy.y;
+        a.z = yy.z;
+        Vn[i] = v;
+        An[i] = a;
+    }
+}
+
 static int grid_for(int64_t n, int threads)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -251,6 +270,25 @@ fsi_status fsi_stage(fsi_mesh *m, fsi_prec prec, const void *y, const void *Vn, 
             (const vec4<float> *)y, (const vec4<float> *)Vn, (const vec4<float> *)An,
             (const float *)s, (vec4<float> *)U, (vec4<float> *)A);
     return check_launch("stage kernel");
+}
+
+fsi_status fsi_advance_history(fsi_mesh *m, fsi_prec prec, const void *y, void *Vn, void *An)
+{
+    FSI_TRY(validate_mesh(m));
+    if (!y || !Vn || !An) return set_error(FSI_ERR_ARG, "fsi_advance_history: NULL argument");
+    if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
+    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    const int threads = 256;
+    const int blocks = grid_for(m->n_nodes, threads);
+    if (prec == FSI_F64)
+        advance_kernel<double><<<blocks, threads, 0, m->stream>>>(
+            m->n_nodes, m->phys.dt, m->gamma, (const vec4<double> *)y, (vec4<double> *)Vn,
+            (vec4<double> *)An);
+    else
+        advance_kernel<float><<<blocks, threads, 0, m->stream>>>(
+            m->n_nodes, (float)m->phys.dt, (float)m->gamma, (const vec4<float> *)y,
+            (vec4<float> *)Vn, (vec4<float> *)An);
+    return check_launch("advance kernel");
 }
 
 fsi_status fsi_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A, const void *f,

