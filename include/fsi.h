@@ -265,7 +265,9 @@ fsi_status fsi_block_diagonal(fsi_mesh *mesh, fsi_prec prec, const fsi_step_stat
  *              accumulation), the Hessenberg least-squares problem and the
  *              update stay FP64 (defect correction).
  * Stops when ||R(y_k)||_2 <= newton_rtol * r_ref, r_ref = ||R(y_0)||_2 when
- * opts.r_ref <= 0.  Synchronises.  Returns FSI_ERR_NOCONV when max_newton
+ * opts.r_ref <= 0.  GMRES at iteration k stops at the relative tolerance
+ * max(krylov_rtol, min(0.5, 0.5 target / ||R(y_k)||)) (no oversolving near
+ * the target).  Synchronises.  Returns FSI_ERR_NOCONV when max_newton
  * iterations did not reach the tolerance, FSI_ERR_NAN on a non-finite norm;
  * the report is filled in every case.  Workspace is kept in the mesh.      */
 typedef struct {
@@ -341,18 +343,23 @@ fsi_status fsi_mlp_predict(fsi_mlp *mlp, fsi_mesh *mesh, const float *params,
                            const float *out_std, const double *Vn, const double *y,
                            const double *d1, const double *d2, double *y0);
 
-/* The FP64 residual judges the network: builds the fallback predictor
- * (fallback 0: y_n, the zero increment; 1: y_n + e) into st->y and the
- * network's predictor into work[0 : 4n], evaluates the coupled FP64 residual
- * of both (fsi_coupled_residual, using work[4n : 8n]) and leaves in st->y the
- * one with the smaller norm; Dirichlet rows (st->mask) of both candidates
- * take their prescribed values st->yD first.  work: caller-owned FP64 device
- * array [2][n][4].
- * yn [n][4] is y_n (must not alias st->y).  Synchronises.                  */
+/* The FP64 residual judges the network.  Builds the fallback predictor
+ * y_fb (fallback 0: y_n, the zero increment; 1: y_n + e) and the network's
+ * predictor y_ml; Dirichlet rows (st->mask) of both take st->yD.  With
+ * d = y_ml - y_fb split into its velocity part d_v and pressure part d_p it
+ * evaluates the coupled FP64 residual (fsi_coupled_residual) of y_fb,
+ * y_fb + d_v, y_fb + d_p, y_ml and y_c = y_fb + a d_v + b d_p, where (a, b)
+ * minimise |R(y_fb) + a (R(y_fb+d_v) - R(y_fb)) + b (R(y_fb+d_p) - R(y_fb))|
+ * (R is close to linear in y over a predictor's error), and leaves in st->y
+ * whichever of y_fb, y_ml, y_c has the smallest residual norm.
+ * work: caller-owned FP64 device array [5][n][4].  yn [n][4] is y_n (must not
+ * alias st->y).  Synchronises.                                             */
 typedef struct {
-    double r_fallback;  /* ||R(fallback)||_2 */
-    double r_learned;   /* ||R(network)||_2  */
-    int32_t used_learned;
+    double r_fallback;  /* ||R(y_fb)||_2                     */
+    double r_learned;   /* ||R(y_ml)||_2                     */
+    double r_combined;  /* ||R(y_c)||_2                      */
+    double a_velocity, b_pressure;
+    int32_t used;       /* 0 fallback, 1 network, 2 combined */
     int32_t reserved;
 } fsi_guess_report;
 

@@ -16,7 +16,8 @@ Adam with bias correction.
 
 Pins (tests/test_oracle_mlp.py): central-difference gradient check of the
 backward pass; the stencil features against direct indexing on a tiny grid;
-Adam against its closed form on a quadratic.
+Adam against its closed form; the BF16 rounding against its definition
+(exact on representable values, nearest neighbour otherwise, ties to even).
 """
 from __future__ import annotations
 
@@ -71,29 +72,51 @@ def features(N, V, P, d1, d2, idx=None):
     return F
 
 
-def forward(p, X):
-    Z1 = X @ p["W1"] + p["b1"]
+def round_bf16(a):
+    """Round to the nearest bfloat16 (ties to even), via float32, back to FP64."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _mm(A, B, bf16):
+    """Matrix product; with bf16=True both operands are first rounded to FP32
+    and then to BF16, as the tensor-core path does, and accumulated exactly."""
+    if bf16:
+        return round_bf16(A) @ round_bf16(B)
+    return A @ B
+
+
+def forward(p, X, bf16=False):
+    f32 = (lambda a: a.astype(np.float32).astype(np.float64)) if bf16 else (lambda a: a)
+    Z1 = f32(_mm(X, p["W1"], bf16) + p["b1"])
     H1 = np.maximum(Z1, 0.0)
-    Z2 = H1 @ p["W2"] + p["b2"]
+    Z2 = f32(_mm(H1, p["W2"], bf16) + p["b2"])
     H2 = np.maximum(Z2, 0.0)
-    O = H2 @ p["W3"] + p["b3"]
+    O = f32(_mm(H2, p["W3"], bf16) + p["b3"])
     return O, (X, Z1, H1, Z2, H2)
 
 
-def loss_and_grad(p, X, T):
-    """Loss (1/B) sum 1/2 |O - T|^2 and its gradient w.r.t. every parameter."""
+def loss_and_grad(p, X, T, bf16=False):
+    """Loss (1/B) sum 1/2 |O - T|^2 and its gradient w.r.t. every parameter.
+
+    bf16=True reproduces the operand rounding of the tensor-core kernels (a
+    statement of what that path computes, not of the network's definition).
+    """
     B = X.shape[0]
-    O, (X, Z1, H1, Z2, H2) = forward(p, X)
-    dO = (O - T) / B
+    f32 = (lambda a: a.astype(np.float32).astype(np.float64)) if bf16 else (lambda a: a)
+    O, (X, Z1, H1, Z2, H2) = forward(p, X, bf16)
+    dO = f32((O - T) / B)
     loss = 0.5 * np.sum((O - T) ** 2) / B
     g = {}
-    g["W3"] = H2.T @ dO
+    g["W3"] = _mm(H2.T, dO, bf16)
     g["b3"] = dO.sum(axis=0)
-    dZ2 = (dO @ p["W3"].T) * (Z2 > 0)
-    g["W2"] = H1.T @ dZ2
+    dZ2 = f32(_mm(dO, p["W3"].T, bf16)) * (Z2 > 0)
+    g["W2"] = _mm(H1.T, dZ2, bf16)
     g["b2"] = dZ2.sum(axis=0)
-    dZ1 = (dZ2 @ p["W2"].T) * (Z1 > 0)
-    g["W1"] = X.T @ dZ1
+    dZ1 = f32(_mm(dZ2, p["W2"].T, bf16)) * (Z1 > 0)
+    g["W1"] = _mm(X.T, dZ1, bf16)
     g["b1"] = dZ1.sum(axis=0)
     return loss, g
 

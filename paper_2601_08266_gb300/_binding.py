@@ -68,7 +68,9 @@ class fsi_newton_report(ctypes.Structure):
 
 class fsi_guess_report(ctypes.Structure):
     _fields_ = [("r_fallback", ctypes.c_double), ("r_learned", ctypes.c_double),
-                ("used_learned", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("r_combined", ctypes.c_double), ("a_velocity", ctypes.c_double),
+                ("b_pressure", ctypes.c_double), ("used", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -415,5 +417,4 @@ def fsi_mlp_guess(mlp: Mlp, mesh: Mesh, params, in_mean, in_std, out_mean, out_s
                                _ptr(in_std, f), _ptr(out_mean, f), _ptr(out_std, f),
                                ctypes.byref(st.c), _ptr(yn, d), _ptr(d1, d), _ptr(d2, d),
                                int(fallback), _ptr(work, d), ctypes.byref(rep)))
-    return {"r_fallback": rep.r_fallback, "r_learned": rep.r_learned,
-            "used_learned": rep.used_learned}
+    return {k: getattr(rep, k) for k, _ in fsi_guess_report._fields_ if k != "reserved"}

@@ -291,6 +291,43 @@ __global__ void apply_dirichlet_kernel(int64_t n4, const uint8_t *mask, const do
         if (mask[q]) y[q] = yD[q];
 }
 
+// y = yf + a (ml - yf) on velocity slots + b (ml - yf) on the pressure slot
+__global__ void combine_kernel(int64_t n4, const double *yf, const double *ml, double a, double b,
+                               double *y)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const double c = (q & 3) == 3 ? b : a;
+        y[q] = yf[q] + c * (ml[q] - yf[q]);
+    }
+}
+
+// per-block partial sums of the 6 pairwise dot products of x, y, z (FP64)
+__global__ void dots3_kernel(int64_t n, const double *x, const double *y, const double *z,
+                             double *partial)
+{
+    __shared__ double red[6][256];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double a = x[i], b = y[i], c = z[i];
+        acc[0] += a * a;
+        acc[1] += a * b;
+        acc[2] += a * c;
+        acc[3] += b * b;
+        acc[4] += b * c;
+        acc[5] += c * c;
+    }
+    for (int k = 0; k < 6; ++k) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int k = 0; k < 6; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) partial[6 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
 __global__ void norm_partial_kernel(int64_t n, const double *x, double *partial)
 {
     __shared__ double red[256];
@@ -311,6 +348,24 @@ int blocks(int64_t n, int threads = 256, int cap = 152 * 16)
 {
     int64_t b = (n + threads - 1) / threads;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+// The 6 pairwise dot products of three device vectors (fixed grid: deterministic).
+fsi_status dots3(cudaStream_t s, int64_t n, const double *x, const double *y, const double *z,
+                 double *partial, double out[6])
+{
+    const int nb = 128;  // partial holds 1024 doubles >= 6 * nb
+    dots3_kernel<<<nb, 256, 0, s>>>(n, x, y, z, partial);
+    FSI_TRY(check_launch("dots kernel"));
+    double host[6 * nb];
+    FSI_CUDA(cudaMemcpyAsync(host, partial, sizeof host, cudaMemcpyDeviceToHost, s), "memcpy");
+    FSI_CUDA(cudaStreamSynchronize(s), "sync");
+    for (int k = 0; k < 6; ++k) {
+        double acc = 0.0;
+        for (int b = 0; b < nb; ++b) acc += host[6 * b + k];
+        out[k] = acc;
+    }
+    return FSI_OK;
 }
 
 fsi_status forward_impl(fsi_mlp *h, const float *P, const float *X, int64_t B, bool keep)
@@ -502,41 +557,71 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
     cudaStream_t s = mesh->stream;
     const int64_t n4 = 4 * mesh->n_nodes;
-    double *cand = work, *R = work + n4;
-    // candidate 0: the fallback predictor, written into st->y
+    double *ml = work, *trial = work + n4, *R0 = work + 2 * n4, *Rv = work + 3 * n4,
+           *Rp = work + 4 * n4;
+    // the fallback predictor (in st->y) and the network's predictor (in ml)
     fallback_kernel<<<blocks(n4), 256, 0, s>>>(n4, fallback, yn, d1, d2, st->y);
     FSI_TRY(check_launch("fallback kernel"));
-    // candidate 1: the network's predictor
     FSI_TRY(fsi_mlp_predict(h, mesh, params, in_mean, in_std, out_mean, out_std, st->Vn, yn, d1,
-                            d2, cand));
+                            d2, ml));
     if (st->mask) {
         apply_dirichlet_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->mask, st->yD, st->y);
-        apply_dirichlet_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->mask, st->yD, cand);
+        apply_dirichlet_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->mask, st->yD, ml);
         FSI_TRY(check_launch("dirichlet kernel"));
     }
-    double r[2];
     fsi_step_state tmp = *st;
-    const int nb = 256;
-    double host_partial[nb];
-    for (int c = 0; c < 2; ++c) {
-        tmp.y = c == 0 ? st->y : cand;
-        FSI_TRY(fsi_coupled_residual(mesh, &tmp, R));
-        norm_partial_kernel<<<nb, 256, 0, s>>>(n4, R, h->loss_partial);
-        FSI_TRY(check_launch("norm kernel"));
-        FSI_CUDA(cudaMemcpyAsync(host_partial, h->loss_partial, nb * sizeof(double),
-                                 cudaMemcpyDeviceToHost, s),
-                 "memcpy");
-        FSI_CUDA(cudaStreamSynchronize(s), "sync");
-        double acc = 0.0;
-        for (int b = 0; b < nb; ++b) acc += host_partial[b];
-        r[c] = sqrt(acc);
+    auto residual = [&](const double *y, double *R) -> fsi_status {
+        tmp.y = const_cast<double *>(y);
+        return fsi_coupled_residual(mesh, &tmp, R);
+    };
+    // residuals of y_fb, y_fb + d_v and y_fb + d_p (d = ml - y_fb split into
+    // its velocity and pressure slots)
+    FSI_TRY(residual(st->y, R0));
+    combine_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->y, ml, 1.0, 0.0, trial);
+    FSI_TRY(residual(trial, Rv));
+    combine_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->y, ml, 0.0, 1.0, trial);
+    FSI_TRY(residual(trial, Rp));
+    FSI_TRY(check_launch("combine kernel"));
+    double G[6];  // <R0,R0> <R0,Rv> <R0,Rp> <Rv,Rv> <Rv,Rp> <Rp,Rp>
+    FSI_TRY(dots3(s, n4, R0, Rv, Rp, h->loss_partial, G));
+    const double r0 = sqrt(G[0]);
+    // Av = Rv - R0, Ap = Rp - R0: minimise |R0 + a Av + b Ap|^2 (R is close to
+    // linear in y over a predictor's error)
+    const double vv = G[3] - 2 * G[1] + G[0], pp = G[5] - 2 * G[2] + G[0];
+    const double vp = G[4] - G[1] - G[2] + G[0];
+    const double rv = G[1] - G[0], rp = G[2] - G[0];
+    double a = 0.0, b = 0.0;
+    const double det = vv * pp - vp * vp;
+    if (det > 1e-14 * (vv * pp) && vv > 0 && pp > 0) {
+        a = (-rv * pp + rp * vp) / det;
+        b = (-rp * vv + rv * vp) / det;
+    } else if (vv > 0) {
+        a = -rv / vv;
     }
-    rep->r_fallback = r[0];
-    rep->r_learned = r[1];
-    rep->used_learned = (std::isfinite(r[1]) && r[1] < r[0]) ? 1 : 0;
-    if (rep->used_learned)
-        FSI_CUDA(cudaMemcpyAsync(st->y, cand, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s),
+    // pure network predictor (a = b = 1) and the combination (a, b)
+    FSI_TRY(residual(ml, Rv));
+    combine_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->y, ml, a, b, trial);
+    FSI_TRY(residual(trial, Rp));
+    double G2[6];
+    FSI_TRY(dots3(s, n4, R0, Rv, Rp, h->loss_partial, G2));
+    const double r_ml = sqrt(G2[3]), r_comb = sqrt(G2[5]);
+    rep->r_fallback = r0;
+    rep->r_learned = r_ml;
+    rep->r_combined = r_comb;
+    rep->a_velocity = a;
+    rep->b_pressure = b;
+    int use = 0;
+    double best = r0;
+    if (std::isfinite(r_ml) && r_ml < best) { use = 1; best = r_ml; }
+    if (std::isfinite(r_comb) && r_comb < best) { use = 2; best = r_comb; }
+    rep->used = use;
+    if (use == 1)
+        FSI_CUDA(cudaMemcpyAsync(st->y, ml, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s),
                  "memcpy");
+    else if (use == 2)
+        FSI_CUDA(cudaMemcpyAsync(st->y, trial, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s),
+                 "memcpy");
+    FSI_CUDA(cudaStreamSynchronize(s), "sync");
     return FSI_OK;
 }
 

@@ -54,13 +54,21 @@ def test_forward_and_gradients_match_oracle(fsi):
     grad = torch.empty_like(P)
     fsi.fsi_mlp_loss_grad(h, P, T(X, torch.float32), T(Tt, torch.float32), loss, grad)
     torch.cuda.synchronize()
+    # against the oracle with the kernels' BF16 operand rounding: FP32
+    # accumulation is the only remaining difference
+    O_b, _ = om.forward(p, X, bf16=True)
+    l_b, g_b = om.loss_and_grad(p, X, Tt, bf16=True)
+    assert rel(H(out), O_b) < 1e-4
+    assert abs(float(loss.item()) - l_b) < 1e-4 * l_b
+    g = om.unflatten(H(grad))
+    for name, _ in om.param_shapes():
+        assert rel(g[name], g_b[name]) < 2e-3, name
+    # against exact FP64 arithmetic: BF16 operands bound the agreement
     O_ref, _ = om.forward(p, X)
     l_ref, g_ref = om.loss_and_grad(p, X, Tt)
     assert rel(H(out), O_ref) < 2e-2
-    assert abs(float(loss.item()) - l_ref) < 2e-2 * l_ref
-    g = om.unflatten(H(grad))
     for name, _ in om.param_shapes():
-        assert rel(g[name], g_ref[name]) < 3e-2, name
+        assert rel(g[name], g_ref[name]) < 8e-2, name
 
 
 def test_features_match_oracle(fsi, oracle):
@@ -139,8 +147,10 @@ def run_series(fsi, N, steps, dt=0.01, period=0.12, learn=None, seed=0):
     cs = torch.empty(mesh.n_elems + 1, dtype=torch.int32, device="cuda")
     pm = torch.empty(m, dtype=torch.int32, device="cuda")
     fsi.fsi_locate(mesh, T(Xp), e, xi, cs, pm)
+    # each point carries its share of the leaflets' volume (3 x 0.8 x 0.5 x 0.02)
+    wpts = torch.full((m,), 0.024 / m, dtype=torch.float64, device="cuda")
     maskd = T(mask)
-    work = torch.empty((2, n, 4), dtype=torch.float64, device="cuda")
+    work = torch.empty((5, n, 4), dtype=torch.float64, device="cuda")
     recs = []
     for k in range(steps):
         t1 = (k + 1) * dt
@@ -150,7 +160,7 @@ def run_series(fsi, N, steps, dt=0.01, period=0.12, learn=None, seed=0):
         yD[:, :3] = (g - Vn[:, :3] - dt * (1 - gamma) * An[:, :3]) / (gamma * dt)
         y = yn.clone()
         st = fsi.StepState(y, Vn, An, mask=maskd, yD=yD, elem=e, xi=xi, cell_start=cs, perm=pm,
-                           drho_s=0.5)
+                           w=wpts, drho_s=0.5)
         rec = {"step": k}
         if learn is not None and k >= 2:
             rec["guess"] = fsi.fsi_mlp_guess(learn["h"], mesh, learn["P"], learn["im"],
@@ -165,8 +175,11 @@ def run_series(fsi, N, steps, dt=0.01, period=0.12, learn=None, seed=0):
                            torch.ones(112, dtype=torch.float32, device="cuda"))
             fsi.fsi_mlp_features(mesh, Vn, yn, d1, d2, None, zeros, ones, Xf)
             rec["X"] = Xf.cpu().numpy()
+        # same absolute target with or without the network: the fallback's residual
+        r_ref = rec["guess"]["r_fallback"] if "guess" in rec else 0.0
         code, rep = fsi.fsi_newton_step(mesh, st, mixed=True, restart=50, max_newton=8,
-                                        max_krylov=3000, newton_rtol=1e-8, krylov_rtol=1e-3)
+                                        max_krylov=3000, newton_rtol=1e-8, krylov_rtol=1e-3,
+                                        r_ref=r_ref)
         rec["rep"] = rep
         d_new = y - yn
         if "X" in rec:
@@ -180,11 +193,20 @@ def run_series(fsi, N, steps, dt=0.01, period=0.12, learn=None, seed=0):
 
 @pytest.mark.slow
 def test_learned_guess_end_to_end(fsi, capsys):
+    """Train on GPU-generated steps of a pulsatile channel (interior rows, after
+    the start-up transient), then predict the Newton predictor on a run with
+    other leaflets.  The FP64 residual judges each step's predictor; the test
+    records what the network gains over the extrapolated fallback."""
     import torch
-    N = 12
-    recs = run_series(fsi, N, steps=12)
-    X = np.concatenate([r["X"] for r in recs if "X" in r])
-    C = np.concatenate([r["C"] for r in recs if "X" in r])
+    N, skip = 14, 5
+    recs = run_series(fsi, N, steps=26)
+    mask, _ = _channel(N, 0.01, 0.12)
+    dirichlet = mask.astype(bool)
+    # all nodes; Dirichlet components get a zero target (they take their
+    # prescribed values after the prediction anyway)
+    X = np.concatenate([r["X"] for r in recs if "X" in r and r["step"] >= skip])
+    C = np.concatenate([np.where(dirichlet, 0.0, r["C"]) for r in recs
+                        if "X" in r and r["step"] >= skip])
     im, isd = X.mean(0), X.std(0) + 1e-6
     om_, osd = C.mean(0), C.std(0) + 1e-12
     Xn = ((X - im) / isd).astype(np.float32)
@@ -198,21 +220,60 @@ def test_learned_guess_end_to_end(fsi, capsys):
     rng = np.random.default_rng(0)
     Xd, Cd = T(Xn), T(Cn)
     losses = []
-    for it in range(1, 601):
-        idx = T(rng.integers(0, len(Xn), size=1024))
+    iters = 1500
+    for it in range(1, iters + 1):
+        idx = T(rng.integers(0, len(Xn), size=2048))
         fsi.fsi_mlp_loss_grad(h, P, Xd[idx].contiguous(), Cd[idx].contiguous(), loss, G)
-        fsi.fsi_mlp_adam(h, P, G, Mo, Vo, it, lr=1e-3)
-        if it in (1, 600):
+        lr = 1e-3 if it < 1000 else 3e-4
+        fsi.fsi_mlp_adam(h, P, G, Mo, Vo, it, lr=lr)
+        if it in (1, iters):
             losses.append(float(loss.item()))
-    assert losses[-1] < 0.5 * losses[0], losses
-    learn = dict(h=h, P=P, im=T(im.astype(np.float32)), is_=None)
+    assert losses[-1] < 0.3 * losses[0], losses
     learn = {"h": h, "P": P, "im": T(im.astype(np.float32)), "is": T(isd.astype(np.float32)),
              "om": T(om_.astype(np.float32)), "os": T(osd.astype(np.float32))}
-    recs2 = run_series(fsi, N, steps=12, learn=learn, seed=1)
-    gains = [(r["guess"]["r_fallback"], r["guess"]["r_learned"], r["guess"]["used_learned"],
-              r["rep"]["krylov_iters"]) for r in recs2 if "guess" in r]
-    for rf, rl, used, _ in gains:
-        # the residual is the judge: the kept predictor is never worse
-        assert min(rf, rl) <= rf
+    recs2 = run_series(fsi, N, steps=16, learn=learn, seed=1)
+    rows = [(r["step"], r["guess"]["r_fallback"], r["guess"]["r_learned"],
+             r["guess"]["r_combined"], r["guess"]["used"], r["rep"]["krylov_iters"],
+             r["rep"]["newton_iters"]) for r in recs2 if "guess" in r]
+    # the same steps with the fallback alone (the method without the network)
+    base = {r["step"]: (r["rep"]["krylov_iters"], r["rep"]["newton_iters"], r["rep"]["r0"])
+            for r in run_series(fsi, N, steps=16, seed=1)}
+    periodic = [rw for rw in rows if rw[0] >= skip + 1]
+    wins = sum(1 for rw in periodic if rw[4] != 0)
+    gain = np.median([rw[1] / min(rw[1], rw[2], rw[3]) for rw in periodic])
     with capsys.disabled():
-        print("\nlearned-guess gains (r_fallback, r_learned, used, krylov):", gains)
+        print("\nloss", losses)
+        print("(step, r_fallback, r_network, r_combined, used, krylov, newton | fallback-only krylov, newton)")
+        for rw in rows:
+            print("  ", rw, "|", base[rw[0]][:2])
+        print(f"network or combination kept in {wins} of {len(periodic)} periodic steps; "
+              f"median residual reduction of the predictor x{gain:.2f}")
+    for rw in rows:   # the residual is the judge: the kept predictor is the best one
+        assert min(rw[1], rw[2], rw[3]) <= rw[1]
+    assert wins >= len(periodic) // 2, rows
+
+
+def test_predict_matches_oracle(fsi):
+    """y0 = y + e + (out_mean + out_std * net((features - in_mean) / in_std))."""
+    import torch
+    from oracle import mlp as om
+    N = (6, 5, 7)
+    mesh = fsi.Mesh(N, device=0)
+    n = mesh.n_nodes
+    rng = np.random.default_rng(4)
+    Vn, y, d1, d2 = (rng.normal(size=(n, 4)) for _ in range(4))
+    im = rng.normal(size=112).astype(np.float32)
+    isd = rng.uniform(0.5, 2, 112).astype(np.float32)
+    omu = rng.normal(size=4).astype(np.float32)
+    osd = rng.uniform(0.5, 2, 4).astype(np.float32)
+    p = om.init_params(5)
+    theta = om.flatten(p).astype(np.float32).astype(np.float64)
+    h = fsi.Mlp(100)  # several chunks
+    y0 = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+    fsi.fsi_mlp_predict(h, mesh, T(theta, torch.float32), T(im), T(isd), T(omu), T(osd), T(Vn),
+                        T(y), T(d1), T(d2), y0)
+    torch.cuda.synchronize()
+    Xf = ((om.features(N, Vn[:, :3], y[:, 3], d1, d2) - im) / isd).astype(np.float32)
+    O, _ = om.forward(om.unflatten(theta), Xf.astype(np.float64), bf16=True)
+    ref = y + 2 * d1 - d2 + (omu.astype(np.float64) + osd.astype(np.float64) * O)
+    assert rel(H(y0), ref) < 3e-4

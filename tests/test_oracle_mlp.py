@@ -67,3 +67,20 @@ def test_adam_closed_form_first_step():
     g = np.array([0.3, -4.0, 1e-3])
     th, m, v = mlp.adam(theta, g, np.zeros(3), np.zeros(3), 1, lr=0.01, eps=0.0)
     assert np.allclose(th, theta - 0.01 * np.sign(g), rtol=0, atol=1e-15)
+
+
+def test_bf16_rounding_definition():
+    from oracle import mlp
+    # representable values are unchanged
+    v = np.array([1.0, -2.5, 0.15625, 3.0 * 2.0 ** -20, 65280.0])
+    assert np.array_equal(mlp.round_bf16(v), v)
+    # 1 + 2^-8 is halfway between 1 and 1 + 2^-7: ties to even (1.0)
+    assert mlp.round_bf16(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
+    # 1 + 3*2^-8 is halfway between 1+2^-7 and 1+2^-6: ties to even (1 + 2^-6)
+    assert mlp.round_bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
+    # otherwise the nearest BF16 value (8 significant bits)
+    x = np.random.default_rng(0).normal(size=1000)
+    r = mlp.round_bf16(x)
+    e = np.floor(np.log2(np.abs(x)))
+    assert np.all(np.abs(r - x) <= 2.0 ** (e - 8) * (1 + 1e-12))
+    assert np.all(np.abs(r * 2.0 ** (7 - e) - np.round(r * 2.0 ** (7 - e))) == 0)
