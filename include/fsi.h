@@ -368,6 +368,72 @@ fsi_status fsi_mlp_guess(fsi_mlp *mlp, fsi_mesh *mesh, const float *params, cons
                          const fsi_step_state *st, const double *yn, const double *d1,
                          const double *d2, int fallback, double *work, fsi_guess_report *rep);
 
+/* ----------------------------------------------------------------------- */
+/* Batched ensemble (an extension; the paper has no counterpart).           */
+/* Many independent instances (each its own mesh: grid, physics) of uneven
+ * size.  One item per instance: device arrays in the batch's precision,
+ * contiguous, owned by the caller and kept valid (same pointers) for the
+ * batch's lifetime: U, A, f (or NULL), x, R, Jx [n_i][4]; points (m may be
+ * 0): elem, cell_start, perm from fsi_locate, xi [m][3], lam [m][3], w [m]
+ * (or NULL), u [m][3]; spreading writes F [n_i][4] (slots 0..2, overwrite).
+ * One batched step = for every instance R = residual(U, A, f),
+ * Jx = J(U, A, f) x, u = C^T U, F = C lambda.                              */
+typedef struct {
+    const void *U, *A, *f, *x;
+    void *R, *Jx;
+    int64_t m;
+    const int32_t *elem, *cell_start, *perm;
+    const void *xi, *lam, *w;
+    void *u, *F;
+} fsi_batch_item;
+
+typedef struct fsi_batch fsi_batch;
+
+enum {
+    FSI_BATCH_PER_INSTANCE = 0, /* the single-mesh entry points, instance by instance */
+    FSI_BATCH_PERSISTENT = 1,   /* persistent grids over all instances' work items      */
+    FSI_BATCH_GRAPH = 2         /* the persistent step captured once in a CUDA graph and
+                                   replayed (needs a non-default stream)                */
+};
+
+/* Build a batch (descriptors, prefix sums and its own scratch) on `cuda_stream`.
+ * All meshes must be on one device.  The batch uses one brick shape for all
+ * instances (default 8x8x4; see fsi_batch_autotune).                       */
+fsi_status fsi_batch_create(fsi_mesh *const *meshes, const fsi_batch_item *items, int count,
+                            fsi_prec prec, void *cuda_stream, fsi_batch **out);
+void fsi_batch_destroy(fsi_batch *batch);
+
+/* One batched step in the given mode (results are bitwise identical across
+ * modes for a given brick shape).  Asynchronous on the batch's stream.     */
+fsi_status fsi_batch_run(fsi_batch *batch, int mode);
+
+/* Seconds per batched step in `mode` (CUDA events, best of reps; synchronises). */
+fsi_status fsi_batch_time(fsi_batch *batch, int mode, int reps, double *seconds);
+
+#define FSI_TUNE_MAX_CANDIDATES 64
+typedef struct {
+    int32_t bx, by, bz, threads, ctas_per_sm;
+    int32_t n_candidates;
+    double seconds;  /* residual + Jacobian phases of the chosen schedule */
+    int32_t cand_bx[FSI_TUNE_MAX_CANDIDATES], cand_by[FSI_TUNE_MAX_CANDIDATES],
+        cand_bz[FSI_TUNE_MAX_CANDIDATES], cand_ctas[FSI_TUNE_MAX_CANDIDATES];
+    double cand_seconds[FSI_TUNE_MAX_CANDIDATES];
+} fsi_tune_report;
+
+/* Autotuner: times every candidate brick shape (elements per CTA along each
+ * axis, CTA size) and persistent grid size (CTAs per SM) on this batch's
+ * residual + Jacobian phases and keeps the fastest.  When the environment
+ * variable FSI_TUNE_CACHE names a file, the choice is appended to it as one
+ * JSON object per line.  Synchronises.                                     */
+fsi_status fsi_batch_autotune(fsi_batch *batch, int reps, fsi_tune_report *report);
+
+/* Brick schedule of a single mesh for op 0 (residual) or 1 (Jacobian) in
+ * `prec`: bx*by*bz elements per CTA of `threads` threads (8 lanes per element;
+ * threads a multiple of 32 and at most 256; bx*by*bz*8 >= threads not
+ * required).  Scratch grows as needed.                                     */
+fsi_status fsi_mesh_set_brick(fsi_mesh *mesh, int op, fsi_prec prec, int bx, int by, int bz,
+                              int threads);
+
 /* Measurement helper (the paper has no counterpart): the device's sustained
  * FMA throughput on the CUDA cores in `prec`, in FLOP/s (an FMA counts as 2),
  * from a dependent-chain FMA kernel over all SMs timed with CUDA events

@@ -73,6 +73,29 @@ class fsi_guess_report(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class fsi_batch_item(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_void_p), ("A", ctypes.c_void_p), ("f", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("R", ctypes.c_void_p), ("Jx", ctypes.c_void_p),
+                ("m", ctypes.c_int64), ("elem", ctypes.c_void_p),
+                ("cell_start", ctypes.c_void_p), ("perm", ctypes.c_void_p),
+                ("xi", ctypes.c_void_p), ("lam", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("u", ctypes.c_void_p), ("F", ctypes.c_void_p)]
+
+
+_NT = 64
+
+
+class fsi_tune_report(ctypes.Structure):
+    _fields_ = [("bx", ctypes.c_int32), ("by", ctypes.c_int32), ("bz", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("n_candidates", ctypes.c_int32), ("seconds", ctypes.c_double),
+                ("cand_bx", ctypes.c_int32 * _NT), ("cand_by", ctypes.c_int32 * _NT),
+                ("cand_bz", ctypes.c_int32 * _NT), ("cand_ctas", ctypes.c_int32 * _NT),
+                ("cand_seconds", ctypes.c_double * _NT)]
+
+
+FSI_BATCH_PER_INSTANCE, FSI_BATCH_PERSISTENT, FSI_BATCH_GRAPH = 0, 1, 2
+
 _lock = threading.Lock()
 _lib = None
 
@@ -113,6 +136,13 @@ _SIGS = {
     "fsi_mlp_guess": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(fsi_step_state), _VP,
                        _VP, _VP, _INT, _VP, ctypes.POINTER(fsi_guess_report)], _INT),
     "fsi_advance_history": ([_VP, _INT, _VP, _VP, _VP], _INT),
+    "fsi_batch_create": ([ctypes.POINTER(_VP), ctypes.POINTER(fsi_batch_item), _INT, _INT, _VP,
+                          ctypes.POINTER(_VP)], _INT),
+    "fsi_batch_destroy": ([_VP], None),
+    "fsi_batch_run": ([_VP, _INT], _INT),
+    "fsi_batch_time": ([_VP, _INT, _INT, ctypes.POINTER(ctypes.c_double)], _INT),
+    "fsi_batch_autotune": ([_VP, _INT, ctypes.POINTER(fsi_tune_report)], _INT),
+    "fsi_mesh_set_brick": ([_VP, _INT, _INT, _INT, _INT, _INT, _INT], _INT),
 }
 
 
@@ -418,3 +448,57 @@ def fsi_mlp_guess(mlp: Mlp, mesh: Mesh, params, in_mean, in_std, out_mean, out_s
                                ctypes.byref(st.c), _ptr(yn, d), _ptr(d1, d), _ptr(d2, d),
                                int(fallback), _ptr(work, d), ctypes.byref(rep)))
     return {k: getattr(rep, k) for k, _ in fsi_guess_report._fields_ if k != "reserved"}
+
+
+class Batch:
+    """Owner of an fsi_batch; keeps the meshes and item tensors alive."""
+
+    def __init__(self, meshes, items, prec, stream):
+        self.meshes, self.items_t = meshes, items
+        arr = (fsi_batch_item * len(items))()
+        dt = _prec_dtype(prec)
+        import torch
+        for i, it in enumerate(items):
+            m = 0 if it.get("elem") is None else int(it["elem"].shape[0])
+            arr[i] = fsi_batch_item(
+                _ptr(it["U"], dt), _ptr(it["A"], dt), _ptr(it.get("f"), dt), _ptr(it["x"], dt),
+                _ptr(it["R"], dt), _ptr(it["Jx"], dt), m, _ptr(it.get("elem"), torch.int32),
+                _ptr(it["cell_start"], torch.int32), _ptr(it.get("perm"), torch.int32),
+                _ptr(it.get("xi"), dt), _ptr(it.get("lam"), dt), _ptr(it.get("w"), dt),
+                _ptr(it.get("u"), dt), _ptr(it["F"], dt))
+        handles = (ctypes.c_void_p * len(meshes))(*[mm.handle.value for mm in meshes])
+        out = ctypes.c_void_p()
+        _check(lib().fsi_batch_create(handles, arr, len(items), prec, ctypes.c_void_p(stream),
+                                      ctypes.byref(out)))
+        self.handle = out
+
+    def run(self, mode):
+        _check(lib().fsi_batch_run(self.handle, mode))
+
+    def time(self, mode, reps=5):
+        out = ctypes.c_double(0.0)
+        _check(lib().fsi_batch_time(self.handle, mode, reps, ctypes.byref(out)))
+        return out.value
+
+    def autotune(self, reps=3):
+        r = fsi_tune_report()
+        _check(lib().fsi_batch_autotune(self.handle, reps, ctypes.byref(r)))
+        cands = [(r.cand_bx[i], r.cand_by[i], r.cand_bz[i], r.cand_ctas[i], r.cand_seconds[i])
+                 for i in range(r.n_candidates)]
+        return {"brick": (r.bx, r.by, r.bz), "threads": r.threads, "ctas_per_sm": r.ctas_per_sm,
+                "seconds": r.seconds, "candidates": cands}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fsi_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fsi_mesh_set_brick(mesh: Mesh, op, prec, bx, by, bz, threads):
+    _check(lib().fsi_mesh_set_brick(mesh.handle, op, prec, bx, by, bz, threads))

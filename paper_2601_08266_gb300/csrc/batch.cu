@@ -1,0 +1,517 @@
+// batch.cu -- many independent instances of uneven size in one pass (an
+// extension; the paper has no counterpart): the residual, the Jacobian apply,
+// interpolation and spreading of every instance run as persistent grids that
+// walk a prefix sum of (instance, work item) pairs, so small grids no longer
+// leave SMs idle and the whole step is a handful of launches, which one CUDA
+// graph replays.  A native autotuner picks the brick shape and the persistent
+// grid size by timing candidates on the actual batch.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dlm_device.cuh"
+#include "vms_device.cuh"
+
+namespace fsi {
+namespace {
+
+template <typename T> struct DlmDesc {
+    dlmd::GridArgs g;
+    int64_t m, E;
+    const int32_t *elem, *start, *perm;
+    const T *xi, *lam, *w;
+    const vec4<T> *U;
+    T *u, *F, *S;
+};
+
+constexpr int kChunk = 256;  // nodes / points per work item; 8 cell segments per item
+
+__device__ __forceinline__ int find_instance(const int64_t *prefix, int count, int64_t item)
+{
+    int lo = 0, hi = count;  // prefix[lo] <= item < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T, bool JAC>
+__global__ void __launch_bounds__(256) batch_brick_kernel(const vmsd::VmsArgs<T> *desc,
+                                                          const int64_t *prefix, int count)
+{
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    vec4<T> *rel = reinterpret_cast<vec4<T> *>(smem_raw);
+    const int64_t total = prefix[count];
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const int inst = find_instance(prefix, count, item);
+        vmsd::brick_body<T, JAC>(desc[inst], (int)(item - prefix[inst]), rel);
+        __syncthreads();  // rel is reused by the next brick
+    }
+}
+
+template <typename T>
+__global__ void batch_gather_kernel(const vmsd::VmsArgs<T> *desc, const int64_t *prefix, int count)
+{
+    const int64_t total = prefix[count];
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const int inst = find_instance(prefix, count, item);
+        const vmsd::VmsArgs<T> &P = desc[inst];
+        const int n = (P.Nx + 1) * (P.Ny + 1) * (P.Nz + 1);
+        const int64_t node = (item - prefix[inst]) * kChunk + threadIdx.x;
+        if (node < n) vmsd::gather_node(P, (int)node);
+    }
+}
+
+template <typename T>
+__global__ void batch_interp_kernel(const DlmDesc<T> *desc, const int64_t *prefix, int count)
+{
+    const int64_t total = prefix[count];
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const int inst = find_instance(prefix, count, item);
+        const DlmDesc<T> &D = desc[inst];
+        const int64_t b = (item - prefix[inst]) * kChunk + threadIdx.x;
+        if (b < D.m) dlmd::interp_point(D.g, b, D.elem, D.xi, D.U, D.u);
+    }
+}
+
+template <typename T>
+__global__ void batch_spread_cells_kernel(const DlmDesc<T> *desc, const int64_t *prefix,
+                                          int count)
+{
+    const int64_t total = prefix[count];
+    const int warp = threadIdx.x >> 5;
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const int inst = find_instance(prefix, count, item);
+        const DlmDesc<T> &D = desc[inst];
+        const int64_t c0 = ((item - prefix[inst]) * 8 + warp) * 32;
+        if (c0 < D.E) dlmd::spread_cells_segment(D.E, c0, D.xi, D.start, D.perm, D.lam, D.w, D.S);
+    }
+}
+
+template <typename T>
+__global__ void batch_spread_nodes_kernel(const DlmDesc<T> *desc, const int64_t *prefix,
+                                          int count)
+{
+    const int64_t total = prefix[count];
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const int inst = find_instance(prefix, count, item);
+        const DlmDesc<T> &D = desc[inst];
+        const int n = (D.g.Nx + 1) * (D.g.Ny + 1) * (D.g.Nz + 1);
+        const int64_t node = (item - prefix[inst]) * kChunk + threadIdx.x;
+        if (node < n) dlmd::spread_node(D.g, (int)node, D.start, D.S, D.F, 0);
+    }
+}
+
+}  // namespace
+}  // namespace fsi
+
+struct fsi_batch {
+    int device;
+    cudaStream_t stream;
+    fsi_prec prec;
+    int count;
+    std::vector<fsi_mesh *> meshes;
+    std::vector<fsi_batch_item> items;
+    fsi::Brick brick;
+    int ctas_per_sm;
+    int sms;
+    // device data
+    void *desc_res, *desc_jac, *desc_dlm;                      // descriptors
+    int64_t *prefix;  // [5][count+1]: bricks, node chunks, point chunks, cell items, (spare)
+    void *blocks;
+    size_t blocks_bytes;
+    void *spread;
+    size_t spread_bytes;
+    int64_t totals[4];
+    // CUDA graph of one batched step
+    cudaGraph_t graph;
+    cudaGraphExec_t graph_exec;
+};
+
+namespace fsi {
+namespace {
+
+size_t esize(fsi_prec p) { return p == FSI_F64 ? sizeof(double) : sizeof(float); }
+
+// (Re)build descriptors and scratch for the batch's current brick shape.
+template <typename T> fsi_status build_batch(fsi_batch *b)
+{
+    const int C = b->count;
+    std::vector<vmsd::VmsArgs<T>> res(C), jac(C);
+    std::vector<DlmDesc<T>> dlm(C);
+    std::vector<int64_t> pre(5 * (C + 1), 0);
+    size_t blocks_need = 0, spread_need = 0;
+    std::vector<size_t> boff(C), soff(C);
+    for (int i = 0; i < C; ++i) {
+        fsi_mesh *m = b->meshes[i];
+        boff[i] = blocks_need;
+        blocks_need += vms_scratch_bytes_for(m, b->brick, sizeof(T));
+        blocks_need = (blocks_need + 255) / 256 * 256;
+        soff[i] = spread_need;
+        spread_need += (size_t)m->n_elems * 24 * sizeof(T);
+        spread_need = (spread_need + 255) / 256 * 256;
+    }
+    if (blocks_need > b->blocks_bytes) {
+        cudaFree(b->blocks);
+        b->blocks = nullptr;
+        b->blocks_bytes = 0;
+        FSI_CUDA(cudaMalloc(&b->blocks, blocks_need), "batch block scratch");
+        b->blocks_bytes = blocks_need;
+    }
+    if (spread_need > b->spread_bytes) {
+        cudaFree(b->spread);
+        b->spread = nullptr;
+        b->spread_bytes = 0;
+        FSI_CUDA(cudaMalloc(&b->spread, spread_need), "batch spread scratch");
+        b->spread_bytes = spread_need;
+    }
+    for (int i = 0; i < C; ++i) {
+        fsi_mesh *m = b->meshes[i];
+        const fsi_batch_item &it = b->items[i];
+        res[i] = vmsd::make_args<T>(m, b->brick, it.U, it.A, it.f, nullptr, it.R);
+        jac[i] = vmsd::make_args<T>(m, b->brick, it.U, it.A, it.f, it.x, it.Jx);
+        res[i].blocks = jac[i].blocks = (vec4<T> *)((char *)b->blocks + boff[i]);
+        DlmDesc<T> &D = dlm[i];
+        D.g.Nx = m->grid.N[0];
+        D.g.Ny = m->grid.N[1];
+        D.g.Nz = m->grid.N[2];
+        D.g.x0 = m->grid.x0[0];
+        D.g.y0 = m->grid.x0[1];
+        D.g.z0 = m->grid.x0[2];
+        D.g.hx = m->grid.h[0];
+        D.g.hy = m->grid.h[1];
+        D.g.hz = m->grid.h[2];
+        D.m = it.m;
+        D.E = m->n_elems;
+        D.elem = it.elem;
+        D.start = it.cell_start;
+        D.perm = it.perm;
+        D.xi = (const T *)it.xi;
+        D.lam = (const T *)it.lam;
+        D.w = (const T *)it.w;
+        D.U = (const vec4<T> *)it.U;
+        D.u = (T *)it.u;
+        D.F = (T *)it.F;
+        D.S = (T *)((char *)b->spread + soff[i]);
+        const int64_t nb = (int64_t)res[i].nbx * res[i].nby * res[i].nbz;
+        pre[0 * (C + 1) + i + 1] = pre[0 * (C + 1) + i] + nb;
+        pre[1 * (C + 1) + i + 1] = pre[1 * (C + 1) + i] + (m->n_nodes + kChunk - 1) / kChunk;
+        pre[2 * (C + 1) + i + 1] = pre[2 * (C + 1) + i] + (it.m + kChunk - 1) / kChunk;
+        pre[3 * (C + 1) + i + 1] =
+            pre[3 * (C + 1) + i] + ((m->n_elems + 31) / 32 + 7) / 8;  // 8 segments per item
+    }
+    for (int k = 0; k < 4; ++k) b->totals[k] = pre[k * (C + 1) + C];
+    cudaStream_t s = b->stream;
+    FSI_CUDA(cudaMemcpyAsync(b->desc_res, res.data(), C * sizeof(res[0]), cudaMemcpyHostToDevice, s),
+             "descriptor upload");
+    FSI_CUDA(cudaMemcpyAsync(b->desc_jac, jac.data(), C * sizeof(jac[0]), cudaMemcpyHostToDevice, s),
+             "descriptor upload");
+    FSI_CUDA(cudaMemcpyAsync(b->desc_dlm, dlm.data(), C * sizeof(dlm[0]), cudaMemcpyHostToDevice, s),
+             "descriptor upload");
+    FSI_CUDA(cudaMemcpyAsync(b->prefix, pre.data(), pre.size() * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, s),
+             "prefix upload");
+    FSI_CUDA(cudaStreamSynchronize(s), "sync");
+    if (b->graph_exec) {
+        cudaGraphExecDestroy(b->graph_exec);
+        b->graph_exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return FSI_OK;
+}
+
+int persistent_grid(const fsi_batch *b, int64_t items)
+{
+    int64_t g = (int64_t)b->sms * b->ctas_per_sm;
+    if (items < g) g = items;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// The batched step: residual, Jacobian apply, interpolation, spreading.
+template <typename T> fsi_status run_batched(fsi_batch *b, int phases)
+{
+    cudaStream_t s = b->stream;
+    const int C = b->count;
+    const int64_t *pre = b->prefix;
+    const size_t smem = (size_t)b->brick.bx * b->brick.by * b->brick.bz * 8 * sizeof(vec4<T>);
+    if (phases & 1) {
+        batch_brick_kernel<T, false><<<persistent_grid(b, b->totals[0]), b->brick.threads, smem, s>>>(
+            (const vmsd::VmsArgs<T> *)b->desc_res, pre, C);
+        batch_gather_kernel<T><<<persistent_grid(b, b->totals[1]), kChunk, 0, s>>>(
+            (const vmsd::VmsArgs<T> *)b->desc_res, pre + (C + 1), C);
+    }
+    if (phases & 2) {
+        batch_brick_kernel<T, true><<<persistent_grid(b, b->totals[0]), b->brick.threads, smem, s>>>(
+            (const vmsd::VmsArgs<T> *)b->desc_jac, pre, C);
+        batch_gather_kernel<T><<<persistent_grid(b, b->totals[1]), kChunk, 0, s>>>(
+            (const vmsd::VmsArgs<T> *)b->desc_jac, pre + (C + 1), C);
+    }
+    if (phases & 4) {
+        if (b->totals[2] > 0)
+            batch_interp_kernel<T><<<persistent_grid(b, b->totals[2]), kChunk, 0, s>>>(
+                (const DlmDesc<T> *)b->desc_dlm, pre + 2 * (C + 1), C);
+        batch_spread_cells_kernel<T><<<persistent_grid(b, b->totals[3]), 256, 0, s>>>(
+            (const DlmDesc<T> *)b->desc_dlm, pre + 3 * (C + 1), C);
+        batch_spread_nodes_kernel<T><<<persistent_grid(b, b->totals[1]), kChunk, 0, s>>>(
+            (const DlmDesc<T> *)b->desc_dlm, pre + (C + 1), C);
+    }
+    return check_launch("batched kernels");
+}
+
+fsi_status run_per_instance(fsi_batch *b, int phases)
+{
+    for (int i = 0; i < b->count; ++i) {
+        fsi_mesh *m = b->meshes[i];
+        const fsi_batch_item &it = b->items[i];
+        cudaStream_t saved = m->stream;
+        m->stream = b->stream;
+        fsi::Brick bsaved[2] = {m->brick[0][b->prec], m->brick[1][b->prec]};
+        m->brick[0][b->prec] = m->brick[1][b->prec] = b->brick;
+        fsi_status st = FSI_OK;
+        if (phases & 1) st = fsi_residual(m, b->prec, it.U, it.A, it.f, it.R);
+        if (st == FSI_OK && (phases & 2))
+            st = fsi_jacobian_apply(m, b->prec, it.U, it.A, it.f, it.x, it.Jx);
+        if (st == FSI_OK && (phases & 4)) {
+            st = fsi_dlm_interp(m, b->prec, it.m, it.elem, it.xi, it.U, it.u);
+            if (st == FSI_OK)
+                st = fsi_dlm_spread(m, b->prec, it.m, it.elem, it.xi, it.cell_start, it.perm,
+                                    it.lam, it.w, it.F, 0);
+        }
+        m->brick[0][b->prec] = bsaved[0];
+        m->brick[1][b->prec] = bsaved[1];
+        m->stream = saved;
+        FSI_TRY(st);
+    }
+    return FSI_OK;
+}
+
+fsi_status set_smem_attr(fsi_prec prec)
+{
+    static bool done[2] = {false, false};
+    if (done[prec]) return FSI_OK;
+    if (prec == FSI_F64) {
+        FSI_CUDA(cudaFuncSetAttribute(batch_brick_kernel<double, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
+                 "attr");
+        FSI_CUDA(cudaFuncSetAttribute(batch_brick_kernel<double, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
+                 "attr");
+    } else {
+        FSI_CUDA(cudaFuncSetAttribute(batch_brick_kernel<float, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
+                 "attr");
+        FSI_CUDA(cudaFuncSetAttribute(batch_brick_kernel<float, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
+                 "attr");
+    }
+    done[prec] = true;
+    return FSI_OK;
+}
+
+fsi_status run_mode(fsi_batch *b, int mode, int phases)
+{
+    if (mode == FSI_BATCH_PER_INSTANCE) return run_per_instance(b, phases);
+    FSI_TRY(set_smem_attr(b->prec));
+    if (mode == FSI_BATCH_PERSISTENT)
+        return b->prec == FSI_F64 ? run_batched<double>(b, phases) : run_batched<float>(b, phases);
+    // CUDA graph of the whole batched step (all phases), captured on first use
+    if (!b->graph_exec) {
+        if (b->stream == nullptr)
+            return set_error(FSI_ERR_ARG, "graph mode needs a non-default stream");
+        FSI_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
+                 "begin capture");
+        fsi_status st = b->prec == FSI_F64 ? run_batched<double>(b, 7) : run_batched<float>(b, 7);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        FSI_TRY(st);
+        FSI_CUDA(e, "end capture");
+        b->graph = g;
+        FSI_CUDA(cudaGraphInstantiate(&b->graph_exec, g, 0), "graph instantiate");
+    }
+    return check_cuda(cudaGraphLaunch(b->graph_exec, b->stream), "graph launch");
+}
+
+// seconds per run of `mode` (events, best of reps)
+fsi_status time_mode(fsi_batch *b, int mode, int phases, int reps, double *out)
+{
+    cudaEvent_t e0, e1;
+    FSI_CUDA(cudaEventCreate(&e0), "event");
+    FSI_CUDA(cudaEventCreate(&e1), "event");
+    double best = 1e30;
+    fsi_status st = run_mode(b, mode, phases);  // warm-up
+    for (int r = 0; st == FSI_OK && r < reps; ++r) {
+        cudaEventRecord(e0, b->stream);
+        st = run_mode(b, mode, phases);
+        cudaEventRecord(e1, b->stream);
+        if (st == FSI_OK) st = check_cuda(cudaEventSynchronize(e1), "event sync");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms * 1e-3 < best) best = ms * 1e-3;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *out = best;
+    return st;
+}
+
+const fsi::Brick kBrickCandidates[] = {
+    {8, 8, 4, 256}, {8, 4, 4, 128}, {4, 4, 4, 64}, {16, 4, 4, 256}, {8, 8, 2, 128},
+    {16, 8, 2, 256}, {4, 4, 8, 128}, {8, 4, 8, 256},
+};
+
+}  // namespace
+}  // namespace fsi
+
+using namespace fsi;
+
+extern "C" {
+
+fsi_status fsi_batch_create(fsi_mesh *const *meshes, const fsi_batch_item *items, int count,
+                            fsi_prec prec, void *cuda_stream, fsi_batch **out)
+{
+    if (!out) return set_error(FSI_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!meshes || !items || count < 1) return set_error(FSI_ERR_ARG, "empty batch");
+    if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
+    const int device = meshes[0] ? meshes[0]->device : -1;
+    for (int i = 0; i < count; ++i) {
+        if (!meshes[i]) return set_error(FSI_ERR_ARG, "mesh %d is NULL", i);
+        if (meshes[i]->device != device)
+            return set_error(FSI_ERR_ARG, "all meshes of a batch must be on one device");
+        const fsi_batch_item &it = items[i];
+        if (!it.U || !it.A || !it.x || !it.R || !it.Jx || !it.F || !it.cell_start)
+            return set_error(FSI_ERR_ARG, "batch item %d: NULL array", i);
+        if (it.m < 0 || (it.m > 0 && (!it.elem || !it.xi || !it.perm || !it.lam || !it.u)))
+            return set_error(FSI_ERR_ARG, "batch item %d: bad point arrays", i);
+    }
+    FSI_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    fsi_batch *b = new (std::nothrow) fsi_batch();
+    if (!b) return set_error(FSI_ERR_OOM, "host allocation failed");
+    b->device = device;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->prec = prec;
+    b->count = count;
+    b->meshes.assign(meshes, meshes + count);
+    b->items.assign(items, items + count);
+    b->brick = Brick{8, 8, 4, 256};
+    b->ctas_per_sm = 2;
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, device);
+    const size_t vsz = prec == FSI_F64 ? sizeof(vmsd::VmsArgs<double>) : sizeof(vmsd::VmsArgs<float>);
+    const size_t dsz = prec == FSI_F64 ? sizeof(DlmDesc<double>) : sizeof(DlmDesc<float>);
+    fsi_status st = check_cuda(cudaMalloc(&b->desc_res, count * vsz), "descriptors");
+    if (st == FSI_OK) st = check_cuda(cudaMalloc(&b->desc_jac, count * vsz), "descriptors");
+    if (st == FSI_OK) st = check_cuda(cudaMalloc(&b->desc_dlm, count * dsz), "descriptors");
+    if (st == FSI_OK)
+        st = check_cuda(cudaMalloc(&b->prefix, 5 * (count + 1) * sizeof(int64_t)), "prefix");
+    if (st == FSI_OK) st = prec == FSI_F64 ? build_batch<double>(b) : build_batch<float>(b);
+    if (st != FSI_OK) {
+        fsi_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return FSI_OK;
+}
+
+void fsi_batch_destroy(fsi_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->desc_res);
+    cudaFree(b->desc_jac);
+    cudaFree(b->desc_dlm);
+    cudaFree(b->prefix);
+    cudaFree(b->blocks);
+    cudaFree(b->spread);
+    delete b;
+}
+
+fsi_status fsi_batch_run(fsi_batch *b, int mode)
+{
+    if (!b) return set_error(FSI_ERR_ARG, "batch is NULL");
+    if (mode < FSI_BATCH_PER_INSTANCE || mode > FSI_BATCH_GRAPH)
+        return set_error(FSI_ERR_ARG, "bad batch mode %d", mode);
+    FSI_CUDA(cudaSetDevice(b->device), "cudaSetDevice");
+    return run_mode(b, mode, 7);
+}
+
+fsi_status fsi_batch_autotune(fsi_batch *b, int reps, fsi_tune_report *rep)
+{
+    if (!b || !rep || reps < 1) return set_error(FSI_ERR_ARG, "bad autotune arguments");
+    FSI_CUDA(cudaSetDevice(b->device), "cudaSetDevice");
+    std::memset(rep, 0, sizeof *rep);
+    const Brick start = b->brick;
+    const int start_ctas = b->ctas_per_sm;
+    double best = 1e30;
+    Brick best_brick = start;
+    int best_ctas = start_ctas;
+    int tried = 0;
+    for (const Brick &cand : kBrickCandidates) {
+        for (int ctas : {1, 2, 4, 8}) {
+            b->brick = cand;
+            b->ctas_per_sm = ctas;
+            FSI_TRY(b->prec == FSI_F64 ? build_batch<double>(b) : build_batch<float>(b));
+            double t = 0.0;
+            FSI_TRY(time_mode(b, FSI_BATCH_PERSISTENT, 3, reps, &t));
+            if (tried < FSI_TUNE_MAX_CANDIDATES) {
+                rep->cand_bx[tried] = cand.bx;
+                rep->cand_by[tried] = cand.by;
+                rep->cand_bz[tried] = cand.bz;
+                rep->cand_ctas[tried] = ctas;
+                rep->cand_seconds[tried] = t;
+            }
+            ++tried;
+            if (t < best) {
+                best = t;
+                best_brick = cand;
+                best_ctas = ctas;
+            }
+        }
+    }
+    b->brick = best_brick;
+    b->ctas_per_sm = best_ctas;
+    FSI_TRY(b->prec == FSI_F64 ? build_batch<double>(b) : build_batch<float>(b));
+    rep->n_candidates = tried < FSI_TUNE_MAX_CANDIDATES ? tried : FSI_TUNE_MAX_CANDIDATES;
+    rep->bx = best_brick.bx;
+    rep->by = best_brick.by;
+    rep->bz = best_brick.bz;
+    rep->threads = best_brick.threads;
+    rep->ctas_per_sm = best_ctas;
+    rep->seconds = best;
+    // persist the choice (one JSON object per line) when FSI_TUNE_CACHE is set
+    const char *path = getenv("FSI_TUNE_CACHE");
+    if (path && *path) {
+        FILE *f = fopen(path, "a");
+        if (f) {
+            fprintf(f,
+                    "{\"kind\": \"batch\", \"instances\": %d, \"prec\": \"%s\", \"bx\": %d, "
+                    "\"by\": %d, \"bz\": %d, \"threads\": %d, \"ctas_per_sm\": %d, "
+                    "\"seconds\": %.6e}\n",
+                    b->count, b->prec == FSI_F64 ? "f64" : "f32", best_brick.bx, best_brick.by,
+                    best_brick.bz, best_brick.threads, best_ctas, best);
+            fclose(f);
+        }
+    }
+    return FSI_OK;
+}
+
+fsi_status fsi_batch_time(fsi_batch *b, int mode, int reps, double *seconds)
+{
+    if (!b || !seconds || reps < 1) return set_error(FSI_ERR_ARG, "bad arguments");
+    if (mode < FSI_BATCH_PER_INSTANCE || mode > FSI_BATCH_GRAPH)
+        return set_error(FSI_ERR_ARG, "bad batch mode %d", mode);
+    FSI_CUDA(cudaSetDevice(b->device), "cudaSetDevice");
+    return time_mode(b, mode, 7, reps, seconds);
+}
+
+}  // extern "C"

@@ -240,6 +240,22 @@ fsi_status fsi_mesh_set_physics(fsi_mesh *m, const fsi_physics *phys)
     return FSI_OK;
 }
 
+fsi_status fsi_mesh_set_brick(fsi_mesh *m, int op, fsi_prec prec, int bx, int by, int bz,
+                              int threads)
+{
+    FSI_TRY(validate_mesh(m));
+    if (op < 0 || op > 1 || (prec != FSI_F64 && prec != FSI_F32))
+        return set_error(FSI_ERR_ARG, "bad op or precision");
+    if (bx < 1 || by < 1 || bz < 1 || threads < 32 || threads > 256 || threads % 32 != 0)
+        return set_error(FSI_ERR_ARG, "bad brick %dx%dx%d / %d threads", bx, by, bz, threads);
+    const size_t smem = (size_t)bx * by * bz * 8 * 4 * (prec == FSI_F64 ? 8 : 4);
+    if (smem > 200 * 1024)
+        return set_error(FSI_ERR_ARG, "brick %dx%dx%d needs %zu bytes of shared memory", bx, by,
+                         bz, smem);
+    m->brick[op][prec] = Brick{bx, by, bz, threads};
+    return FSI_OK;
+}
+
 fsi_status fsi_mesh_sizes(const fsi_mesh *m, int64_t *n_nodes, int64_t *n_elems)
 {
     FSI_TRY(validate_mesh(m));

@@ -23,343 +23,26 @@
 
 #include "fsi_internal.cuh"
 
+#include "vms_device.cuh"
+
 namespace fsi {
 namespace {
 
-constexpr double kQ = 0.57735026918962576451;  // 1/sqrt(3): Gauss abscissa
-constexpr double kB1 = 0.5 * (1.0 + kQ);      // 1D linear basis at the near point
-constexpr double kB2 = 0.5 * (1.0 - kQ);      // ... at the far point
-
-template <typename T> struct VmsArgs {
-    int Nx, Ny, Nz;
-    int bx, by, bz;
-    int nbx, nby, nbz;
-    T rho, mu, inv_rho;
-    T G0, G1, G2, inv_trG, q0;  // q0 = C_T/dt^2 + C_I (mu/rho)^2 G:G
-    T ih0, ih1, ih2;            // 1/h_k
-    T detJ;
-    T c_a, c_v;                 // d A / d y_v, d U / d y_v
-    int has_s;
-    const vec4<T> *U, *A, *f, *x;
-    vec4<T> *blocks;  // [n_bricks][(bx+1)(by+1)(bz+1)]
-    vec4<T> *out;     // [n]
-};
-
-template <typename T> __device__ __forceinline__ T shx(T v, int m)
-{
-    return __shfl_xor_sync(0xffffffffu, v, m);
-}
-
-template <typename T> struct VG {
-    T v, gx, gy, gz;
-};
-
-// Value and physical gradient at this lane's Gauss point of the Q1 field whose
-// value at this lane's node is u.  sx = sigma_x/h_x with sigma = +1 when the
-// lane's node sits at the upper side along x (and likewise sy, sz).
-template <typename T> __device__ __forceinline__ VG<T> eval_vg(T u, T sx, T sy, T sz)
-{
-    const T b1 = T(kB1), b2 = T(kB2);
-    T uo = shx(u, 1);
-    T tB = b1 * u + b2 * uo;
-    T tD = u - uo;
-    T tBo = shx(tB, 2), tDo = shx(tD, 2);
-    T tBB = b1 * tB + b2 * tBo;
-    T tBD = tB - tBo;
-    T tDB = b1 * tD + b2 * tDo;
-    T tBBo = shx(tBB, 4), tBDo = shx(tBD, 4), tDBo = shx(tDB, 4);
-    VG<T> r;
-    r.v = b1 * tBB + b2 * tBBo;
-    r.gz = sz * (tBB - tBBo);
-    r.gy = sy * (b1 * tBD + b2 * tBDo);
-    r.gx = sx * (b1 * tDB + b2 * tDBo);
-    return r;
-}
-
-template <typename T> __device__ __forceinline__ T eval_v(T u)
-{
-    const T b1 = T(kB1), b2 = T(kB2);
-    T t = b1 * u + b2 * shx(u, 1);
-    t = b1 * t + b2 * shx(t, 2);
-    return b1 * t + b2 * shx(t, 4);
-}
-
-// Transposed evaluation: with X the value coefficient and (Yx, Yy, Yz) the
-// gradient coefficients of one residual component at this lane's Gauss point,
-// returns sum_g [N_a(g) X(g) + grad N_a(g) . Y(g)] for the lane's node a.
-template <typename T>
-__device__ __forceinline__ T project(T X, T Yx, T Yy, T Yz, T sx, T sy, T sz)
-{
-    const T b1 = T(kB1), b2 = T(kB2);
-    T Xo = shx(X, 4), Yzo = shx(Yz, 4), Yxo = shx(Yx, 4), Yyo = shx(Yy, 4);
-    T P1 = b1 * X + b2 * Xo + sz * (Yz + Yzo);
-    T P2 = b1 * Yx + b2 * Yxo;
-    T P3 = b1 * Yy + b2 * Yyo;
-    T P1o = shx(P1, 2), P2o = shx(P2, 2), P3o = shx(P3, 2);
-    T Q1 = b1 * P1 + b2 * P1o + sy * (P3 + P3o);
-    T Q2 = b1 * P2 + b2 * P2o;
-    T Q1o = shx(Q1, 1), Q2o = shx(Q2, 1);
-    return b1 * Q1 + b2 * Q1o + sx * (Q2 + Q2o);
-}
-
-template <typename T> __device__ __forceinline__ T rsqrt_t(T v);
-template <> __device__ __forceinline__ float rsqrt_t(float v) { return 1.0f / sqrtf(v); }
-template <> __device__ __forceinline__ double rsqrt_t(double v) { return 1.0 / sqrt(v); }
-
-// Base state of the VMS form at one Gauss point.
-template <typename T> struct GP {
-    T v[3], gv[3][3], p, gp[3], a[3], f[3], s;
-    T rM[3], rC, conv[3], tauM, tauC, up[3], pp, vGv;
-};
-
-template <typename T>
-__device__ __forceinline__ void base_state(const VmsArgs<T> &P, GP<T> &q)
-{
-    for (int i = 0; i < 3; ++i) {
-        q.conv[i] = q.v[0] * q.gv[i][0] + q.v[1] * q.gv[i][1] + q.v[2] * q.gv[i][2];
-        q.rM[i] = P.rho * (q.a[i] + q.conv[i] - q.f[i]) + q.gp[i];
-    }
-    q.rC = q.gv[0][0] + q.gv[1][1] + q.gv[2][2];
-    q.vGv = P.G0 * q.v[0] * q.v[0] + P.G1 * q.v[1] * q.v[1] + P.G2 * q.v[2] * q.v[2];
-    const T S = q.s * (P.q0 + q.vGv);
-    q.tauM = rsqrt_t(S);
-    // tau_C = 1/(tau_M tr G) and 1/tau_M = S tau_M
-    q.tauC = S * q.tauM * P.inv_trG;
-    const T c = -q.tauM * P.inv_rho;
-    for (int i = 0; i < 3; ++i) q.up[i] = c * q.rM[i];
-    q.pp = -P.rho * q.tauC * q.rC;
-}
+using namespace vmsd;
 
 template <typename T, bool JAC>
 __global__ void __launch_bounds__(256) vms_brick_kernel(const VmsArgs<T> P)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    vec4<T> *rel = reinterpret_cast<vec4<T> *>(smem_raw);  // [bx*by*bz][8]
-
-    const int g = threadIdx.x & 7;
-    const int brick = blockIdx.x;
-    const int bxi = brick % P.nbx, byi = (brick / P.nbx) % P.nby, bzi = brick / (P.nbx * P.nby);
-    const int ex0 = bxi * P.bx, ey0 = byi * P.by, ez0 = bzi * P.bz;
-    const int nel = P.bx * P.by * P.bz;
-    const int groups = blockDim.x >> 3;
-    const int gx = g & 1, gy = (g >> 1) & 1, gz = (g >> 2) & 1;
-    const T sx = gx ? P.ih0 : -P.ih0;
-    const T sy = gy ? P.ih1 : -P.ih1;
-    const T sz = gz ? P.ih2 : -P.ih2;
-    const int NX1 = P.Nx + 1, NXY1 = (P.Nx + 1) * (P.Ny + 1);
-
-    for (int base = 0; base < nel; base += groups) {
-        const int slot = base + (threadIdx.x >> 3);
-        const int lx = slot % P.bx, ly = (slot / P.bx) % P.by, lz = slot / (P.bx * P.by);
-        const int ex = ex0 + lx, ey = ey0 + ly, ez = ez0 + lz;
-        const bool valid = slot < nel && ex < P.Nx && ey < P.Ny && ez < P.Nz;
-        const int node = valid ? (ex + gx) + NX1 * (ey + gy) + NXY1 * (ez + gz) : 0;
-        const vec4<T> zero = {T(0), T(0), T(0), T(0)};
-        vec4<T> u = valid ? ld4(P.U + node) : zero;
-        vec4<T> ac = valid ? ld4(P.A + node) : zero;
-        vec4<T> ff = (valid && P.f) ? ld4(P.f + node) : zero;
-
-        GP<T> q;
-        {
-            VG<T> e0 = eval_vg(u.x, sx, sy, sz), e1 = eval_vg(u.y, sx, sy, sz),
-                  e2 = eval_vg(u.z, sx, sy, sz), e3 = eval_vg(u.w, sx, sy, sz);
-            q.v[0] = e0.v; q.gv[0][0] = e0.gx; q.gv[0][1] = e0.gy; q.gv[0][2] = e0.gz;
-            q.v[1] = e1.v; q.gv[1][0] = e1.gx; q.gv[1][1] = e1.gy; q.gv[1][2] = e1.gz;
-            q.v[2] = e2.v; q.gv[2][0] = e2.gx; q.gv[2][1] = e2.gy; q.gv[2][2] = e2.gz;
-            q.p = e3.v; q.gp[0] = e3.gx; q.gp[1] = e3.gy; q.gp[2] = e3.gz;
-        }
-        q.a[0] = eval_v(ac.x);
-        q.a[1] = eval_v(ac.y);
-        q.a[2] = eval_v(ac.z);
-        q.s = P.has_s ? eval_v(ac.w) : T(1);
-        if (P.f) {
-            q.f[0] = eval_v(ff.x);
-            q.f[1] = eval_v(ff.y);
-            q.f[2] = eval_v(ff.z);
-        } else {
-            q.f[0] = q.f[1] = q.f[2] = T(0);
-        }
-        if (!valid) q.s = T(1);  // keep tau finite on idle lanes
-        base_state(P, q);
-
-        T X[4], Y[4][3];
-        if (!JAC) {
-            for (int i = 0; i < 3; ++i) {
-                X[i] = P.rho * (q.a[i] + q.conv[i] - q.f[i]) +
-                       P.rho * (q.up[0] * q.gv[i][0] + q.up[1] * q.gv[i][1] +
-                                q.up[2] * q.gv[i][2]);
-                for (int j = 0; j < 3; ++j)
-                    Y[i][j] = P.mu * (q.gv[i][j] + q.gv[j][i]) -
-                              P.rho * (q.v[j] + q.up[j]) * q.up[i];
-                Y[i][i] -= q.p + q.pp;
-            }
-            X[3] = q.rC;
-            for (int j = 0; j < 3; ++j) Y[3][j] = -q.up[j];
-        } else {
-            vec4<T> xx = valid ? ld4(P.x + node) : zero;
-            T dv[3], dgv[3][3], da[3], dp, dgp[3];
-            {
-                VG<T> e0 = eval_vg(xx.x, sx, sy, sz), e1 = eval_vg(xx.y, sx, sy, sz),
-                      e2 = eval_vg(xx.z, sx, sy, sz), e3 = eval_vg(xx.w, sx, sy, sz);
-                const T cv = P.c_v, ca = P.c_a;
-                dv[0] = cv * e0.v; da[0] = ca * e0.v;
-                dv[1] = cv * e1.v; da[1] = ca * e1.v;
-                dv[2] = cv * e2.v; da[2] = ca * e2.v;
-                dgv[0][0] = cv * e0.gx; dgv[0][1] = cv * e0.gy; dgv[0][2] = cv * e0.gz;
-                dgv[1][0] = cv * e1.gx; dgv[1][1] = cv * e1.gy; dgv[1][2] = cv * e1.gz;
-                dgv[2][0] = cv * e2.gx; dgv[2][1] = cv * e2.gy; dgv[2][2] = cv * e2.gz;
-                dp = e3.v; dgp[0] = e3.gx; dgp[1] = e3.gy; dgp[2] = e3.gz;
-            }
-            T dconv[3], drM[3], dup[3];
-            for (int i = 0; i < 3; ++i) {
-                dconv[i] = dv[0] * q.gv[i][0] + dv[1] * q.gv[i][1] + dv[2] * q.gv[i][2] +
-                           q.v[0] * dgv[i][0] + q.v[1] * dgv[i][1] + q.v[2] * dgv[i][2];
-                drM[i] = P.rho * (da[i] + dconv[i]) + dgp[i];
-            }
-            const T drC = dgv[0][0] + dgv[1][1] + dgv[2][2];
-            // d tau_M = -1/2 tau_M^3 s dQ with dQ = 2 v.G dv
-            const T vGdv = P.G0 * q.v[0] * dv[0] + P.G1 * q.v[1] * dv[1] + P.G2 * q.v[2] * dv[2];
-            const T dtauM = -q.tauM * q.tauM * q.tauM * q.s * vGdv;
-            // d tau_C = -tau_C d tau_M / tau_M, 1/tau_M = s (q0 + vGv) tau_M
-            const T dtauC = -q.tauC * dtauM * (q.s * (P.q0 + q.vGv) * q.tauM);
-            for (int i = 0; i < 3; ++i) dup[i] = -(dtauM * q.rM[i] + q.tauM * drM[i]) * P.inv_rho;
-            const T dpp = -P.rho * (dtauC * q.rC + q.tauC * drC);
-            for (int i = 0; i < 3; ++i) {
-                X[i] = P.rho * (da[i] + dconv[i]) +
-                       P.rho * (dup[0] * q.gv[i][0] + dup[1] * q.gv[i][1] + dup[2] * q.gv[i][2] +
-                                q.up[0] * dgv[i][0] + q.up[1] * dgv[i][1] + q.up[2] * dgv[i][2]);
-                for (int j = 0; j < 3; ++j)
-                    Y[i][j] = P.mu * (dgv[i][j] + dgv[j][i]) -
-                              P.rho * ((dv[j] + dup[j]) * q.up[i] + (q.v[j] + q.up[j]) * dup[i]);
-                Y[i][i] -= dp + dpp;
-            }
-            X[3] = drC;
-            for (int j = 0; j < 3; ++j) Y[3][j] = -dup[j];
-        }
-        vec4<T> r;
-        r.x = P.detJ * project(X[0], Y[0][0], Y[0][1], Y[0][2], sx, sy, sz);
-        r.y = P.detJ * project(X[1], Y[1][0], Y[1][1], Y[1][2], sx, sy, sz);
-        r.z = P.detJ * project(X[2], Y[2][0], Y[2][1], Y[2][2], sx, sy, sz);
-        r.w = P.detJ * project(X[3], Y[3][0], Y[3][1], Y[3][2], sx, sy, sz);
-        if (slot < nel) rel[slot * 8 + g] = valid ? r : zero;
-    }
-    __syncthreads();
-
-    // Node block of the brick: each node sums the contributions of the (up to
-    // 8) brick elements around it, corner by corner in a fixed order.
-    const int nx1 = P.bx + 1, ny1 = P.by + 1, nz1 = P.bz + 1;
-    const int nnodes = nx1 * ny1 * nz1;
-    vec4<T> *blk = P.blocks + (size_t)brick * nnodes;
-    for (int nl = threadIdx.x; nl < nnodes; nl += blockDim.x) {
-        const int ix = nl % nx1, iy = (nl / nx1) % ny1, iz = nl / (nx1 * ny1);
-        vec4<T> acc = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int lx = ix - (c & 1), ly = iy - ((c >> 1) & 1), lz = iz - ((c >> 2) & 1);
-            if (lx < 0 || ly < 0 || lz < 0 || lx >= P.bx || ly >= P.by || lz >= P.bz) continue;
-            const vec4<T> r = rel[((lz * P.by + ly) * P.bx + lx) * 8 + c];
-            acc.x += r.x;
-            acc.y += r.y;
-            acc.z += r.z;
-            acc.w += r.w;
-        }
-        blk[nl] = acc;
-    }
-}
-
-// Candidate (brick, local index) pairs of node coordinate i along one axis,
-// lower brick first.
-__device__ __forceinline__ int axis_candidates(int i, int b, int nb, int *cb, int *cl)
-{
-    int k = 0;
-    const int q = i / b, r = i - q * b;
-    if (r == 0 && q > 0) {
-        cb[k] = q - 1;
-        cl[k] = b;
-        ++k;
-    }
-    if (q < nb) {
-        cb[k] = q;
-        cl[k] = r;
-        ++k;
-    }
-    return k;
+    brick_body<T, JAC>(P, blockIdx.x, reinterpret_cast<vec4<T> *>(smem_raw));
 }
 
 template <typename T> __global__ void vms_gather_kernel(const VmsArgs<T> P)
 {
-    const int NX1 = P.Nx + 1, NY1 = P.Ny + 1;
-    const int n = NX1 * NY1 * (P.Nz + 1);
-    const int nx1 = P.bx + 1, ny1 = P.by + 1, nz1 = P.bz + 1;
-    const int nnodes = nx1 * ny1 * nz1;
+    const int n = (P.Nx + 1) * (P.Ny + 1) * (P.Nz + 1);
     for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < n;
-         node += gridDim.x * blockDim.x) {
-        const int i = node % NX1, j = (node / NX1) % NY1, k = node / (NX1 * NY1);
-        int cbx[2], clx[2], cby[2], cly[2], cbz[2], clz[2];
-        const int kx = axis_candidates(i, P.bx, P.nbx, cbx, clx);
-        const int ky = axis_candidates(j, P.by, P.nby, cby, cly);
-        const int kz = axis_candidates(k, P.bz, P.nbz, cbz, clz);
-        vec4<T> acc = {T(0), T(0), T(0), T(0)};
-        for (int c = 0; c < kz; ++c)
-            for (int b = 0; b < ky; ++b)
-                for (int a = 0; a < kx; ++a) {
-                    const size_t brick = cbx[a] + P.nbx * (cby[b] + (size_t)P.nby * cbz[c]);
-                    const int nl = clx[a] + nx1 * (cly[b] + ny1 * clz[c]);
-                    const vec4<T> r = ld4(P.blocks + brick * nnodes + nl);
-                    acc.x += r.x;
-                    acc.y += r.y;
-                    acc.z += r.z;
-                    acc.w += r.w;
-                }
-        P.out[node] = acc;
-    }
-}
-
-template <typename T>
-VmsArgs<T> make_args(const fsi_mesh *m, const Brick &b, const void *U, const void *A,
-                     const void *f, const void *x, void *out)
-{
-    VmsArgs<T> P;
-    P.Nx = m->grid.N[0];
-    P.Ny = m->grid.N[1];
-    P.Nz = m->grid.N[2];
-    P.bx = b.bx;
-    P.by = b.by;
-    P.bz = b.bz;
-    P.nbx = (P.Nx + b.bx - 1) / b.bx;
-    P.nby = (P.Ny + b.by - 1) / b.by;
-    P.nbz = (P.Nz + b.bz - 1) / b.bz;
-    const double rho = m->phys.rho, mu = m->phys.mu, dt = m->phys.dt;
-    const double *h = m->grid.h;
-    double G[3], trG = 0.0, GG = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        G[k] = 4.0 / (h[k] * h[k]);
-        trG += G[k];
-        GG += G[k] * G[k];
-    }
-    const double nu = mu / rho;
-    P.rho = (T)rho;
-    P.mu = (T)mu;
-    P.inv_rho = (T)(1.0 / rho);
-    P.G0 = (T)G[0];
-    P.G1 = (T)G[1];
-    P.G2 = (T)G[2];
-    P.inv_trG = (T)(1.0 / trG);
-    P.q0 = (T)(m->phys.C_T / (dt * dt) + m->phys.C_I * nu * nu * GG);
-    P.ih0 = (T)(1.0 / h[0]);
-    P.ih1 = (T)(1.0 / h[1]);
-    P.ih2 = (T)(1.0 / h[2]);
-    P.detJ = (T)(h[0] * h[1] * h[2] / 8.0);
-    P.c_a = (T)m->alpha_m;
-    P.c_v = (T)(m->alpha_f * m->gamma * dt);
-    P.has_s = m->phys.has_s != 0;
-    P.U = (const vec4<T> *)U;
-    P.A = (const vec4<T> *)A;
-    P.f = (const vec4<T> *)f;
-    P.x = (const vec4<T> *)x;
-    P.blocks = (vec4<T> *)m->vms_scratch;
-    P.out = (vec4<T> *)out;
-    return P;
+         node += gridDim.x * blockDim.x)
+        gather_node(P, node);
 }
 
 template <typename T, bool JAC>
