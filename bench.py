@@ -402,6 +402,12 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
                "sample": f"{passes} full FP64 oracle pass(es) of the step on the 64^3 workload "
                          f"({el:.1f} s, OpenMP over elements)"}
 
+    extras = {}
+    if not args.no_extras:
+        stream2 = torch.cuda.Stream(device=dev)
+        extras["newton"] = newton_section(args, dev, stream2)
+        extras["batch"] = batch_section(args, dev, stream2)
+        extras["mlp_inference"] = mlp_section(args, dev, stream2, W)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
@@ -427,11 +433,243 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
         "alu_peaks_tflop_s": {"f64": fma64 / 1e12, "f32": fma32 / 1e12},
         "hbm_peak_gbs": hbm,
     }
+    line.update(extras)
     print(json.dumps(line))
     if ws > 1:
         torch.distributed.barrier()
     mesh.close()
     return 0
+
+# ------------------------------------------------------------------ Newton section
+def newton_section(args, dev, stream):
+    """One implicit step of a pulsatile channel with leaflets (N^3 grid, 200k
+    volume-weighted points): plain FP64 vs mixed vs mixed + learned predictor,
+    all to ||R|| <= 1e-8 r_ref with r_ref the residual of the extrapolated
+    predictor.  A network is trained on the run's first steps (GPU kernels)."""
+    import torch
+    import paper_2601_08266_gb300 as fsi
+    from paper_2601_08266_gb300 import inputs
+    N, dt, period = args.newton_grid, 0.01, 0.12
+    mesh = fsi.Mesh(N, rho=1.0, mu=0.01, dt=dt, rho_inf=0.5, device=dev.index,
+                    stream=stream.cuda_stream)
+    n = mesh.n_nodes
+    ax = np.arange(N + 1) / N
+    Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+    X, Y, Z = X.ravel(), Y.ravel(), Z.ravel()
+    prof = 16.0 * Y * (1 - Y) * Z * (1 - Z)
+    wall = (Y < 1e-12) | (Y > 1 - 1e-12) | (Z < 1e-12) | (Z > 1 - 1e-12)
+    inflow = (X < 1e-12) & ~wall
+    mask = np.zeros((n, 4), dtype=np.uint8)
+    mask[wall | inflow, :3] = 1
+    gamma = 2.0 / 3.0
+    m = 200_000
+    with torch.cuda.stream(stream):
+        T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+        Vn = torch.zeros((n, 4), dtype=torch.float64, device=dev)
+        An, yn, d1, d2 = (torch.zeros_like(Vn) for _ in range(4))
+        Xp = inputs.leaflet_points(m, seed=SEED + 40)
+        e = torch.empty(m, dtype=torch.int32, device=dev)
+        xi = torch.empty((m, 3), dtype=torch.float64, device=dev)
+        cs = torch.empty(mesh.n_elems + 1, dtype=torch.int32, device=dev)
+        pm = torch.empty(m, dtype=torch.int32, device=dev)
+        wpts = torch.full((m,), 0.024 / m, dtype=torch.float64, device=dev)
+        maskd = T(mask)
+        work = torch.empty((5, n, 4), dtype=torch.float64, device=dev)
+    fsi.fsi_locate(mesh, T(Xp), e, xi, cs, pm)
+
+    def dirichlet(k):
+        g = np.zeros((n, 3))
+        g[inflow, 0] = prof[inflow] * np.sin(2 * np.pi * (k + 1) * dt / period)
+        with torch.cuda.stream(stream):
+            yD = torch.zeros_like(Vn)
+            yD[:, :3] = (T(g) - Vn[:, :3] - dt * (1 - gamma) * An[:, :3]) / (gamma * dt)
+        return yD
+
+    feats, targs = [], []
+    zeros = torch.zeros(112, dtype=torch.float32, device=dev)
+    ones = torch.ones(112, dtype=torch.float32, device=dev)
+    warm = args.newton_warm
+    for k in range(warm):
+        yD = dirichlet(k)
+        with torch.cuda.stream(stream):
+            y = yn + 2 * d1 - d2
+            y[maskd.bool()] = yD[maskd.bool()]
+        st = fsi.StepState(y, Vn, An, mask=maskd, yD=yD, elem=e, xi=xi, cell_start=cs, perm=pm,
+                           w=wpts, drho_s=0.5)
+        if k >= 2:
+            Xf = torch.empty((n, 112), dtype=torch.float32, device=dev)
+            fsi.fsi_mlp_features(mesh, Vn, yn, d1, d2, None, zeros, ones, Xf)
+        fsi.fsi_newton_step(mesh, st, mixed=True, restart=50, max_newton=10, max_krylov=4000)
+        with torch.cuda.stream(stream):
+            dn = y - yn
+            if k >= 2:
+                feats.append(Xf)
+                targs.append(torch.where(maskd.bool(), torch.zeros_like(dn), dn - (2 * d1 - d2)))
+            d2, d1, yn = d1, dn, y.clone()
+        fsi.fsi_advance_history(mesh, fsi.FSI_F64, y, Vn, An)
+    # train the network on the GPU (BF16 tensor-core kernels)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        Xa = torch.cat(feats)
+        Ca = torch.cat(targs).float()
+        im, isd = Xa.mean(0), Xa.std(0) + 1e-6
+        om, osd = Ca.mean(0), Ca.std(0) + 1e-12
+        Xn = ((Xa - im) / isd).contiguous()
+        Cn = ((Ca - om) / osd).contiguous()
+        P = torch.randn(fsi.fsi_mlp_num_params(), device=dev) * 0.0
+        gen = torch.Generator(device=dev).manual_seed(SEED)
+        off = 0
+        for fan_in, size in ((112, 112 * 256), (0, 256), (256, 256 * 256), (0, 256), (256, 1024),
+                             (0, 4)):
+            if fan_in:
+                P[off:off + size] = torch.randn(size, device=dev, generator=gen) * (2.0 / fan_in) ** 0.5
+            off += size
+        Mo, Vo, G = torch.zeros_like(P), torch.zeros_like(P), torch.empty_like(P)
+        loss = torch.empty(1, dtype=torch.float32, device=dev)
+    h = fsi.Mlp(65536, device=dev.index, stream=stream.cuda_stream)
+    losses = []
+    for it in range(1, args.mlp_iters + 1):
+        with torch.cuda.stream(stream):
+            idx = torch.randint(0, Xn.shape[0], (4096,), device=dev, generator=gen)
+            xb, cb = Xn[idx].contiguous(), Cn[idx].contiguous()
+        fsi.fsi_mlp_loss_grad(h, P, xb, cb, loss, G)
+        fsi.fsi_mlp_adam(h, P, G, Mo, Vo, it, lr=1e-3)
+        if it in (1, args.mlp_iters):
+            stream.synchronize()
+            losses.append(float(loss.item()))
+    stream.synchronize()
+    train_s = time.perf_counter() - t0
+    # the timed step: three variants from the same history
+    k = warm
+    yD = dirichlet(k)
+    out = {"grid": [N, N, N], "dofs": 4 * n, "points": m, "train_seconds": train_s,
+           "train_samples": int(Xn.shape[0]), "train_loss": losses}
+    variants = [("fp64", False, False), ("mixed", True, False), ("mixed_learned", True, True)]
+    r_ref = None
+    for name, mixed, learned in variants:
+        with torch.cuda.stream(stream):
+            y = yn + 2 * d1 - d2
+            y[maskd.bool()] = yD[maskd.bool()]
+        st = fsi.StepState(y, Vn, An, mask=maskd, yD=yD, elem=e, xi=xi, cell_start=cs, perm=pm,
+                           w=wpts, drho_s=0.5)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        guess = None
+        if learned:
+            guess = fsi.fsi_mlp_guess(h, mesh, P, (im).float().contiguous(),
+                                      isd.float().contiguous(), om.contiguous(), osd.contiguous(),
+                                      st, yn, d1, d2, 1, work)
+        code, rep = fsi.fsi_newton_step(mesh, st, mixed=mixed, restart=50, max_newton=10,
+                                        max_krylov=4000, newton_rtol=1e-8, krylov_rtol=1e-3,
+                                        r_ref=r_ref or 0.0, check=False)
+        stream.synchronize()
+        el = time.perf_counter() - t0
+        if r_ref is None:
+            r_ref = rep["r_ref"]
+        out[name] = {"seconds": el, "newton_iters": rep["newton_iters"],
+                     "krylov_iters": rep["krylov_iters"], "r_final_over_ref": rep["r_final"] / r_ref,
+                     "converged": bool(rep["converged"]), "status": code}
+        if guess is not None:
+            out[name]["predictor"] = {k2: guess[k2] for k2 in ("r_fallback", "r_learned",
+                                                               "r_combined", "used")}
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    out["speedup_mixed_learned_vs_fp64"] = out["fp64"]["seconds"] / out["mixed_learned"]["seconds"]
+    h.close()
+    mesh.close()
+    return out
+
+
+# ------------------------------------------------------------------ batched ensemble
+def batch_section(args, dev, stream):
+    """64 independent instances (N ~ U{16..48}, mu ~ logU[1e-3, 1e-1], 10k-150k
+    leaflet points each): per-instance launches vs persistent grids vs the CUDA
+    graph of the persistent step, FP32 and FP64."""
+    import torch
+    import paper_2601_08266_gb300 as fsi
+    from paper_2601_08266_gb300 import inputs
+    rng = np.random.default_rng(SEED + 50)
+    count = args.batch_count
+    Ns = rng.integers(16, 49, size=count)
+    mus = np.exp(rng.uniform(np.log(1e-3), np.log(1e-1), size=count))
+    ms = rng.integers(10_000, 150_001, size=count)
+    out = {"instances": count, "dofs_total": int(sum(4 * (N + 1) ** 3 for N in Ns)),
+           "points_total": int(ms.sum())}
+    for prec_name, dt_t, P in (("f32", torch.float32, fsi.FSI_F32), ("f64", torch.float64, fsi.FSI_F64)):
+        meshes, items = [], []
+        for i in range(count):
+            N, m = int(Ns[i]), int(ms[i])
+            mesh = fsi.Mesh(N, rho=1.0, mu=float(mus[i]), dt=1e-3, rho_inf=0.5, device=dev.index,
+                            stream=stream.cuda_stream)
+            n = mesh.n_nodes
+            with torch.cuda.stream(stream):
+                g = torch.Generator(device=dev).manual_seed(SEED + i)
+                it = {k: (torch.rand((n, 4), device=dev, generator=g) * 2 - 1).to(dt_t)
+                      for k in ("U", "A", "x")}
+                it.update(R=torch.empty((n, 4), dtype=dt_t, device=dev),
+                          Jx=torch.empty((n, 4), dtype=dt_t, device=dev),
+                          F=torch.empty((n, 4), dtype=dt_t, device=dev),
+                          cell_start=torch.empty(N ** 3 + 1, dtype=torch.int32, device=dev),
+                          elem=torch.empty(m, dtype=torch.int32, device=dev),
+                          perm=torch.empty(m, dtype=torch.int32, device=dev),
+                          lam=torch.randn((m, 3), device=dev, generator=g).to(dt_t),
+                          u=torch.empty((m, 3), dtype=dt_t, device=dev))
+                xi64 = torch.empty((m, 3), dtype=torch.float64, device=dev)
+                Xp = torch.as_tensor(inputs.leaflet_points(m, seed=SEED + 100 + i), device=dev)
+            fsi.fsi_locate(mesh, Xp, it["elem"], xi64, it["cell_start"], it["perm"],
+                           want_outside=False)
+            with torch.cuda.stream(stream):
+                it["xi"] = xi64.to(dt_t).contiguous()
+            meshes.append(mesh)
+            items.append(it)
+        stream.synchronize()
+        b = fsi.Batch(meshes, items, P, stream.cuda_stream)
+        res = {}
+        if prec_name == "f32" or args.batch_tune_f64:
+            tune = b.autotune(reps=1)
+            res["autotuned"] = {"brick": tune["brick"], "threads": tune["threads"],
+                                "ctas_per_sm": tune["ctas_per_sm"]}
+        for name, mode in (("per_instance", fsi.FSI_BATCH_PER_INSTANCE),
+                           ("persistent", fsi.FSI_BATCH_PERSISTENT), ("graph", fsi.FSI_BATCH_GRAPH)):
+            t = b.time(mode, reps=args.batch_reps)
+            res[name] = {"ms": t * 1e3, "gdof_s": out["dofs_total"] / t / 1e9}
+        res["speedup_graph_vs_per_instance"] = res["per_instance"]["ms"] / res["graph"]["ms"]
+        out[prec_name] = res
+        b.close()
+        for mm in meshes:
+            mm.close()
+    return out
+
+
+# ------------------------------------------------------------------ MLP inference
+def mlp_section(args, dev, stream, W):
+    import torch
+    import paper_2601_08266_gb300 as fsi
+    N = W["N"]
+    mesh = fsi.Mesh(N, device=dev.index, stream=stream.cuda_stream)
+    n = mesh.n_nodes
+    with torch.cuda.stream(stream):
+        P = torch.randn(fsi.fsi_mlp_num_params(), device=dev) * 0.05
+        st = [torch.as_tensor(W[k], device=dev).contiguous() for k in ("Vn", "y", "An", "x")]
+        stats = [torch.zeros(112, device=dev), torch.ones(112, device=dev),
+                 torch.zeros(4, device=dev), torch.ones(4, device=dev)]
+        y0 = torch.empty((n, 4), dtype=torch.float64, device=dev)
+    h = fsi.Mlp(131072, device=dev.index, stream=stream.cuda_stream)
+    for _ in range(2):
+        fsi.fsi_mlp_predict(h, mesh, P, *stats, st[0], st[1], st[2], st[3], y0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        fsi.fsi_mlp_predict(h, mesh, P, *stats, st[0], st[1], st[2], st[3], y0)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * n * (112 * 256 + 256 * 256 + 256 * 4)
+    h.close()
+    mesh.close()
+    return {"nodes": n, "ms": ms, "tflop_s": flops / (ms * 1e-3) / 1e12,
+            "kernel": "mma.sync m16n8k16 BF16, FP32 accumulate"}
+
 
 
 def main():
@@ -445,6 +683,13 @@ def main():
     ap.add_argument("--grid", type=int, default=N_GRID, help="elements per axis (profiling)")
     ap.add_argument("--points", type=int, default=M_POINTS, help="solid points (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip Newton, batch and MLP sections")
+    ap.add_argument("--newton-grid", type=int, default=64)
+    ap.add_argument("--newton-warm", type=int, default=5)
+    ap.add_argument("--mlp-iters", type=int, default=300)
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--batch-tune-f64", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
