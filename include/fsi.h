@@ -56,7 +56,12 @@ typedef enum {
     FSI_ERR_NAN = 7       /* a non-finite norm was met                        */
 } fsi_status;
 
-typedef enum { FSI_F64 = 0, FSI_F32 = 1 } fsi_prec;
+/* FSI_F64: IEEE double arrays and arithmetic.  FSI_F32: IEEE float.
+ * FSI_DF64: IEEE double arrays, arithmetic in double-float (pairs of floats,
+ * about 48 significant bits) on the FP32 pipe -- GB300 runs FP32 ~70x faster
+ * than FP64; accepted by fsi_residual and fsi_jacobian_apply, whose results
+ * then agree with FP64 to ~1e-13 relative.                                 */
+typedef enum { FSI_F64 = 0, FSI_F32 = 1, FSI_DF64 = 2 } fsi_prec;
 
 /* Opaque handle: grid, physics, stream, tuning and library-owned scratch. */
 typedef struct fsi_mesh fsi_mesh;

@@ -15,7 +15,7 @@ from . import build as _build
 
 FSI_OK, FSI_ERR_ARG, FSI_ERR_CUDA, FSI_ERR_OOM, FSI_ERR_OUTSIDE = 0, 1, 2, 3, 4
 FSI_ERR_NOCONV, FSI_ERR_TIMEOUT, FSI_ERR_NAN = 5, 6, 7
-FSI_F64, FSI_F32 = 0, 1
+FSI_F64, FSI_F32, FSI_DF64 = 0, 1, 2
 STATUS_NAMES = {0: "FSI_OK", 1: "FSI_ERR_ARG", 2: "FSI_ERR_CUDA", 3: "FSI_ERR_OOM",
                 4: "FSI_ERR_OUTSIDE", 5: "FSI_ERR_NOCONV", 6: "FSI_ERR_TIMEOUT",
                 7: "FSI_ERR_NAN"}
@@ -187,7 +187,7 @@ def _ptr(t, dtype=None):
 
 def _prec_dtype(prec):
     import torch
-    return torch.float64 if prec == FSI_F64 else torch.float32
+    return torch.float32 if prec == FSI_F32 else torch.float64
 
 
 class Mesh:

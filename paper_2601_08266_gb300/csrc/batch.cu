@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) batch_brick_kernel(const vmsd::VmsArgs<T>
                                                           const int64_t *prefix, int count)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    vec4<T> *rel = reinterpret_cast<vec4<T> *>(smem_raw);
+    auto *rel = reinterpret_cast<vec4<T> *>(smem_raw);
     const int64_t total = prefix[count];
     for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
         const int inst = find_instance(prefix, count, item);

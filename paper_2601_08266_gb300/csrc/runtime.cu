@@ -314,7 +314,8 @@ fsi_status fsi_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A
     if (!U || !A || !R) return set_error(FSI_ERR_ARG, "fsi_residual: NULL array argument");
     if (R == U || R == A || (f && R == f))
         return set_error(FSI_ERR_ARG, "fsi_residual: R aliases an input");
-    if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
+    if (prec != FSI_F64 && prec != FSI_F32 && prec != FSI_DF64)
+        return set_error(FSI_ERR_ARG, "bad precision");
     FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
     return vms_residual(m, prec, U, A, f, R);
 }
@@ -327,7 +328,8 @@ fsi_status fsi_jacobian_apply(fsi_mesh *m, fsi_prec prec, const void *U, const v
         return set_error(FSI_ERR_ARG, "fsi_jacobian_apply: NULL array argument");
     if (Jx == U || Jx == A || Jx == x)
         return set_error(FSI_ERR_ARG, "fsi_jacobian_apply: Jx aliases an input");
-    if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
+    if (prec != FSI_F64 && prec != FSI_F32 && prec != FSI_DF64)
+        return set_error(FSI_ERR_ARG, "bad precision");
     FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
     return vms_jacobian(m, prec, U, A, f, x, Jx);
 }

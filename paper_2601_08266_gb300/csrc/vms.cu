@@ -49,11 +49,11 @@ template <typename T, bool JAC>
 fsi_status launch(fsi_mesh *m, const void *U, const void *A, const void *f, const void *x,
                   void *out)
 {
-    const Brick &b = m->brick[JAC ? 1 : 0][sizeof(T) == 8 ? FSI_F64 : FSI_F32];
+    const Brick &b = m->brick[JAC ? 1 : 0][sizeof(typename StorageOf<T>::type) == 8 ? FSI_F64 : FSI_F32];
     FSI_TRY(ensure_vms_scratch(m, b, sizeof(T)));
     VmsArgs<T> P = make_args<T>(m, b, U, A, f, x, out);
     const int nbricks = P.nbx * P.nby * P.nbz;
-    const size_t smem = (size_t)b.bx * b.by * b.bz * 8 * sizeof(vec4<T>);
+    const size_t smem = (size_t)b.bx * b.by * b.bz * 8 * sizeof(vec4<typename StorageOf<T>::type>);
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
         FSI_CUDA(cudaFuncSetAttribute(vms_brick_kernel<T, JAC>,
@@ -76,6 +76,7 @@ fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A
                         const void *f, void *R)
 {
     if (prec == FSI_F64) return launch<double, false>(m, U, A, f, nullptr, R);
+    if (prec == FSI_DF64) return launch<df64, false>(m, U, A, f, nullptr, R);
     return launch<float, false>(m, U, A, f, nullptr, R);
 }
 
@@ -83,6 +84,7 @@ fsi_status vms_jacobian(fsi_mesh *m, fsi_prec prec, const void *U, const void *A
                         const void *f, const void *x, void *Jx)
 {
     if (prec == FSI_F64) return launch<double, true>(m, U, A, f, x, Jx);
+    if (prec == FSI_DF64) return launch<df64, true>(m, U, A, f, x, Jx);
     return launch<float, true>(m, U, A, f, x, Jx);
 }
 

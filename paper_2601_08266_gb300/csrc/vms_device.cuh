@@ -3,6 +3,7 @@
 // (batch.cu).  See vms.cu for the design.
 #pragma once
 
+#include "df64.cuh"
 #include "fsi_internal.cuh"
 
 namespace fsi {
@@ -11,8 +12,51 @@ namespace vmsd {
 constexpr double kQ = 0.57735026918962576451;  // 1/sqrt(3): Gauss abscissa
 constexpr double kB1 = 0.5 * (1.0 + kQ);      // 1D linear basis at the near point
 constexpr double kB2 = 0.5 * (1.0 - kQ);      // ... at the far point
+// the same constants as exact float pairs (split at compile time)
+constexpr float kB1h = static_cast<float>(kB1);
+constexpr float kB1l = static_cast<float>(kB1 - static_cast<double>(kB1h));
+constexpr float kB2h = static_cast<float>(kB2);
+constexpr float kB2l = static_cast<float>(kB2 - static_cast<double>(kB2h));
+
+template <typename T> __device__ __forceinline__ T cB1() { return T(kB1); }
+template <typename T> __device__ __forceinline__ T cB2() { return T(kB2); }
+template <> __device__ __forceinline__ df64 cB1<df64>() { return df64(kB1h, kB1l); }
+template <> __device__ __forceinline__ df64 cB2<df64>() { return df64(kB2h, kB2l); }
+
+// Storage (I/O) type of a compute type: double-float computes on FP64 data.
+template <typename C> struct StorageOf {
+    using type = C;
+};
+template <> struct StorageOf<df64> {
+    using type = double;
+};
+
+template <typename C> __device__ __forceinline__ C to_c(typename StorageOf<C>::type v)
+{
+    return C(v);
+}
+template <> __device__ __forceinline__ df64 to_c<df64>(double v) { return df_split(v); }
+
+// node record of double-float values (two float4 loads)
+__device__ __forceinline__ vec4<df64> ld4_df(const vec4<df64> *p)
+{
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    const float4 a = __ldg(q), b = __ldg(q + 1);
+    return {df64(a.x, a.y), df64(a.z, a.w), df64(b.x, b.y), df64(b.z, b.w)};
+}
+template <typename T> __device__ __forceinline__ vec4<T> ld4_blk(const vec4<T> *p) { return ld4(p); }
+template <> __device__ __forceinline__ vec4<df64> ld4_blk<df64>(const vec4<df64> *p)
+{
+    return ld4_df(p);
+}
+template <typename C> __device__ __forceinline__ typename StorageOf<C>::type to_s(C v)
+{
+    return v;
+}
+template <> __device__ __forceinline__ double to_s<df64>(df64 v) { return v.to_double(); }
 
 template <typename T> struct VmsArgs {
+    using S = typename StorageOf<T>::type;
     int Nx, Ny, Nz;
     int bx, by, bz;
     int nbx, nby, nbz;
@@ -22,14 +66,23 @@ template <typename T> struct VmsArgs {
     T detJ;
     T c_a, c_v;                 // d A / d y_v, d U / d y_v
     int has_s;
-    const vec4<T> *U, *A, *f, *x;
-    vec4<T> *blocks;  // [n_bricks][(bx+1)(by+1)(bz+1)]
-    vec4<T> *out;     // [n]
+    const vec4<S> *U, *A, *f, *x;
+    vec4<T> *blocks;  // [n_bricks][(bx+1)(by+1)(bz+1)], in the compute type
+    vec4<S> *out;     // [n]
 };
 
 template <typename T> __device__ __forceinline__ T shx(T v, int m)
 {
     return __shfl_xor_sync(0xffffffffu, v, m);
+}
+template <> __device__ __forceinline__ df64 shx<df64>(df64 v, int m) { return df_shfl_xor(v, m); }
+
+// one node record of storage type S as compute type T
+template <typename T>
+__device__ __forceinline__ vec4<T> load_c(const vec4<typename StorageOf<T>::type> *p)
+{
+    const auto v = ld4(p);
+    return {to_c<T>(v.x), to_c<T>(v.y), to_c<T>(v.z), to_c<T>(v.w)};
 }
 
 template <typename T> struct VG {
@@ -41,7 +94,7 @@ template <typename T> struct VG {
 // lane's node sits at the upper side along x (and likewise sy, sz).
 template <typename T> __device__ __forceinline__ VG<T> eval_vg(T u, T sx, T sy, T sz)
 {
-    const T b1 = T(kB1), b2 = T(kB2);
+    const T b1 = cB1<T>(), b2 = cB2<T>();
     T uo = shx(u, 1);
     T tB = b1 * u + b2 * uo;
     T tD = u - uo;
@@ -60,7 +113,7 @@ template <typename T> __device__ __forceinline__ VG<T> eval_vg(T u, T sx, T sy, 
 
 template <typename T> __device__ __forceinline__ T eval_v(T u)
 {
-    const T b1 = T(kB1), b2 = T(kB2);
+    const T b1 = cB1<T>(), b2 = cB2<T>();
     T t = b1 * u + b2 * shx(u, 1);
     t = b1 * t + b2 * shx(t, 2);
     return b1 * t + b2 * shx(t, 4);
@@ -72,7 +125,7 @@ template <typename T> __device__ __forceinline__ T eval_v(T u)
 template <typename T>
 __device__ __forceinline__ T project(T X, T Yx, T Yy, T Yz, T sx, T sy, T sz)
 {
-    const T b1 = T(kB1), b2 = T(kB2);
+    const T b1 = cB1<T>(), b2 = cB2<T>();
     T Xo = shx(X, 4), Yzo = shx(Yz, 4), Yxo = shx(Yx, 4), Yyo = shx(Yy, 4);
     T P1 = b1 * X + b2 * Xo + sz * (Yz + Yzo);
     T P2 = b1 * Yx + b2 * Yxo;
@@ -87,6 +140,7 @@ __device__ __forceinline__ T project(T X, T Yx, T Yy, T Yz, T sx, T sy, T sz)
 template <typename T> __device__ __forceinline__ T rsqrt_t(T v);
 template <> __device__ __forceinline__ float rsqrt_t(float v) { return 1.0f / sqrtf(v); }
 template <> __device__ __forceinline__ double rsqrt_t(double v) { return 1.0 / sqrt(v); }
+template <> __device__ __forceinline__ df64 rsqrt_t(df64 v) { return df_rsqrt(v); }
 
 // Base state of the VMS form at one Gauss point.
 template <typename T> struct GP {
@@ -135,9 +189,9 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
         const bool valid = slot < nel && ex < P.Nx && ey < P.Ny && ez < P.Nz;
         const int node = valid ? (ex + gx) + NX1 * (ey + gy) + NXY1 * (ez + gz) : 0;
         const vec4<T> zero = {T(0), T(0), T(0), T(0)};
-        vec4<T> u = valid ? ld4(P.U + node) : zero;
-        vec4<T> ac = valid ? ld4(P.A + node) : zero;
-        vec4<T> ff = (valid && P.f) ? ld4(P.f + node) : zero;
+        vec4<T> u = valid ? load_c<T>(P.U + node) : zero;
+        vec4<T> ac = valid ? load_c<T>(P.A + node) : zero;
+        vec4<T> ff = (valid && P.f) ? load_c<T>(P.f + node) : zero;
 
         GP<T> q;
         {
@@ -176,7 +230,7 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
             X[3] = q.rC;
             for (int j = 0; j < 3; ++j) Y[3][j] = -q.up[j];
         } else {
-            vec4<T> xx = valid ? ld4(P.x + node) : zero;
+            vec4<T> xx = valid ? load_c<T>(P.x + node) : zero;
             T dv[3], dgv[3][3], da[3], dp, dgp[3];
             {
                 VG<T> e0 = eval_vg(xx.x, sx, sy, sz), e1 = eval_vg(xx.y, sx, sy, sz),
@@ -270,6 +324,7 @@ static __device__ __forceinline__ int axis_candidates(int i, int b, int nb, int 
 // bricks first.
 template <typename T> __device__ __forceinline__ void gather_node(const VmsArgs<T> &P, int node)
 {
+    using S = typename StorageOf<T>::type;
     const int NX1 = P.Nx + 1, NY1 = P.Ny + 1;
     const int nx1 = P.bx + 1, ny1 = P.by + 1, nz1 = P.bz + 1;
     const int nnodes = nx1 * ny1 * nz1;
@@ -285,13 +340,13 @@ template <typename T> __device__ __forceinline__ void gather_node(const VmsArgs<
                 for (int a = 0; a < kx; ++a) {
                     const size_t brick = cbx[a] + P.nbx * (cby[b] + (size_t)P.nby * cbz[c]);
                     const int nl = clx[a] + nx1 * (cly[b] + ny1 * clz[c]);
-                    const vec4<T> r = ld4(P.blocks + brick * nnodes + nl);
+                    const vec4<T> r = ld4_blk(P.blocks + brick * nnodes + nl);
                     acc.x += r.x;
                     acc.y += r.y;
                     acc.z += r.z;
                     acc.w += r.w;
                 }
-        P.out[node] = acc;
+        P.out[node] = {to_s(acc.x), to_s(acc.y), to_s(acc.z), to_s(acc.w)};
     }
 }
 
@@ -333,12 +388,13 @@ VmsArgs<T> make_args(const fsi_mesh *m, const Brick &b, const void *U, const voi
     P.c_a = (T)m->alpha_m;
     P.c_v = (T)(m->alpha_f * m->gamma * dt);
     P.has_s = m->phys.has_s != 0;
-    P.U = (const vec4<T> *)U;
-    P.A = (const vec4<T> *)A;
-    P.f = (const vec4<T> *)f;
-    P.x = (const vec4<T> *)x;
+    using S = typename StorageOf<T>::type;
+    P.U = (const vec4<S> *)U;
+    P.A = (const vec4<S> *)A;
+    P.f = (const vec4<S> *)f;
+    P.x = (const vec4<S> *)x;
     P.blocks = (vec4<T> *)m->vms_scratch;
-    P.out = (vec4<T> *)out;
+    P.out = (vec4<S> *)out;
     return P;
 }
 

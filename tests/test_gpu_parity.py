@@ -13,7 +13,7 @@ from paper_2601_08266_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5}
+TOL = {"f64": 1e-12, "f32": 1e-5, "df64": 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +47,7 @@ def cast(prec, a):
 
 def dtype_of(prec):
     import torch
-    return torch.float64 if prec == "f64" else torch.float32
+    return torch.float32 if prec == "f32" else torch.float64
 
 
 def make(fsi, oracle, N, h=None, x0=(0.0, 0.0, 0.0), **phys):
@@ -60,7 +60,7 @@ def make(fsi, oracle, N, h=None, x0=(0.0, 0.0, 0.0), **phys):
 
 def vms_case(fsi, oracle, mesh, grid, p, U, A, f, x, prec):
     import torch
-    P = fsi.FSI_F64 if prec == "f64" else fsi.FSI_F32
+    P = {"f64": fsi.FSI_F64, "f32": fsi.FSI_F32, "df64": fsi.FSI_DF64}[prec]
     dt = dtype_of(prec)
     U, A, x = cast(prec, U), cast(prec, A), cast(prec, x)
     f = None if f is None else cast(prec, f)
@@ -96,7 +96,7 @@ def test_stage_matches_generalized_alpha(fsi, oracle, prec):
 
 
 # ---------------------------------------------------------------- VMS
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64"])
 def test_vms_config1_one_implicit_step(fsi, oracle, prec):
     """8^3 grid, y ~ U[-1,1], zero history, stage by generalized alpha."""
     mesh, grid, p = make(fsi, oracle, 8)
@@ -108,7 +108,7 @@ def test_vms_config1_one_implicit_step(fsi, oracle, prec):
     assert eJ < TOL[prec], eJ
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64"])
 @pytest.mark.parametrize("N,h", [((13, 10, 9), (0.07, 0.11, 0.09)), ((1, 1, 1), (0.3, 0.3, 0.3)),
                                  ((17, 3, 5), None)])
 def test_vms_ragged_bricks_anisotropic(fsi, oracle, prec, N, h):
@@ -144,7 +144,7 @@ def test_vms_deterministic(fsi, oracle):
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64"])
 def test_vms_config2_full_size(fsi, oracle, prec):
     """64^3 grid (262k elements, 1.1M DOFs), smooth Fourier velocity and pressure
     plus noise: the whole residual and Jacobian apply against the oracle."""
@@ -158,6 +158,7 @@ def test_vms_config2_full_size(fsi, oracle, prec):
     eR, eJ, _ = vms_case(fsi, oracle, mesh, grid, p, U, A, None, x, prec)
     assert eR < TOL[prec], eR
     assert eJ < TOL[prec], eJ
+    print(f"\n64^3 {prec}: residual rel err {eR:.2e}, Jacobian rel err {eJ:.2e}")
 
 
 # ---------------------------------------------------------------- DLM
