@@ -25,8 +25,10 @@
  *     mesh was created with has_s != 0 (it is ignored otherwise).
  *     Elements are numbered e = ex + Nx*(ey + Ny*ez).
  *   - fsi_prec selects the element type of the floating-point arrays of that
- *     call: FSI_F64 = double, FSI_F32 = float.  Point coordinates X are always
- *     double.
+ *     call: FSI_F64 = double, FSI_F32 = float.  FSI_DF64 takes double arrays
+ *     and computes in double-float arithmetic (pairs of floats on the FP32
+ *     units, about 2^-44 relative per operation); the calls that accept it
+ *     say so.  Point coordinates X are always double.
  *   - Calls are asynchronous and stream-ordered on the mesh's stream, except
  *     where a comment says the call synchronises.  Arrays must stay valid
  *     until the stream has passed the call.
@@ -192,7 +194,8 @@ fsi_status fsi_locate_noalloc(const fsi_grid *grid, int64_t m, const double *X, 
 /* Interpolation of the fluid velocity to the solid points, u = C^T V
  * (Eq. nodal_solid_velo): u_B = sum_A N_A(xi_B) V_A over the 8 nodes of
  * element elem[B], velocity slots only.  xi [m][3] and U [n][4] and u [m][3]
- * are in `prec`; elem [m] int32 from fsi_locate.  Outside points (elem < 0)
+ * are in `prec` (FSI_F64, FSI_F32 or FSI_DF64 on double arrays); elem [m]
+ * int32 from fsi_locate.  Outside points (elem < 0)
  * get u = 0; so do points whose elem is >= E (never produced by
  * fsi_locate), which are never dereferenced.                               */
 fsi_status fsi_dlm_interp(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_t *elem,
@@ -202,8 +205,9 @@ fsi_status fsi_dlm_interp(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
  * (Eq. fsi_constraint_matrix): F_A += sum_B w_B N_A(xi_B) lambda_B into the
  * momentum slots 0..2 of F [n][4]; slot 3 is neither read nor written.
  * accumulate == 0 overwrites slots 0..2 instead of adding.  lam [m][3],
- * w [m] (NULL: w_B = 1), xi [m][3] and F are in `prec`.  elem, cell_start
- * and perm are the outputs of fsi_locate for the same points.  No atomic
+ * w [m] (NULL: w_B = 1), xi [m][3] and F are in `prec` (FP64 for FSI_DF64,
+ * which computes in double-float on FP32 units to about 2^-44 relative).
+ * elem, cell_start and perm are the outputs of fsi_locate for the same points.  No atomic
  * operation is used and the result is deterministic: each cell's corner sums
  * are formed over its points in perm order with a fixed reduction tree (in
  * mesh scratch), then each node adds the sums of its (up to) 8 cells in a

@@ -75,7 +75,7 @@ __global__ void batch_interp_kernel(const DlmDesc<T> *desc, const int64_t *prefi
         const int inst = find_instance(prefix, count, item);
         const DlmDesc<T> &D = desc[inst];
         const int64_t b = (item - prefix[inst]) * kChunk + threadIdx.x;
-        if (b < D.m) dlmd::interp_point(D.g, b, D.elem, D.xi, D.U, D.u);
+        if (b < D.m) dlmd::interp_point<T>(D.g, b, D.elem, D.xi, D.U, D.u);
     }
 }
 
@@ -89,7 +89,7 @@ __global__ void batch_spread_cells_kernel(const DlmDesc<T> *desc, const int64_t 
         const int inst = find_instance(prefix, count, item);
         const DlmDesc<T> &D = desc[inst];
         const int64_t c0 = ((item - prefix[inst]) * 8 + warp) * 32;
-        if (c0 < D.E) dlmd::spread_cells_segment(D.E, c0, D.xi, D.start, D.perm, D.lam, D.w, D.S);
+        if (c0 < D.E) dlmd::spread_cells_segment<T>(D.E, c0, D.xi, D.start, D.perm, D.lam, D.w, D.S);
     }
 }
 
@@ -103,7 +103,7 @@ __global__ void batch_spread_nodes_kernel(const DlmDesc<T> *desc, const int64_t 
         const DlmDesc<T> &D = desc[inst];
         const int n = (D.g.Nx + 1) * (D.g.Ny + 1) * (D.g.Nz + 1);
         const int64_t node = (item - prefix[inst]) * kChunk + threadIdx.x;
-        if (node < n) dlmd::spread_node(D.g, (int)node, D.start, D.S, D.F, 0);
+        if (node < n) dlmd::spread_node<T>(D.g, (int)node, D.start, D.S, D.F, 0);
     }
 }
 
@@ -135,8 +135,6 @@ struct fsi_batch {
 
 namespace fsi {
 namespace {
-
-size_t esize(fsi_prec p) { return p == FSI_F64 ? sizeof(double) : sizeof(float); }
 
 // (Re)build descriptors and scratch for the batch's current brick shape.
 template <typename T> fsi_status build_batch(fsi_batch *b)

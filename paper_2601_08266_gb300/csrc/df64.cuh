@@ -24,6 +24,7 @@ struct df64 {
         hi = (float)d;
         lo = (float)(d - (double)hi);
     }
+    __host__ __device__ constexpr explicit df64(float h) : hi(h), lo(0.0f) {}
     // small integers are exact in one float
     __host__ __device__ constexpr df64(int i) : hi((float)i), lo(0.0f) {}
     __host__ __device__ double to_double() const { return (double)hi + (double)lo; }
@@ -110,5 +111,33 @@ __device__ __forceinline__ df64 df_shfl_xor(df64 v, int m)
 {
     return df64(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
 }
+
+
+// Storage (I/O) type of a compute type: double-float computes on FP64 data.
+template <typename C> struct StorageOf {
+    using type = C;
+};
+template <> struct StorageOf<df64> {
+    using type = double;
+};
+
+template <typename C> __device__ __forceinline__ C to_c(typename StorageOf<C>::type v)
+{
+    return C(v);
+}
+
+template <> __device__ __forceinline__ df64 to_c<df64>(double v) { return df_split(v); }
+
+template <typename C> __device__ __forceinline__ typename StorageOf<C>::type to_s(C v)
+{
+    return v;
+}
+template <> __device__ __forceinline__ double to_s<df64>(df64 v) { return v.to_double(); }
+
+template <typename T> __device__ __forceinline__ T shfl_x(T v, int m)
+{
+    return __shfl_xor_sync(0xffffffffu, v, m);
+}
+template <> __device__ __forceinline__ df64 shfl_x<df64>(df64 v, int m) { return df_shfl_xor(v, m); }
 
 }  // namespace fsi

@@ -163,9 +163,9 @@ __global__ void scatter_kernel(int64_t m, int64_t E, const int32_t *__restrict__
 // Sort every cell's slice of perm ascending (restores the stable order).
 // Cell E is the tail of outside points [start[E], m).  One warp per segment of
 // 32 consecutive cells; each slice is sorted by ranks (values are distinct
-// point indices, so rank_i = #{j : v_j < v_i} is a permutation): registers for
-// slices of up to 32, a two-phase rank pass through local arrays up to 1024,
-// and a single-lane shell sort beyond (rare: very dense cells).
+// point indices, so rank_i = #{j : v_j < v_i} is a permutation) held in
+// registers for slices of up to 128 points, and a single-lane shell sort
+// beyond (rare: very dense cells).
 __device__ void shell_sort(int32_t *s, int len)
 {
     int gap = 1;
@@ -214,22 +214,26 @@ __global__ void cell_sort_kernel(int64_t E, int64_t m, const int32_t *__restrict
                 __syncwarp();
                 if (lane < n) sl[rank] = v;
                 __syncwarp();
-            } else if (n <= 1024) {
-                int own[32], rk[32];
-                const int nown = (n - lane + 31) / 32;  // elements lane, lane+32, ...
-                for (int i = 0; i < 32; ++i) {
-                    own[i] = (i < nown) ? sl[lane + 32 * i] : INT32_MAX;
-                    rk[i] = 0;
+            } else if (n <= 128) {
+                // four values per lane, all in registers
+                int own[4], rk[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    own[k] = (lane + 32 * k < n) ? sl[lane + 32 * k] : INT32_MAX;
+                    rk[k] = 0;
                 }
-                for (int k = 0; k < (n + 31) / 32; ++k) {
-                    const int w = (32 * k + lane < n) ? sl[32 * k + lane] : INT32_MAX;
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll 8
                     for (int j = 0; j < 32; ++j) {
-                        const int wj = __shfl_sync(0xffffffffu, w, j);
-                        for (int i = 0; i < nown; ++i) rk[i] += wj < own[i];
+                        const int wj = __shfl_sync(0xffffffffu, own[c], j);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) rk[k] += wj < own[k];
                     }
-                }
                 __syncwarp();
-                for (int i = 0; i < nown; ++i) sl[rk[i]] = own[i];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (lane + 32 * k < n) sl[rk[k]] = own[k];
                 __syncwarp();
             } else {
                 if (lane == 0) shell_sort(sl, n);
@@ -240,39 +244,44 @@ __global__ void cell_sort_kernel(int64_t E, int64_t m, const int32_t *__restrict
 }
 
 // --------------------------------------------------------------- interp / spread
-template <typename T>
+template <typename T, typename S = typename StorageOf<T>::type>
 __global__ void interp_kernel(int64_t m, GridArgs g, const int32_t *__restrict__ elem,
-                              const T *__restrict__ xi, const vec4<T> *__restrict__ U,
-                              T *__restrict__ u)
+                              const S *__restrict__ xi, const vec4<S> *__restrict__ U,
+                              S *__restrict__ u)
 {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
          b += (int64_t)gridDim.x * blockDim.x)
-        interp_point(g, b, elem, xi, U, u);
+        interp_point<T>(g, b, elem, xi, U, u);
 }
 
 // Spreading, pass 1: one warp per segment of 32 consecutive cells (see
 // spread_cells_segment).
+// T is the compute type (double, float or double-float); xi, lam, w and F are
+// in its storage type, the corner sums S in T.
 template <typename T>
-__global__ void spread_cells_kernel(int64_t E, const T *__restrict__ xi,
+__global__ void spread_cells_kernel(int64_t E, const typename StorageOf<T>::type *__restrict__ xi,
                                     const int32_t *__restrict__ start,
-                                    const int32_t *__restrict__ perm, const T *__restrict__ lam,
-                                    const T *__restrict__ w, T *__restrict__ S)
+                                    const int32_t *__restrict__ perm,
+                                    const typename StorageOf<T>::type *__restrict__ lam,
+                                    const typename StorageOf<T>::type *__restrict__ w,
+                                    T *__restrict__ S)
 {
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c0 = warp * 32; c0 < E; c0 += nwarps * 32)
-        spread_cells_segment(E, c0, xi, start, perm, lam, w, S);
+        spread_cells_segment<T>(E, c0, xi, start, perm, lam, w, S);
 }
 
 // Spreading, pass 2: every node sums the corner sums of its occupied cells.
 template <typename T>
 __global__ void spread_nodes_kernel(GridArgs g, const int32_t *__restrict__ start,
-                                    const T *__restrict__ S, T *__restrict__ F, int accumulate)
+                                    const T *__restrict__ S,
+                                    typename StorageOf<T>::type *__restrict__ F, int accumulate)
 {
     const int n = (g.Nx + 1) * (g.Ny + 1) * (g.Nz + 1);
     for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < n;
          node += gridDim.x * blockDim.x)
-        spread_node(g, node, start, S, F, accumulate);
+        spread_node<T>(g, node, start, S, F, accumulate);
 }
 
 // ---------------------------------------------------------------- no-allocation locate
@@ -392,13 +401,17 @@ fsi_status fsi_dlm_interp(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
 {
     FSI_TRY(validate_mesh(mesh));
     if (m < 0 || m >= INT32_MAX) return set_error(FSI_ERR_ARG, "fsi_dlm_interp: m out of range");
-    if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
+    if (prec != FSI_F64 && prec != FSI_F32 && prec != FSI_DF64)
+        return set_error(FSI_ERR_ARG, "bad precision");
     if (m == 0) return FSI_OK;
     if (!elem || !xi || !U || !u) return set_error(FSI_ERR_ARG, "fsi_dlm_interp: NULL argument");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
     GridArgs g = grid_args(mesh);
     if (prec == FSI_F64)
         interp_kernel<double><<<blocks_for(m, 256), 256, 0, mesh->stream>>>(
+            m, g, elem, (const double *)xi, (const vec4<double> *)U, (double *)u);
+    else if (prec == FSI_DF64)
+        interp_kernel<df64><<<blocks_for(m, 256), 256, 0, mesh->stream>>>(
             m, g, elem, (const double *)xi, (const vec4<double> *)U, (double *)u);
     else
         interp_kernel<float><<<blocks_for(m, 256), 256, 0, mesh->stream>>>(
@@ -413,13 +426,15 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
     (void)elem;
     FSI_TRY(validate_mesh(mesh));
     if (m < 0 || m >= INT32_MAX) return set_error(FSI_ERR_ARG, "fsi_dlm_spread: m out of range");
-    if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
+    if (prec != FSI_F64 && prec != FSI_F32 && prec != FSI_DF64)
+        return set_error(FSI_ERR_ARG, "bad precision");
     if (!F || !cell_start) return set_error(FSI_ERR_ARG, "fsi_dlm_spread: NULL F or cell_start");
     if (m > 0 && (!xi || !perm || !lam))
         return set_error(FSI_ERR_ARG, "fsi_dlm_spread: NULL xi, perm or lam");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
     GridArgs g = grid_args(mesh);
-    const size_t esz = prec == FSI_F64 ? sizeof(double) : sizeof(float);
+    // corner sums: 8 bytes per value for FP64 and double-float, 4 for FP32
+    const size_t esz = prec == FSI_F32 ? sizeof(float) : sizeof(double);
     FSI_TRY(ensure_spread_scratch(mesh, (size_t)mesh->n_elems * 24 * esz));
     const int64_t E = mesh->n_elems;
     const int cgrid = blocks_for((E + 31) / 32 * 32, 256, 152 * 64);
@@ -431,6 +446,13 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
         FSI_TRY(check_launch("spread cells kernel"));
         spread_nodes_kernel<double><<<ngrid, 256, 0, mesh->stream>>>(
             g, cell_start, (const double *)mesh->spread_scratch, (double *)F, accumulate);
+    } else if (prec == FSI_DF64) {
+        spread_cells_kernel<df64><<<cgrid, 256, 0, mesh->stream>>>(
+            E, (const double *)xi, cell_start, perm, (const double *)lam, (const double *)w,
+            (df64 *)mesh->spread_scratch);
+        FSI_TRY(check_launch("spread cells kernel"));
+        spread_nodes_kernel<df64><<<ngrid, 256, 0, mesh->stream>>>(
+            g, cell_start, (const df64 *)mesh->spread_scratch, (double *)F, accumulate);
     } else {
         spread_cells_kernel<float><<<cgrid, 256, 0, mesh->stream>>>(
             E, (const float *)xi, cell_start, perm, (const float *)lam, (const float *)w,

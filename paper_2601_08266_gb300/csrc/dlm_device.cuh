@@ -3,6 +3,7 @@
 // kernels (batch.cu).  See dlm.cu for the design.
 #pragma once
 
+#include "df64.cuh"
 #include "fsi_internal.cuh"
 
 namespace fsi {
@@ -18,12 +19,14 @@ template <typename T> __device__ __forceinline__ T shape_1d(T xi, int side)
     return side ? (T(1) + xi) : (T(1) - xi);
 }
 
-// Interpolation for one point b (u = C^T V, Eq. nodal_solid_velo).
+// Interpolation for one point b (u = C^T V, Eq. nodal_solid_velo).  T is the
+// compute type; xi, U and u are in StorageOf<T>.
 template <typename T>
-__device__ __forceinline__ void interp_point(const GridArgs &g, int64_t b,
-                                             const int32_t *__restrict__ elem,
-                                             const T *__restrict__ xi,
-                                             const vec4<T> *__restrict__ U, T *__restrict__ u)
+__device__ __forceinline__ void interp_point(
+    const GridArgs &g, int64_t b, const int32_t *__restrict__ elem,
+    const typename StorageOf<T>::type *__restrict__ xi,
+    const vec4<typename StorageOf<T>::type> *__restrict__ U,
+    typename StorageOf<T>::type *__restrict__ u)
 {
     const int NX1 = g.Nx + 1, NXY1 = (g.Nx + 1) * (g.Ny + 1);
     const int E = g.Nx * g.Ny * g.Nz;
@@ -31,21 +34,22 @@ __device__ __forceinline__ void interp_point(const GridArgs &g, int64_t b,
     T ux = T(0), uy = T(0), uz = T(0);
     if (e >= 0 && e < E) {
         const int ex = e % g.Nx, ey = (e / g.Nx) % g.Ny, ez = e / (g.Nx * g.Ny);
-        const T x0 = xi[3 * b], x1 = xi[3 * b + 1], x2 = xi[3 * b + 2];
+        const T x0 = to_c<T>(xi[3 * b]), x1 = to_c<T>(xi[3 * b + 1]),
+                x2 = to_c<T>(xi[3 * b + 2]);
         const int n0 = ex + NX1 * ey + NXY1 * ez;
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
             const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
-            const T Na = shape_1d(x0, ax) * shape_1d(x1, ay) * shape_1d(x2, az) * T(0.125);
-            const vec4<T> v = ld4(U + n0 + ax + NX1 * ay + NXY1 * az);
-            ux += Na * v.x;
-            uy += Na * v.y;
-            uz += Na * v.z;
+            const T Na = shape_1d(x0, ax) * shape_1d(x1, ay) * shape_1d(x2, az) * T(0.125f);
+            const auto v = ld4(U + n0 + ax + NX1 * ay + NXY1 * az);
+            ux += Na * to_c<T>(v.x);
+            uy += Na * to_c<T>(v.y);
+            uz += Na * to_c<T>(v.z);
         }
     }
-    u[3 * b] = ux;
-    u[3 * b + 1] = uy;
-    u[3 * b + 2] = uz;
+    u[3 * b] = to_s(ux);
+    u[3 * b + 1] = to_s(uy);
+    u[3 * b + 2] = to_s(uz);
 }
 
 // Spreading, pass 1: one warp per segment of 32 consecutive cells.  For each
@@ -54,13 +58,13 @@ __device__ __forceinline__ void interp_point(const GridArgs &g, int64_t b,
 // reduction (fixed lane order, so deterministic) gives the cell's corner sums
 // S[cell][8][3].
 // (called by all 32 lanes of a warp for the segment of cells [c0, c0+32))
+// T is the compute type; inputs are in StorageOf<T> (FP64 for double-float).
 template <typename T>
-__device__ __forceinline__ void spread_cells_segment(int64_t E, int64_t c0,
-                                                     const T *__restrict__ xi,
-                                                     const int32_t *__restrict__ start,
-                                                     const int32_t *__restrict__ perm,
-                                                     const T *__restrict__ lam,
-                                                     const T *__restrict__ w, T *__restrict__ S)
+__device__ __forceinline__ void spread_cells_segment(
+    int64_t E, int64_t c0, const typename StorageOf<T>::type *__restrict__ xi,
+    const int32_t *__restrict__ start, const int32_t *__restrict__ perm,
+    const typename StorageOf<T>::type *__restrict__ lam,
+    const typename StorageOf<T>::type *__restrict__ w, T *__restrict__ S)
 {
     const int lane = threadIdx.x & 31;
     {
@@ -81,9 +85,11 @@ __device__ __forceinline__ void spread_cells_segment(int64_t E, int64_t c0,
             for (int k = 0; k < 24; ++k) acc[k] = T(0);
             for (int p = plo + lane; p < phi; p += 32) {
                 const int b = perm[p];
-                const T x0 = xi[3 * b], x1 = xi[3 * b + 1], x2 = xi[3 * b + 2];
-                const T s = w ? w[b] * T(0.125) : T(0.125);
-                const T l0 = lam[3 * b], l1 = lam[3 * b + 1], l2 = lam[3 * b + 2];
+                const T x0 = to_c<T>(xi[3 * b]), x1 = to_c<T>(xi[3 * b + 1]),
+                        x2 = to_c<T>(xi[3 * b + 2]);
+                const T s = w ? to_c<T>(w[b]) * T(0.125f) : T(0.125f);
+                const T l0 = to_c<T>(lam[3 * b]), l1 = to_c<T>(lam[3 * b + 1]),
+                        l2 = to_c<T>(lam[3 * b + 2]);
 #pragma unroll
                 for (int a = 0; a < 8; ++a) {
                     const T Na = shape_1d(x0, a & 1) * shape_1d(x1, (a >> 1) & 1) *
@@ -101,24 +107,24 @@ __device__ __forceinline__ void spread_cells_segment(int64_t E, int64_t c0,
             for (int k = 0; k < 12; ++k) {
                 const T send = b4 ? acc[k] : acc[12 + k];
                 const T keep = b4 ? acc[12 + k] : acc[k];
-                acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                acc[k] = keep + shfl_x(send, 16);
             }
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 const T send = b3 ? acc[k] : acc[6 + k];
                 const T keep = b3 ? acc[6 + k] : acc[k];
-                acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                acc[k] = keep + shfl_x(send, 8);
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const T send = b2 ? acc[k] : acc[3 + k];
                 const T keep = b2 ? acc[3 + k] : acc[k];
-                acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                acc[k] = keep + shfl_x(send, 4);
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 2);
-                acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 1);
+                acc[k] = acc[k] + shfl_x(acc[k], 2);
+                acc[k] = acc[k] + shfl_x(acc[k], 1);
             }
             if ((lane & 3) == 0) {
                 const int idx0 = (b4 ? 12 : 0) + (b3 ? 6 : 0) + (b2 ? 3 : 0);
@@ -136,7 +142,8 @@ __device__ __forceinline__ void spread_cells_segment(int64_t E, int64_t c0,
 template <typename T>
 __device__ __forceinline__ void spread_node(const GridArgs &g, int node,
                                             const int32_t *__restrict__ start,
-                                            const T *__restrict__ S, T *__restrict__ F,
+                                            const T *__restrict__ S,
+                                            typename StorageOf<T>::type *__restrict__ F,
                                             int accumulate)
 {
     const int NX1 = g.Nx + 1, NY1 = g.Ny + 1;
@@ -153,22 +160,22 @@ __device__ __forceinline__ void spread_node(const GridArgs &g, int node,
             const int cell = ex + g.Nx * (ey + g.Ny * ez);
             if (start[cell + 1] == start[cell]) continue;
             const T *sc = S + (size_t)cell * 24 + 3 * c;
-            fx += sc[0];
-            fy += sc[1];
-            fz += sc[2];
+            fx = fx + sc[0];
+            fy = fy + sc[1];
+            fz = fz + sc[2];
             touched = true;
         }
-        T *o = F + 4 * (size_t)node;
+        auto *o = F + 4 * (size_t)node;
         if (accumulate) {
             if (touched) {
-                o[0] += fx;
-                o[1] += fy;
-                o[2] += fz;
+                o[0] = to_s(to_c<T>(o[0]) + fx);
+                o[1] = to_s(to_c<T>(o[1]) + fy);
+                o[2] = to_s(to_c<T>(o[2]) + fz);
             }
         } else {
-            o[0] = fx;
-            o[1] = fy;
-            o[2] = fz;
+            o[0] = to_s(fx);
+            o[1] = to_s(fy);
+            o[2] = to_s(fz);
         }
     }
 }

@@ -328,22 +328,6 @@ __global__ void dots3_kernel(int64_t n, const double *x, const double *y, const 
     if (threadIdx.x < 6) partial[6 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
 }
 
-__global__ void norm_partial_kernel(int64_t n, const double *x, double *partial)
-{
-    __shared__ double red[256];
-    double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        acc += x[i] * x[i];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
-}
-
 int blocks(int64_t n, int threads = 256, int cap = 152 * 16)
 {
     int64_t b = (n + threads - 1) / threads;

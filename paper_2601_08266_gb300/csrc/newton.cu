@@ -11,6 +11,7 @@
 #include <cstring>
 #include <vector>
 
+#include "df64.cuh"
 #include "fsi_internal.cuh"
 
 namespace fsi {
@@ -110,26 +111,46 @@ __global__ void dirichlet_rows_kernel(int64_t n4, const uint8_t *mask, const T *
 
 // ------------------------------------------------------------ reductions
 // partial[k][block] = sum over the block's grid-stride range of V_k . w, for
-// k in [k0, k0+cnt), FP64 accumulation; fixed grid and block size.
+// k in [k0, k0+cnt); fixed grid and block size (deterministic).  FP64 vectors
+// accumulate in FP64.  FP32 vectors accumulate FP64-grade on the FP32 pipe:
+// each product is exact as the pair (p, e) of an FMA-based TwoProd and is
+// added into a double-float accumulator (GB300's FP64 unit is ~70x slower).
+__device__ __forceinline__ void dot_acc(double &acc, double v, double w) { acc += v * w; }
+__device__ __forceinline__ void dot_acc(df64 &acc, float v, float w)
+{
+    const float p = __fmul_rn(v, w);
+    const float e = __fmaf_rn(v, w, -p);
+    acc = acc + df64(p, e);
+}
+__device__ __forceinline__ double dot_value(double a) { return a; }
+__device__ __forceinline__ double dot_value(df64 a) { return a.to_double(); }
+template <typename T> struct DotAcc {
+    using type = double;
+};
+template <> struct DotAcc<float> {
+    using type = df64;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) multi_dot_partial_kernel(
     int k0, int cnt, int64_t len, const T *V, int64_t ld, const T *w, double *partial)
 {
+    using Acc = typename DotAcc<T>::type;
     __shared__ double red[kDotGroup][kRedThreads / 32];
-    double acc[kDotGroup];
+    Acc acc[kDotGroup];
 #pragma unroll
-    for (int j = 0; j < kDotGroup; ++j) acc[j] = 0.0;
+    for (int j = 0; j < kDotGroup; ++j) acc[j] = Acc(0);
     GRID_STRIDE(i, len)
     {
-        const double wi = (double)w[i];
+        const T wi = w[i];
 #pragma unroll
         for (int j = 0; j < kDotGroup; ++j)
-            if (j < cnt) acc[j] += (double)V[(int64_t)(k0 + j) * ld + i] * wi;
+            if (j < cnt) dot_acc(acc[j], V[(int64_t)(k0 + j) * ld + i], wi);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int j = 0; j < kDotGroup; ++j) {
-        double v = acc[j];
+        double v = dot_value(acc[j]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[j][wid] = v;
@@ -164,16 +185,31 @@ __global__ void multi_dot_final_kernel(int cnt, const double *partial, double *o
     (void)cnt;
 }
 
-// w_i -= sum_k V_k[i] h[k], k < cnt (FP64 accumulation)
-template <typename T>
-__global__ void multi_axpy_kernel(int cnt, int64_t len, const T *V, int64_t ld, const double *h,
-                                  T *w)
+// w_i -= sum_k V_k[i] h[k], k < cnt: FP64 vectors in FP64; FP32 vectors
+// (the mixed mode's Krylov basis) with FP32 FMAs and h rounded to FP32.
+__global__ void multi_axpy_kernel(int cnt, int64_t len, const double *V, int64_t ld,
+                                  const double *h, double *w)
 {
     GRID_STRIDE(i, len)
     {
-        double acc = (double)w[i];
-        for (int k = 0; k < cnt; ++k) acc -= (double)V[(int64_t)k * ld + i] * h[k];
-        w[i] = (T)acc;
+        double acc = w[i];
+        for (int k = 0; k < cnt; ++k) acc -= V[(int64_t)k * ld + i] * h[k];
+        w[i] = acc;
+    }
+}
+
+constexpr int kMaxAxpy = 256;
+__global__ void multi_axpy_kernel(int cnt, int64_t len, const float *V, int64_t ld,
+                                  const double *h, float *w)
+{
+    __shared__ float hs[kMaxAxpy];
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) hs[k] = (float)h[k];
+    __syncthreads();
+    GRID_STRIDE(i, len)
+    {
+        float acc = w[i];
+        for (int k = 0; k < cnt; ++k) acc = __fmaf_rn(-V[(int64_t)k * ld + i], hs[k], acc);
+        w[i] = acc;
     }
 }
 
@@ -518,9 +554,9 @@ fsi_status gmres(fsi_mesh *mesh, const fsi_step_state *st, int restart, int max_
             FSI_TRY(coupled_jacobian_impl<T>(mesh, st, z, w));
             // classical Gram-Schmidt with one reorthogonalisation
             FSI_TRY(multi_dot<T>(mesh, j + 1, V, ld, w, W.hcol, 0));
-            multi_axpy_kernel<T><<<grid1d(len), 256, 0, s>>>(j + 1, len, V, ld, W.hcol, w);
+            multi_axpy_kernel<<<grid1d(len), 256, 0, s>>>(j + 1, len, V, ld, W.hcol, w);
             FSI_TRY(multi_dot<T>(mesh, j + 1, V, ld, w, W.h2, 0));
-            multi_axpy_kernel<T><<<grid1d(len), 256, 0, s>>>(j + 1, len, V, ld, W.h2, w);
+            multi_axpy_kernel<<<grid1d(len), 256, 0, s>>>(j + 1, len, V, ld, W.h2, w);
             add_kernel<double><<<1, 64, 0, s>>>(j + 1, W.h2, W.hcol);
             FSI_TRY(norm2<T>(mesh, w, W.hcol + j + 1));
             scale_by_inv_kernel<T><<<grid1d(len), 256, 0, s>>>(len, W.hcol + j + 1, w,
@@ -563,7 +599,7 @@ fsi_status gmres(fsi_mesh *mesh, const fsi_step_state *st, int restart, int max_
         FSI_CUDA(cudaMemcpyAsync(W.h2, W.hhost, jj * sizeof(double), cudaMemcpyHostToDevice, s),
                  "memcpy");
         zero_kernel<T><<<grid1d(len), 256, 0, s>>>(len, w);
-        multi_axpy_kernel<T><<<grid1d(len), 256, 0, s>>>(jj, len, V, ld, W.h2, w);  // w = V y
+        multi_axpy_kernel<<<grid1d(len), 256, 0, s>>>(jj, len, V, ld, W.h2, w);  // w = V y
         block_apply_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, w, z);
         add_kernel<T><<<grid1d(len), 256, 0, s>>>(len, z, x);
         FSI_TRY(check_launch("GMRES update"));

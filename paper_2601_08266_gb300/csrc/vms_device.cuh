@@ -23,20 +23,6 @@ template <typename T> __device__ __forceinline__ T cB2() { return T(kB2); }
 template <> __device__ __forceinline__ df64 cB1<df64>() { return df64(kB1h, kB1l); }
 template <> __device__ __forceinline__ df64 cB2<df64>() { return df64(kB2h, kB2l); }
 
-// Storage (I/O) type of a compute type: double-float computes on FP64 data.
-template <typename C> struct StorageOf {
-    using type = C;
-};
-template <> struct StorageOf<df64> {
-    using type = double;
-};
-
-template <typename C> __device__ __forceinline__ C to_c(typename StorageOf<C>::type v)
-{
-    return C(v);
-}
-template <> __device__ __forceinline__ df64 to_c<df64>(double v) { return df_split(v); }
-
 // node record of double-float values (two float4 loads)
 __device__ __forceinline__ vec4<df64> ld4_df(const vec4<df64> *p)
 {
@@ -49,11 +35,6 @@ template <> __device__ __forceinline__ vec4<df64> ld4_blk<df64>(const vec4<df64>
 {
     return ld4_df(p);
 }
-template <typename C> __device__ __forceinline__ typename StorageOf<C>::type to_s(C v)
-{
-    return v;
-}
-template <> __device__ __forceinline__ double to_s<df64>(df64 v) { return v.to_double(); }
 
 template <typename T> struct VmsArgs {
     using S = typename StorageOf<T>::type;

@@ -165,7 +165,7 @@ def test_vms_config2_full_size(fsi, oracle, prec):
 def dlm_run(fsi, mesh, X, prec, lam, w, U, F0, accumulate):
     import torch
     dt = dtype_of(prec)
-    P = fsi.FSI_F64 if prec == "f64" else fsi.FSI_F32
+    P = {"f64": fsi.FSI_F64, "f32": fsi.FSI_F32, "df64": fsi.FSI_DF64}[prec]
     m = X.shape[0]
     elem = torch.empty(m, dtype=torch.int32, device="cuda")
     xi = torch.empty((m, 3), dtype=torch.float64, device="cuda")
@@ -210,14 +210,14 @@ def dlm_check(fsi, oracle, N, X, prec, weighted, accumulate, seed=0, h=None, x0=
     return g
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64"])
 @pytest.mark.parametrize("weighted,accumulate", [(False, False), (True, True)])
 def test_dlm_config1_ball(fsi, oracle, prec, weighted, accumulate):
     X = inputs.ball_points(500, seed=2)
     dlm_check(fsi, oracle, 8, X, prec, weighted, accumulate)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64"])
 def test_dlm_edges_outside_and_boundaries(fsi, oracle, prec):
     X = inputs.edge_points((6, 5, 7), seed=4, m_random=3000)
     X = X * np.array([1.2, 0.5, 0.7])
@@ -242,6 +242,15 @@ def test_dlm_empty_and_all_outside(fsi, oracle):
         assert np.all(g["F"][:, :3] == 0)
 
 
+def test_dlm_medium_density_cells(fsi, oracle):
+    """33..128 points per cell (the register rank-sort path) and > 128."""
+    X = np.random.default_rng(5).uniform(size=(700, 3))
+    dlm_check(fsi, oracle, 2, X, "f64", True, False)
+    dlm_check(fsi, oracle, 2, X, "df64", True, True)
+    X = np.random.default_rng(6).uniform(size=(1500, 3))
+    dlm_check(fsi, oracle, 2, X, "f64", False, True)
+
+
 def test_dlm_dense_cell_and_strict(fsi, oracle):
     """Many points in one cell (the long-slice sort path) and strict mode."""
     import torch
@@ -258,7 +267,7 @@ def test_dlm_dense_cell_and_strict(fsi, oracle):
     assert ei.value.status == 4
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64"])
 def test_dlm_config2_leaflets_full_size(fsi, oracle, prec):
     """64^3 grid, 200k points on three thin leaflets (all inside)."""
     X = inputs.leaflet_points(200_000, seed=20)
