@@ -483,83 +483,138 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
     return 0
 
 # ------------------------------------------------------------------ Newton section
-def newton_section(args, dev, stream):
-    """One implicit step of a pulsatile channel with leaflets (N^3 grid, 200k
-    volume-weighted points): plain FP64 vs mixed vs mixed + learned predictor,
-    all to ||R|| <= 1e-8 r_ref with r_ref the residual of the extrapolated
-    predictor.  A network is trained on the run's first steps (GPU kernels)."""
-    import torch
-    import paper_2601_08266_gb300 as fsi
-    from paper_2601_08266_gb300 import inputs
-    N, dt, period = args.newton_grid, 0.01, 0.12
-    mesh = fsi.Mesh(N, rho=1.0, mu=0.01, dt=dt, rho_inf=0.5, device=dev.index,
-                    stream=stream.cuda_stream)
-    n = mesh.n_nodes
-    ax = np.arange(N + 1) / N
-    Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
-    X, Y, Z = X.ravel(), Y.ravel(), Z.ravel()
-    prof = 16.0 * Y * (1 - Y) * Z * (1 - Z)
-    wall = (Y < 1e-12) | (Y > 1 - 1e-12) | (Z < 1e-12) | (Z > 1 - 1e-12)
-    inflow = (X < 1e-12) & ~wall
-    mask = np.zeros((n, 4), dtype=np.uint8)
-    mask[wall | inflow, :3] = 1
-    gamma = 2.0 / 3.0
-    m = 200_000
-    with torch.cuda.stream(stream):
-        T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
-        Vn = torch.zeros((n, 4), dtype=torch.float64, device=dev)
-        An, yn, d1, d2 = (torch.zeros_like(Vn) for _ in range(4))
-        Xp = inputs.leaflet_points(m, seed=SEED + 40)
-        e = torch.empty(m, dtype=torch.int32, device=dev)
-        xi = torch.empty((m, 3), dtype=torch.float64, device=dev)
-        cs = torch.empty(mesh.n_elems + 1, dtype=torch.int32, device=dev)
-        pm = torch.empty(m, dtype=torch.int32, device=dev)
-        wpts = torch.full((m,), 0.024 / m, dtype=torch.float64, device=dev)
-        maskd = T(mask)
-        work = torch.empty((5, n, 4), dtype=torch.float64, device=dev)
-    fsi.fsi_locate(mesh, T(Xp), e, xi, cs, pm)
+class Channel:
+    """Channel-like flow on an N^3 unit-cube grid (Re ~ 1000: mu = 1e-3, peak
+    inflow 1): inflow v_x = 16 y(1-y) z(1-z) at x = 0, no-slip walls at y, z in
+    {0, 1}, traction-free outflow at x = 1; initial velocity = the inflow
+    profile plus 0.01 x a seeded smooth Fourier perturbation.  Three leaflets
+    of m volume-weighted points (total volume 0.024, rho_s - rho_f = 0.5)."""
 
-    def dirichlet(k):
+    def __init__(self, fsi, dev, stream, N, m, leaflet_seed, dt=1e-3, mu=1e-3):
+        import torch
+        from paper_2601_08266_gb300 import inputs
+        self.fsi, self.dev, self.stream, self.N, self.m, self.dt = fsi, dev, stream, N, m, dt
+        self.mesh = fsi.Mesh(N, rho=1.0, mu=mu, dt=dt, rho_inf=0.5, device=dev.index,
+                             stream=stream.cuda_stream)
+        n = self.n = self.mesh.n_nodes
+        ax = np.arange(N + 1) / N
+        Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+        X, Y, Z = X.ravel(), Y.ravel(), Z.ravel()
+        prof = 16.0 * Y * (1 - Y) * Z * (1 - Z)
+        wall = (Y < 1e-12) | (Y > 1 - 1e-12) | (Z < 1e-12) | (Z > 1 - 1e-12)
+        inflow = (X < 1e-12) & ~wall
+        mask = np.zeros((n, 4), dtype=np.uint8)
+        mask[wall | inflow, :3] = 1
+        V0 = np.zeros((n, 4))
+        V0[:, 0] = prof
+        V0[:, :3] += 0.01 * inputs.fourier_field(N, seed=SEED + 30, noise=0.0, ncomp=3)
+        V0[mask[:, 0].astype(bool), :3] = 0.0
+        V0[inflow, 0] = prof[inflow]
         g = np.zeros((n, 3))
-        g[inflow, 0] = prof[inflow] * np.sin(2 * np.pi * (k + 1) * dt / period)
+        g[inflow, 0] = prof[inflow]
+        self.gamma = 2.0 / 3.0
+        T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
         with torch.cuda.stream(stream):
-            yD = torch.zeros_like(Vn)
-            yD[:, :3] = (T(g) - Vn[:, :3] - dt * (1 - gamma) * An[:, :3]) / (gamma * dt)
+            self.Vn = T(V0)
+            self.An = torch.zeros_like(self.Vn)
+            self.yn, self.d1, self.d2 = (torch.zeros_like(self.Vn) for _ in range(3))
+            self.g = T(g)
+            self.mask = T(mask)
+            self.maskb = self.mask.bool()
+            self.e = torch.empty(m, dtype=torch.int32, device=dev)
+            self.xi = torch.empty((m, 3), dtype=torch.float64, device=dev)
+            self.cs = torch.empty(self.mesh.n_elems + 1, dtype=torch.int32, device=dev)
+            self.pm = torch.empty(m, dtype=torch.int32, device=dev)
+            self.w = torch.full((m,), 0.024 / m, dtype=torch.float64, device=dev)
+        fsi.fsi_locate(self.mesh, T(inputs.leaflet_points(m, seed=leaflet_seed)), self.e,
+                       self.xi, self.cs, self.pm)
+        self.k = 0
+
+    def dirichlet(self):
+        """y_D for the unknown V_dot_{n+1}: the velocity update reaches g."""
+        import torch
+        with torch.cuda.stream(self.stream):
+            yD = torch.zeros_like(self.Vn)
+            yD[:, :3] = (self.g - self.Vn[:, :3] - self.dt * (1 - self.gamma) * self.An[:, :3]) / (
+                self.gamma * self.dt)
         return yD
 
-    feats, targs = [], []
+    def state(self, guess="extrapolated"):
+        """Predictor y (extrapolated increment or zero increment) and its step state."""
+        import torch
+        yD = self.dirichlet()
+        with torch.cuda.stream(self.stream):
+            y = self.yn + 2 * self.d1 - self.d2 if guess == "extrapolated" else self.yn.clone()
+            y[self.maskb] = yD[self.maskb]
+        st = self.fsi.StepState(y, self.Vn, self.An, mask=self.mask, yD=yD, elem=self.e,
+                                xi=self.xi, cell_start=self.cs, perm=self.pm, w=self.w,
+                                drho_s=0.5)
+        return y, st
+
+    def advance(self, y):
+        """Accept y as the step's solution: increments and history move on."""
+        import torch
+        with torch.cuda.stream(self.stream):
+            dn = y - self.yn
+            self.d2, self.d1, self.yn = self.d1, dn, y.clone()
+        self.fsi.fsi_advance_history(self.mesh, self.fsi.FSI_F64, y, self.Vn, self.An)
+        self.k += 1
+
+    def close(self):
+        self.mesh.close()
+
+
+def newton_section(args, dev, stream):
+    """Implicit steps of the channel flow with leaflets (Re ~ 1000, dt = 1e-3).
+    A BF16 network is trained on the GPU on node samples from plain-solver runs
+    on 64^3 grids with seeded leaflet positions, then applied on the 128^3 grid
+    with 1M points.  One step there is solved to ||R|| <= 1e-8 r_ref (r_ref =
+    residual of the extrapolated predictor) by plain FP64 Newton-GMRES, by the
+    mixed FP32/FP64 solver from the zero and the extrapolated guess, and by the
+    mixed solver from the learned guess."""
+    import torch
+    import paper_2601_08266_gb300 as fsi
+    solve = dict(restart=50, max_newton=10, max_krylov=4000, newton_rtol=1e-8, krylov_rtol=1e-3)
     zeros = torch.zeros(112, dtype=torch.float32, device=dev)
     ones = torch.ones(112, dtype=torch.float32, device=dev)
-    warm = args.newton_warm
-    for k in range(warm):
-        yD = dirichlet(k)
-        with torch.cuda.stream(stream):
-            y = yn + 2 * d1 - d2
-            y[maskd.bool()] = yD[maskd.bool()]
-        st = fsi.StepState(y, Vn, An, mask=maskd, yD=yD, elem=e, xi=xi, cell_start=cs, perm=pm,
-                           w=wpts, drho_s=0.5)
-        if k >= 2:
-            Xf = torch.empty((n, 112), dtype=torch.float32, device=dev)
-            fsi.fsi_mlp_features(mesh, Vn, yn, d1, d2, None, zeros, ones, Xf)
-        fsi.fsi_newton_step(mesh, st, mixed=True, restart=50, max_newton=10, max_krylov=4000)
-        with torch.cuda.stream(stream):
-            dn = y - yn
+    gen = torch.Generator(device=dev).manual_seed(SEED)
+    # 1) training pairs from plain-solver runs on the training grid
+    t0 = time.perf_counter()
+    feats, targs = [], []
+    runs, steps = args.train_runs, args.train_steps
+    per_step = -(-args.train_samples // (runs * (steps - 2)))
+    for r in range(runs):
+        ch = Channel(fsi, dev, stream, args.train_grid, args.train_points, SEED + 40 + r)
+        for k in range(steps):
+            y, st = ch.state()
             if k >= 2:
-                feats.append(Xf)
-                targs.append(torch.where(maskd.bool(), torch.zeros_like(dn), dn - (2 * d1 - d2)))
-            d2, d1, yn = d1, dn, y.clone()
-        fsi.fsi_advance_history(mesh, fsi.FSI_F64, y, Vn, An)
-    # train the network on the GPU (BF16 tensor-core kernels)
+                with torch.cuda.stream(stream):
+                    idx = torch.randint(0, ch.n, (per_step,), device=dev, generator=gen,
+                                        dtype=torch.int64).to(torch.int32)
+                    Xf = torch.empty((per_step, 112), dtype=torch.float32, device=dev)
+                fsi.fsi_mlp_features(ch.mesh, ch.Vn, ch.yn, ch.d1, ch.d2, idx, zeros, ones, Xf)
+            fsi.fsi_newton_step(ch.mesh, st, mixed=True, **solve)
+            if k >= 2:
+                with torch.cuda.stream(stream):
+                    dn = (y - ch.yn)[idx.long()]
+                    tg = dn - (2 * ch.d1 - ch.d2)[idx.long()]
+                    tg[ch.maskb[idx.long()]] = 0.0
+                    feats.append(Xf)
+                    targs.append(tg)
+            ch.advance(y)
+        ch.close()
+    stream.synchronize()
+    gen_s = time.perf_counter() - t0
+    # 2) training on the GPU (BF16 tensor-core forward/backward, Adam)
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        Xa = torch.cat(feats)
-        Ca = torch.cat(targs).float()
+        Xa = torch.cat(feats)[:args.train_samples]
+        Ca = torch.cat(targs)[:args.train_samples].float()
         im, isd = Xa.mean(0), Xa.std(0) + 1e-6
         om, osd = Ca.mean(0), Ca.std(0) + 1e-12
         Xn = ((Xa - im) / isd).contiguous()
         Cn = ((Ca - om) / osd).contiguous()
-        P = torch.randn(fsi.fsi_mlp_num_params(), device=dev) * 0.0
-        gen = torch.Generator(device=dev).manual_seed(SEED)
+        P = torch.zeros(fsi.fsi_mlp_num_params(), device=dev)
         off = 0
         for fan_in, size in ((112, 112 * 256), (0, 256), (256, 256 * 256), (0, 256), (256, 1024),
                              (0, 4)):
@@ -581,43 +636,49 @@ def newton_section(args, dev, stream):
             losses.append(float(loss.item()))
     stream.synchronize()
     train_s = time.perf_counter() - t0
-    # the timed step: three variants from the same history
-    k = warm
-    yD = dirichlet(k)
-    out = {"grid": [N, N, N], "dofs": 4 * n, "points": m, "train_seconds": train_s,
-           "train_samples": int(Xn.shape[0]), "train_loss": losses}
-    variants = [("fp64", False, False), ("mixed", True, False), ("mixed_learned", True, True)]
+    # 3) the evaluation grid: warm steps, then one step four ways
+    ch = Channel(fsi, dev, stream, args.newton_grid, args.newton_points, SEED + 60)
+    for _ in range(args.newton_warm):
+        y, st = ch.state()
+        fsi.fsi_newton_step(ch.mesh, st, mixed=True, **solve)
+        ch.advance(y)
+    work = torch.empty((5, ch.n, 4), dtype=torch.float64, device=dev)
+    out = {"grid": [ch.N] * 3, "dofs": 4 * ch.n, "points": ch.m, "dt": ch.dt, "mu": 1e-3,
+           "history_steps": ch.k,
+           "training": {"grid": [args.train_grid] * 3, "points": args.train_points,
+                        "runs": runs, "steps_per_run": steps,
+                        "samples": int(Xn.shape[0]), "generate_seconds": gen_s,
+                        "train_seconds": train_s, "iters": args.mlp_iters, "loss": losses}}
+    variants = [("fp64", False, "extrapolated"), ("mixed_zero_guess", True, "zero"),
+                ("mixed", True, "extrapolated"), ("mixed_learned", True, "learned")]
     r_ref = None
-    for name, mixed, learned in variants:
-        with torch.cuda.stream(stream):
-            y = yn + 2 * d1 - d2
-            y[maskd.bool()] = yD[maskd.bool()]
-        st = fsi.StepState(y, Vn, An, mask=maskd, yD=yD, elem=e, xi=xi, cell_start=cs, perm=pm,
-                           w=wpts, drho_s=0.5)
+    for name, mixed, guess_kind in variants:
+        y, st = ch.state("zero" if guess_kind == "zero" else "extrapolated")
         stream.synchronize()
         t0 = time.perf_counter()
         guess = None
-        if learned:
-            guess = fsi.fsi_mlp_guess(h, mesh, P, (im).float().contiguous(),
+        if guess_kind == "learned":
+            guess = fsi.fsi_mlp_guess(h, ch.mesh, P, im.float().contiguous(),
                                       isd.float().contiguous(), om.contiguous(), osd.contiguous(),
-                                      st, yn, d1, d2, 1, work)
-        code, rep = fsi.fsi_newton_step(mesh, st, mixed=mixed, restart=50, max_newton=10,
-                                        max_krylov=4000, newton_rtol=1e-8, krylov_rtol=1e-3,
-                                        r_ref=r_ref or 0.0, check=False)
+                                      st, ch.yn, ch.d1, ch.d2, 1, work)
+        code, rep = fsi.fsi_newton_step(ch.mesh, st, mixed=mixed, r_ref=r_ref or 0.0,
+                                        check=False, **solve)
         stream.synchronize()
         el = time.perf_counter() - t0
         if r_ref is None:
             r_ref = rep["r_ref"]
         out[name] = {"seconds": el, "newton_iters": rep["newton_iters"],
-                     "krylov_iters": rep["krylov_iters"], "r_final_over_ref": rep["r_final"] / r_ref,
+                     "krylov_iters": rep["krylov_iters"], "r0_over_ref": rep["r0"] / r_ref,
+                     "r_final_over_ref": rep["r_final"] / r_ref,
                      "converged": bool(rep["converged"]), "status": code}
         if guess is not None:
             out[name]["predictor"] = {k2: guess[k2] for k2 in ("r_fallback", "r_learned",
                                                                "r_combined", "used")}
     out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
     out["speedup_mixed_learned_vs_fp64"] = out["fp64"]["seconds"] / out["mixed_learned"]["seconds"]
+    out["speedup_learned_vs_extrapolated"] = out["mixed"]["seconds"] / out["mixed_learned"]["seconds"]
     h.close()
-    mesh.close()
+    ch.close()
     return out
 
 
@@ -726,9 +787,15 @@ def main():
     ap.add_argument("--points", type=int, default=M_POINTS, help="solid points (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip Newton, batch and MLP sections")
-    ap.add_argument("--newton-grid", type=int, default=64)
-    ap.add_argument("--newton-warm", type=int, default=5)
-    ap.add_argument("--mlp-iters", type=int, default=300)
+    ap.add_argument("--newton-grid", type=int, default=128)
+    ap.add_argument("--newton-points", type=int, default=1_000_000)
+    ap.add_argument("--newton-warm", type=int, default=3)
+    ap.add_argument("--train-grid", type=int, default=64)
+    ap.add_argument("--train-points", type=int, default=200_000)
+    ap.add_argument("--train-runs", type=int, default=2)
+    ap.add_argument("--train-steps", type=int, default=6)
+    ap.add_argument("--train-samples", type=int, default=50_000)
+    ap.add_argument("--mlp-iters", type=int, default=600)
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--batch-tune-f64", action="store_true")
