@@ -53,6 +53,10 @@ FLOPS_PER_ELEM = {"jacobian": 4808.0, "residual": 3008.0}
 # FP32 pipe instructions (FADD + FMUL + FFMA) per element of the double-float
 # kernels, from ncu's executed-instruction-mix counters (128^3 capture).
 FP32_INSTR_PER_ELEM_DF64 = {"jacobian": 40160.0, "residual": 25012.0}
+# dram__bytes_read.sum + dram__bytes_write.sum of one double-float Jacobian apply
+# at 64^3 (brick kernel 26,477,056 B + gather kernel 13,289,216 B; the writes
+# stay in L2 within the launch)
+TRAFFIC_JAC_DF64_64 = 39_766_272
 
 
 def dist_env():
@@ -396,12 +400,9 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
     jac_ms = per64[ops.index("jacobian")]
     achieved = FP32_INSTR_PER_ELEM_DF64["jacobian"] * E / (jac_ms * 1e-3)
     peak_instr = fma32 / 2.0  # the probe counts an FMA instruction as 2 flops
-    traffic = None
-    try:
-        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        traffic = tr.get("vms_jacobian_df64_64cubed_bytes_per_launch")
-    except (OSError, ValueError):
-        pass
+    # DRAM bytes of one launch (brick + gather kernels), from an ncu capture of
+    # this workload; only meaningful for the 64^3 grid it was taken on
+    traffic = TRAFFIC_JAC_DF64_64 if N == N_GRID else None
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
 

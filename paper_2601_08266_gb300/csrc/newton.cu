@@ -17,7 +17,7 @@
 namespace fsi {
 namespace {
 
-constexpr int kRedGrid = 304;   // fixed partial-sum grid: deterministic dots
+constexpr int kRedGrid = 608;   // fixed partial-sum grid (4 CTAs per SM): deterministic dots
 constexpr int kRedThreads = 256;
 constexpr int kDotGroup = 8;    // vectors per multi-dot pass
 
@@ -26,6 +26,9 @@ int grid1d(int64_t n, int threads = 256, int cap = 152 * 16)
     int64_t b = (n + threads - 1) / threads;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
+
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 #define GRID_STRIDE(i, n)                                                                  \
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n);              \
@@ -133,19 +136,28 @@ template <> struct DotAcc<float> {
 
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) multi_dot_partial_kernel(
-    int k0, int cnt, int64_t len, const T *V, int64_t ld, const T *w, double *partial)
+    int k0, int cnt, int64_t len4, const vec4<T> *V, int64_t vstride, const vec4<T> *w,
+    double *partial)
 {
     using Acc = typename DotAcc<T>::type;
     __shared__ double red[kDotGroup][kRedThreads / 32];
     Acc acc[kDotGroup];
 #pragma unroll
     for (int j = 0; j < kDotGroup; ++j) acc[j] = Acc(0);
-    GRID_STRIDE(i, len)
+    // one 4-value record per thread and step: the loads of all cnt vectors are
+    // independent, so each thread keeps up to 9 vector loads in flight
+    GRID_STRIDE(i, len4)
     {
-        const T wi = w[i];
+        const vec4<T> wi = ld4(w + i);
 #pragma unroll
         for (int j = 0; j < kDotGroup; ++j)
-            if (j < cnt) dot_acc(acc[j], V[(int64_t)(k0 + j) * ld + i], wi);
+            if (j < cnt) {
+                const vec4<T> v = ld4(V + (int64_t)(k0 + j) * vstride + i);
+                dot_acc(acc[j], v.x, wi.x);
+                dot_acc(acc[j], v.y, wi.y);
+                dot_acc(acc[j], v.z, wi.z);
+                dot_acc(acc[j], v.w, wi.w);
+            }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -186,29 +198,42 @@ __global__ void multi_dot_final_kernel(int cnt, const double *partial, double *o
 }
 
 // w_i -= sum_k V_k[i] h[k], k < cnt: FP64 vectors in FP64; FP32 vectors
-// (the mixed mode's Krylov basis) with FP32 FMAs and h rounded to FP32.
-__global__ void multi_axpy_kernel(int cnt, int64_t len, const double *V, int64_t ld,
-                                  const double *h, double *w)
-{
-    GRID_STRIDE(i, len)
-    {
-        double acc = w[i];
-        for (int k = 0; k < cnt; ++k) acc -= V[(int64_t)k * ld + i] * h[k];
-        w[i] = acc;
-    }
-}
-
+// (the mixed mode's Krylov basis) with FP32 FMAs and h rounded to FP32.  One
+// 4-value record per thread and step, four basis vectors loaded ahead of their
+// FMAs (the FMA order per entry is k = 0, 1, 2, ...).
 constexpr int kMaxAxpy = 256;
-__global__ void multi_axpy_kernel(int cnt, int64_t len, const float *V, int64_t ld,
-                                  const double *h, float *w)
+template <typename T>
+__global__ void multi_axpy_kernel(int cnt, int64_t len4, const vec4<T> *V, int64_t vstride,
+                                  const double *h, vec4<T> *w)
 {
-    __shared__ float hs[kMaxAxpy];
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) hs[k] = (float)h[k];
+    __shared__ T hs[kMaxAxpy];
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) hs[k] = (T)h[k];
     __syncthreads();
-    GRID_STRIDE(i, len)
+    GRID_STRIDE(i, len4)
     {
-        float acc = w[i];
-        for (int k = 0; k < cnt; ++k) acc = __fmaf_rn(-V[(int64_t)k * ld + i], hs[k], acc);
+        vec4<T> acc = w[i];
+        int k = 0;
+        for (; k + 4 <= cnt; k += 4) {
+            vec4<T> v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = ld4(V + (int64_t)(k + q) * vstride + i);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const T hk = hs[k + q];
+                acc.x = fma_rn(-v[q].x, hk, acc.x);
+                acc.y = fma_rn(-v[q].y, hk, acc.y);
+                acc.z = fma_rn(-v[q].z, hk, acc.z);
+                acc.w = fma_rn(-v[q].w, hk, acc.w);
+            }
+        }
+        for (; k < cnt; ++k) {
+            const vec4<T> v = ld4(V + (int64_t)k * vstride + i);
+            const T hk = hs[k];
+            acc.x = fma_rn(-v.x, hk, acc.x);
+            acc.y = fma_rn(-v.y, hk, acc.y);
+            acc.z = fma_rn(-v.z, hk, acc.z);
+            acc.w = fma_rn(-v.w, hk, acc.w);
+        }
         w[i] = acc;
     }
 }
@@ -491,12 +516,21 @@ fsi_status multi_dot(fsi_mesh *mesh, int cnt, const T *V, int64_t ld, const T *w
     const int64_t len = 4 * mesh->n_nodes;
     for (int k0 = 0; k0 < cnt; k0 += kDotGroup) {
         const int c = cnt - k0 < kDotGroup ? cnt - k0 : kDotGroup;
-        multi_dot_partial_kernel<T><<<kRedGrid, kRedThreads, 0, s>>>(k0, c, len, V, ld, w,
-                                                                    W.partial);
+        multi_dot_partial_kernel<T><<<kRedGrid, kRedThreads, 0, s>>>(
+            k0, c, len / 4, (const vec4<T> *)V, ld / 4, (const vec4<T> *)w, W.partial);
     }
     FSI_TRY(check_launch("multi-dot partial"));
     multi_dot_final_kernel<<<cnt, kRedThreads, 0, s>>>(cnt, W.partial, out, mode);
     return check_launch("multi-dot final");
+}
+
+// w -= V[:, :cnt] h (vectors of len = 4n entries, 16/32-byte aligned records)
+template <typename T>
+void multi_axpy(cudaStream_t s, int cnt, int64_t len, const T *V, int64_t ld, const double *h,
+                T *w)
+{
+    multi_axpy_kernel<T><<<grid1d(len / 4), 256, 0, s>>>(cnt, len / 4, (const vec4<T> *)V,
+                                                         ld / 4, h, (vec4<T> *)w);
 }
 
 template <typename T> fsi_status norm2(fsi_mesh *mesh, const T *x, double *dev_out)
@@ -554,9 +588,9 @@ fsi_status gmres(fsi_mesh *mesh, const fsi_step_state *st, int restart, int max_
             FSI_TRY(coupled_jacobian_impl<T>(mesh, st, z, w));
             // classical Gram-Schmidt with one reorthogonalisation
             FSI_TRY(multi_dot<T>(mesh, j + 1, V, ld, w, W.hcol, 0));
-            multi_axpy_kernel<<<grid1d(len), 256, 0, s>>>(j + 1, len, V, ld, W.hcol, w);
+            multi_axpy<T>(s, j + 1, len, V, ld, W.hcol, w);
             FSI_TRY(multi_dot<T>(mesh, j + 1, V, ld, w, W.h2, 0));
-            multi_axpy_kernel<<<grid1d(len), 256, 0, s>>>(j + 1, len, V, ld, W.h2, w);
+            multi_axpy<T>(s, j + 1, len, V, ld, W.h2, w);
             add_kernel<double><<<1, 64, 0, s>>>(j + 1, W.h2, W.hcol);
             FSI_TRY(norm2<T>(mesh, w, W.hcol + j + 1));
             scale_by_inv_kernel<T><<<grid1d(len), 256, 0, s>>>(len, W.hcol + j + 1, w,
@@ -599,7 +633,7 @@ fsi_status gmres(fsi_mesh *mesh, const fsi_step_state *st, int restart, int max_
         FSI_CUDA(cudaMemcpyAsync(W.h2, W.hhost, jj * sizeof(double), cudaMemcpyHostToDevice, s),
                  "memcpy");
         zero_kernel<T><<<grid1d(len), 256, 0, s>>>(len, w);
-        multi_axpy_kernel<<<grid1d(len), 256, 0, s>>>(jj, len, V, ld, W.h2, w);  // w = V y
+        multi_axpy<T>(s, jj, len, V, ld, W.h2, w);  // w = -V (-y)
         block_apply_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, w, z);
         add_kernel<T><<<grid1d(len), 256, 0, s>>>(len, z, x);
         FSI_TRY(check_launch("GMRES update"));
