@@ -21,8 +21,15 @@ with tau_M ~ dt / sqrt(C_T) has the same size.  The preconditioner is
     S_hat = sigma (K + kappa M),  kappa = (pi / (2 L))^2,
 
 L the largest extent of the grid; the kappa M term (M the Q1 mass matrix) keeps
-S_hat non-singular where only Neumann conditions bound the pressure.  S_hat^{-1}
-is replaced by one V-cycle (the definitions below), a fixed linear operator.
+S_hat non-singular where only Neumann conditions bound the pressure.  On a
+face of the box where the velocity is not prescribed (a traction-free outflow)
+the true Schur complement behaves like a Dirichlet problem for the pressure
+(its largest eigenvalues against sigma K live there and grow like 1/h), so the
+nodes of such faces are eliminated from S_hat: their rows and columns are
+dropped except the diagonal entry.  A face counts as such when more than half
+of its nodes have all three velocity components free (``faces_from_mask``).
+S_hat^{-1} is replaced by one V-cycle (the definitions below), a fixed linear
+operator.
 
 Definitions, all on a uniform grid with Q1 elements:
   K_e, M_e   element matrices int grad N_a . grad N_b and int N_a N_b, 2x2x2
@@ -37,7 +44,8 @@ Definitions, all on a uniform grid with Q1 elements:
              symbol to diagonal over the modes with theta_d in {0, pi};
   coarsest   a direct solve when it has at most 1000 nodes, otherwise a
              Chebyshev semi-iteration of degree 8 over [hi / 30, hi] from zero;
-  V-cycle    x = smooth(nu, from 0); r = b - A x; x += P V(R r); x = smooth(nu, from x).
+  V-cycle    x = smooth(nu, from 0); r = b - A x; x += P V(R r); x = smooth(nu, from x),
+             with the restricted right-hand side zeroed on eliminated nodes.
 
 Pins (tests/test_oracle_precond.py): K 1 = 0; u^T K u and u^T M u against the
 integrals for trilinear u; Galerkin property P^T A_l P = A_{l+1}; exact
@@ -64,6 +72,39 @@ class Level:
         self.N = tuple(int(v) for v in N)
         self.h = tuple(float(v) for v in h)
         self.n = (self.N[0] + 1) * (self.N[1] + 1) * (self.N[2] + 1)
+
+    def face_nodes(self, faces):
+        """Boolean [n]: nodes on the eliminated faces, faces = (x0, x1, y0, y1, z0, z1)."""
+        ijk = np.indices((self.N[2] + 1, self.N[1] + 1, self.N[0] + 1)).reshape(3, -1)
+        k, j, i = ijk
+        on = np.zeros(self.n, dtype=bool)
+        for d, idx in enumerate((i, j, k)):
+            if faces[2 * d]:
+                on |= idx == 0
+            if faces[2 * d + 1]:
+                on |= idx == self.N[d]
+        return on
+
+
+def faces_from_mask(N, mask):
+    """Faces (x0, x1, y0, y1, z0, z1) on which more than half of the nodes
+    inside the face (off its edges; all of its nodes if it has none inside)
+    have all three velocity components free (mask [n, 4] of the Dirichlet rows)."""
+    L = Level(N, (1.0, 1.0, 1.0))
+    free = ~np.asarray(mask, dtype=bool)[:, :3].any(axis=1)
+    k, j, i = np.indices((L.N[2] + 1, L.N[1] + 1, L.N[0] + 1)).reshape(3, -1)
+    idx = (i, j, k)
+    out = []
+    for d in range(3):
+        inner = np.ones(L.n, dtype=bool)
+        for e in range(3):
+            if e != d:
+                inner &= (idx[e] > 0) & (idx[e] < L.N[e])
+        for side in (0, L.N[d]):
+            on = idx[d] == side
+            sel = on & inner if np.any(on & inner) else on
+            out.append(int(2 * np.count_nonzero(free & sel) > np.count_nonzero(sel)))
+    return tuple(out)
 
 
 def _element_matrices(h):
@@ -101,8 +142,9 @@ def _connectivity(N):
     return np.array(conn, dtype=np.int64)
 
 
-def assemble(level: Level, kappa: float = 0.0):
-    """(K + kappa M), K and M of a level as CSR matrices."""
+def assemble(level: Level, kappa: float = 0.0, faces=(0,) * 6):
+    """(K + kappa M) with the nodes of `faces` eliminated (rows and columns
+    dropped, diagonal kept), K and M of a level as CSR matrices."""
     Ke, Me = _element_matrices(level.h)
     conn = _connectivity(level.N)
     rows = np.repeat(conn, 8, axis=1).ravel()
@@ -110,7 +152,12 @@ def assemble(level: Level, kappa: float = 0.0):
     E = conn.shape[0]
     K = sp.csr_matrix((np.tile(Ke.ravel(), E), (rows, cols)), shape=(level.n, level.n))
     M = sp.csr_matrix((np.tile(Me.ravel(), E), (rows, cols)), shape=(level.n, level.n))
-    return (K + kappa * M).tocsr(), K, M
+    A = (K + kappa * M).tocsr()
+    dirn = level.face_nodes(faces)
+    if dirn.any():
+        keep = sp.diags((~dirn).astype(float))
+        A = (keep @ A @ keep + sp.diags(np.where(dirn, A.diagonal(), 0.0))).tocsr()
+    return A, K, M
 
 
 def kappa_of(N, h):
@@ -190,12 +237,14 @@ def chebyshev(A, Dinv, b, x, degree, lo, hi):
 class MultigridOracle:
     """The V-cycle of the module docstring, with assembled matrices."""
 
-    def __init__(self, N, h=None):
+    def __init__(self, N, h=None, faces=(0,) * 6):
         N = (N, N, N) if np.isscalar(N) else tuple(N)
         h = tuple(1.0 / v for v in N) if h is None else tuple(h)
         self.kappa = kappa_of(N, h)
+        self.faces = tuple(int(bool(f)) for f in faces)
         self.levels = hierarchy(N, h)
-        self.A = [assemble(L, self.kappa)[0] for L in self.levels]
+        self.A = [assemble(L, self.kappa, self.faces)[0] for L in self.levels]
+        self.dirn = [L.face_nodes(self.faces) for L in self.levels]
         self.Dinv = [1.0 / A.diagonal() for A in self.A]
         self.hi = [spectrum_bound(L.h, self.kappa) for L in self.levels]
         self.P = [prolongation(self.levels[l], self.levels[l + 1])
@@ -220,7 +269,9 @@ class MultigridOracle:
             return self.coarse_solve(b)
         x = self.smooth(l, b, np.zeros_like(b))
         r = b - self.A[l] @ x
-        x = x + self.P[l] @ self.vcycle(self.P[l].T @ r, l + 1)
+        bc = self.P[l].T @ r
+        bc[self.dirn[l + 1]] = 0.0
+        x = x + self.P[l] @ self.vcycle(bc, l + 1)
         return self.smooth(l, b, x)
 
 

@@ -129,3 +129,80 @@ def test_sigma_is_the_generalized_alpha_chain_ratio():
     # rho_inf = 0.5: alpha_m = 5/6, alpha_f = gamma = 2/3 -> sigma = 0.5333 dt / rho
     assert pc.sigma_of(1.0, 1e-3) == pytest.approx(0.16 / 0.3 * 1e-3)
     assert pc.sigma_of(2.0, 1e-2) == pytest.approx(0.16 / 0.3 * 1e-2 / 2.0)
+
+
+def test_faces_from_mask_finds_the_free_faces():
+    N = (6, 5, 4)
+    L = pc.Level(N, (1.0, 1.0, 1.0))
+    k, j, i = np.indices((N[2] + 1, N[1] + 1, N[0] + 1)).reshape(3, -1)
+    mask = np.zeros((L.n, 4), dtype=bool)
+    walls = (j == 0) | (j == N[1]) | (k == 0) | (k == N[2])
+    mask[walls | (i == 0), :3] = True          # no-slip walls and an inflow at x = 0
+    assert pc.faces_from_mask(N, mask) == (0, 1, 0, 0, 0, 0)
+    assert pc.faces_from_mask(N, np.zeros((L.n, 4), bool)) == (1,) * 6
+    assert pc.faces_from_mask(N, np.ones((L.n, 4), bool)) == (0,) * 6
+
+
+def test_eliminated_faces_keep_galerkin_and_contraction():
+    faces = (0, 1, 0, 0, 1, 0)
+    mg = pc.MultigridOracle((16, 16, 16), faces=faces)
+    for l in range(len(mg.levels) - 1):
+        keep_f, keep_c = ~mg.dirn[l], ~mg.dirn[l + 1]
+        Pi = mg.P[l][keep_f][:, keep_c]
+        G = (Pi.T @ mg.A[l][keep_f][:, keep_f] @ Pi).toarray()
+        Ac = mg.A[l + 1][keep_c][:, keep_c].toarray()
+        assert np.abs(G - Ac).max() < 1e-12 * np.abs(Ac).max()
+        # the eliminated rows are decoupled diagonal rows
+        Ad = mg.A[l][mg.dirn[l]]
+        assert Ad.nnz == int(mg.dirn[l].sum())
+    A = mg.A[0]
+    b = np.random.default_rng(4).normal(size=A.shape[0])
+    xs = spla.spsolve(A.tocsc(), b)
+    x = np.zeros_like(b)
+    errs = []
+    for _ in range(4):
+        x = x + mg.vcycle(b - A @ x)
+        e = x - xs
+        errs.append(math.sqrt(e @ (A @ e)))
+    assert max(errs[i + 1] / errs[i] for i in range(3)) < 0.1
+
+
+@pytest.mark.parametrize("N", [6, 10])
+def test_schur_complement_is_spectrally_equivalent_to_the_approximation(N):
+    """The pressure Schur complement of the oracle's assembled Jacobian (a
+    channel with leaflets, dt = 1e-3) against sigma (K + kappa M) with the
+    free outflow face eliminated: eigenvalue ratios stay in a fixed band as h
+    shrinks (without the elimination the largest grows like 1/h)."""
+    from oracle import core, newton
+    from paper_2601_08266_gb300 import inputs
+    grid = core.Grid(N)
+    n = grid.n_nodes
+    X, Y, Z = grid.node_coords().T
+    wall = (Y < 1e-12) | (Y > 1 - 1e-12) | (Z < 1e-12) | (Z > 1 - 1e-12)
+    inflow = (X < 1e-12) & ~wall
+    mask = np.zeros((n, 4), bool)
+    mask[wall | inflow, :3] = True
+    rng = np.random.default_rng(2)
+    Vn = np.zeros((n, 4))
+    Vn[:, 0] = 16 * Y * (1 - Y) * Z * (1 - Z)
+    Vn[:, :3] += 0.05 * rng.normal(size=(n, 3))
+    Vn[mask] = 0.0
+    m = 800
+    e, xi, _ = core.locate(grid, inputs.leaflet_points(m, seed=5))
+    dt = 1e-3
+    P = newton.Problem(grid, dict(rho=1.0, mu=1e-3, dt=dt, rho_inf=0.5), Vn, np.zeros((n, 4)),
+                       mask=mask, yD=np.zeros((n, 4)), points=(e, xi, np.full(m, 0.024 / m)),
+                       solid=dict(drho=0.5, k=0.0, g=(0, 0, 0)))
+    J = P.jacobian(np.zeros((n, 4))).toarray()
+    vel = np.arange(4 * n) % 4 < 3
+    S = J[np.ix_(~vel, ~vel)] - J[np.ix_(~vel, vel)] @ np.linalg.solve(
+        J[np.ix_(vel, vel)], J[np.ix_(vel, ~vel)])
+    faces = pc.faces_from_mask((N,) * 3, mask)
+    assert faces == (0, 1, 0, 0, 0, 0)
+    sig = pc.sigma_of(1.0, dt)
+    kap = pc.kappa_of((N,) * 3, (1.0 / N,) * 3)
+    lev = pc.Level((N,) * 3, (1.0 / N,) * 3)
+    ev = sla.eigvals(S, sig * pc.assemble(lev, kap, faces)[0].toarray()).real
+    assert ev.min() > 0.4 and ev.max() < 2.0, (ev.min(), ev.max())
+    ev0 = sla.eigvals(S, sig * pc.assemble(lev, kap)[0].toarray()).real
+    assert ev0.max() > 3.0 * ev.max()          # the Neumann-only approximation is far off
