@@ -440,9 +440,13 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
     extras = {}
     if not args.no_extras:
         stream2 = torch.cuda.Stream(device=dev)
-        extras["newton"] = newton_section(args, dev, stream2)
-        extras["batch"] = batch_section(args, dev, stream2)
-        extras["mlp_inference"] = mlp_section(args, dev, stream2, W)
+        sections = args.sections.split(",")
+        if "newton" in sections:
+            extras["newton"] = newton_section(args, dev, stream2)
+        if "batch" in sections:
+            extras["batch"] = batch_section(args, dev, stream2)
+        if "mlp" in sections:
+            extras["mlp_inference"] = mlp_section(args, dev, stream2, W)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
@@ -650,10 +654,15 @@ def newton_section(args, dev, stream):
                         "runs": runs, "steps_per_run": steps,
                         "samples": int(Xn.shape[0]), "generate_seconds": gen_s,
                         "train_seconds": train_s, "iters": args.mlp_iters, "loss": losses}}
-    variants = [("fp64", False, "extrapolated"), ("mixed_zero_guess", True, "zero"),
-                ("mixed", True, "extrapolated"), ("mixed_learned", True, "learned")]
+    S, BJ = fsi.PRECOND_SCHUR, fsi.PRECOND_BLOCK_JACOBI
+    variants = [("fp64", False, "extrapolated", S), ("mixed_zero_guess", True, "zero", S),
+                ("mixed", True, "extrapolated", S), ("mixed_learned", True, "learned", S),
+                ("mixed_block_jacobi", True, "extrapolated", BJ)]
+    out["preconditioner"] = ("block-diagonal Schur complement: 3x3 velocity blocks + one "
+                             "pressure multigrid V-cycle (mixed_block_jacobi: nodal 4x4 "
+                             "block-Jacobi)")
     r_ref = None
-    for name, mixed, guess_kind in variants:
+    for name, mixed, guess_kind, pc in variants:
         y, st = ch.state("zero" if guess_kind == "zero" else "extrapolated")
         stream.synchronize()
         t0 = time.perf_counter()
@@ -663,7 +672,7 @@ def newton_section(args, dev, stream):
                                       isd.float().contiguous(), om.contiguous(), osd.contiguous(),
                                       st, ch.yn, ch.d1, ch.d2, 1, work)
         code, rep = fsi.fsi_newton_step(ch.mesh, st, mixed=mixed, r_ref=r_ref or 0.0,
-                                        check=False, **solve)
+                                        check=False, precond=pc, **solve)
         stream.synchronize()
         el = time.perf_counter() - t0
         if r_ref is None:
@@ -788,6 +797,8 @@ def main():
     ap.add_argument("--points", type=int, default=M_POINTS, help="solid points (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip Newton, batch and MLP sections")
+    ap.add_argument("--sections", default="newton,batch,mlp",
+                    help="comma-separated extra sections to run")
     ap.add_argument("--newton-grid", type=int, default=128)
     ap.add_argument("--newton-points", type=int, default=1_000_000)
     ap.add_argument("--newton-warm", type=int, default=3)

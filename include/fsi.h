@@ -267,7 +267,7 @@ fsi_status fsi_block_diagonal(fsi_mesh *mesh, fsi_prec prec, const fsi_step_stat
 /* Newton on the reduced system (Sec. 2.4) from st->y (the predictor; on
  * return the iterate that met the tolerance, or the last one).  Each
  * iteration: FP64 residual; right-preconditioned restarted GMRES on
- * J dy = -R with a nodal 4x4 block-Jacobi preconditioner; y += dy in FP64.
+ * J dy = -R (preconditioner per opts.precond); y += dy in FP64.
  *   mixed = 0: every step in FP64 (the plain method);
  *   mixed = 1: Krylov vectors, Jacobian applies and preconditioner in FP32;
  *              the residual, the Gram-Schmidt dot products and norms (FP64
@@ -287,9 +287,13 @@ typedef struct {
     double newton_rtol;    /* e.g. 1e-8                                        */
     double krylov_rtol;    /* inner relative tolerance, e.g. 1e-3              */
     double r_ref;          /* > 0: reference norm of the stopping test         */
-    int32_t precond_every; /* rebuild the block-Jacobi every k Newton iterations
-                              (0: build once per call, at y_0)                */
-    int32_t reserved;
+    int32_t precond_every; /* rebuild the preconditioner every k Newton
+                              iterations (0: build once per call, at y_0)     */
+    int32_t precond;       /* 0: nodal 4x4 block-Jacobi; 1: block-diagonal
+                              Schur-complement preconditioner (3x3 velocity
+                              blocks, pressure Schur complement approximated
+                              by sigma (K + kappa M) and inverted by one
+                              multigrid V-cycle; see fsi_pressure_vcycle)     */
 } fsi_newton_opts;
 
 typedef struct {
@@ -305,6 +309,57 @@ typedef struct {
 
 fsi_status fsi_newton_step(fsi_mesh *mesh, const fsi_newton_opts *opts, const fsi_step_state *st,
                            fsi_newton_report *report);
+
+/* ----------------------------------------------------------------------- */
+/* Pressure block of the Schur-complement preconditioner (opts.precond = 1;
+ * Sec. 2.4 solves the reduced system with block preconditioners built from
+ * its sub-matrices).  With the fluid blocks [[A, B], [C, D]] (A = dR^{f,m}/dVdot
+ * mass-dominated, B gradient, C = c_v x divergence + PSPG, D PSPG), the
+ * pressure Schur complement D - C A^{-1} B is approximated by sigma (K + kappa M):
+ * K, M the Q1 stiffness and mass matrices of the pressure space on the mesh
+ * grid, sigma = alpha_f gamma dt / (alpha_m rho), kappa = (pi / (2 L))^2 with L
+ * the largest grid extent.  Its inverse is replaced by one V-cycle over the
+ * levels: the mesh grid, then every other node while all N_d are even and the
+ * level has more than 125 nodes; trilinear prolongation P, restriction P^T;
+ * Chebyshev smoothing of degree 2 (pre and post) on D^{-1}(K + kappa M) over
+ * [hi/4, hi] (hi = 1.1 x the largest symbol-to-diagonal ratio of the modes
+ * theta_d in {0, pi}); a dense inverse on a coarsest level of <= 1000 nodes,
+ * else Chebyshev of degree 8 over [hi/30, hi].  The paper fixes none of these
+ * choices; the V-cycle is a fixed symmetric linear operator.
+ *
+ * On a face of the box where the velocity is free (a traction-free outflow)
+ * the true Schur complement acts like a Dirichlet problem for the pressure:
+ * the nodes of "eliminated" faces keep only their diagonal entry and drop
+ * out of every other row, on every level, and the restricted right-hand side
+ * is zeroed there.  fsi_newton_step picks the faces from its Dirichlet mask:
+ * a face is eliminated when more than half of the nodes inside it (off its
+ * edges; all its nodes if none is inside) have all three velocity
+ * components free.
+ *
+ * Vectors are scalar nodal fields [n_l] of the level (lexicographic, x
+ * fastest) in `prec` (FSI_F64 or FSI_F32), device pointers owned by the
+ * caller.  Level 0 is the mesh grid.  The hierarchy is built on first use
+ * and kept in the mesh.  Stream-ordered on the mesh stream.                */
+/* faces[6] (x0, x1, y0, y1, z0, z1), nonzero = eliminated; none by default.
+ * Synchronises the mesh stream when the set changes (the coarse inverse is
+ * rebuilt).                                                                */
+fsi_status fsi_pressure_set_faces(fsi_mesh *mesh, const int32_t *faces);
+fsi_status fsi_pressure_levels(fsi_mesh *mesh, int32_t *n_levels, int32_t *N /* [16][3] or NULL */);
+/* y = (K + kappa M) x on level `level` */
+fsi_status fsi_pressure_apply(fsi_mesh *mesh, fsi_prec prec, int32_t level, const void *x, void *y);
+/* b (level+1) = P^T r (level) */
+fsi_status fsi_pressure_restrict(fsi_mesh *mesh, fsi_prec prec, int32_t level, const void *r,
+                                 void *b);
+/* x (level) += P xc (level+1) */
+fsi_status fsi_pressure_prolong_add(fsi_mesh *mesh, fsi_prec prec, int32_t level, const void *xc,
+                                    void *x);
+/* `degree` Chebyshev steps on level `level` over [hi/4, hi] for (K + kappa M) x = b,
+ * from x = 0 (from_zero != 0; x is overwritten) or from the given x.  Uses the
+ * level's scratch direction vector. */
+fsi_status fsi_pressure_smooth(fsi_mesh *mesh, fsi_prec prec, int32_t level, int32_t degree,
+                               const void *b, void *x, int32_t from_zero);
+/* x = V(b) ~ (K + kappa M)^{-1} b on the mesh grid (b, x: [n], not aliased). */
+fsi_status fsi_pressure_vcycle(fsi_mesh *mesh, fsi_prec prec, const void *b, void *x);
 
 /* ----------------------------------------------------------------------- */
 /* Learned initial guess (an extension; the paper has no counterpart).      */

@@ -53,7 +53,7 @@ class fsi_newton_opts(ctypes.Structure):
                 ("max_newton", ctypes.c_int32), ("max_krylov", ctypes.c_int32),
                 ("newton_rtol", ctypes.c_double), ("krylov_rtol", ctypes.c_double),
                 ("r_ref", ctypes.c_double), ("precond_every", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("precond", ctypes.c_int32)]
 
 
 class fsi_newton_report(ctypes.Structure):
@@ -122,6 +122,13 @@ _SIGS = {
     "fsi_block_diagonal": ([_VP, _INT, ctypes.POINTER(fsi_step_state), _VP], _INT),
     "fsi_newton_step": ([_VP, ctypes.POINTER(fsi_newton_opts), ctypes.POINTER(fsi_step_state),
                          ctypes.POINTER(fsi_newton_report)], _INT),
+    "fsi_pressure_levels": ([_VP, ctypes.POINTER(ctypes.c_int32), _VP], _INT),
+    "fsi_pressure_set_faces": ([_VP, ctypes.POINTER(ctypes.c_int32)], _INT),
+    "fsi_pressure_apply": ([_VP, _INT, _INT, _VP, _VP], _INT),
+    "fsi_pressure_restrict": ([_VP, _INT, _INT, _VP, _VP], _INT),
+    "fsi_pressure_prolong_add": ([_VP, _INT, _INT, _VP, _VP], _INT),
+    "fsi_pressure_smooth": ([_VP, _INT, _INT, _INT, _VP, _VP, _INT], _INT),
+    "fsi_pressure_vcycle": ([_VP, _INT, _VP, _VP], _INT),
     "fsi_locate_noalloc": ([ctypes.POINTER(fsi_grid), _I64, _VP, _VP, _VP, _VP, _VP,
                             ctypes.POINTER(_I64), _INT, _INT, _VP], _INT),
     "fsi_mlp_create": ([_INT, _VP, _I64, ctypes.POINTER(_VP)], _INT),
@@ -332,12 +339,15 @@ def fsi_block_diagonal(mesh: Mesh, prec, st: StepState, blocks):
     _check(lib().fsi_block_diagonal(mesh.handle, prec, ctypes.byref(st.c), _ptr(blocks, dt)))
 
 
+PRECOND_BLOCK_JACOBI, PRECOND_SCHUR = 0, 1
+
+
 def fsi_newton_step(mesh: Mesh, st: StepState, mixed=True, restart=50, max_newton=10,
                     max_krylov=1000, newton_rtol=1e-8, krylov_rtol=1e-3, r_ref=0.0,
-                    precond_every=0, check=True):
+                    precond_every=0, precond=PRECOND_SCHUR, check=True):
     """Returns (status, report dict); raises on error when check is True."""
     o = fsi_newton_opts(1 if mixed else 0, restart, max_newton, max_krylov, newton_rtol,
-                        krylov_rtol, r_ref, precond_every, 0)
+                        krylov_rtol, r_ref, precond_every, int(precond))
     rep = fsi_newton_report()
     st_code = lib().fsi_newton_step(mesh.handle, ctypes.byref(o), ctypes.byref(st.c),
                                     ctypes.byref(rep))
@@ -448,6 +458,59 @@ def fsi_mlp_guess(mlp: Mlp, mesh: Mesh, params, in_mean, in_std, out_mean, out_s
                                ctypes.byref(st.c), _ptr(yn, d), _ptr(d1, d), _ptr(d2, d),
                                int(fallback), _ptr(work, d), ctypes.byref(rep)))
     return {k: getattr(rep, k) for k, _ in fsi_guess_report._fields_ if k != "reserved"}
+
+
+def _prec_of(t):
+    import torch
+    if t.dtype == torch.float64:
+        return FSI_F64
+    if t.dtype == torch.float32:
+        return FSI_F32
+    raise TypeError("pressure vectors must be float64 or float32")
+
+
+def fsi_pressure_levels(mesh: Mesh):
+    """List of (Nx, Ny, Nz) per level of the pressure hierarchy."""
+    n = ctypes.c_int32(0)
+    buf = (ctypes.c_int32 * 48)()
+    _check(lib().fsi_pressure_levels(mesh.handle, ctypes.byref(n), buf))
+    return [tuple(buf[3 * l + d] for d in range(3)) for l in range(n.value)]
+
+
+def fsi_pressure_set_faces(mesh: Mesh, faces):
+    arr = (ctypes.c_int32 * 6)(*[int(bool(f)) for f in faces])
+    _check(lib().fsi_pressure_set_faces(mesh.handle, arr))
+
+
+def fsi_pressure_apply(mesh: Mesh, level, x, y):
+    p = _prec_of(x)
+    dt = _prec_dtype(p)
+    _check(lib().fsi_pressure_apply(mesh.handle, p, int(level), _ptr(x, dt), _ptr(y, dt)))
+
+
+def fsi_pressure_restrict(mesh: Mesh, level, r, b):
+    p = _prec_of(r)
+    dt = _prec_dtype(p)
+    _check(lib().fsi_pressure_restrict(mesh.handle, p, int(level), _ptr(r, dt), _ptr(b, dt)))
+
+
+def fsi_pressure_prolong_add(mesh: Mesh, level, xc, x):
+    p = _prec_of(x)
+    dt = _prec_dtype(p)
+    _check(lib().fsi_pressure_prolong_add(mesh.handle, p, int(level), _ptr(xc, dt), _ptr(x, dt)))
+
+
+def fsi_pressure_smooth(mesh: Mesh, level, degree, b, x, from_zero=True):
+    p = _prec_of(x)
+    dt = _prec_dtype(p)
+    _check(lib().fsi_pressure_smooth(mesh.handle, p, int(level), int(degree), _ptr(b, dt),
+                                     _ptr(x, dt), 1 if from_zero else 0))
+
+
+def fsi_pressure_vcycle(mesh: Mesh, b, x):
+    p = _prec_of(x)
+    dt = _prec_dtype(p)
+    _check(lib().fsi_pressure_vcycle(mesh.handle, p, _ptr(b, dt), _ptr(x, dt)))
 
 
 class Batch:

@@ -53,6 +53,7 @@ struct Brick {
 };
 
 struct NewtonWorkspace;
+struct PressureMG;
 
 // ---------------------------------------------------------------- mesh
 }  // namespace fsi
@@ -79,6 +80,8 @@ struct fsi_mesh {
     size_t spread_scratch_bytes;
     // Newton / Krylov workspace (newton.cu), created on first use
     fsi::NewtonWorkspace *newton;
+    // pressure multigrid hierarchy of the Schur preconditioner (pmg.cu)
+    fsi::PressureMG *pmg;
 };
 
 namespace fsi {
@@ -88,6 +91,13 @@ fsi_status ensure_vms_scratch(fsi_mesh *m, const Brick &b, size_t elem_bytes);
 size_t vms_scratch_bytes_for(const fsi_mesh *m, const Brick &b, size_t elem_bytes);
 fsi_status ensure_spread_scratch(fsi_mesh *m, size_t bytes);
 void destroy_newton_workspace(fsi_mesh *m);
+
+// pressure multigrid (pmg.cu)
+fsi_status pmg_ensure(fsi_mesh *m);
+fsi_status pmg_set_faces(fsi_mesh *m, const int faces[6]);
+template <typename T> fsi_status pmg_vcycle(fsi_mesh *m, const T *b, T *x);
+void *pmg_fine_buffer(fsi_mesh *m, int which);
+void destroy_pmg(fsi_mesh *m);
 
 // VMS operators (vms.cu)
 fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,

@@ -327,6 +327,108 @@ template <typename T> __global__ void block_apply_kernel(int n, const T *inv, co
     }
 }
 
+// Schur-complement block preconditioner, velocity part: inverse of the 3x3
+// velocity sub-block of each nodal block (Gauss-Jordan, partial pivoting,
+// FP64), stored in the upper-left 3x3 of the node's 16 slots.
+template <typename T> __global__ void block_invert3_kernel(int n, const T *blocks, T *inv)
+{
+    GRID_STRIDE(node, n)
+    {
+        double a[3][6];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                a[r][c] = (double)blocks[16 * node + 4 * r + c];
+                a[r][3 + c] = r == c ? 1.0 : 0.0;
+            }
+        bool ok = true;
+        for (int col = 0; col < 3 && ok; ++col) {
+            int p = col;
+            for (int r = col + 1; r < 3; ++r)
+                if (fabs(a[r][col]) > fabs(a[p][col])) p = r;
+            if (!(fabs(a[p][col]) > 0.0)) {
+                ok = false;
+                break;
+            }
+            if (p != col)
+                for (int c = 0; c < 6; ++c) {
+                    const double t = a[p][c];
+                    a[p][c] = a[col][c];
+                    a[col][c] = t;
+                }
+            const double piv = 1.0 / a[col][col];
+            for (int c = 0; c < 6; ++c) a[col][c] *= piv;
+            for (int r = 0; r < 3; ++r)
+                if (r != col) {
+                    const double f = a[r][col];
+                    for (int c = 0; c < 6; ++c) a[r][c] -= f * a[col][c];
+                }
+        }
+        for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c)
+                inv[16 * node + 4 * r + c] =
+                    (r < 3 && c < 3) ? (ok ? (T)a[r][3 + c] : (T)(r == c ? 1.0 : 0.0)) : T(0);
+    }
+}
+
+// Per box face f (x0, x1, y0, y1, z0, z1): cnt[f][0..3] = nodes inside the face
+// (off its edges), of those with all three velocity components free, all
+// nodes of the face, of those free.  Shared-memory sums per block, then one
+// atomic per counter and block.
+__global__ void face_count_kernel(int NX1, int NY1, int NZ1, const uint8_t *mask, int *cnt)
+{
+    __shared__ int c[24];
+    if (threadIdx.x < 24) c[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t n = (int64_t)NX1 * NY1 * NZ1;
+    const int dims[3] = {NX1 - 1, NY1 - 1, NZ1 - 1};
+    GRID_STRIDE(node, n)
+    {
+        const int idx[3] = {(int)(node % NX1), (int)((node / NX1) % NY1),
+                            (int)(node / ((int64_t)NX1 * NY1))};
+        const bool fr = !mask || !(mask[4 * node] | mask[4 * node + 1] | mask[4 * node + 2]);
+        for (int d = 0; d < 3; ++d)
+            for (int side = 0; side < 2; ++side) {
+                if (idx[d] != (side ? dims[d] : 0)) continue;
+                bool inner = true;
+                for (int e = 0; e < 3; ++e)
+                    if (e != d) inner = inner && idx[e] > 0 && idx[e] < dims[e];
+                int *cf = c + 4 * (2 * d + side);
+                if (inner) {
+                    atomicAdd(cf, 1);
+                    if (fr) atomicAdd(cf + 1, 1);
+                }
+                atomicAdd(cf + 2, 1);
+                if (fr) atomicAdd(cf + 3, 1);
+            }
+    }
+    __syncthreads();
+    if (threadIdx.x < 24 && c[threadIdx.x]) atomicAdd(cnt + threadIdx.x, c[threadIdx.x]);
+}
+
+// z_v = (3x3 velocity block)^{-1} v_v per node; the pressure entries are
+// gathered into the contiguous right-hand side bp of the pressure V-cycle
+template <typename T>
+__global__ void schur_split_kernel(int n, const T *inv, const T *v, T *z, T *bp)
+{
+    GRID_STRIDE(node, n)
+    {
+        const T x0 = v[4 * node], x1 = v[4 * node + 1], x2 = v[4 * node + 2];
+        const T *M = inv + 16 * node;
+        for (int r = 0; r < 3; ++r)
+            z[4 * node + r] = M[4 * r] * x0 + M[4 * r + 1] * x1 + M[4 * r + 2] * x2;
+        bp[node] = v[4 * node + 3];
+    }
+}
+
+// z_p = V-cycle result / sigma, or z_p = v_p on Dirichlet pressure rows
+template <typename T>
+__global__ void schur_merge_kernel(int n, const T *v, const T *xp, const uint8_t *mask,
+                                   T inv_sigma, T *z)
+{
+    GRID_STRIDE(node, n)
+    z[4 * node + 3] = (mask && mask[4 * node + 3]) ? v[4 * node + 3] : xp[node] * inv_sigma;
+}
+
 // ------------------------------------------------------------ workspace
 struct Work {
     int64_t n = 0, m = 0;
@@ -344,6 +446,7 @@ struct Work {
     double *partial = nullptr;              // [restart+2][kRedGrid]
     double *hcol = nullptr, *h2 = nullptr;  // [restart+2]
     double *hhost = nullptr;                // pinned
+    int precond = 0;                        // 0 block-Jacobi, 1 Schur (pmg.cu)
 };
 
 void free_work(Work &W)
@@ -486,7 +589,8 @@ fsi_status coupled_jacobian_impl(fsi_mesh *mesh, const fsi_step_state *st, const
     return FSI_OK;
 }
 
-template <typename T> fsi_status build_block_jacobi(fsi_mesh *mesh, const fsi_step_state *st)
+template <typename T>
+fsi_status build_block_jacobi(fsi_mesh *mesh, const fsi_step_state *st, int precond)
 {
     Work &W = mesh->newton->w;
     cudaStream_t s = mesh->stream;
@@ -502,6 +606,26 @@ template <typename T> fsi_status build_block_jacobi(fsi_mesh *mesh, const fsi_st
                                                              (T *)W.blocks);
             FSI_TRY(check_launch("probe extract"));
         }
+    if (precond == 1) {
+        block_invert3_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.blocks, (T *)W.inv);
+        FSI_TRY(check_launch("block invert"));
+        // faces where the velocity is free (more than half of the face's inner
+        // nodes, or of all its nodes when it has none inside) get Dirichlet
+        // pressure in the Schur approximation
+        int *cnt = (int *)W.partial;
+        FSI_CUDA(cudaMemsetAsync(cnt, 0, 24 * sizeof(int), s), "memset");
+        face_count_kernel<<<grid1d(n), 256, 0, s>>>(NX1, NY1, mesh->grid.N[2] + 1, st->mask, cnt);
+        FSI_TRY(check_launch("face count"));
+        int h[24];
+        FSI_CUDA(cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, s), "memcpy");
+        FSI_CUDA(cudaStreamSynchronize(s), "sync");
+        int faces[6];
+        for (int f = 0; f < 6; ++f) {
+            const int *c = h + 4 * f;
+            faces[f] = c[0] > 0 ? (2 * c[1] > c[0]) : (2 * c[3] > c[2]);
+        }
+        return pmg_set_faces(mesh, faces);
+    }
     block_invert_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.blocks, (T *)W.inv);
     return check_launch("block invert");
 }
@@ -548,6 +672,28 @@ fsi_status host_scalar(fsi_mesh *mesh, const double *dev, double *out)
     return FSI_OK;
 }
 
+// out = M^{-1} in: nodal 4x4 block-Jacobi (precond 0), or the block-diagonal
+// Schur-complement preconditioner (precond 1): 3x3 velocity blocks and
+// sigma^{-1} x one pressure V-cycle, sigma = alpha_f gamma dt / (alpha_m rho)
+template <typename T>
+fsi_status apply_precond(fsi_mesh *mesh, const fsi_step_state *st, const T *in, T *out)
+{
+    Work &W = mesh->newton->w;
+    cudaStream_t s = mesh->stream;
+    const int n = (int)mesh->n_nodes;
+    if (W.precond == 0) {
+        block_apply_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, in, out);
+        return check_launch("block apply");
+    }
+    T *bp = (T *)pmg_fine_buffer(mesh, 0), *xp = (T *)pmg_fine_buffer(mesh, 1);
+    schur_split_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, in, out, bp);
+    FSI_TRY(check_launch("Schur split"));
+    FSI_TRY(pmg_vcycle<T>(mesh, bp, xp));
+    const double sigma = mesh->alpha_f * mesh->gamma * mesh->phys.dt / (mesh->alpha_m * mesh->phys.rho);
+    schur_merge_kernel<T><<<grid1d(n), 256, 0, s>>>(n, in, xp, st->mask, (T)(1.0 / sigma), out);
+    return check_launch("Schur merge");
+}
+
 // GMRES(restart) with right preconditioning M^{-1} (block Jacobi) on
 // J x = b, x0 = 0, to ||b - J x|| <= rtol ||b||.  Result in W.x.
 template <typename T>
@@ -584,7 +730,7 @@ fsi_status gmres(fsi_mesh *mesh, const fsi_step_state *st, int restart, int max_
         bool done = false;
         for (int j = 0; j < restart && its < max_its; ++j) {
             T *Vj = V + (int64_t)j * ld;
-            block_apply_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, Vj, z);
+            FSI_TRY(apply_precond<T>(mesh, st, Vj, z));
             FSI_TRY(coupled_jacobian_impl<T>(mesh, st, z, w));
             // classical Gram-Schmidt with one reorthogonalisation
             FSI_TRY(multi_dot<T>(mesh, j + 1, V, ld, w, W.hcol, 0));
@@ -634,7 +780,7 @@ fsi_status gmres(fsi_mesh *mesh, const fsi_step_state *st, int restart, int max_
                  "memcpy");
         zero_kernel<T><<<grid1d(len), 256, 0, s>>>(len, w);
         multi_axpy<T>(s, jj, len, V, ld, W.h2, w);  // w = -V (-y)
-        block_apply_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, w, z);
+        FSI_TRY(apply_precond<T>(mesh, st, w, z));
         add_kernel<T><<<grid1d(len), 256, 0, s>>>(len, z, x);
         FSI_TRY(check_launch("GMRES update"));
         if (done || its >= max_its) break;
@@ -670,7 +816,7 @@ fsi_status newton_impl(fsi_mesh *mesh, const fsi_newton_opts *o, const fsi_step_
     while (r > target && it < o->max_newton) {
         FSI_TRY(prepare_linearisation<T>(mesh, st));
         if (rep->precond_builds == 0 || (o->precond_every > 0 && it % o->precond_every == 0)) {
-            FSI_TRY(build_block_jacobi<T>(mesh, st));
+            FSI_TRY(build_block_jacobi<T>(mesh, st, o->precond));
             rep->precond_builds++;
         }
         neg_cast_kernel<T><<<grid1d(len), 256, 0, s>>>(len, W.R, (T *)W.b);
@@ -762,10 +908,10 @@ fsi_status fsi_block_diagonal(fsi_mesh *mesh, fsi_prec prec, const fsi_step_stat
     const size_t bytes = (size_t)mesh->n_nodes * 16 * (prec == FSI_F64 ? 8 : 4);
     if (prec == FSI_F64) {
         FSI_TRY(prepare_linearisation<double>(mesh, st));
-        FSI_TRY(build_block_jacobi<double>(mesh, st));
+        FSI_TRY(build_block_jacobi<double>(mesh, st, 0));
     } else {
         FSI_TRY(prepare_linearisation<float>(mesh, st));
-        FSI_TRY(build_block_jacobi<float>(mesh, st));
+        FSI_TRY(build_block_jacobi<float>(mesh, st, 0));
     }
     FSI_CUDA(cudaMemcpyAsync(blocks, W.blocks, bytes, cudaMemcpyDeviceToDevice, mesh->stream),
              "memcpy");
@@ -779,12 +925,14 @@ fsi_status fsi_newton_step(fsi_mesh *mesh, const fsi_newton_opts *opts, const fs
     FSI_TRY(validate_state(mesh, st));
     if (!opts || !report) return set_error(FSI_ERR_ARG, "opts or report is NULL");
     if (opts->restart < 1 || opts->restart > 200 || opts->max_newton < 0 ||
-        opts->max_krylov < 1 || !(opts->newton_rtol > 0.0) || !(opts->krylov_rtol > 0.0))
+        opts->max_krylov < 1 || !(opts->newton_rtol > 0.0) || !(opts->krylov_rtol > 0.0) ||
+        opts->precond < 0 || opts->precond > 1)
         return set_error(FSI_ERR_ARG, "invalid Newton options");
     std::memset(report, 0, sizeof *report);
     const auto t0 = std::chrono::steady_clock::now();
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
     FSI_TRY(ensure_work(mesh, st->m, opts->restart));
+    mesh->newton->w.precond = opts->precond;
     fsi_status stt = opts->mixed ? newton_impl<float>(mesh, opts, st, report)
                                  : newton_impl<double>(mesh, opts, st, report);
     cudaStreamSynchronize(mesh->stream);

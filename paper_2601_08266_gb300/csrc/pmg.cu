@@ -1,0 +1,704 @@
+// pmg.cu -- pressure block of the Schur-complement block preconditioner
+// (Sec. 2.4 solves the reduced system with block preconditioners built from
+// its sub-matrices).  For the saddle-point blocks [[A, B], [C, D]] of the
+// linearised fluid system with a mass-dominated velocity block
+// A ~ alpha_m rho M, the pressure Schur complement D - C A^{-1} B acts like
+// sigma K, K the Q1 stiffness matrix of the pressure space and
+// sigma = alpha_f gamma dt / (alpha_m rho).  The preconditioner replaces it by
+// sigma (K + kappa M), kappa = (pi / (2 L))^2 with L the largest extent of the
+// grid (M the Q1 mass matrix; the shift keeps the operator non-singular where
+// only Neumann conditions bound the pressure).  On faces of the box where the
+// velocity is free (traction-free outflow) the true Schur complement acts like
+// a Dirichlet problem for the pressure, so the nodes of such faces are
+// eliminated (rows and columns dropped, diagonal kept; the restricted
+// right-hand side is zeroed there).  The approximation is inverted with one
+// geometric multigrid V-cycle on the uniform grid:
+//
+//   levels     the mesh grid, then every other node while all N_d are even and
+//              the grid has more than 125 nodes;
+//   operator   K + kappa M applied matrix-free: on a uniform grid both are
+//              tensor products of the 1D linear-element matrices
+//              M1 = h/6 [1 4 1] (h/3 on boundary nodes) and
+//              K1 = 1/h [-1 2 -1] (1/h on boundary nodes):
+//              K = K1 x M1 x M1 + M1 x K1 x M1 + M1 x M1 x K1;
+//   transfer   trilinear interpolation P, restriction P^T (weights 1, 1/2);
+//              the coarse operators equal P^T A P (Galerkin) exactly;
+//   smoother   Chebyshev semi-iteration of degree 2 on D^{-1} A over
+//              [hi/4, hi], hi = 1.1 x the largest symbol/diagonal ratio over
+//              the modes theta_d in {0, pi} (pre- and post-smoothing);
+//   coarsest   a dense inverse (<= 1000 nodes, built once on the host in
+//              FP64) or, on grids that do not coarsen, Chebyshev degree 8 over
+//              [hi/30, hi].
+//
+// The V-cycle is a fixed linear operator (symmetric), so it can precondition
+// plain GMRES.  Every kernel is one thread per node, deterministic; FP64 or
+// FP32 arithmetic follows the caller's precision.
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+#include <vector>
+
+#include "fsi_internal.cuh"
+
+namespace fsi {
+
+constexpr int kPmgMaxLevels = 16;
+constexpr int kPmgNu = 2;
+constexpr int kPmgCoarseDegree = 8;
+constexpr int64_t kPmgDirectMax = 1000;
+constexpr int64_t kPmgMinCoarsen = 125;
+
+struct PmgLevel {
+    int N[3];
+    double h[3];
+    int64_t n;
+    double hi;          // Chebyshev upper bound of D^{-1} A
+    void *b, *x, *r, *d;  // level vectors (8 bytes per entry: either precision fits)
+};
+
+struct PressureMG {
+    int nlev = 0;
+    PmgLevel lev[kPmgMaxLevels];
+    double kappa = 0.0;
+    int faces[6] = {0, 0, 0, 0, 0, 0};  // eliminated faces x0, x1, y0, y1, z0, z1
+    bool direct = false;
+    int64_t nc = 0;
+    double *inv64 = nullptr;  // [nc][nc]
+    float *inv32 = nullptr;
+};
+
+namespace {
+
+// 1D coefficients of a level in the working type: mass and stiffness
+// entries of interior / boundary diagonals and of the off-diagonals.
+template <typename T> struct Axis {
+    int N;
+    T m_in, m_bd, m_off, k_in, k_bd, k_off;
+};
+
+template <typename T> struct LevelArgs {
+    Axis<T> a[3];
+    T kappa;
+    int NX1, NY1, NZ1;
+    int faces[6];
+};
+
+template <typename T> LevelArgs<T> level_args(const PressureMG &P, int l)
+{
+    const PmgLevel &L = P.lev[l];
+    LevelArgs<T> A;
+    for (int d = 0; d < 3; ++d) {
+        const double h = L.h[d];
+        A.a[d] = {L.N[d], (T)(2.0 * h / 3.0), (T)(h / 3.0), (T)(h / 6.0),
+                  (T)(2.0 / h), (T)(1.0 / h), (T)(-1.0 / h)};
+    }
+    A.kappa = (T)P.kappa;
+    A.NX1 = L.N[0] + 1;
+    A.NY1 = L.N[1] + 1;
+    A.NZ1 = L.N[2] + 1;
+    for (int f = 0; f < 6; ++f) A.faces[f] = P.faces[f];
+    return A;
+}
+
+// node (i, j, k) lies on an eliminated face
+template <typename T>
+__device__ __forceinline__ bool eliminated(const LevelArgs<T> &L, int i, int j, int k)
+{
+    return (L.faces[0] && i == 0) || (L.faces[1] && i == L.NX1 - 1) ||
+           (L.faces[2] && j == 0) || (L.faces[3] && j == L.NY1 - 1) ||
+           (L.faces[4] && k == 0) || (L.faces[5] && k == L.NZ1 - 1);
+}
+
+// entries (mass, stiffness) of row i, column i + d (|d| <= 1, in range)
+template <typename T>
+__device__ __forceinline__ void coef(const Axis<T> &a, int i, int d, T &m, T &k)
+{
+    if (d == 0) {
+        const bool bd = (i == 0) || (i == a.N);
+        m = bd ? a.m_bd : a.m_in;
+        k = bd ? a.k_bd : a.k_in;
+    } else {
+        m = a.m_off;
+        k = a.k_off;
+    }
+}
+
+template <typename T> __device__ __forceinline__ T diag_of(const LevelArgs<T> &L, int i, int j, int k)
+{
+    T mx, kx, my, ky, mz, kz;
+    coef(L.a[0], i, 0, mx, kx);
+    coef(L.a[1], j, 0, my, ky);
+    coef(L.a[2], k, 0, mz, kz);
+    return kx * my * mz + mx * ky * mz + mx * my * kz + L.kappa * mx * my * mz;
+}
+
+// (A x)_node for node (i, j, k): nine x-lines, each reduced with the 1D
+// stiffness and mass rows, then combined with the y/z coefficients.  Rows of
+// eliminated nodes keep only the diagonal; their columns are skipped.
+template <typename T>
+__device__ __forceinline__ T apply_row(const LevelArgs<T> &L, const T *__restrict__ x, int i,
+                                       int j, int k)
+{
+    const int64_t node = i + (int64_t)L.NX1 * (j + (int64_t)L.NY1 * k);
+    if (eliminated(L, i, j, k)) return diag_of(L, i, j, k) * x[node];
+    // the eliminated neighbours lie on faces: the lines that would touch them
+    // are cut at i/j/k = 0 or N when the face is eliminated
+    const int ilo = L.faces[0] ? 1 : 0, ihi = L.faces[1] ? L.NX1 - 2 : L.NX1 - 1;
+    const int jlo = L.faces[2] ? 1 : 0, jhi = L.faces[3] ? L.NY1 - 2 : L.NY1 - 1;
+    const int klo = L.faces[4] ? 1 : 0, khi = L.faces[5] ? L.NZ1 - 2 : L.NZ1 - 1;
+    T acc = T(0);
+    for (int dk = -1; dk <= 1; ++dk) {
+        const int kk = k + dk;
+        if (kk < klo || kk > khi) continue;
+        T mz, kz;
+        coef(L.a[2], k, dk, mz, kz);
+        for (int dj = -1; dj <= 1; ++dj) {
+            const int jj = j + dj;
+            if (jj < jlo || jj > jhi) continue;
+            T my, ky;
+            coef(L.a[1], j, dj, my, ky);
+            const T *row = x + (int64_t)L.NX1 * (jj + (int64_t)L.NY1 * kk);
+            T sK = T(0), sM = T(0);
+            for (int di = -1; di <= 1; ++di) {
+                const int ii = i + di;
+                if (ii < ilo || ii > ihi) continue;
+                T mx, kx;
+                coef(L.a[0], i, di, mx, kx);
+                const T v = row[ii];
+                sK += kx * v;
+                sM += mx * v;
+            }
+            acc += sK * (my * mz) + sM * (ky * mz + my * kz + L.kappa * my * mz);
+        }
+    }
+    return acc;
+}
+
+#define NODE_LOOP(L, node, i, j, k)                                                          \
+    const int64_t n_ = (int64_t)(L).NX1 * (L).NY1 * (L).NZ1;                                 \
+    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < n_;           \
+         node += (int64_t)gridDim.x * blockDim.x)                                            \
+        for (int i = (int)(node % (L).NX1), j = (int)((node / (L).NX1) % (L).NY1),          \
+                 k = (int)(node / ((int64_t)(L).NX1 * (L).NY1)), once_ = 1;                 \
+             once_; once_ = 0)
+
+// y = A x (b == null) or y = b - A x
+template <typename T>
+__global__ void apply_kernel(LevelArgs<T> L, const T *__restrict__ x, const T *__restrict__ b,
+                             T *__restrict__ y)
+{
+    NODE_LOOP(L, node, i, j, k)
+    {
+        const T ax = apply_row(L, x, i, j, k);
+        y[node] = b ? b[node] - ax : ax;
+    }
+}
+
+// Chebyshev, first direction: d = D^{-1} (b - A x) / theta  (x == null: x = 0)
+template <typename T>
+__global__ void cheb_first_kernel(LevelArgs<T> L, const T *__restrict__ b, const T *__restrict__ x,
+                                  T inv_theta, T *__restrict__ d)
+{
+    NODE_LOOP(L, node, i, j, k)
+    {
+        const T r = x ? b[node] - apply_row(L, x, i, j, k) : b[node];
+        d[node] = inv_theta * r / diag_of(L, i, j, k);
+    }
+}
+
+// d = c1 d + c2 D^{-1} (b - A x)   (in place on d: neighbours read x only)
+template <typename T>
+__global__ void cheb_next_kernel(LevelArgs<T> L, const T *__restrict__ b, const T *__restrict__ x,
+                                 T c1, T c2, T *__restrict__ d)
+{
+    NODE_LOOP(L, node, i, j, k)
+    {
+        const T r = b[node] - apply_row(L, x, i, j, k);
+        d[node] = c1 * d[node] + c2 * (r / diag_of(L, i, j, k));
+    }
+}
+
+// x += d, or x = d when set
+template <typename T> __global__ void add_dir_kernel(int64_t n, const T *d, T *x, int set)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = set ? d[i] : x[i] + d[i];
+}
+
+// b_c = P^T r: each coarse node gathers the fine nodes within one fine cell,
+// weights 1 (coincident) and 1/2 (neighbour) per axis
+template <typename T>
+__global__ void restrict_kernel(LevelArgs<T> F, LevelArgs<T> C, const T *__restrict__ r,
+                                T *__restrict__ bc)
+{
+    NODE_LOOP(C, node, I, J, K)
+    {
+        T acc = T(0);
+        for (int dk = -1; dk <= 1; ++dk) {
+            const int k = 2 * K + dk;
+            if (k < 0 || k >= F.NZ1) continue;
+            const T wk = dk ? T(0.5) : T(1);
+            for (int dj = -1; dj <= 1; ++dj) {
+                const int j = 2 * J + dj;
+                if (j < 0 || j >= F.NY1) continue;
+                const T wjk = (dj ? T(0.5) : T(1)) * wk;
+                const T *row = r + (int64_t)F.NX1 * (j + (int64_t)F.NY1 * k);
+                T s = T(0);
+                for (int di = -1; di <= 1; ++di) {
+                    const int i = 2 * I + di;
+                    if (i < 0 || i >= F.NX1) continue;
+                    s += (di ? T(0.5) : T(1)) * row[i];
+                }
+                acc += wjk * s;
+            }
+        }
+        bc[node] = eliminated(C, I, J, K) ? T(0) : acc;
+    }
+}
+
+// x += P x_c: trilinear interpolation of the coarse correction
+template <typename T>
+__global__ void prolong_kernel(LevelArgs<T> F, LevelArgs<T> C, const T *__restrict__ xc,
+                               T *__restrict__ x)
+{
+    NODE_LOOP(F, node, i, j, k)
+    {
+        const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+        const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+        const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1),
+                wk = (k & 1) ? T(0.5) : T(1);
+        T acc = T(0);
+        for (int c = 0; c < nk; ++c)
+            for (int b = 0; b < nj; ++b) {
+                const T *row = xc + (int64_t)C.NX1 * ((j0 + b) + (int64_t)C.NY1 * (k0 + c));
+                T s = T(0);
+                for (int a = 0; a < ni; ++a) s += row[i0 + a];
+                acc += (wj * wk) * (wi * s);
+            }
+        x[node] += acc;
+    }
+}
+
+// x = Ainv b on the coarsest grid: one warp per row, fixed reduction order
+template <typename T>
+__global__ void dense_apply_kernel(int64_t nc, const T *__restrict__ Ainv, const T *__restrict__ b,
+                                   T *__restrict__ x)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = warp; row < nc; row += nwarps) {
+        T s = T(0);
+        for (int64_t c = lane; c < nc; c += 32) s += Ainv[row * nc + c] * b[c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) x[row] = s;
+    }
+}
+
+int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+
+double spectrum_bound(const double h[3], double kappa)
+{
+    double diag = kappa;
+    for (int d = 0; d < 3; ++d) diag *= 2.0 * h[d] / 3.0;
+    for (int d = 0; d < 3; ++d) {
+        double t = 2.0 / h[d];
+        for (int e = 0; e < 3; ++e)
+            if (e != d) t *= 2.0 * h[e] / 3.0;
+        diag += t;
+    }
+    double best = 0.0;
+    for (int s = 0; s < 8; ++s) {
+        double k[3], m[3];
+        for (int d = 0; d < 3; ++d) {
+            const bool pi = (s >> d) & 1;
+            k[d] = pi ? 4.0 / h[d] : 0.0;
+            m[d] = pi ? h[d] / 3.0 : h[d];
+        }
+        const double sym = k[0] * m[1] * m[2] + m[0] * k[1] * m[2] + m[0] * m[1] * k[2] +
+                           kappa * m[0] * m[1] * m[2];
+        best = std::max(best, sym / diag);
+    }
+    return 1.1 * best;
+}
+
+// Dense K + kappa M of a (small) level from the same 1D coefficients, then
+// its inverse by Gauss-Jordan with partial pivoting (FP64, host).
+bool dense_inverse(const PmgLevel &L, double kappa, const int faces[6], std::vector<double> &inv)
+{
+    auto elim = [&](int i, int j, int k) {
+        return (faces[0] && i == 0) || (faces[1] && i == L.N[0]) || (faces[2] && j == 0) ||
+               (faces[3] && j == L.N[1]) || (faces[4] && k == 0) || (faces[5] && k == L.N[2]);
+    };
+    const int nx = L.N[0] + 1, ny = L.N[1] + 1, nz = L.N[2] + 1;
+    const int64_t n = L.n;
+    auto c1 = [&](int d, int i, int off, double &m, double &k) {
+        const double h = L.h[d];
+        if (off == 0) {
+            const bool bd = i == 0 || i == L.N[d];
+            m = bd ? h / 3.0 : 2.0 * h / 3.0;
+            k = bd ? 1.0 / h : 2.0 / h;
+        } else {
+            m = h / 6.0;
+            k = -1.0 / h;
+        }
+    };
+    std::vector<double> a((size_t)n * 2 * n, 0.0);
+    const int64_t w = 2 * n;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const int64_t row = i + (int64_t)nx * (j + (int64_t)ny * k);
+                for (int dk = -1; dk <= 1; ++dk)
+                    for (int dj = -1; dj <= 1; ++dj)
+                        for (int di = -1; di <= 1; ++di) {
+                            const int ii = i + di, jj = j + dj, kk = k + dk;
+                            if (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz)
+                                continue;
+                            double mx, kx, my, ky, mz, kz;
+                            c1(0, i, di, mx, kx);
+                            c1(1, j, dj, my, ky);
+                            c1(2, k, dk, mz, kz);
+                            const int64_t col = ii + (int64_t)nx * (jj + (int64_t)ny * kk);
+                            if (col != row && (elim(i, j, k) || elim(ii, jj, kk))) continue;
+                            a[row * w + col] = kx * my * mz + mx * ky * mz + mx * my * kz +
+                                               kappa * mx * my * mz;
+                        }
+                a[row * w + n + row] = 1.0;
+            }
+    for (int64_t c = 0; c < n; ++c) {
+        int64_t p = c;
+        for (int64_t r = c + 1; r < n; ++r)
+            if (std::fabs(a[r * w + c]) > std::fabs(a[p * w + c])) p = r;
+        if (!(std::fabs(a[p * w + c]) > 0.0)) return false;
+        if (p != c)
+            for (int64_t q = 0; q < w; ++q) std::swap(a[p * w + q], a[c * w + q]);
+        const double piv = 1.0 / a[c * w + c];
+        for (int64_t q = 0; q < w; ++q) a[c * w + q] *= piv;
+        for (int64_t r = 0; r < n; ++r)
+            if (r != c) {
+                const double f = a[r * w + c];
+                if (f != 0.0)
+                    for (int64_t q = 0; q < w; ++q) a[r * w + q] -= f * a[c * w + q];
+            }
+    }
+    inv.assign((size_t)n * n, 0.0);
+    for (int64_t r = 0; r < n; ++r)
+        for (int64_t c = 0; c < n; ++c) inv[r * n + c] = a[r * w + n + c];
+    return true;
+}
+
+template <typename T> T *vec(void *p) { return static_cast<T *>(p); }
+
+// Chebyshev semi-iteration of `degree` on level l: x <- x + p(D^{-1}A) (..),
+// from x = 0 when from_zero (x is then overwritten).
+template <typename T>
+fsi_status chebyshev(fsi_mesh *m, int l, int degree, double lo, double hi, const T *b, T *x,
+                     bool from_zero)
+{
+    PressureMG &P = *m->pmg;
+    PmgLevel &L = P.lev[l];
+    const LevelArgs<T> A = level_args<T>(P, l);
+    cudaStream_t s = m->stream;
+    const int g = grid_for(L.n);
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), s1 = theta / delta;
+    T *d = vec<T>(L.d);
+    cheb_first_kernel<T><<<g, 256, 0, s>>>(A, b, from_zero ? nullptr : x, (T)(1.0 / theta), d);
+    double rho = 1.0 / s1;
+    bool set = from_zero;
+    for (int it = 1; it < degree; ++it) {
+        add_dir_kernel<T><<<g, 256, 0, s>>>(L.n, d, x, set ? 1 : 0);
+        set = false;
+        const double rho_new = 1.0 / (2.0 * s1 - rho);
+        cheb_next_kernel<T><<<g, 256, 0, s>>>(A, b, x, (T)(rho_new * rho), (T)(2.0 * rho_new / delta), d);
+        rho = rho_new;
+    }
+    add_dir_kernel<T><<<g, 256, 0, s>>>(L.n, d, x, set ? 1 : 0);
+    return check_launch("pressure smoother");
+}
+
+template <typename T> fsi_status coarse_solve(fsi_mesh *m, const T *b, T *x)
+{
+    PressureMG &P = *m->pmg;
+    const int l = P.nlev - 1;
+    if (P.direct) {
+        const T *inv = std::is_same<T, double>::value ? (const T *)P.inv64 : (const T *)P.inv32;
+        const int warps_per_block = 8;
+        const int blocks = (int)std::min<int64_t>((P.nc + warps_per_block - 1) / warps_per_block, 152 * 8);
+        dense_apply_kernel<T><<<blocks, 32 * warps_per_block, 0, m->stream>>>(P.nc, inv, b, x);
+        return check_launch("pressure coarse solve");
+    }
+    return chebyshev<T>(m, l, kPmgCoarseDegree, P.lev[l].hi / 30.0, P.lev[l].hi, b, x, true);
+}
+
+template <typename T> fsi_status vcycle_level(fsi_mesh *m, int l, const T *b, T *x)
+{
+    PressureMG &P = *m->pmg;
+    if (l == P.nlev - 1) return coarse_solve<T>(m, b, x);
+    PmgLevel &L = P.lev[l], &Lc = P.lev[l + 1];
+    const double hi = L.hi;
+    FSI_TRY(chebyshev<T>(m, l, kPmgNu, hi / 4.0, hi, b, x, true));
+    const LevelArgs<T> A = level_args<T>(P, l), Ac = level_args<T>(P, l + 1);
+    apply_kernel<T><<<grid_for(L.n), 256, 0, m->stream>>>(A, x, b, vec<T>(L.r));
+    restrict_kernel<T><<<grid_for(Lc.n), 256, 0, m->stream>>>(A, Ac, vec<T>(L.r), vec<T>(Lc.b));
+    FSI_TRY(check_launch("pressure restrict"));
+    FSI_TRY(vcycle_level<T>(m, l + 1, vec<T>(Lc.b), vec<T>(Lc.x)));
+    prolong_kernel<T><<<grid_for(L.n), 256, 0, m->stream>>>(A, Ac, vec<T>(Lc.x), x);
+    FSI_TRY(check_launch("pressure prolong"));
+    return chebyshev<T>(m, l, kPmgNu, hi / 4.0, hi, b, x, false);
+}
+
+fsi_status check_prec(fsi_prec p)
+{
+    if (p != FSI_F64 && p != FSI_F32) return set_error(FSI_ERR_ARG, "pressure operator: precision must be FSI_F64 or FSI_F32");
+    return FSI_OK;
+}
+
+fsi_status check_level(fsi_mesh *m, int level, bool need_coarser)
+{
+    if (level < 0 || level >= m->pmg->nlev || (need_coarser && level + 1 >= m->pmg->nlev))
+        return set_error(FSI_ERR_ARG, "pressure operator: level %d out of range", level);
+    return FSI_OK;
+}
+
+}  // namespace
+
+void destroy_pmg(fsi_mesh *m)
+{
+    if (!m->pmg) return;
+    PressureMG &P = *m->pmg;
+    for (int l = 0; l < P.nlev; ++l) {
+        cudaFree(P.lev[l].b);
+        cudaFree(P.lev[l].x);
+        cudaFree(P.lev[l].r);
+        cudaFree(P.lev[l].d);
+    }
+    cudaFree(P.inv64);
+    cudaFree(P.inv32);
+    delete m->pmg;
+    m->pmg = nullptr;
+}
+
+// dense inverse of the coarsest level for the current faces (FP64 host
+// Gauss-Jordan), copied to the device in FP64 and FP32
+fsi_status build_coarse_inverse(fsi_mesh *m)
+{
+    PressureMG &P = *m->pmg;
+    const PmgLevel &C = P.lev[P.nlev - 1];
+    std::vector<double> inv;
+    if (!dense_inverse(C, P.kappa, P.faces, inv))
+        return set_error(FSI_ERR_ARG, "pressure hierarchy: singular coarse operator");
+    std::vector<float> inv32(inv.begin(), inv.end());
+    FSI_CUDA(cudaMemcpy(P.inv64, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice),
+             "memcpy");
+    FSI_CUDA(cudaMemcpy(P.inv32, inv32.data(), inv32.size() * sizeof(float),
+                        cudaMemcpyHostToDevice),
+             "memcpy");
+    return FSI_OK;
+}
+
+fsi_status pmg_ensure(fsi_mesh *m)
+{
+    if (m->pmg) return FSI_OK;
+    PressureMG *P = new (std::nothrow) PressureMG();
+    if (!P) return set_error(FSI_ERR_OOM, "host allocation of the pressure hierarchy failed");
+    m->pmg = P;
+    double Lmax = 0.0;
+    for (int d = 0; d < 3; ++d) Lmax = std::max(Lmax, m->grid.N[d] * m->grid.h[d]);
+    const double q = 3.14159265358979323846 / (2.0 * Lmax);
+    P->kappa = q * q;
+    PmgLevel cur{};
+    for (int d = 0; d < 3; ++d) {
+        cur.N[d] = m->grid.N[d];
+        cur.h[d] = m->grid.h[d];
+    }
+    while (true) {
+        cur.n = (int64_t)(cur.N[0] + 1) * (cur.N[1] + 1) * (cur.N[2] + 1);
+        cur.hi = spectrum_bound(cur.h, P->kappa);
+        P->lev[P->nlev++] = cur;
+        const bool even = cur.N[0] % 2 == 0 && cur.N[1] % 2 == 0 && cur.N[2] % 2 == 0;
+        if (!even || cur.n <= kPmgMinCoarsen || P->nlev == kPmgMaxLevels) break;
+        for (int d = 0; d < 3; ++d) {
+            cur.N[d] /= 2;
+            cur.h[d] *= 2.0;
+        }
+    }
+    for (int l = 0; l < P->nlev; ++l) {
+        const size_t bytes = (size_t)P->lev[l].n * sizeof(double);
+        void **bufs[] = {&P->lev[l].b, &P->lev[l].x, &P->lev[l].r, &P->lev[l].d};
+        for (void **b : bufs) {
+            *b = nullptr;
+            if (cudaMalloc(b, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                destroy_pmg(m);
+                return set_error(FSI_ERR_OOM, "pressure hierarchy: cudaMalloc failed");
+            }
+        }
+    }
+    const PmgLevel &C = P->lev[P->nlev - 1];
+    P->nc = C.n;
+    P->direct = C.n <= kPmgDirectMax;
+    if (P->direct) {
+        if (cudaMalloc((void **)&P->inv64, (size_t)C.n * C.n * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void **)&P->inv32, (size_t)C.n * C.n * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            destroy_pmg(m);
+            return set_error(FSI_ERR_OOM, "pressure hierarchy: cudaMalloc failed");
+        }
+        fsi_status st = build_coarse_inverse(m);
+        if (st != FSI_OK) {
+            destroy_pmg(m);
+            return st;
+        }
+    }
+    return FSI_OK;
+}
+
+fsi_status pmg_set_faces(fsi_mesh *m, const int faces[6])
+{
+    FSI_TRY(pmg_ensure(m));
+    PressureMG &P = *m->pmg;
+    bool same = true;
+    for (int f = 0; f < 6; ++f) same = same && (P.faces[f] != 0) == (faces[f] != 0);
+    if (same) return FSI_OK;
+    for (int f = 0; f < 6; ++f) P.faces[f] = faces[f] != 0;
+    // the coarse inverse is in use by work already queued on the stream
+    FSI_CUDA(cudaStreamSynchronize(m->stream), "sync");
+    return P.direct ? build_coarse_inverse(m) : FSI_OK;
+}
+
+template <typename T> fsi_status pmg_vcycle(fsi_mesh *m, const T *b, T *x)
+{
+    FSI_TRY(pmg_ensure(m));
+    return vcycle_level<T>(m, 0, b, x);
+}
+template fsi_status pmg_vcycle<double>(fsi_mesh *, const double *, double *);
+template fsi_status pmg_vcycle<float>(fsi_mesh *, const float *, float *);
+
+// level-0 right-hand side (which = 0) and solution (which = 1) buffers, n
+// entries of either precision; the Newton preconditioner gathers into them
+void *pmg_fine_buffer(fsi_mesh *m, int which) { return which == 0 ? m->pmg->lev[0].b : m->pmg->lev[0].x; }
+
+}  // namespace fsi
+
+// ---------------------------------------------------------------- C ABI
+using namespace fsi;
+
+extern "C" {
+
+fsi_status fsi_pressure_levels(fsi_mesh *mesh, int32_t *n_levels, int32_t *N)
+{
+    FSI_TRY(validate_mesh(mesh));
+    if (!n_levels) return set_error(FSI_ERR_ARG, "fsi_pressure_levels: n_levels is NULL");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_TRY(pmg_ensure(mesh));
+    *n_levels = mesh->pmg->nlev;
+    if (N)
+        for (int l = 0; l < mesh->pmg->nlev; ++l)
+            for (int d = 0; d < 3; ++d) N[3 * l + d] = mesh->pmg->lev[l].N[d];
+    return FSI_OK;
+}
+
+fsi_status fsi_pressure_set_faces(fsi_mesh *mesh, const int32_t *faces)
+{
+    FSI_TRY(validate_mesh(mesh));
+    if (!faces) return set_error(FSI_ERR_ARG, "fsi_pressure_set_faces: faces is NULL");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    int f[6];
+    for (int q = 0; q < 6; ++q) f[q] = faces[q] != 0;
+    return pmg_set_faces(mesh, f);
+}
+
+fsi_status fsi_pressure_apply(fsi_mesh *mesh, fsi_prec prec, int32_t level, const void *x, void *y)
+{
+    FSI_TRY(validate_mesh(mesh));
+    FSI_TRY(check_prec(prec));
+    if (!x || !y) return set_error(FSI_ERR_ARG, "fsi_pressure_apply: NULL argument");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_TRY(pmg_ensure(mesh));
+    FSI_TRY(check_level(mesh, level, false));
+    const int g = grid_for(mesh->pmg->lev[level].n);
+    if (prec == FSI_F64)
+        apply_kernel<double><<<g, 256, 0, mesh->stream>>>(level_args<double>(*mesh->pmg, level),
+                                                         (const double *)x, nullptr, (double *)y);
+    else
+        apply_kernel<float><<<g, 256, 0, mesh->stream>>>(level_args<float>(*mesh->pmg, level),
+                                                        (const float *)x, nullptr, (float *)y);
+    return check_launch("pressure apply");
+}
+
+fsi_status fsi_pressure_restrict(fsi_mesh *mesh, fsi_prec prec, int32_t level, const void *r,
+                                 void *b)
+{
+    FSI_TRY(validate_mesh(mesh));
+    FSI_TRY(check_prec(prec));
+    if (!r || !b) return set_error(FSI_ERR_ARG, "fsi_pressure_restrict: NULL argument");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_TRY(pmg_ensure(mesh));
+    FSI_TRY(check_level(mesh, level, true));
+    PressureMG &P = *mesh->pmg;
+    const int g = grid_for(P.lev[level + 1].n);
+    if (prec == FSI_F64)
+        restrict_kernel<double><<<g, 256, 0, mesh->stream>>>(
+            level_args<double>(P, level), level_args<double>(P, level + 1), (const double *)r,
+            (double *)b);
+    else
+        restrict_kernel<float><<<g, 256, 0, mesh->stream>>>(
+            level_args<float>(P, level), level_args<float>(P, level + 1), (const float *)r,
+            (float *)b);
+    return check_launch("pressure restrict");
+}
+
+fsi_status fsi_pressure_prolong_add(fsi_mesh *mesh, fsi_prec prec, int32_t level,
+                                    const void *xc, void *x)
+{
+    FSI_TRY(validate_mesh(mesh));
+    FSI_TRY(check_prec(prec));
+    if (!xc || !x) return set_error(FSI_ERR_ARG, "fsi_pressure_prolong_add: NULL argument");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_TRY(pmg_ensure(mesh));
+    FSI_TRY(check_level(mesh, level, true));
+    PressureMG &P = *mesh->pmg;
+    const int g = grid_for(P.lev[level].n);
+    if (prec == FSI_F64)
+        prolong_kernel<double><<<g, 256, 0, mesh->stream>>>(
+            level_args<double>(P, level), level_args<double>(P, level + 1), (const double *)xc,
+            (double *)x);
+    else
+        prolong_kernel<float><<<g, 256, 0, mesh->stream>>>(
+            level_args<float>(P, level), level_args<float>(P, level + 1), (const float *)xc,
+            (float *)x);
+    return check_launch("pressure prolong");
+}
+
+fsi_status fsi_pressure_smooth(fsi_mesh *mesh, fsi_prec prec, int32_t level, int32_t degree,
+                               const void *b, void *x, int32_t from_zero)
+{
+    FSI_TRY(validate_mesh(mesh));
+    FSI_TRY(check_prec(prec));
+    if (!b || !x) return set_error(FSI_ERR_ARG, "fsi_pressure_smooth: NULL argument");
+    if (degree < 1 || degree > 64) return set_error(FSI_ERR_ARG, "fsi_pressure_smooth: degree 1..64");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_TRY(pmg_ensure(mesh));
+    FSI_TRY(check_level(mesh, level, false));
+    const double hi = mesh->pmg->lev[level].hi;
+    if (prec == FSI_F64)
+        return chebyshev<double>(mesh, level, degree, hi / 4.0, hi, (const double *)b,
+                                 (double *)x, from_zero != 0);
+    return chebyshev<float>(mesh, level, degree, hi / 4.0, hi, (const float *)b, (float *)x,
+                            from_zero != 0);
+}
+
+fsi_status fsi_pressure_vcycle(fsi_mesh *mesh, fsi_prec prec, const void *b, void *x)
+{
+    FSI_TRY(validate_mesh(mesh));
+    FSI_TRY(check_prec(prec));
+    if (!b || !x) return set_error(FSI_ERR_ARG, "fsi_pressure_vcycle: NULL argument");
+    if (b == x) return set_error(FSI_ERR_ARG, "fsi_pressure_vcycle: b and x must not alias");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    if (prec == FSI_F64) return pmg_vcycle<double>(mesh, (const double *)b, (double *)x);
+    return pmg_vcycle<float>(mesh, (const float *)b, (float *)x);
+}
+
+}  // extern "C"

@@ -221,6 +221,7 @@ void fsi_mesh_destroy(fsi_mesh *m)
     cudaFree(m->dev_counters);
     cudaFree(m->spread_scratch);
     destroy_newton_workspace(m);
+    destroy_pmg(m);
     delete m;
 }
 

@@ -113,14 +113,16 @@ def test_block_diagonal_parity(fsi, oracle):
     assert rel(H(B), ref) < 1e-12
 
 
+@pytest.mark.parametrize("precond", [0, 1])
 @pytest.mark.parametrize("mixed", [False, True])
-def test_newton_step_matches_direct_newton(fsi, oracle, mixed):
-    """Both the plain FP64 and the mixed step reach ||R|| <= 1e-8 ||R0|| (FP64) and
-    land on the oracle's direct-solve solution."""
+def test_newton_step_matches_direct_newton(fsi, oracle, mixed, precond):
+    """Both the plain FP64 and the mixed step, with either preconditioner, reach
+    ||R|| <= 1e-8 ||R0|| (FP64) and land on the oracle's direct-solve solution."""
     from oracle import newton
     mesh, st, dev, P, y0 = setup(fsi, oracle, seed=3)
     code, rep = fsi.fsi_newton_step(mesh, st, mixed=mixed, restart=50, max_newton=12,
-                                    max_krylov=2000, newton_rtol=1e-8, krylov_rtol=1e-3)
+                                    max_krylov=2000, newton_rtol=1e-8, krylov_rtol=1e-3,
+                                    precond=precond)
     assert code == 0 and rep["converged"] == 1
     y_gpu = H(dev["y"])
     r_check = np.linalg.norm(P.residual(y_gpu))
