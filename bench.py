@@ -598,7 +598,7 @@ def newton_section(args, dev, stream):
                                         dtype=torch.int64).to(torch.int32)
                     Xf = torch.empty((per_step, 112), dtype=torch.float32, device=dev)
                 fsi.fsi_mlp_features(ch.mesh, ch.Vn, ch.yn, ch.d1, ch.d2, idx, zeros, ones, Xf)
-            fsi.fsi_newton_step(ch.mesh, st, mixed=True, **solve)
+            fsi.fsi_newton_step(ch.mesh, st, mixed=True, residual_prec=fsi.FSI_DF64, **solve)
             if k >= 2:
                 with torch.cuda.stream(stream):
                     dn = (y - ch.yn)[idx.long()]
@@ -645,7 +645,7 @@ def newton_section(args, dev, stream):
     ch = Channel(fsi, dev, stream, args.newton_grid, args.newton_points, SEED + 60)
     for _ in range(args.newton_warm):
         y, st = ch.state()
-        fsi.fsi_newton_step(ch.mesh, st, mixed=True, **solve)
+        fsi.fsi_newton_step(ch.mesh, st, mixed=True, residual_prec=fsi.FSI_DF64, **solve)
         ch.advance(y)
     work = torch.empty((5, ch.n, 4), dtype=torch.float64, device=dev)
     out = {"grid": [ch.N] * 3, "dofs": 4 * ch.n, "points": ch.m, "dt": ch.dt, "mu": 1e-3,
@@ -661,6 +661,9 @@ def newton_section(args, dev, stream):
     out["preconditioner"] = ("block-diagonal Schur complement: 3x3 velocity blocks + one "
                              "pressure multigrid V-cycle (mixed_block_jacobi: nodal 4x4 "
                              "block-Jacobi)")
+    out["residual"] = ("fp64: native FP64 residual; mixed variants: FP64-accurate double-float "
+                       "residual (VMS, interp, spread; ~1e-14 vs FP64), also for the predictor's "
+                       "judge")
     r_ref = None
     for name, mixed, guess_kind, pc in variants:
         y, st = ch.state("zero" if guess_kind == "zero" else "extrapolated")
@@ -670,9 +673,12 @@ def newton_section(args, dev, stream):
         if guess_kind == "learned":
             guess = fsi.fsi_mlp_guess(h, ch.mesh, P, im.float().contiguous(),
                                       isd.float().contiguous(), om.contiguous(), osd.contiguous(),
-                                      st, ch.yn, ch.d1, ch.d2, 1, work)
+                                      st, ch.yn, ch.d1, ch.d2, 1, work,
+                                      judge_prec=fsi.FSI_DF64)
         code, rep = fsi.fsi_newton_step(ch.mesh, st, mixed=mixed, r_ref=r_ref or 0.0,
-                                        check=False, precond=pc, **solve)
+                                        check=False, precond=pc,
+                                        residual_prec=fsi.FSI_DF64 if mixed else fsi.FSI_F64,
+                                        **solve)
         stream.synchronize()
         el = time.perf_counter() - t0
         if r_ref is None:

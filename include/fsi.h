@@ -244,10 +244,14 @@ typedef struct {
     double g_s[3];
 } fsi_step_state;
 
-/* Full FP64 residual of the reduced system (Sec. 2.4) at st->y:
+/* Full residual of the reduced system (Sec. 2.4) at st->y:
  * R = [R^{f,m} + C W r^s ; R^{f,c}] with Dirichlet rows replaced by y - yD.
- * R [n][4] FP64 device, overwritten.                                       */
-fsi_status fsi_coupled_residual(fsi_mesh *mesh, const fsi_step_state *st, double *R);
+ * R [n][4] FP64 device, overwritten.  prec = FSI_F64 computes in native FP64,
+ * FSI_DF64 the VMS residual, interpolation and spreading in double-float
+ * (FP64-accurate to ~1e-14 relative, several times faster on GB300); the
+ * stage values and the solid force are FP64 in both.                       */
+fsi_status fsi_coupled_residual(fsi_mesh *mesh, fsi_prec prec, const fsi_step_state *st,
+                                double *R);
 
 /* Jacobian-vector product of fsi_coupled_residual at st->y in `prec`:
  * Jx = J_f x + C W (drho_s + k_s gamma dt^2) C^T x_v, with Dirichlet rows
@@ -294,6 +298,9 @@ typedef struct {
                               blocks, pressure Schur complement approximated
                               by sigma (K + kappa M) and inverted by one
                               multigrid V-cycle; see fsi_pressure_vcycle)     */
+    int32_t residual_prec; /* FSI_F64 or FSI_DF64: arithmetic of the Newton
+                              residual (see fsi_coupled_residual)             */
+    int32_t reserved;
 } fsi_newton_opts;
 
 typedef struct {
@@ -415,7 +422,8 @@ fsi_status fsi_mlp_predict(fsi_mlp *mlp, fsi_mesh *mesh, const float *params,
  * y_fb + d_v, y_fb + d_p, y_ml and y_c = y_fb + a d_v + b d_p, where (a, b)
  * minimise |R(y_fb) + a (R(y_fb+d_v) - R(y_fb)) + b (R(y_fb+d_p) - R(y_fb))|
  * (R is close to linear in y over a predictor's error), and leaves in st->y
- * whichever of y_fb, y_ml, y_c has the smallest residual norm.
+ * whichever of y_fb, y_ml, y_c has the smallest residual norm.  judge_prec
+ * (FSI_F64 or FSI_DF64) is the residual's arithmetic (fsi_coupled_residual).
  * work: caller-owned FP64 device array [5][n][4].  yn [n][4] is y_n (must not
  * alias st->y).  Synchronises.                                             */
 typedef struct {
@@ -430,7 +438,8 @@ typedef struct {
 fsi_status fsi_mlp_guess(fsi_mlp *mlp, fsi_mesh *mesh, const float *params, const float *in_mean,
                          const float *in_std, const float *out_mean, const float *out_std,
                          const fsi_step_state *st, const double *yn, const double *d1,
-                         const double *d2, int fallback, double *work, fsi_guess_report *rep);
+                         const double *d2, int fallback, fsi_prec judge_prec, double *work,
+                         fsi_guess_report *rep);
 
 /* ----------------------------------------------------------------------- */
 /* Batched ensemble (an extension; the paper has no counterpart).           */

@@ -53,7 +53,8 @@ class fsi_newton_opts(ctypes.Structure):
                 ("max_newton", ctypes.c_int32), ("max_krylov", ctypes.c_int32),
                 ("newton_rtol", ctypes.c_double), ("krylov_rtol", ctypes.c_double),
                 ("r_ref", ctypes.c_double), ("precond_every", ctypes.c_int32),
-                ("precond", ctypes.c_int32)]
+                ("precond", ctypes.c_int32), ("residual_prec", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class fsi_newton_report(ctypes.Structure):
@@ -117,7 +118,7 @@ _SIGS = {
     "fsi_dlm_interp": ([_VP, _INT, _I64, _VP, _VP, _VP, _VP], _INT),
     "fsi_dlm_spread": ([_VP, _INT, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _INT], _INT),
     "fsi_measure_fma_peak": ([_INT, _INT, ctypes.POINTER(ctypes.c_double)], _INT),
-    "fsi_coupled_residual": ([_VP, ctypes.POINTER(fsi_step_state), _VP], _INT),
+    "fsi_coupled_residual": ([_VP, _INT, ctypes.POINTER(fsi_step_state), _VP], _INT),
     "fsi_coupled_jacobian_apply": ([_VP, _INT, ctypes.POINTER(fsi_step_state), _VP, _VP], _INT),
     "fsi_block_diagonal": ([_VP, _INT, ctypes.POINTER(fsi_step_state), _VP], _INT),
     "fsi_newton_step": ([_VP, ctypes.POINTER(fsi_newton_opts), ctypes.POINTER(fsi_step_state),
@@ -141,7 +142,7 @@ _SIGS = {
     "fsi_mlp_features": ([_VP, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP], _INT),
     "fsi_mlp_predict": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _INT),
     "fsi_mlp_guess": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(fsi_step_state), _VP,
-                       _VP, _VP, _INT, _VP, ctypes.POINTER(fsi_guess_report)], _INT),
+                       _VP, _VP, _INT, _INT, _VP, ctypes.POINTER(fsi_guess_report)], _INT),
     "fsi_advance_history": ([_VP, _INT, _VP, _VP, _VP], _INT),
     "fsi_batch_create": ([ctypes.POINTER(_VP), ctypes.POINTER(fsi_batch_item), _INT, _INT, _VP,
                           ctypes.POINTER(_VP)], _INT),
@@ -323,9 +324,10 @@ class StepState:
             _ptr(w, f64), float(drho_s), float(k_s), (ctypes.c_double * 3)(*g_s))
 
 
-def fsi_coupled_residual(mesh: Mesh, st: StepState, R):
+def fsi_coupled_residual(mesh: Mesh, st: StepState, R, prec=FSI_F64):
     import torch
-    _check(lib().fsi_coupled_residual(mesh.handle, ctypes.byref(st.c), _ptr(R, torch.float64)))
+    _check(lib().fsi_coupled_residual(mesh.handle, int(prec), ctypes.byref(st.c),
+                                      _ptr(R, torch.float64)))
 
 
 def fsi_coupled_jacobian_apply(mesh: Mesh, prec, st: StepState, x, Jx):
@@ -344,10 +346,10 @@ PRECOND_BLOCK_JACOBI, PRECOND_SCHUR = 0, 1
 
 def fsi_newton_step(mesh: Mesh, st: StepState, mixed=True, restart=50, max_newton=10,
                     max_krylov=1000, newton_rtol=1e-8, krylov_rtol=1e-3, r_ref=0.0,
-                    precond_every=0, precond=PRECOND_SCHUR, check=True):
+                    precond_every=0, precond=PRECOND_SCHUR, residual_prec=FSI_F64, check=True):
     """Returns (status, report dict); raises on error when check is True."""
     o = fsi_newton_opts(1 if mixed else 0, restart, max_newton, max_krylov, newton_rtol,
-                        krylov_rtol, r_ref, precond_every, int(precond))
+                        krylov_rtol, r_ref, precond_every, int(precond), int(residual_prec), 0)
     rep = fsi_newton_report()
     st_code = lib().fsi_newton_step(mesh.handle, ctypes.byref(o), ctypes.byref(st.c),
                                     ctypes.byref(rep))
@@ -449,14 +451,15 @@ def fsi_advance_history(mesh: Mesh, prec, y, Vn, An):
 
 
 def fsi_mlp_guess(mlp: Mlp, mesh: Mesh, params, in_mean, in_std, out_mean, out_std,
-                  st: "StepState", yn, d1, d2, fallback, work):
+                  st: "StepState", yn, d1, d2, fallback, work, judge_prec=FSI_F64):
     import torch
     d, f = torch.float64, torch.float32
     rep = fsi_guess_report()
     _check(lib().fsi_mlp_guess(mlp.handle, mesh.handle, _ptr(params, f), _ptr(in_mean, f),
                                _ptr(in_std, f), _ptr(out_mean, f), _ptr(out_std, f),
                                ctypes.byref(st.c), _ptr(yn, d), _ptr(d1, d), _ptr(d2, d),
-                               int(fallback), _ptr(work, d), ctypes.byref(rep)))
+                               int(fallback), int(judge_prec), _ptr(work, d),
+                               ctypes.byref(rep)))
     return {k: getattr(rep, k) for k, _ in fsi_guess_report._fields_ if k != "reserved"}
 
 

@@ -531,12 +531,15 @@ fsi_status fsi_mlp_predict(fsi_mlp *h, fsi_mesh *mesh, const float *params, cons
 fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const float *in_mean,
                          const float *in_std, const float *out_mean, const float *out_std,
                          const fsi_step_state *st, const double *yn, const double *d1,
-                         const double *d2, int fallback, double *work, fsi_guess_report *rep)
+                         const double *d2, int fallback, fsi_prec judge_prec, double *work,
+                         fsi_guess_report *rep)
 {
     FSI_TRY(validate_mesh(mesh));
     if (!h || !st || !st->y || !yn || !d1 || !d2 || !work || !rep)
         return set_error(FSI_ERR_ARG, "NULL argument");
     if (fallback != 0 && fallback != 1) return set_error(FSI_ERR_ARG, "fallback must be 0 or 1");
+    if (judge_prec != FSI_F64 && judge_prec != FSI_DF64)
+        return set_error(FSI_ERR_ARG, "judge_prec must be FSI_F64 or FSI_DF64");
     if (st->y == yn) return set_error(FSI_ERR_ARG, "st->y must not alias yn");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
     cudaStream_t s = mesh->stream;
@@ -556,7 +559,7 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
     fsi_step_state tmp = *st;
     auto residual = [&](const double *y, double *R) -> fsi_status {
         tmp.y = const_cast<double *>(y);
-        return fsi_coupled_residual(mesh, &tmp, R);
+        return fsi_coupled_residual(mesh, judge_prec, &tmp, R);
     };
     // residuals of y_fb, y_fb + d_v and y_fb + d_p (d = ml - y_fb split into
     // its velocity and pressure slots)

@@ -522,24 +522,27 @@ template <typename T> fsi_prec prec_of() { return sizeof(T) == 8 ? FSI_F64 : FSI
 
 // ------------------------------------------------------------ operators
 // FP64 coupled residual at st->y; leaves the FP64 stage in W.U, W.A.
-fsi_status coupled_residual_impl(fsi_mesh *mesh, const fsi_step_state *st, double *R)
+// prec: FSI_F64 (native FP64) or FSI_DF64 (double-float VMS and coupling
+// arithmetic on FP64 arrays, FP64-accurate to ~1e-14); stage and solid force in FP64
+fsi_status coupled_residual_impl(fsi_mesh *mesh, const fsi_step_state *st, double *R,
+                                 fsi_prec prec = FSI_F64)
 {
     Work &W = mesh->newton->w;
     cudaStream_t s = mesh->stream;
     const int64_t n = mesh->n_nodes;
     FSI_TRY(fsi_stage(mesh, FSI_F64, st->y, st->Vn, st->An, st->s, W.U, W.A));
-    FSI_TRY(vms_residual(mesh, FSI_F64, W.U, W.A, st->f, R));
+    FSI_TRY(vms_residual(mesh, prec, W.U, W.A, st->f, R));
     if (st->m > 0) {
         velocity_next_kernel<<<grid1d(n), 256, 0, s>>>(n, mesh->phys.dt, mesh->gamma, st->y,
                                                       st->Vn, st->An, W.V1);
         FSI_TRY(check_launch("velocity_next kernel"));
-        FSI_TRY(fsi_dlm_interp(mesh, FSI_F64, st->m, st->elem, st->xi, st->y, W.pa));
-        FSI_TRY(fsi_dlm_interp(mesh, FSI_F64, st->m, st->elem, st->xi, W.V1, W.pv));
+        FSI_TRY(fsi_dlm_interp(mesh, prec, st->m, st->elem, st->xi, st->y, W.pa));
+        FSI_TRY(fsi_dlm_interp(mesh, prec, st->m, st->elem, st->xi, W.V1, W.pv));
         solid_force_kernel<<<grid1d(st->m), 256, 0, s>>>(
             st->m, st->elem, W.pa, W.pv, st->drho_s, st->k_s * mesh->phys.dt, st->g_s[0],
             st->g_s[1], st->g_s[2], W.prs);
         FSI_TRY(check_launch("solid force kernel"));
-        FSI_TRY(fsi_dlm_spread(mesh, FSI_F64, st->m, st->elem, st->xi, st->cell_start, st->perm,
+        FSI_TRY(fsi_dlm_spread(mesh, prec, st->m, st->elem, st->xi, st->cell_start, st->perm,
                                W.prs, st->w, R, 1));
     }
     if (st->mask) {
@@ -597,8 +600,10 @@ fsi_status build_block_jacobi(fsi_mesh *mesh, const fsi_step_state *st, int prec
     const int n = (int)mesh->n_nodes;
     const int NX1 = mesh->grid.N[0] + 1, NY1 = mesh->grid.N[1] + 1;
     T *px = (T *)W.z, *pj = (T *)W.w;
+    // the Schur preconditioner needs only the 3x3 velocity blocks
+    const int ncomp = precond == 1 ? 3 : 4;
     for (int color = 0; color < 8; ++color)
-        for (int comp = 0; comp < 4; ++comp) {
+        for (int comp = 0; comp < ncomp; ++comp) {
             probe_fill_kernel<T><<<grid1d(n), 256, 0, s>>>(n, NX1, NY1, color, comp, px);
             FSI_TRY(check_launch("probe fill"));
             FSI_TRY(coupled_jacobian_impl<T>(mesh, st, px, pj));
@@ -803,7 +808,8 @@ fsi_status newton_impl(fsi_mesh *mesh, const fsi_newton_opts *o, const fsi_step_
     Work &W = mesh->newton->w;
     cudaStream_t s = mesh->stream;
     const int64_t len = 4 * mesh->n_nodes;
-    FSI_TRY(coupled_residual_impl(mesh, st, W.R));
+    const fsi_prec rp = o->residual_prec == FSI_DF64 ? FSI_DF64 : FSI_F64;
+    FSI_TRY(coupled_residual_impl(mesh, st, W.R, rp));
     double r = 0.0;
     FSI_TRY(norm2<double>(mesh, W.R, W.hcol));
     FSI_TRY(host_scalar(mesh, W.hcol, &r));
@@ -831,7 +837,7 @@ fsi_status newton_impl(fsi_mesh *mesh, const fsi_newton_opts *o, const fsi_step_
         add_to_f64_kernel<T><<<grid1d(len), 256, 0, s>>>(len, (const T *)W.x, st->y);
         FSI_TRY(check_launch("Newton update"));
         ++it;
-        FSI_TRY(coupled_residual_impl(mesh, st, W.R));
+        FSI_TRY(coupled_residual_impl(mesh, st, W.R, rp));
         FSI_TRY(norm2<double>(mesh, W.R, W.hcol));
         FSI_TRY(host_scalar(mesh, W.hcol, &r));
         rep->r_final = r;
@@ -865,14 +871,17 @@ using namespace fsi;
 
 extern "C" {
 
-fsi_status fsi_coupled_residual(fsi_mesh *mesh, const fsi_step_state *st, double *R)
+fsi_status fsi_coupled_residual(fsi_mesh *mesh, fsi_prec prec, const fsi_step_state *st,
+                                double *R)
 {
     FSI_TRY(validate_mesh(mesh));
     FSI_TRY(validate_state(mesh, st));
     if (!R) return set_error(FSI_ERR_ARG, "R is NULL");
+    if (prec != FSI_F64 && prec != FSI_DF64)
+        return set_error(FSI_ERR_ARG, "fsi_coupled_residual: precision must be FSI_F64 or FSI_DF64");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
     FSI_TRY(ensure_work(mesh, st->m, 1));
-    return coupled_residual_impl(mesh, st, R);
+    return coupled_residual_impl(mesh, st, R, prec);
 }
 
 fsi_status fsi_coupled_jacobian_apply(fsi_mesh *mesh, fsi_prec prec, const fsi_step_state *st,
@@ -926,7 +935,8 @@ fsi_status fsi_newton_step(fsi_mesh *mesh, const fsi_newton_opts *opts, const fs
     if (!opts || !report) return set_error(FSI_ERR_ARG, "opts or report is NULL");
     if (opts->restart < 1 || opts->restart > 200 || opts->max_newton < 0 ||
         opts->max_krylov < 1 || !(opts->newton_rtol > 0.0) || !(opts->krylov_rtol > 0.0) ||
-        opts->precond < 0 || opts->precond > 1)
+        opts->precond < 0 || opts->precond > 1 ||
+        (opts->residual_prec != FSI_F64 && opts->residual_prec != FSI_DF64))
         return set_error(FSI_ERR_ARG, "invalid Newton options");
     std::memset(report, 0, sizeof *report);
     const auto t0 = std::chrono::steady_clock::now();

@@ -74,11 +74,12 @@ def setup(fsi, oracle, N=8, m=300, seed=0, dt=0.01, k_s=2.0, mu=0.05, y_scale=1.
     return mesh, st, dev, P, y
 
 
-def test_coupled_residual_parity(fsi, oracle):
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_coupled_residual_parity(fsi, oracle, prec):
     import torch
     mesh, st, dev, P, y = setup(fsi, oracle)
     R = torch.empty_like(dev["y"])
-    fsi.fsi_coupled_residual(mesh, st, R)
+    fsi.fsi_coupled_residual(mesh, st, R, prec=fsi.FSI_F64 if prec == "f64" else fsi.FSI_DF64)
     torch.cuda.synchronize()
     assert rel(H(R), P.residual(y)) < 1e-12
 
@@ -113,16 +114,17 @@ def test_block_diagonal_parity(fsi, oracle):
     assert rel(H(B), ref) < 1e-12
 
 
-@pytest.mark.parametrize("precond", [0, 1])
-@pytest.mark.parametrize("mixed", [False, True])
-def test_newton_step_matches_direct_newton(fsi, oracle, mixed, precond):
-    """Both the plain FP64 and the mixed step, with either preconditioner, reach
-    ||R|| <= 1e-8 ||R0|| (FP64) and land on the oracle's direct-solve solution."""
+@pytest.mark.parametrize("mixed,precond,rprec", [(False, 0, 0), (True, 0, 0), (False, 1, 0),
+                                                 (True, 1, 0), (True, 1, 2)])
+def test_newton_step_matches_direct_newton(fsi, oracle, mixed, precond, rprec):
+    """The plain FP64 and the mixed step, with either preconditioner and an FP64
+    or double-float residual, reach ||R|| <= 1e-8 ||R0|| (checked with the
+    oracle's FP64 residual) and land on the oracle's direct-solve solution."""
     from oracle import newton
     mesh, st, dev, P, y0 = setup(fsi, oracle, seed=3)
     code, rep = fsi.fsi_newton_step(mesh, st, mixed=mixed, restart=50, max_newton=12,
                                     max_krylov=2000, newton_rtol=1e-8, krylov_rtol=1e-3,
-                                    precond=precond)
+                                    precond=precond, residual_prec=rprec)
     assert code == 0 and rep["converged"] == 1
     y_gpu = H(dev["y"])
     r_check = np.linalg.norm(P.residual(y_gpu))
