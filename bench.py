@@ -761,34 +761,66 @@ def batch_section(args, dev, stream):
 
 # ------------------------------------------------------------------ MLP inference
 def mlp_section(args, dev, stream, W):
+    """Per-node inference of the initial-guess network over whole grids: the
+    fused tcgen05 predictor (features, three layers, predictor in one
+    persistent kernel) against the unfused path of the training kernels
+    (features to HBM, then mma.sync GEMMs per chunk)."""
     import torch
     import paper_2601_08266_gb300 as fsi
-    N = W["N"]
-    mesh = fsi.Mesh(N, device=dev.index, stream=stream.cuda_stream)
-    n = mesh.n_nodes
-    with torch.cuda.stream(stream):
-        P = torch.randn(fsi.fsi_mlp_num_params(), device=dev) * 0.05
-        st = [torch.as_tensor(W[k], device=dev).contiguous() for k in ("Vn", "y", "An", "x")]
-        stats = [torch.zeros(112, device=dev), torch.ones(112, device=dev),
-                 torch.zeros(4, device=dev), torch.ones(4, device=dev)]
-        y0 = torch.empty((n, 4), dtype=torch.float64, device=dev)
-    h = fsi.Mlp(131072, device=dev.index, stream=stream.cuda_stream)
-    for _ in range(2):
-        fsi.fsi_mlp_predict(h, mesh, P, *stats, st[0], st[1], st[2], st[3], y0)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 5
-    e0.record(stream)
-    for _ in range(reps):
-        fsi.fsi_mlp_predict(h, mesh, P, *stats, st[0], st[1], st[2], st[3], y0)
-    e1.record(stream)
-    stream.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    flops = 2.0 * n * (112 * 256 + 256 * 256 + 256 * 4)
-    h.close()
-    mesh.close()
-    return {"nodes": n, "ms": ms, "tflop_s": flops / (ms * 1e-3) / 1e12,
-            "kernel": "mma.sync m16n8k16 BF16, FP32 accumulate"}
+    out = {"kernel": "fused: tcgen05.mma kind::f16 (BF16 in, FP32 accumulate in TMEM), weights "
+                     "resident in shared memory via cp.async.bulk; unfused: mma.sync m16n8k16"}
+    peaks = measured_peaks()
+    bf16_peak = peaks.get("bf16_tflops", 1865.6)
+    for N in (64, 128):
+        mesh = fsi.Mesh(N, device=dev.index, stream=stream.cuda_stream)
+        n = mesh.n_nodes
+        g = torch.Generator(device=dev).manual_seed(SEED + N)
+        with torch.cuda.stream(stream):
+            P = torch.randn(fsi.fsi_mlp_num_params(), device=dev, generator=g) * 0.05
+            st = [torch.randn((n, 4), dtype=torch.float64, device=dev, generator=g)
+                  for _ in range(4)]
+            stats = [torch.zeros(112, device=dev), torch.ones(112, device=dev),
+                     torch.zeros(4, device=dev), torch.ones(4, device=dev)]
+            y0 = torch.empty((n, 4), dtype=torch.float64, device=dev)
+        chunk = 131072
+        h = fsi.Mlp(chunk, device=dev.index, stream=stream.cuda_stream)
+        flops = 2.0 * n * (112 * 256 + 256 * 256 + 256 * 4)
 
+        def fused():
+            fsi.fsi_mlp_predict(h, mesh, P, *stats, st[0], st[1], st[2], st[3], y0)
+
+        with torch.cuda.stream(stream):
+            Xc = torch.empty((chunk, 112), dtype=torch.float32, device=dev)
+            Oc = torch.empty((chunk, 4), dtype=torch.float32, device=dev)
+            idxs = [torch.arange(b0, min(n, b0 + chunk), dtype=torch.int32, device=dev)
+                    for b0 in range(0, n, chunk)]
+
+        def unfused():
+            for idx in idxs:
+                k = idx.shape[0]
+                fsi.fsi_mlp_features(mesh, st[0], st[1], st[2], st[3], idx, stats[0], stats[1],
+                                     Xc[:k])
+                fsi.fsi_mlp_forward(h, P, Xc[:k], Oc[:k])
+        res = {"nodes": n}
+        for name, fn in (("fused_tcgen05", fused), ("unfused_mma_sync", unfused)):
+            for _ in range(2):
+                fn()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            res[name] = {"ms": ms, "tflop_s": flops / (ms * 1e-3) / 1e12,
+                         "frac_of_bf16_peak": flops / (ms * 1e-3) / 1e12 / bf16_peak}
+        out[f"{N}^3"] = res
+        h.close()
+        mesh.close()
+    out["bf16_peak_tflop_s"] = bf16_peak
+    return out
 
 
 def main():

@@ -99,6 +99,14 @@ template <typename T> fsi_status pmg_vcycle(fsi_mesh *m, const T *b, T *x);
 void *pmg_fine_buffer(fsi_mesh *m, int which);
 void destroy_pmg(fsi_mesh *m);
 
+// fused tensor-core inference of the initial-guess network (mlp_tc.cu)
+size_t mlp_tc_packed_bytes();
+fsi_status mlp_predict_tc(cudaStream_t s, int device, const fsi_grid &g, int64_t n,
+                          const float *params, const float *in_mean, const float *in_std,
+                          const float *out_mean, const float *out_std, const double *Vn,
+                          const double *y, const double *d1, const double *d2, double *y0,
+                          void *packed, int *dev_err);
+
 // VMS operators (vms.cu)
 fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
                         const void *f, void *R);

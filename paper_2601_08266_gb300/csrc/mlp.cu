@@ -24,6 +24,8 @@ struct fsi_mlp {
     float *Z1, *H1, *Z2, *H2, *O, *dO, *dZ1, *dZ2;
     float *X;       // features of a predict chunk [max_batch][112]
     double *loss_partial;
+    void *packed;   // BF16 weights in the tensor-core operand layout (mlp_tc.cu)
+    int *tc_err;    // wait-timeout flag of the tensor-core predict kernel
 };
 
 namespace fsi {
@@ -404,6 +406,8 @@ fsi_status fsi_mlp_create(int device, void *cuda_stream, int64_t max_batch, fsi_
         }
     }
     cudaError_t e = cudaMalloc(&h->loss_partial, 1024 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->packed, mlp_tc_packed_bytes());
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->tc_err, sizeof(int));
     if (e != cudaSuccess) {
         fsi_mlp_destroy(h);
         return check_cuda(e, "mlp allocation");
@@ -420,6 +424,8 @@ void fsi_mlp_destroy(fsi_mlp *h)
     float *ptrs[] = {h->Z1, h->H1, h->Z2, h->H2, h->O, h->dO, h->dZ1, h->dZ2, h->X};
     for (float *p : ptrs) cudaFree(p);
     cudaFree(h->loss_partial);
+    cudaFree(h->packed);
+    cudaFree(h->tc_err);
     delete h;
 }
 
@@ -507,25 +513,9 @@ fsi_status fsi_mlp_predict(fsi_mlp *h, fsi_mesh *mesh, const float *params, cons
         return set_error(FSI_ERR_ARG, "NULL argument");
     if (h->device != mesh->device) return set_error(FSI_ERR_ARG, "mlp and mesh on other devices");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
-    cudaStream_t s = mesh->stream;
-    const cudaStream_t saved = h->stream;
-    h->stream = s;
-    fsi_status st = FSI_OK;
-    for (int64_t base = 0; base < mesh->n_nodes && st == FSI_OK; base += h->max_batch) {
-        const int64_t k = mesh->n_nodes - base < h->max_batch ? mesh->n_nodes - base : h->max_batch;
-        features_kernel<<<blocks(k), 256, 0, s>>>(mesh->grid.N[0], mesh->grid.N[1],
-                                                 mesh->grid.N[2], base, k, nullptr, Vn, y, d1, d2,
-                                                 in_mean, in_std, h->X);
-        st = check_launch("features kernel");
-        if (st == FSI_OK) st = forward_impl(h, params, h->X, k, false);
-        if (st == FSI_OK) {
-            predict_combine_kernel<<<blocks(k), 256, 0, s>>>(base, k, y, d1, d2, h->O, out_mean,
-                                                            out_std, y0);
-            st = check_launch("predict combine kernel");
-        }
-    }
-    h->stream = saved;
-    return st;
+    // fused features -> network -> predictor on the tcgen05 tensor cores
+    return mlp_predict_tc(mesh->stream, mesh->device, mesh->grid, mesh->n_nodes, params, in_mean,
+                          in_std, out_mean, out_std, Vn, y, d1, d2, y0, h->packed, h->tc_err);
 }
 
 fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const float *in_mean,

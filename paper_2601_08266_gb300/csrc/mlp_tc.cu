@@ -1,0 +1,485 @@
+// mlp_tc.cu -- fused inference of the initial-guess network on the 5th-
+// generation tensor cores (tcgen05, TMEM accumulators).
+//
+// One persistent CTA per SM (128 threads, ~222 KB shared memory) processes
+// tiles of 128 nodes.  Thread t owns node row t of the tile, which is also
+// TMEM lane t of the accumulators.  Per tile:
+//
+//   features   each thread builds its node's 112 features (27-node stencil of
+//              V_n velocity and y_n pressure, the extrapolant 2 d1 - d2),
+//              normalised and rounded to BF16, into the A tile X [128 x 112];
+//   layer 1    D1 [128 x 256] (TMEM columns 0..255) = X W1^T: 7 MMAs of
+//              M=128, N=256, K=16 (kind::f16, BF16 in, FP32 accumulate);
+//   layer 2    H1 = BF16(ReLU(D1 + b1)) is written back to shared memory in
+//              two K-halves of 128 (the half buffer aliases X), each followed
+//              by 8 MMAs accumulating D2 (columns 256..511) = H1 W2^T; the
+//              second half is loaded from TMEM into registers while the MMAs of
+//              the first half run;
+//   layer 3    H2 = BF16(ReLU(D2 + b2)) stays in registers; the 4 outputs are
+//              FP32 dot products with the BF16 rows of W3 (+ b3), and the
+//              predictor y0 = y + e + (out_mean + out_std * out) is written in
+//              FP64.
+//
+// The BF16 rounding points are those of the training kernels (inputs and
+// weights of every layer).  Weights are packed once per call into the
+// no-swizzle K-major canonical layout of the UMMA shared-memory descriptors
+// (8-row x 16-byte core matrices; LBO = 128 B between core matrices along K,
+// SBO = 16 B x K between 8-row groups) and copied to shared memory with bulk
+// asynchronous copies.  Every wait is bounded: a wait that runs out sets an
+// error flag that the host reads, the CTA stops issuing work, waits (bounded)
+// for what it issued, frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "fsi_internal.cuh"
+
+namespace fsi {
+namespace {
+
+constexpr int NI = 112, NH = 256, NO = 4;
+constexpr int64_t OFF_W1 = 0, OFF_b1 = OFF_W1 + NI * NH, OFF_W2 = OFF_b1 + NH,
+                  OFF_b2 = OFF_W2 + NH * NH, OFF_W3 = OFF_b2 + NH, OFF_b3 = OFF_W3 + NH * NO;
+
+constexpr int TM = 128;                         // nodes per tile (MMA M)
+constexpr uint32_t KC1 = NI / 8, KC2 = 128 / 8;  // 16-byte K chunks: layer 1, half of layer 2
+constexpr uint32_t SZ_W1 = NH * NI * 2;          // 57,344
+constexpr uint32_t SZ_W2H = NH * 128 * 2;        // 65,536 (one K-half of W2)
+constexpr uint32_t SZ_XH = TM * 128 * 2;         // 32,768 (X [128 x 112] or H1 half)
+constexpr uint32_t OFF_SW1 = 0, OFF_SW2A = OFF_SW1 + SZ_W1, OFF_SW2B = OFF_SW2A + SZ_W2H,
+                   OFF_SXH = OFF_SW2B + SZ_W2H, OFF_SW3 = OFF_SXH + SZ_XH,
+                   OFF_SB1 = OFF_SW3 + NH * 16, OFF_SB2 = OFF_SB1 + NH * 4,
+                   SMEM_BYTES = OFF_SB2 + NH * 4;  // 227,328
+constexpr uint32_t PACKED_BYTES = SZ_W1 + 2 * SZ_W2H;  // 188,416
+constexpr uint32_t TMEM_COLS = 512;
+constexpr long long kWaitLimit = 4000000;  // try_wait polls (each suspends briefly)
+
+// byte offset of element (row, k) in a K-major canonical tile with kc chunks
+__host__ __device__ __forceinline__ uint32_t kmaj(uint32_t row, uint32_t k, uint32_t kc)
+{
+    return (row >> 3) * (kc * 128u) + (k >> 3) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// UMMA shared-memory descriptor: start, LBO, SBO (all >> 4), version 1 at
+// bit 46, no swizzle (layout type 0 in bits 61..63), base offset 0
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: D FP32 (bit 4), A and B BF16 (bits 7, 10),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NH >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait; false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (long long it = 0; it < kWaitLimit; ++it)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    const __nv_bfloat16 lo = __float2bfloat16_rn(a), hi = __float2bfloat16_rn(b);
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ float bf16r(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
+
+// W1 [NI][NH] and W2 [NH][NH] (input-major, as trained) -> B operands
+// [N = out][K = in] BF16 in the canonical layout: W1 (K = 112), then the two
+// K-halves of W2 (K = 0..127, 128..255)
+__global__ void pack_weights_kernel(const float *P, uint8_t *packed)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)NH * (NI + NH);
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(e % NH);
+        const int k = (int)(e / NH);
+        __nv_bfloat16 v;
+        uint32_t off;
+        if (k < NI) {
+            v = __float2bfloat16_rn(P[OFF_W1 + (int64_t)k * NH + n]);
+            off = OFF_SW1 + kmaj(n, k, KC1);
+        } else {
+            const int k2 = k - NI;
+            v = __float2bfloat16_rn(P[OFF_W2 + (int64_t)k2 * NH + n]);
+            off = (k2 < 128 ? OFF_SW2A : OFF_SW2B) + kmaj(n, k2 & 127, KC2);
+        }
+        *reinterpret_cast<__nv_bfloat16 *>(packed + off) = v;
+    }
+}
+
+struct TcArgs {
+    int Nx, Ny, Nz;
+    int64_t n;
+    const float *P;  // FP32 parameters (biases, W3)
+    const uint8_t *packed;
+    const float *in_mean, *in_std, *out_mean, *out_std;
+    const double *Vn, *y, *d1, *d2;
+    double *y0;
+    int *err;
+};
+
+__global__ void __launch_bounds__(128, 1) mlp_predict_tc_kernel(const TcArgs a)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    __shared__ __align__(8) uint64_t bars[2];  // [0] weights, [1] MMA completion
+    __shared__ uint32_t tmem_holder;
+    __shared__ int abort_flag;
+    __shared__ float smean[NI], sistd[NI];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t s0 = smem_u32(sm);
+    const uint32_t bar_w = smem_u32(&bars[0]), bar_m = smem_u32(&bars[1]);
+
+    if (tid == 0) {
+        abort_flag = 0;
+        mbar_init(bar_w, 1);
+        mbar_init(bar_m, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_async_smem();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // small operands: W3 (BF16-rounded, one float4 per hidden unit), b1, b2
+    float4 *sW3 = reinterpret_cast<float4 *>(sm + OFF_SW3);
+    float *sb1 = reinterpret_cast<float *>(sm + OFF_SB1), *sb2 = reinterpret_cast<float *>(sm + OFF_SB2);
+    for (int f = tid; f < NI; f += blockDim.x) {
+        smean[f] = a.in_mean[f];
+        sistd[f] = 1.0f / a.in_std[f];
+    }
+    for (int c = tid; c < NH; c += blockDim.x) {
+        const float *w = a.P + OFF_W3 + (int64_t)c * NO;
+        sW3[c] = make_float4(bf16r(w[0]), bf16r(w[1]), bf16r(w[2]), bf16r(w[3]));
+        sb1[c] = a.P[OFF_b1 + c];
+        sb2[c] = a.P[OFF_b2 + c];
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_holder;
+    // weights: bulk asynchronous copies into shared memory, once per CTA
+    if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w),
+                     "r"(PACKED_BYTES)
+                     : "memory");
+        for (uint32_t off = 0; off < PACKED_BYTES; off += 16384) {
+            const uint32_t bytes = PACKED_BYTES - off < 16384 ? PACKED_BYTES - off : 16384;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    s0 + off),
+                "l"(a.packed + off), "r"(bytes), "r"(bar_w)
+                : "memory");
+        }
+    }
+    uint32_t mma_phase = 0;
+    bool mma_pending = false;  // a commit was issued and not yet observed
+    const bool weights_ok = mbar_wait(bar_w, 0);
+    bool ok = weights_ok;
+    if (!ok) atomicExch(&abort_flag, 1);
+    __syncthreads();
+    const float b3[4] = {a.P[OFF_b3], a.P[OFF_b3 + 1], a.P[OFF_b3 + 2], a.P[OFF_b3 + 3]};
+    const float om[4] = {a.out_mean[0], a.out_mean[1], a.out_mean[2], a.out_mean[3]};
+    const float os[4] = {a.out_std[0], a.out_std[1], a.out_std[2], a.out_std[3]};
+    const int nx = a.Nx + 1, ny = a.Ny + 1, nz = a.Nz + 1;
+    const int64_t ntiles = (a.n + TM - 1) / TM;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    uint8_t *xh = sm + OFF_SXH;
+
+    for (int64_t tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+        const int64_t node = tile * TM + tid;
+        const bool live = node < a.n;
+        // ---- features -> X (BF16, canonical K-major, 14 chunks of 8).  The
+        // normalisation runs in FP32 ((value - mean) * (1 / std)): the result is
+        // rounded to BF16 right away, and GB300's FP64 unit is ~70x slower.
+        {
+            int i = 0, j = 0, k = 0;
+            if (live) {
+                i = (int)(node % nx);
+                j = (int)((node / nx) % ny);
+                k = (int)(node / ((int64_t)nx * ny));
+            }
+            float f8[8];
+            int q = 0;
+#pragma unroll
+            for (int s = 0; s < 27; ++s) {
+                const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+                const int ii = i + dx, jj = j + dy, kk = k + dz;
+                const bool in = live && ii >= 0 && ii < nx && jj >= 0 && jj < ny && kk >= 0 && kk < nz;
+                const int64_t nb = in ? ii + (int64_t)nx * (jj + (int64_t)ny * kk) : 0;
+                double raw[4] = {0.0, 0.0, 0.0, 0.0};
+                if (in) {
+                    const double2 v01 = __ldg(reinterpret_cast<const double2 *>(a.Vn + 4 * nb));
+                    raw[0] = v01.x;
+                    raw[1] = v01.y;
+                    raw[2] = __ldg(a.Vn + 4 * nb + 2);
+                    raw[3] = __ldg(a.y + 4 * nb + 3);
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int f = 4 * s + c;
+                    f8[q++] = live ? ((float)raw[c] - smean[f]) * sistd[f] : 0.0f;
+                    if (q == 8) {
+                        const uint4 v = make_uint4(pack_bf16(f8[0], f8[1]), pack_bf16(f8[2], f8[3]),
+                                                   pack_bf16(f8[4], f8[5]), pack_bf16(f8[6], f8[7]));
+                        *reinterpret_cast<uint4 *>(xh + kmaj(tid, f - 7, KC1)) = v;
+                        q = 0;
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int f = 108 + c;
+                const double e = live ? 2.0 * a.d1[4 * node + c] - a.d2[4 * node + c] : 0.0;
+                f8[q++] = live ? ((float)e - smean[f]) * sistd[f] : 0.0f;
+            }
+            const uint4 v = make_uint4(pack_bf16(f8[0], f8[1]), pack_bf16(f8[2], f8[3]),
+                                       pack_bf16(f8[4], f8[5]), pack_bf16(f8[6], f8[7]));
+            *reinterpret_cast<uint4 *>(xh + kmaj(tid, 104, KC1)) = v;
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        // ---- layer 1: D1 = X W1^T
+        if (tid == 0) {
+            fence_after();
+            for (uint32_t ks = 0; ks < NI / 16; ++ks)
+                mma_bf16(tmem + 0, sdesc(s0 + OFF_SXH + ks * 256, 128, KC1 * 128),
+                         sdesc(s0 + OFF_SW1 + ks * 256, 128, KC1 * 128), ks > 0);
+            mma_commit(bar_m);
+        }
+        mma_pending = true;
+        ok = mbar_wait(bar_m, mma_phase);
+        if (ok) {
+            mma_phase ^= 1;
+            mma_pending = false;
+        } else {
+            atomicExch(&abort_flag, 1);
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        fence_after();
+        // ---- H1, first K-half (columns 0..127) -> shared memory (aliases X)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float v[32];
+            tmem_ld32(tmem + lane_base + 32 * c, v);
+#pragma unroll
+            for (int q8 = 0; q8 < 4; ++q8) {
+                float h[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int col = 32 * c + 8 * q8 + t;
+                    h[t] = fmaxf(v[8 * q8 + t] + sb1[col], 0.0f);
+                }
+                *reinterpret_cast<uint4 *>(xh + kmaj(tid, 32 * c + 8 * q8, KC2)) =
+                    make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
+                               pack_bf16(h[6], h[7]));
+            }
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            for (uint32_t ks = 0; ks < 8; ++ks)
+                mma_bf16(tmem + NH, sdesc(s0 + OFF_SXH + ks * 256, 128, KC2 * 128),
+                         sdesc(s0 + OFF_SW2A + ks * 256, 128, KC2 * 128), ks > 0);
+            mma_commit(bar_m);
+        }
+        // second K-half of H1 into registers while those MMAs run
+        uint32_t hp[64];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float v[32];
+            tmem_ld32(tmem + lane_base + 128 + 32 * c, v);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int col = 128 + 32 * c + 2 * t;
+                hp[16 * c + t] = pack_bf16(fmaxf(v[2 * t] + sb1[col], 0.0f),
+                                           fmaxf(v[2 * t + 1] + sb1[col + 1], 0.0f));
+            }
+        }
+        mma_pending = true;
+        ok = mbar_wait(bar_m, mma_phase);
+        if (ok) {
+            mma_phase ^= 1;
+            mma_pending = false;
+        } else {
+            atomicExch(&abort_flag, 1);
+        }
+        __syncthreads();
+        if (abort_flag) break;
+#pragma unroll
+        for (int q8 = 0; q8 < 16; ++q8)
+            *reinterpret_cast<uint4 *>(xh + kmaj(tid, 8 * q8, KC2)) =
+                make_uint4(hp[4 * q8], hp[4 * q8 + 1], hp[4 * q8 + 2], hp[4 * q8 + 3]);
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            for (uint32_t ks = 0; ks < 8; ++ks)
+                mma_bf16(tmem + NH, sdesc(s0 + OFF_SXH + ks * 256, 128, KC2 * 128),
+                         sdesc(s0 + OFF_SW2B + ks * 256, 128, KC2 * 128), 1);
+            mma_commit(bar_m);
+        }
+        mma_pending = true;
+        ok = mbar_wait(bar_m, mma_phase);
+        if (ok) {
+            mma_phase ^= 1;
+            mma_pending = false;
+        } else {
+            atomicExch(&abort_flag, 1);
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        fence_after();
+        // ---- layer 3 and the predictor
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+            float v[32];
+            tmem_ld32(tmem + lane_base + NH + 32 * c, v);
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const int col = 32 * c + t;
+                const float h = bf16r(fmaxf(v[t] + sb2[col], 0.0f));
+                const float4 w = sW3[col];
+                o[0] = fmaf(h, w.x, o[0]);
+                o[1] = fmaf(h, w.y, o[1]);
+                o[2] = fmaf(h, w.z, o[2]);
+                o[3] = fmaf(h, w.w, o[3]);
+            }
+        }
+        if (live)
+            for (int c = 0; c < 4; ++c) {
+                const int64_t qn = 4 * node + c;
+                const double e = 2.0 * a.d1[qn] - a.d2[qn];
+                const float out = o[c] + b3[c];
+                a.y0[qn] = a.y[qn] + e + ((double)om[c] + (double)os[c] * (double)out);
+            }
+        // the next tile overwrites X (read by the finished MMAs) and D1
+        fence_before();
+        __syncthreads();
+    }
+    if (abort_flag && tid == 0) atomicExch(a.err, 1);
+    // nothing may still be in flight when the TMEM is freed: a CTA that gave
+    // up waits (bounded) for its last commit before releasing
+    if (abort_flag) {
+        if (mma_pending) mbar_wait(bar_m, mma_phase);
+        if (!weights_ok) mbar_wait(bar_w, 0);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+size_t mlp_tc_packed_bytes() { return PACKED_BYTES; }
+
+fsi_status mlp_predict_tc(cudaStream_t s, int device, const fsi_grid &g, int64_t n,
+                          const float *params, const float *in_mean, const float *in_std,
+                          const float *out_mean, const float *out_std, const double *Vn,
+                          const double *y, const double *d1, const double *d2, double *y0,
+                          void *packed, int *dev_err)
+{
+    if (n <= 0) return FSI_OK;
+    static bool attr_set[64] = {};
+    if (device >= 0 && device < 64 && !attr_set[device]) {
+        FSI_CUDA(cudaFuncSetAttribute(mlp_predict_tc_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
+                 "cudaFuncSetAttribute");
+        attr_set[device] = true;
+    }
+    int sms = 0;
+    FSI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device), "attribute");
+    pack_weights_kernel<<<152 * 4, 256, 0, s>>>(params, (uint8_t *)packed);
+    FSI_TRY(check_launch("pack weights"));
+    FSI_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(int), s), "memset");
+    TcArgs a{g.N[0], g.N[1], g.N[2], n, params, (const uint8_t *)packed, in_mean, in_std,
+             out_mean, out_std, Vn, y, d1, d2, y0, dev_err};
+    const int64_t tiles = (n + TM - 1) / TM;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    mlp_predict_tc_kernel<<<grid, 128, SMEM_BYTES, s>>>(a);
+    FSI_TRY(check_launch("tensor-core predict"));
+    int h = 0;
+    FSI_CUDA(cudaMemcpyAsync(&h, dev_err, sizeof h, cudaMemcpyDeviceToHost, s), "memcpy");
+    FSI_CUDA(cudaStreamSynchronize(s), "sync");
+    if (h) return set_error(FSI_ERR_TIMEOUT, "tensor-core predict: a wait ran out");
+    return FSI_OK;
+}
+
+}  // namespace fsi
