@@ -569,49 +569,10 @@ class Channel:
         self.mesh.close()
 
 
-def newton_section(args, dev, stream):
-    """Implicit steps of the channel flow with leaflets (Re ~ 1000, dt = 1e-3).
-    A BF16 network is trained on the GPU on node samples from plain-solver runs
-    on 64^3 grids with seeded leaflet positions, then applied on the 128^3 grid
-    with 1M points.  One step there is solved to ||R|| <= 1e-8 r_ref (r_ref =
-    residual of the extrapolated predictor) by plain FP64 Newton-GMRES, by the
-    mixed FP32/FP64 solver from the zero and the extrapolated guess, and by the
-    mixed solver from the learned guess."""
+def train_network(args, dev, stream, fsi, feats, targs, gen):
+    """Adam on the GPU (BF16 tensor-core forward/backward) over the collected
+    (features, correction) pairs; per-channel normalisation from the pairs."""
     import torch
-    import paper_2601_08266_gb300 as fsi
-    solve = dict(restart=50, max_newton=10, max_krylov=4000, newton_rtol=1e-8, krylov_rtol=1e-3)
-    zeros = torch.zeros(112, dtype=torch.float32, device=dev)
-    ones = torch.ones(112, dtype=torch.float32, device=dev)
-    gen = torch.Generator(device=dev).manual_seed(SEED)
-    # 1) training pairs from plain-solver runs on the training grid
-    t0 = time.perf_counter()
-    feats, targs = [], []
-    runs, steps = args.train_runs, args.train_steps
-    per_step = -(-args.train_samples // (runs * (steps - 2)))
-    for r in range(runs):
-        ch = Channel(fsi, dev, stream, args.train_grid, args.train_points, SEED + 40 + r)
-        for k in range(steps):
-            y, st = ch.state()
-            if k >= 2:
-                with torch.cuda.stream(stream):
-                    idx = torch.randint(0, ch.n, (per_step,), device=dev, generator=gen,
-                                        dtype=torch.int64).to(torch.int32)
-                    Xf = torch.empty((per_step, 112), dtype=torch.float32, device=dev)
-                fsi.fsi_mlp_features(ch.mesh, ch.Vn, ch.yn, ch.d1, ch.d2, idx, zeros, ones, Xf)
-            fsi.fsi_newton_step(ch.mesh, st, mixed=True, residual_prec=fsi.FSI_DF64, **solve)
-            if k >= 2:
-                with torch.cuda.stream(stream):
-                    dn = (y - ch.yn)[idx.long()]
-                    tg = dn - (2 * ch.d1 - ch.d2)[idx.long()]
-                    tg[ch.maskb[idx.long()]] = 0.0
-                    feats.append(Xf)
-                    targs.append(tg)
-            ch.advance(y)
-        ch.close()
-    stream.synchronize()
-    gen_s = time.perf_counter() - t0
-    # 2) training on the GPU (BF16 tensor-core forward/backward, Adam)
-    t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         Xa = torch.cat(feats)[:args.train_samples]
         Ca = torch.cat(targs)[:args.train_samples].float()
@@ -640,6 +601,61 @@ def newton_section(args, dev, stream):
             stream.synchronize()
             losses.append(float(loss.item()))
     stream.synchronize()
+    return h, P, im, isd, om, osd, Xn, losses
+
+
+def newton_section(args, dev, stream):
+    """Implicit steps of the channel flow with leaflets (Re ~ 1000, dt = 1e-3).
+    A BF16 network is trained on the GPU on node samples from plain-solver runs
+    on 64^3 grids with seeded leaflet positions, then applied on the 128^3 grid
+    with 1M points.  One step there is solved to ||R|| <= 1e-8 r_ref (r_ref =
+    residual of the extrapolated predictor) by plain FP64 Newton-GMRES, by the
+    mixed FP32/FP64 solver from the zero and the extrapolated guess, and by the
+    mixed solver from the learned guess."""
+    import torch
+    import paper_2601_08266_gb300 as fsi
+    solve = dict(restart=50, max_newton=10, max_krylov=4000, newton_rtol=1e-8, krylov_rtol=1e-3)
+    wanted = set(args.newton_variants.split(","))
+    learned = "mixed_learned" in wanted
+    zeros = torch.zeros(112, dtype=torch.float32, device=dev)
+    ones = torch.ones(112, dtype=torch.float32, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(SEED)
+    # 1) training pairs from plain-solver runs on the training grid
+    t0 = time.perf_counter()
+    feats, targs = [], []
+    runs, steps = (args.train_runs, args.train_steps) if learned else (0, 3)
+    per_step = -(-args.train_samples // (runs * (steps - 2))) if runs else 0
+    for r in range(runs):
+        ch = Channel(fsi, dev, stream, args.train_grid, args.train_points, SEED + 40 + r)
+        for k in range(steps):
+            y, st = ch.state()
+            if k >= 2:
+                with torch.cuda.stream(stream):
+                    idx = torch.randint(0, ch.n, (per_step,), device=dev, generator=gen,
+                                        dtype=torch.int64).to(torch.int32)
+                    Xf = torch.empty((per_step, 112), dtype=torch.float32, device=dev)
+                fsi.fsi_mlp_features(ch.mesh, ch.Vn, ch.yn, ch.d1, ch.d2, idx, zeros, ones, Xf)
+            fsi.fsi_newton_step(ch.mesh, st, mixed=True, residual_prec=fsi.FSI_DF64, **solve)
+            if k >= 2:
+                with torch.cuda.stream(stream):
+                    dn = (y - ch.yn)[idx.long()]
+                    tg = dn - (2 * ch.d1 - ch.d2)[idx.long()]
+                    tg[ch.maskb[idx.long()]] = 0.0
+                    feats.append(Xf)
+                    targs.append(tg)
+            ch.advance(y)
+        ch.close()
+    stream.synchronize()
+    gen_s = time.perf_counter() - t0
+    # 2) training on the GPU (BF16 tensor-core forward/backward, Adam)
+    t0 = time.perf_counter()
+    h = None
+    losses = []
+    Xn = torch.empty((0, 112), device=dev)
+    im = isd = om = osd = P = None
+    if learned:
+        h, P, im, isd, om, osd, Xn, losses = train_network(args, dev, stream, fsi, feats, targs,
+                                                          gen)
     train_s = time.perf_counter() - t0
     # 3) the evaluation grid: warm steps, then one step four ways
     ch = Channel(fsi, dev, stream, args.newton_grid, args.newton_points, SEED + 60)
@@ -658,6 +674,7 @@ def newton_section(args, dev, stream):
     variants = [("fp64", False, "extrapolated", S), ("mixed_zero_guess", True, "zero", S),
                 ("mixed", True, "extrapolated", S), ("mixed_learned", True, "learned", S),
                 ("mixed_block_jacobi", True, "extrapolated", BJ)]
+    variants = [v for v in variants if v[0] in wanted]
     out["preconditioner"] = ("block-diagonal Schur complement: 3x3 velocity blocks + one "
                              "pressure multigrid V-cycle (mixed_block_jacobi: nodal 4x4 "
                              "block-Jacobi)")
@@ -668,6 +685,7 @@ def newton_section(args, dev, stream):
     for name, mixed, guess_kind, pc in variants:
         y, st = ch.state("zero" if guess_kind == "zero" else "extrapolated")
         stream.synchronize()
+        torch.cuda.nvtx.range_push(f"newton_{name}")
         t0 = time.perf_counter()
         guess = None
         if guess_kind == "learned":
@@ -681,6 +699,7 @@ def newton_section(args, dev, stream):
                                         **solve)
         stream.synchronize()
         el = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
         if r_ref is None:
             r_ref = rep["r_ref"]
         out[name] = {"seconds": el, "newton_iters": rep["newton_iters"],
@@ -690,10 +709,16 @@ def newton_section(args, dev, stream):
         if guess is not None:
             out[name]["predictor"] = {k2: guess[k2] for k2 in ("r_fallback", "r_learned",
                                                                "r_combined", "used")}
-    out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
-    out["speedup_mixed_learned_vs_fp64"] = out["fp64"]["seconds"] / out["mixed_learned"]["seconds"]
-    out["speedup_learned_vs_extrapolated"] = out["mixed"]["seconds"] / out["mixed_learned"]["seconds"]
-    h.close()
+    if {"fp64", "mixed"} <= wanted:
+        out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    if {"fp64", "mixed_learned"} <= wanted:
+        out["speedup_mixed_learned_vs_fp64"] = (out["fp64"]["seconds"] /
+                                                out["mixed_learned"]["seconds"])
+    if {"mixed", "mixed_learned"} <= wanted:
+        out["speedup_learned_vs_extrapolated"] = (out["mixed"]["seconds"] /
+                                                  out["mixed_learned"]["seconds"])
+    if h is not None:
+        h.close()
     ch.close()
     return out
 
@@ -846,6 +871,9 @@ def main():
     ap.add_argument("--train-steps", type=int, default=6)
     ap.add_argument("--train-samples", type=int, default=50_000)
     ap.add_argument("--mlp-iters", type=int, default=600)
+    ap.add_argument("--newton-variants",
+                    default="fp64,mixed_zero_guess,mixed,mixed_learned,mixed_block_jacobi",
+                    help="comma-separated Newton variants to time")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--batch-tune-f64", action="store_true")

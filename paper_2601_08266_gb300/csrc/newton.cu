@@ -134,10 +134,11 @@ template <> struct DotAcc<float> {
     using type = df64;
 };
 
+// (index self_k, when in [k0, k0+cnt), stands for w itself: w . w)
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) multi_dot_partial_kernel(
     int k0, int cnt, int64_t len4, const vec4<T> *V, int64_t vstride, const vec4<T> *w,
-    double *partial)
+    double *partial, int self_k)
 {
     using Acc = typename DotAcc<T>::type;
     __shared__ double red[kDotGroup][kRedThreads / 32];
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kRedThreads) multi_dot_partial_kernel(
 #pragma unroll
         for (int j = 0; j < kDotGroup; ++j)
             if (j < cnt) {
-                const vec4<T> v = ld4(V + (int64_t)(k0 + j) * vstride + i);
+                const vec4<T> v = k0 + j == self_k ? wi : ld4(V + (int64_t)(k0 + j) * vstride + i);
                 dot_acc(acc[j], v.x, wi.x);
                 dot_acc(acc[j], v.y, wi.y);
                 dot_acc(acc[j], v.z, wi.z);
@@ -238,13 +239,14 @@ __global__ void multi_axpy_kernel(int cnt, int64_t len4, const vec4<T> *V, int64
     }
 }
 
-// y = x / *den (0 when the norm vanished: lucky breakdown)
+// y = x / *den (0 when the norm vanished: lucky breakdown), in the vector's
+// own precision (the scale is rounded once; GB300's FP64 unit is ~70x slower)
 template <typename T>
 __global__ void scale_by_inv_kernel(int64_t len, const double *den, const T *x, T *y)
 {
     const double d = *den;
-    const double s = d > 0.0 ? 1.0 / d : 0.0;
-    GRID_STRIDE(i, len) y[i] = (T)((double)x[i] * s);
+    const T s = (T)(d > 0.0 ? 1.0 / d : 0.0);
+    GRID_STRIDE(i, len) y[i] = x[i] * s;
 }
 
 // ------------------------------------------------------------ block Jacobi
@@ -447,6 +449,7 @@ struct Work {
     double *hcol = nullptr, *h2 = nullptr;  // [restart+2]
     double *hhost = nullptr;                // pinned
     int precond = 0;                        // 0 block-Jacobi, 1 Schur (pmg.cu)
+    int64_t reorth = 0;                     // second Gram-Schmidt passes taken
 };
 
 void free_work(Work &W)
@@ -636,9 +639,10 @@ fsi_status build_block_jacobi(fsi_mesh *mesh, const fsi_step_state *st, int prec
 }
 
 // ------------------------------------------------------------ Krylov helpers
+// out[k] = V_k . w for k < cnt (with self_k: out[self_k] = w . w)
 template <typename T>
 fsi_status multi_dot(fsi_mesh *mesh, int cnt, const T *V, int64_t ld, const T *w, double *out,
-                     int mode)
+                     int mode, int self_k = -1)
 {
     Work &W = mesh->newton->w;
     cudaStream_t s = mesh->stream;
@@ -646,7 +650,7 @@ fsi_status multi_dot(fsi_mesh *mesh, int cnt, const T *V, int64_t ld, const T *w
     for (int k0 = 0; k0 < cnt; k0 += kDotGroup) {
         const int c = cnt - k0 < kDotGroup ? cnt - k0 : kDotGroup;
         multi_dot_partial_kernel<T><<<kRedGrid, kRedThreads, 0, s>>>(
-            k0, c, len / 4, (const vec4<T> *)V, ld / 4, (const vec4<T> *)w, W.partial);
+            k0, c, len / 4, (const vec4<T> *)V, ld / 4, (const vec4<T> *)w, W.partial, self_k);
     }
     FSI_TRY(check_launch("multi-dot partial"));
     multi_dot_final_kernel<<<cnt, kRedThreads, 0, s>>>(cnt, W.partial, out, mode);
@@ -737,12 +741,24 @@ fsi_status gmres(fsi_mesh *mesh, const fsi_step_state *st, int restart, int max_
             T *Vj = V + (int64_t)j * ld;
             FSI_TRY(apply_precond<T>(mesh, st, Vj, z));
             FSI_TRY(coupled_jacobian_impl<T>(mesh, st, z, w));
-            // classical Gram-Schmidt with one reorthogonalisation
-            FSI_TRY(multi_dot<T>(mesh, j + 1, V, ld, w, W.hcol, 0));
+            // classical Gram-Schmidt, h = V^T w (and |w|^2 in the same pass), with
+            // a second pass only when Kahan's criterion flags a loss of
+            // orthogonality: |h|^2 > |w|^2 / 2, i.e. |w - V h| < |w| / sqrt(2)
+            FSI_TRY(multi_dot<T>(mesh, j + 2, V, ld, w, W.hcol, 0, j + 1));
+            FSI_CUDA(cudaMemcpyAsync(W.hhost, W.hcol, (j + 2) * sizeof(double),
+                                     cudaMemcpyDeviceToHost, s),
+                     "memcpy");
+            FSI_CUDA(cudaStreamSynchronize(s), "GMRES sync");
+            double hh = 0.0;
+            for (int i = 0; i <= j; ++i) hh += W.hhost[i] * W.hhost[i];
+            const bool reorth = !(hh <= 0.5 * W.hhost[j + 1]);
             multi_axpy<T>(s, j + 1, len, V, ld, W.hcol, w);
-            FSI_TRY(multi_dot<T>(mesh, j + 1, V, ld, w, W.h2, 0));
-            multi_axpy<T>(s, j + 1, len, V, ld, W.h2, w);
-            add_kernel<double><<<1, 64, 0, s>>>(j + 1, W.h2, W.hcol);
+            if (reorth) {
+                FSI_TRY(multi_dot<T>(mesh, j + 1, V, ld, w, W.h2, 0));
+                multi_axpy<T>(s, j + 1, len, V, ld, W.h2, w);
+                add_kernel<double><<<1, 64, 0, s>>>(j + 1, W.h2, W.hcol);
+                ++W.reorth;
+            }
             FSI_TRY(norm2<T>(mesh, w, W.hcol + j + 1));
             scale_by_inv_kernel<T><<<grid1d(len), 256, 0, s>>>(len, W.hcol + j + 1, w,
                                                               V + (int64_t)(j + 1) * ld);

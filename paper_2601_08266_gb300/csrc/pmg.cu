@@ -53,7 +53,10 @@ struct PmgLevel {
     double h[3];
     int64_t n;
     double hi;          // Chebyshev upper bound of D^{-1} A
-    void *b, *x, *r, *d;  // level vectors (8 bytes per entry: either precision fits)
+    // level vectors, 8 bytes per entry (either precision fits): right-hand
+    // side, solution, residual (also the second x buffer of the smoother),
+    // pre-smoothed iterate, two smoother directions, one more x buffer
+    void *b, *x, *r, *t, *d0, *d1, *xa;
 };
 
 struct PressureMG {
@@ -132,15 +135,22 @@ template <typename T> __device__ __forceinline__ T diag_of(const LevelArgs<T> &L
     return kx * my * mz + mx * ky * mz + mx * my * kz + L.kappa * mx * my * mz;
 }
 
-// (A x)_node for node (i, j, k): nine x-lines, each reduced with the 1D
-// stiffness and mass rows, then combined with the y/z coefficients.  Rows of
-// eliminated nodes keep only the diagonal; their columns are skipped.
+// (A v)_node for node (i, j, k), v = x + d (x == null: v = d; d == null:
+// v = x): nine x-lines, each reduced with the 1D stiffness and mass rows, then
+// combined with the y/z coefficients.  Rows of eliminated nodes keep only the
+// diagonal; their columns are skipped.
 template <typename T>
-__device__ __forceinline__ T apply_row(const LevelArgs<T> &L, const T *__restrict__ x, int i,
-                                       int j, int k)
+__device__ __forceinline__ T val(const T *__restrict__ x, const T *__restrict__ d, int64_t q)
+{
+    return x ? (d ? x[q] + d[q] : x[q]) : d[q];
+}
+
+template <typename T>
+__device__ __forceinline__ T apply_row(const LevelArgs<T> &L, const T *__restrict__ x,
+                                       const T *__restrict__ d, int i, int j, int k)
 {
     const int64_t node = i + (int64_t)L.NX1 * (j + (int64_t)L.NY1 * k);
-    if (eliminated(L, i, j, k)) return diag_of(L, i, j, k) * x[node];
+    if (eliminated(L, i, j, k)) return diag_of(L, i, j, k) * val(x, d, node);
     // the eliminated neighbours lie on faces: the lines that would touch them
     // are cut at i/j/k = 0 or N when the face is eliminated
     const int ilo = L.faces[0] ? 1 : 0, ihi = L.faces[1] ? L.NX1 - 2 : L.NX1 - 1;
@@ -157,14 +167,14 @@ __device__ __forceinline__ T apply_row(const LevelArgs<T> &L, const T *__restric
             if (jj < jlo || jj > jhi) continue;
             T my, ky;
             coef(L.a[1], j, dj, my, ky);
-            const T *row = x + (int64_t)L.NX1 * (jj + (int64_t)L.NY1 * kk);
+            const int64_t row = (int64_t)L.NX1 * (jj + (int64_t)L.NY1 * kk);
             T sK = T(0), sM = T(0);
             for (int di = -1; di <= 1; ++di) {
                 const int ii = i + di;
                 if (ii < ilo || ii > ihi) continue;
                 T mx, kx;
                 coef(L.a[0], i, di, mx, kx);
-                const T v = row[ii];
+                const T v = val(x, d, row + ii);
                 sK += kx * v;
                 sM += mx * v;
             }
@@ -174,87 +184,85 @@ __device__ __forceinline__ T apply_row(const LevelArgs<T> &L, const T *__restric
     return acc;
 }
 
-#define NODE_LOOP(L, node, i, j, k)                                                          \
-    const int64_t n_ = (int64_t)(L).NX1 * (L).NY1 * (L).NZ1;                                 \
-    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < n_;           \
-         node += (int64_t)gridDim.x * blockDim.x)                                            \
-        for (int i = (int)(node % (L).NX1), j = (int)((node / (L).NX1) % (L).NY1),          \
-                 k = (int)(node / ((int64_t)(L).NX1 * (L).NY1)), once_ = 1;                 \
-             once_; once_ = 0)
+// One thread per node on a 3D launch: x from the block/thread index, y and z
+// from the grid (no per-node division).
+#define NODE3(L, i, j, k)                                                                    \
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;  \
+    if (i >= (L).NX1) return;                                                             \
+    const int64_t node = i + (int64_t)(L).NX1 * (j + (int64_t)(L).NY1 * k)
 
 // y = A x (b == null) or y = b - A x
 template <typename T>
 __global__ void apply_kernel(LevelArgs<T> L, const T *__restrict__ x, const T *__restrict__ b,
                              T *__restrict__ y)
 {
-    NODE_LOOP(L, node, i, j, k)
-    {
-        const T ax = apply_row(L, x, i, j, k);
-        y[node] = b ? b[node] - ax : ax;
-    }
+    NODE3(L, i, j, k);
+    const T ax = apply_row(L, x, (const T *)nullptr, i, j, k);
+    y[node] = b ? b[node] - ax : ax;
 }
 
-// Chebyshev, first direction: d = D^{-1} (b - A x) / theta  (x == null: x = 0)
+// Chebyshev, first direction d0 = D^{-1} (b - A x) / theta (x == null: x = 0).
+// With x_out != null (degree 1) it writes x_out = x + d0 instead of d0.
 template <typename T>
-__global__ void cheb_first_kernel(LevelArgs<T> L, const T *__restrict__ b, const T *__restrict__ x,
-                                  T inv_theta, T *__restrict__ d)
+__global__ void cheb0_kernel(LevelArgs<T> L, const T *__restrict__ b, const T *__restrict__ x,
+                             T inv_theta, T *__restrict__ d_out, T *__restrict__ x_out)
 {
-    NODE_LOOP(L, node, i, j, k)
-    {
-        const T r = x ? b[node] - apply_row(L, x, i, j, k) : b[node];
-        d[node] = inv_theta * r / diag_of(L, i, j, k);
-    }
+    NODE3(L, i, j, k);
+    const T r = x ? b[node] - apply_row(L, x, (const T *)nullptr, i, j, k) : b[node];
+    const T d0 = inv_theta * r / diag_of(L, i, j, k);
+    if (x_out)
+        x_out[node] = x ? x[node] + d0 : d0;
+    else
+        d_out[node] = d0;
 }
 
-// d = c1 d + c2 D^{-1} (b - A x)   (in place on d: neighbours read x only)
+// One Chebyshev step from (x, d) of the previous step: x' = x + d,
+// d' = c1 d + c2 D^{-1} (b - A x'); writes (x', d'), or x' + d' into x_final
+// on the last step.  x == null stands for x = 0.
 template <typename T>
-__global__ void cheb_next_kernel(LevelArgs<T> L, const T *__restrict__ b, const T *__restrict__ x,
-                                 T c1, T c2, T *__restrict__ d)
+__global__ void cheb_step_kernel(LevelArgs<T> L, const T *__restrict__ b, const T *__restrict__ x,
+                                 const T *__restrict__ d, T c1, T c2, T *__restrict__ x_next,
+                                 T *__restrict__ d_next, T *__restrict__ x_final)
 {
-    NODE_LOOP(L, node, i, j, k)
-    {
-        const T r = b[node] - apply_row(L, x, i, j, k);
-        d[node] = c1 * d[node] + c2 * (r / diag_of(L, i, j, k));
+    NODE3(L, i, j, k);
+    const T xk = val(x, d, node);
+    const T r = b[node] - apply_row(L, x, d, i, j, k);
+    const T dn = c1 * d[node] + c2 * (r / diag_of(L, i, j, k));
+    if (x_final) {
+        x_final[node] = xk + dn;
+    } else {
+        x_next[node] = xk;
+        d_next[node] = dn;
     }
-}
-
-// x += d, or x = d when set
-template <typename T> __global__ void add_dir_kernel(int64_t n, const T *d, T *x, int set)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = set ? d[i] : x[i] + d[i];
 }
 
 // b_c = P^T r: each coarse node gathers the fine nodes within one fine cell,
-// weights 1 (coincident) and 1/2 (neighbour) per axis
+// weights 1 (coincident) and 1/2 (neighbour) per axis; zero on eliminated nodes
 template <typename T>
 __global__ void restrict_kernel(LevelArgs<T> F, LevelArgs<T> C, const T *__restrict__ r,
                                 T *__restrict__ bc)
 {
-    NODE_LOOP(C, node, I, J, K)
-    {
-        T acc = T(0);
-        for (int dk = -1; dk <= 1; ++dk) {
-            const int k = 2 * K + dk;
-            if (k < 0 || k >= F.NZ1) continue;
-            const T wk = dk ? T(0.5) : T(1);
-            for (int dj = -1; dj <= 1; ++dj) {
-                const int j = 2 * J + dj;
-                if (j < 0 || j >= F.NY1) continue;
-                const T wjk = (dj ? T(0.5) : T(1)) * wk;
-                const T *row = r + (int64_t)F.NX1 * (j + (int64_t)F.NY1 * k);
-                T s = T(0);
-                for (int di = -1; di <= 1; ++di) {
-                    const int i = 2 * I + di;
-                    if (i < 0 || i >= F.NX1) continue;
-                    s += (di ? T(0.5) : T(1)) * row[i];
-                }
-                acc += wjk * s;
+    NODE3(C, I, J, K);
+    T acc = T(0);
+    for (int dk = -1; dk <= 1; ++dk) {
+        const int k = 2 * K + dk;
+        if (k < 0 || k >= F.NZ1) continue;
+        const T wk = dk ? T(0.5) : T(1);
+        for (int dj = -1; dj <= 1; ++dj) {
+            const int j = 2 * J + dj;
+            if (j < 0 || j >= F.NY1) continue;
+            const T wjk = (dj ? T(0.5) : T(1)) * wk;
+            const T *row = r + (int64_t)F.NX1 * (j + (int64_t)F.NY1 * k);
+            T s = T(0);
+            for (int di = -1; di <= 1; ++di) {
+                const int i = 2 * I + di;
+                if (i < 0 || i >= F.NX1) continue;
+                s += (di ? T(0.5) : T(1)) * row[i];
             }
+            acc += wjk * s;
         }
-        bc[node] = eliminated(C, I, J, K) ? T(0) : acc;
     }
+    bc[node] = eliminated(C, I, J, K) ? T(0) : acc;
 }
 
 // x += P x_c: trilinear interpolation of the coarse correction
@@ -262,22 +270,27 @@ template <typename T>
 __global__ void prolong_kernel(LevelArgs<T> F, LevelArgs<T> C, const T *__restrict__ xc,
                                T *__restrict__ x)
 {
-    NODE_LOOP(F, node, i, j, k)
-    {
-        const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
-        const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
-        const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1),
-                wk = (k & 1) ? T(0.5) : T(1);
-        T acc = T(0);
-        for (int c = 0; c < nk; ++c)
-            for (int b = 0; b < nj; ++b) {
-                const T *row = xc + (int64_t)C.NX1 * ((j0 + b) + (int64_t)C.NY1 * (k0 + c));
-                T s = T(0);
-                for (int a = 0; a < ni; ++a) s += row[i0 + a];
-                acc += (wj * wk) * (wi * s);
-            }
-        x[node] += acc;
-    }
+    NODE3(F, i, j, k);
+    const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+    const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1),
+            wk = (k & 1) ? T(0.5) : T(1);
+    T acc = T(0);
+    for (int c = 0; c < nk; ++c)
+        for (int bb = 0; bb < nj; ++bb) {
+            const T *row = xc + (int64_t)C.NX1 * ((j0 + bb) + (int64_t)C.NY1 * (k0 + c));
+            T s = T(0);
+            for (int a = 0; a < ni; ++a) s += row[i0 + a];
+            acc += (wj * wk) * (wi * s);
+        }
+    x[node] += acc;
+}
+
+template <typename T> __global__ void copy_kernel(int64_t n, const T *a, T *b)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        b[q] = a[q];
 }
 
 // x = Ainv b on the coarsest grid: one warp per row, fixed reduction order
@@ -297,6 +310,13 @@ __global__ void dense_apply_kernel(int64_t nc, const T *__restrict__ Ainv, const
 }
 
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+
+constexpr int kRowThreads = 128;
+dim3 grid3(const PmgLevel &L)
+{
+    return dim3((unsigned)((L.N[0] + 1 + kRowThreads - 1) / kRowThreads), (unsigned)(L.N[1] + 1),
+                (unsigned)(L.N[2] + 1));
+}
 
 double spectrum_bound(const double h[3], double kappa)
 {
@@ -391,30 +411,41 @@ bool dense_inverse(const PmgLevel &L, double kappa, const int faces[6], std::vec
 
 template <typename T> T *vec(void *p) { return static_cast<T *>(p); }
 
-// Chebyshev semi-iteration of `degree` on level l: x <- x + p(D^{-1}A) (..),
-// from x = 0 when from_zero (x is then overwritten).
+// Chebyshev semi-iteration of `degree` on level l for A x = b over [lo, hi],
+// from x_in (null: zero) into x_out; x_out may equal x_in only for degree 1.
+// One kernel per step: step k reads (x_{k-1}, d_{k-1}) and writes
+// (x_k, d_k) to the other buffers of a ping-pong pair; the last step writes
+// x_m = x_{m-1} + d_{m-1} straight into x_out.
 template <typename T>
-fsi_status chebyshev(fsi_mesh *m, int l, int degree, double lo, double hi, const T *b, T *x,
-                     bool from_zero)
+fsi_status chebyshev(fsi_mesh *m, int l, int degree, double lo, double hi, const T *b,
+                     const T *x_in, T *x_out)
 {
     PressureMG &P = *m->pmg;
     PmgLevel &L = P.lev[l];
     const LevelArgs<T> A = level_args<T>(P, l);
     cudaStream_t s = m->stream;
-    const int g = grid_for(L.n);
+    const dim3 g = grid3(L);
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), s1 = theta / delta;
-    T *d = vec<T>(L.d);
-    cheb_first_kernel<T><<<g, 256, 0, s>>>(A, b, from_zero ? nullptr : x, (T)(1.0 / theta), d);
+    if (degree == 1) {
+        cheb0_kernel<T><<<g, kRowThreads, 0, s>>>(A, b, x_in, (T)(1.0 / theta), nullptr, x_out);
+        return check_launch("pressure smoother");
+    }
+    T *dbuf[2] = {vec<T>(L.d0), vec<T>(L.d1)}, *xbuf[2] = {vec<T>(L.xa), vec<T>(L.r)};
+    cheb0_kernel<T><<<g, kRowThreads, 0, s>>>(A, b, x_in, (T)(1.0 / theta), dbuf[0], nullptr);
+    const T *xc = x_in;
+    const T *dc = dbuf[0];
     double rho = 1.0 / s1;
-    bool set = from_zero;
     for (int it = 1; it < degree; ++it) {
-        add_dir_kernel<T><<<g, 256, 0, s>>>(L.n, d, x, set ? 1 : 0);
-        set = false;
         const double rho_new = 1.0 / (2.0 * s1 - rho);
-        cheb_next_kernel<T><<<g, 256, 0, s>>>(A, b, x, (T)(rho_new * rho), (T)(2.0 * rho_new / delta), d);
+        const T c1 = (T)(rho_new * rho), c2 = (T)(2.0 * rho_new / delta);
+        const bool last = it == degree - 1;
+        T *xn = xbuf[it & 1], *dn = dbuf[it & 1];
+        cheb_step_kernel<T><<<g, kRowThreads, 0, s>>>(A, b, xc, dc, c1, c2, last ? nullptr : xn,
+                                                      last ? nullptr : dn, last ? x_out : nullptr);
+        xc = xn;
+        dc = dn;
         rho = rho_new;
     }
-    add_dir_kernel<T><<<g, 256, 0, s>>>(L.n, d, x, set ? 1 : 0);
     return check_launch("pressure smoother");
 }
 
@@ -429,24 +460,27 @@ template <typename T> fsi_status coarse_solve(fsi_mesh *m, const T *b, T *x)
         dense_apply_kernel<T><<<blocks, 32 * warps_per_block, 0, m->stream>>>(P.nc, inv, b, x);
         return check_launch("pressure coarse solve");
     }
-    return chebyshev<T>(m, l, kPmgCoarseDegree, P.lev[l].hi / 30.0, P.lev[l].hi, b, x, true);
+    return chebyshev<T>(m, l, kPmgCoarseDegree, P.lev[l].hi / 30.0, P.lev[l].hi, b, nullptr, x);
 }
 
+// x = V_l(b): pre-smoothing from zero into t, residual, restriction, the
+// coarse cycle, prolongation into t, post-smoothing from t into x
 template <typename T> fsi_status vcycle_level(fsi_mesh *m, int l, const T *b, T *x)
 {
     PressureMG &P = *m->pmg;
     if (l == P.nlev - 1) return coarse_solve<T>(m, b, x);
     PmgLevel &L = P.lev[l], &Lc = P.lev[l + 1];
     const double hi = L.hi;
-    FSI_TRY(chebyshev<T>(m, l, kPmgNu, hi / 4.0, hi, b, x, true));
+    T *t = vec<T>(L.t);
+    FSI_TRY(chebyshev<T>(m, l, kPmgNu, hi / 4.0, hi, b, (const T *)nullptr, t));
     const LevelArgs<T> A = level_args<T>(P, l), Ac = level_args<T>(P, l + 1);
-    apply_kernel<T><<<grid_for(L.n), 256, 0, m->stream>>>(A, x, b, vec<T>(L.r));
-    restrict_kernel<T><<<grid_for(Lc.n), 256, 0, m->stream>>>(A, Ac, vec<T>(L.r), vec<T>(Lc.b));
+    apply_kernel<T><<<grid3(L), kRowThreads, 0, m->stream>>>(A, t, b, vec<T>(L.r));
+    restrict_kernel<T><<<grid3(Lc), kRowThreads, 0, m->stream>>>(A, Ac, vec<T>(L.r), vec<T>(Lc.b));
     FSI_TRY(check_launch("pressure restrict"));
     FSI_TRY(vcycle_level<T>(m, l + 1, vec<T>(Lc.b), vec<T>(Lc.x)));
-    prolong_kernel<T><<<grid_for(L.n), 256, 0, m->stream>>>(A, Ac, vec<T>(Lc.x), x);
+    prolong_kernel<T><<<grid3(L), kRowThreads, 0, m->stream>>>(A, Ac, vec<T>(Lc.x), t);
     FSI_TRY(check_launch("pressure prolong"));
-    return chebyshev<T>(m, l, kPmgNu, hi / 4.0, hi, b, x, false);
+    return chebyshev<T>(m, l, kPmgNu, hi / 4.0, hi, b, t, x);
 }
 
 fsi_status check_prec(fsi_prec p)
@@ -469,10 +503,9 @@ void destroy_pmg(fsi_mesh *m)
     if (!m->pmg) return;
     PressureMG &P = *m->pmg;
     for (int l = 0; l < P.nlev; ++l) {
-        cudaFree(P.lev[l].b);
-        cudaFree(P.lev[l].x);
-        cudaFree(P.lev[l].r);
-        cudaFree(P.lev[l].d);
+        void *bufs[] = {P.lev[l].b, P.lev[l].x, P.lev[l].r, P.lev[l].t,
+                        P.lev[l].d0, P.lev[l].d1, P.lev[l].xa};
+        for (void *q : bufs) cudaFree(q);
     }
     cudaFree(P.inv64);
     cudaFree(P.inv32);
@@ -508,6 +541,10 @@ fsi_status pmg_ensure(fsi_mesh *m)
     for (int d = 0; d < 3; ++d) Lmax = std::max(Lmax, m->grid.N[d] * m->grid.h[d]);
     const double q = 3.14159265358979323846 / (2.0 * Lmax);
     P->kappa = q * q;
+    if (m->grid.N[1] + 1 > 65535 || m->grid.N[2] + 1 > 65535) {
+        destroy_pmg(m);
+        return set_error(FSI_ERR_ARG, "pressure hierarchy: at most 65535 nodes along y and z");
+    }
     PmgLevel cur{};
     for (int d = 0; d < 3; ++d) {
         cur.N[d] = m->grid.N[d];
@@ -526,7 +563,8 @@ fsi_status pmg_ensure(fsi_mesh *m)
     }
     for (int l = 0; l < P->nlev; ++l) {
         const size_t bytes = (size_t)P->lev[l].n * sizeof(double);
-        void **bufs[] = {&P->lev[l].b, &P->lev[l].x, &P->lev[l].r, &P->lev[l].d};
+        void **bufs[] = {&P->lev[l].b,  &P->lev[l].x,  &P->lev[l].r, &P->lev[l].t,
+                         &P->lev[l].d0, &P->lev[l].d1, &P->lev[l].xa};
         for (void **b : bufs) {
             *b = nullptr;
             if (cudaMalloc(b, bytes) != cudaSuccess) {
@@ -618,13 +656,13 @@ fsi_status fsi_pressure_apply(fsi_mesh *mesh, fsi_prec prec, int32_t level, cons
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, false));
-    const int g = grid_for(mesh->pmg->lev[level].n);
+    const dim3 g = grid3(mesh->pmg->lev[level]);
     if (prec == FSI_F64)
-        apply_kernel<double><<<g, 256, 0, mesh->stream>>>(level_args<double>(*mesh->pmg, level),
-                                                         (const double *)x, nullptr, (double *)y);
+        apply_kernel<double><<<g, kRowThreads, 0, mesh->stream>>>(
+            level_args<double>(*mesh->pmg, level), (const double *)x, nullptr, (double *)y);
     else
-        apply_kernel<float><<<g, 256, 0, mesh->stream>>>(level_args<float>(*mesh->pmg, level),
-                                                        (const float *)x, nullptr, (float *)y);
+        apply_kernel<float><<<g, kRowThreads, 0, mesh->stream>>>(
+            level_args<float>(*mesh->pmg, level), (const float *)x, nullptr, (float *)y);
     return check_launch("pressure apply");
 }
 
@@ -638,13 +676,13 @@ fsi_status fsi_pressure_restrict(fsi_mesh *mesh, fsi_prec prec, int32_t level, c
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, true));
     PressureMG &P = *mesh->pmg;
-    const int g = grid_for(P.lev[level + 1].n);
+    const dim3 g = grid3(P.lev[level + 1]);
     if (prec == FSI_F64)
-        restrict_kernel<double><<<g, 256, 0, mesh->stream>>>(
+        restrict_kernel<double><<<g, kRowThreads, 0, mesh->stream>>>(
             level_args<double>(P, level), level_args<double>(P, level + 1), (const double *)r,
             (double *)b);
     else
-        restrict_kernel<float><<<g, 256, 0, mesh->stream>>>(
+        restrict_kernel<float><<<g, kRowThreads, 0, mesh->stream>>>(
             level_args<float>(P, level), level_args<float>(P, level + 1), (const float *)r,
             (float *)b);
     return check_launch("pressure restrict");
@@ -660,13 +698,13 @@ fsi_status fsi_pressure_prolong_add(fsi_mesh *mesh, fsi_prec prec, int32_t level
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, true));
     PressureMG &P = *mesh->pmg;
-    const int g = grid_for(P.lev[level].n);
+    const dim3 g = grid3(P.lev[level]);
     if (prec == FSI_F64)
-        prolong_kernel<double><<<g, 256, 0, mesh->stream>>>(
+        prolong_kernel<double><<<g, kRowThreads, 0, mesh->stream>>>(
             level_args<double>(P, level), level_args<double>(P, level + 1), (const double *)xc,
             (double *)x);
     else
-        prolong_kernel<float><<<g, 256, 0, mesh->stream>>>(
+        prolong_kernel<float><<<g, kRowThreads, 0, mesh->stream>>>(
             level_args<float>(P, level), level_args<float>(P, level + 1), (const float *)xc,
             (float *)x);
     return check_launch("pressure prolong");
@@ -683,11 +721,26 @@ fsi_status fsi_pressure_smooth(fsi_mesh *mesh, fsi_prec prec, int32_t level, int
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, false));
     const double hi = mesh->pmg->lev[level].hi;
-    if (prec == FSI_F64)
-        return chebyshev<double>(mesh, level, degree, hi / 4.0, hi, (const double *)b,
-                                 (double *)x, from_zero != 0);
-    return chebyshev<float>(mesh, level, degree, hi / 4.0, hi, (const float *)b, (float *)x,
-                            from_zero != 0);
+    const int64_t n = mesh->pmg->lev[level].n;
+    // from a given x: the iteration reads x while it writes the result, so
+    // it starts from a copy in the level's t buffer
+    if (prec == FSI_F64) {
+        const double *xin = nullptr;
+        if (!from_zero) {
+            copy_kernel<double><<<grid_for(n), 256, 0, mesh->stream>>>(
+                n, (const double *)x, (double *)mesh->pmg->lev[level].t);
+            xin = (const double *)mesh->pmg->lev[level].t;
+        }
+        return chebyshev<double>(mesh, level, degree, hi / 4.0, hi, (const double *)b, xin,
+                                 (double *)x);
+    }
+    const float *xin = nullptr;
+    if (!from_zero) {
+        copy_kernel<float><<<grid_for(n), 256, 0, mesh->stream>>>(
+            n, (const float *)x, (float *)mesh->pmg->lev[level].t);
+        xin = (const float *)mesh->pmg->lev[level].t;
+    }
+    return chebyshev<float>(mesh, level, degree, hi / 4.0, hi, (const float *)b, xin, (float *)x);
 }
 
 fsi_status fsi_pressure_vcycle(fsi_mesh *mesh, fsi_prec prec, const void *b, void *x)
