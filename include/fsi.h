@@ -191,6 +191,19 @@ fsi_status fsi_locate_noalloc(const fsi_grid *grid, int64_t m, const double *X, 
                               double *xi, int32_t *cell_start, int32_t *perm,
                               int64_t *n_outside, int strict, int device, void *cuda_stream);
 
+/* Interface scaling field of Sec. 2.1: tau_M's bracket is multiplied by s,
+ * s >> 1 in an O(h) neighbourhood of the fluid-solid interface and 1
+ * elsewhere, defined at the fluid nodes and interpolated like the pressure
+ * (Q1), which gives a smooth transition over one element.  The paper fixes no
+ * band width; here the band is every cell holding a solid point, dilated by
+ * `layers` cells in each direction (clipped at the grid), and
+ * s [n] (FP64 device, overwritten) = s_band on every node of a band cell, 1
+ * elsewhere.  cell_start [E+1] is fsi_locate's cell table of the points.
+ * Pass s as fsi_stage's s (or fsi_step_state.s) on a mesh created with
+ * has_s != 0.  s_band > 0 and finite; 0 <= layers <= 64.                  */
+fsi_status fsi_interface_scaling(fsi_mesh *mesh, const int32_t *cell_start, double s_band,
+                                 int32_t layers, double *s);
+
 /* Interpolation of the fluid velocity to the solid points, u = C^T V
  * (Eq. nodal_solid_velo): u_B = sum_A N_A(xi_B) V_A over the 8 nodes of
  * element elem[B], velocity slots only.  xi [m][3] and U [n][4] and u [m][3]

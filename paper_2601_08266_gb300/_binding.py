@@ -123,6 +123,7 @@ _SIGS = {
     "fsi_block_diagonal": ([_VP, _INT, ctypes.POINTER(fsi_step_state), _VP], _INT),
     "fsi_newton_step": ([_VP, ctypes.POINTER(fsi_newton_opts), ctypes.POINTER(fsi_step_state),
                          ctypes.POINTER(fsi_newton_report)], _INT),
+    "fsi_interface_scaling": ([_VP, _VP, ctypes.c_double, _INT, _VP], _INT),
     "fsi_pressure_levels": ([_VP, ctypes.POINTER(ctypes.c_int32), _VP], _INT),
     "fsi_pressure_set_faces": ([_VP, ctypes.POINTER(ctypes.c_int32)], _INT),
     "fsi_pressure_apply": ([_VP, _INT, _INT, _VP, _VP], _INT),
@@ -478,6 +479,12 @@ def fsi_pressure_levels(mesh: Mesh):
     buf = (ctypes.c_int32 * 48)()
     _check(lib().fsi_pressure_levels(mesh.handle, ctypes.byref(n), buf))
     return [tuple(buf[3 * l + d] for d in range(3)) for l in range(n.value)]
+
+
+def fsi_interface_scaling(mesh: Mesh, cell_start, s_band, layers, s):
+    import torch
+    _check(lib().fsi_interface_scaling(mesh.handle, _ptr(cell_start, torch.int32), float(s_band),
+                                       int(layers), _ptr(s, torch.float64)))
 
 
 def fsi_pressure_set_faces(mesh: Mesh, faces):

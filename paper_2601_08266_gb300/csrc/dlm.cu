@@ -284,6 +284,37 @@ __global__ void spread_nodes_kernel(GridArgs g, const int32_t *__restrict__ star
         spread_node<T>(g, node, start, S, F, accumulate);
 }
 
+// ------------------------------------------------------------- interface scaling
+// s at node (i, j, k) = s_band when one of the cells within `layers` cells of
+// the node's (up to) 8 cells holds a point, 1 otherwise: the node touches a
+// band cell exactly when a cell of [i-1-layers, i+layers] x ... (clipped) is
+// occupied.
+__global__ void interface_scaling_kernel(int Nx, int Ny, int Nz, const int32_t *__restrict__ start,
+                                         double s_band, int layers, double *__restrict__ s)
+{
+    const int NX1 = Nx + 1, NY1 = Ny + 1;
+    const int64_t n = (int64_t)NX1 * NY1 * (Nz + 1);
+    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < n;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(node % NX1), j = (int)((node / NX1) % NY1),
+                  k = (int)(node / ((int64_t)NX1 * NY1));
+        const int i0 = max(0, i - 1 - layers), i1 = min(Nx - 1, i + layers);
+        const int j0 = max(0, j - 1 - layers), j1 = min(Ny - 1, j + layers);
+        const int k0 = max(0, k - 1 - layers), k1 = min(Nz - 1, k + layers);
+        bool on = false;
+        for (int c = k0; c <= k1 && !on; ++c)
+            for (int b = j0; b <= j1 && !on; ++b) {
+                const int64_t row = (int64_t)Nx * (b + (int64_t)Ny * c);
+                for (int a = i0; a <= i1; ++a)
+                    if (start[row + a + 1] > start[row + a]) {
+                        on = true;
+                        break;
+                    }
+            }
+        s[node] = on ? s_band : 1.0;
+    }
+}
+
 // ---------------------------------------------------------------- no-allocation locate
 // fsi_locate_noalloc keeps its scratch (outside-point counter, per-cell fill
 // counters, scan tile sums) in one file-scope device array instead of mesh
@@ -462,6 +493,22 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
             g, cell_start, (const float *)mesh->spread_scratch, (float *)F, accumulate);
     }
     return check_launch("spread nodes kernel");
+}
+
+fsi_status fsi_interface_scaling(fsi_mesh *mesh, const int32_t *cell_start, double s_band,
+                                 int32_t layers, double *s)
+{
+    FSI_TRY(validate_mesh(mesh));
+    if (!cell_start || !s) return set_error(FSI_ERR_ARG, "fsi_interface_scaling: NULL argument");
+    if (!(s_band > 0.0) || !std::isfinite(s_band))
+        return set_error(FSI_ERR_ARG, "fsi_interface_scaling: s_band must be positive and finite");
+    if (layers < 0 || layers > 64)
+        return set_error(FSI_ERR_ARG, "fsi_interface_scaling: layers must be in [0, 64]");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    const fsi_grid &g = mesh->grid;
+    interface_scaling_kernel<<<blocks_for(mesh->n_nodes, 256), 256, 0, mesh->stream>>>(
+        g.N[0], g.N[1], g.N[2], cell_start, s_band, layers, s);
+    return check_launch("interface scaling kernel");
 }
 
 fsi_status fsi_locate_noalloc(const fsi_grid *grid, int64_t m, const double *X, int32_t *elem,

@@ -142,3 +142,61 @@ def test_newton_reports_non_convergence(fsi, oracle):
                                     krylov_rtol=1e-2, check=False)
     assert code == 5  # FSI_ERR_NOCONV
     assert rep["converged"] == 0 and rep["newton_iters"] == 1 and rep["r_final"] < rep["r0"]
+
+
+def test_interface_scaling_suppresses_spurious_flow_in_a_hydrostatic_state(fsi):
+    """Analogue of the paper's closed-valve check (Sec. 2.1 scaling s): a duct
+    (no-slip walls, traction-free ends) driven by a uniform body force and
+    blocked by a tethered plate of solid points has a hydrostatic steady state
+    (v = 0, a pressure jump across the plate).  The continuous pressure cannot
+    jump, so VMS leaks a spurious flow; s >> 1 on the band around the plate
+    must reduce it, monotonically in s."""
+    import torch
+    Nx, Ny, Nz, h = 24, 8, 8, 0.125
+    ax = [np.arange(N + 1) * h for N in (Nx, Ny, Nz)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    X, Y, Z = X.ravel(), Y.ravel(), Z.ravel()
+    wall = (Y < 1e-12) | (Y > 1 - 1e-12) | (Z < 1e-12) | (Z > 1 - 1e-12)
+    rng = np.random.default_rng(0)
+    m = 40000
+    plate = np.stack([rng.uniform(1.45, 1.55, m), rng.uniform(0, 1, m), rng.uniform(0, 1, m)], 1)
+    vmax, perr = {}, {}
+    for s_band in (1.0, 10.0, 100.0):
+        mesh = fsi.Mesh((Nx, Ny, Nz), h=(h, h, h), rho=1.0, mu=0.05, dt=0.05, rho_inf=0.5,
+                        has_s=True, device=0)
+        n = mesh.n_nodes
+        mask = np.zeros((n, 4), np.uint8)
+        mask[wall, :3] = 1
+        e = torch.empty(m, dtype=torch.int32, device="cuda")
+        xi = torch.empty((m, 3), dtype=torch.float64, device="cuda")
+        cs = torch.empty(mesh.n_elems + 1, dtype=torch.int32, device="cuda")
+        pm = torch.empty(m, dtype=torch.int32, device="cuda")
+        fsi.fsi_locate(mesh, T(plate), e, xi, cs, pm)
+        s = torch.empty(n, dtype=torch.float64, device="cuda")
+        fsi.fsi_interface_scaling(mesh, cs, s_band, 0, s)
+        f = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+        f[:, 0] = 1.0
+        Vn = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+        An, yn, yD = torch.zeros_like(Vn), torch.zeros_like(Vn), torch.zeros_like(Vn)
+        w = torch.full((m,), 0.1 / m, dtype=torch.float64, device="cuda")
+        for _ in range(30):
+            y = yn.clone()
+            st = fsi.StepState(y, Vn, An, s=s, f=f, mask=T(mask), yD=yD, elem=e, xi=xi,
+                               cell_start=cs, perm=pm, w=w, drho_s=0.0, k_s=2e5)
+            code, rep = fsi.fsi_newton_step(mesh, st, mixed=False, max_newton=10, max_krylov=3000,
+                                            newton_rtol=1e-8)
+            assert code == 0
+            yn = y.clone()
+            fsi.fsi_advance_history(mesh, fsi.FSI_F64, y, Vn, An)
+        vmax[s_band] = float(Vn[:, :3].norm(dim=1).max())
+        p = H(y)[:, 3]
+        centre = (np.abs(Y - 0.5) < 1e-9) & (np.abs(Z - 0.5) < 1e-9)
+        # upstream of the plate the pressure is hydrostatic, p = x from the
+        # traction-free end, once the leak is suppressed (with s = 1 the leak
+        # flow costs ~10 % of the slope)
+        up = centre & (X > 0.3) & (X < 1.2)
+        perr[s_band] = float(np.abs(p[up] - X[up]).max())
+    print("\nspurious max |v| by s:", vmax, "upstream pressure error:", perr)
+    assert vmax[1.0] > vmax[10.0] > vmax[100.0]
+    assert vmax[100.0] < vmax[1.0] / 3
+    assert perr[100.0] < 0.05 and perr[100.0] < perr[1.0]

@@ -273,3 +273,35 @@ def test_dlm_config2_leaflets_full_size(fsi, oracle, prec):
     X = inputs.leaflet_points(200_000, seed=20)
     g = dlm_check(fsi, oracle, 64, X, prec, False, True)
     assert g["nout"] == 0
+
+
+@pytest.mark.parametrize("layers", [0, 1, 2])
+def test_interface_scaling_matches_oracle(fsi, oracle, layers):
+    """Sec. 2.1's band field from located leaflet points, bit-exact, and a
+    VMS residual on a mesh with has_s that uses it."""
+    import torch
+    from oracle import interface as itf
+    N = (20, 16, 18)
+    mesh, grid, p = make(fsi, oracle, N, has_s=True)
+    X = inputs.leaflet_points(3000, seed=31)
+    m = X.shape[0]
+    elem = torch.empty(m, dtype=torch.int32, device="cuda")
+    xi = torch.empty((m, 3), dtype=torch.float64, device="cuda")
+    cs = torch.empty(mesh.n_elems + 1, dtype=torch.int32, device="cuda")
+    perm = torch.empty(m, dtype=torch.int32, device="cuda")
+    fsi.fsi_locate(mesh, T(X), elem, xi, cs, perm)
+    s = torch.empty(mesh.n_nodes, dtype=torch.float64, device="cuda")
+    fsi.fsi_interface_scaling(mesh, cs, 100.0, layers, s)
+    torch.cuda.synchronize()
+    e, _, _ = oracle.core.locate(grid, X)
+    ref = itf.scaling_field(grid, e, 100.0, layers)
+    assert np.array_equal(H(s), ref)
+    assert (ref == 100.0).sum() > 0 and (ref == 1.0).sum() > 0
+    # the field in the acceleration's 4th slot scales tau_M in the VMS operators
+    rng = np.random.default_rng(layers)
+    U = rng.uniform(-1, 1, (mesh.n_nodes, 4))
+    A = rng.uniform(-1, 1, (mesh.n_nodes, 4))
+    A[:, 3] = ref
+    x = rng.uniform(-1, 1, (mesh.n_nodes, 4))
+    eR, eJ, _ = vms_case(fsi, oracle, mesh, grid, p, U, A, None, x, "df64")
+    assert eR < 1e-12 and eJ < 1e-12
