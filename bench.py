@@ -66,6 +66,21 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate_over_ranks(ms_step, e2e_ms, units_per_rank, ws, device):
+    """Weak scaling over replicas: the step time is the maximum over ranks (a
+    collective MAX when ws > 1), and the whole-job value is the units all ranks
+    processed (ws x units_per_rank) per second of that time, in G units/s.
+    Returns (max step ms, max e2e ms, value, e2e value or None)."""
+    import torch
+    if ws > 1:
+        t = torch.tensor([ms_step, e2e_ms], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step, e2e_ms = float(t[0]), float(t[1])
+    value = ws * units_per_rank / (ms_step * 1e-3) / 1e9
+    e2e_val = ws * units_per_rank / (e2e_ms * 1e-3) / 1e9 if math.isfinite(e2e_ms) else None
+    return ms_step, e2e_ms, value, e2e_val
+
+
 def make_workload(N=N_GRID, m=M_POINTS, seed=SEED):
     from paper_2601_08266_gb300 import inputs
     n = inputs.n_nodes(N)
@@ -378,14 +393,7 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
     dev = torch.device(f"cuda:{local}")
     if e2e_ms is None:
         e2e_ms = float("nan")
-    # max over ranks
-    t_step = ms64
-    if ws > 1:
-        t = torch.tensor([ms64, e2e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step, e2e_ms = float(t[0]), float(t[1])
-    value = ws * 4.0 * n / (t_step * 1e-3) / 1e9
-    e2e_val = ws * 4.0 * n / (e2e_ms * 1e-3) / 1e9 if math.isfinite(e2e_ms) else None
+    t_step, e2e_ms, value, e2e_val = aggregate_over_ranks(ms64, e2e_ms, 4.0 * n, ws, dev)
 
     if rank != 0:
         if ws > 1:
