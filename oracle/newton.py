@@ -74,7 +74,7 @@ class Problem:
     """One implicit step: unknown y = [Vdot_{n+1} | P_{n+1}] per node."""
 
     def __init__(self, grid, phys, Vn, An, f=None, s=None, mask=None, yD=None,
-                 points=None, solid=None):
+                 points=None, solid=None, body=None):
         self.grid, self.phys = grid, phys
         self.Vn, self.An, self.f, self.s = Vn, An, f, s
         self.mask = None if mask is None else np.asarray(mask, dtype=bool)
@@ -83,6 +83,38 @@ class Problem:
         self.c_a, self.c_v = timeint.chain_factors(self.rho_inf, self.dt)
         self.points = points  # (elem, xi, w) or None
         self.solid = solid or {}
+        # hyperelastic immersed solid (oracle/solid.py) instead of the point-mass
+        # stand-in: dict(mesh, u, v, a (history at the solid nodes), mat, g);
+        # its nodes, located at X + u_n, are the coupling points
+        self.body = body
+        if body is not None:
+            x_n = body["mesh"].X + body["u"]
+            e, xi, nout = core.locate(grid, x_n)
+            assert nout == 0, "solid nodes must lie inside the fluid grid"
+            self.body_points = (e, xi)
+
+    def body_residual(self, a_next):
+        from . import solid as so
+        b = self.body
+        u_af, v_af, a_am, _, _ = so.kinematics(b["u"], b["v"], b["a"], a_next, self.dt,
+                                               self.rho_inf)
+        return so.residual(b["mesh"], u_af, v_af, a_am, b["u"], b["mat"], self.phys["mu"],
+                           b.get("g", (0.0, 0.0, 0.0)))
+
+    def body_tangent(self, a_next):
+        """Dense dR^s/duddot_{n+1} [3 ns, 3 ns] (unit-vector applications)."""
+        from . import solid as so
+        b = self.body
+        u_af, _, _, _, _ = so.kinematics(b["u"], b["v"], b["a"], a_next, self.dt, self.rho_inf)
+        ca, cu, cv = so.chain(self.dt, self.rho_inf)
+        ns = b["mesh"].ns
+        K = np.zeros((3 * ns, 3 * ns))
+        for col in range(3 * ns):
+            x = np.zeros((ns, 3))
+            x[col // 3, col % 3] = 1.0
+            K[:, col] = so.tangent_apply(b["mesh"], u_af, b["u"], x, b["mat"], self.phys["mu"],
+                                         ca, cu, cv).ravel()
+        return K
 
     def stage(self, y):
         return timeint.stage(y, self.Vn, self.An, self.dt, self.rho_inf, s=self.s)
@@ -101,6 +133,11 @@ class Problem:
             dx = self.dt * core.interp(self.grid, elem, xi, V1)
             rs = drho * (a - gvec[None, :]) + k * dx
             R = core.spread(self.grid, elem, xi, rs, w=w, F=R, accumulate=True)
+        if self.body is not None:
+            elem, xi = self.body_points
+            a_next = core.interp(self.grid, elem, xi, y)         # uddot_{n+1} = C^T Vdot_{n+1}
+            R = core.spread(self.grid, elem, xi, self.body_residual(a_next), F=R,
+                            accumulate=True)
         if self.mask is not None:
             R = R.copy()
             R[self.mask] = (y - self.yD)[self.mask]
@@ -118,6 +155,11 @@ class Problem:
             wv = np.ones(len(elem)) if w is None else np.asarray(w)
             D = sp.diags(np.repeat(wv * (drho + k * gamma * self.dt ** 2), 3))
             J = J + (Ct.T @ D @ Ct)
+        if self.body is not None:
+            elem, xi = self.body_points
+            Ct = coupling_matrix(self.grid, elem, xi)
+            a_next = core.interp(self.grid, elem, xi, y)
+            J = J + Ct.T @ sp.csr_matrix(self.body_tangent(a_next)) @ Ct
         if self.mask is not None:
             J = J.tolil()
             idx = np.flatnonzero(self.mask.ravel())
