@@ -245,6 +245,8 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
  *   dx_B = dt (C^T V_{n+1})_B,
  * spread with the point weights: R^{f,m} += C W r^s, so that the solid block
  * of the reduced Jacobian is C W (drho_s + k_s gamma dt^2) C^T.            */
+typedef struct fsi_solid fsi_solid;
+
 typedef struct {
     double *y;
     const double *Vn, *An, *s, *f;
@@ -255,6 +257,13 @@ typedef struct {
     const double *xi, *w;
     double drho_s, k_s;
     double g_s[3];
+    /* hyperelastic immersed solid (fsi_solid_create) instead of the
+     * point-mass stand-in, or NULL.  When set, the m points are the solid's
+     * nodes located at X + us (m = its node count; w, drho_s, k_s are
+     * ignored; g_s is the body force f of Sec. 2.2), and us, vs, as [m][3]
+     * FP64 are its displacement, velocity and acceleration at t_n.          */
+    fsi_solid *body;
+    const double *us, *vs, *as;
 } fsi_step_state;
 
 /* Full residual of the reduced system (Sec. 2.4) at st->y:
@@ -330,6 +339,48 @@ typedef struct {
 fsi_status fsi_newton_step(fsi_mesh *mesh, const fsi_newton_opts *opts, const fsi_step_state *st,
                            fsi_newton_report *report);
 
+
+/* ----------------------------------------------------------------------- */
+/* Immersed hyperelastic solid (Sec. 2.2, Eq. solid_weak_form) on a Q1
+ * hexahedral solid mesh.  Nodal residual
+ *   R^s_a = sum_g N_a (rho_s - rho_f)(uddot(g) - f) detJ0
+ *         + sum_g P(F) grad_X N_a detJ0
+ *         - sum_g 2 mu_f D grad_x N_a J detJ0
+ * (2x2x2 Gauss points in the reference configuration; compressible
+ * neo-Hookean P = mu_s (F - F^-T) + lambda_s ln J F^-T; D the symmetric
+ * gradient of the solid's velocity field on the configuration X + u_n at the
+ * start of the step; rho_f and mu_f are the mesh's fluid properties).  The
+ * paper leaves the material and the evaluation of the artificial-fluid term
+ * open; these are this library's choices.  Time stepping is generalized-alpha
+ * with Newmark beta = (1 + alpha_m - alpha_f)^2 / 4: the residual is taken
+ * at uddot_{n+alpha_m}, v_{n+alpha_f}, u_{n+alpha_f}, functions of
+ * uddot_{n+1} = C^T Vdot_{n+1}; in fsi_newton_step the reduced system gets
+ * R^{f,m} += C R^s and J += C dR^s/duddot_{n+1} C^T (Sec. 2.4).
+ *
+ * X [n_nodes][3] (reference coordinates) and conn [n_elems][8] (corner a =
+ * ax + 2 ay + 4 az of the element's trilinear map, positive Jacobian) are
+ * device arrays, copied.  All nodal arrays below are [n_nodes][3] FP64 device
+ * arrays unless a precision is given.  Calls run on the mesh's stream.      */
+fsi_status fsi_solid_create(fsi_mesh *mesh, int64_t n_nodes, int64_t n_elems, const double *X,
+                            const int32_t *conn, double rho_s, double mu_s, double lambda_s,
+                            fsi_solid **out);
+void fsi_solid_destroy(fsi_solid *body);
+/* R [n][3] = R^s at the stage values (u_af, v_af, a_am), viscous term on
+ * X + u_n; g [3] the body force f (NULL: 0).                                */
+fsi_status fsi_solid_residual(fsi_solid *body, const double *u_af, const double *v_af,
+                              const double *a_am, const double *u_n, const double *g, double *R);
+/* Jx = dR^s/duddot_{n+1} x = alpha_m M x + alpha_f beta dt^2 K(u_af) x
+ *      - alpha_f gamma dt K_visc(u_n) x, with u_af, x, Jx in `prec`.         */
+fsi_status fsi_solid_tangent_apply(fsi_solid *body, fsi_prec prec, const void *u_af,
+                                   const double *u_n, const void *x, void *Jx);
+/* stage values from uddot_{n+1} and the history (u, v, a) at t_n           */
+fsi_status fsi_solid_stage(fsi_solid *body, const double *u, const double *v, const double *a,
+                           const double *a_next, double *u_af, double *v_af, double *a_am);
+/* history advance (u, v, a) <- (u_{n+1}, v_{n+1}, uddot_{n+1}), in place     */
+fsi_status fsi_solid_advance(fsi_solid *body, double *u, double *v, double *a,
+                             const double *a_next);
+/* current node positions x = X + u (to locate the nodes for the next step) */
+fsi_status fsi_solid_positions(fsi_solid *body, const double *u, double *x);
 /* ----------------------------------------------------------------------- */
 /* Pressure block of the Schur-complement preconditioner (opts.precond = 1;
  * Sec. 2.4 solves the reduced system with block preconditioners built from

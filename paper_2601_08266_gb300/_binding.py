@@ -45,7 +45,9 @@ class fsi_step_state(ctypes.Structure):
                 ("yD", ctypes.c_void_p), ("m", ctypes.c_int64), ("elem", ctypes.c_void_p),
                 ("cell_start", ctypes.c_void_p), ("perm", ctypes.c_void_p),
                 ("xi", ctypes.c_void_p), ("w", ctypes.c_void_p), ("drho_s", ctypes.c_double),
-                ("k_s", ctypes.c_double), ("g_s", ctypes.c_double * 3)]
+                ("k_s", ctypes.c_double), ("g_s", ctypes.c_double * 3),
+                ("body", ctypes.c_void_p), ("us", ctypes.c_void_p), ("vs", ctypes.c_void_p),
+                ("as_", ctypes.c_void_p)]
 
 
 class fsi_newton_opts(ctypes.Structure):
@@ -123,6 +125,14 @@ _SIGS = {
     "fsi_block_diagonal": ([_VP, _INT, ctypes.POINTER(fsi_step_state), _VP], _INT),
     "fsi_newton_step": ([_VP, ctypes.POINTER(fsi_newton_opts), ctypes.POINTER(fsi_step_state),
                          ctypes.POINTER(fsi_newton_report)], _INT),
+    "fsi_solid_create": ([_VP, _I64, _I64, _VP, _VP, ctypes.c_double, ctypes.c_double,
+                          ctypes.c_double, ctypes.POINTER(_VP)], _INT),
+    "fsi_solid_destroy": ([_VP], None),
+    "fsi_solid_residual": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP], _INT),
+    "fsi_solid_tangent_apply": ([_VP, _INT, _VP, _VP, _VP, _VP], _INT),
+    "fsi_solid_stage": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _INT),
+    "fsi_solid_advance": ([_VP, _VP, _VP, _VP, _VP], _INT),
+    "fsi_solid_positions": ([_VP, _VP, _VP], _INT),
     "fsi_interface_scaling": ([_VP, _VP, ctypes.c_double, _INT, _VP], _INT),
     "fsi_pressure_levels": ([_VP, ctypes.POINTER(ctypes.c_int32), _VP], _INT),
     "fsi_pressure_set_faces": ([_VP, ctypes.POINTER(ctypes.c_int32)], _INT),
@@ -312,17 +322,21 @@ class StepState:
     """Owns the torch tensors behind an fsi_step_state (all FP64 on the device)."""
 
     def __init__(self, y, Vn, An, s=None, f=None, mask=None, yD=None, elem=None, xi=None,
-                 cell_start=None, perm=None, w=None, drho_s=0.5, k_s=0.0, g_s=(0.0, 0.0, 0.0)):
+                 cell_start=None, perm=None, w=None, drho_s=0.5, k_s=0.0, g_s=(0.0, 0.0, 0.0),
+                 body=None, us=None, vs=None, as_=None):
         import torch
         self.t = dict(y=y, Vn=Vn, An=An, s=s, f=f, mask=mask, yD=yD, elem=elem, xi=xi,
-                      cell_start=cell_start, perm=perm, w=w)
+                      cell_start=cell_start, perm=perm, w=w, us=us, vs=vs, as_=as_)
+        self.body = body
         m = 0 if elem is None else int(elem.shape[0])
         f64 = torch.float64
         self.c = fsi_step_state(
             _ptr(y, f64), _ptr(Vn, f64), _ptr(An, f64), _ptr(s, f64), _ptr(f, f64),
             _ptr(mask, torch.uint8), _ptr(yD, f64), m, _ptr(elem, torch.int32),
             _ptr(cell_start, torch.int32), _ptr(perm, torch.int32), _ptr(xi, f64),
-            _ptr(w, f64), float(drho_s), float(k_s), (ctypes.c_double * 3)(*g_s))
+            _ptr(w, f64), float(drho_s), float(k_s), (ctypes.c_double * 3)(*g_s),
+            None if body is None else body.handle.value, _ptr(us, f64), _ptr(vs, f64),
+            _ptr(as_, f64))
 
 
 def fsi_coupled_residual(mesh: Mesh, st: StepState, R, prec=FSI_F64):
@@ -479,6 +493,68 @@ def fsi_pressure_levels(mesh: Mesh):
     buf = (ctypes.c_int32 * 48)()
     _check(lib().fsi_pressure_levels(mesh.handle, ctypes.byref(n), buf))
     return [tuple(buf[3 * l + d] for d in range(3)) for l in range(n.value)]
+
+
+class Solid:
+    """Owner of an fsi_solid handle (hyperelastic immersed solid, Q1 hexahedra)."""
+
+    def __init__(self, mesh: Mesh, X, conn, rho_s, mu_s, lambda_s):
+        import torch
+        self.mesh = mesh
+        self.X = X
+        self.ns, self.es = int(X.shape[0]), int(conn.shape[0])
+        h = _VP()
+        _check(lib().fsi_solid_create(mesh.handle, self.ns, self.es, _ptr(X, torch.float64),
+                                      _ptr(conn, torch.int32), float(rho_s), float(mu_s),
+                                      float(lambda_s), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fsi_solid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fsi_solid_residual(body: Solid, u_af, v_af, a_am, u_n, g, R):
+    import torch
+    d = torch.float64
+    g_arr = None if g is None else (ctypes.c_double * 3)(*g)   # alive during the call
+    g_ptr = None if g_arr is None else ctypes.cast(g_arr, ctypes.c_void_p)
+    _check(lib().fsi_solid_residual(body.handle, _ptr(u_af, d), _ptr(v_af, d), _ptr(a_am, d),
+                                    _ptr(u_n, d), g_ptr, _ptr(R, d)))
+
+
+def fsi_solid_tangent_apply(body: Solid, prec, u_af, u_n, x, Jx):
+    import torch
+    dt = _prec_dtype(prec)
+    _check(lib().fsi_solid_tangent_apply(body.handle, prec, _ptr(u_af, dt),
+                                         _ptr(u_n, torch.float64), _ptr(x, dt), _ptr(Jx, dt)))
+
+
+def fsi_solid_stage(body: Solid, u, v, a, a_next, u_af, v_af, a_am):
+    import torch
+    d = torch.float64
+    _check(lib().fsi_solid_stage(body.handle, _ptr(u, d), _ptr(v, d), _ptr(a, d),
+                                 _ptr(a_next, d), _ptr(u_af, d), _ptr(v_af, d), _ptr(a_am, d)))
+
+
+def fsi_solid_advance(body: Solid, u, v, a, a_next):
+    import torch
+    d = torch.float64
+    _check(lib().fsi_solid_advance(body.handle, _ptr(u, d), _ptr(v, d), _ptr(a, d),
+                                   _ptr(a_next, d)))
+
+
+def fsi_solid_positions(body: Solid, u, x):
+    import torch
+    d = torch.float64
+    _check(lib().fsi_solid_positions(body.handle, _ptr(u, d), _ptr(x, d)))
 
 
 def fsi_interface_scaling(mesh: Mesh, cell_start, s_band, layers, s):

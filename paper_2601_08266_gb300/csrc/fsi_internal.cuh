@@ -99,6 +99,15 @@ template <typename T> fsi_status pmg_vcycle(fsi_mesh *m, const T *b, T *x);
 void *pmg_fine_buffer(fsi_mesh *m, int which);
 void destroy_pmg(fsi_mesh *m);
 
+// immersed hyperelastic solid (solid.cu)
+fsi_status solid_residual_impl(fsi_solid *b, const double *u_af, const double *v_af,
+                               const double *a_am, const double *u_n, const double g[3], double *R);
+template <typename T>
+fsi_status solid_tangent_impl(fsi_solid *b, const T *u_af, const double *u_n, const T *x, T *Jx);
+fsi_status solid_stage_impl(fsi_solid *b, const double *u, const double *v, const double *a,
+                            const double *a1, double *u_af, double *v_af, double *a_am);
+int64_t solid_nodes(const fsi_solid *b);
+
 // fused tensor-core inference of the initial-guess network (mlp_tc.cu)
 size_t mlp_tc_packed_bytes();
 fsi_status mlp_predict_tc(cudaStream_t s, int device, const fsi_grid &g, int64_t n,

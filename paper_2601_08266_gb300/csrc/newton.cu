@@ -442,6 +442,8 @@ struct Work {
     // working-precision buffers (8 bytes per entry so that either type fits)
     void *Uw = nullptr, *Aw = nullptr, *fw = nullptr, *xiw = nullptr, *ww = nullptr;
     void *pu = nullptr;                    // [m][3] point work
+    double *bu = nullptr, *bv = nullptr, *ba = nullptr;  // solid stage values [m][3]
+    void *buw = nullptr, *pw = nullptr;    // solid u_af and tangent output (working precision)
     void *Vk = nullptr;                    // [restart+1][4n]
     void *w = nullptr, *z = nullptr, *x = nullptr, *b = nullptr;
     void *blocks = nullptr, *inv = nullptr;  // [n][16]
@@ -455,6 +457,7 @@ struct Work {
 void free_work(Work &W)
 {
     void *ptrs[] = {W.U, W.A, W.R, W.V1, W.pa, W.pv, W.prs, W.Uw, W.Aw, W.fw, W.xiw, W.ww, W.pu,
+                    W.bu, W.bv, W.ba, W.buw, W.pw,
                     W.Vk, W.w, W.z, W.x, W.b, W.blocks, W.inv, W.partial, W.hcol, W.h2};
     for (void *p : ptrs) cudaFree(p);
     if (W.hhost) cudaFreeHost(W.hhost);
@@ -499,6 +502,8 @@ fsi_status ensure_work(fsi_mesh *mesh, int64_t m_pts, int restart)
         {(void **)&W.U, v}, {(void **)&W.A, v}, {(void **)&W.R, v}, {(void **)&W.V1, v},
         {(void **)&W.pa, pm}, {(void **)&W.pv, pm}, {(void **)&W.prs, pm},
         {&W.Uw, v}, {&W.Aw, v}, {&W.fw, v}, {&W.xiw, pm}, {&W.ww, pm / 3 + 8}, {&W.pu, pm},
+        {(void **)&W.bu, pm}, {(void **)&W.bv, pm}, {(void **)&W.ba, pm}, {&W.buw, pm},
+        {&W.pw, pm},
         {&W.Vk, v * (size_t)(restart + 1)}, {&W.w, v}, {&W.z, v}, {&W.x, v}, {&W.b, v},
         {&W.blocks, v * 4}, {&W.inv, v * 4},
         {(void **)&W.partial, (size_t)(restart + 2) * kRedGrid * sizeof(double)},
@@ -535,7 +540,15 @@ fsi_status coupled_residual_impl(fsi_mesh *mesh, const fsi_step_state *st, doubl
     const int64_t n = mesh->n_nodes;
     FSI_TRY(fsi_stage(mesh, FSI_F64, st->y, st->Vn, st->An, st->s, W.U, W.A));
     FSI_TRY(vms_residual(mesh, prec, W.U, W.A, st->f, R));
-    if (st->m > 0) {
+    if (st->m > 0 && st->body) {
+        // hyperelastic body: uddot_{n+1} = C^T Vdot_{n+1} at its nodes, stage
+        // values, nodal residual R^s, spread without weights
+        FSI_TRY(fsi_dlm_interp(mesh, prec, st->m, st->elem, st->xi, st->y, W.pa));
+        FSI_TRY(solid_stage_impl(st->body, st->us, st->vs, st->as, W.pa, W.bu, W.bv, W.ba));
+        FSI_TRY(solid_residual_impl(st->body, W.bu, W.bv, W.ba, st->us, st->g_s, W.prs));
+        FSI_TRY(fsi_dlm_spread(mesh, prec, st->m, st->elem, st->xi, st->cell_start, st->perm,
+                               W.prs, nullptr, R, 1));
+    } else if (st->m > 0) {
         velocity_next_kernel<<<grid1d(n), 256, 0, s>>>(n, mesh->phys.dt, mesh->gamma, st->y,
                                                       st->Vn, st->An, W.V1);
         FSI_TRY(check_launch("velocity_next kernel"));
@@ -566,6 +579,8 @@ template <typename T> fsi_status prepare_linearisation(fsi_mesh *mesh, const fsi
     if (st->f) cast_kernel<double, T><<<grid1d(n4), 256, 0, s>>>(n4, st->f, (T *)W.fw);
     if (st->m > 0) {
         cast_kernel<double, T><<<grid1d(3 * st->m), 256, 0, s>>>(3 * st->m, st->xi, (T *)W.xiw);
+        if (st->body)
+            cast_kernel<double, T><<<grid1d(3 * st->m), 256, 0, s>>>(3 * st->m, W.bu, (T *)W.buw);
         if (st->w) cast_kernel<double, T><<<grid1d(st->m), 256, 0, s>>>(st->m, st->w, (T *)W.ww);
     }
     return check_launch("linearisation casts");
@@ -579,7 +594,13 @@ fsi_status coupled_jacobian_impl(fsi_mesh *mesh, const fsi_step_state *st, const
     const int64_t n = mesh->n_nodes;
     const fsi_prec P = prec_of<T>();
     FSI_TRY(vms_jacobian(mesh, P, W.Uw, W.Aw, st->f ? W.fw : nullptr, x, Jx));
-    if (st->m > 0) {
+    if (st->m > 0 && st->body) {
+        FSI_TRY(fsi_dlm_interp(mesh, P, st->m, st->elem, W.xiw, x, W.pu));
+        FSI_TRY(solid_tangent_impl<T>(st->body, (const T *)W.buw, st->us, (const T *)W.pu,
+                                      (T *)W.pw));
+        FSI_TRY(fsi_dlm_spread(mesh, P, st->m, st->elem, W.xiw, st->cell_start, st->perm, W.pw,
+                               nullptr, Jx, 1));
+    } else if (st->m > 0) {
         FSI_TRY(fsi_dlm_interp(mesh, P, st->m, st->elem, W.xiw, x, W.pu));
         const double D = st->drho_s + st->k_s * mesh->gamma * mesh->phys.dt * mesh->phys.dt;
         scale_kernel<T><<<grid1d(3 * st->m), 256, 0, s>>>(3 * st->m, (T)D, (const T *)W.pu,
@@ -876,6 +897,12 @@ fsi_status validate_state(const fsi_mesh *mesh, const fsi_step_state *st)
     if (st->m < 0 || st->m >= INT32_MAX) return set_error(FSI_ERR_ARG, "state: m out of range");
     if (st->m > 0 && (!st->elem || !st->xi || !st->cell_start || !st->perm))
         return set_error(FSI_ERR_ARG, "state: points need elem, xi, cell_start and perm");
+    if (st->body) {
+        if (st->m != solid_nodes(st->body))
+            return set_error(FSI_ERR_ARG, "state: m must be the solid's node count");
+        if (!st->us || !st->vs || !st->as)
+            return set_error(FSI_ERR_ARG, "state: the solid needs us, vs and as");
+    }
     (void)mesh;
     return FSI_OK;
 }
