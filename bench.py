@@ -455,6 +455,8 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
             extras["batch"] = batch_section(args, dev, stream2)
         if "mlp" in sections:
             extras["mlp_inference"] = mlp_section(args, dev, stream2, W)
+        if "solid" in sections:
+            extras["solid"] = solid_section(args, dev, stream2)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
@@ -792,6 +794,89 @@ def batch_section(args, dev, stream):
     return out
 
 
+# ------------------------------------------------------------------ hyperelastic solid
+def solid_section(args, dev, stream):
+    """The three leaflets as neo-Hookean hexahedral solids (Sec. 2.2): the
+    element residual and tangent kernels alone, and one implicit step of the
+    64^3 channel with the body coupled through C (plain FP64 vs mixed)."""
+    import torch
+    import paper_2601_08266_gb300 as fsi
+    from paper_2601_08266_gb300 import inputs
+    X, conn = inputs.leaflet_hex_mesh(2, 96, 128, seed=SEED + 70)
+    ns, es = X.shape[0], conn.shape[0]
+    out = {"elements": int(es), "nodes": int(ns), "material": "neo-Hookean mu_s 50, lambda_s 500, "
+           "rho_s 1.2 (fluid rho 1, mu 1e-3)"}
+    ch = Channel(fsi, dev, stream, 64, 1, SEED + 71)
+    with torch.cuda.stream(stream):
+        Xd = torch.as_tensor(X, device=dev)
+        body = fsi.Solid(ch.mesh, Xd, torch.as_tensor(conn, device=dev), 1.2, 50.0, 500.0)
+        g = torch.Generator(device=dev).manual_seed(SEED + 72)
+        st3 = [0.001 * torch.randn((ns, 3), dtype=torch.float64, device=dev, generator=g)
+               for _ in range(4)]
+        R = torch.empty((ns, 3), dtype=torch.float64, device=dev)
+        x = torch.randn((ns, 3), dtype=torch.float64, device=dev, generator=g)
+        Jx = torch.empty_like(R)
+        x32, u32, J32 = x.float(), st3[0].float(), torch.empty((ns, 3), dtype=torch.float32,
+                                                                device=dev)
+
+    def timeit(fn, reps=10):
+        for _ in range(2):
+            fn()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms = {
+        "residual_f64": timeit(lambda: fsi.fsi_solid_residual(body, st3[0], st3[1], st3[2], st3[3],
+                                                              (0.0, 0.0, -1.0), R)),
+        "tangent_f64": timeit(lambda: fsi.fsi_solid_tangent_apply(body, fsi.FSI_F64, st3[0],
+                                                                  st3[3], x, Jx)),
+        "tangent_f32": timeit(lambda: fsi.fsi_solid_tangent_apply(body, fsi.FSI_F32, u32, st3[3],
+                                                                  x32, J32)),
+    }
+    out["kernels"] = {k: {"ms": v, "elements_per_s": es / (v * 1e-3)} for k, v in ms.items()}
+    # one implicit step of the channel with the body as the immersed solid
+    with torch.cuda.stream(stream):
+        us, vs, as_ = (torch.zeros((ns, 3), dtype=torch.float64, device=dev) for _ in range(3))
+        xs = torch.empty((ns, 3), dtype=torch.float64, device=dev)
+        e = torch.empty(ns, dtype=torch.int32, device=dev)
+        xi = torch.empty((ns, 3), dtype=torch.float64, device=dev)
+        cs = torch.empty(ch.mesh.n_elems + 1, dtype=torch.int32, device=dev)
+        pm = torch.empty(ns, dtype=torch.int32, device=dev)
+    fsi.fsi_solid_positions(body, us, xs)
+    fsi.fsi_locate(ch.mesh, xs, e, xi, cs, pm)
+    solve = dict(restart=50, max_newton=10, max_krylov=4000, newton_rtol=1e-8, krylov_rtol=1e-3)
+    r_ref = None
+    for name, mixed in (("fp64", False), ("mixed", True)):
+        yD = ch.dirichlet()
+        with torch.cuda.stream(stream):
+            y = ch.yn.clone()
+            y[ch.maskb] = yD[ch.maskb]
+        st = fsi.StepState(y, ch.Vn, ch.An, mask=ch.mask, yD=yD, elem=e, xi=xi, cell_start=cs,
+                           perm=pm, g_s=(0.0, 0.0, -1.0), body=body, us=us, vs=vs, as_=as_)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        code, rep = fsi.fsi_newton_step(ch.mesh, st, mixed=mixed, r_ref=r_ref or 0.0, check=False,
+                                        residual_prec=fsi.FSI_DF64 if mixed else fsi.FSI_F64,
+                                        **solve)
+        stream.synchronize()
+        el = time.perf_counter() - t0
+        r_ref = r_ref or rep["r_ref"]
+        out["newton_" + name] = {"seconds": el, "newton_iters": rep["newton_iters"],
+                                 "krylov_iters": rep["krylov_iters"],
+                                 "r_final_over_ref": rep["r_final"] / r_ref,
+                                 "converged": bool(rep["converged"]), "status": code}
+    out["newton_speedup_mixed_vs_fp64"] = out["newton_fp64"]["seconds"] / out["newton_mixed"]["seconds"]
+    body.close()
+    ch.close()
+    return out
+
+
 # ------------------------------------------------------------------ MLP inference
 def mlp_section(args, dev, stream, W):
     """Per-node inference of the initial-guess network over whole grids: the
@@ -868,7 +953,7 @@ def main():
     ap.add_argument("--points", type=int, default=M_POINTS, help="solid points (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip Newton, batch and MLP sections")
-    ap.add_argument("--sections", default="newton,batch,mlp",
+    ap.add_argument("--sections", default="newton,batch,mlp,solid",
                     help="comma-separated extra sections to run")
     ap.add_argument("--newton-grid", type=int, default=128)
     ap.add_argument("--newton-points", type=int, default=1_000_000)

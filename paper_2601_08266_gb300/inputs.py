@@ -121,3 +121,37 @@ def edge_points(N, seed: int, m_random: int = 64):
     pts += [(float("nan"), 0.5, 0.5)]
     R = g.uniform(-0.1, 1.1, size=(m_random, 3))
     return np.concatenate([np.asarray(pts, dtype=np.float64), R], axis=0)
+
+
+def leaflet_hex_mesh(n_r: int, n_theta: int, n_x: int, seed: int, theta0: float | None = None,
+                     radius: float = 0.3, thickness: float = 0.02, x_range=(0.1, 0.9),
+                     arc: float = 0.5):
+    """The three leaflet shells of leaflet_points as a trilinear hexahedral solid
+    mesh: per leaflet n_r x n_theta x n_x elements over r in [radius -
+    thickness/2, radius + thickness/2], its arc and x_range.  Returns (X [ns, 3],
+    conn [es, 8] int32) with corners a = ar + 2 atheta + 4 ax ordered so that
+    every element has a positive Jacobian."""
+    g = rng(seed)
+    if theta0 is None:
+        theta0 = g.uniform(0.0, 2.0 * math.pi)
+    half = 0.5 * arc / radius
+    r = np.linspace(radius - 0.5 * thickness, radius + 0.5 * thickness, n_r + 1)
+    xs = np.linspace(x_range[0], x_range[1], n_x + 1)
+    X_all, conn_all = [], []
+    base = 0
+    for which in range(3):
+        c = theta0 + which * (2.0 * math.pi / 3.0)
+        th = np.linspace(c - half, c + half, n_theta + 1)
+        # node (ir, it, ix) -> index ir + (n_r+1) (it + (n_theta+1) ix)
+        XX, TT, RR = np.meshgrid(xs, th, r, indexing="ij")
+        pts = np.stack([XX.ravel(), 0.5 + RR.ravel() * np.cos(TT.ravel()),
+                        0.5 + RR.ravel() * np.sin(TT.ravel())], axis=1)
+        X_all.append(pts)
+        nr1, nt1 = n_r + 1, n_theta + 1
+        ir, it, ix = np.meshgrid(np.arange(n_r), np.arange(n_theta), np.arange(n_x), indexing="ij")
+        n0 = ir + nr1 * (it + nt1 * ix)
+        corners = [n0 + (a & 1) + nr1 * ((a >> 1) & 1) + nr1 * nt1 * ((a >> 2) & 1)
+                   for a in range(8)]
+        conn_all.append(np.stack([cc.ravel() for cc in corners], axis=1) + base)
+        base += pts.shape[0]
+    return np.concatenate(X_all), np.concatenate(conn_all).astype(np.int32)
