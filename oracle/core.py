@@ -67,6 +67,13 @@ def lib():
                                               ctypes.c_double, d, i64, ctypes.c_int]
             L.or_locate.argtypes = [ci, d, d, ctypes.c_int64, d, i32, d]
             L.or_locate.restype = ctypes.c_int64
+            L.or_residual_x.argtypes = [ci, d, d, d, d, d, ctypes.c_int, d, ctypes.c_int]
+            L.or_jacobian_apply_x.argtypes = [ci, d, d, d, d, d, d, ctypes.c_double,
+                                              ctypes.c_double, d, ctypes.c_int]
+            L.or_element_jacobian_x.argtypes = [ci, d, d, d, d, d, ctypes.c_double,
+                                                ctypes.c_double, d, i64, ctypes.c_int]
+            L.or_locate_x.argtypes = [ci, d, ctypes.c_int64, d, i32, d]
+            L.or_locate_x.restype = ctypes.c_int64
             L.or_cell_hash.argtypes = [ci, ctypes.c_int64, i32, i32, i32]
             L.or_interp.argtypes = [ci, ctypes.c_int64, i32, d, d, d]
             L.or_spread.argtypes = [ci, ctypes.c_int64, i32, d, d, d, d, ctypes.c_int]
@@ -88,9 +95,12 @@ def _f64(a, shape=None):
 
 
 class Grid:
-    """Uniform axis-aligned hex grid: N[k] elements of size h[k] from x0."""
+    """Structured hex grid of N[k] elements per axis: uniform and axis-aligned
+    (spacing h[k] from x0), or mapped when `coords` [n, 3] gives every node's
+    position (same node numbering); the operators then take the geometry of
+    each Gauss point from the trilinear map."""
 
-    def __init__(self, N, x0=(0.0, 0.0, 0.0), h=None):
+    def __init__(self, N, x0=(0.0, 0.0, 0.0), h=None, coords=None):
         if np.isscalar(N):
             N = (int(N),) * 3
         self.N = tuple(int(v) for v in N)
@@ -100,6 +110,7 @@ class Grid:
         elif np.isscalar(h):
             h = (float(h),) * 3
         self.h = tuple(float(v) for v in h)
+        self.coords = None if coords is None else _f64(coords, (self.n_nodes, 3))
 
     @property
     def n_nodes(self):
@@ -111,6 +122,8 @@ class Grid:
 
     def node_coords(self):
         """[n, 3] coordinates of the nodes in storage order."""
+        if self.coords is not None:
+            return self.coords.copy()
         ax = [self.x0[k] + self.h[k] * np.arange(self.N[k] + 1) for k in range(3)]
         Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
         return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
@@ -153,6 +166,10 @@ def residual(grid: Grid, phys, U, A, f=None, stab=True, nthreads=0):
     f = None if f is None else _f64(f, (n, 4))
     R = np.zeros((n, 4))
     Nc, _, h = grid._c()
+    if grid.coords is not None:
+        lib().or_residual_x(Nc, _p(grid.coords), _p(phys_array(phys)), _p(U), _p(A), _p(f),
+                            1 if stab else 0, _p(R), int(nthreads))
+        return R
     lib().or_residual(Nc, _p(h), _p(phys_array(phys)), _p(U), _p(A), _p(f),
                       1 if stab else 0, _p(R), int(nthreads))
     return R
@@ -166,6 +183,10 @@ def jacobian_apply(grid: Grid, phys, U, A, x, c_a, c_v, f=None, nthreads=0):
     f = None if f is None else _f64(f, (n, 4))
     Jx = np.zeros((n, 4))
     Nc, _, h = grid._c()
+    if grid.coords is not None:
+        lib().or_jacobian_apply_x(Nc, _p(grid.coords), _p(phys_array(phys)), _p(U), _p(A),
+                                  _p(f), _p(x), float(c_a), float(c_v), _p(Jx), int(nthreads))
+        return Jx
     lib().or_jacobian_apply(Nc, _p(h), _p(phys_array(phys)), _p(U), _p(A), _p(f), _p(x),
                             float(c_a), float(c_v), _p(Jx), int(nthreads))
     return Jx
@@ -180,6 +201,11 @@ def element_jacobian(grid: Grid, phys, U, A, c_a, c_v, f=None, nthreads=0):
     Ke = np.zeros((E, 32, 32))
     conn = np.zeros((E, 8), dtype=np.int64)
     Nc, _, h = grid._c()
+    if grid.coords is not None:
+        lib().or_element_jacobian_x(Nc, _p(grid.coords), _p(phys_array(phys)), _p(U), _p(A),
+                                    _p(f), float(c_a), float(c_v), _p(Ke),
+                                    _p(conn, ctypes.c_int64), int(nthreads))
+        return Ke, conn
     lib().or_element_jacobian(Nc, _p(h), _p(phys_array(phys)), _p(U), _p(A), _p(f),
                               float(c_a), float(c_v), _p(Ke), _p(conn, ctypes.c_int64),
                               int(nthreads))
@@ -193,6 +219,9 @@ def locate(grid: Grid, X):
     elem = np.zeros(m, dtype=np.int32)
     xi = np.zeros((m, 3))
     Nc, x0, h = grid._c()
+    if grid.coords is not None:
+        nout = lib().or_locate_x(Nc, _p(grid.coords), m, _p(X), _p(elem, ctypes.c_int32), _p(xi))
+        return elem, xi, int(nout)
     nout = lib().or_locate(Nc, _p(x0), _p(h), m, _p(X), _p(elem, ctypes.c_int32), _p(xi))
     return elem, xi, int(nout)
 

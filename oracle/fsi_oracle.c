@@ -74,20 +74,29 @@ static int64_t elem_node(const int N[3], int ex, int ey, int ez, int a)
  *   G_ij  = sum_k dxi_k/dx_i dxi_k/dx_j.
  * On the axis-aligned uniform grid dxi_k/dx_k = 2/h_k, so G = diag(4/h_k^2).
  * ct_dt2 is C_T/dt^2 (0 for a steady problem).                               */
-void or_tau(const double v[3], double s, const double h[3], double rho, double mu,
-            double ct_dt2, double C_I, double out[2])
+static void tau_of_G(const double v[3], double s, const double G[3][3], double rho, double mu,
+                     double ct_dt2, double C_I, double out[2])
 {
-    double G[3], trG = 0.0, GG = 0.0, vGv = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        G[k] = 4.0 / (h[k] * h[k]);
-        trG += G[k];
-        GG += G[k] * G[k];
-        vGv += v[k] * G[k] * v[k];
+    double trG = 0.0, GG = 0.0, vGv = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        trG += G[i][i];
+        for (int j = 0; j < 3; ++j) {
+            GG += G[i][j] * G[i][j];
+            vGv += v[i] * G[i][j] * v[j];
+        }
     }
     double nu = mu / rho;
     double tau_m = 1.0 / sqrt(s * (ct_dt2 + vGv + C_I * nu * nu * GG));
     out[0] = tau_m;
     out[1] = 1.0 / (tau_m * trG);
+}
+
+void or_tau(const double v[3], double s, const double h[3], double rho, double mu,
+            double ct_dt2, double C_I, double out[2])
+{
+    double G[3][3] = {{0}};
+    for (int k = 0; k < 3; ++k) G[k][k] = 4.0 / (h[k] * h[k]);
+    tau_of_G(v, s, G, rho, mu, ct_dt2, C_I, out);
 }
 
 /* Physical parameters passed as an array so that ctypes stays simple:
@@ -114,19 +123,67 @@ typedef struct {
     double v[3], gv[3][3];  /* v_i, gv[i][j] = d v_i / d x_j            */
     double p, gp[3];
     double a[3], f[3], s;
+    double detJ, G[3][3];   /* Jacobian determinant, metric G of Sec. 2.1 */
 } gp_state;
 
-static void eval_gp(const int N[3], const double h[3], int ex, int ey, int ez, int g,
-                    const double *U, const double *A, const double *f, int has_s,
+/* Geometry at a Gauss point.  Uniform grid (Xn == NULL): dxi_k/dx_k = 2/h_k,
+ * detJ = h_x h_y h_z / 8, G = diag(4/h_k^2).  Mapped grid (node coordinates
+ * Xn [n][3]): J_ik = dx_i/dxi_k = sum_a x_ai dN_a/dxi_k, dN_a/dx_j =
+ * sum_k dN_a/dxi_k (J^-1)_kj, G_ij = sum_k (J^-1)_ki (J^-1)_kj (Sec. 2.1).   */
+static void gp_geometry(const int N[3], const double h[3], const double *Xn, int ex, int ey,
+                        int ez, const double dNdxi[24], gp_state *st)
+{
+    if (!Xn) {
+        for (int a = 0; a < 8; ++a)
+            for (int j = 0; j < 3; ++j) st->dN[a][j] = dNdxi[3 * a + j] * (2.0 / h[j]);
+        st->detJ = h[0] * h[1] * h[2] / 8.0;
+        memset(st->G, 0, sizeof st->G);
+        for (int k = 0; k < 3; ++k) st->G[k][k] = 4.0 / (h[k] * h[k]);
+        return;
+    }
+    double J[3][3] = {{0}};
+    for (int a = 0; a < 8; ++a) {
+        const double *x = Xn + 3 * elem_node(N, ex, ey, ez, a);
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) J[i][k] += x[i] * dNdxi[3 * a + k];
+    }
+    double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                 J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                 J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    double Ji[3][3];
+    Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    for (int a = 0; a < 8; ++a)
+        for (int j = 0; j < 3; ++j) {
+            double t = 0.0;
+            for (int k = 0; k < 3; ++k) t += dNdxi[3 * a + k] * Ji[k][j];
+            st->dN[a][j] = t;
+        }
+    st->detJ = det;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double t = 0.0;
+            for (int k = 0; k < 3; ++k) t += Ji[k][i] * Ji[k][j];
+            st->G[i][j] = t;
+        }
+}
+
+static void eval_gp(const int N[3], const double h[3], const double *Xn, int ex, int ey, int ez,
+                    int g, const double *U, const double *A, const double *f, int has_s,
                     gp_state *st)
 {
     const double gq = 1.0 / sqrt(3.0);
     double xi[3] = {(g & 1) ? gq : -gq, (g & 2) ? gq : -gq, (g & 4) ? gq : -gq};
     double dNdxi[24];
     or_shape(xi, st->N, dNdxi);
-    for (int a = 0; a < 8; ++a)
-        for (int j = 0; j < 3; ++j)
-            st->dN[a][j] = dNdxi[3 * a + j] * (2.0 / h[j]);
+    gp_geometry(N, h, Xn, ex, ey, ez, dNdxi, st);
     memset(st->v, 0, sizeof st->v);
     memset(st->gv, 0, sizeof st->gv);
     memset(st->gp, 0, sizeof st->gp);
@@ -168,16 +225,16 @@ static void eval_gp(const int N[3], const double h[3], int ex, int ey, int ez, i
  * with the strong residuals r_M = rho (a + v.grad v - f) + grad p,
  * r_C = div v, and the fine scales u' = -(tau_M/rho) r_M, p' = -rho tau_C r_C.
  * stab = 0 drops every term carrying u' or p' (plain Galerkin).             */
-static void element_residual(const int N[3], const double h[3], const or_phys *ph,
-                             int ex, int ey, int ez, const double *U, const double *A,
-                             const double *f, int stab, double Re[8][4])
+static void element_residual(const int N[3], const double h[3], const double *Xn,
+                             const or_phys *ph, int ex, int ey, int ez, const double *U,
+                             const double *A, const double *f, int stab, double Re[8][4])
 {
-    const double detJ = h[0] * h[1] * h[2] / 8.0;
     const double rho = ph->rho, mu = ph->mu;
     memset(Re, 0, 8 * 4 * sizeof(double));
     for (int g = 0; g < 8; ++g) {
         gp_state st;
-        eval_gp(N, h, ex, ey, ez, g, U, A, f, ph->has_s, &st);
+        eval_gp(N, h, Xn, ex, ey, ez, g, U, A, f, ph->has_s, &st);
+        const double detJ = st.detJ;
         double conv[3], rM[3], up[3];
         for (int i = 0; i < 3; ++i) {
             conv[i] = 0.0;
@@ -186,7 +243,7 @@ static void element_residual(const int N[3], const double h[3], const or_phys *p
         }
         double rC = st.gv[0][0] + st.gv[1][1] + st.gv[2][2];
         double tau[2];
-        or_tau(st.v, st.s, h, rho, mu, ph->ct_dt2, ph->C_I, tau);
+        tau_of_G(st.v, st.s, st.G, rho, mu, ph->ct_dt2, ph->C_I, tau);
         double pp = 0.0;
         for (int i = 0; i < 3; ++i) up[i] = stab ? -(tau[0] / rho) * rM[i] : 0.0;
         if (stab) pp = -rho * tau[1] * rC;
@@ -221,23 +278,18 @@ static void element_residual(const int N[3], const double h[3], const or_phys *p
  * c_v = alpha_f gamma dt (Sec. 2.4).  xe holds the 8x4 local direction.
  * Every term of element_residual is differentiated, including the
  * dependence of tau_M and tau_C on v.                                        */
-static void element_jacobian_apply(const int N[3], const double h[3], const or_phys *ph,
-                                   int ex, int ey, int ez, const double *U,
+static void element_jacobian_apply(const int N[3], const double h[3], const double *Xn,
+                                   const or_phys *ph, int ex, int ey, int ez, const double *U,
                                    const double *A, const double *f,
                                    const double xe[8][4], double c_a, double c_v,
                                    double Je[8][4])
 {
-    const double detJ = h[0] * h[1] * h[2] / 8.0;
     const double rho = ph->rho, mu = ph->mu;
-    double G[3], trG = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        G[k] = 4.0 / (h[k] * h[k]);
-        trG += G[k];
-    }
     memset(Je, 0, 8 * 4 * sizeof(double));
     for (int g = 0; g < 8; ++g) {
         gp_state st;
-        eval_gp(N, h, ex, ey, ez, g, U, A, f, ph->has_s, &st);
+        eval_gp(N, h, Xn, ex, ey, ez, g, U, A, f, ph->has_s, &st);
+        const double detJ = st.detJ;
         /* direction at the Gauss point */
         double dv[3] = {0, 0, 0}, dgv[3][3] = {{0}}, dp = 0.0, dgp[3] = {0, 0, 0};
         double da[3] = {0, 0, 0};
@@ -259,7 +311,7 @@ static void element_jacobian_apply(const int N[3], const double h[3], const or_p
         }
         double rC = st.gv[0][0] + st.gv[1][1] + st.gv[2][2];
         double tau[2];
-        or_tau(st.v, st.s, h, rho, mu, ph->ct_dt2, ph->C_I, tau);
+        tau_of_G(st.v, st.s, st.G, rho, mu, ph->ct_dt2, ph->C_I, tau);
         double tauM = tau[0], tauC = tau[1];
         for (int i = 0; i < 3; ++i) up[i] = -(tauM / rho) * rM[i];
         /* derivatives */
@@ -274,7 +326,8 @@ static void element_jacobian_apply(const int N[3], const double h[3], const or_p
          * d tau_M = -1/2 tau_M^3 s dQ, dQ = 2 v.G dv ;
          * tau_C = 1/(tau_M trG) -> d tau_C = -tau_C d tau_M / tau_M          */
         double dQ = 0.0;
-        for (int k = 0; k < 3; ++k) dQ += 2.0 * st.v[k] * G[k] * dv[k];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) dQ += 2.0 * st.v[i] * st.G[i][j] * dv[j];
         double dtauM = -0.5 * tauM * tauM * tauM * st.s * dQ;
         double dtauC = -tauC * dtauM / tauM;
         for (int i = 0; i < 3; ++i) dup[i] = -(dtauM * rM[i] + tauM * drM[i]) / rho;
@@ -318,9 +371,9 @@ static void set_threads(int nthreads)
 
 /* Assembled VMS residual R[n][4] (Sec. 2.1, Eq. fluid_weak_form + VMS).
  * f may be NULL (no body force).                                            */
-void or_residual(const int N[3], const double h[3], const double phys[5],
-                 const double *U, const double *A, const double *f, int stab,
-                 double *R, int nthreads)
+static void residual_drv(const int N[3], const double h[3], const double *Xn,
+                         const double phys[5], const double *U, const double *A, const double *f,
+                         int stab, double *R, int nthreads)
 {
     or_phys ph = unpack_phys(phys);
     int64_t E = (int64_t)N[0] * N[1] * N[2];
@@ -330,7 +383,7 @@ void or_residual(const int N[3], const double h[3], const double phys[5],
 #pragma omp parallel for schedule(static)
     for (int64_t e = 0; e < E; ++e) {
         int ex = (int)(e % N[0]), ey = (int)((e / N[0]) % N[1]), ez = (int)(e / ((int64_t)N[0] * N[1]));
-        element_residual(N, h, &ph, ex, ey, ez, U, A, f, stab, (double(*)[4])(Rel + 32 * e));
+        element_residual(N, h, Xn, &ph, ex, ey, ez, U, A, f, stab, (double(*)[4])(Rel + 32 * e));
     }
     memset(R, 0, (size_t)n * 4 * sizeof(double));
     for (int64_t e = 0; e < E; ++e) {
@@ -344,9 +397,10 @@ void or_residual(const int N[3], const double h[3], const double phys[5],
 }
 
 /* Assembled Jacobian-vector product Jx[n][4] of or_residual (stab = 1). */
-void or_jacobian_apply(const int N[3], const double h[3], const double phys[5],
-                       const double *U, const double *A, const double *f,
-                       const double *x, double c_a, double c_v, double *Jx, int nthreads)
+static void jacobian_drv(const int N[3], const double h[3], const double *Xn,
+                         const double phys[5], const double *U, const double *A,
+                         const double *f, const double *x, double c_a, double c_v, double *Jx,
+                         int nthreads)
 {
     or_phys ph = unpack_phys(phys);
     int64_t E = (int64_t)N[0] * N[1] * N[2];
@@ -361,8 +415,8 @@ void or_jacobian_apply(const int N[3], const double h[3], const double phys[5],
             int64_t nd = elem_node(N, ex, ey, ez, a);
             for (int c = 0; c < 4; ++c) xe[a][c] = x[4 * nd + c];
         }
-        element_jacobian_apply(N, h, &ph, ex, ey, ez, U, A, f, (const double(*)[4])xe, c_a, c_v,
-                               (double(*)[4])(Jel + 32 * e));
+        element_jacobian_apply(N, h, Xn, &ph, ex, ey, ez, U, A, f, (const double(*)[4])xe, c_a,
+                               c_v, (double(*)[4])(Jel + 32 * e));
     }
     memset(Jx, 0, (size_t)n * 4 * sizeof(double));
     for (int64_t e = 0; e < E; ++e) {
@@ -375,13 +429,45 @@ void or_jacobian_apply(const int N[3], const double h[3], const double phys[5],
     free(Jel);
 }
 
+void or_residual(const int N[3], const double h[3], const double phys[5], const double *U,
+                 const double *A, const double *f, int stab, double *R, int nthreads)
+{
+    residual_drv(N, h, NULL, phys, U, A, f, stab, R, nthreads);
+}
+
+void or_jacobian_apply(const int N[3], const double h[3], const double phys[5],
+                       const double *U, const double *A, const double *f,
+                       const double *x, double c_a, double c_v, double *Jx, int nthreads)
+{
+    jacobian_drv(N, h, NULL, phys, U, A, f, x, c_a, c_v, Jx, nthreads);
+}
+
+/* The same operators on a mapped (curvilinear) structured grid: node
+ * coordinates Xn [n][3] in the node numbering of the uniform grid, the
+ * geometry of every Gauss point from the trilinear map (gp_geometry).       */
+void or_residual_x(const int N[3], const double *Xn, const double phys[5], const double *U,
+                   const double *A, const double *f, int stab, double *R, int nthreads)
+{
+    const double h[3] = {1.0, 1.0, 1.0};
+    residual_drv(N, h, Xn, phys, U, A, f, stab, R, nthreads);
+}
+
+void or_jacobian_apply_x(const int N[3], const double *Xn, const double phys[5],
+                         const double *U, const double *A, const double *f, const double *x,
+                         double c_a, double c_v, double *Jx, int nthreads)
+{
+    const double h[3] = {1.0, 1.0, 1.0};
+    jacobian_drv(N, h, Xn, phys, U, A, f, x, c_a, c_v, Jx, nthreads);
+}
+
 /* Element tangent matrices Ke[E][32][32], column (4b+d) = element Jacobian
  * applied to the unit direction at local node b, component d.  Used by the
  * oracle's direct Newton solves on small grids.  conn[E][8] receives the
  * global node of each local node.                                           */
-void or_element_jacobian(const int N[3], const double h[3], const double phys[5],
-                         const double *U, const double *A, const double *f, double c_a,
-                         double c_v, double *Ke, int64_t *conn, int nthreads)
+static void element_jacobian_drv(const int N[3], const double h[3], const double *Xn,
+                                 const double phys[5], const double *U, const double *A,
+                                 const double *f, double c_a, double c_v, double *Ke,
+                                 int64_t *conn, int nthreads)
 {
     or_phys ph = unpack_phys(phys);
     int64_t E = (int64_t)N[0] * N[1] * N[2];
@@ -394,12 +480,27 @@ void or_element_jacobian(const int N[3], const double h[3], const double phys[5]
             double xe[8][4] = {{0}};
             double Je[8][4];
             xe[col / 4][col % 4] = 1.0;
-            element_jacobian_apply(N, h, &ph, ex, ey, ez, U, A, f, (const double(*)[4])xe, c_a,
-                                   c_v, Je);
+            element_jacobian_apply(N, h, Xn, &ph, ex, ey, ez, U, A, f, (const double(*)[4])xe,
+                                   c_a, c_v, Je);
             for (int row = 0; row < 32; ++row)
                 Ke[(int64_t)1024 * e + 32 * row + col] = Je[row / 4][row % 4];
         }
     }
+}
+
+void or_element_jacobian(const int N[3], const double h[3], const double phys[5],
+                         const double *U, const double *A, const double *f, double c_a,
+                         double c_v, double *Ke, int64_t *conn, int nthreads)
+{
+    element_jacobian_drv(N, h, NULL, phys, U, A, f, c_a, c_v, Ke, conn, nthreads);
+}
+
+void or_element_jacobian_x(const int N[3], const double *Xn, const double phys[5],
+                           const double *U, const double *A, const double *f, double c_a,
+                           double c_v, double *Ke, int64_t *conn, int nthreads)
+{
+    const double h[3] = {1.0, 1.0, 1.0};
+    element_jacobian_drv(N, h, Xn, phys, U, A, f, c_a, c_v, Ke, conn, nthreads);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -431,6 +532,80 @@ int64_t or_locate(const int N[3], const double x0[3], const double h[3], int64_t
             xi[3 * b + k] = 2.0 * (t[k] - (double)e[k]) - 1.0;
         }
         elem[b] = (int32_t)(e[0] + N[0] * (e[1] + N[1] * e[2]));
+    }
+    return outside;
+}
+
+/* Point location on a mapped structured grid (node coordinates Xn [n][3]):
+ * brute force over the elements in element order; in each, Newton's method
+ * on the trilinear map x(xi) = sum_a N_a(xi) x_a from xi = 0 (at most 50
+ * iterations, stop when the update is below 1e-15); the point belongs to
+ * the first element whose xi satisfies |xi_k| <= 1 + 1e-10.  Outside points
+ * get elem = -1, xi = 0.  Returns the outside count.                        */
+static int invert_trilinear(const int N[3], const double *Xn, int ex, int ey, int ez,
+                            const double X[3], double xi[3])
+{
+    double xa[8][3];
+    for (int a = 0; a < 8; ++a) {
+        const double *x = Xn + 3 * elem_node(N, ex, ey, ez, a);
+        for (int i = 0; i < 3; ++i) xa[a][i] = x[i];
+    }
+    xi[0] = xi[1] = xi[2] = 0.0;
+    for (int it = 0; it < 50; ++it) {
+        double Nv[8], dN[24], r[3] = {0, 0, 0}, J[3][3] = {{0}};
+        or_shape(xi, Nv, dN);
+        for (int a = 0; a < 8; ++a)
+            for (int i = 0; i < 3; ++i) {
+                r[i] += Nv[a] * xa[a][i];
+                for (int k = 0; k < 3; ++k) J[i][k] += xa[a][i] * dN[3 * a + k];
+            }
+        for (int i = 0; i < 3; ++i) r[i] -= X[i];
+        double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                     J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                     J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        if (!(fabs(det) > 0.0)) return 0;
+        double d[3];
+        /* Cramer's rule for J d = r */
+        d[0] = (r[0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                J[0][1] * (r[1] * J[2][2] - J[1][2] * r[2]) +
+                J[0][2] * (r[1] * J[2][1] - J[1][1] * r[2])) / det;
+        d[1] = (J[0][0] * (r[1] * J[2][2] - J[1][2] * r[2]) -
+                r[0] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                J[0][2] * (J[1][0] * r[2] - r[1] * J[2][0])) / det;
+        d[2] = (J[0][0] * (J[1][1] * r[2] - r[1] * J[2][1]) -
+                J[0][1] * (J[1][0] * r[2] - r[1] * J[2][0]) +
+                r[0] * (J[1][0] * J[2][1] - J[1][1] * J[2][0])) / det;
+        double mx = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            xi[k] -= d[k];
+            if (fabs(d[k]) > mx) mx = fabs(d[k]);
+            if (!(fabs(xi[k]) < 10.0)) return 0;
+        }
+        if (mx < 1e-15) break;
+    }
+    for (int k = 0; k < 3; ++k)
+        if (!(fabs(xi[k]) <= 1.0 + 1e-10)) return 0;
+    return 1;
+}
+
+int64_t or_locate_x(const int N[3], const double *Xn, int64_t m, const double *X, int32_t *elem,
+                    double *xi)
+{
+    int64_t outside = 0;
+    for (int64_t b = 0; b < m; ++b) {
+        int found = 0;
+        for (int ez = 0; ez < N[2] && !found; ++ez)
+            for (int ey = 0; ey < N[1] && !found; ++ey)
+                for (int ex = 0; ex < N[0] && !found; ++ex)
+                    if (invert_trilinear(N, Xn, ex, ey, ez, X + 3 * b, xi + 3 * b)) {
+                        elem[b] = ex + N[0] * (ey + N[1] * ez);
+                        found = 1;
+                    }
+        if (!found) {
+            elem[b] = -1;
+            xi[3 * b] = xi[3 * b + 1] = xi[3 * b + 2] = 0.0;
+            ++outside;
+        }
     }
     return outside;
 }
