@@ -540,7 +540,8 @@ int64_t or_locate(const int N[3], const double x0[3], const double h[3], int64_t
  * brute force over the elements in element order; in each, Newton's method
  * on the trilinear map x(xi) = sum_a N_a(xi) x_a from xi = 0 (at most 50
  * iterations, stop when the update is below 1e-15); the point belongs to
- * the first element whose xi satisfies |xi_k| <= 1 + 1e-10.  Outside points
+ * the first element where the iteration settles (last update below 1e-12:
+ * a root of x(xi) = X) at a xi with |xi_k| <= 1 + 1e-10.  Outside points
  * get elem = -1, xi = 0.  Returns the outside count.                        */
 static int invert_trilinear(const int N[3], const double *Xn, int ex, int ey, int ez,
                             const double X[3], double xi[3])
@@ -551,6 +552,7 @@ static int invert_trilinear(const int N[3], const double *Xn, int ex, int ey, in
         for (int i = 0; i < 3; ++i) xa[a][i] = x[i];
     }
     xi[0] = xi[1] = xi[2] = 0.0;
+    double last = 1.0;
     for (int it = 0; it < 50; ++it) {
         double Nv[8], dN[24], r[3] = {0, 0, 0}, J[3][3] = {{0}};
         or_shape(xi, Nv, dN);
@@ -581,8 +583,11 @@ static int invert_trilinear(const int N[3], const double *Xn, int ex, int ey, in
             if (fabs(d[k]) > mx) mx = fabs(d[k]);
             if (!(fabs(xi[k]) < 10.0)) return 0;
         }
+        last = mx;
         if (mx < 1e-15) break;
     }
+    /* a root only: an iteration that has not settled says nothing */
+    if (!(last < 1e-12)) return 0;
     for (int k = 0; k < 3; ++k)
         if (!(fabs(xi[k]) <= 1.0 + 1e-10)) return 0;
     return 1;

@@ -205,3 +205,26 @@ def test_mapped_location_inverts_the_trilinear_map(oracle):
     e0, xi0, _ = core.locate(gu, Q)
     e1, xi1, _ = core.locate(core.Grid(N, coords=gu.node_coords()), Q)
     assert np.array_equal(e0, e1) and np.abs(xi0 - xi1).max() < 1e-13
+
+
+def test_mapped_location_on_strongly_distorted_grid(oracle):
+    """Nodes moved by up to 0.2 h per axis: the brute-force search passes
+    through many far elements whose Newton iteration wanders without settling;
+    only a settled root inside the cube counts, so every point lands in the
+    element it was mapped from."""
+    core = oracle.core
+    rng = np.random.default_rng(3)
+    N = (7, 6, 5)
+    X = core.Grid(N).node_coords()
+    d = 0.2 * rng.uniform(-1, 1, X.shape) * (1.0 / np.array(N))[None, :]
+    d[np.any((X < 1e-12) | (X > 1 - 1e-12), axis=1)] = 0.0
+    X = X + d
+    g = core.Grid(N, coords=X)
+    m = 800
+    rng = np.random.default_rng(4)
+    e_true = rng.integers(0, g.n_elems, m)
+    xi_true = rng.uniform(-0.95, 0.95, (m, 3))
+    P = np.array([core.shape(xi_true[b])[0] @ X[local_nodes(g, e_true[b])] for b in range(m)])
+    e, xi, nout = core.locate(g, P)
+    assert nout == 0 and np.array_equal(e, e_true.astype(np.int32))
+    assert np.abs(xi - xi_true).max() < 1e-12
