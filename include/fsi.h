@@ -229,6 +229,21 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
                           const void *xi, const int32_t *cell_start, const int32_t *perm,
                           const void *lam, const void *w, void *F, int accumulate);
 
+/* Mapped (curvilinear) structured background grid: X [n][3] FP64 device
+ * array of node coordinates in the mesh's node numbering (copied), NULL to
+ * return to the uniform grid.  Every element must map the parent cube with a
+ * positive Jacobian.  With coordinates the VMS operators take the geometry of
+ * each Gauss point from the trilinear map (dx/dxi, det, the full metric
+ * G_ij = sum_k dxi_k/dx_i dxi_k/dx_j of Sec. 2.1, gradients through J^-T),
+ * and fsi_locate finds elements by a bounded walk with Newton inversion of the
+ * trilinear map (started in the element the nominal uniform box gives; at
+ * most Nx + Ny + Nz + 8 elements, 30 Newton iterations each; a point counts
+ * as inside when |xi_k| <= 1 + 1e-10).  Interpolation and spreading only
+ * need (elem, xi) and work unchanged.  The nominal N, x0, h of the mesh stay
+ * in use for the walk's start and the Schur preconditioner's pressure
+ * operator (an approximation there).  Synchronises the mesh stream.        */
+fsi_status fsi_mesh_set_coordinates(fsi_mesh *mesh, const double *X);
+
 /* ----------------------------------------------------------------------- */
 /* One implicit step: the reduced FSI system of Sec. 2.4.                    */
 
@@ -534,8 +549,9 @@ enum {
 };
 
 /* Build a batch (descriptors, prefix sums and its own scratch) on `cuda_stream`.
- * All meshes must be on one device.  The batch uses one brick shape for all
- * instances (default 8x8x4; see fsi_batch_autotune).                       */
+ * All meshes must be on one device and uniform (no fsi_mesh_set_coordinates;
+ * FSI_ERR_ARG otherwise).  The batch uses one brick shape for all instances
+ * (default 8x8x4; see fsi_batch_autotune).                                 */
 fsi_status fsi_batch_create(fsi_mesh *const *meshes, const fsi_batch_item *items, int count,
                             fsi_prec prec, void *cuda_stream, fsi_batch **out);
 void fsi_batch_destroy(fsi_batch *batch);

@@ -133,6 +133,7 @@ _SIGS = {
     "fsi_solid_stage": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _INT),
     "fsi_solid_advance": ([_VP, _VP, _VP, _VP, _VP], _INT),
     "fsi_solid_positions": ([_VP, _VP, _VP], _INT),
+    "fsi_mesh_set_coordinates": ([_VP, _VP], _INT),
     "fsi_interface_scaling": ([_VP, _VP, ctypes.c_double, _INT, _VP], _INT),
     "fsi_pressure_levels": ([_VP, ctypes.POINTER(ctypes.c_int32), _VP], _INT),
     "fsi_pressure_set_faces": ([_VP, ctypes.POINTER(ctypes.c_int32)], _INT),
@@ -245,6 +246,10 @@ class Mesh:
     def set_stream(self, stream):
         self._stream = stream
         _check(lib().fsi_mesh_set_stream(self.handle, ctypes.c_void_p(stream)))
+
+    def set_coordinates(self, X):
+        """Node coordinates [n, 3] FP64 (device) of a mapped grid, None = uniform."""
+        fsi_mesh_set_coordinates(self, X)
 
     def set_physics(self, **kw):
         for k, v in kw.items():
@@ -555,6 +560,13 @@ def fsi_solid_positions(body: Solid, u, x):
     import torch
     d = torch.float64
     _check(lib().fsi_solid_positions(body.handle, _ptr(u, d), _ptr(x, d)))
+
+
+def fsi_mesh_set_coordinates(mesh: Mesh, X):
+    import torch
+    if X is not None and X.numel() != 3 * mesh.n_nodes:
+        raise ValueError("coordinates must be [n_nodes, 3]")
+    _check(lib().fsi_mesh_set_coordinates(mesh.handle, _ptr(X, torch.float64)))
 
 
 def fsi_interface_scaling(mesh: Mesh, cell_start, s_band, layers, s):

@@ -107,6 +107,15 @@ __device__ __forceinline__ df64 df_rsqrt(df64 x)
     return r + r * (corr * half);
 }
 
+// 1/x: float reciprocal, then one Newton step r += r (1 - x r) in
+// double-float (doubles the ~24 correct bits)
+__device__ __forceinline__ df64 df_rcp(df64 x)
+{
+    const df64 r(__frcp_rn(x.hi), 0.0f);
+    const df64 one(1.0f, 0.0f);
+    return r + r * (one - x * r);
+}
+
 __device__ __forceinline__ df64 df_shfl_xor(df64 v, int m)
 {
     return df64(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));

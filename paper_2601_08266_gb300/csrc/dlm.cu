@@ -74,6 +74,123 @@ __global__ void locate_kernel(int64_t m, GridArgs g, const double *__restrict__ 
     }
 }
 
+// Mapped grid (node coordinates C [n][4]): element walk with Newton's method
+// on the trilinear map.  Start in the element the uniform formula gives (the
+// mesh's nominal box, clamped), invert x(xi) = X there (at most 30 Newton
+// iterations from xi = 0, a root once the update falls below 1e-12); inside
+// when |xi_k| <= 1 + 1e-10; otherwise step to
+// the neighbour across the face of the largest violation, at most
+// Nx + Ny + Nz + 8 steps.  Leaving the grid, or running out of steps, is
+// "outside".  Every loop is bounded.
+__device__ bool newton_in_element(const GridArgs &g, const double4 *__restrict__ C, int ex, int ey,
+                                  int ez, const double X[3], double xi[3])
+{
+    const int NX1 = g.Nx + 1, NXY1 = (g.Nx + 1) * (g.Ny + 1);
+    const int64_t n0 = ex + (int64_t)NX1 * ey + (int64_t)NXY1 * ez;
+    double xa[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const double4 c = C[n0 + (a & 1) + NX1 * ((a >> 1) & 1) + (int64_t)NXY1 * ((a >> 2) & 1)];
+        xa[a][0] = c.x;
+        xa[a][1] = c.y;
+        xa[a][2] = c.z;
+    }
+    xi[0] = xi[1] = xi[2] = 0.0;
+    double last = 1.0;
+    for (int it = 0; it < 30; ++it) {
+        double r[3] = {-X[0], -X[1], -X[2]}, J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const double s0 = (a & 1) ? 1.0 : -1.0, s1 = (a & 2) ? 1.0 : -1.0, s2 = (a & 4) ? 1.0 : -1.0;
+            const double l0 = 1.0 + s0 * xi[0], l1 = 1.0 + s1 * xi[1], l2 = 1.0 + s2 * xi[2];
+            const double N = 0.125 * l0 * l1 * l2;
+            const double d0 = 0.125 * s0 * l1 * l2, d1 = 0.125 * l0 * s1 * l2, d2 = 0.125 * l0 * l1 * s2;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                r[i] += N * xa[a][i];
+                J[i][0] += xa[a][i] * d0;
+                J[i][1] += xa[a][i] * d1;
+                J[i][2] += xa[a][i] * d2;
+            }
+        }
+        const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+        if (!(fabs(det) > 0.0)) return false;
+        // J d = r by Cramer's rule
+        const double d0 = (r[0] * c00 + J[0][1] * (J[1][2] * r[2] - r[1] * J[2][2]) +
+                           J[0][2] * (r[1] * J[2][1] - J[1][1] * r[2])) / det;
+        const double d1 = (J[0][0] * (r[1] * J[2][2] - J[1][2] * r[2]) + r[0] * c01 +
+                           J[0][2] * (J[1][0] * r[2] - r[1] * J[2][0])) / det;
+        const double d2 = (J[0][0] * (J[1][1] * r[2] - r[1] * J[2][1]) +
+                           J[0][1] * (r[1] * J[2][0] - J[1][0] * r[2]) + r[0] * c02) / det;
+        xi[0] -= d0;
+        xi[1] -= d1;
+        xi[2] -= d2;
+        if (!(fabs(xi[0]) < 10.0 && fabs(xi[1]) < 10.0 && fabs(xi[2]) < 10.0)) return false;
+        last = fmax(fabs(d0), fmax(fabs(d1), fabs(d2)));
+        if (last < 1e-15) break;
+    }
+    return last < 1e-12;  // a settled root only
+}
+
+__global__ void locate_mapped_kernel(int64_t m, GridArgs g, const double4 *__restrict__ C,
+                                     const double *__restrict__ Xp, int32_t *__restrict__ elem,
+                                     double *__restrict__ xi, int32_t *__restrict__ count,
+                                     unsigned long long *n_out)
+{
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const double X[3] = {Xp[3 * b], Xp[3 * b + 1], Xp[3 * b + 2]};
+        const double t[3] = {(X[0] - g.x0) / g.hx, (X[1] - g.y0) / g.hy, (X[2] - g.z0) / g.hz};
+        const int N3[3] = {g.Nx, g.Ny, g.Nz};
+        int e3[3];
+        bool finite = true;
+        for (int k = 0; k < 3; ++k) {
+            finite = finite && isfinite(t[k]);
+            const double c = finite ? floor(t[k]) : 0.0;
+            e3[k] = c < 0.0 ? 0 : (c > (double)(N3[k] - 1) ? N3[k] - 1 : (int)c);
+        }
+        int found = 0;
+        double q[3] = {0.0, 0.0, 0.0};
+        const int max_steps = g.Nx + g.Ny + g.Nz + 8;
+        for (int step = 0; step < max_steps && finite; ++step) {
+            const bool ok = newton_in_element(g, C, e3[0], e3[1], e3[2], X, q);
+            if (ok && fabs(q[0]) <= 1.0 + 1e-10 && fabs(q[1]) <= 1.0 + 1e-10 &&
+                fabs(q[2]) <= 1.0 + 1e-10) {
+                found = 1;
+                break;
+            }
+            // the face of the largest violation (Newton failure: toward the
+            // point from the element's centre is not known, stop)
+            if (!ok) break;
+            int k = 0;
+            double worst = fabs(q[0]);
+            for (int d = 1; d < 3; ++d)
+                if (fabs(q[d]) > worst) {
+                    worst = fabs(q[d]);
+                    k = d;
+                }
+            const int next = e3[k] + (q[k] > 0.0 ? 1 : -1);
+            if (next < 0 || next >= N3[k]) break;
+            e3[k] = next;
+        }
+        if (!found) {
+            elem[b] = -1;
+            xi[3 * b] = xi[3 * b + 1] = xi[3 * b + 2] = 0.0;
+            atomicAdd(n_out, 1ull);
+            continue;
+        }
+        const int e = e3[0] + g.Nx * (e3[1] + g.Ny * e3[2]);
+        elem[b] = e;
+        xi[3 * b] = q[0];
+        xi[3 * b + 1] = q[1];
+        xi[3 * b + 2] = q[2];
+        if (count) atomicAdd(count + e, 1);
+    }
+}
+
 // --------------------------------------------------------------- scan
 // Exclusive scan of count[0..E) into start[0..E] (start[E] = total) with
 // 2048-entry tiles: (1) tile-local inclusive scan + tile totals, (2) one CTA
@@ -392,7 +509,12 @@ fsi_status fsi_locate(fsi_mesh *mesh, int64_t m, const double *X, int32_t *elem,
     const bool table = cell_start != nullptr;
     if (table) FSI_CUDA(cudaMemsetAsync(mesh->hash_fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
     GridArgs g = grid_args(mesh);
-    if (m > 0) {
+    if (m > 0 && mesh->coords64) {
+        locate_mapped_kernel<<<blocks_for(m, 128), 128, 0, s>>>(
+            m, g, (const double4 *)mesh->coords64, X, elem, xi,
+            table ? mesh->hash_fill : nullptr, nout);
+        FSI_TRY(check_launch("locate kernel"));
+    } else if (m > 0) {
         locate_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, g, X, elem, xi,
                                                          table ? mesh->hash_fill : nullptr, nout);
         FSI_TRY(check_launch("locate kernel"));

@@ -82,6 +82,9 @@ struct fsi_mesh {
     fsi::NewtonWorkspace *newton;
     // pressure multigrid hierarchy of the Schur preconditioner (pmg.cu)
     fsi::PressureMG *pmg;
+    // mapped grid: node coordinates padded to [n][4], FP64 and FP32 copies
+    // (null on the uniform grid)
+    void *coords64, *coords32;
 };
 
 namespace fsi {

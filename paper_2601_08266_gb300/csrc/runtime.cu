@@ -222,6 +222,8 @@ void fsi_mesh_destroy(fsi_mesh *m)
     cudaFree(m->spread_scratch);
     destroy_newton_workspace(m);
     destroy_pmg(m);
+    cudaFree(m->coords64);
+    cudaFree(m->coords32);
     delete m;
 }
 
@@ -230,6 +232,45 @@ fsi_status fsi_mesh_set_stream(fsi_mesh *m, void *cuda_stream)
     FSI_TRY(validate_mesh(m));
     m->stream = (cudaStream_t)cuda_stream;
     return FSI_OK;
+}
+
+namespace {
+__global__ void pad_coords_kernel(int64_t n, const double *X, double4 *C64, float4 *C32)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
+        C64[i] = make_double4(x, y, z, 0.0);
+        C32[i] = make_float4((float)x, (float)y, (float)z, 0.0f);
+    }
+}
+}  // namespace
+
+fsi_status fsi_mesh_set_coordinates(fsi_mesh *m, const double *X)
+{
+    FSI_TRY(validate_mesh(m));
+    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    FSI_CUDA(cudaStreamSynchronize(m->stream), "sync");
+    if (!X) {
+        cudaFree(m->coords64);
+        cudaFree(m->coords32);
+        m->coords64 = m->coords32 = nullptr;
+        return FSI_OK;
+    }
+    if (!m->coords64) {
+        if (cudaMalloc(&m->coords64, (size_t)m->n_nodes * sizeof(double4)) != cudaSuccess ||
+            cudaMalloc(&m->coords32, (size_t)m->n_nodes * sizeof(float4)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(m->coords64);
+            m->coords64 = m->coords32 = nullptr;
+            return set_error(FSI_ERR_OOM, "fsi_mesh_set_coordinates: cudaMalloc failed");
+        }
+    }
+    int64_t blocks = (m->n_nodes + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    pad_coords_kernel<<<(int)blocks, 256, 0, m->stream>>>(m->n_nodes, X, (double4 *)m->coords64,
+                                                          (float4 *)m->coords32);
+    return check_launch("pad coordinates kernel");
 }
 
 fsi_status fsi_mesh_set_physics(fsi_mesh *m, const fsi_physics *phys)

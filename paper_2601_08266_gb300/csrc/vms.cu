@@ -30,11 +30,11 @@ namespace {
 
 using namespace vmsd;
 
-template <typename T, bool JAC>
+template <typename T, bool JAC, bool MAPPED>
 __global__ void __launch_bounds__(256) vms_brick_kernel(const VmsArgs<T> P)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    brick_body<T, JAC>(P, blockIdx.x, reinterpret_cast<vec4<T> *>(smem_raw));
+    brick_body<T, JAC, MAPPED>(P, blockIdx.x, reinterpret_cast<vec4<T> *>(smem_raw));
 }
 
 template <typename T> __global__ void vms_gather_kernel(const VmsArgs<T> P)
@@ -45,9 +45,9 @@ template <typename T> __global__ void vms_gather_kernel(const VmsArgs<T> P)
         gather_node(P, node);
 }
 
-template <typename T, bool JAC>
-fsi_status launch(fsi_mesh *m, const void *U, const void *A, const void *f, const void *x,
-                  void *out)
+template <typename T, bool JAC, bool MAPPED>
+fsi_status launch_geo(fsi_mesh *m, const void *U, const void *A, const void *f, const void *x,
+                      void *out)
 {
     const Brick &b = m->brick[JAC ? 1 : 0][sizeof(typename StorageOf<T>::type) == 8 ? FSI_F64 : FSI_F32];
     FSI_TRY(ensure_vms_scratch(m, b, sizeof(T)));
@@ -56,18 +56,28 @@ fsi_status launch(fsi_mesh *m, const void *U, const void *A, const void *f, cons
     const size_t smem = (size_t)b.bx * b.by * b.bz * 8 * sizeof(vec4<typename StorageOf<T>::type>);
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
-        FSI_CUDA(cudaFuncSetAttribute(vms_brick_kernel<T, JAC>,
+        FSI_CUDA(cudaFuncSetAttribute(vms_brick_kernel<T, JAC, MAPPED>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
                  "cudaFuncSetAttribute");
         attr_set = true;
     }
-    vms_brick_kernel<T, JAC><<<nbricks, b.threads, smem, m->stream>>>(P);
+    vms_brick_kernel<T, JAC, MAPPED><<<nbricks, b.threads, smem, m->stream>>>(P);
     FSI_TRY(check_launch("vms brick kernel"));
     const int threads = 256;
     int64_t nb = (m->n_nodes + threads - 1) / threads;
     if (nb > 152 * 32) nb = 152 * 32;
     vms_gather_kernel<T><<<(int)nb, threads, 0, m->stream>>>(P);
     return check_launch("vms gather kernel");
+}
+
+// the mapped-grid kernels take the geometry of every Gauss point from the
+// node coordinates (set by fsi_mesh_set_coordinates)
+template <typename T, bool JAC>
+fsi_status launch(fsi_mesh *m, const void *U, const void *A, const void *f, const void *x,
+                  void *out)
+{
+    if (m->coords64) return launch_geo<T, JAC, true>(m, U, A, f, x, out);
+    return launch_geo<T, JAC, false>(m, U, A, f, x, out);
 }
 
 }  // namespace

@@ -46,7 +46,9 @@ template <typename T> struct VmsArgs {
     T ih0, ih1, ih2;            // 1/h_k
     T detJ;
     T c_a, c_v;                 // d A / d y_v, d U / d y_v
+    T ct_dt2, CInu2;            // C_T/dt^2 and C_I (mu/rho)^2 (mapped grids: G per Gauss point)
     int has_s;
+    const vec4<S> *Xc;          // mapped grids: node coordinates [n][4] (x, y, z, 0), else null
     const vec4<S> *U, *A, *f, *x;
     vec4<T> *blocks;  // [n_bricks][(bx+1)(by+1)(bz+1)], in the compute type
     vec4<S> *out;     // [n]
@@ -118,6 +120,9 @@ __device__ __forceinline__ T project(T X, T Yx, T Yy, T Yz, T sx, T sy, T sz)
     return b1 * Q1 + b2 * Q1o + sx * (Q2 + Q2o);
 }
 
+template <typename T> __device__ __forceinline__ T inv_t(T v) { return T(1) / v; }
+template <> __device__ __forceinline__ df64 inv_t<df64>(df64 v) { return df_rcp(v); }
+
 template <typename T> __device__ __forceinline__ T rsqrt_t(T v);
 template <> __device__ __forceinline__ float rsqrt_t(float v) { return 1.0f / sqrtf(v); }
 template <> __device__ __forceinline__ double rsqrt_t(double v) { return 1.0 / sqrt(v); }
@@ -147,9 +152,46 @@ __device__ __forceinline__ void base_state(const VmsArgs<T> &P, GP<T> &q)
     q.pp = -P.rho * q.tauC * q.rC;
 }
 
+// Geometry of one Gauss point on a mapped grid: Ji = (dx/dxi)^{-1}, det,
+// the metric G = Ji^T Ji of Sec. 2.1 (full), tr G and the bracket constant.
+template <typename T> struct Geo {
+    T Ji[3][3], det, G[3][3], inv_trG, q0;
+};
+
+// base state with a per-Gauss-point metric (mapped grids)
+template <typename T>
+__device__ __forceinline__ void base_state_g(const VmsArgs<T> &P, const Geo<T> &geo, GP<T> &q)
+{
+    for (int i = 0; i < 3; ++i) {
+        q.conv[i] = q.v[0] * q.gv[i][0] + q.v[1] * q.gv[i][1] + q.v[2] * q.gv[i][2];
+        q.rM[i] = P.rho * (q.a[i] + q.conv[i] - q.f[i]) + q.gp[i];
+    }
+    q.rC = q.gv[0][0] + q.gv[1][1] + q.gv[2][2];
+    T vGv = T(0);
+    for (int i = 0; i < 3; ++i)
+        vGv += q.v[i] * (geo.G[i][0] * q.v[0] + geo.G[i][1] * q.v[1] + geo.G[i][2] * q.v[2]);
+    q.vGv = vGv;
+    const T S = q.s * (geo.q0 + q.vGv);
+    q.tauM = rsqrt_t(S);
+    q.tauC = S * q.tauM * geo.inv_trG;
+    const T c = -q.tauM * P.inv_rho;
+    for (int i = 0; i < 3; ++i) q.up[i] = c * q.rM[i];
+    q.pp = -P.rho * q.tauC * q.rC;
+}
+
+// physical gradient from the reference one: g_j = sum_k gref_k Ji[k][j]
+template <typename T>
+__device__ __forceinline__ void to_phys(const Geo<T> &geo, VG<T> &e)
+{
+    const T a = e.gx, b = e.gy, c = e.gz;
+    e.gx = a * geo.Ji[0][0] + b * geo.Ji[1][0] + c * geo.Ji[2][0];
+    e.gy = a * geo.Ji[0][1] + b * geo.Ji[1][1] + c * geo.Ji[2][1];
+    e.gz = a * geo.Ji[0][2] + b * geo.Ji[1][2] + c * geo.Ji[2][2];
+}
+
 // One brick of elements: element contributions into rel (shared memory,
 // [bx*by*bz][8] node records), then the brick's node block into P.blocks.
-template <typename T, bool JAC>
+template <typename T, bool JAC, bool MAPPED = false>
 __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<T> *rel)
 {
     const int g = threadIdx.x & 7;
@@ -158,9 +200,11 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
     const int nel = P.bx * P.by * P.bz;
     const int groups = blockDim.x >> 3;
     const int gx = g & 1, gy = (g >> 1) & 1, gz = (g >> 2) & 1;
-    const T sx = gx ? P.ih0 : -P.ih0;
-    const T sy = gy ? P.ih1 : -P.ih1;
-    const T sz = gz ? P.ih2 : -P.ih2;
+    // gradient signs of the butterfly: physical (+-1/h) on the uniform grid,
+    // reference (+-1/2 per unit of xi) on a mapped grid
+    const T sx = MAPPED ? (gx ? T(0.5f) : T(-0.5f)) : (gx ? P.ih0 : -P.ih0);
+    const T sy = MAPPED ? (gy ? T(0.5f) : T(-0.5f)) : (gy ? P.ih1 : -P.ih1);
+    const T sz = MAPPED ? (gz ? T(0.5f) : T(-0.5f)) : (gz ? P.ih2 : -P.ih2);
     const int NX1 = P.Nx + 1, NXY1 = (P.Nx + 1) * (P.Ny + 1);
 
     for (int base = 0; base < nel; base += groups) {
@@ -174,10 +218,50 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
         vec4<T> ac = valid ? load_c<T>(P.A + node) : zero;
         vec4<T> ff = (valid && P.f) ? load_c<T>(P.f + node) : zero;
 
+        Geo<T> geo;
+        if constexpr (MAPPED) {
+            // dx_c/dxi_k at this lane's Gauss point; idle lanes take a unit cell
+            vec4<T> xc = valid ? load_c<T>(P.Xc + node)
+                               : vec4<T>{gx ? T(1) : T(0), gy ? T(1) : T(0), gz ? T(1) : T(0), T(0)};
+            const VG<T> cx = eval_vg(xc.x, sx, sy, sz), cy = eval_vg(xc.y, sx, sy, sz),
+                        cz = eval_vg(xc.z, sx, sy, sz);
+            const T J[3][3] = {{cx.gx, cx.gy, cx.gz}, {cy.gx, cy.gy, cy.gz}, {cz.gx, cz.gy, cz.gz}};
+            const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+            const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+            const T c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+            geo.det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+            const T id = inv_t(geo.det);
+            geo.Ji[0][0] = c00 * id;
+            geo.Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+            geo.Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+            geo.Ji[1][0] = c01 * id;
+            geo.Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+            geo.Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+            geo.Ji[2][0] = c02 * id;
+            geo.Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+            geo.Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+            T trG = T(0), GG = T(0);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    const T gij = geo.Ji[0][i] * geo.Ji[0][j] + geo.Ji[1][i] * geo.Ji[1][j] +
+                                  geo.Ji[2][i] * geo.Ji[2][j];
+                    geo.G[i][j] = gij;
+                    GG += gij * gij;
+                }
+            trG = geo.G[0][0] + geo.G[1][1] + geo.G[2][2];
+            geo.inv_trG = inv_t(trG);
+            geo.q0 = P.ct_dt2 + P.CInu2 * GG;
+        }
         GP<T> q;
         {
             VG<T> e0 = eval_vg(u.x, sx, sy, sz), e1 = eval_vg(u.y, sx, sy, sz),
                   e2 = eval_vg(u.z, sx, sy, sz), e3 = eval_vg(u.w, sx, sy, sz);
+            if constexpr (MAPPED) {
+                to_phys(geo, e0);
+                to_phys(geo, e1);
+                to_phys(geo, e2);
+                to_phys(geo, e3);
+            }
             q.v[0] = e0.v; q.gv[0][0] = e0.gx; q.gv[0][1] = e0.gy; q.gv[0][2] = e0.gz;
             q.v[1] = e1.v; q.gv[1][0] = e1.gx; q.gv[1][1] = e1.gy; q.gv[1][2] = e1.gz;
             q.v[2] = e2.v; q.gv[2][0] = e2.gx; q.gv[2][1] = e2.gy; q.gv[2][2] = e2.gz;
@@ -195,7 +279,10 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
             q.f[0] = q.f[1] = q.f[2] = T(0);
         }
         if (!valid) q.s = T(1);  // keep tau finite on idle lanes
-        base_state(P, q);
+        if constexpr (MAPPED)
+            base_state_g(P, geo, q);
+        else
+            base_state(P, q);
 
         T X[4], Y[4][3];
         if (!JAC) {
@@ -216,6 +303,12 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
             {
                 VG<T> e0 = eval_vg(xx.x, sx, sy, sz), e1 = eval_vg(xx.y, sx, sy, sz),
                       e2 = eval_vg(xx.z, sx, sy, sz), e3 = eval_vg(xx.w, sx, sy, sz);
+                if constexpr (MAPPED) {
+                    to_phys(geo, e0);
+                    to_phys(geo, e1);
+                    to_phys(geo, e2);
+                    to_phys(geo, e3);
+                }
                 const T cv = P.c_v, ca = P.c_a;
                 dv[0] = cv * e0.v; da[0] = ca * e0.v;
                 dv[1] = cv * e1.v; da[1] = ca * e1.v;
@@ -233,10 +326,19 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
             }
             const T drC = dgv[0][0] + dgv[1][1] + dgv[2][2];
             // d tau_M = -1/2 tau_M^3 s dQ with dQ = 2 v.G dv
-            const T vGdv = P.G0 * q.v[0] * dv[0] + P.G1 * q.v[1] * dv[1] + P.G2 * q.v[2] * dv[2];
+            T vGdv;
+            if constexpr (MAPPED) {
+                vGdv = T(0);
+                for (int i = 0; i < 3; ++i)
+                    vGdv += q.v[i] * (geo.G[i][0] * dv[0] + geo.G[i][1] * dv[1] + geo.G[i][2] * dv[2]);
+            } else {
+                vGdv = P.G0 * q.v[0] * dv[0] + P.G1 * q.v[1] * dv[1] + P.G2 * q.v[2] * dv[2];
+            }
             const T dtauM = -q.tauM * q.tauM * q.tauM * q.s * vGdv;
             // d tau_C = -tau_C d tau_M / tau_M, 1/tau_M = s (q0 + vGv) tau_M
-            const T dtauC = -q.tauC * dtauM * (q.s * (P.q0 + q.vGv) * q.tauM);
+            T q0 = P.q0;
+            if constexpr (MAPPED) q0 = geo.q0;
+            const T dtauC = -q.tauC * dtauM * (q.s * (q0 + q.vGv) * q.tauM);
             for (int i = 0; i < 3; ++i) dup[i] = -(dtauM * q.rM[i] + q.tauM * drM[i]) * P.inv_rho;
             const T dpp = -P.rho * (dtauC * q.rC + q.tauC * drC);
             for (int i = 0; i < 3; ++i) {
@@ -252,10 +354,25 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
             for (int j = 0; j < 3; ++j) Y[3][j] = -dup[j];
         }
         vec4<T> r;
-        r.x = P.detJ * project(X[0], Y[0][0], Y[0][1], Y[0][2], sx, sy, sz);
-        r.y = P.detJ * project(X[1], Y[1][0], Y[1][1], Y[1][2], sx, sy, sz);
-        r.z = P.detJ * project(X[2], Y[2][0], Y[2][1], Y[2][2], sx, sy, sz);
-        r.w = P.detJ * project(X[3], Y[3][0], Y[3][1], Y[3][2], sx, sy, sz);
+        if constexpr (MAPPED) {
+            // grad N . Y = grad_xi N . (Ji Y); det J per Gauss point
+            for (int c = 0; c < 4; ++c) {
+                const T y0 = Y[c][0], y1 = Y[c][1], y2 = Y[c][2];
+                Y[c][0] = geo.det * (geo.Ji[0][0] * y0 + geo.Ji[0][1] * y1 + geo.Ji[0][2] * y2);
+                Y[c][1] = geo.det * (geo.Ji[1][0] * y0 + geo.Ji[1][1] * y1 + geo.Ji[1][2] * y2);
+                Y[c][2] = geo.det * (geo.Ji[2][0] * y0 + geo.Ji[2][1] * y1 + geo.Ji[2][2] * y2);
+                X[c] = geo.det * X[c];
+            }
+            r.x = project(X[0], Y[0][0], Y[0][1], Y[0][2], sx, sy, sz);
+            r.y = project(X[1], Y[1][0], Y[1][1], Y[1][2], sx, sy, sz);
+            r.z = project(X[2], Y[2][0], Y[2][1], Y[2][2], sx, sy, sz);
+            r.w = project(X[3], Y[3][0], Y[3][1], Y[3][2], sx, sy, sz);
+        } else {
+            r.x = P.detJ * project(X[0], Y[0][0], Y[0][1], Y[0][2], sx, sy, sz);
+            r.y = P.detJ * project(X[1], Y[1][0], Y[1][1], Y[1][2], sx, sy, sz);
+            r.z = P.detJ * project(X[2], Y[2][0], Y[2][1], Y[2][2], sx, sy, sz);
+            r.w = P.detJ * project(X[3], Y[3][0], Y[3][1], Y[3][2], sx, sy, sz);
+        }
         if (slot < nel) rel[slot * 8 + g] = valid ? r : zero;
     }
     __syncthreads();
@@ -368,8 +485,11 @@ VmsArgs<T> make_args(const fsi_mesh *m, const Brick &b, const void *U, const voi
     P.detJ = (T)(h[0] * h[1] * h[2] / 8.0);
     P.c_a = (T)m->alpha_m;
     P.c_v = (T)(m->alpha_f * m->gamma * dt);
+    P.ct_dt2 = (T)(m->phys.C_T / (dt * dt));
+    P.CInu2 = (T)(m->phys.C_I * nu * nu);
     P.has_s = m->phys.has_s != 0;
     using S = typename StorageOf<T>::type;
+    P.Xc = (const vec4<S> *)(sizeof(S) == 8 ? m->coords64 : m->coords32);
     P.U = (const vec4<S> *)U;
     P.A = (const vec4<S> *)A;
     P.f = (const vec4<S> *)f;
