@@ -457,6 +457,8 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
             extras["mlp_inference"] = mlp_section(args, dev, stream2, W)
         if "solid" in sections:
             extras["solid"] = solid_section(args, dev, stream2)
+        if "mapped" in sections:
+            extras["mapped"] = mapped_section(args, dev, stream2)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
@@ -505,7 +507,7 @@ class Channel:
     profile plus 0.01 x a seeded smooth Fourier perturbation.  Three leaflets
     of m volume-weighted points (total volume 0.024, rho_s - rho_f = 0.5)."""
 
-    def __init__(self, fsi, dev, stream, N, m, leaflet_seed, dt=1e-3, mu=1e-3):
+    def __init__(self, fsi, dev, stream, N, m, leaflet_seed, dt=1e-3, mu=1e-3, bubble=0.0):
         import torch
         from paper_2601_08266_gb300 import inputs
         self.fsi, self.dev, self.stream, self.N, self.m, self.dt = fsi, dev, stream, N, m, dt
@@ -515,6 +517,11 @@ class Channel:
         ax = np.arange(N + 1) / N
         Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
         X, Y, Z = X.ravel(), Y.ravel(), Z.ravel()
+        if bubble:
+            # a mapped grid: the faces of the cube stay in place (same masks)
+            with torch.cuda.stream(stream):
+                self.mesh.set_coordinates(torch.as_tensor(bubble_map(np.stack([X, Y, Z], 1),
+                                                                     bubble), device=dev))
         prof = 16.0 * Y * (1 - Y) * Z * (1 - Z)
         wall = (Y < 1e-12) | (Y > 1 - 1e-12) | (Z < 1e-12) | (Z > 1 - 1e-12)
         inflow = (X < 1e-12) & ~wall
@@ -877,6 +884,101 @@ def solid_section(args, dev, stream):
     return out
 
 
+# ------------------------------------------------------------------ mapped grids
+def bubble_map(X, delta):
+    """Smooth map of the unit cube onto itself, identity on its faces."""
+    b = np.sin(2 * np.pi * X[:, 0]) * np.sin(2 * np.pi * X[:, 1]) * np.sin(2 * np.pi * X[:, 2])
+    return X + delta * b[:, None] * np.array([1.0, -0.7, 0.4])[None, :]
+
+
+def mapped_section(args, dev, stream):
+    """Mapped (curvilinear) structured grids: the VMS kernels with per-Gauss-point
+    geometry against the uniform kernels on the same 128^3 grid, point location
+    by the element walk, and the mixed Newton step of the 64^3 channel on a
+    bubble-mapped grid (the Schur preconditioner keeps the nominal uniform
+    pressure operator there)."""
+    import torch
+    import paper_2601_08266_gb300 as fsi
+    N = 128
+    out = {"grid": [N, N, N], "map": "x + 0.02 sin(2 pi x) sin(2 pi y) sin(2 pi z) (1, -0.7, 0.4)"}
+    mesh = fsi.Mesh(N, rho=1.0, mu=1e-3, dt=1e-3, rho_inf=0.5, device=dev.index,
+                    stream=stream.cuda_stream)
+    n = mesh.n_nodes
+    ax = np.arange(N + 1) / N
+    Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+    Xm = bubble_map(np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1), 0.02)
+    g = torch.Generator(device=dev).manual_seed(SEED + 80)
+    with torch.cuda.stream(stream):
+        Xd = torch.as_tensor(Xm, device=dev)
+        U = 0.5 * torch.randn((n, 4), dtype=torch.float64, device=dev, generator=g)
+        A = 0.5 * torch.randn((n, 4), dtype=torch.float64, device=dev, generator=g)
+        x = torch.randn((n, 4), dtype=torch.float64, device=dev, generator=g)
+        R = torch.empty_like(U)
+        U32, A32, x32, R32 = U.float(), A.float(), x.float(), torch.empty((n, 4),
+                                                                           dtype=torch.float32,
+                                                                           device=dev)
+
+    def timeit(fn, reps=10):
+        for _ in range(3):
+            fn()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    cases = {
+        "residual_f32": lambda: fsi.fsi_residual(mesh, fsi.FSI_F32, U32, A32, None, R32),
+        "jacobian_f32": lambda: fsi.fsi_jacobian_apply(mesh, fsi.FSI_F32, U32, A32, None, x32, R32),
+        "residual_df64": lambda: fsi.fsi_residual(mesh, fsi.FSI_DF64, U, A, None, R),
+        "jacobian_df64": lambda: fsi.fsi_jacobian_apply(mesh, fsi.FSI_DF64, U, A, None, x, R),
+        "residual_f64": lambda: fsi.fsi_residual(mesh, fsi.FSI_F64, U, A, None, R),
+        "jacobian_f64": lambda: fsi.fsi_jacobian_apply(mesh, fsi.FSI_F64, U, A, None, x, R),
+    }
+    uni = {k: timeit(f) for k, f in cases.items()}
+    with torch.cuda.stream(stream):
+        mesh.set_coordinates(Xd)
+    mapped = {k: timeit(f) for k, f in cases.items()}
+    out["vms_kernels"] = {k: {"uniform_ms": uni[k], "mapped_ms": mapped[k],
+                              "mapped_gdof_per_s": 4 * n / (mapped[k] * 1e-3) / 1e9,
+                              "mapped_over_uniform": mapped[k] / uni[k]} for k in cases}
+    # location of 2^20 points spread over the interior
+    m = 1 << 20
+    with torch.cuda.stream(stream):
+        P = 0.02 + 0.96 * torch.rand((m, 3), dtype=torch.float64, device=dev, generator=g)
+        e = torch.empty(m, dtype=torch.int32, device=dev)
+        xi = torch.empty((m, 3), dtype=torch.float64, device=dev)
+        cs = torch.empty(mesh.n_elems + 1, dtype=torch.int32, device=dev)
+        pm = torch.empty(m, dtype=torch.int32, device=dev)
+    loc = lambda: fsi.fsi_locate(mesh, P, e, xi, cs, pm, want_outside=False)
+    t_m = timeit(loc)
+    with torch.cuda.stream(stream):
+        mesh.set_coordinates(None)
+    t_u = timeit(loc)
+    out["locate"] = {"points": m, "uniform_ms": t_u, "mapped_ms": t_m,
+                     "mapped_points_per_s": m / (t_m * 1e-3)}
+    mesh.close()
+    # the mixed Newton step of the 64^3 channel, uniform against mapped
+    solve = dict(restart=50, max_newton=10, max_krylov=4000, newton_rtol=1e-8, krylov_rtol=1e-3)
+    for name, bub in (("uniform", 0.0), ("mapped", 0.02)):
+        ch = Channel(fsi, dev, stream, 64, M_POINTS, SEED + 81, bubble=bub)
+        y, st = ch.state(guess="zero")
+        stream.synchronize()
+        t0 = time.perf_counter()
+        code, rep = fsi.fsi_newton_step(ch.mesh, st, mixed=True, check=False,
+                                        residual_prec=fsi.FSI_DF64, **solve)
+        stream.synchronize()
+        out["newton_mixed_64cubed_" + name] = {
+            "seconds": time.perf_counter() - t0, "newton_iters": rep["newton_iters"],
+            "krylov_iters": rep["krylov_iters"], "r_final_over_r0": rep["r_final"] / rep["r0"],
+            "converged": bool(rep["converged"]), "status": code}
+        ch.close()
+    return out
+
+
 # ------------------------------------------------------------------ MLP inference
 def mlp_section(args, dev, stream, W):
     """Per-node inference of the initial-guess network over whole grids: the
@@ -953,7 +1055,7 @@ def main():
     ap.add_argument("--points", type=int, default=M_POINTS, help="solid points (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip Newton, batch and MLP sections")
-    ap.add_argument("--sections", default="newton,batch,mlp,solid",
+    ap.add_argument("--sections", default="newton,batch,mlp,solid,mapped",
                     help="comma-separated extra sections to run")
     ap.add_argument("--newton-grid", type=int, default=128)
     ap.add_argument("--newton-points", type=int, default=1_000_000)

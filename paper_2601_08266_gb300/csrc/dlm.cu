@@ -74,65 +74,119 @@ __global__ void locate_kernel(int64_t m, GridArgs g, const double *__restrict__ 
     }
 }
 
-// Mapped grid (node coordinates C [n][4]): element walk with Newton's method
-// on the trilinear map.  Start in the element the uniform formula gives (the
-// mesh's nominal box, clamped), invert x(xi) = X there (at most 30 Newton
-// iterations from xi = 0, a root once the update falls below 1e-12); inside
-// when |xi_k| <= 1 + 1e-10; otherwise step to
-// the neighbour across the face of the largest violation, at most
-// Nx + Ny + Nz + 8 steps.  Leaving the grid, or running out of steps, is
-// "outside".  Every loop is bounded.
-__device__ bool newton_in_element(const GridArgs &g, const double4 *__restrict__ C, int ex, int ey,
-                                  int ez, const double X[3], double xi[3])
+// Mapped grid (node coordinates C [n][4]): element walk guided by Newton's
+// method on the trilinear map x(xi) = sum_a N_a(xi) x_a.
+//
+// Walk (FP32, coordinates relative to the element's first node): start in
+// the element the nominal uniform box gives (clamped); solve x(xi) = X there
+// (at most 16 iterations from xi = 0); the extended map's root tells how many
+// elements away the point lies, so the first 6 moves jump floor((xi_k+1)/2)
+// elements per axis (at most 8), later moves one element across the face of
+// the largest violation.  Once the FP32 root lies in the cube widened by 1e-3,
+// Newton's method in FP64 from that root decides: a settled root (last update
+// below 1e-12) with |xi_k| <= 1 + 1e-10 places the point; otherwise the FP64
+// root steers the next move.  At most Nx + Ny + Nz + 8 elements; leaving the
+// grid, a singular map or running out of moves is "outside".  Every loop is
+// bounded.
+struct HexNodes {
+    double o[3];      // first node
+    double d[8][3];   // node - first node
+};
+
+__device__ __forceinline__ void load_hex(const GridArgs &g, const double4 *__restrict__ C, int ex,
+                                         int ey, int ez, HexNodes &H)
 {
     const int NX1 = g.Nx + 1, NXY1 = (g.Nx + 1) * (g.Ny + 1);
     const int64_t n0 = ex + (int64_t)NX1 * ey + (int64_t)NXY1 * ez;
-    double xa[8][3];
+    const double4 c0 = C[n0];
+    H.o[0] = c0.x;
+    H.o[1] = c0.y;
+    H.o[2] = c0.z;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
         const double4 c = C[n0 + (a & 1) + NX1 * ((a >> 1) & 1) + (int64_t)NXY1 * ((a >> 2) & 1)];
-        xa[a][0] = c.x;
-        xa[a][1] = c.y;
-        xa[a][2] = c.z;
+        H.d[a][0] = c.x - c0.x;
+        H.d[a][1] = c.y - c0.y;
+        H.d[a][2] = c.z - c0.z;
     }
-    xi[0] = xi[1] = xi[2] = 0.0;
-    double last = 1.0;
-    for (int it = 0; it < 30; ++it) {
-        double r[3] = {-X[0], -X[1], -X[2]}, J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+}
+
+// One Newton update d of x(xi) = Y (Y relative to the first node): r, J at xi,
+// J d = r by Cramer's rule.  False when J is singular.
+template <typename R>
+__device__ __forceinline__ bool newton_update(const R (&xa)[8][3], const R (&Y)[3], const R (&xi)[3],
+                                              R (&d)[3])
+{
+    R r[3] = {-Y[0], -Y[1], -Y[2]}, J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const double s0 = (a & 1) ? 1.0 : -1.0, s1 = (a & 2) ? 1.0 : -1.0, s2 = (a & 4) ? 1.0 : -1.0;
-            const double l0 = 1.0 + s0 * xi[0], l1 = 1.0 + s1 * xi[1], l2 = 1.0 + s2 * xi[2];
-            const double N = 0.125 * l0 * l1 * l2;
-            const double d0 = 0.125 * s0 * l1 * l2, d1 = 0.125 * l0 * s1 * l2, d2 = 0.125 * l0 * l1 * s2;
+    for (int a = 0; a < 8; ++a) {
+        const R s0 = (a & 1) ? R(1) : R(-1), s1 = (a & 2) ? R(1) : R(-1), s2 = (a & 4) ? R(1) : R(-1);
+        const R l0 = R(1) + s0 * xi[0], l1 = R(1) + s1 * xi[1], l2 = R(1) + s2 * xi[2];
+        const R N = R(0.125) * l0 * l1 * l2;
+        const R d0 = R(0.125) * s0 * l1 * l2, d1 = R(0.125) * l0 * s1 * l2, d2 = R(0.125) * l0 * l1 * s2;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                r[i] += N * xa[a][i];
-                J[i][0] += xa[a][i] * d0;
-                J[i][1] += xa[a][i] * d1;
-                J[i][2] += xa[a][i] * d2;
-            }
+        for (int i = 0; i < 3; ++i) {
+            r[i] += N * xa[a][i];
+            J[i][0] += xa[a][i] * d0;
+            J[i][1] += xa[a][i] * d1;
+            J[i][2] += xa[a][i] * d2;
         }
-        const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-        const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-        const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-        const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-        if (!(fabs(det) > 0.0)) return false;
-        // J d = r by Cramer's rule
-        const double d0 = (r[0] * c00 + J[0][1] * (J[1][2] * r[2] - r[1] * J[2][2]) +
-                           J[0][2] * (r[1] * J[2][1] - J[1][1] * r[2])) / det;
-        const double d1 = (J[0][0] * (r[1] * J[2][2] - J[1][2] * r[2]) + r[0] * c01 +
-                           J[0][2] * (J[1][0] * r[2] - r[1] * J[2][0])) / det;
-        const double d2 = (J[0][0] * (J[1][1] * r[2] - r[1] * J[2][1]) +
-                           J[0][1] * (r[1] * J[2][0] - J[1][0] * r[2]) + r[0] * c02) / det;
-        xi[0] -= d0;
-        xi[1] -= d1;
-        xi[2] -= d2;
-        if (!(fabs(xi[0]) < 10.0 && fabs(xi[1]) < 10.0 && fabs(xi[2]) < 10.0)) return false;
-        last = fmax(fabs(d0), fmax(fabs(d1), fabs(d2)));
+    }
+    const R c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const R c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const R c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const R det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    if (!(fabs(det) > R(0))) return false;
+    const R inv = R(1) / det;
+    d[0] = (r[0] * c00 + J[0][1] * (J[1][2] * r[2] - r[1] * J[2][2]) +
+            J[0][2] * (r[1] * J[2][1] - J[1][1] * r[2])) * inv;
+    d[1] = (J[0][0] * (r[1] * J[2][2] - J[1][2] * r[2]) + r[0] * c01 +
+            J[0][2] * (J[1][0] * r[2] - r[1] * J[2][0])) * inv;
+    d[2] = (J[0][0] * (J[1][1] * r[2] - r[1] * J[2][1]) +
+            J[0][1] * (r[1] * J[2][0] - J[1][0] * r[2]) + r[0] * c02) * inv;
+    return true;
+}
+
+// FP32 root of the extended map: 1 settled, 0 not settled (xi = last iterate,
+// a direction only), -1 singular or blown up.
+__device__ int newton_f32(const HexNodes &H, const double X[3], float (&xi)[3])
+{
+    float xa[8][3], Y[3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) xa[a][i] = (float)H.d[a][i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Y[i] = (float)(X[i] - H.o[i]);
+    xi[0] = xi[1] = xi[2] = 0.0f;
+    for (int it = 0; it < 16; ++it) {
+        float d[3];
+        if (!newton_update<float>(xa, Y, xi, d)) return -1;
+        xi[0] -= d[0];
+        xi[1] -= d[1];
+        xi[2] -= d[2];
+        if (!(fabsf(xi[0]) < 64.0f && fabsf(xi[1]) < 64.0f && fabsf(xi[2]) < 64.0f)) return -1;
+        if (fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))) < 1e-5f) return 1;
+    }
+    return 0;
+}
+
+// FP64 root from the start xi: true when settled (last update < 1e-12).
+__device__ bool newton_f64(const HexNodes &H, const double X[3], double (&xi)[3])
+{
+    const double Y[3] = {X[0] - H.o[0], X[1] - H.o[1], X[2] - H.o[2]};
+    double last = 1.0;
+    for (int it = 0; it < 12; ++it) {
+        double d[3];
+        if (!newton_update<double>(H.d, Y, xi, d)) return false;
+        xi[0] -= d[0];
+        xi[1] -= d[1];
+        xi[2] -= d[2];
+        if (!(fabs(xi[0]) < 64.0 && fabs(xi[1]) < 64.0 && fabs(xi[2]) < 64.0)) return false;
+        last = fmax(fabs(d[0]), fmax(fabs(d[1]), fabs(d[2])));
         if (last < 1e-15) break;
     }
-    return last < 1e-12;  // a settled root only
+    return last < 1e-12;
 }
 
 __global__ void locate_mapped_kernel(int64_t m, GridArgs g, const double4 *__restrict__ C,
@@ -148,7 +202,7 @@ __global__ void locate_mapped_kernel(int64_t m, GridArgs g, const double4 *__res
         int e3[3];
         bool finite = true;
         for (int k = 0; k < 3; ++k) {
-            finite = finite && isfinite(t[k]);
+            finite = finite && isfinite(t[k]) && isfinite(X[k]);
             const double c = finite ? floor(t[k]) : 0.0;
             e3[k] = c < 0.0 ? 0 : (c > (double)(N3[k] - 1) ? N3[k] - 1 : (int)c);
         }
@@ -156,23 +210,53 @@ __global__ void locate_mapped_kernel(int64_t m, GridArgs g, const double4 *__res
         double q[3] = {0.0, 0.0, 0.0};
         const int max_steps = g.Nx + g.Ny + g.Nz + 8;
         for (int step = 0; step < max_steps && finite; ++step) {
-            const bool ok = newton_in_element(g, C, e3[0], e3[1], e3[2], X, q);
-            if (ok && fabs(q[0]) <= 1.0 + 1e-10 && fabs(q[1]) <= 1.0 + 1e-10 &&
-                fabs(q[2]) <= 1.0 + 1e-10) {
-                found = 1;
-                break;
+            HexNodes H;
+            load_hex(g, C, e3[0], e3[1], e3[2], H);
+            float q32[3];
+            const int st = newton_f32(H, X, q32);
+            // direction of the next move, from the FP64 root where there is one
+            double dir[3] = {q32[0], q32[1], q32[2]};
+            bool jump = st == 1 && step < 6;
+            if (st == 1 && fabsf(q32[0]) <= 1.001f && fabsf(q32[1]) <= 1.001f &&
+                fabsf(q32[2]) <= 1.001f) {
+                q[0] = q32[0];
+                q[1] = q32[1];
+                q[2] = q32[2];
+                const bool ok = newton_f64(H, X, q);
+                if (ok && fabs(q[0]) <= 1.0 + 1e-10 && fabs(q[1]) <= 1.0 + 1e-10 &&
+                    fabs(q[2]) <= 1.0 + 1e-10) {
+                    found = 1;
+                    break;
+                }
+                if (!ok) break;
+                dir[0] = q[0];
+                dir[1] = q[1];
+                dir[2] = q[2];
+                jump = false;
             }
-            // the face of the largest violation (Newton failure: toward the
-            // point from the element's centre is not known, stop)
-            if (!ok) break;
+            if (st < 0) break;
+            if (jump) {
+                bool moved = false;
+                for (int k = 0; k < 3; ++k) {
+                    double s = floor(0.5 * (dir[k] + 1.0));
+                    s = s > 8.0 ? 8.0 : (s < -8.0 ? -8.0 : s);
+                    int nk = e3[k] + (int)s;
+                    nk = nk < 0 ? 0 : (nk > N3[k] - 1 ? N3[k] - 1 : nk);
+                    moved = moved || nk != e3[k];
+                    e3[k] = nk;
+                }
+                if (moved) continue;
+                // clamped at the grid's edge: fall through to a plain move
+            }
             int k = 0;
-            double worst = fabs(q[0]);
+            double worst = fabs(dir[0]);
             for (int d = 1; d < 3; ++d)
-                if (fabs(q[d]) > worst) {
-                    worst = fabs(q[d]);
+                if (fabs(dir[d]) > worst) {
+                    worst = fabs(dir[d]);
                     k = d;
                 }
-            const int next = e3[k] + (q[k] > 0.0 ? 1 : -1);
+            if (!(worst > 1.0)) break;
+            const int next = e3[k] + (dir[k] > 0.0 ? 1 : -1);
             if (next < 0 || next >= N3[k]) break;
             e3[k] = next;
         }

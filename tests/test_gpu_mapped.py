@@ -218,6 +218,27 @@ def test_mapped_locate_interp_spread(fsi, oracle, prec):
     assert rel(H(F)[:, :3], core.spread(grid, eo, xw, lam, w=w)[:, :3]) < TOL[prec]
 
 
+@pytest.mark.parametrize("delta", [0.03, 0.08])
+def test_mapped_locate_walks_across_elements(fsi, oracle, delta):
+    """A smooth map that moves nodes by up to 1 and 2.6 element widths: the
+    nominal start element is far off and the walk has to travel; every point
+    mapped from (element, xi) is found there with that xi."""
+    import torch
+    core = oracle.core
+    N = 32
+    X = bubble(core.Grid(N).node_coords(), delta)
+    grid = core.Grid(N, coords=X)
+    mesh, _ = mapped_mesh(fsi, N, X)
+    P, e_true, xi_true = points_in_elements(core, grid, X, 4000, seed=15, lo=-0.999, hi=0.999)
+    m = P.shape[0]
+    elem = torch.empty(m, dtype=torch.int32, device="cuda")
+    xi = torch.empty((m, 3), dtype=torch.float64, device="cuda")
+    nout = fsi.fsi_locate(mesh, T(P), elem, xi)
+    assert nout == 0
+    assert np.array_equal(elem.cpu().numpy(), e_true)
+    assert np.abs(H(xi) - xi_true).max() < 1e-12
+
+
 def test_mapped_locate_faces_and_nodes_are_valid(fsi, oracle):
     """Points on element faces and at nodes belong to several elements: the
     walk's answer must be one of them (|xi| <= 1 + 1e-10, maps back to X)."""
