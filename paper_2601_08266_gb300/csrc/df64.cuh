@@ -94,6 +94,34 @@ __device__ __forceinline__ df64 operator*(df64 a, df64 b)
     return df_fast_two_sum(p, e);
 }
 
+// a b + c: the exact product error and the low parts join the sum before
+// one renormalisation (the product is not renormalised on its own).  Error
+// a few units of 2^-47 of max(|a b|, |c|), like a product followed by a sum.
+__device__ __forceinline__ df64 df_fma(df64 a, df64 b, df64 c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const df64 s = df_two_sum(p, c.hi);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+}
+
+// a b + c d with one renormalisation
+__device__ __forceinline__ df64 df_dot2(df64 a, df64 b, df64 c, df64 d)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float q = __fmul_rn(c.hi, d.hi);
+    float f = __fmaf_rn(c.hi, d.hi, -q);
+    f = __fmaf_rn(c.hi, d.lo, f);
+    f = __fmaf_rn(c.lo, d.hi, f);
+    const df64 s = df_two_sum(p, q);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, f)));
+}
+
 __device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a = a + b; }
 __device__ __forceinline__ df64 &operator-=(df64 &a, df64 b) { return a = a - b; }
 

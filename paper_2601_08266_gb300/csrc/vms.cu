@@ -20,6 +20,7 @@
 //     blocks that contain it in a fixed brick order.  The result is
 //     deterministic (bitwise reproducible) and atomic-free.
 #include <cmath>
+#include <type_traits>
 
 #include "fsi_internal.cuh"
 
@@ -32,6 +33,16 @@ using namespace vmsd;
 
 template <typename T, bool JAC, bool MAPPED>
 __global__ void __launch_bounds__(256) vms_brick_kernel(const VmsArgs<T> P)
+{
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    brick_body<T, JAC, MAPPED>(P, blockIdx.x, reinterpret_cast<vec4<T> *>(smem_raw));
+}
+
+// The same, held to 128 registers (two 256-thread CTAs per SM): used for the
+// mapped double-float kernels, whose Jacobian otherwise takes 185 registers
+// and runs 1.5x slower at one CTA per SM.
+template <typename T, bool JAC, bool MAPPED>
+__global__ void __launch_bounds__(256, 2) vms_brick_kernel_capped(const VmsArgs<T> P)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     brick_body<T, JAC, MAPPED>(P, blockIdx.x, reinterpret_cast<vec4<T> *>(smem_raw));
@@ -54,14 +65,19 @@ fsi_status launch_geo(fsi_mesh *m, const void *U, const void *A, const void *f, 
     VmsArgs<T> P = make_args<T>(m, b, U, A, f, x, out);
     const int nbricks = P.nbx * P.nby * P.nbz;
     const size_t smem = (size_t)b.bx * b.by * b.bz * 8 * sizeof(vec4<typename StorageOf<T>::type>);
+    void (*kernel)(const VmsArgs<T>);
+    if constexpr (MAPPED && std::is_same<T, df64>::value)
+        kernel = vms_brick_kernel_capped<T, JAC, MAPPED>;
+    else
+        kernel = vms_brick_kernel<T, JAC, MAPPED>;
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
-        FSI_CUDA(cudaFuncSetAttribute(vms_brick_kernel<T, JAC, MAPPED>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
+        FSI_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024),
                  "cudaFuncSetAttribute");
         attr_set = true;
     }
-    vms_brick_kernel<T, JAC, MAPPED><<<nbricks, b.threads, smem, m->stream>>>(P);
+    kernel<<<nbricks, b.threads, smem, m->stream>>>(P);
     FSI_TRY(check_launch("vms brick kernel"));
     const int threads = 256;
     int64_t nb = (m->n_nodes + threads - 1) / threads;

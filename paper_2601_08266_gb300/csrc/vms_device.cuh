@@ -3,6 +3,8 @@
 // (batch.cu).  See vms.cu for the design.
 #pragma once
 
+#include <type_traits>
+
 #include "df64.cuh"
 #include "fsi_internal.cuh"
 
@@ -54,6 +56,27 @@ template <typename T> struct VmsArgs {
     vec4<S> *out;     // [n]
 };
 
+// a b + c and a b + c d: plain expressions (contracted to FMAs) for float and
+// double, one renormalisation for double-float.
+template <typename T> __device__ __forceinline__ T fma_t(T a, T b, T c) { return a * b + c; }
+template <> __device__ __forceinline__ df64 fma_t<df64>(df64 a, df64 b, df64 c)
+{
+    return df_fma(a, b, c);
+}
+template <typename T> __device__ __forceinline__ T dot2_t(T a, T b, T c, T d)
+{
+    return a * b + c * d;
+}
+template <> __device__ __forceinline__ df64 dot2_t<df64>(df64 a, df64 b, df64 c, df64 d)
+{
+    return df_dot2(a, b, c, d);
+}
+// a . b over three components
+template <typename T> __device__ __forceinline__ T dot3_t(T a0, T b0, T a1, T b1, T a2, T b2)
+{
+    return fma_t(a2, b2, dot2_t(a0, b0, a1, b1));
+}
+
 template <typename T> __device__ __forceinline__ T shx(T v, int m)
 {
     return __shfl_xor_sync(0xffffffffu, v, m);
@@ -79,27 +102,27 @@ template <typename T> __device__ __forceinline__ VG<T> eval_vg(T u, T sx, T sy, 
 {
     const T b1 = cB1<T>(), b2 = cB2<T>();
     T uo = shx(u, 1);
-    T tB = b1 * u + b2 * uo;
+    T tB = dot2_t(b1, u, b2, uo);
     T tD = u - uo;
     T tBo = shx(tB, 2), tDo = shx(tD, 2);
-    T tBB = b1 * tB + b2 * tBo;
+    T tBB = dot2_t(b1, tB, b2, tBo);
     T tBD = tB - tBo;
-    T tDB = b1 * tD + b2 * tDo;
+    T tDB = dot2_t(b1, tD, b2, tDo);
     T tBBo = shx(tBB, 4), tBDo = shx(tBD, 4), tDBo = shx(tDB, 4);
     VG<T> r;
-    r.v = b1 * tBB + b2 * tBBo;
+    r.v = dot2_t(b1, tBB, b2, tBBo);
     r.gz = sz * (tBB - tBBo);
-    r.gy = sy * (b1 * tBD + b2 * tBDo);
-    r.gx = sx * (b1 * tDB + b2 * tDBo);
+    r.gy = sy * dot2_t(b1, tBD, b2, tBDo);
+    r.gx = sx * dot2_t(b1, tDB, b2, tDBo);
     return r;
 }
 
 template <typename T> __device__ __forceinline__ T eval_v(T u)
 {
     const T b1 = cB1<T>(), b2 = cB2<T>();
-    T t = b1 * u + b2 * shx(u, 1);
-    t = b1 * t + b2 * shx(t, 2);
-    return b1 * t + b2 * shx(t, 4);
+    T t = dot2_t(b1, u, b2, shx(u, 1));
+    t = dot2_t(b1, t, b2, shx(t, 2));
+    return dot2_t(b1, t, b2, shx(t, 4));
 }
 
 // Transposed evaluation: with X the value coefficient and (Yx, Yy, Yz) the
@@ -110,14 +133,14 @@ __device__ __forceinline__ T project(T X, T Yx, T Yy, T Yz, T sx, T sy, T sz)
 {
     const T b1 = cB1<T>(), b2 = cB2<T>();
     T Xo = shx(X, 4), Yzo = shx(Yz, 4), Yxo = shx(Yx, 4), Yyo = shx(Yy, 4);
-    T P1 = b1 * X + b2 * Xo + sz * (Yz + Yzo);
-    T P2 = b1 * Yx + b2 * Yxo;
-    T P3 = b1 * Yy + b2 * Yyo;
+    T P1 = fma_t(sz, Yz + Yzo, dot2_t(b1, X, b2, Xo));
+    T P2 = dot2_t(b1, Yx, b2, Yxo);
+    T P3 = dot2_t(b1, Yy, b2, Yyo);
     T P1o = shx(P1, 2), P2o = shx(P2, 2), P3o = shx(P3, 2);
-    T Q1 = b1 * P1 + b2 * P1o + sy * (P3 + P3o);
-    T Q2 = b1 * P2 + b2 * P2o;
+    T Q1 = fma_t(sy, P3 + P3o, dot2_t(b1, P1, b2, P1o));
+    T Q2 = dot2_t(b1, P2, b2, P2o);
     T Q1o = shx(Q1, 1), Q2o = shx(Q2, 1);
-    return b1 * Q1 + b2 * Q1o + sx * (Q2 + Q2o);
+    return fma_t(sx, Q2 + Q2o, dot2_t(b1, Q1, b2, Q1o));
 }
 
 template <typename T> __device__ __forceinline__ T inv_t(T v) { return T(1) / v; }
@@ -138,11 +161,11 @@ template <typename T>
 __device__ __forceinline__ void base_state(const VmsArgs<T> &P, GP<T> &q)
 {
     for (int i = 0; i < 3; ++i) {
-        q.conv[i] = q.v[0] * q.gv[i][0] + q.v[1] * q.gv[i][1] + q.v[2] * q.gv[i][2];
-        q.rM[i] = P.rho * (q.a[i] + q.conv[i] - q.f[i]) + q.gp[i];
+        q.conv[i] = dot3_t(q.v[0], q.gv[i][0], q.v[1], q.gv[i][1], q.v[2], q.gv[i][2]);
+        q.rM[i] = fma_t(P.rho, q.a[i] + q.conv[i] - q.f[i], q.gp[i]);
     }
     q.rC = q.gv[0][0] + q.gv[1][1] + q.gv[2][2];
-    q.vGv = P.G0 * q.v[0] * q.v[0] + P.G1 * q.v[1] * q.v[1] + P.G2 * q.v[2] * q.v[2];
+    q.vGv = dot3_t(P.G0 * q.v[0], q.v[0], P.G1 * q.v[1], q.v[1], P.G2 * q.v[2], q.v[2]);
     const T S = q.s * (P.q0 + q.vGv);
     q.tauM = rsqrt_t(S);
     // tau_C = 1/(tau_M tr G) and 1/tau_M = S tau_M
@@ -163,8 +186,8 @@ template <typename T>
 __device__ __forceinline__ void base_state_g(const VmsArgs<T> &P, const Geo<T> &geo, GP<T> &q)
 {
     for (int i = 0; i < 3; ++i) {
-        q.conv[i] = q.v[0] * q.gv[i][0] + q.v[1] * q.gv[i][1] + q.v[2] * q.gv[i][2];
-        q.rM[i] = P.rho * (q.a[i] + q.conv[i] - q.f[i]) + q.gp[i];
+        q.conv[i] = dot3_t(q.v[0], q.gv[i][0], q.v[1], q.gv[i][1], q.v[2], q.gv[i][2]);
+        q.rM[i] = fma_t(P.rho, q.a[i] + q.conv[i] - q.f[i], q.gp[i]);
     }
     q.rC = q.gv[0][0] + q.gv[1][1] + q.gv[2][2];
     T vGv = T(0);
@@ -208,6 +231,10 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
     const int NX1 = P.Nx + 1, NXY1 = (P.Nx + 1) * (P.Ny + 1);
 
     for (int base = 0; base < nel; base += groups) {
+        // the double-float body is long: a barrier per pass keeps the CTA's
+        // warps on the same stretch of it (instruction-cache locality; 3-5 %
+        // faster on GB300, a loss for the shorter float/double bodies)
+        if constexpr (std::is_same<T, df64>::value) __syncthreads();
         const int slot = base + (threadIdx.x >> 3);
         const int lx = slot % P.bx, ly = (slot / P.bx) % P.by, lz = slot / (P.bx * P.by);
         const int ex = ex0 + lx, ey = ey0 + ly, ez = ez0 + lz;
@@ -287,12 +314,12 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
         T X[4], Y[4][3];
         if (!JAC) {
             for (int i = 0; i < 3; ++i) {
-                X[i] = P.rho * (q.a[i] + q.conv[i] - q.f[i]) +
-                       P.rho * (q.up[0] * q.gv[i][0] + q.up[1] * q.gv[i][1] +
-                                q.up[2] * q.gv[i][2]);
+                X[i] = P.rho * (q.a[i] + q.conv[i] - q.f[i] +
+                                dot3_t(q.up[0], q.gv[i][0], q.up[1], q.gv[i][1], q.up[2],
+                                       q.gv[i][2]));
                 for (int j = 0; j < 3; ++j)
-                    Y[i][j] = P.mu * (q.gv[i][j] + q.gv[j][i]) -
-                              P.rho * (q.v[j] + q.up[j]) * q.up[i];
+                    Y[i][j] = dot2_t(P.mu, q.gv[i][j] + q.gv[j][i], -P.rho * (q.v[j] + q.up[j]),
+                                     q.up[i]);
                 Y[i][i] -= q.p + q.pp;
             }
             X[3] = q.rC;
@@ -320,9 +347,9 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
             }
             T dconv[3], drM[3], dup[3];
             for (int i = 0; i < 3; ++i) {
-                dconv[i] = dv[0] * q.gv[i][0] + dv[1] * q.gv[i][1] + dv[2] * q.gv[i][2] +
-                           q.v[0] * dgv[i][0] + q.v[1] * dgv[i][1] + q.v[2] * dgv[i][2];
-                drM[i] = P.rho * (da[i] + dconv[i]) + dgp[i];
+                dconv[i] = dot3_t(dv[0], q.gv[i][0], dv[1], q.gv[i][1], dv[2], q.gv[i][2]) +
+                           dot3_t(q.v[0], dgv[i][0], q.v[1], dgv[i][1], q.v[2], dgv[i][2]);
+                drM[i] = fma_t(P.rho, da[i] + dconv[i], dgp[i]);
             }
             const T drC = dgv[0][0] + dgv[1][1] + dgv[2][2];
             // d tau_M = -1/2 tau_M^3 s dQ with dQ = 2 v.G dv
@@ -332,22 +359,23 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
                 for (int i = 0; i < 3; ++i)
                     vGdv += q.v[i] * (geo.G[i][0] * dv[0] + geo.G[i][1] * dv[1] + geo.G[i][2] * dv[2]);
             } else {
-                vGdv = P.G0 * q.v[0] * dv[0] + P.G1 * q.v[1] * dv[1] + P.G2 * q.v[2] * dv[2];
+                vGdv = dot3_t(P.G0 * q.v[0], dv[0], P.G1 * q.v[1], dv[1], P.G2 * q.v[2], dv[2]);
             }
             const T dtauM = -q.tauM * q.tauM * q.tauM * q.s * vGdv;
             // d tau_C = -tau_C d tau_M / tau_M, 1/tau_M = s (q0 + vGv) tau_M
             T q0 = P.q0;
             if constexpr (MAPPED) q0 = geo.q0;
             const T dtauC = -q.tauC * dtauM * (q.s * (q0 + q.vGv) * q.tauM);
-            for (int i = 0; i < 3; ++i) dup[i] = -(dtauM * q.rM[i] + q.tauM * drM[i]) * P.inv_rho;
-            const T dpp = -P.rho * (dtauC * q.rC + q.tauC * drC);
+            for (int i = 0; i < 3; ++i) dup[i] = -dot2_t(dtauM, q.rM[i], q.tauM, drM[i]) * P.inv_rho;
+            const T dpp = -P.rho * dot2_t(dtauC, q.rC, q.tauC, drC);
             for (int i = 0; i < 3; ++i) {
-                X[i] = P.rho * (da[i] + dconv[i]) +
-                       P.rho * (dup[0] * q.gv[i][0] + dup[1] * q.gv[i][1] + dup[2] * q.gv[i][2] +
-                                q.up[0] * dgv[i][0] + q.up[1] * dgv[i][1] + q.up[2] * dgv[i][2]);
+                X[i] = P.rho * (da[i] + dconv[i] +
+                                dot3_t(dup[0], q.gv[i][0], dup[1], q.gv[i][1], dup[2], q.gv[i][2]) +
+                                dot3_t(q.up[0], dgv[i][0], q.up[1], dgv[i][1], q.up[2], dgv[i][2]));
                 for (int j = 0; j < 3; ++j)
-                    Y[i][j] = P.mu * (dgv[i][j] + dgv[j][i]) -
-                              P.rho * ((dv[j] + dup[j]) * q.up[i] + (q.v[j] + q.up[j]) * dup[i]);
+                    Y[i][j] = fma_t(P.mu, dgv[i][j] + dgv[j][i],
+                                    -P.rho * dot2_t(dv[j] + dup[j], q.up[i], q.v[j] + q.up[j],
+                                                    dup[i]));
                 Y[i][i] -= dp + dpp;
             }
             X[3] = drC;
