@@ -88,7 +88,7 @@ __global__ void batch_spread_cells_kernel(const DlmDesc<T> *desc, const int64_t 
     for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
         const int inst = find_instance(prefix, count, item);
         const DlmDesc<T> &D = desc[inst];
-        const int64_t c0 = ((item - prefix[inst]) * 8 + warp) * 32;
+        const int64_t c0 = ((item - prefix[inst]) * 8 + warp) * dlmd::kSpreadSeg;
         if (c0 < D.E) dlmd::spread_cells_segment<T>(D.E, c0, D.xi, D.start, D.perm, D.lam, D.w, D.S);
     }
 }
@@ -201,7 +201,8 @@ template <typename T> fsi_status build_batch(fsi_batch *b)
         pre[1 * (C + 1) + i + 1] = pre[1 * (C + 1) + i] + (m->n_nodes + kChunk - 1) / kChunk;
         pre[2 * (C + 1) + i + 1] = pre[2 * (C + 1) + i] + (it.m + kChunk - 1) / kChunk;
         pre[3 * (C + 1) + i + 1] =
-            pre[3 * (C + 1) + i] + ((m->n_elems + 31) / 32 + 7) / 8;  // 8 segments per item
+            pre[3 * (C + 1) + i] +
+            ((m->n_elems + dlmd::kSpreadSeg - 1) / dlmd::kSpreadSeg + 7) / 8;  // 8 segments per item
     }
     for (int k = 0; k < 4; ++k) b->totals[k] = pre[k * (C + 1) + C];
     cudaStream_t s = b->stream;

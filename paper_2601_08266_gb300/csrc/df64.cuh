@@ -122,6 +122,14 @@ __device__ __forceinline__ df64 df_dot2(df64 a, df64 b, df64 c, df64 d)
     return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, f)));
 }
 
+// a b + c in any compute type: the plain expression (contracted to an FMA)
+// for float and double, df_fma for double-float
+template <typename T> __device__ __forceinline__ T madd(T a, T b, T c) { return a * b + c; }
+template <> __device__ __forceinline__ df64 madd<df64>(df64 a, df64 b, df64 c)
+{
+    return df_fma(a, b, c);
+}
+
 __device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a = a + b; }
 __device__ __forceinline__ df64 &operator-=(df64 &a, df64 b) { return a = a - b; }
 

@@ -2,14 +2,17 @@
 // point location with a cell -> points table, interpolation u = C^T V
 // (Eq. nodal_solid_velo) and spreading F = C lambda (Eq. fsi_constraint_matrix).
 //
-// Location is closed-form on the uniform grid.  The cell table is a stable
-// counting sort: histogram (integer atomics, order-free), a three-kernel
-// exclusive scan, a scatter through per-cell cursors, and a per-cell sort of
-// each cell's slice by point index, which restores the stable order exactly.
-// Spreading is atomic-free in two passes: per-cell corner sums (one warp per
-// 32-cell segment, butterfly reductions), then a node gather over the (up to)
-// eight cells of each node in a fixed order.  No races, no atomics, and the
-// result does not depend on scheduling.
+// Location is closed-form on the uniform grid (a bounded element walk with
+// Newton inversion on a mapped grid).  The cell table is a stable counting
+// sort: histogram (integer atomics, order-free), a three-kernel exclusive
+// scan, a scatter through per-cell cursors, and a per-cell sort of each
+// cell's slice by point index, which restores the stable order exactly (a
+// bitonic network in one lane's registers up to 32 points, a warp rank sort
+// up to 128, a shell sort beyond).  Spreading is atomic-free in two passes:
+// per-cell corner sums (four lanes per cell of up to 128 points, the warp for
+// fuller cells, fixed transpose-reduce trees), then a node gather over the
+// (up to) eight cells of each node in a fixed order.  No races, no atomics,
+// and the result does not depend on scheduling.
 #include <cmath>
 #include <mutex>
 
@@ -387,6 +390,26 @@ __device__ void shell_sort(int32_t *s, int len)
     }
 }
 
+// Ascending bitonic sorting network over 32 values in registers (all indices
+// compile-time constants, so nothing goes to local memory).
+__device__ __forceinline__ void bitonic32(int (&v)[32])
+{
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const int a = v[i], b = v[l];
+                    const bool up = (i & k) == 0;
+                    v[i] = up ? min(a, b) : max(a, b);
+                    v[l] = up ? max(a, b) : min(a, b);
+                }
+            }
+}
+
 __global__ void cell_sort_kernel(int64_t E, int64_t m, const int32_t *__restrict__ start,
                                  int32_t *__restrict__ perm)
 {
@@ -400,22 +423,27 @@ __global__ void cell_sort_kernel(int64_t E, int64_t m, const int32_t *__restrict
             lo = start[c];
             len = (c < E ? start[c + 1] : (int)m) - lo;
         }
-        unsigned todo = __ballot_sync(0xffffffffu, len >= 2);
+        // up to 32 points: each lane sorts its own cell's slice in registers
+        if (len >= 2 && len <= 32) {
+            int32_t *sl = perm + lo;
+            int v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = i < len ? sl[i] : INT32_MAX;
+            bitonic32(v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if (i < len) sl[i] = v[i];
+        }
+        // fuller cells: the warp together
+        unsigned todo = __ballot_sync(0xffffffffu, len > 32);
         while (todo) {
             const int l = __ffs(todo) - 1;
             todo &= todo - 1;
             const int base = __shfl_sync(0xffffffffu, lo, l);
             const int n = __shfl_sync(0xffffffffu, len, l);
             int32_t *sl = perm + base;
-            if (n <= 32) {
-                const int v = lane < n ? sl[lane] : INT32_MAX;
-                int rank = 0;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) rank += __shfl_sync(0xffffffffu, v, j) < v;
-                __syncwarp();
-                if (lane < n) sl[rank] = v;
-                __syncwarp();
-            } else if (n <= 128) {
+            __syncwarp();
+            if (n <= 128) {
                 // four values per lane, all in registers
                 int own[4], rk[4];
 #pragma unroll
@@ -455,8 +483,8 @@ __global__ void interp_kernel(int64_t m, GridArgs g, const int32_t *__restrict__
         interp_point<T>(g, b, elem, xi, U, u);
 }
 
-// Spreading, pass 1: one warp per segment of 32 consecutive cells (see
-// spread_cells_segment).
+// Spreading, pass 1: one warp per segment of kSpreadSeg consecutive cells
+// (see spread_cells_segment).
 // T is the compute type (double, float or double-float); xi, lam, w and F are
 // in its storage type, the corner sums S in T.
 template <typename T>
@@ -469,7 +497,7 @@ __global__ void spread_cells_kernel(int64_t E, const typename StorageOf<T>::type
 {
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c0 = warp * 32; c0 < E; c0 += nwarps * 32)
+    for (int64_t c0 = warp * kSpreadSeg; c0 < E; c0 += nwarps * kSpreadSeg)
         spread_cells_segment<T>(E, c0, xi, start, perm, lam, w, S);
 }
 
@@ -674,7 +702,7 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
     const size_t esz = prec == FSI_F32 ? sizeof(float) : sizeof(double);
     FSI_TRY(ensure_spread_scratch(mesh, (size_t)mesh->n_elems * 24 * esz));
     const int64_t E = mesh->n_elems;
-    const int cgrid = blocks_for((E + 31) / 32 * 32, 256, 152 * 64);
+    const int cgrid = blocks_for((E + kSpreadSeg - 1) / kSpreadSeg * 32, 256, 152 * 64);
     const int ngrid = blocks_for(mesh->n_nodes, 256, 152 * 32);
     if (prec == FSI_F64) {
         spread_cells_kernel<double><<<cgrid, 256, 0, mesh->stream>>>(
