@@ -50,13 +50,14 @@ LAUNCHES_PER_STEP = 14
 # FP64 flops per element of one VMS Jacobian apply / residual (DFMA = 2,
 # DMUL = DADD = 1), from ncu instruction counts of the native FP64 kernels.
 FLOPS_PER_ELEM = {"jacobian": 4808.0, "residual": 3008.0}
-# FP32 pipe instructions (FADD + FMUL + FFMA) per element of the double-float
-# kernels, from ncu's executed-instruction-mix counters (128^3 capture).
-FP32_INSTR_PER_ELEM_DF64 = {"jacobian": 40160.0, "residual": 25012.0}
+# FP32 pipe instructions (FADD + FMUL + FFMA; no paired FADD2/FMUL2/FFMA2 are
+# issued) per element of the double-float kernels, brick + gather, from ncu's
+# sm__sass_thread_inst_executed_op_*_pred_on counters (64^3 capture).
+FP32_INSTR_PER_ELEM_DF64 = {"jacobian": 33827.0 + 69.6, "residual": 20979.0 + 69.6}
 # dram__bytes_read.sum + dram__bytes_write.sum of one double-float Jacobian apply
-# at 64^3 (brick kernel 26,477,056 B + gather kernel 13,289,216 B; the writes
-# stay in L2 within the launch)
-TRAFFIC_JAC_DF64_64 = 39_766_272
+# at 64^3 (brick kernel 26,461,440 + 1,280 B + gather kernel 13,288,448 B; the
+# writes stay in L2 within the launch)
+TRAFFIC_JAC_DF64_64 = 39_751_168
 
 
 def dist_env():

@@ -7,7 +7,7 @@
 // sort: histogram (integer atomics, order-free), a three-kernel exclusive
 // scan, a scatter through per-cell cursors, and a per-cell sort of each
 // cell's slice by point index, which restores the stable order exactly (a
-// bitonic network in one lane's registers up to 32 points, a warp rank sort
+// bitonic network in one lane's registers up to 64 points, a warp rank sort
 // up to 128, a shell sort beyond).  Spreading is atomic-free in two passes:
 // per-cell corner sums (four lanes per cell of up to 128 points, the warp for
 // fuller cells, fixed transpose-reduce trees), then a node gather over the
@@ -390,16 +390,16 @@ __device__ void shell_sort(int32_t *s, int len)
     }
 }
 
-// Ascending bitonic sorting network over 32 values in registers (all indices
+// Ascending bitonic sorting network over N values in registers (all indices
 // compile-time constants, so nothing goes to local memory).
-__device__ __forceinline__ void bitonic32(int (&v)[32])
+template <int N> __device__ __forceinline__ void bitonic(int (&v)[N])
 {
 #pragma unroll
-    for (int k = 2; k <= 32; k <<= 1)
+    for (int k = 2; k <= N; k <<= 1)
 #pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1)
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
+            for (int i = 0; i < N; ++i) {
                 const int l = i ^ j;
                 if (l > i) {
                     const int a = v[i], b = v[l];
@@ -408,6 +408,18 @@ __device__ __forceinline__ void bitonic32(int (&v)[32])
                     v[l] = up ? max(a, b) : min(a, b);
                 }
             }
+}
+
+// one lane sorts a slice of len <= N values in place
+template <int N> __device__ __forceinline__ void sort_slice(int32_t *sl, int len)
+{
+    int v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = i < len ? sl[i] : INT32_MAX;
+    bitonic<N>(v);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        if (i < len) sl[i] = v[i];
 }
 
 __global__ void cell_sort_kernel(int64_t E, int64_t m, const int32_t *__restrict__ start,
@@ -423,19 +435,13 @@ __global__ void cell_sort_kernel(int64_t E, int64_t m, const int32_t *__restrict
             lo = start[c];
             len = (c < E ? start[c + 1] : (int)m) - lo;
         }
-        // up to 32 points: each lane sorts its own cell's slice in registers
-        if (len >= 2 && len <= 32) {
-            int32_t *sl = perm + lo;
-            int v[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = i < len ? sl[i] : INT32_MAX;
-            bitonic32(v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i)
-                if (i < len) sl[i] = v[i];
-        }
+        // up to 64 points: each lane sorts its own cell's slice in registers
+        if (len >= 2 && len <= 32)
+            sort_slice<32>(perm + lo, len);
+        else if (len > 32 && len <= 64)
+            sort_slice<64>(perm + lo, len);
         // fuller cells: the warp together
-        unsigned todo = __ballot_sync(0xffffffffu, len > 32);
+        unsigned todo = __ballot_sync(0xffffffffu, len > 64);
         while (todo) {
             const int l = __ffs(todo) - 1;
             todo &= todo - 1;

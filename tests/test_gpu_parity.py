@@ -243,7 +243,12 @@ def test_dlm_empty_and_all_outside(fsi, oracle):
 
 
 def test_dlm_medium_density_cells(fsi, oracle):
-    """33..128 points per cell (the register rank-sort path) and > 128."""
+    """33..64 points per cell (one lane's bitonic network), 65..128 (the warp's
+    register rank sort) and > 128 (four-lane spreading groups give way to the
+    whole warp above 128 points)."""
+    X = np.random.default_rng(4).uniform(size=(400, 3))
+    dlm_check(fsi, oracle, 2, X, "f64", True, False)
+    dlm_check(fsi, oracle, 2, X, "df64", False, True)
     X = np.random.default_rng(5).uniform(size=(700, 3))
     dlm_check(fsi, oracle, 2, X, "f64", True, False)
     dlm_check(fsi, oracle, 2, X, "df64", True, True)
