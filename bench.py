@@ -53,11 +53,11 @@ FLOPS_PER_ELEM = {"jacobian": 4808.0, "residual": 3008.0}
 # FP32 pipe instructions (FADD + FMUL + FFMA; no paired FADD2/FMUL2/FFMA2 are
 # issued) per element of the double-float kernels, brick + gather, from ncu's
 # sm__sass_thread_inst_executed_op_*_pred_on counters (64^3 capture).
-FP32_INSTR_PER_ELEM_DF64 = {"jacobian": 33827.0 + 69.6, "residual": 20979.0 + 69.6}
+FP32_INSTR_PER_ELEM_DF64 = {"jacobian": 34339.0 + 69.6, "residual": 20979.0 + 69.6}
 # dram__bytes_read.sum + dram__bytes_write.sum of one double-float Jacobian apply
-# at 64^3 (brick kernel 26,461,440 + 1,280 B + gather kernel 13,288,448 B; the
+# at 64^3 (brick kernel 26,429,952 + 3,072 B + gather kernel 13,288,448 B; the
 # writes stay in L2 within the launch)
-TRAFFIC_JAC_DF64_64 = 39_751_168
+TRAFFIC_JAC_DF64_64 = 39_721_472
 
 
 def dist_env():

@@ -98,7 +98,7 @@ template <typename T> struct VG {
 // Value and physical gradient at this lane's Gauss point of the Q1 field whose
 // value at this lane's node is u.  sx = sigma_x/h_x with sigma = +1 when the
 // lane's node sits at the upper side along x (and likewise sy, sz).
-template <typename T> __device__ __forceinline__ VG<T> eval_vg(T u, T sx, T sy, T sz)
+template <typename T> __device__ __forceinline__ VG<T> eval_vg_body(T u, T sx, T sy, T sz)
 {
     const T b1 = cB1<T>(), b2 = cB2<T>();
     T uo = shx(u, 1);
@@ -117,7 +117,7 @@ template <typename T> __device__ __forceinline__ VG<T> eval_vg(T u, T sx, T sy, 
     return r;
 }
 
-template <typename T> __device__ __forceinline__ T eval_v(T u)
+template <typename T> __device__ __forceinline__ T eval_v_body(T u)
 {
     const T b1 = cB1<T>(), b2 = cB2<T>();
     T t = dot2_t(b1, u, b2, shx(u, 1));
@@ -129,7 +129,7 @@ template <typename T> __device__ __forceinline__ T eval_v(T u)
 // gradient coefficients of one residual component at this lane's Gauss point,
 // returns sum_g [N_a(g) X(g) + grad N_a(g) . Y(g)] for the lane's node a.
 template <typename T>
-__device__ __forceinline__ T project(T X, T Yx, T Yy, T Yz, T sx, T sy, T sz)
+__device__ __forceinline__ T project_body(T X, T Yx, T Yy, T Yz, T sx, T sy, T sz)
 {
     const T b1 = cB1<T>(), b2 = cB2<T>();
     T Xo = shx(X, 4), Yzo = shx(Yz, 4), Yxo = shx(Yx, 4), Yyo = shx(Yy, 4);
@@ -141,6 +141,45 @@ __device__ __forceinline__ T project(T X, T Yx, T Yy, T Yz, T sx, T sy, T sz)
     T Q2 = dot2_t(b1, P2, b2, P2o);
     T Q1o = shx(Q1, 1), Q2o = shx(Q2, 1);
     return fma_t(sx, Q2 + Q2o, dot2_t(b1, Q1, b2, Q1o));
+}
+
+// Evaluation and projection entry points.  With OUT set, double-float calls
+// one out-of-line copy of each body instead of inlining it: inlined at all 8 +
+// 4 + 4 call sites the double-float Jacobian body outgrows what the
+// instruction cache holds for its 16 warps per SM (out of line: -6 % at 64^3,
+// -12 % at 128^3); the shorter residual body is faster inlined (+3-5 %
+// out of line), except on mapped grids.  float and double always inline.
+static __device__ __noinline__ VG<df64> eval_vg_df(df64 u, df64 sx, df64 sy, df64 sz)
+{
+    return eval_vg_body(u, sx, sy, sz);
+}
+static __device__ __noinline__ df64 eval_v_df(df64 u) { return eval_v_body(u); }
+static __device__ __noinline__ df64 project_df(df64 X, df64 Yx, df64 Yy, df64 Yz, df64 sx,
+                                               df64 sy, df64 sz)
+{
+    return project_body(X, Yx, Yy, Yz, sx, sy, sz);
+}
+template <bool OUT, typename T> __device__ __forceinline__ VG<T> eval_vg(T u, T sx, T sy, T sz)
+{
+    if constexpr (OUT && std::is_same<T, df64>::value)
+        return eval_vg_df(u, sx, sy, sz);
+    else
+        return eval_vg_body(u, sx, sy, sz);
+}
+template <bool OUT, typename T> __device__ __forceinline__ T eval_v(T u)
+{
+    if constexpr (OUT && std::is_same<T, df64>::value)
+        return eval_v_df(u);
+    else
+        return eval_v_body(u);
+}
+template <bool OUT, typename T>
+__device__ __forceinline__ T project(T X, T Yx, T Yy, T Yz, T sx, T sy, T sz)
+{
+    if constexpr (OUT && std::is_same<T, df64>::value)
+        return project_df(X, Yx, Yy, Yz, sx, sy, sz);
+    else
+        return project_body(X, Yx, Yy, Yz, sx, sy, sz);
 }
 
 template <typename T> __device__ __forceinline__ T inv_t(T v) { return T(1) / v; }
@@ -217,6 +256,7 @@ __device__ __forceinline__ void to_phys(const Geo<T> &geo, VG<T> &e)
 template <typename T, bool JAC, bool MAPPED = false>
 __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<T> *rel)
 {
+    constexpr bool OUT = JAC || MAPPED;  // out-of-line double-float evaluation
     const int g = threadIdx.x & 7;
     const int bxi = brick % P.nbx, byi = (brick / P.nbx) % P.nby, bzi = brick / (P.nbx * P.nby);
     const int ex0 = bxi * P.bx, ey0 = byi * P.by, ez0 = bzi * P.bz;
@@ -250,8 +290,8 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
             // dx_c/dxi_k at this lane's Gauss point; idle lanes take a unit cell
             vec4<T> xc = valid ? load_c<T>(P.Xc + node)
                                : vec4<T>{gx ? T(1) : T(0), gy ? T(1) : T(0), gz ? T(1) : T(0), T(0)};
-            const VG<T> cx = eval_vg(xc.x, sx, sy, sz), cy = eval_vg(xc.y, sx, sy, sz),
-                        cz = eval_vg(xc.z, sx, sy, sz);
+            const VG<T> cx = eval_vg<OUT>(xc.x, sx, sy, sz), cy = eval_vg<OUT>(xc.y, sx, sy, sz),
+                        cz = eval_vg<OUT>(xc.z, sx, sy, sz);
             const T J[3][3] = {{cx.gx, cx.gy, cx.gz}, {cy.gx, cy.gy, cy.gz}, {cz.gx, cz.gy, cz.gz}};
             const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
             const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
@@ -281,8 +321,8 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
         }
         GP<T> q;
         {
-            VG<T> e0 = eval_vg(u.x, sx, sy, sz), e1 = eval_vg(u.y, sx, sy, sz),
-                  e2 = eval_vg(u.z, sx, sy, sz), e3 = eval_vg(u.w, sx, sy, sz);
+            VG<T> e0 = eval_vg<OUT>(u.x, sx, sy, sz), e1 = eval_vg<OUT>(u.y, sx, sy, sz),
+                  e2 = eval_vg<OUT>(u.z, sx, sy, sz), e3 = eval_vg<OUT>(u.w, sx, sy, sz);
             if constexpr (MAPPED) {
                 to_phys(geo, e0);
                 to_phys(geo, e1);
@@ -294,14 +334,14 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
             q.v[2] = e2.v; q.gv[2][0] = e2.gx; q.gv[2][1] = e2.gy; q.gv[2][2] = e2.gz;
             q.p = e3.v; q.gp[0] = e3.gx; q.gp[1] = e3.gy; q.gp[2] = e3.gz;
         }
-        q.a[0] = eval_v(ac.x);
-        q.a[1] = eval_v(ac.y);
-        q.a[2] = eval_v(ac.z);
-        q.s = P.has_s ? eval_v(ac.w) : T(1);
+        q.a[0] = eval_v<OUT>(ac.x);
+        q.a[1] = eval_v<OUT>(ac.y);
+        q.a[2] = eval_v<OUT>(ac.z);
+        q.s = P.has_s ? eval_v<OUT>(ac.w) : T(1);
         if (P.f) {
-            q.f[0] = eval_v(ff.x);
-            q.f[1] = eval_v(ff.y);
-            q.f[2] = eval_v(ff.z);
+            q.f[0] = eval_v<OUT>(ff.x);
+            q.f[1] = eval_v<OUT>(ff.y);
+            q.f[2] = eval_v<OUT>(ff.z);
         } else {
             q.f[0] = q.f[1] = q.f[2] = T(0);
         }
@@ -328,8 +368,8 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
             vec4<T> xx = valid ? load_c<T>(P.x + node) : zero;
             T dv[3], dgv[3][3], da[3], dp, dgp[3];
             {
-                VG<T> e0 = eval_vg(xx.x, sx, sy, sz), e1 = eval_vg(xx.y, sx, sy, sz),
-                      e2 = eval_vg(xx.z, sx, sy, sz), e3 = eval_vg(xx.w, sx, sy, sz);
+                VG<T> e0 = eval_vg<OUT>(xx.x, sx, sy, sz), e1 = eval_vg<OUT>(xx.y, sx, sy, sz),
+                      e2 = eval_vg<OUT>(xx.z, sx, sy, sz), e3 = eval_vg<OUT>(xx.w, sx, sy, sz);
                 if constexpr (MAPPED) {
                     to_phys(geo, e0);
                     to_phys(geo, e1);
@@ -391,15 +431,15 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
                 Y[c][2] = geo.det * (geo.Ji[2][0] * y0 + geo.Ji[2][1] * y1 + geo.Ji[2][2] * y2);
                 X[c] = geo.det * X[c];
             }
-            r.x = project(X[0], Y[0][0], Y[0][1], Y[0][2], sx, sy, sz);
-            r.y = project(X[1], Y[1][0], Y[1][1], Y[1][2], sx, sy, sz);
-            r.z = project(X[2], Y[2][0], Y[2][1], Y[2][2], sx, sy, sz);
-            r.w = project(X[3], Y[3][0], Y[3][1], Y[3][2], sx, sy, sz);
+            r.x = project<OUT>(X[0], Y[0][0], Y[0][1], Y[0][2], sx, sy, sz);
+            r.y = project<OUT>(X[1], Y[1][0], Y[1][1], Y[1][2], sx, sy, sz);
+            r.z = project<OUT>(X[2], Y[2][0], Y[2][1], Y[2][2], sx, sy, sz);
+            r.w = project<OUT>(X[3], Y[3][0], Y[3][1], Y[3][2], sx, sy, sz);
         } else {
-            r.x = P.detJ * project(X[0], Y[0][0], Y[0][1], Y[0][2], sx, sy, sz);
-            r.y = P.detJ * project(X[1], Y[1][0], Y[1][1], Y[1][2], sx, sy, sz);
-            r.z = P.detJ * project(X[2], Y[2][0], Y[2][1], Y[2][2], sx, sy, sz);
-            r.w = P.detJ * project(X[3], Y[3][0], Y[3][1], Y[3][2], sx, sy, sz);
+            r.x = P.detJ * project<OUT>(X[0], Y[0][0], Y[0][1], Y[0][2], sx, sy, sz);
+            r.y = P.detJ * project<OUT>(X[1], Y[1][0], Y[1][1], Y[1][2], sx, sy, sz);
+            r.z = P.detJ * project<OUT>(X[2], Y[2][0], Y[2][1], Y[2][2], sx, sy, sz);
+            r.w = P.detJ * project<OUT>(X[3], Y[3][0], Y[3][1], Y[3][2], sx, sy, sz);
         }
         if (slot < nel) rel[slot * 8 + g] = valid ? r : zero;
     }
