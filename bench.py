@@ -50,14 +50,17 @@ LAUNCHES_PER_STEP = 14
 # FP64 flops per element of one VMS Jacobian apply / residual (DFMA = 2,
 # DMUL = DADD = 1), from ncu instruction counts of the native FP64 kernels.
 FLOPS_PER_ELEM = {"jacobian": 4808.0, "residual": 3008.0}
-# FP32 pipe instructions (FADD + FMUL + FFMA; no paired FADD2/FMUL2/FFMA2 are
-# issued) per element of the double-float kernels, brick + gather, from ncu's
-# sm__sass_thread_inst_executed_op_*_pred_on counters (64^3 capture).
-FP32_INSTR_PER_ELEM_DF64 = {"jacobian": 34339.0 + 69.6, "residual": 20979.0 + 69.6}
+# FP32-pipe operations per element of the double-float kernels, brick + gather:
+# FADD + FMUL + FFMA + 2 x (FADD2 + FMUL2 + FFMA2) (a paired instruction does two
+# lanes of work), from ncu's sm__sass_thread_inst_executed_op_*_pred_on counters
+# (64^3 capture).  Jacobian: 16,075 scalar + 9,360 paired; residual: 8,091 +
+# 6,672; gather 69.6 scalar.
+FP32_OPS_PER_ELEM_DF64 = {"jacobian": 16075.0 + 2 * 9360.0 + 69.6,
+                          "residual": 8091.0 + 2 * 6672.0 + 69.6}
 # dram__bytes_read.sum + dram__bytes_write.sum of one double-float Jacobian apply
-# at 64^3 (brick kernel 26,429,952 + 3,072 B + gather kernel 13,288,448 B; the
+# at 64^3 (brick kernel 26,459,904 + 2,304 B + gather kernel 13,288,448 B; the
 # writes stay in L2 within the launch)
-TRAFFIC_JAC_DF64_64 = 39_721_472
+TRAFFIC_JAC_DF64_64 = 39_750_656
 
 
 def dist_env():
@@ -434,8 +437,8 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
     fma32 = B.fsi_measure_fma_peak(local, fsi.FSI_F32)
     E = N ** 3
     jac_ms = per64[ops.index("jacobian")]
-    achieved = FP32_INSTR_PER_ELEM_DF64["jacobian"] * E / (jac_ms * 1e-3)
-    peak_instr = fma32 / 2.0  # the probe counts an FMA instruction as 2 flops
+    achieved = FP32_OPS_PER_ELEM_DF64["jacobian"] * E / (jac_ms * 1e-3)
+    peak_instr = fma32 / 2.0  # FMA operations/s: the probe counts an FMA as 2 flops
     # DRAM bytes of one launch (brick + gather kernels), from an ncu capture of
     # this workload; only meaningful for the 64^3 grid it was taken on
     traffic = TRAFFIC_JAC_DF64_64 if N == N_GRID else None
@@ -501,10 +504,11 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "kernel": "vms_jacobian df64 (brick + gather)",
                      "achieved": achieved / 1e12, "peak": peak_instr / 1e12,
-                     "unit": "T FP32-pipe instructions/s", "frac": achieved / peak_instr,
+                     "unit": "T FP32-pipe operations/s", "frac": achieved / peak_instr,
                      "traffic": traffic,
-                     "peak_source": "measured FP32 FMA instruction rate (fsi_measure_fma_peak / 2, "
-                                    "this run); instructions per element from ncu"},
+                     "peak_source": "measured FP32 FMA operation rate (fsi_measure_fma_peak / 2, "
+                                    "this run); operations per element from ncu instruction "
+                                    "counts, a paired FADD2/FMUL2/FFMA2 counted as two"},
         "cpu_baseline": cpu,
         "e2e": None if e2e_val is None else {
             "value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
