@@ -6,8 +6,11 @@
 // butterflies run the same instruction sequence for every field, so two fields
 // at a time go through these pairs.  float and double-float pairs use the
 // paired intrinsics (__fadd2_rn, __fmul2_rn, __ffma2_rn): each half rounds to
-// nearest exactly like the scalar operation, so the results equal the scalar
-// code's bit for bit.  double has no paired form; its pair is two scalars.
+// nearest exactly like the scalar operation.  The double-float pair performs
+// the scalar double-float sequence operation for operation, so its results
+// equal the scalar code's bit for bit; a float pair fixes where a*b + c*d is
+// contracted into an FMA, which the compiler chooses freely in scalar code.
+// double has no paired form; its pair is two scalars.
 #pragma once
 
 #include <cuda_runtime.h>
