@@ -30,7 +30,14 @@ MUTATIONS = {
                           "return node_id(N, ex + ((a >> 1) & 1), ey + (a & 1), ez + ((a >> 2) & 1));"),
     "locate_xi_sign": ("xi[3 * b + k] = 2.0 * (t[k] - (double)e[k]) - 1.0;",
                        "xi[3 * b + k] = 1.0 - 2.0 * (t[k] - (double)e[k]);"),
+    # mapped grids: caught by the pins of tests/test_oracle_mapped.py
+    "mapped_gradient_transposed": ("t += dNdxi[3 * a + k] * Ji[k][j];",
+                                   "t += dNdxi[3 * a + k] * Ji[j][k];"),
+    "mapped_metric_transposed": ("t += Ji[k][i] * Ji[k][j];", "t += Ji[i][k] * Ji[j][k];"),
+    "mapped_det_dropped": ("st->detJ = det;", "st->detJ = 1.0;"),
+    "mapped_locate_unsettled": ("if (!(last < 1e-12)) return 0;", ";"),
 }
+MAPPED = {k for k in MUTATIONS if k.startswith("mapped_")}
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
@@ -43,8 +50,9 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", str(lib),
                            str(tmp_path / "fsi_oracle.c"), "-lm"])
     env = dict(os.environ, FSI_ORACLE_LIB=str(lib))
+    files = (["tests/test_oracle_mapped.py"] if name in MAPPED
+             else ["tests/test_oracle_vms.py", "tests/test_oracle_dlm.py"])
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        "tests/test_oracle_vms.py", "tests/test_oracle_dlm.py",
-                        "-k", "not manufactured and not quadratic"],
+                        *files, "-k", "not manufactured and not quadratic"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"planted mistake {name} was not caught:\n{r.stdout[-2000:]}"
