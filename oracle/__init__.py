@@ -14,6 +14,8 @@ Contents and the passages they follow:
   product (Eq. fluid_weak_form + the VMS terms Sec. 2.1 refers to; reduced
   system of Sec. 2.4), point location, interpolation (Eq. nodal_solid_velo)
   and spreading (Eq. fsi_constraint_matrix).
+* ``tet``       -- the same operators on unstructured meshes of linear
+  tetrahedra (the element family of the paper's valve mesh, Sec. 4).
 * ``timeint``   -- generalized-alpha constants and stage values (Sec. 2.4).
 * ``newton``    -- the Newton step of Sec. 2.4 on the reduced 2x2 block system
   with direct sparse solves (small grids), and the point-mass solid stand-in.

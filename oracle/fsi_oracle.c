@@ -18,6 +18,10 @@
  *   - Point location, the interpolation u_A = sum_B N_B(phi(X_A)) v_B of
  *     Eq. (nodal_solid_velo) and the spreading C^lambda lambda with
  *     C_AB = N_A(phi(X_B)) I of Eq. (fsi_constraint_matrix) (Sec. 2.3).
+ *   - The same operators on mapped structured grids (node coordinates) and on
+ *     unstructured meshes of linear tetrahedra (the element family of the
+ *     paper's valve mesh, Sec. 4), with the weak form per quadrature point
+ *     shared by all element types (gp_residual, gp_jacobian).
  *
  * Everything is the definition written out: loops over elements, the eight
  * 2x2x2 Gauss points and the eight test nodes; no sum factorisation, no
@@ -225,48 +229,57 @@ static void eval_gp(const int N[3], const double h[3], const double *Xn, int ex,
  * with the strong residuals r_M = rho (a + v.grad v - f) + grad p,
  * r_C = div v, and the fine scales u' = -(tau_M/rho) r_M, p' = -rho tau_C r_C.
  * stab = 0 drops every term carrying u' or p' (plain Galerkin).             */
+/* The weak form above at one quadrature point: st holds the shape values and
+ * physical gradients of the nloc local nodes and the field values there; w is
+ * the quadrature weight times det J.  Adds into Re[nloc][4].                 */
+static void gp_residual(const gp_state *stp, const or_phys *ph, int nloc, double w, int stab,
+                        double Re[][4])
+{
+    const gp_state st = *stp;
+    const double rho = ph->rho, mu = ph->mu;
+    double conv[3], rM[3], up[3];
+    for (int i = 0; i < 3; ++i) {
+        conv[i] = 0.0;
+        for (int j = 0; j < 3; ++j) conv[i] += st.v[j] * st.gv[i][j];
+        rM[i] = rho * (st.a[i] + conv[i] - st.f[i]) + st.gp[i];
+    }
+    double rC = st.gv[0][0] + st.gv[1][1] + st.gv[2][2];
+    double tau[2];
+    tau_of_G(st.v, st.s, st.G, rho, mu, ph->ct_dt2, ph->C_I, tau);
+    double pp = 0.0;
+    for (int i = 0; i < 3; ++i) up[i] = stab ? -(tau[0] / rho) * rM[i] : 0.0;
+    if (stab) pp = -rho * tau[1] * rC;
+
+    for (int A_ = 0; A_ < nloc; ++A_) {
+        const double NA = st.N[A_];
+        const double *dNA = st.dN[A_];
+        double vgradN = 0.0;
+        for (int j = 0; j < 3; ++j) vgradN += st.v[j] * dNA[j];
+        for (int i = 0; i < 3; ++i) {
+            double t = NA * rho * (st.a[i] + conv[i] - st.f[i]);
+            for (int j = 0; j < 3; ++j) t += dNA[j] * mu * (st.gv[i][j] + st.gv[j][i]);
+            t -= dNA[i] * st.p;
+            t -= rho * vgradN * up[i];
+            t -= dNA[i] * pp;
+            for (int j = 0; j < 3; ++j) t += NA * rho * up[j] * st.gv[i][j];
+            for (int j = 0; j < 3; ++j) t -= rho * dNA[j] * up[i] * up[j];
+            Re[A_][i] += w * t;
+        }
+        double c = NA * rC;
+        for (int j = 0; j < 3; ++j) c -= dNA[j] * up[j];
+        Re[A_][3] += w * c;
+    }
+}
+
 static void element_residual(const int N[3], const double h[3], const double *Xn,
                              const or_phys *ph, int ex, int ey, int ez, const double *U,
                              const double *A, const double *f, int stab, double Re[8][4])
 {
-    const double rho = ph->rho, mu = ph->mu;
     memset(Re, 0, 8 * 4 * sizeof(double));
     for (int g = 0; g < 8; ++g) {
         gp_state st;
         eval_gp(N, h, Xn, ex, ey, ez, g, U, A, f, ph->has_s, &st);
-        const double detJ = st.detJ;
-        double conv[3], rM[3], up[3];
-        for (int i = 0; i < 3; ++i) {
-            conv[i] = 0.0;
-            for (int j = 0; j < 3; ++j) conv[i] += st.v[j] * st.gv[i][j];
-            rM[i] = rho * (st.a[i] + conv[i] - st.f[i]) + st.gp[i];
-        }
-        double rC = st.gv[0][0] + st.gv[1][1] + st.gv[2][2];
-        double tau[2];
-        tau_of_G(st.v, st.s, st.G, rho, mu, ph->ct_dt2, ph->C_I, tau);
-        double pp = 0.0;
-        for (int i = 0; i < 3; ++i) up[i] = stab ? -(tau[0] / rho) * rM[i] : 0.0;
-        if (stab) pp = -rho * tau[1] * rC;
-
-        for (int A_ = 0; A_ < 8; ++A_) {
-            const double NA = st.N[A_];
-            const double *dNA = st.dN[A_];
-            double vgradN = 0.0;
-            for (int j = 0; j < 3; ++j) vgradN += st.v[j] * dNA[j];
-            for (int i = 0; i < 3; ++i) {
-                double t = NA * rho * (st.a[i] + conv[i] - st.f[i]);
-                for (int j = 0; j < 3; ++j) t += dNA[j] * mu * (st.gv[i][j] + st.gv[j][i]);
-                t -= dNA[i] * st.p;
-                t -= rho * vgradN * up[i];
-                t -= dNA[i] * pp;
-                for (int j = 0; j < 3; ++j) t += NA * rho * up[j] * st.gv[i][j];
-                for (int j = 0; j < 3; ++j) t -= rho * dNA[j] * up[i] * up[j];
-                Re[A_][i] += detJ * t;
-            }
-            double c = NA * rC;
-            for (int j = 0; j < 3; ++j) c -= dNA[j] * up[j];
-            Re[A_][3] += detJ * c;
-        }
+        gp_residual(&st, ph, 8, st.detJ, stab, Re);
     }
 }
 
@@ -278,85 +291,94 @@ static void element_residual(const int N[3], const double h[3], const double *Xn
  * c_v = alpha_f gamma dt (Sec. 2.4).  xe holds the 8x4 local direction.
  * Every term of element_residual is differentiated, including the
  * dependence of tau_M and tau_C on v.                                        */
+/* The directional derivative of gp_residual at one quadrature point in the
+ * direction xe[nloc][4] (velocity columns scaled by c_v in U and c_a in A,
+ * pressure column unscaled); w = quadrature weight times det J.            */
+static void gp_jacobian(const gp_state *stp, const or_phys *ph, int nloc, double w,
+                        const double xe[][4], double c_a, double c_v, double Je[][4])
+{
+    const gp_state st = *stp;
+    const double rho = ph->rho, mu = ph->mu;
+    /* direction at the Gauss point */
+    double dv[3] = {0, 0, 0}, dgv[3][3] = {{0}}, dp = 0.0, dgp[3] = {0, 0, 0};
+    double da[3] = {0, 0, 0};
+    for (int a = 0; a < nloc; ++a) {
+        for (int i = 0; i < 3; ++i) {
+            dv[i] += st.N[a] * c_v * xe[a][i];
+            da[i] += st.N[a] * c_a * xe[a][i];
+            for (int j = 0; j < 3; ++j) dgv[i][j] += st.dN[a][j] * c_v * xe[a][i];
+        }
+        dp += st.N[a] * xe[a][3];
+        for (int j = 0; j < 3; ++j) dgp[j] += st.dN[a][j] * xe[a][3];
+    }
+    /* base state */
+    double conv[3], rM[3], up[3];
+    for (int i = 0; i < 3; ++i) {
+        conv[i] = 0.0;
+        for (int j = 0; j < 3; ++j) conv[i] += st.v[j] * st.gv[i][j];
+        rM[i] = rho * (st.a[i] + conv[i] - st.f[i]) + st.gp[i];
+    }
+    double rC = st.gv[0][0] + st.gv[1][1] + st.gv[2][2];
+    double tau[2];
+    tau_of_G(st.v, st.s, st.G, rho, mu, ph->ct_dt2, ph->C_I, tau);
+    double tauM = tau[0], tauC = tau[1];
+    for (int i = 0; i < 3; ++i) up[i] = -(tauM / rho) * rM[i];
+    /* derivatives */
+    double dconv[3], drM[3], dup[3];
+    for (int i = 0; i < 3; ++i) {
+        dconv[i] = 0.0;
+        for (int j = 0; j < 3; ++j) dconv[i] += dv[j] * st.gv[i][j] + st.v[j] * dgv[i][j];
+        drM[i] = rho * (da[i] + dconv[i]) + dgp[i];
+    }
+    double drC = dgv[0][0] + dgv[1][1] + dgv[2][2];
+    /* tau_M = (s Q)^(-1/2), Q = C_T/dt^2 + v.G v + C_I nu^2 G:G
+     * d tau_M = -1/2 tau_M^3 s dQ, dQ = 2 v.G dv ;
+     * tau_C = 1/(tau_M trG) -> d tau_C = -tau_C d tau_M / tau_M          */
+    double dQ = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) dQ += 2.0 * st.v[i] * st.G[i][j] * dv[j];
+    double dtauM = -0.5 * tauM * tauM * tauM * st.s * dQ;
+    double dtauC = -tauC * dtauM / tauM;
+    for (int i = 0; i < 3; ++i) dup[i] = -(dtauM * rM[i] + tauM * drM[i]) / rho;
+    double dpp = -rho * (dtauC * rC + tauC * drC);
+
+    for (int A_ = 0; A_ < nloc; ++A_) {
+        const double NA = st.N[A_];
+        const double *dNA = st.dN[A_];
+        double vgradN = 0.0, dvgradN = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            vgradN += st.v[j] * dNA[j];
+            dvgradN += dv[j] * dNA[j];
+        }
+        for (int i = 0; i < 3; ++i) {
+            double t = NA * rho * (da[i] + dconv[i]);
+            for (int j = 0; j < 3; ++j) t += dNA[j] * mu * (dgv[i][j] + dgv[j][i]);
+            t -= dNA[i] * dp;
+            t -= rho * (dvgradN * up[i] + vgradN * dup[i]);
+            t -= dNA[i] * dpp;
+            for (int j = 0; j < 3; ++j)
+                t += NA * rho * (dup[j] * st.gv[i][j] + up[j] * dgv[i][j]);
+            for (int j = 0; j < 3; ++j)
+                t -= rho * dNA[j] * (dup[i] * up[j] + up[i] * dup[j]);
+            Je[A_][i] += w * t;
+        }
+        double c = NA * drC;
+        for (int j = 0; j < 3; ++j) c -= dNA[j] * dup[j];
+        Je[A_][3] += w * c;
+    }
+}
+
 static void element_jacobian_apply(const int N[3], const double h[3], const double *Xn,
                                    const or_phys *ph, int ex, int ey, int ez, const double *U,
                                    const double *A, const double *f,
                                    const double xe[8][4], double c_a, double c_v,
                                    double Je[8][4])
 {
-    const double rho = ph->rho, mu = ph->mu;
     memset(Je, 0, 8 * 4 * sizeof(double));
     for (int g = 0; g < 8; ++g) {
         gp_state st;
         eval_gp(N, h, Xn, ex, ey, ez, g, U, A, f, ph->has_s, &st);
-        const double detJ = st.detJ;
-        /* direction at the Gauss point */
-        double dv[3] = {0, 0, 0}, dgv[3][3] = {{0}}, dp = 0.0, dgp[3] = {0, 0, 0};
-        double da[3] = {0, 0, 0};
-        for (int a = 0; a < 8; ++a) {
-            for (int i = 0; i < 3; ++i) {
-                dv[i] += st.N[a] * c_v * xe[a][i];
-                da[i] += st.N[a] * c_a * xe[a][i];
-                for (int j = 0; j < 3; ++j) dgv[i][j] += st.dN[a][j] * c_v * xe[a][i];
-            }
-            dp += st.N[a] * xe[a][3];
-            for (int j = 0; j < 3; ++j) dgp[j] += st.dN[a][j] * xe[a][3];
-        }
-        /* base state */
-        double conv[3], rM[3], up[3];
-        for (int i = 0; i < 3; ++i) {
-            conv[i] = 0.0;
-            for (int j = 0; j < 3; ++j) conv[i] += st.v[j] * st.gv[i][j];
-            rM[i] = rho * (st.a[i] + conv[i] - st.f[i]) + st.gp[i];
-        }
-        double rC = st.gv[0][0] + st.gv[1][1] + st.gv[2][2];
-        double tau[2];
-        tau_of_G(st.v, st.s, st.G, rho, mu, ph->ct_dt2, ph->C_I, tau);
-        double tauM = tau[0], tauC = tau[1];
-        for (int i = 0; i < 3; ++i) up[i] = -(tauM / rho) * rM[i];
-        /* derivatives */
-        double dconv[3], drM[3], dup[3];
-        for (int i = 0; i < 3; ++i) {
-            dconv[i] = 0.0;
-            for (int j = 0; j < 3; ++j) dconv[i] += dv[j] * st.gv[i][j] + st.v[j] * dgv[i][j];
-            drM[i] = rho * (da[i] + dconv[i]) + dgp[i];
-        }
-        double drC = dgv[0][0] + dgv[1][1] + dgv[2][2];
-        /* tau_M = (s Q)^(-1/2), Q = C_T/dt^2 + v.G v + C_I nu^2 G:G
-         * d tau_M = -1/2 tau_M^3 s dQ, dQ = 2 v.G dv ;
-         * tau_C = 1/(tau_M trG) -> d tau_C = -tau_C d tau_M / tau_M          */
-        double dQ = 0.0;
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) dQ += 2.0 * st.v[i] * st.G[i][j] * dv[j];
-        double dtauM = -0.5 * tauM * tauM * tauM * st.s * dQ;
-        double dtauC = -tauC * dtauM / tauM;
-        for (int i = 0; i < 3; ++i) dup[i] = -(dtauM * rM[i] + tauM * drM[i]) / rho;
-        double dpp = -rho * (dtauC * rC + tauC * drC);
-
-        for (int A_ = 0; A_ < 8; ++A_) {
-            const double NA = st.N[A_];
-            const double *dNA = st.dN[A_];
-            double vgradN = 0.0, dvgradN = 0.0;
-            for (int j = 0; j < 3; ++j) {
-                vgradN += st.v[j] * dNA[j];
-                dvgradN += dv[j] * dNA[j];
-            }
-            for (int i = 0; i < 3; ++i) {
-                double t = NA * rho * (da[i] + dconv[i]);
-                for (int j = 0; j < 3; ++j) t += dNA[j] * mu * (dgv[i][j] + dgv[j][i]);
-                t -= dNA[i] * dp;
-                t -= rho * (dvgradN * up[i] + vgradN * dup[i]);
-                t -= dNA[i] * dpp;
-                for (int j = 0; j < 3; ++j)
-                    t += NA * rho * (dup[j] * st.gv[i][j] + up[j] * dgv[i][j]);
-                for (int j = 0; j < 3; ++j)
-                    t -= rho * dNA[j] * (dup[i] * up[j] + up[i] * dup[j]);
-                Je[A_][i] += detJ * t;
-            }
-            double c = NA * drC;
-            for (int j = 0; j < 3; ++j) c -= dNA[j] * dup[j];
-            Je[A_][3] += detJ * c;
-        }
+        gp_jacobian(&st, ph, 8, st.detJ, xe, c_a, c_v, Je);
     }
 }
 
@@ -679,5 +701,276 @@ void or_spread(const int N[3], int64_t m, const int32_t *elem, const double *xi,
             int64_t nd = elem_node(N, ex, ey, ez, a);
             for (int i = 0; i < 3; ++i) F[4 * nd + i] += wb * Nv[a] * lam[3 * b + i];
         }
+    }
+}
+
+/* ======================================================================== */
+/* Unstructured tetrahedral background meshes: linear (P1-P1) tetrahedra,    */
+/* the element family of the paper's valve fluid mesh (Sec. 4).              */
+/*                                                                          */
+/* Nodes X[n][3], elements tets[E][4] (node numbers, any orientation).       */
+/* Reference tetrahedron with vertices (0,0,0), (1,0,0), (0,1,0), (0,0,1):   */
+/* N_0 = 1 - xi_1 - xi_2 - xi_3, N_k = xi_k.  J_ik = dx_i/dxi_k =            */
+/* x_{k,i} - x_{0,i}; dN_a/dx_j = sum_k dN_a/dxi_k (J^-1)_kj; the metric of   */
+/* Sec. 2.1 is G = J^-T J^-1 with the reference tetrahedron as the parent    */
+/* domain.  Quadrature: the symmetric 4-point rule of degree 2, barycentric  */
+/* coordinates (al, be, be, be) and permutations, al = (5 + 3 sqrt 5)/20,    */
+/* be = (5 - sqrt 5)/20, each with weight |det J|/24 (the volume / 4).      */
+/* The weak form per quadrature point is gp_residual / gp_jacobian, the same */
+/* as on hexahedra.  On P1 elements the gradients are constant per element,  */
+/* so the dropped viscous term of r_M is exactly zero here.                  */
+/* ======================================================================== */
+
+static void tet_geometry(const double *X, const int32_t *t, double dN[4][3], double *det,
+                         double G[3][3])
+{
+    double J[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) J[i][k] = X[3 * t[k + 1] + i] - X[3 * t[0] + i];
+    double d = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+               J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    double Ji[3][3];
+    Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / d;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / d;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / d;
+    Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / d;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / d;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / d;
+    Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / d;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / d;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / d;
+    /* dN_k/dx_j = (J^-1)_{k-1,j} for k = 1..3, dN_0 = -(sum of the others) */
+    for (int j = 0; j < 3; ++j) {
+        dN[1][j] = Ji[0][j];
+        dN[2][j] = Ji[1][j];
+        dN[3][j] = Ji[2][j];
+        dN[0][j] = -(Ji[0][j] + Ji[1][j] + Ji[2][j]);
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += Ji[k][i] * Ji[k][j];
+            G[i][j] = s;
+        }
+    *det = d;
+}
+
+static void eval_qp_tet(const double *X, const int32_t *t, int q, const double *U,
+                        const double *A, const double *f, int has_s, gp_state *st)
+{
+    const double al = (5.0 + 3.0 * sqrt(5.0)) / 20.0, be = (5.0 - sqrt(5.0)) / 20.0;
+    memset(st, 0, sizeof *st);
+    double det;
+    tet_geometry(X, t, st->dN, &det, st->G);
+    st->detJ = det;
+    st->s = has_s ? 0.0 : 1.0;
+    for (int a = 0; a < 4; ++a) {
+        st->N[a] = (a == q) ? al : be;
+        const int64_t nd = t[a];
+        const double *u = U + 4 * nd;
+        const double *ac = A + 4 * nd;
+        for (int i = 0; i < 3; ++i) {
+            st->v[i] += st->N[a] * u[i];
+            st->a[i] += st->N[a] * ac[i];
+            if (f) st->f[i] += st->N[a] * f[4 * nd + i];
+            for (int j = 0; j < 3; ++j) st->gv[i][j] += st->dN[a][j] * u[i];
+        }
+        st->p += st->N[a] * u[3];
+        for (int j = 0; j < 3; ++j) st->gp[j] += st->dN[a][j] * u[3];
+        if (has_s) st->s += st->N[a] * ac[3];
+    }
+}
+
+static void tet_element_residual(const double *X, const int32_t *t, const or_phys *ph,
+                                 const double *U, const double *A, const double *f, int stab,
+                                 double Re[4][4])
+{
+    memset(Re, 0, 16 * sizeof(double));
+    for (int q = 0; q < 4; ++q) {
+        gp_state st;
+        eval_qp_tet(X, t, q, U, A, f, ph->has_s, &st);
+        gp_residual(&st, ph, 4, fabs(st.detJ) / 24.0, stab, Re);
+    }
+}
+
+static void tet_element_jacobian_apply(const double *X, const int32_t *t, const or_phys *ph,
+                                       const double *U, const double *A, const double *f,
+                                       const double xe[4][4], double c_a, double c_v,
+                                       double Je[4][4])
+{
+    memset(Je, 0, 16 * sizeof(double));
+    for (int q = 0; q < 4; ++q) {
+        gp_state st;
+        eval_qp_tet(X, t, q, U, A, f, ph->has_s, &st);
+        gp_jacobian(&st, ph, 4, fabs(st.detJ) / 24.0, xe, c_a, c_v, Je);
+    }
+}
+
+/* Assembled residual R[n][4] on a tetrahedral mesh (element contributions in
+ * parallel, assembly serial in element order).                              */
+void or_tet_residual(int64_t n, const double *X, int64_t E, const int32_t *tets,
+                     const double phys[5], const double *U, const double *A, const double *f,
+                     int stab, double *R, int nthreads)
+{
+    or_phys ph = unpack_phys(phys);
+    double *Rel = (double *)malloc((size_t)E * 16 * sizeof(double));
+    set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < E; ++e)
+        tet_element_residual(X, tets + 4 * e, &ph, U, A, f, stab, (double(*)[4])(Rel + 16 * e));
+    memset(R, 0, (size_t)n * 4 * sizeof(double));
+    for (int64_t e = 0; e < E; ++e)
+        for (int a = 0; a < 4; ++a)
+            for (int c = 0; c < 4; ++c) R[4 * (int64_t)tets[4 * e + a] + c] += Rel[16 * e + 4 * a + c];
+    free(Rel);
+}
+
+/* Assembled Jacobian-vector product Jx[n][4] (stab = 1), chain factors c_a,
+ * c_v as on hexahedra.                                                        */
+void or_tet_jacobian_apply(int64_t n, const double *X, int64_t E, const int32_t *tets,
+                           const double phys[5], const double *U, const double *A,
+                           const double *f, const double *x, double c_a, double c_v, double *Jx,
+                           int nthreads)
+{
+    or_phys ph = unpack_phys(phys);
+    double *Jel = (double *)malloc((size_t)E * 16 * sizeof(double));
+    set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t *t = tets + 4 * e;
+        double xe[4][4];
+        for (int a = 0; a < 4; ++a)
+            for (int c = 0; c < 4; ++c) xe[a][c] = x[4 * (int64_t)t[a] + c];
+        tet_element_jacobian_apply(X, t, &ph, U, A, f, (const double(*)[4])xe, c_a, c_v,
+                                   (double(*)[4])(Jel + 16 * e));
+    }
+    memset(Jx, 0, (size_t)n * 4 * sizeof(double));
+    for (int64_t e = 0; e < E; ++e)
+        for (int a = 0; a < 4; ++a)
+            for (int c = 0; c < 4; ++c)
+                Jx[4 * (int64_t)tets[4 * e + a] + c] += Jel[16 * e + 4 * a + c];
+    free(Jel);
+}
+
+/* Element Jacobians Ke[E][16][16] (row = 4 a + c of the residual, column =
+ * 4 b + d of the direction), by applying the element linearisation to the
+ * 16 unit directions.                                                        */
+void or_tet_element_jacobian(const double *X, int64_t E, const int32_t *tets,
+                             const double phys[5], const double *U, const double *A,
+                             const double *f, double c_a, double c_v, double *Ke, int nthreads)
+{
+    or_phys ph = unpack_phys(phys);
+    set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < E; ++e)
+        for (int col = 0; col < 16; ++col) {
+            double xe[4][4] = {{0}};
+            double Je[4][4];
+            xe[col / 4][col % 4] = 1.0;
+            tet_element_jacobian_apply(X, tets + 4 * e, &ph, U, A, f, (const double(*)[4])xe,
+                                       c_a, c_v, Je);
+            for (int row = 0; row < 16; ++row)
+                Ke[(int64_t)256 * e + 16 * row + col] = Je[row / 4][row % 4];
+        }
+}
+
+/* Barycentric coordinates of P in tetrahedron t: with e_k = x_k - x_0 and
+ * d = P - x_0, lam_1 = d.(e2 x e3)/D, lam_2 = e1.(d x e3)/D,
+ * lam_3 = e1.(e2 x d)/D, D = e1.(e2 x e3), lam_0 = 1 - lam_1 - lam_2 - lam_3,
+ * each product and sum evaluated left to right as written.                   */
+void or_tet_barycentric(const double *X, const int32_t *t, const double P[3], double lam[4])
+{
+    double e1[3], e2[3], e3[3], d[3];
+    for (int i = 0; i < 3; ++i) {
+        e1[i] = X[3 * t[1] + i] - X[3 * t[0] + i];
+        e2[i] = X[3 * t[2] + i] - X[3 * t[0] + i];
+        e3[i] = X[3 * t[3] + i] - X[3 * t[0] + i];
+        d[i] = P[i] - X[3 * t[0] + i];
+    }
+    /* c = e2 x e3 */
+    double c0 = e2[1] * e3[2] - e2[2] * e3[1];
+    double c1 = e2[2] * e3[0] - e2[0] * e3[2];
+    double c2 = e2[0] * e3[1] - e2[1] * e3[0];
+    double D = e1[0] * c0 + e1[1] * c1 + e1[2] * c2;
+    double l1 = (d[0] * c0 + d[1] * c1 + d[2] * c2) / D;
+    /* d x e3 and e2 x d */
+    double a0 = d[1] * e3[2] - d[2] * e3[1];
+    double a1 = d[2] * e3[0] - d[0] * e3[2];
+    double a2 = d[0] * e3[1] - d[1] * e3[0];
+    double l2 = (e1[0] * a0 + e1[1] * a1 + e1[2] * a2) / D;
+    double b0 = e2[1] * d[2] - e2[2] * d[1];
+    double b1 = e2[2] * d[0] - e2[0] * d[2];
+    double b2 = e2[0] * d[1] - e2[1] * d[0];
+    double l3 = (e1[0] * b0 + e1[1] * b1 + e1[2] * b2) / D;
+    lam[1] = l1;
+    lam[2] = l2;
+    lam[3] = l3;
+    lam[0] = 1.0 - l1 - l2 - l3;
+}
+
+/* Point location on a tetrahedral mesh (the point search of Sec. 3 /
+ * Algorithm 1): brute force over the elements in element order; the point
+ * belongs to the first tetrahedron whose four barycentric coordinates are all
+ * >= -1e-12.  lam_out[m][3] = (lam_1, lam_2, lam_3) of that element.
+ * Outside points get elem = -1 and zeros.  Returns the outside count.        */
+int64_t or_tet_locate(const double *X, int64_t E, const int32_t *tets, int64_t m,
+                      const double *P, int32_t *elem, double *lam_out)
+{
+    int64_t outside = 0;
+    for (int64_t b = 0; b < m; ++b) {
+        int found = 0;
+        for (int64_t e = 0; e < E && !found; ++e) {
+            double lam[4];
+            or_tet_barycentric(X, tets + 4 * e, P + 3 * b, lam);
+            if (lam[0] >= -1e-12 && lam[1] >= -1e-12 && lam[2] >= -1e-12 && lam[3] >= -1e-12) {
+                elem[b] = (int32_t)e;
+                lam_out[3 * b] = lam[1];
+                lam_out[3 * b + 1] = lam[2];
+                lam_out[3 * b + 2] = lam[3];
+                found = 1;
+            }
+        }
+        if (!found) {
+            elem[b] = -1;
+            lam_out[3 * b] = lam_out[3 * b + 1] = lam_out[3 * b + 2] = 0.0;
+            ++outside;
+        }
+    }
+    return outside;
+}
+
+/* Interpolation u_B = sum_a N_a(lam_B) v_a (Eq. nodal_solid_velo) on
+ * tetrahedra, N_0 = 1 - lam_1 - lam_2 - lam_3, N_k = lam_k.                  */
+void or_tet_interp(const int32_t *tets, int64_t m, const int32_t *elem, const double *lam,
+                   const double *U, double *u)
+{
+    for (int64_t b = 0; b < m; ++b) {
+        u[3 * b] = u[3 * b + 1] = u[3 * b + 2] = 0.0;
+        if (elem[b] < 0) continue;
+        const int32_t *t = tets + 4 * (int64_t)elem[b];
+        const double l1 = lam[3 * b], l2 = lam[3 * b + 1], l3 = lam[3 * b + 2];
+        const double Nv[4] = {1.0 - l1 - l2 - l3, l1, l2, l3};
+        for (int a = 0; a < 4; ++a)
+            for (int i = 0; i < 3; ++i) u[3 * b + i] += Nv[a] * U[4 * (int64_t)t[a] + i];
+    }
+}
+
+/* Spreading F_a += w_B N_a(lam_B) lambda_B (Eq. fsi_constraint_matrix) on
+ * tetrahedra, velocity slots only; accumulate = 0 zeroes them first.        */
+void or_tet_spread(int64_t n, const int32_t *tets, int64_t m, const int32_t *elem,
+                   const double *lam, const double *lamv, const double *w, double *F,
+                   int accumulate)
+{
+    if (!accumulate)
+        for (int64_t a = 0; a < n; ++a) F[4 * a] = F[4 * a + 1] = F[4 * a + 2] = 0.0;
+    for (int64_t b = 0; b < m; ++b) {
+        if (elem[b] < 0) continue;
+        const int32_t *t = tets + 4 * (int64_t)elem[b];
+        const double l1 = lam[3 * b], l2 = lam[3 * b + 1], l3 = lam[3 * b + 2];
+        const double Nv[4] = {1.0 - l1 - l2 - l3, l1, l2, l3};
+        const double wb = w ? w[b] : 1.0;
+        for (int a = 0; a < 4; ++a)
+            for (int i = 0; i < 3; ++i) F[4 * (int64_t)t[a] + i] += wb * Nv[a] * lamv[3 * b + i];
     }
 }

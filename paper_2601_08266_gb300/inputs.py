@@ -155,3 +155,52 @@ def leaflet_hex_mesh(n_r: int, n_theta: int, n_x: int, seed: int, theta0: float 
         conn_all.append(np.stack([cc.ravel() for cc in corners], axis=1) + base)
         base += pts.shape[0]
     return np.concatenate(X_all), np.concatenate(conn_all).astype(np.int32)
+
+
+def tet_box_mesh(N, seed: int, perturb: float = 0.0, shuffle: bool = True, lo=(0.0, 0.0, 0.0),
+                 hi=(1.0, 1.0, 1.0)):
+    """Unstructured tetrahedral mesh of a box: the N^3 (or Nx x Ny x Nz) grid
+    split into 6 tetrahedra per cube along its main diagonal (Freudenthal-Kuhn
+    split, conforming across cubes); interior nodes moved by up to
+    perturb * h per axis; with shuffle, node numbers, element numbers and the
+    corner order of every element are permuted at random, so nothing about
+    the numbering is structured.  Returns X [n, 3] float64, tets [E, 4] int32."""
+    if isinstance(N, int):
+        N = (N, N, N)
+    Nx, Ny, Nz = N
+    g = rng(seed)
+    ax = [np.linspace(lo[d], hi[d], N[d] + 1) for d in range(3)]
+    Z, Y, Xc = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    X = np.stack([Xc.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    h = np.array([(hi[d] - lo[d]) / N[d] for d in range(3)])
+    if perturb:
+        inner = np.all((X > np.array(lo) + 1e-12) & (X < np.array(hi) - 1e-12), axis=1)
+        X[inner] += perturb * g.uniform(-1, 1, (int(inner.sum()), 3)) * h[None, :]
+
+    def nid(i, j, k):
+        return i + (Nx + 1) * (j + (Ny + 1) * k)
+
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    tets = []
+    for k in range(Nz):
+        for j in range(Ny):
+            for i in range(Nx):
+                for p in perms:
+                    c = [0, 0, 0]
+                    t = [nid(i, j, k)]
+                    for d in p:
+                        c[d] = 1
+                        t.append(nid(i + c[0], j + c[1], k + c[2]))
+                    tets.append(t)
+    tets = np.array(tets, dtype=np.int64)
+    if shuffle:
+        n = X.shape[0]
+        new_of_old = g.permutation(n)
+        Xs = np.empty_like(X)
+        Xs[new_of_old] = X
+        X = Xs
+        tets = new_of_old[tets]
+        tets = tets[g.permutation(len(tets))]
+        rot = g.integers(0, 4, len(tets))
+        tets = np.stack([np.roll(t, r) for t, r in zip(tets, rot)])
+    return X, tets.astype(np.int32)

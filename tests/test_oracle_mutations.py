@@ -36,8 +36,21 @@ MUTATIONS = {
     "mapped_metric_transposed": ("t += Ji[k][i] * Ji[k][j];", "t += Ji[i][k] * Ji[j][k];"),
     "mapped_det_dropped": ("st->detJ = det;", "st->detJ = 1.0;"),
     "mapped_locate_unsettled": ("if (!(last < 1e-12)) return 0;", ";"),
+    # tetrahedra: caught by the pins of tests/test_oracle_tet.py
+    "tet_quadrature_weight": ("gp_residual(&st, ph, 4, fabs(st.detJ) / 24.0, stab, Re);",
+                              "gp_residual(&st, ph, 4, fabs(st.detJ) / 6.0, stab, Re);"),
+    "tet_gradient_node0": ("dN[0][j] = -(Ji[0][j] + Ji[1][j] + Ji[2][j]);",
+                           "dN[0][j] = (Ji[0][j] + Ji[1][j] + Ji[2][j]);"),
+    "tet_quadrature_points_swapped": ("st->N[a] = (a == q) ? al : be;",
+                                      "st->N[a] = (a == q) ? be : al;"),
+    "tet_metric_transposed": ("s += Ji[k][i] * Ji[k][j];", "s += Ji[i][k] * Ji[j][k];"),
+    "tet_jacobian_weight": ("gp_jacobian(&st, ph, 4, fabs(st.detJ) / 24.0, xe, c_a, c_v, Je);",
+                            "gp_jacobian(&st, ph, 4, st.detJ / 24.0, xe, c_a, c_v, Je);"),
+    "tet_locate_lam0_ignored": ("if (lam[0] >= -1e-12 && lam[1] >= -1e-12",
+                                "if (1 && lam[1] >= -1e-12"),
 }
 MAPPED = {k for k in MUTATIONS if k.startswith("mapped_")}
+TET = {k for k in MUTATIONS if k.startswith("tet_")}
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
@@ -51,6 +64,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                            str(tmp_path / "fsi_oracle.c"), "-lm"])
     env = dict(os.environ, FSI_ORACLE_LIB=str(lib))
     files = (["tests/test_oracle_mapped.py"] if name in MAPPED
+             else ["tests/test_oracle_tet.py"] if name in TET
              else ["tests/test_oracle_vms.py", "tests/test_oracle_dlm.py"])
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         *files, "-k", "not manufactured and not quadratic"],
