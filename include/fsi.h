@@ -245,6 +245,64 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
 fsi_status fsi_mesh_set_coordinates(fsi_mesh *mesh, const double *X);
 
 /* ----------------------------------------------------------------------- */
+/* Unstructured tetrahedral background meshes: linear P1-P1 tetrahedra, the  */
+/* element family of the paper's valve fluid mesh (Sec. 4), with the same    */
+/* VMS weak form (Sec. 2.1), linearisation (Sec. 2.4) and coupling operators */
+/* (Sec. 2.3) as the structured grid.                                        */
+/*                                                                          */
+/* Discretisation: reference tetrahedron (0,0,0),(1,0,0),(0,1,0),(0,0,1),    */
+/* N_0 = 1 - xi_1 - xi_2 - xi_3, N_k = xi_k; J = [x1-x0, x2-x0, x3-x0];       */
+/* G = J^-T J^-1 (the metric of Sec. 2.1 with this parent domain); the      */
+/* symmetric 4-point quadrature rule of degree 2, weight |det J|/24 each.    */
+/* Elements may have either orientation.                                     */
+/* ----------------------------------------------------------------------- */
+typedef struct fsi_tetmesh fsi_tetmesh;
+
+/* Build a tetrahedral mesh on `device`, ordered on `cuda_stream`: X [n][3]
+ * FP64 node coordinates and tets [E][4] int32 node numbers, both device
+ * arrays (copied; the caller keeps ownership).  Builds the node -> element
+ * slot lists of the atomic-free assembly and a uniform bucket grid for point
+ * location (host work proportional to n + E); synchronises the stream.
+ * FSI_ERR_ARG for bad sizes, node numbers out of range, non-finite
+ * coordinates or invalid physics; FSI_ERR_OOM if device memory runs out.  */
+fsi_status fsi_tetmesh_create(int64_t n_nodes, const double *X, int64_t n_tets,
+                              const int32_t *tets, const fsi_physics *phys, int device,
+                              void *cuda_stream, fsi_tetmesh **out);
+void fsi_tetmesh_destroy(fsi_tetmesh *mesh);
+
+/* VMS residual and Jacobian apply on the tetrahedral mesh: the same
+ * arguments, layouts and precisions as fsi_residual / fsi_jacobian_apply
+ * (U, A, f, x, R, Jx [n][4] device arrays; f may be NULL).  Deterministic.  */
+fsi_status fsi_tet_residual(fsi_tetmesh *mesh, fsi_prec prec, const void *U, const void *A,
+                            const void *f, void *R);
+fsi_status fsi_tet_jacobian_apply(fsi_tetmesh *mesh, fsi_prec prec, const void *U,
+                                  const void *A, const void *f, const void *x, void *Jx);
+
+/* Point location (Sec. 3, Algorithm 1): for each of the m points P [m][3]
+ * (FP64 device array) the element elem [m] and the barycentric coordinates
+ * lam [m][3] = (lam_1, lam_2, lam_3) (lam_0 = 1 - their sum).  A point
+ * belongs to the lowest-numbered element whose four coordinates, computed in
+ * FP64 in the order e_k = x_k - x_0, d = P - x_0, D = e1.(e2 x e3),
+ * lam_1 = d.(e2 x e3)/D, lam_2 = e1.(d x e3)/D, lam_3 = e1.(e2 x d)/D,
+ * lam_0 = ((1 - lam_1) - lam_2) - lam_3, are all >= -1e-12; others get
+ * elem = -1, lam = 0.  cell_start [E+1] / perm [m] (both or neither; perm
+ * may be NULL when m = 0) receive the element -> points table (stable,
+ * outside points last).  n_outside
+ * (host, may be NULL) synchronises the stream.                             */
+fsi_status fsi_tet_locate(fsi_tetmesh *mesh, int64_t m, const double *P, int32_t *elem,
+                          double *lam, int32_t *cell_start, int32_t *perm, int64_t *n_outside);
+
+/* Interpolation u = C^T U (Eq. nodal_solid_velo) and spreading F = C w lambda
+ * (Eq. fsi_constraint_matrix) with the barycentric shape functions; the same
+ * arguments, precisions and semantics as fsi_dlm_interp / fsi_dlm_spread
+ * (lam in the working precision, FP64 for FSI_DF64).                       */
+fsi_status fsi_tet_interp(fsi_tetmesh *mesh, fsi_prec prec, int64_t m, const int32_t *elem,
+                          const void *lam, const void *U, void *u);
+fsi_status fsi_tet_spread(fsi_tetmesh *mesh, fsi_prec prec, int64_t m, const int32_t *elem,
+                          const void *lam, const int32_t *cell_start, const int32_t *perm,
+                          const void *lamv, const void *w, void *F, int accumulate);
+
+/* ----------------------------------------------------------------------- */
 /* One implicit step: the reduced FSI system of Sec. 2.4.                    */
 
 /* The state of one time step.  All arrays are DEVICE pointers, FP64.

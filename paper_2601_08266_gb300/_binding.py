@@ -134,6 +134,14 @@ _SIGS = {
     "fsi_solid_advance": ([_VP, _VP, _VP, _VP, _VP], _INT),
     "fsi_solid_positions": ([_VP, _VP, _VP], _INT),
     "fsi_mesh_set_coordinates": ([_VP, _VP], _INT),
+    "fsi_tetmesh_create": ([_I64, _VP, _I64, _VP, ctypes.POINTER(fsi_physics), _INT, _VP,
+                            ctypes.POINTER(_VP)], _INT),
+    "fsi_tetmesh_destroy": ([_VP], None),
+    "fsi_tet_residual": ([_VP, _INT, _VP, _VP, _VP, _VP], _INT),
+    "fsi_tet_jacobian_apply": ([_VP, _INT, _VP, _VP, _VP, _VP, _VP], _INT),
+    "fsi_tet_locate": ([_VP, _I64, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_I64)], _INT),
+    "fsi_tet_interp": ([_VP, _INT, _I64, _VP, _VP, _VP, _VP], _INT),
+    "fsi_tet_spread": ([_VP, _INT, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _INT], _INT),
     "fsi_interface_scaling": ([_VP, _VP, ctypes.c_double, _INT, _VP], _INT),
     "fsi_pressure_levels": ([_VP, ctypes.POINTER(ctypes.c_int32), _VP], _INT),
     "fsi_pressure_set_faces": ([_VP, ctypes.POINTER(ctypes.c_int32)], _INT),
@@ -314,6 +322,78 @@ def fsi_dlm_spread(mesh: Mesh, prec, elem, xi, cell_start, perm, lam, w, F, accu
     _check(lib().fsi_dlm_spread(mesh.handle, prec, m, _ptr(elem, torch.int32), _ptr(xi, dt),
                                 _ptr(cell_start, torch.int32), _ptr(perm, torch.int32),
                                 _ptr(lam, dt), _ptr(w, dt), _ptr(F, dt),
+                                1 if accumulate else 0))
+
+
+class TetMesh:
+    """Owner of an fsi_tetmesh handle: X [n, 3] float64 and tets [E, 4] int32
+    device tensors (copied by the library)."""
+
+    def __init__(self, X, tets, rho=1.0, mu=0.01, dt=1e-3, rho_inf=0.5, C_I=36.0, C_T=4.0,
+                 has_s=False, device=0, stream=None):
+        import torch
+        self.n_nodes, self.n_elems = int(X.shape[0]), int(tets.shape[0])
+        if tuple(X.shape) != (self.n_nodes, 3) or tuple(tets.shape) != (self.n_elems, 4):
+            raise ValueError("X must be [n, 3] and tets [E, 4]")
+        self.device = device
+        self.phys = fsi_physics(rho, mu, dt, rho_inf, C_I, C_T, 1 if has_s else 0, 0)
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        out = ctypes.c_void_p()
+        _check(lib().fsi_tetmesh_create(self.n_nodes, _ptr(X, torch.float64), self.n_elems,
+                                        _ptr(tets, torch.int32), ctypes.byref(self.phys), device,
+                                        ctypes.c_void_p(stream), ctypes.byref(out)))
+        self.handle = out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fsi_tetmesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fsi_tet_residual(mesh: TetMesh, prec, U, A, f, R):
+    dt = _prec_dtype(prec)
+    _check(lib().fsi_tet_residual(mesh.handle, prec, _ptr(U, dt), _ptr(A, dt), _ptr(f, dt),
+                                  _ptr(R, dt)))
+
+
+def fsi_tet_jacobian_apply(mesh: TetMesh, prec, U, A, f, x, Jx):
+    dt = _prec_dtype(prec)
+    _check(lib().fsi_tet_jacobian_apply(mesh.handle, prec, _ptr(U, dt), _ptr(A, dt),
+                                        _ptr(f, dt), _ptr(x, dt), _ptr(Jx, dt)))
+
+
+def fsi_tet_locate(mesh: TetMesh, P, elem, lam, cell_start=None, perm=None, want_outside=True):
+    import torch
+    m = 0 if P is None else P.shape[0]
+    nout = _I64(0)
+    _check(lib().fsi_tet_locate(mesh.handle, m, _ptr(P, torch.float64), _ptr(elem, torch.int32),
+                                _ptr(lam, torch.float64), _ptr(cell_start, torch.int32),
+                                _ptr(perm, torch.int32),
+                                ctypes.byref(nout) if want_outside else None))
+    return int(nout.value) if want_outside else None
+
+
+def fsi_tet_interp(mesh: TetMesh, prec, elem, lam, U, u):
+    import torch
+    dt = _prec_dtype(prec)
+    _check(lib().fsi_tet_interp(mesh.handle, prec, elem.shape[0], _ptr(elem, torch.int32),
+                                _ptr(lam, dt), _ptr(U, dt), _ptr(u, dt)))
+
+
+def fsi_tet_spread(mesh: TetMesh, prec, elem, lam, cell_start, perm, lamv, w, F, accumulate):
+    import torch
+    dt = _prec_dtype(prec)
+    m = elem.shape[0] if elem is not None else lamv.shape[0]
+    _check(lib().fsi_tet_spread(mesh.handle, prec, m, _ptr(elem, torch.int32), _ptr(lam, dt),
+                                _ptr(cell_start, torch.int32), _ptr(perm, torch.int32),
+                                _ptr(lamv, dt), _ptr(w, dt), _ptr(F, dt),
                                 1 if accumulate else 0))
 
 

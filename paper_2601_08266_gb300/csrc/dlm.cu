@@ -602,6 +602,30 @@ GridArgs grid_args_of(const fsi_grid &gr)
 }
 
 }  // namespace
+
+int64_t cell_table_scan_ints(int64_t E) { return (E + kScanTile - 1) / kScanTile; }
+
+fsi_status build_cell_table(cudaStream_t s, int64_t E, int64_t m, const int32_t *elem,
+                            int32_t *fill, int32_t *scan_tmp, int32_t *cell_start, int32_t *perm)
+{
+    const int64_t ntiles = cell_table_scan_ints(E);
+    scan_tiles_kernel<<<(int)ntiles, 1024, 0, s>>>(E, fill, cell_start, scan_tmp);
+    FSI_TRY(check_launch("scan tiles kernel"));
+    scan_totals_kernel<<<1, 1024, 0, s>>>(ntiles, scan_tmp);
+    FSI_TRY(check_launch("scan totals kernel"));
+    scan_add_kernel<<<(int)ntiles, 256, 0, s>>>(E, cell_start, scan_tmp);
+    FSI_TRY(check_launch("scan add kernel"));
+    if (m > 0) {
+        FSI_CUDA(cudaMemsetAsync(fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
+        scatter_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, E, elem, cell_start, fill, perm);
+        FSI_TRY(check_launch("scatter kernel"));
+        cell_sort_kernel<<<blocks_for((E + 32) / 32 * 32, 256, 152 * 64), 256, 0, s>>>(
+            E, m, cell_start, perm);
+        FSI_TRY(check_launch("cell sort kernel"));
+    }
+    return FSI_OK;
+}
+
 }  // namespace fsi
 
 using namespace fsi;
@@ -637,25 +661,8 @@ fsi_status fsi_locate(fsi_mesh *mesh, int64_t m, const double *X, int32_t *elem,
                                                          table ? mesh->hash_fill : nullptr, nout);
         FSI_TRY(check_launch("locate kernel"));
     }
-    if (table) {
-        const int64_t ntiles = (E + kScanTile - 1) / kScanTile;
-        scan_tiles_kernel<<<(int)ntiles, 1024, 0, s>>>(E, mesh->hash_fill, cell_start,
-                                                       mesh->scan_tmp);
-        FSI_TRY(check_launch("scan tiles kernel"));
-        scan_totals_kernel<<<1, 1024, 0, s>>>(ntiles, mesh->scan_tmp);
-        FSI_TRY(check_launch("scan totals kernel"));
-        scan_add_kernel<<<(int)ntiles, 256, 0, s>>>(E, cell_start, mesh->scan_tmp);
-        FSI_TRY(check_launch("scan add kernel"));
-        if (m > 0) {
-            FSI_CUDA(cudaMemsetAsync(mesh->hash_fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
-            scatter_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, E, elem, cell_start,
-                                                              mesh->hash_fill, perm);
-            FSI_TRY(check_launch("scatter kernel"));
-            cell_sort_kernel<<<blocks_for((E + 32) / 32 * 32, 256, 152 * 64), 256, 0, s>>>(
-                E, m, cell_start, perm);
-            FSI_TRY(check_launch("cell sort kernel"));
-        }
-    }
+    if (table)
+        FSI_TRY(build_cell_table(s, E, m, elem, mesh->hash_fill, mesh->scan_tmp, cell_start, perm));
     if (n_outside || strict) {
         unsigned long long h = 0;
         FSI_CUDA(cudaMemcpyAsync(&h, nout, sizeof h, cudaMemcpyDeviceToHost, s), "memcpy");

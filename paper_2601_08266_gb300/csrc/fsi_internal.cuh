@@ -125,4 +125,12 @@ fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A
 fsi_status vms_jacobian(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
                         const void *f, const void *x, void *Jx);
 
+// cell -> points table (dlm.cu): from per-cell counts in fill[0..E), an
+// exclusive scan into cell_start[E+1], a scatter of the points into perm and
+// a per-cell sort by point index (outside points last).  fill is reused as
+// cursors; scan_tmp holds cell_table_scan_ints(E) ints.
+int64_t cell_table_scan_ints(int64_t E);
+fsi_status build_cell_table(cudaStream_t s, int64_t E, int64_t m, const int32_t *elem,
+                            int32_t *fill, int32_t *scan_tmp, int32_t *cell_start, int32_t *perm);
+
 }  // namespace fsi

@@ -358,6 +358,67 @@ __device__ __forceinline__ void to_phys(const Geo<T> &geo, VG<T> &e)
     e.gz = a * geo.Ji[0][2] + b * geo.Ji[1][2] + c * geo.Ji[2][2];
 }
 
+// Test-function coefficients of the residual at one quadrature point: X
+// multiplies N_A, Y[c][j] multiplies dN_A/dx_j for residual component c.
+template <typename T>
+__device__ __forceinline__ void gp_residual_terms(const VmsArgs<T> &P, const GP<T> &q, T (&X)[4],
+                                                  T (&Y)[4][3])
+{
+    for (int i = 0; i < 3; ++i) {
+        X[i] = P.rho * (q.a[i] + q.conv[i] - q.f[i] +
+                        dot3_t(q.up[0], q.gv[i][0], q.up[1], q.gv[i][1], q.up[2], q.gv[i][2]));
+        for (int j = 0; j < 3; ++j)
+            Y[i][j] = dot2_t(P.mu, q.gv[i][j] + q.gv[j][i], -P.rho * (q.v[j] + q.up[j]), q.up[i]);
+        Y[i][i] -= q.p + q.pp;
+    }
+    X[3] = q.rC;
+    for (int j = 0; j < 3; ++j) Y[3][j] = -q.up[j];
+}
+
+// v . G dv with the full metric of a Gauss point
+template <typename T>
+__device__ __forceinline__ T vGdv_full(const Geo<T> &geo, const GP<T> &q, const T (&dv)[3])
+{
+    T vGdv = T(0);
+    for (int i = 0; i < 3; ++i)
+        vGdv += q.v[i] * (geo.G[i][0] * dv[0] + geo.G[i][1] * dv[1] + geo.G[i][2] * dv[2]);
+    return vGdv;
+}
+
+// The same coefficients of the Jacobian in the direction (dv, grad dv, da, dp,
+// grad dp) (physical gradients, chain factors applied); vGdv = v . G dv and
+// q0 = C_T/dt^2 + C_I nu^2 G:G at this point.
+template <typename T>
+__device__ __forceinline__ void gp_jacobian_terms(const VmsArgs<T> &P, const GP<T> &q,
+                                                  const T (&dv)[3], const T (&dgv)[3][3],
+                                                  const T (&da)[3], T dp, const T (&dgp)[3],
+                                                  T vGdv, T q0, T (&X)[4], T (&Y)[4][3])
+{
+    T dconv[3], drM[3], dup[3];
+    for (int i = 0; i < 3; ++i) {
+        dconv[i] = dot3_t(dv[0], q.gv[i][0], dv[1], q.gv[i][1], dv[2], q.gv[i][2]) +
+                   dot3_t(q.v[0], dgv[i][0], q.v[1], dgv[i][1], q.v[2], dgv[i][2]);
+        drM[i] = fma_t(P.rho, da[i] + dconv[i], dgp[i]);
+    }
+    const T drC = dgv[0][0] + dgv[1][1] + dgv[2][2];
+    const T dtauM = -q.tauM * q.tauM * q.tauM * q.s * vGdv;
+    // d tau_C = -tau_C d tau_M / tau_M, 1/tau_M = s (q0 + vGv) tau_M
+    const T dtauC = -q.tauC * dtauM * (q.s * (q0 + q.vGv) * q.tauM);
+    for (int i = 0; i < 3; ++i) dup[i] = -dot2_t(dtauM, q.rM[i], q.tauM, drM[i]) * P.inv_rho;
+    const T dpp = -P.rho * dot2_t(dtauC, q.rC, q.tauC, drC);
+    for (int i = 0; i < 3; ++i) {
+        X[i] = P.rho * (da[i] + dconv[i] +
+                        dot3_t(dup[0], q.gv[i][0], dup[1], q.gv[i][1], dup[2], q.gv[i][2]) +
+                        dot3_t(q.up[0], dgv[i][0], q.up[1], dgv[i][1], q.up[2], dgv[i][2]));
+        for (int j = 0; j < 3; ++j)
+            Y[i][j] = fma_t(P.mu, dgv[i][j] + dgv[j][i],
+                            -P.rho * dot2_t(dv[j] + dup[j], q.up[i], q.v[j] + q.up[j], dup[i]));
+        Y[i][i] -= dp + dpp;
+    }
+    X[3] = drC;
+    for (int j = 0; j < 3; ++j) Y[3][j] = -dup[j];
+}
+
 // One brick of elements: element contributions into rel (shared memory,
 // [bx*by*bz][8] node records), then the brick's node block into P.blocks.
 template <typename T, bool JAC, bool MAPPED = false>
@@ -464,17 +525,7 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
 
         T X[4], Y[4][3];
         if (!JAC) {
-            for (int i = 0; i < 3; ++i) {
-                X[i] = P.rho * (q.a[i] + q.conv[i] - q.f[i] +
-                                dot3_t(q.up[0], q.gv[i][0], q.up[1], q.gv[i][1], q.up[2],
-                                       q.gv[i][2]));
-                for (int j = 0; j < 3; ++j)
-                    Y[i][j] = dot2_t(P.mu, q.gv[i][j] + q.gv[j][i], -P.rho * (q.v[j] + q.up[j]),
-                                     q.up[i]);
-                Y[i][i] -= q.p + q.pp;
-            }
-            X[3] = q.rC;
-            for (int j = 0; j < 3; ++j) Y[3][j] = -q.up[j];
+            gp_residual_terms(P, q, X, Y);
         } else {
             vec4<T> xx = valid ? load_c<T>(P.x + node) : zero;
             T dv[3], dgv[3][3], da[3], dp, dgp[3];
@@ -496,41 +547,16 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
                 dgv[2][0] = cv * e2.gx; dgv[2][1] = cv * e2.gy; dgv[2][2] = cv * e2.gz;
                 dp = e3.v; dgp[0] = e3.gx; dgp[1] = e3.gy; dgp[2] = e3.gz;
             }
-            T dconv[3], drM[3], dup[3];
-            for (int i = 0; i < 3; ++i) {
-                dconv[i] = dot3_t(dv[0], q.gv[i][0], dv[1], q.gv[i][1], dv[2], q.gv[i][2]) +
-                           dot3_t(q.v[0], dgv[i][0], q.v[1], dgv[i][1], q.v[2], dgv[i][2]);
-                drM[i] = fma_t(P.rho, da[i] + dconv[i], dgp[i]);
-            }
-            const T drC = dgv[0][0] + dgv[1][1] + dgv[2][2];
             // d tau_M = -1/2 tau_M^3 s dQ with dQ = 2 v.G dv
-            T vGdv;
+            T vGdv, q0;
             if constexpr (MAPPED) {
-                vGdv = T(0);
-                for (int i = 0; i < 3; ++i)
-                    vGdv += q.v[i] * (geo.G[i][0] * dv[0] + geo.G[i][1] * dv[1] + geo.G[i][2] * dv[2]);
+                vGdv = vGdv_full(geo, q, dv);
+                q0 = geo.q0;
             } else {
                 vGdv = dot3_t(P.G0 * q.v[0], dv[0], P.G1 * q.v[1], dv[1], P.G2 * q.v[2], dv[2]);
+                q0 = P.q0;
             }
-            const T dtauM = -q.tauM * q.tauM * q.tauM * q.s * vGdv;
-            // d tau_C = -tau_C d tau_M / tau_M, 1/tau_M = s (q0 + vGv) tau_M
-            T q0 = P.q0;
-            if constexpr (MAPPED) q0 = geo.q0;
-            const T dtauC = -q.tauC * dtauM * (q.s * (q0 + q.vGv) * q.tauM);
-            for (int i = 0; i < 3; ++i) dup[i] = -dot2_t(dtauM, q.rM[i], q.tauM, drM[i]) * P.inv_rho;
-            const T dpp = -P.rho * dot2_t(dtauC, q.rC, q.tauC, drC);
-            for (int i = 0; i < 3; ++i) {
-                X[i] = P.rho * (da[i] + dconv[i] +
-                                dot3_t(dup[0], q.gv[i][0], dup[1], q.gv[i][1], dup[2], q.gv[i][2]) +
-                                dot3_t(q.up[0], dgv[i][0], q.up[1], dgv[i][1], q.up[2], dgv[i][2]));
-                for (int j = 0; j < 3; ++j)
-                    Y[i][j] = fma_t(P.mu, dgv[i][j] + dgv[j][i],
-                                    -P.rho * dot2_t(dv[j] + dup[j], q.up[i], q.v[j] + q.up[j],
-                                                    dup[i]));
-                Y[i][i] -= dp + dpp;
-            }
-            X[3] = drC;
-            for (int j = 0; j < 3; ++j) Y[3][j] = -dup[j];
+            gp_jacobian_terms(P, q, dv, dgv, da, dp, dgp, vGdv, q0, X, Y);
         }
         vec4<T> r;
         if constexpr (MAPPED) {
