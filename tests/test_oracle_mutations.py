@@ -13,14 +13,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 MUTATIONS = {
     "cross_term_sign": ("t += NA * rho * up[j] * st.gv[i][j];",
                         "t -= NA * rho * up[j] * st.gv[i][j];"),
-    "convection_transposed": ("conv[i] += st.v[j] * st.gv[i][j];\n            rM[i]",
-                              "conv[i] += st.v[j] * st.gv[j][i];\n            rM[i]"),
+    "convection_transposed": ("conv[i] += st.v[j] * st.gv[i][j];\n        rM[i]",
+                              "conv[i] += st.v[j] * st.gv[j][i];\n        rM[i]"),
     "supg_sign": ("t -= rho * vgradN * up[i];", "t += rho * vgradN * up[i];"),
     "lsic_dropped": ("t -= dNA[i] * pp;", ";"),
     "reynolds_index": ("t -= rho * dNA[j] * up[i] * up[j];",
                        "t -= rho * dNA[i] * up[j] * up[j];"),
-    "pspg_sign": ("for (int j = 0; j < 3; ++j) c -= dNA[j] * up[j];\n            Re",
-                  "for (int j = 0; j < 3; ++j) c += dNA[j] * up[j];\n            Re"),
+    "pspg_sign": ("for (int j = 0; j < 3; ++j) c -= dNA[j] * up[j];\n        Re",
+                  "for (int j = 0; j < 3; ++j) c += dNA[j] * up[j];\n        Re"),
     "viscous_not_symmetric": ("t += dNA[j] * mu * (st.gv[i][j] + st.gv[j][i]);",
                               "t += dNA[j] * mu * (st.gv[i][j] + st.gv[i][j]);"),
     "tau_time_term_dropped": ("sqrt(s * (ct_dt2 + vGv", "sqrt(s * (0.0 * ct_dt2 + vGv"),
