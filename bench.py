@@ -490,6 +490,8 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
             extras["solid"] = solid_section(args, dev, stream2)
         if "mapped" in sections:
             extras["mapped"] = mapped_section(args, dev, stream2)
+        if "tet" in sections:
+            extras["tet"] = tet_section(args, dev, stream2)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
@@ -1014,6 +1016,83 @@ def mapped_section(args, dev, stream):
     return out
 
 
+# ------------------------------------------------------------------ tetrahedral meshes
+def tet_section(args, dev, stream):
+    """Unstructured tetrahedral meshes: the 64^3 grid split into 1,572,864
+    linear tetrahedra (nodes moved by up to 0.2 h, node and element numbers
+    shuffled), the same 274,625 nodes as the 64^3 step.  VMS residual and
+    Jacobian apply in the three precisions, location of the 200k leaflet
+    points, interpolation and spreading."""
+    import torch
+    import paper_2601_08266_gb300 as fsi
+    from paper_2601_08266_gb300 import inputs
+    N = 64
+    X, Tt = inputs.tet_box_mesh(N, seed=SEED + 90, perturb=0.2)
+    with torch.cuda.stream(stream):
+        Xd, Td = torch.as_tensor(X, device=dev), torch.as_tensor(Tt, device=dev)
+    stream.synchronize()
+    t0 = time.perf_counter()
+    mesh = fsi.TetMesh(Xd, Td, rho=1.0, mu=1e-3, dt=1e-3, rho_inf=0.5, device=dev.index,
+                       stream=stream.cuda_stream)
+    create_s = time.perf_counter() - t0
+    n, E = mesh.n_nodes, mesh.n_elems
+    out = {"elements": E, "nodes": n, "dofs": 4 * n, "mesh": "64^3 cubes x 6 tetrahedra, "
+           "interior nodes moved by up to 0.2 h, numbering shuffled", "create_seconds": create_s}
+    g = torch.Generator(device=dev).manual_seed(SEED + 91)
+    with torch.cuda.stream(stream):
+        U = 0.5 * torch.randn((n, 4), dtype=torch.float64, device=dev, generator=g)
+        A = 0.5 * torch.randn((n, 4), dtype=torch.float64, device=dev, generator=g)
+        x = torch.randn((n, 4), dtype=torch.float64, device=dev, generator=g)
+        R = torch.empty_like(U)
+        U32, A32, x32, R32 = U.float(), A.float(), x.float(), R.float()
+
+    def timeit(fn, reps=10):
+        for _ in range(3):
+            fn()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    cases = {
+        "residual_f32": lambda: fsi.fsi_tet_residual(mesh, fsi.FSI_F32, U32, A32, None, R32),
+        "jacobian_f32": lambda: fsi.fsi_tet_jacobian_apply(mesh, fsi.FSI_F32, U32, A32, None, x32,
+                                                           R32),
+        "residual_df64": lambda: fsi.fsi_tet_residual(mesh, fsi.FSI_DF64, U, A, None, R),
+        "jacobian_df64": lambda: fsi.fsi_tet_jacobian_apply(mesh, fsi.FSI_DF64, U, A, None, x, R),
+        "residual_f64": lambda: fsi.fsi_tet_residual(mesh, fsi.FSI_F64, U, A, None, R),
+        "jacobian_f64": lambda: fsi.fsi_tet_jacobian_apply(mesh, fsi.FSI_F64, U, A, None, x, R),
+    }
+    out["vms_kernels"] = {}
+    for k, f in cases.items():
+        ms = timeit(f)
+        out["vms_kernels"][k] = {"ms": ms, "gdof_s": 4 * n / (ms * 1e-3) / 1e9,
+                                 "elements_per_s": E / (ms * 1e-3)}
+    m = M_POINTS
+    with torch.cuda.stream(stream):
+        P = torch.as_tensor(inputs.leaflet_points(m, seed=SEED + 92), device=dev)
+        e = torch.empty(m, dtype=torch.int32, device=dev)
+        lam = torch.empty((m, 3), dtype=torch.float64, device=dev)
+        cs = torch.empty(E + 1, dtype=torch.int32, device=dev)
+        pm = torch.empty(m, dtype=torch.int32, device=dev)
+        lv = torch.randn((m, 3), dtype=torch.float64, device=dev, generator=g)
+        u = torch.empty((m, 3), dtype=torch.float64, device=dev)
+        F = torch.zeros((n, 4), dtype=torch.float64, device=dev)
+    nout = fsi.fsi_tet_locate(mesh, P, e, lam, cs, pm)
+    out["points"] = {"m": m, "outside": nout}
+    out["locate_ms"] = timeit(lambda: fsi.fsi_tet_locate(mesh, P, e, lam, cs, pm,
+                                                         want_outside=False))
+    out["interp_df64_ms"] = timeit(lambda: fsi.fsi_tet_interp(mesh, fsi.FSI_DF64, e, lam, U, u))
+    out["spread_df64_ms"] = timeit(lambda: fsi.fsi_tet_spread(mesh, fsi.FSI_DF64, e, lam, cs, pm,
+                                                              lv, None, F, False))
+    mesh.close()
+    return out
+
+
 # ------------------------------------------------------------------ MLP inference
 def mlp_section(args, dev, stream, W):
     """Per-node inference of the initial-guess network over whole grids: the
@@ -1090,7 +1169,7 @@ def main():
     ap.add_argument("--points", type=int, default=M_POINTS, help="solid points (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip Newton, batch and MLP sections")
-    ap.add_argument("--sections", default="newton,batch,mlp,solid,mapped",
+    ap.add_argument("--sections", default="newton,batch,mlp,solid,mapped,tet",
                     help="comma-separated extra sections to run")
     ap.add_argument("--newton-grid", type=int, default=128)
     ap.add_argument("--newton-points", type=int, default=1_000_000)

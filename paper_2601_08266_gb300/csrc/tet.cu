@@ -22,8 +22,9 @@
 // Location.  A uniform bucket grid over the mesh's bounding box lists, in
 // increasing element order, the elements whose (padded) bounding box meets
 // each bucket.  A point tests the candidates of its bucket in that order:
-// an FP32 barycentric test discards elements it is clearly outside of, and
-// the FP64 barycentric coordinates, evaluated with round-to-nearest
+// an FP32 barycentric test discards elements it is clearly outside of (and
+// stops the scan at one it is almost surely inside of), and the FP64
+// barycentric coordinates, evaluated with round-to-nearest
 // operations in the same order as the definition (no contraction), decide:
 // the first element whose four coordinates are all >= -1e-12 holds the
 // point.  That is the first element in element order, as a search over all
@@ -315,11 +316,11 @@ __device__ __forceinline__ void barycentric64(const double4 &x0, const double4 &
     lam[0] = __dsub_rn(__dsub_rn(__dsub_rn(1.0, l1), l2), l3);
 }
 
-// FP32 screen: false only where the point is clearly outside (some
-// barycentric coordinate below -1e-2)
-__device__ __forceinline__ bool maybe_inside32(const float4 &x0, const float4 &x1,
-                                               const float4 &x2, const float4 &x3,
-                                               const float P[3])
+// FP32 screen: 0 where the point is clearly outside (some barycentric
+// coordinate below -1e-2), 2 where it is almost surely inside (all above
+// -1e-5), 1 in between
+__device__ __forceinline__ int screen32(const float4 &x0, const float4 &x1, const float4 &x2,
+                                        const float4 &x3, const float P[3])
 {
     const float e1[3] = {x1.x - x0.x, x1.y - x0.y, x1.z - x0.z};
     const float e2[3] = {x2.x - x0.x, x2.y - x0.y, x2.z - x0.z};
@@ -337,8 +338,9 @@ __device__ __forceinline__ bool maybe_inside32(const float4 &x0, const float4 &x
                 b2 = e2[0] * d[1] - e2[1] * d[0];
     const float l3 = (e1[0] * b0 + e1[1] * b1 + e1[2] * b2) * iD;
     const float l0 = 1.0f - l1 - l2 - l3;
-    const float tol = -1e-2f;
-    return !(l0 < tol || l1 < tol || l2 < tol || l3 < tol);  // NaN keeps the exact test
+    const float lmin = fminf(fminf(l0, l1), fminf(l2, l3));
+    if (lmin < -1e-2f) return 0;  // (a NaN falls through to the exact test)
+    return lmin >= -1e-5f ? 2 : 1;
 }
 
 __global__ void tet_locate_kernel(int64_t m, BucketArgs B, const double4 *__restrict__ X64,
@@ -364,15 +366,31 @@ __global__ void tet_locate_kernel(int64_t m, BucketArgs B, const double4 *__rest
             }
             const int64_t bk = bi[0] + (int64_t)B.nb[0] * (bi[1] + (int64_t)B.nb[1] * bi[2]);
             const float pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
-            for (int c = bstart[bk]; c < bstart[bk + 1]; ++c) {
-                const int e = btets[c];
-                const int4 t = tets[e];
-                if (!maybe_inside32(X32[t.x], X32[t.y], X32[t.z], X32[t.w], pf)) continue;
-                barycentric64(X64[t.x], X64[t.y], X64[t.z], X64[t.w], p, lam);
-                if (lam[0] >= -1e-12 && lam[1] >= -1e-12 && lam[2] >= -1e-12 &&
-                    lam[3] >= -1e-12) {
-                    found = e;
-                    break;
+            // the FP32 screen collects candidates in list order (up to four,
+            // or up to one it finds almost surely inside), then the exact FP64
+            // test runs on them in that order; the lanes of a warp reach the
+            // FP64 block together far more often than if each ran it at its
+            // own position in the list
+            int c = bstart[bk];
+            const int cend = bstart[bk + 1];
+            while (c < cend && found < 0) {
+                int cand[4], nc = 0;
+                bool likely = false;
+                for (; c < cend && nc < 4 && !likely; ++c) {
+                    const int e = btets[c];
+                    const int4 t = tets[e];
+                    const int sc = screen32(X32[t.x], X32[t.y], X32[t.z], X32[t.w], pf);
+                    if (sc > 0) cand[nc++] = e;
+                    likely = sc == 2;
+                }
+                for (int k = 0; k < nc; ++k) {
+                    const int4 t = tets[cand[k]];
+                    barycentric64(X64[t.x], X64[t.y], X64[t.z], X64[t.w], p, lam);
+                    if (lam[0] >= -1e-12 && lam[1] >= -1e-12 && lam[2] >= -1e-12 &&
+                        lam[3] >= -1e-12) {
+                        found = cand[k];
+                        break;
+                    }
                 }
             }
         }

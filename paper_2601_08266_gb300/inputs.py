@@ -177,22 +177,18 @@ def tet_box_mesh(N, seed: int, perturb: float = 0.0, shuffle: bool = True, lo=(0
         inner = np.all((X > np.array(lo) + 1e-12) & (X < np.array(hi) - 1e-12), axis=1)
         X[inner] += perturb * g.uniform(-1, 1, (int(inner.sum()), 3)) * h[None, :]
 
-    def nid(i, j, k):
-        return i + (Nx + 1) * (j + (Ny + 1) * k)
-
-    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
-    tets = []
-    for k in range(Nz):
-        for j in range(Ny):
-            for i in range(Nx):
-                for p in perms:
-                    c = [0, 0, 0]
-                    t = [nid(i, j, k)]
-                    for d in p:
-                        c[d] = 1
-                        t.append(nid(i + c[0], j + c[1], k + c[2]))
-                    tets.append(t)
-    tets = np.array(tets, dtype=np.int64)
+    perms = np.array([(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)])
+    # corner offsets of the 6 tetrahedra: the path 0 -> e_p0 -> e_p0 + e_p1 -> (1,1,1)
+    off = np.zeros((6, 4, 3), dtype=np.int64)
+    for t, p in enumerate(perms):
+        c = np.zeros(3, dtype=np.int64)
+        for s_, d in enumerate(p):
+            c[d] = 1
+            off[t, s_ + 1] = c
+    k, j, i = np.meshgrid(np.arange(Nz), np.arange(Ny), np.arange(Nx), indexing="ij")
+    base = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)           # cubes, x fastest
+    corner = base[:, None, None, :] + off[None, :, :, :]                   # [cubes, 6, 4, 3]
+    tets = (corner[..., 0] + (Nx + 1) * (corner[..., 1] + (Ny + 1) * corner[..., 2])).reshape(-1, 4)
     if shuffle:
         n = X.shape[0]
         new_of_old = g.permutation(n)
@@ -202,5 +198,5 @@ def tet_box_mesh(N, seed: int, perturb: float = 0.0, shuffle: bool = True, lo=(0
         tets = new_of_old[tets]
         tets = tets[g.permutation(len(tets))]
         rot = g.integers(0, 4, len(tets))
-        tets = np.stack([np.roll(t, r) for t, r in zip(tets, rot)])
+        tets = tets[np.arange(len(tets))[:, None], (np.arange(4)[None, :] - rot[:, None]) % 4]
     return X, tets.astype(np.int32)
