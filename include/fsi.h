@@ -302,6 +302,14 @@ fsi_status fsi_tet_spread(fsi_tetmesh *mesh, fsi_prec prec, int64_t m, const int
                           const void *lam, const int32_t *cell_start, const int32_t *perm,
                           const void *lamv, const void *w, void *F, int accumulate);
 
+/* Self-test of the bounded waits in the tensor-core kernels (no counterpart
+ * in the paper): one thread waits, with the same wait loop the kernels use,
+ * on an mbarrier whose expected arrival never comes.  The wait gives up after
+ * its poll limit (a few seconds at most), the kernel raises its error flag and
+ * returns, and the context stays usable.  *timed_out = 1 when that happened,
+ * *seconds = the kernel's time.  Synchronises the device.                   */
+fsi_status fsi_wait_selftest(int device, int *timed_out, double *seconds);
+
 /* ----------------------------------------------------------------------- */
 /* One implicit step: the reduced FSI system of Sec. 2.4.                    */
 

@@ -16,7 +16,7 @@ from ._binding import (FSI_BATCH_GRAPH, FSI_BATCH_PER_INSTANCE, FSI_BATCH_PERSIS
                        library_path, PRECOND_BLOCK_JACOBI, PRECOND_SCHUR, fsi_interface_scaling,
                        fsi_mesh_set_coordinates,
                        TetMesh, fsi_tet_residual, fsi_tet_jacobian_apply, fsi_tet_locate,
-                       fsi_tet_interp, fsi_tet_spread,
+                       fsi_tet_interp, fsi_tet_spread, fsi_wait_selftest,
                        Solid, fsi_solid_residual, fsi_solid_tangent_apply, fsi_solid_stage,
                        fsi_solid_advance, fsi_solid_positions,
                        fsi_pressure_levels, fsi_pressure_set_faces, fsi_pressure_apply, fsi_pressure_restrict,

@@ -134,6 +134,7 @@ _SIGS = {
     "fsi_solid_advance": ([_VP, _VP, _VP, _VP, _VP], _INT),
     "fsi_solid_positions": ([_VP, _VP, _VP], _INT),
     "fsi_mesh_set_coordinates": ([_VP, _VP], _INT),
+    "fsi_wait_selftest": ([_INT, ctypes.POINTER(_INT), ctypes.POINTER(ctypes.c_double)], _INT),
     "fsi_tetmesh_create": ([_I64, _VP, _I64, _VP, ctypes.POINTER(fsi_physics), _INT, _VP,
                             ctypes.POINTER(_VP)], _INT),
     "fsi_tetmesh_destroy": ([_VP], None),
@@ -395,6 +396,14 @@ def fsi_tet_spread(mesh: TetMesh, prec, elem, lam, cell_start, perm, lamv, w, F,
                                 _ptr(cell_start, torch.int32), _ptr(perm, torch.int32),
                                 _ptr(lamv, dt), _ptr(w, dt), _ptr(F, dt),
                                 1 if accumulate else 0))
+
+
+def fsi_wait_selftest(device=0):
+    """(timed_out, seconds) of the planted never-ending wait (see fsi.h)."""
+    t = _INT(0)
+    sec = ctypes.c_double(0.0)
+    _check(lib().fsi_wait_selftest(device, ctypes.byref(t), ctypes.byref(sec)))
+    return bool(t.value), sec.value
 
 
 def fsi_measure_fma_peak(device, prec):

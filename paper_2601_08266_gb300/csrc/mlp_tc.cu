@@ -446,6 +446,20 @@ __global__ void __launch_bounds__(128, 1) mlp_predict_tc_kernel(const TcArgs a)
     }
 }
 
+// Self-test of the bounded wait: one thread waits, with the production wait
+// loop, on an mbarrier that expects one arrival that never comes.  The wait
+// must run out; the kernel then raises the error flag and returns.
+__global__ void wait_selftest_kernel(int *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+        mbar_init(b, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!mbar_wait(b, 0)) atomicExch(err, 1);
+    }
+}
+
 }  // namespace
 
 size_t mlp_tc_packed_bytes() { return PACKED_BYTES; }
@@ -483,3 +497,31 @@ fsi_status mlp_predict_tc(cudaStream_t s, int device, const fsi_grid &g, int64_t
 }
 
 }  // namespace fsi
+
+extern "C" fsi_status fsi_wait_selftest(int device, int *timed_out, double *seconds)
+{
+    using namespace fsi;
+    if (!timed_out || !seconds) return set_error(FSI_ERR_ARG, "fsi_wait_selftest: NULL output");
+    FSI_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    int *err = nullptr;
+    FSI_CUDA(cudaMalloc(&err, sizeof(int)), "cudaMalloc");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaMemset(err, 0, sizeof(int));
+    cudaEventRecord(e0);
+    wait_selftest_kernel<<<1, 32>>>(err);
+    cudaEventRecord(e1);
+    fsi_status st = check_launch("wait self-test");
+    int h = 0;
+    if (st == FSI_OK) st = check_cuda(cudaMemcpy(&h, err, sizeof h, cudaMemcpyDeviceToHost),
+                                      "memcpy");
+    float ms = 0.0f;
+    if (st == FSI_OK) st = check_cuda(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(err);
+    *timed_out = h;
+    *seconds = ms * 1e-3;
+    return st;
+}
