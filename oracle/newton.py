@@ -70,8 +70,74 @@ def coupling_matrix(grid: core.Grid, elem, xi):
     return sp.csr_matrix((vals, (rows, cols)), shape=(3 * m, 4 * grid.n_nodes))
 
 
+def _is_tet(mesh):
+    from . import tet
+    return isinstance(mesh, tet.TetMesh)
+
+
+def tet_coupling_matrix(mesh, elem, lam):
+    """C^T on a tetrahedral mesh: (C^T V)_B = sum_a N_a(lam_B) V_a (velocity)."""
+    m = len(elem)
+    rows, cols, vals = [], [], []
+    for b in range(m):
+        e = int(elem[b])
+        if e < 0:
+            continue
+        l1, l2, l3 = lam[b]
+        Nv = (1.0 - l1 - l2 - l3, l1, l2, l3)
+        for a in range(4):
+            nd = int(mesh.tets[e, a])
+            for c in range(3):
+                rows.append(3 * b + c)
+                cols.append(4 * nd + c)
+                vals.append(Nv[a])
+    return sp.csr_matrix((vals, (rows, cols)), shape=(3 * m, 4 * mesh.n_nodes))
+
+
+# the operators of the step on either mesh kind: the structured grid (core)
+# or a tetrahedral mesh (tet)
+def _residual(mesh, phys, U, A, f):
+    if _is_tet(mesh):
+        from . import tet
+        return tet.residual(mesh, phys, U, A, f=f)
+    return core.residual(mesh, phys, U, A, f=f)
+
+
+def _assemble(mesh, phys, U, A, c_a, c_v, f):
+    if _is_tet(mesh):
+        from . import tet
+        return tet.assemble(mesh, tet.element_jacobian(mesh, phys, U, A, c_a, c_v, f=f))
+    return assemble(mesh, phys, U, A, c_a, c_v, f=f)
+
+
+def _interp(mesh, elem, xi, U):
+    if _is_tet(mesh):
+        from . import tet
+        return tet.interp(mesh, elem, xi, U)
+    return core.interp(mesh, elem, xi, U)
+
+
+def _spread(mesh, elem, xi, lam, w=None, F=None, accumulate=False):
+    if _is_tet(mesh):
+        from . import tet
+        return tet.spread(mesh, elem, xi, lam, w=w, F=F, accumulate=accumulate)
+    return core.spread(mesh, elem, xi, lam, w=w, F=F, accumulate=accumulate)
+
+
+def _coupling(mesh, elem, xi):
+    return tet_coupling_matrix(mesh, elem, xi) if _is_tet(mesh) else coupling_matrix(mesh, elem, xi)
+
+
+def _locate(mesh, X):
+    if _is_tet(mesh):
+        from . import tet
+        return tet.locate(mesh, X)
+    return core.locate(mesh, X)
+
+
 class Problem:
-    """One implicit step: unknown y = [Vdot_{n+1} | P_{n+1}] per node."""
+    """One implicit step: unknown y = [Vdot_{n+1} | P_{n+1}] per node, on a
+    structured grid (core.Grid) or a tetrahedral mesh (tet.TetMesh)."""
 
     def __init__(self, grid, phys, Vn, An, f=None, s=None, mask=None, yD=None,
                  points=None, solid=None, body=None):
@@ -89,7 +155,7 @@ class Problem:
         self.body = body
         if body is not None:
             x_n = body["mesh"].X + body["u"]
-            e, xi, nout = core.locate(grid, x_n)
+            e, xi, nout = _locate(grid, x_n)
             assert nout == 0, "solid nodes must lie inside the fluid grid"
             self.body_points = (e, xi)
 
@@ -121,23 +187,22 @@ class Problem:
 
     def residual(self, y):
         U, A = self.stage(y)
-        R = core.residual(self.grid, self.phys, U, A, f=self.f)
+        R = _residual(self.grid, self.phys, U, A, self.f)
         if self.points is not None:
             elem, xi, w = self.points
             drho = self.solid.get("drho", 0.5)
             k = self.solid.get("k", 0.0)
             gvec = np.asarray(self.solid.get("g", (0.0, 0.0, 0.0)))
-            a = core.interp(self.grid, elem, xi, y)
+            a = _interp(self.grid, elem, xi, y)
             V1 = np.zeros_like(y)
             V1[:, :3] = timeint.velocity_next(y, self.Vn, self.An, self.dt, self.rho_inf)
-            dx = self.dt * core.interp(self.grid, elem, xi, V1)
+            dx = self.dt * _interp(self.grid, elem, xi, V1)
             rs = drho * (a - gvec[None, :]) + k * dx
-            R = core.spread(self.grid, elem, xi, rs, w=w, F=R, accumulate=True)
+            R = _spread(self.grid, elem, xi, rs, w=w, F=R, accumulate=True)
         if self.body is not None:
             elem, xi = self.body_points
-            a_next = core.interp(self.grid, elem, xi, y)         # uddot_{n+1} = C^T Vdot_{n+1}
-            R = core.spread(self.grid, elem, xi, self.body_residual(a_next), F=R,
-                            accumulate=True)
+            a_next = _interp(self.grid, elem, xi, y)             # uddot_{n+1} = C^T Vdot_{n+1}
+            R = _spread(self.grid, elem, xi, self.body_residual(a_next), F=R, accumulate=True)
         if self.mask is not None:
             R = R.copy()
             R[self.mask] = (y - self.yD)[self.mask]
@@ -145,20 +210,20 @@ class Problem:
 
     def jacobian(self, y):
         U, A = self.stage(y)
-        J = assemble(self.grid, self.phys, U, A, self.c_a, self.c_v, f=self.f)
+        J = _assemble(self.grid, self.phys, U, A, self.c_a, self.c_v, self.f)
         if self.points is not None:
             elem, xi, w = self.points
             drho = self.solid.get("drho", 0.5)
             k = self.solid.get("k", 0.0)
             _, _, gamma = timeint.alphas(self.rho_inf)
-            Ct = coupling_matrix(self.grid, elem, xi)
+            Ct = _coupling(self.grid, elem, xi)
             wv = np.ones(len(elem)) if w is None else np.asarray(w)
             D = sp.diags(np.repeat(wv * (drho + k * gamma * self.dt ** 2), 3))
             J = J + (Ct.T @ D @ Ct)
         if self.body is not None:
             elem, xi = self.body_points
-            Ct = coupling_matrix(self.grid, elem, xi)
-            a_next = core.interp(self.grid, elem, xi, y)
+            Ct = _coupling(self.grid, elem, xi)
+            a_next = _interp(self.grid, elem, xi, y)
             J = J + Ct.T @ sp.csr_matrix(self.body_tangent(a_next)) @ Ct
         if self.mask is not None:
             J = J.tolil()
