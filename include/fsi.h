@@ -270,7 +270,23 @@ fsi_status fsi_tetmesh_create(int64_t n_nodes, const double *X, int64_t n_tets,
                               void *cuda_stream, fsi_tetmesh **out);
 void fsi_tetmesh_destroy(fsi_tetmesh *mesh);
 
-/* VMS residual and Jacobian apply on the tetrahedral mesh: the same
+/* The implicit step on a tetrahedral mesh: an fsi_mesh handle backed by a
+ * tetrahedral mesh (same arguments as fsi_tetmesh_create).  On it
+ * fsi_residual, fsi_jacobian_apply, fsi_stage, fsi_advance_history,
+ * fsi_locate (xi = barycentric lam), fsi_dlm_interp, fsi_dlm_spread,
+ * fsi_coupled_residual, fsi_coupled_jacobian_apply, fsi_block_diagonal and
+ * fsi_newton_step act as on the structured grid (cell_start has n_tets + 1
+ * entries).  The nodal diagonal blocks are probed with a distance-2 node
+ * colouring built at creation (no two nodes of one element share a colour),
+ * so fsi_newton_step needs the block-Jacobi preconditioner here; the Schur
+ * preconditioner, the interface band, mapped coordinates, brick shapes, the
+ * learned guess (stencil features) and the batched ensemble need a
+ * structured grid and return FSI_ERR_ARG on this handle.                   */
+fsi_status fsi_mesh_create_tet(int64_t n_nodes, const double *X, int64_t n_tets,
+                               const int32_t *tets, const fsi_physics *phys, int device,
+                               void *cuda_stream, fsi_mesh **out);
+
+/* VMS residual and Jacobian apply on the tetrahedral mesh:/* VMS residual and Jacobian apply on the tetrahedral mesh: the same
  * arguments, layouts and precisions as fsi_residual / fsi_jacobian_apply
  * (U, A, f, x, R, Jx [n][4] device arrays; f may be NULL).  Deterministic.  */
 fsi_status fsi_tet_residual(fsi_tetmesh *mesh, fsi_prec prec, const void *U, const void *A,

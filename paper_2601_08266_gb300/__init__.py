@@ -15,7 +15,7 @@ from ._binding import (FSI_BATCH_GRAPH, FSI_BATCH_PER_INSTANCE, FSI_BATCH_PERSIS
                        fsi_locate_noalloc, fsi_newton_step, fsi_residual, fsi_stage, lib,
                        library_path, PRECOND_BLOCK_JACOBI, PRECOND_SCHUR, fsi_interface_scaling,
                        fsi_mesh_set_coordinates,
-                       TetMesh, fsi_tet_residual, fsi_tet_jacobian_apply, fsi_tet_locate,
+                       TetMesh, MeshTet, fsi_tet_residual, fsi_tet_jacobian_apply, fsi_tet_locate,
                        fsi_tet_interp, fsi_tet_spread, fsi_wait_selftest,
                        Solid, fsi_solid_residual, fsi_solid_tangent_apply, fsi_solid_stage,
                        fsi_solid_advance, fsi_solid_positions,

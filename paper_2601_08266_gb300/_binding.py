@@ -135,6 +135,8 @@ _SIGS = {
     "fsi_solid_positions": ([_VP, _VP, _VP], _INT),
     "fsi_mesh_set_coordinates": ([_VP, _VP], _INT),
     "fsi_wait_selftest": ([_INT, ctypes.POINTER(_INT), ctypes.POINTER(ctypes.c_double)], _INT),
+    "fsi_mesh_create_tet": ([_I64, _VP, _I64, _VP, ctypes.POINTER(fsi_physics), _INT, _VP,
+                             ctypes.POINTER(_VP)], _INT),
     "fsi_tetmesh_create": ([_I64, _VP, _I64, _VP, ctypes.POINTER(fsi_physics), _INT, _VP,
                             ctypes.POINTER(_VP)], _INT),
     "fsi_tetmesh_destroy": ([_VP], None),
@@ -356,6 +358,39 @@ class TetMesh:
             self.close()
         except Exception:
             pass
+
+
+class MeshTet(Mesh):
+    """An fsi_mesh handle backed by a tetrahedral mesh (fsi_mesh_create_tet):
+    the step's entry points (fsi_residual, fsi_locate, fsi_newton_step, ...)
+    accept it like a structured-grid Mesh.  X [n, 3] float64 and tets [E, 4]
+    int32 device tensors."""
+
+    def __init__(self, X, tets, rho=1.0, mu=0.01, dt=1e-3, rho_inf=0.5, C_I=36.0, C_T=4.0,
+                 has_s=False, device=0, stream=None):
+        import torch
+        self._n, self._E = int(X.shape[0]), int(tets.shape[0])
+        if tuple(X.shape) != (self._n, 3) or tuple(tets.shape) != (self._E, 4):
+            raise ValueError("X must be [n, 3] and tets [E, 4]")
+        self.N = None
+        self.device = device
+        self.phys = fsi_physics(rho, mu, dt, rho_inf, C_I, C_T, 1 if has_s else 0, 0)
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self._stream = stream
+        out = ctypes.c_void_p()
+        _check(lib().fsi_mesh_create_tet(self._n, _ptr(X, torch.float64), self._E,
+                                         _ptr(tets, torch.int32), ctypes.byref(self.phys), device,
+                                         ctypes.c_void_p(stream), ctypes.byref(out)))
+        self.handle = out
+
+    @property
+    def n_nodes(self):
+        return self._n
+
+    @property
+    def n_elems(self):
+        return self._E
 
 
 def fsi_tet_residual(mesh: TetMesh, prec, U, A, f, R):

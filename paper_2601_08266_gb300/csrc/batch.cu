@@ -383,7 +383,7 @@ fsi_status fsi_batch_create(fsi_mesh *const *meshes, const fsi_batch_item *items
     const int device = meshes[0] ? meshes[0]->device : -1;
     for (int i = 0; i < count; ++i) {
         if (!meshes[i]) return set_error(FSI_ERR_ARG, "mesh %d is NULL", i);
-        if (meshes[i]->coords64)
+        if (meshes[i]->coords64 || meshes[i]->tet)
             return set_error(FSI_ERR_ARG, "mesh %d: the batch runs uniform grids only", i);
         if (meshes[i]->device != device)
             return set_error(FSI_ERR_ARG, "all meshes of a batch must be on one device");

@@ -644,6 +644,16 @@ fsi_status fsi_locate(fsi_mesh *mesh, int64_t m, const double *X, int32_t *elem,
     if (cell_start != nullptr && perm == nullptr && m > 0)
         return set_error(FSI_ERR_ARG, "fsi_locate: cell_start given without perm");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    if (mesh->tet) {
+        int64_t h = 0;
+        FSI_TRY(fsi_tet_locate(mesh->tet, m, X, elem, xi, cell_start, perm,
+                               (n_outside || strict) ? &h : nullptr));
+        if (n_outside) *n_outside = h;
+        if (strict && h > 0)
+            return set_error(FSI_ERR_OUTSIDE, "fsi_locate: %lld points outside the mesh",
+                             (long long)h);
+        return FSI_OK;
+    }
     const int64_t E = mesh->n_elems;
     cudaStream_t s = mesh->stream;
     unsigned long long *nout = (unsigned long long *)mesh->dev_counters;
@@ -684,6 +694,7 @@ fsi_status fsi_dlm_interp(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
     if (m == 0) return FSI_OK;
     if (!elem || !xi || !U || !u) return set_error(FSI_ERR_ARG, "fsi_dlm_interp: NULL argument");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    if (mesh->tet) return fsi_tet_interp(mesh->tet, prec, m, elem, xi, U, u);
     GridArgs g = grid_args(mesh);
     if (prec == FSI_F64)
         interp_kernel<double><<<blocks_for(m, 256), 256, 0, mesh->stream>>>(
@@ -710,6 +721,9 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
     if (m > 0 && (!xi || !perm || !lam))
         return set_error(FSI_ERR_ARG, "fsi_dlm_spread: NULL xi, perm or lam");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    if (mesh->tet)
+        return fsi_tet_spread(mesh->tet, prec, m, elem, xi, cell_start, perm, lam, w, F,
+                              accumulate);
     GridArgs g = grid_args(mesh);
     // corner sums: 8 bytes per value for FP64 and double-float, 4 for FP32
     const size_t esz = prec == FSI_F32 ? sizeof(float) : sizeof(double);
@@ -745,6 +759,7 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
 fsi_status fsi_interface_scaling(fsi_mesh *mesh, const int32_t *cell_start, double s_band,
                                  int32_t layers, double *s)
 {
+    if (mesh) FSI_TRY(require_structured(mesh, "fsi_interface_scaling"));
     FSI_TRY(validate_mesh(mesh));
     if (!cell_start || !s) return set_error(FSI_ERR_ARG, "fsi_interface_scaling: NULL argument");
     if (!(s_band > 0.0) || !std::isfinite(s_band))

@@ -85,6 +85,9 @@ struct fsi_mesh {
     // mapped grid: node coordinates padded to [n][4], FP64 and FP32 copies
     // (null on the uniform grid)
     void *coords64, *coords32;
+    // unstructured tetrahedral mesh behind this handle (fsi_mesh_create_tet);
+    // null for the structured grid
+    fsi_tetmesh *tet;
 };
 
 namespace fsi {
@@ -124,6 +127,14 @@ fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A
                         const void *f, void *R);
 fsi_status vms_jacobian(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
                         const void *f, const void *x, void *Jx);
+
+// tetrahedral meshes (tet.cu): stream and physics follow the owning fsi_mesh;
+// a distance-2 node colouring (no two nodes of one element share a colour)
+// for probing the nodal diagonal blocks
+void tet_set_stream(fsi_tetmesh *t, cudaStream_t s);
+void tet_set_physics(fsi_tetmesh *t, const fsi_physics *p);
+const int32_t *tet_colors(const fsi_tetmesh *t, int *n_colors);
+fsi_status require_structured(const fsi_mesh *m, const char *what);
 
 // cell -> points table (dlm.cu): from per-cell counts in fill[0..E), an
 // exclusive scan into cell_start[E+1], a scatter of the points into perm and

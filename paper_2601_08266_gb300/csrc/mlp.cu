@@ -490,6 +490,7 @@ fsi_status fsi_mlp_features(fsi_mesh *mesh, const double *Vn, const double *y, c
                             const float *in_mean, const float *in_std, float *X)
 {
     FSI_TRY(validate_mesh(mesh));
+    FSI_TRY(require_structured(mesh, "fsi_mlp_features (3x3x3 stencil features)"));
     if (!Vn || !y || !d1 || !d2 || !in_mean || !in_std || !X)
         return set_error(FSI_ERR_ARG, "NULL argument");
     if (!idx) k = mesh->n_nodes;
@@ -508,6 +509,7 @@ fsi_status fsi_mlp_predict(fsi_mlp *h, fsi_mesh *mesh, const float *params, cons
                            double *y0)
 {
     FSI_TRY(validate_mesh(mesh));
+    FSI_TRY(require_structured(mesh, "fsi_mlp_predict (3x3x3 stencil features)"));
     if (!h) return set_error(FSI_ERR_ARG, "mlp handle is NULL");
     if (!params || !in_mean || !in_std || !out_mean || !out_std || !Vn || !y || !d1 || !d2 || !y0)
         return set_error(FSI_ERR_ARG, "NULL argument");
@@ -525,6 +527,7 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
                          fsi_guess_report *rep)
 {
     FSI_TRY(validate_mesh(mesh));
+    FSI_TRY(require_structured(mesh, "fsi_mlp_guess (3x3x3 stencil features)"));
     if (!h || !st || !st->y || !yn || !d1 || !d2 || !work || !rep)
         return set_error(FSI_ERR_ARG, "NULL argument");
     if (fallback != 0 && fallback != 1) return set_error(FSI_ERR_ARG, "fallback must be 0 or 1");

@@ -256,22 +256,30 @@ __device__ __forceinline__ int node_color(int node, int NX1, int NY1)
     return (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
 }
 
+// colours: the node's entry of `colors` when given (tetrahedral meshes), else
+// the parity colour of the structured grid
+__device__ __forceinline__ int probe_color(int node, int NX1, int NY1, const int32_t *colors)
+{
+    return colors ? colors[node] : node_color(node, NX1, NY1);
+}
+
 template <typename T>
-__global__ void probe_fill_kernel(int n, int NX1, int NY1, int color, int comp, T *x)
+__global__ void probe_fill_kernel(int n, int NX1, int NY1, const int32_t *colors, int color,
+                                  int comp, T *x)
 {
     GRID_STRIDE(node, n)
     {
-        const bool on = node_color((int)node, NX1, NY1) == color;
+        const bool on = probe_color((int)node, NX1, NY1, colors) == color;
         for (int c = 0; c < 4; ++c) x[4 * node + c] = (on && c == comp) ? T(1) : T(0);
     }
 }
 
 template <typename T>
-__global__ void probe_extract_kernel(int n, int NX1, int NY1, int color, int comp, const T *Jx,
-                                     T *blocks)
+__global__ void probe_extract_kernel(int n, int NX1, int NY1, const int32_t *colors, int color,
+                                     int comp, const T *Jx, T *blocks)
 {
     GRID_STRIDE(node, n)
-    if (node_color((int)node, NX1, NY1) == color)
+    if (probe_color((int)node, NX1, NY1, colors) == color)
         for (int r = 0; r < 4; ++r) blocks[16 * node + 4 * r + comp] = Jx[4 * node + r];
 }
 
@@ -626,13 +634,24 @@ fsi_status build_block_jacobi(fsi_mesh *mesh, const fsi_step_state *st, int prec
     T *px = (T *)W.z, *pj = (T *)W.w;
     // the Schur preconditioner needs only the 3x3 velocity blocks
     const int ncomp = precond == 1 ? 3 : 4;
-    for (int color = 0; color < 8; ++color)
+    // 8 parity colours on the structured grid; a distance-2 colouring on a
+    // tetrahedral mesh
+    int ncolors = 8;
+    const int32_t *colors = nullptr;
+    if (mesh->tet) {
+        if (precond == 1)
+            return set_error(FSI_ERR_ARG, "the Schur preconditioner needs a structured grid; "
+                                          "use the block-Jacobi preconditioner on a "
+                                          "tetrahedral mesh");
+        colors = tet_colors(mesh->tet, &ncolors);
+    }
+    for (int color = 0; color < ncolors; ++color)
         for (int comp = 0; comp < ncomp; ++comp) {
-            probe_fill_kernel<T><<<grid1d(n), 256, 0, s>>>(n, NX1, NY1, color, comp, px);
+            probe_fill_kernel<T><<<grid1d(n), 256, 0, s>>>(n, NX1, NY1, colors, color, comp, px);
             FSI_TRY(check_launch("probe fill"));
             FSI_TRY(coupled_jacobian_impl<T>(mesh, st, px, pj));
-            probe_extract_kernel<T><<<grid1d(n), 256, 0, s>>>(n, NX1, NY1, color, comp, pj,
-                                                             (T *)W.blocks);
+            probe_extract_kernel<T><<<grid1d(n), 256, 0, s>>>(n, NX1, NY1, colors, color, comp,
+                                                             pj, (T *)W.blocks);
             FSI_TRY(check_launch("probe extract"));
         }
     if (precond == 1) {

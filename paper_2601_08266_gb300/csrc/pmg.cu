@@ -533,6 +533,7 @@ fsi_status build_coarse_inverse(fsi_mesh *m)
 
 fsi_status pmg_ensure(fsi_mesh *m)
 {
+    FSI_TRY(require_structured(m, "the pressure multigrid"));
     if (m->pmg) return FSI_OK;
     PressureMG *P = new (std::nothrow) PressureMG();
     if (!P) return set_error(FSI_ERR_OOM, "host allocation of the pressure hierarchy failed");

@@ -58,6 +58,13 @@ fsi_status validate_mesh(const fsi_mesh *m)
     return FSI_OK;
 }
 
+fsi_status require_structured(const fsi_mesh *m, const char *what)
+{
+    if (m->tet) return set_error(FSI_ERR_ARG, "%s needs a structured grid (not a tetrahedral mesh)",
+                                 what);
+    return FSI_OK;
+}
+
 size_t vms_scratch_bytes_for(const fsi_mesh *m, const Brick &b, size_t elem_bytes)
 {
     const int *N = m->grid.N;
@@ -224,6 +231,7 @@ void fsi_mesh_destroy(fsi_mesh *m)
     destroy_pmg(m);
     cudaFree(m->coords64);
     cudaFree(m->coords32);
+    if (m->tet) fsi_tetmesh_destroy(m->tet);
     delete m;
 }
 
@@ -231,6 +239,7 @@ fsi_status fsi_mesh_set_stream(fsi_mesh *m, void *cuda_stream)
 {
     FSI_TRY(validate_mesh(m));
     m->stream = (cudaStream_t)cuda_stream;
+    if (m->tet) tet_set_stream(m->tet, m->stream);
     return FSI_OK;
 }
 
@@ -249,6 +258,7 @@ __global__ void pad_coords_kernel(int64_t n, const double *X, double4 *C64, floa
 fsi_status fsi_mesh_set_coordinates(fsi_mesh *m, const double *X)
 {
     FSI_TRY(validate_mesh(m));
+    FSI_TRY(require_structured(m, "fsi_mesh_set_coordinates"));
     FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
     FSI_CUDA(cudaStreamSynchronize(m->stream), "sync");
     if (!X) {
@@ -279,6 +289,7 @@ fsi_status fsi_mesh_set_physics(fsi_mesh *m, const fsi_physics *phys)
     FSI_TRY(validate_physics(phys));
     m->phys = *phys;
     derive(m);
+    if (m->tet) tet_set_physics(m->tet, phys);
     return FSI_OK;
 }
 
@@ -286,6 +297,7 @@ fsi_status fsi_mesh_set_brick(fsi_mesh *m, int op, fsi_prec prec, int bx, int by
                               int threads)
 {
     FSI_TRY(validate_mesh(m));
+    FSI_TRY(require_structured(m, "fsi_mesh_set_brick"));
     if (op < 0 || op > 1 || (prec != FSI_F64 && prec != FSI_F32))
         return set_error(FSI_ERR_ARG, "bad op or precision");
     if (bx < 1 || by < 1 || bz < 1 || threads < 32 || threads > 256 || threads % 32 != 0)

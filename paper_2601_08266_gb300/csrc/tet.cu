@@ -38,6 +38,7 @@
 // in slot order.
 #include <algorithm>
 #include <cmath>
+#include <new>
 #include <vector>
 
 #include "fsi_internal.cuh"
@@ -63,6 +64,9 @@ struct fsi_tetmesh {
     int32_t *fill;         // [E+1]
     int32_t *scan_tmp;
     unsigned long long *nout;
+    // distance-2 node colouring for probing the nodal diagonal blocks
+    int32_t *colors;
+    int n_colors;
 };
 
 namespace fsi {
@@ -594,11 +598,61 @@ fsi_status tet_vms(fsi_tetmesh *m, const void *U, const void *A, const void *f, 
 }
 
 }  // namespace
+
+void tet_set_stream(fsi_tetmesh *t, cudaStream_t s) { t->stream = s; }
+
+void tet_set_physics(fsi_tetmesh *t, const fsi_physics *p)
+{
+    t->phys = *p;
+    const double r = p->rho_inf;
+    t->alpha_m = 0.5 * (3.0 - r) / (1.0 + r);
+    t->alpha_f = 1.0 / (1.0 + r);
+    t->gamma = 0.5 + t->alpha_m - t->alpha_f;
+}
+
+const int32_t *tet_colors(const fsi_tetmesh *t, int *n_colors)
+{
+    *n_colors = t->n_colors;
+    return t->colors;
+}
+
 }  // namespace fsi
 
 using namespace fsi;
 
 extern "C" {
+
+fsi_status fsi_mesh_create_tet(int64_t n_nodes, const double *X, int64_t n_tets,
+                               const int32_t *tets, const fsi_physics *phys, int device,
+                               void *cuda_stream, fsi_mesh **out)
+{
+    if (!out) return set_error(FSI_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    fsi_tetmesh *t = nullptr;
+    FSI_TRY(fsi_tetmesh_create(n_nodes, X, n_tets, tets, phys, device, cuda_stream, &t));
+    fsi_mesh *m = new (std::nothrow) fsi_mesh();
+    if (!m) {
+        fsi_tetmesh_destroy(t);
+        return set_error(FSI_ERR_OOM, "host allocation of the mesh handle failed");
+    }
+    m->phys = *phys;
+    m->device = device;
+    m->stream = (cudaStream_t)cuda_stream;
+    m->n_nodes = n_nodes;
+    m->n_elems = n_tets;
+    m->alpha_m = t->alpha_m;
+    m->alpha_f = t->alpha_f;
+    m->gamma = t->gamma;
+    m->tet = t;
+    if (cudaMalloc(&m->dev_counters, 8 * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        fsi_mesh_destroy(m);
+        return set_error(FSI_ERR_OOM, "fsi_mesh_create_tet: cudaMalloc failed");
+    }
+    *out = m;
+    return FSI_OK;
+}
+
 
 fsi_status fsi_tetmesh_create(int64_t n_nodes, const double *X, int64_t n_tets,
                               const int32_t *tets, const fsi_physics *phys, int device,
@@ -631,6 +685,29 @@ fsi_status fsi_tetmesh_create(int64_t n_nodes, const double *X, int64_t n_tets,
     {
         std::vector<int32_t> cur(nstart.begin(), nstart.end() - 1);
         for (size_t sl = 0; sl < ht.size(); ++sl) nslot[cur[ht[sl]]++] = (int32_t)sl;
+    }
+    // greedy distance-2 colouring in node order: a node takes the smallest
+    // colour no node of its elements holds yet
+    std::vector<int32_t> hcol((size_t)n_nodes, -1);
+    int ncol = 0;
+    {
+        std::vector<int64_t> seen;  // per colour: last node that saw it
+        for (int64_t v = 0; v < n_nodes; ++v) {
+            for (int k = nstart[v]; k < nstart[v + 1]; ++k) {
+                const int64_t e = nslot[k] >> 2;
+                for (int a = 0; a < 4; ++a) {
+                    const int c = hcol[ht[4 * e + a]];
+                    if (c >= 0) {
+                        if ((size_t)c >= seen.size()) seen.resize(c + 1, -1);
+                        seen[c] = v;
+                    }
+                }
+            }
+            int c = 0;
+            while ((size_t)c < seen.size() && seen[c] == v) ++c;
+            hcol[v] = c;
+            ncol = std::max(ncol, c + 1);
+        }
     }
     // bucket grid: about two elements per bucket, cells as cubic as the box allows
     double lo[3], hi[3];
@@ -720,7 +797,8 @@ fsi_status fsi_tetmesh_create(int64_t n_nodes, const double *X, int64_t n_tets,
               cudaMalloc(&m->corner_scratch, (size_t)n_tets * 12 * 8) == cudaSuccess &&
               cudaMalloc(&m->fill, (size_t)(n_tets + 1) * sizeof(int32_t)) == cudaSuccess &&
               cudaMalloc(&m->scan_tmp, (size_t)ntmp * sizeof(int32_t)) == cudaSuccess &&
-              cudaMalloc(&m->nout, sizeof(unsigned long long)) == cudaSuccess;
+              cudaMalloc(&m->nout, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&m->colors, (size_t)n_nodes * sizeof(int32_t)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         fsi_tetmesh_destroy(m);
@@ -734,7 +812,9 @@ fsi_status fsi_tetmesh_create(int64_t n_nodes, const double *X, int64_t n_tets,
          up(m->node_start, nstart.data(), nstart.size() * sizeof(int32_t)) &&
          up(m->node_slot, nslot.data(), nslot.size() * sizeof(int32_t)) &&
          up(m->bucket_start, bstart.data(), bstart.size() * sizeof(int32_t)) &&
-         (btets.empty() || up(m->bucket_tets, btets.data(), btets.size() * sizeof(int32_t)));
+         (btets.empty() || up(m->bucket_tets, btets.data(), btets.size() * sizeof(int32_t))) &&
+         up(m->colors, hcol.data(), hcol.size() * sizeof(int32_t));
+    m->n_colors = ncol;
     if (!ok) {
         fsi_tetmesh_destroy(m);
         return set_error(FSI_ERR_CUDA, "fsi_tetmesh_create: copy failed");
@@ -767,6 +847,7 @@ void fsi_tetmesh_destroy(fsi_tetmesh *m)
     cudaFree(m->fill);
     cudaFree(m->scan_tmp);
     cudaFree(m->nout);
+    cudaFree(m->colors);
     delete m;
 }
 

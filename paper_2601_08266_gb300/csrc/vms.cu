@@ -101,6 +101,7 @@ fsi_status launch(fsi_mesh *m, const void *U, const void *A, const void *f, cons
 fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
                         const void *f, void *R)
 {
+    if (m->tet) return fsi_tet_residual(m->tet, prec, U, A, f, R);
     if (prec == FSI_F64) return launch<double, false>(m, U, A, f, nullptr, R);
     if (prec == FSI_DF64) return launch<df64, false>(m, U, A, f, nullptr, R);
     return launch<float, false>(m, U, A, f, nullptr, R);
@@ -109,6 +110,7 @@ fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A
 fsi_status vms_jacobian(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
                         const void *f, const void *x, void *Jx)
 {
+    if (m->tet) return fsi_tet_jacobian_apply(m->tet, prec, U, A, f, x, Jx);
     if (prec == FSI_F64) return launch<double, true>(m, U, A, f, x, Jx);
     if (prec == FSI_DF64) return launch<df64, true>(m, U, A, f, x, Jx);
     return launch<float, true>(m, U, A, f, x, Jx);
