@@ -1105,6 +1105,72 @@ def tet_section(args, dev, stream):
     out["spread_df64_ms"] = timeit(lambda: fsi.fsi_tet_spread(mesh, fsi.FSI_DF64, e, lam, cs, pm,
                                                               lv, None, F, False))
     mesh.close()
+    out["newton_channel"] = tet_newton(fsi, dev, stream)
+    return out
+
+
+def tet_newton(fsi, dev, stream, N=32, m=50_000):
+    """One implicit step of the channel flow (inflow 16 y(1-y) z(1-z) at x = 0,
+    no-slip walls, traction-free outflow, mu = 1e-3, dt = 1e-3) on a
+    tetrahedral mesh (32^3 cubes x 6, shuffled numbering) with leaflet points:
+    plain FP64 against mixed FP32/FP64 Newton-GMRES, block-Jacobi."""
+    import torch
+    from paper_2601_08266_gb300 import inputs
+    X, Tt = inputs.tet_box_mesh(N, seed=SEED + 95, perturb=0.1)
+    n = X.shape[0]
+    dt, mu, gamma = 1e-3, 1e-3, 2.0 / 3.0
+    x, y, z = X[:, 0], X[:, 1], X[:, 2]
+    prof = 16.0 * y * (1 - y) * z * (1 - z)
+    wall = (y < 1e-12) | (y > 1 - 1e-12) | (z < 1e-12) | (z > 1 - 1e-12)
+    inflow = (x < 1e-12) & ~wall
+    mask = np.zeros((n, 4), dtype=np.uint8)
+    mask[wall | inflow, :3] = 1
+    Vn = np.zeros((n, 4))
+    Vn[:, 0] = prof * (1.0 + 0.05 * np.sin(2 * np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z))
+    Vn[mask[:, 0].astype(bool), :3] = 0.0
+    Vn[inflow, 0] = prof[inflow]
+    g = np.zeros((n, 3))
+    g[inflow, 0] = prof[inflow]
+    yD = np.zeros((n, 4))
+    yD[:, :3] = (g - Vn[:, :3]) / (gamma * dt)
+    out = {"elements": int(Tt.shape[0]), "nodes": int(n), "dofs": 4 * int(n), "points": m,
+           "preconditioner": "nodal 4x4 block-Jacobi (probed with a distance-2 colouring)"}
+    with torch.cuda.stream(stream):
+        mesh = fsi.MeshTet(torch.as_tensor(X, device=dev), torch.as_tensor(Tt, device=dev),
+                           rho=1.0, mu=mu, dt=dt, rho_inf=0.5, device=dev.index,
+                           stream=stream.cuda_stream)
+        P = torch.as_tensor(inputs.leaflet_points(m, seed=SEED + 96), device=dev)
+        e = torch.empty(m, dtype=torch.int32, device=dev)
+        xi = torch.empty((m, 3), dtype=torch.float64, device=dev)
+        cs = torch.empty(mesh.n_elems + 1, dtype=torch.int32, device=dev)
+        pm = torch.empty(m, dtype=torch.int32, device=dev)
+        w = torch.full((m,), 0.024 / m, dtype=torch.float64, device=dev)
+        Vd, Ad = torch.as_tensor(Vn, device=dev), torch.zeros((n, 4), dtype=torch.float64,
+                                                              device=dev)
+        md, yDd = torch.as_tensor(mask, device=dev), torch.as_tensor(yD, device=dev)
+    fsi.fsi_locate(mesh, P, e, xi, cs, pm)
+    r_ref = None
+    for name, mixed in (("fp64", False), ("mixed", True)):
+        with torch.cuda.stream(stream):
+            yv = torch.zeros((n, 4), dtype=torch.float64, device=dev)
+            yv[md.bool()] = yDd[md.bool()]
+        st = fsi.StepState(yv, Vd, Ad, mask=md, yD=yDd, elem=e, xi=xi, cell_start=cs, perm=pm,
+                           w=w, drho_s=0.5)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        code, rep = fsi.fsi_newton_step(mesh, st, mixed=mixed, restart=50, max_newton=10,
+                                        max_krylov=20000, newton_rtol=1e-8, krylov_rtol=1e-3,
+                                        r_ref=r_ref or 0.0, check=False,
+                                        precond=fsi.PRECOND_BLOCK_JACOBI,
+                                        residual_prec=fsi.FSI_DF64 if mixed else fsi.FSI_F64)
+        stream.synchronize()
+        r_ref = r_ref or rep["r_ref"]
+        out[name] = {"seconds": time.perf_counter() - t0, "newton_iters": rep["newton_iters"],
+                     "krylov_iters": rep["krylov_iters"],
+                     "r_final_over_ref": rep["r_final"] / r_ref,
+                     "converged": bool(rep["converged"]), "status": code}
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    mesh.close()
     return out
 
 
