@@ -286,9 +286,14 @@ fsi_status fsi_mesh_create_tet(int64_t n_nodes, const double *X, int64_t n_tets,
                                const int32_t *tets, const fsi_physics *phys, int device,
                                void *cuda_stream, fsi_mesh **out);
 
-/* VMS residual and Jacobian apply on the tetrahedral mesh:/* VMS residual and Jacobian apply on the tetrahedral mesh: the same
+/* VMS residual and Jacobian apply on the tetrahedral mesh: the same
  * arguments, layouts and precisions as fsi_residual / fsi_jacobian_apply
- * (U, A, f, x, R, Jx [n][4] device arrays; f may be NULL).  Deterministic.  */
+ * (U, A, f, x, R, Jx [n][4] device arrays; f may be NULL).  Deterministic.
+ * The first call of each compute type builds that type's per-element
+ * geometry table (J^-1, G, the weight: 18 values per element) on the mesh's
+ * stream and keeps it with the mesh; it allocates, so that first call must
+ * not be made while the stream is being captured into a CUDA graph
+ * (FSI_ERR_ARG then).  FSI_ERR_OOM if the table cannot be allocated.      */
 fsi_status fsi_tet_residual(fsi_tetmesh *mesh, fsi_prec prec, const void *U, const void *A,
                             const void *f, void *R);
 fsi_status fsi_tet_jacobian_apply(fsi_tetmesh *mesh, fsi_prec prec, const void *U,

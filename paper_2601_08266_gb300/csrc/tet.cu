@@ -7,8 +7,10 @@
 // loads node a of the element (fields and coordinates) and then acts as
 // quadrature point a of the symmetric 4-point rule (barycentric coordinates
 // al at node a, be elsewhere).  The element geometry (J = [x1-x0, x2-x0,
-// x3-x0], J^-1, the metric G = J^-T J^-1 of Sec. 2.1) is formed in every lane
-// from the group's coordinates (shuffles); P1 gradients are constant per
+// x3-x0], J^-1, the metric G = J^-T J^-1 of Sec. 2.1, G:G, 1/tr G, the weight)
+// is a per-element table computed once per compute type (the mesh does not
+// move; reading 72-144 B per element costs less than forming it in every
+// lane of every apply); P1 gradients are constant per
 // element, so a field's gradient is the group sum of u_a grad N_a and its
 // value at point q is be * sum_a u_a + (al - be) u_q.  The Gauss-point
 // algebra is the one the hexahedral kernels use (gp_residual_terms /
@@ -39,6 +41,7 @@
 #include <algorithm>
 #include <cmath>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "fsi_internal.cuh"
@@ -67,6 +70,9 @@ struct fsi_tetmesh {
     // distance-2 node colouring for probing the nodal diagonal blocks
     int32_t *colors;
     int n_colors;
+    // per-element geometry (J^-1, G, G:G, 1/tr G, |det J|/24) in each compute
+    // type [FSI_F64, FSI_F32, FSI_DF64], computed on first use
+    void *geo[3];
 };
 
 namespace fsi {
@@ -90,17 +96,6 @@ constexpr float kTetBeL = static_cast<float>(kTetBe - static_cast<double>(kTetBe
 template <> __device__ __forceinline__ df64 tet_al<df64>() { return df64(kTetAlH, kTetAlL); }
 template <> __device__ __forceinline__ df64 tet_be<df64>() { return df64(kTetBeH, kTetBeL); }
 
-// value of lane (group base + b) within the aligned group of four lanes
-template <typename T> __device__ __forceinline__ T from_lane(T v, int b)
-{
-    return __shfl_sync(0xffffffffu, v, ((int)threadIdx.x & 28) | b);
-}
-template <> __device__ __forceinline__ df64 from_lane<df64>(df64 v, int b)
-{
-    const int src = ((int)threadIdx.x & 28) | b;
-    return df64(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
-}
-
 // sum over the group of four lanes (butterfly; every lane gets the same value)
 template <typename T> __device__ __forceinline__ T group_sum(T v)
 {
@@ -111,12 +106,88 @@ template <typename T> __device__ __forceinline__ T group_sum(T v)
 template <typename T> __device__ __forceinline__ T abs_t(T v) { return v < T(0) ? -v : v; }
 template <> __device__ __forceinline__ df64 abs_t<df64>(df64 v) { return v.hi < 0.0f ? -v : v; }
 
+// Element geometry from the four corner coordinates c[b][i]: J[i][k] =
+// c[k+1][i] - c[0][i], J^-1 by cofactors, G = J^-T J^-1, G:G, 1/tr G and
+// the quadrature weight |det J| / 24; it fills the per-element geometry table
+// that the VMS kernels read.
+constexpr int kTetGeo = 18;  // Ji[9], G00 G01 G02 G11 G12 G22, G:G, 1/trG, w
+
+template <typename T> __device__ __forceinline__ void tet_geometry(const T (&c)[4][3], T (&out)[kTetGeo])
+{
+    T J[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) J[i][k] = c[k + 1][i] - c[0][i];
+    const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const T c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const T det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    const T id = inv_t(det);
+    T Ji[3][3];
+    Ji[0][0] = c00 * id;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+    Ji[1][0] = c01 * id;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+    Ji[2][0] = c02 * id;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+    T G[3][3], GG = T(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            G[i][j] = dot3_t(Ji[0][i], Ji[0][j], Ji[1][i], Ji[1][j], Ji[2][i], Ji[2][j]);
+            GG = fma_t(G[i][j], G[i][j], GG);
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) out[3 * i + k] = Ji[i][k];
+    out[9] = G[0][0];
+    out[10] = G[0][1];
+    out[11] = G[0][2];
+    out[12] = G[1][1];
+    out[13] = G[1][2];
+    out[14] = G[2][2];
+    out[15] = GG;
+    out[16] = inv_t(G[0][0] + G[1][1] + G[2][2]);
+    out[17] = abs_t(det) * T(1.0 / 24.0);
+}
+
+template <typename T>
+__global__ void tet_geo_kernel(int64_t E, const int4 *__restrict__ tets,
+                               const vec4<typename StorageOf<T>::type> *__restrict__ X,
+                               T *__restrict__ geo)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int4 t = tets[e];
+        const int nd[4] = {t.x, t.y, t.z, t.w};
+        T c[4][3];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const vec4<T> x = load_c<T>(X + nd[b]);
+            c[b][0] = x.x;
+            c[b][1] = x.y;
+            c[b][2] = x.z;
+        }
+        T g[kTetGeo];
+        tet_geometry(c, g);
+#pragma unroll
+        for (int k = 0; k < kTetGeo; ++k) geo[e * kTetGeo + k] = g[k];
+    }
+}
+
 template <typename T> struct TetArgs {
     using S = typename StorageOf<T>::type;
     VmsArgs<T> V;  // physics, chain factors and the field pointers U, A, f, x
     int64_t E;
     const vec4<S> *X;
     const int4 *tets;
+    const T *geo;  // [E][kTetGeo]
     vec4<T> *slots;
 };
 
@@ -137,54 +208,38 @@ template <typename T, bool JAC> __global__ void __launch_bounds__(256) tet_vms_k
             const int4 tt = P.tets[e];
             node = a == 0 ? tt.x : (a == 1 ? tt.y : (a == 2 ? tt.z : tt.w));
         }
-        // idle lanes carry the unit reference tetrahedron
-        const vec4<T> xc = valid ? load_c<T>(P.X + node)
-                                 : vec4<T>{a == 1 ? T(1) : T(0), a == 2 ? T(1) : T(0),
-                                           a == 3 ? T(1) : T(0), T(0)};
         const vec4<T> u = valid ? load_c<T>(V.U + node) : zero;
         const vec4<T> ac = valid ? load_c<T>(V.A + node) : zero;
         const vec4<T> ff = (valid && V.f) ? load_c<T>(V.f + node) : zero;
 
-        // geometry: J[i][k] = x_{k+1,i} - x_{0,i}
-        T c[4][3];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            c[b][0] = from_lane(xc.x, b);
-            c[b][1] = from_lane(xc.y, b);
-            c[b][2] = from_lane(xc.z, b);
-        }
-        T J[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) J[i][k] = c[k + 1][i] - c[0][i];
-        const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-        const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-        const T c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-        const T det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-        const T id = inv_t(det);
+        // element geometry from the table (idle lanes: the unit reference
+        // tetrahedron, J = I)
         Geo<T> geo;
-        geo.Ji[0][0] = c00 * id;
-        geo.Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
-        geo.Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
-        geo.Ji[1][0] = c01 * id;
-        geo.Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
-        geo.Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
-        geo.Ji[2][0] = c02 * id;
-        geo.Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
-        geo.Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
-        geo.det = det;
-        T GG = T(0);
+        T GG;
+        if (valid) {
+            const T *g = P.geo + e * kTetGeo;
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const T gij = dot3_t(geo.Ji[0][i], geo.Ji[0][j], geo.Ji[1][i], geo.Ji[1][j],
-                                     geo.Ji[2][i], geo.Ji[2][j]);
-                geo.G[i][j] = gij;
-                GG = fma_t(gij, gij, GG);
-            }
-        geo.inv_trG = inv_t(geo.G[0][0] + geo.G[1][1] + geo.G[2][2]);
+                for (int k = 0; k < 3; ++k) geo.Ji[i][k] = g[3 * i + k];
+            geo.G[0][0] = g[9];
+            geo.G[0][1] = geo.G[1][0] = g[10];
+            geo.G[0][2] = geo.G[2][0] = g[11];
+            geo.G[1][1] = g[12];
+            geo.G[1][2] = geo.G[2][1] = g[13];
+            geo.G[2][2] = g[14];
+            GG = g[15];
+            geo.inv_trG = g[16];
+            geo.det = g[17];  // holds the quadrature weight |det J| / 24
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) geo.Ji[i][k] = geo.G[i][k] = T(i == k ? 1 : 0);
+            GG = T(3);
+            geo.inv_trG = inv_t(T(3));
+            geo.det = T(1.0 / 24.0);
+        }
         geo.q0 = fma_t(V.CInu2, GG, V.ct_dt2);
         // grad N of this lane's node
         T dN[3];
@@ -249,7 +304,7 @@ template <typename T, bool JAC> __global__ void __launch_bounds__(256) tet_vms_k
             gp_jacobian_terms(V, q, dv, dgv, da, dp, dgp, vGdv, geo.q0, X, Y);
         }
         // projection onto this lane's test function
-        const T w = abs_t(det) * T(1.0 / 24.0);
+        const T w = geo.det;
         const T Xs[4] = {X[0], X[1], X[2], X[3]};
         T r[4];
 #pragma unroll
@@ -583,12 +638,42 @@ TetArgs<T> tet_args(fsi_tetmesh *m, const void *U, const void *A, const void *f,
     return P;
 }
 
+template <typename T> constexpr int geo_slot()
+{
+    return std::is_same<T, double>::value ? 0 : (std::is_same<T, float>::value ? 1 : 2);
+}
+
+// the per-element geometry table of compute type T, built on first use
+template <typename T> fsi_status ensure_geo(fsi_tetmesh *m)
+{
+    using S = typename StorageOf<T>::type;
+    void *&g = m->geo[geo_slot<T>()];
+    if (g) return FSI_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FSI_CUDA(cudaStreamIsCapturing(m->stream, &cap), "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+        return set_error(FSI_ERR_ARG, "tetrahedral geometry table: first apply of this compute "
+                                      "type inside a stream capture");
+    if (cudaMalloc(&g, (size_t)m->n_elems * kTetGeo * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        g = nullptr;
+        return set_error(FSI_ERR_OOM, "tetrahedral geometry table: cudaMalloc failed");
+    }
+    const vec4<S> *X = (const vec4<S> *)(sizeof(S) == 8 ? (const void *)m->X64
+                                                         : (const void *)m->X32);
+    tet_geo_kernel<T><<<grid_for(m->n_elems, 256), 256, 0, m->stream>>>(m->n_elems, m->tets, X,
+                                                                        (T *)g);
+    return check_launch("tet geometry kernel");
+}
+
 template <typename T, bool JAC>
 fsi_status tet_vms(fsi_tetmesh *m, const void *U, const void *A, const void *f, const void *x,
                    void *out)
 {
     using S = typename StorageOf<T>::type;
+    FSI_TRY(ensure_geo<T>(m));
     TetArgs<T> P = tet_args<T>(m, U, A, f, x);
+    P.geo = (const T *)m->geo[geo_slot<T>()];
     const int64_t threads = 4 * m->n_elems;
     tet_vms_kernel<T, JAC><<<grid_for(threads, 256, 152 * 64), 256, 0, m->stream>>>(P);
     FSI_TRY(check_launch("tet vms kernel"));
@@ -848,6 +933,7 @@ void fsi_tetmesh_destroy(fsi_tetmesh *m)
     cudaFree(m->scan_tmp);
     cudaFree(m->nout);
     cudaFree(m->colors);
+    for (void *g : m->geo) cudaFree(g);
     delete m;
 }
 
