@@ -277,9 +277,10 @@ void fsi_tetmesh_destroy(fsi_tetmesh *mesh);
  * fsi_coupled_residual, fsi_coupled_jacobian_apply, fsi_block_diagonal and
  * fsi_newton_step act as on the structured grid (cell_start has n_tets + 1
  * entries).  The nodal diagonal blocks are probed with a distance-2 node
- * colouring built at creation (no two nodes of one element share a colour),
- * so fsi_newton_step needs the block-Jacobi preconditioner here; the Schur
- * preconditioner, the interface band, mapped coordinates, brick shapes, the
+ * colouring built at creation (no two nodes of one element share a colour);
+ * fsi_newton_step takes either preconditioner (the Schur one with an
+ * algebraic multigrid for the pressure; see fsi_pressure_vcycle).  The
+ * interface band, mapped coordinates, brick shapes, the
  * learned guess (stencil features) and the batched ensemble need a
  * structured grid and return FSI_ERR_ARG on this handle.                   */
 fsi_status fsi_mesh_create_tet(int64_t n_nodes, const double *X, int64_t n_tets,
@@ -421,7 +422,9 @@ typedef struct {
                               Schur-complement preconditioner (3x3 velocity
                               blocks, pressure Schur complement approximated
                               by sigma (K + kappa M) and inverted by one
-                              multigrid V-cycle; see fsi_pressure_vcycle)     */
+                              multigrid V-cycle: geometric on the structured
+                              grid, algebraic on a tetrahedral mesh; see
+                              fsi_pressure_vcycle)                            */
     int32_t residual_prec; /* FSI_F64 or FSI_DF64: arithmetic of the Newton
                               residual (see fsi_coupled_residual)             */
     int32_t reserved;
@@ -512,7 +515,32 @@ fsi_status fsi_solid_positions(fsi_solid *body, const double *u, double *x);
  * Vectors are scalar nodal fields [n_l] of the level (lexicographic, x
  * fastest) in `prec` (FSI_F64 or FSI_F32), device pointers owned by the
  * caller.  Level 0 is the mesh grid.  The hierarchy is built on first use
- * and kept in the mesh.  Stream-ordered on the mesh stream.                */
+ * and kept in the mesh.  Stream-ordered on the mesh stream.
+ *
+ * On an fsi_mesh backed by a tetrahedral mesh (fsi_mesh_create_tet) the same
+ * entry points act on K + kappa M of the P1 pressure space (element
+ * matrices K_ab = V grad l_a . grad l_b, M_ab = V (1 + delta_ab) / 20; L the
+ * largest extent of the bounding box), and the levels are those of a
+ * smoothed-aggregation algebraic multigrid built on the host in FP64 (one
+ * synchronisation) on first use and whenever the elimination set changes:
+ * strong neighbours |a_ij| >= 0.08 sqrt(a_ii a_jj); greedy aggregation in
+ * node order; P = (I - 4/(3 rho) D^-1 A) P0 with P0 the aggregate indicator
+ * and rho the spectral radius of D^-1 A (30 power iterations, at most the
+ * Gershgorin bound); R = P^T, Galerkin coarse operators R A P; levels until
+ * <= 600 unknowns (dense inverse) or the coarsening stalls; Chebyshev of
+ * degree 2 over [hi/10, hi], hi = 1.1 rho.  Vectors are in node order.
+ * Eliminated nodes are given per node (fsi_pressure_set_eliminated); none
+ * by default.  fsi_newton_step eliminates the nodes on the mesh boundary
+ * whose three velocity components are free and the nodes whose pressure is
+ * fixed.  fsi_pressure_levels and fsi_pressure_set_faces are for the
+ * structured grid only (FSI_ERR_ARG here).                                  */
+/* number of levels and the unknowns per level n[l] ([16] or NULL); either
+ * mesh kind */
+fsi_status fsi_pressure_level_sizes(fsi_mesh *mesh, int32_t *n_levels, int64_t *n);
+/* tetrahedral mesh only: eliminated[n] device flags (nonzero = eliminated),
+ * NULL = none.  Synchronises the mesh stream; rebuilds the hierarchy when
+ * the set changes.  FSI_ERR_ARG on a structured grid.                      */
+fsi_status fsi_pressure_set_eliminated(fsi_mesh *mesh, const uint8_t *eliminated);
 /* faces[6] (x0, x1, y0, y1, z0, z1), nonzero = eliminated; none by default.
  * Synchronises the mesh stream when the set changes (the coarse inverse is
  * rebuilt).                                                                */
@@ -526,7 +554,8 @@ fsi_status fsi_pressure_restrict(fsi_mesh *mesh, fsi_prec prec, int32_t level, c
 /* x (level) += P xc (level+1) */
 fsi_status fsi_pressure_prolong_add(fsi_mesh *mesh, fsi_prec prec, int32_t level, const void *xc,
                                     void *x);
-/* `degree` Chebyshev steps on level `level` over [hi/4, hi] for (K + kappa M) x = b,
+/* `degree` Chebyshev steps on level `level` over [hi/4, hi] ([hi/10, hi] on a
+ * tetrahedral mesh) for (K + kappa M) x = b,
  * from x = 0 (from_zero != 0; x is overwritten) or from the given x.  Uses the
  * level's scratch direction vector. */
 fsi_status fsi_pressure_smooth(fsi_mesh *mesh, fsi_prec prec, int32_t level, int32_t degree,

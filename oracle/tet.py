@@ -155,3 +155,36 @@ def spread(mesh: TetMesh, elem, lam, lamv, w=None, F=None, accumulate=False):
                          _p(_f64(lamv, (m, 3))), None if w is None else _p(_f64(w, (m,))),
                          _p(F), 1 if accumulate else 0)
     return F
+
+
+def pressure_operator(mesh: TetMesh, kappa, eliminated=None):
+    """K + kappa M of the P1 pressure space as a scipy CSR matrix [n, n]: the
+    pressure Schur approximation sigma (K + kappa M) of the block
+    preconditioner (Sec. 2.4 builds its block preconditioners from the
+    sub-matrices of the reduced system; the stiffness-plus-mass form is the
+    reading used on the structured grid too).  Per element, with the
+    barycentric functions l_a(x) = c_a0 + c_a . x read off the inverse of
+    [1 x_b] (rows b = corners): K_ab = V c_a . c_b, M_ab = V (1 + delta_ab) / 20,
+    V = |det [1 x_b]| / 6.  Nodes flagged in `eliminated` keep only their
+    diagonal entry (their rows and columns are dropped otherwise).
+    """
+    import scipy.sparse as sp
+    E = mesh.n_elems
+    M4 = np.ones((E, 4, 4))
+    M4[:, :, 1:] = mesh.X[mesh.tets]
+    C = np.linalg.inv(M4)               # column a: (c_a0, c_a)
+    grad = np.transpose(C[:, 1:, :], (0, 2, 1))   # [E, a, 3]
+    V = np.abs(np.linalg.det(M4)) / 6.0
+    Ke = V[:, None, None] * np.einsum("eai,ebi->eab", grad, grad)
+    Me = V[:, None, None] * (np.ones((4, 4)) + np.eye(4))[None] / 20.0
+    Ae = Ke + kappa * Me
+    rows = np.repeat(mesh.tets, 4, axis=1).ravel()
+    cols = np.tile(mesh.tets, (1, 4)).ravel()
+    A = sp.csr_matrix((Ae.reshape(-1), (rows, cols)), shape=(mesh.n_nodes, mesh.n_nodes))
+    if eliminated is not None:
+        el = np.asarray(eliminated, dtype=bool)
+        A = A.tocoo()
+        keep = (A.row == A.col) | ~(el[A.row] | el[A.col])
+        A = sp.csr_matrix((A.data[keep], (A.row[keep], A.col[keep])), shape=A.shape)
+    return A
+

@@ -148,6 +148,9 @@ _SIGS = {
     "fsi_interface_scaling": ([_VP, _VP, ctypes.c_double, _INT, _VP], _INT),
     "fsi_pressure_levels": ([_VP, ctypes.POINTER(ctypes.c_int32), _VP], _INT),
     "fsi_pressure_set_faces": ([_VP, ctypes.POINTER(ctypes.c_int32)], _INT),
+    "fsi_pressure_level_sizes": ([_VP, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_int64)], _INT),
+    "fsi_pressure_set_eliminated": ([_VP, _VP], _INT),
     "fsi_pressure_apply": ([_VP, _INT, _INT, _VP, _VP], _INT),
     "fsi_pressure_restrict": ([_VP, _INT, _INT, _VP, _VP], _INT),
     "fsi_pressure_prolong_add": ([_VP, _INT, _INT, _VP, _VP], _INT),
@@ -702,6 +705,26 @@ def fsi_interface_scaling(mesh: Mesh, cell_start, s_band, layers, s):
 def fsi_pressure_set_faces(mesh: Mesh, faces):
     arr = (ctypes.c_int32 * 6)(*[int(bool(f)) for f in faces])
     _check(lib().fsi_pressure_set_faces(mesh.handle, arr))
+
+
+def fsi_pressure_level_sizes(mesh: Mesh):
+    """Unknowns per level of the pressure hierarchy (either mesh kind)."""
+    n = ctypes.c_int32(0)
+    buf = (ctypes.c_int64 * 16)()
+    _check(lib().fsi_pressure_level_sizes(mesh.handle, ctypes.byref(n), buf))
+    return [int(buf[l]) for l in range(n.value)]
+
+
+def fsi_pressure_set_eliminated(mesh: Mesh, eliminated=None):
+    """Tetrahedral mesh: per-node uint8 device flags of eliminated pressure
+    nodes (None: none)."""
+    if eliminated is None:
+        _check(lib().fsi_pressure_set_eliminated(mesh.handle, None))
+        return
+    import torch
+    if eliminated.dtype != torch.uint8 or eliminated.numel() != mesh.n_nodes:
+        raise ValueError("eliminated must be a uint8 tensor of n_nodes entries")
+    _check(lib().fsi_pressure_set_eliminated(mesh.handle, _ptr(eliminated.contiguous())))
 
 
 def fsi_pressure_apply(mesh: Mesh, level, x, y):

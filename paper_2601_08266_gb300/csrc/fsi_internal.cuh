@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "fsi.h"
 
@@ -54,6 +55,7 @@ struct Brick {
 
 struct NewtonWorkspace;
 struct PressureMG;
+struct TetAmg;
 
 // ---------------------------------------------------------------- mesh
 }  // namespace fsi
@@ -88,6 +90,9 @@ struct fsi_mesh {
     // unstructured tetrahedral mesh behind this handle (fsi_mesh_create_tet);
     // null for the structured grid
     fsi_tetmesh *tet;
+    // algebraic multigrid of the pressure Schur approximation on the
+    // tetrahedral mesh (amg.cu)
+    fsi::TetAmg *amg;
 };
 
 namespace fsi {
@@ -104,6 +109,21 @@ fsi_status pmg_set_faces(fsi_mesh *m, const int faces[6]);
 template <typename T> fsi_status pmg_vcycle(fsi_mesh *m, const T *b, T *x);
 void *pmg_fine_buffer(fsi_mesh *m, int which);
 void destroy_pmg(fsi_mesh *m);
+
+// pressure algebraic multigrid on a tetrahedral mesh (amg.cu); the
+// elimination set is one flag per node, or derived from a step's Dirichlet
+// mask (boundary nodes with free velocity, nodes with fixed pressure)
+fsi_status amg_set_eliminated(fsi_mesh *m, const std::vector<uint8_t> &elim);
+fsi_status amg_set_from_mask(fsi_mesh *m, const uint8_t *mask);
+template <typename T> fsi_status amg_vcycle(fsi_mesh *m, const T *b, T *x);
+void *amg_fine_buffer(fsi_mesh *m, int which);
+fsi_status amg_level_sizes(fsi_mesh *m, int32_t *n_levels, int64_t *n);
+fsi_status amg_apply(fsi_mesh *m, fsi_prec prec, int level, const void *x, void *y);
+fsi_status amg_restrict(fsi_mesh *m, fsi_prec prec, int level, const void *r, void *b);
+fsi_status amg_prolong_add(fsi_mesh *m, fsi_prec prec, int level, const void *xc, void *x);
+fsi_status amg_smooth(fsi_mesh *m, fsi_prec prec, int level, int degree, const void *b, void *x,
+                      int from_zero);
+void destroy_amg(fsi_mesh *m);
 
 // immersed hyperelastic solid (solid.cu)
 fsi_status solid_residual_impl(fsi_solid *b, const double *u_af, const double *v_af,
@@ -134,6 +154,10 @@ fsi_status vms_jacobian(fsi_mesh *m, fsi_prec prec, const void *U, const void *A
 void tet_set_stream(fsi_tetmesh *t, cudaStream_t s);
 void tet_set_physics(fsi_tetmesh *t, const fsi_physics *p);
 const int32_t *tet_colors(const fsi_tetmesh *t, int *n_colors);
+// host copies of the node coordinates [n][3] and elements [E][4], and the
+// bounding box (synchronises the mesh stream)
+fsi_status tet_download(fsi_tetmesh *t, std::vector<double> &X, std::vector<int32_t> &tets,
+                        double box_lo[3], double box_hi[3]);
 fsi_status require_structured(const fsi_mesh *m, const char *what);
 
 // cell -> points table (dlm.cu): from per-cell counts in fill[0..E), an

@@ -638,13 +638,7 @@ fsi_status build_block_jacobi(fsi_mesh *mesh, const fsi_step_state *st, int prec
     // tetrahedral mesh
     int ncolors = 8;
     const int32_t *colors = nullptr;
-    if (mesh->tet) {
-        if (precond == 1)
-            return set_error(FSI_ERR_ARG, "the Schur preconditioner needs a structured grid; "
-                                          "use the block-Jacobi preconditioner on a "
-                                          "tetrahedral mesh");
-        colors = tet_colors(mesh->tet, &ncolors);
-    }
+    if (mesh->tet) colors = tet_colors(mesh->tet, &ncolors);
     for (int color = 0; color < ncolors; ++color)
         for (int comp = 0; comp < ncomp; ++comp) {
             probe_fill_kernel<T><<<grid1d(n), 256, 0, s>>>(n, NX1, NY1, colors, color, comp, px);
@@ -657,6 +651,9 @@ fsi_status build_block_jacobi(fsi_mesh *mesh, const fsi_step_state *st, int prec
     if (precond == 1) {
         block_invert3_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.blocks, (T *)W.inv);
         FSI_TRY(check_launch("block invert"));
+        // tetrahedral mesh: the algebraic multigrid eliminates boundary nodes
+        // with free velocity and nodes with fixed pressure
+        if (mesh->tet) return amg_set_from_mask(mesh, st->mask);
         // faces where the velocity is free (more than half of the face's inner
         // nodes, or of all its nodes when it has none inside) get Dirichlet
         // pressure in the Schur approximation
@@ -734,10 +731,12 @@ fsi_status apply_precond(fsi_mesh *mesh, const fsi_step_state *st, const T *in, 
         block_apply_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, in, out);
         return check_launch("block apply");
     }
-    T *bp = (T *)pmg_fine_buffer(mesh, 0), *xp = (T *)pmg_fine_buffer(mesh, 1);
+    const bool tet = mesh->tet != nullptr;
+    T *bp = (T *)(tet ? amg_fine_buffer(mesh, 0) : pmg_fine_buffer(mesh, 0));
+    T *xp = (T *)(tet ? amg_fine_buffer(mesh, 1) : pmg_fine_buffer(mesh, 1));
     schur_split_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, in, out, bp);
     FSI_TRY(check_launch("Schur split"));
-    FSI_TRY(pmg_vcycle<T>(mesh, bp, xp));
+    FSI_TRY(tet ? amg_vcycle<T>(mesh, bp, xp) : pmg_vcycle<T>(mesh, bp, xp));
     const double sigma = mesh->alpha_f * mesh->gamma * mesh->phys.dt / (mesh->alpha_m * mesh->phys.rho);
     schur_merge_kernel<T><<<grid1d(n), 256, 0, s>>>(n, in, xp, st->mask, (T)(1.0 / sigma), out);
     return check_launch("Schur merge");
@@ -752,7 +751,6 @@ fsi_status gmres(fsi_mesh *mesh, const fsi_step_state *st, int restart, int max_
     Work &W = mesh->newton->w;
     cudaStream_t s = mesh->stream;
     const int64_t len = 4 * mesh->n_nodes;
-    const int n = (int)mesh->n_nodes;
     T *V = (T *)W.Vk, *w = (T *)W.w, *z = (T *)W.z, *x = (T *)W.x, *b = (T *)W.b;
     const int64_t ld = len;
     std::vector<double> H((size_t)(restart + 1) * restart, 0.0), cs(restart), sn(restart),

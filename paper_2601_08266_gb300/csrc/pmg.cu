@@ -639,6 +639,38 @@ fsi_status fsi_pressure_levels(fsi_mesh *mesh, int32_t *n_levels, int32_t *N)
     return FSI_OK;
 }
 
+fsi_status fsi_pressure_level_sizes(fsi_mesh *mesh, int32_t *n_levels, int64_t *n)
+{
+    FSI_TRY(validate_mesh(mesh));
+    if (!n_levels) return set_error(FSI_ERR_ARG, "fsi_pressure_level_sizes: n_levels is NULL");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    if (mesh->tet) return amg_level_sizes(mesh, n_levels, n);
+    FSI_TRY(pmg_ensure(mesh));
+    *n_levels = mesh->pmg->nlev;
+    if (n)
+        for (int l = 0; l < mesh->pmg->nlev; ++l) n[l] = mesh->pmg->lev[l].n;
+    return FSI_OK;
+}
+
+fsi_status fsi_pressure_set_eliminated(fsi_mesh *mesh, const uint8_t *eliminated)
+{
+    FSI_TRY(validate_mesh(mesh));
+    if (!mesh->tet)
+        return set_error(FSI_ERR_ARG, "fsi_pressure_set_eliminated: the mesh is not tetrahedral "
+                                      "(a structured grid eliminates faces: "
+                                      "fsi_pressure_set_faces)");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    std::vector<uint8_t> e((size_t)mesh->n_nodes, 0);
+    if (eliminated) {
+        FSI_CUDA(cudaMemcpyAsync(e.data(), eliminated, e.size(), cudaMemcpyDeviceToHost,
+                                 mesh->stream),
+                 "memcpy");
+        FSI_CUDA(cudaStreamSynchronize(mesh->stream), "sync");
+        for (uint8_t &v : e) v = v != 0;
+    }
+    return amg_set_eliminated(mesh, e);
+}
+
 fsi_status fsi_pressure_set_faces(fsi_mesh *mesh, const int32_t *faces)
 {
     FSI_TRY(validate_mesh(mesh));
@@ -655,6 +687,7 @@ fsi_status fsi_pressure_apply(fsi_mesh *mesh, fsi_prec prec, int32_t level, cons
     FSI_TRY(check_prec(prec));
     if (!x || !y) return set_error(FSI_ERR_ARG, "fsi_pressure_apply: NULL argument");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    if (mesh->tet) return amg_apply(mesh, prec, level, x, y);
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, false));
     const dim3 g = grid3(mesh->pmg->lev[level]);
@@ -674,6 +707,7 @@ fsi_status fsi_pressure_restrict(fsi_mesh *mesh, fsi_prec prec, int32_t level, c
     FSI_TRY(check_prec(prec));
     if (!r || !b) return set_error(FSI_ERR_ARG, "fsi_pressure_restrict: NULL argument");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    if (mesh->tet) return amg_restrict(mesh, prec, level, r, b);
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, true));
     PressureMG &P = *mesh->pmg;
@@ -696,6 +730,7 @@ fsi_status fsi_pressure_prolong_add(fsi_mesh *mesh, fsi_prec prec, int32_t level
     FSI_TRY(check_prec(prec));
     if (!xc || !x) return set_error(FSI_ERR_ARG, "fsi_pressure_prolong_add: NULL argument");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    if (mesh->tet) return amg_prolong_add(mesh, prec, level, xc, x);
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, true));
     PressureMG &P = *mesh->pmg;
@@ -719,6 +754,7 @@ fsi_status fsi_pressure_smooth(fsi_mesh *mesh, fsi_prec prec, int32_t level, int
     if (!b || !x) return set_error(FSI_ERR_ARG, "fsi_pressure_smooth: NULL argument");
     if (degree < 1 || degree > 64) return set_error(FSI_ERR_ARG, "fsi_pressure_smooth: degree 1..64");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    if (mesh->tet) return amg_smooth(mesh, prec, level, degree, b, x, from_zero);
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, false));
     const double hi = mesh->pmg->lev[level].hi;
@@ -751,6 +787,10 @@ fsi_status fsi_pressure_vcycle(fsi_mesh *mesh, fsi_prec prec, const void *b, voi
     if (!b || !x) return set_error(FSI_ERR_ARG, "fsi_pressure_vcycle: NULL argument");
     if (b == x) return set_error(FSI_ERR_ARG, "fsi_pressure_vcycle: b and x must not alias");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    if (mesh->tet) {
+        if (prec == FSI_F64) return amg_vcycle<double>(mesh, (const double *)b, (double *)x);
+        return amg_vcycle<float>(mesh, (const float *)b, (float *)x);
+    }
     if (prec == FSI_F64) return pmg_vcycle<double>(mesh, (const double *)b, (double *)x);
     return pmg_vcycle<float>(mesh, (const float *)b, (float *)x);
 }

@@ -229,6 +229,7 @@ void fsi_mesh_destroy(fsi_mesh *m)
     cudaFree(m->spread_scratch);
     destroy_newton_workspace(m);
     destroy_pmg(m);
+    destroy_amg(m);
     cudaFree(m->coords64);
     cudaFree(m->coords32);
     if (m->tet) fsi_tetmesh_destroy(m->tet);

@@ -701,6 +701,34 @@ const int32_t *tet_colors(const fsi_tetmesh *t, int *n_colors)
     return t->colors;
 }
 
+fsi_status tet_download(fsi_tetmesh *t, std::vector<double> &X, std::vector<int32_t> &tets,
+                        double box_lo[3], double box_hi[3])
+{
+    std::vector<double4> x4((size_t)t->n_nodes);
+    tets.resize((size_t)t->n_elems * 4);
+    FSI_CUDA(cudaMemcpyAsync(x4.data(), t->X64, x4.size() * sizeof(double4), cudaMemcpyDeviceToHost,
+                             t->stream),
+             "memcpy");
+    FSI_CUDA(cudaMemcpyAsync(tets.data(), t->tets, tets.size() * sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, t->stream),
+             "memcpy");
+    FSI_CUDA(cudaStreamSynchronize(t->stream), "sync");
+    X.resize((size_t)t->n_nodes * 3);
+    for (int k = 0; k < 3; ++k) {
+        box_lo[k] = INFINITY;
+        box_hi[k] = -INFINITY;
+    }
+    for (int64_t i = 0; i < t->n_nodes; ++i) {
+        const double v[3] = {x4[i].x, x4[i].y, x4[i].z};
+        for (int k = 0; k < 3; ++k) {
+            X[3 * i + k] = v[k];
+            box_lo[k] = std::min(box_lo[k], v[k]);
+            box_hi[k] = std::max(box_hi[k], v[k]);
+        }
+    }
+    return FSI_OK;
+}
+
 }  // namespace fsi
 
 using namespace fsi;

@@ -1,6 +1,6 @@
 """Plant plausible mistakes in a copy of the Python oracle modules (the
-immersed solid, the Schur preconditioner's pressure multigrid and the
-interface band) and check that their pins catch each one.  The oracle package
+immersed solid, the Schur preconditioner's pressure multigrid, the
+tetrahedral pressure operator and the interface band) and check that their pins catch each one.  The oracle package
 and the pin files are copied to a temporary directory and patched there; the
 committed oracle is never modified."""
 import os
@@ -35,6 +35,16 @@ MUTATIONS = {
                                      "rho_new = 1.0 / (2.0 * s1 + rho)", "test_oracle_precond.py"),
     "precond_sigma_chain": ("precond.py", "return af * gm * dt / (am * rho)",
                             "return gm * dt / (am * rho)", "test_oracle_precond.py"),
+    "tet_pressure_mass_diagonal": ("tet.py", "(np.ones((4, 4)) + np.eye(4))[None] / 20.0",
+                                   "np.ones((4, 4))[None] / 20.0", "test_oracle_tet_pressure.py"),
+    "tet_pressure_gradient_index": ("tet.py", "grad = np.transpose(C[:, 1:, :], (0, 2, 1))",
+                                    "grad = C[:, :, 1:]", "test_oracle_tet_pressure.py"),
+    "tet_pressure_volume_factor": ("tet.py", "V = np.abs(np.linalg.det(M4)) / 6.0",
+                                   "V = np.abs(np.linalg.det(M4)) / 2.0",
+                                   "test_oracle_tet_pressure.py"),
+    "tet_pressure_elimination_rows_only": (
+        "tet.py", "keep = (A.row == A.col) | ~(el[A.row] | el[A.col])",
+        "keep = (A.row == A.col) | ~el[A.row]", "test_oracle_tet_pressure.py"),
     "band_dilation_short": ("interface.py", "max(0, i - layers):min(Nx, i + layers + 1)",
                             "max(0, i - layers):min(Nx, i + layers)", "test_oracle_interface.py"),
     "band_lower_corner_only": ("interface.py", "on[dk:dk + Nz, dj:dj + Ny, di:di + Nx] |= band",
