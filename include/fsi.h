@@ -241,7 +241,14 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
  * as inside when |xi_k| <= 1 + 1e-10).  Interpolation and spreading only
  * need (elem, xi) and work unchanged.  The nominal N, x0, h of the mesh stay
  * in use for the walk's start and the Schur preconditioner's pressure
- * operator (an approximation there).  Synchronises the mesh stream.        */
+ * operator (an approximation there).  Synchronises the mesh stream.  The
+ * geometry of the Gauss points (J^-1, G, G:G, 1/tr G, det J: 18 values per
+ * point) is computed once per compute type, on the first residual or
+ * Jacobian apply in it, into a table kept with the mesh (E x 144 values:
+ * 8 bytes each for FSI_F64 and FSI_DF64, 4 for FSI_F32) and dropped by the
+ * next call of this function; that first apply allocates, so it must not run
+ * inside a stream capture (FSI_ERR_ARG then; FSI_ERR_OOM if the table does
+ * not fit).                                                                */
 fsi_status fsi_mesh_set_coordinates(fsi_mesh *mesh, const double *X);
 
 /* ----------------------------------------------------------------------- */

@@ -87,6 +87,9 @@ struct fsi_mesh {
     // mapped grid: node coordinates padded to [n][4], FP64 and FP32 copies
     // (null on the uniform grid)
     void *coords64, *coords32;
+    // mapped grid: per-Gauss-point geometry tables [double, float, double-float],
+    // built on first use, dropped when the coordinates change (vms.cu)
+    void *map_geo[3];
     // unstructured tetrahedral mesh behind this handle (fsi_mesh_create_tet);
     // null for the structured grid
     fsi_tetmesh *tet;

@@ -232,6 +232,7 @@ void fsi_mesh_destroy(fsi_mesh *m)
     destroy_amg(m);
     cudaFree(m->coords64);
     cudaFree(m->coords32);
+    for (void *g : m->map_geo) cudaFree(g);
     if (m->tet) fsi_tetmesh_destroy(m->tet);
     delete m;
 }
@@ -262,6 +263,10 @@ fsi_status fsi_mesh_set_coordinates(fsi_mesh *m, const double *X)
     FSI_TRY(require_structured(m, "fsi_mesh_set_coordinates"));
     FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
     FSI_CUDA(cudaStreamSynchronize(m->stream), "sync");
+    for (void *&g : m->map_geo) {
+        cudaFree(g);
+        g = nullptr;
+    }
     if (!X) {
         cudaFree(m->coords64);
         cudaFree(m->coords32);

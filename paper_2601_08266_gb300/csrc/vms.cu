@@ -39,13 +39,72 @@ __global__ void __launch_bounds__(256) vms_brick_kernel(const VmsArgs<T> P)
 }
 
 // The same, held to 128 registers (two 256-thread CTAs per SM): used for the
-// mapped double-float kernels, whose Jacobian otherwise takes 185 registers
-// and runs 1.5x slower at one CTA per SM.
+// mapped double-float kernels, whose Jacobian otherwise takes more registers
+// and runs 1.2x slower at one CTA per SM.
 template <typename T, bool JAC, bool MAPPED>
 __global__ void __launch_bounds__(256, 2) vms_brick_kernel_capped(const VmsArgs<T> P)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     brick_body<T, JAC, MAPPED>(P, blockIdx.x, reinterpret_cast<vec4<T> *>(smem_raw));
+}
+
+// Geometry table of a mapped grid: 8 lanes per element (lane = node, then
+// Gauss point), the same butterfly as the VMS kernels.  The loop bound is
+// uniform over the block, so every lane reaches every shuffle.
+template <typename T>
+__global__ void __launch_bounds__(256) mapped_geo_kernel(const VmsArgs<T> P,
+                                                         typename GeoStore<T>::type *tab)
+{
+    const int g = threadIdx.x & 7;
+    const int gx = g & 1, gy = (g >> 1) & 1, gz = (g >> 2) & 1;
+    const T sx = gx ? T(0.5f) : T(-0.5f), sy = gy ? T(0.5f) : T(-0.5f),
+            sz = gz ? T(0.5f) : T(-0.5f);
+    const int64_t E = (int64_t)P.Nx * P.Ny * P.Nz;
+    const int64_t NX1 = P.Nx + 1, NXY1 = NX1 * (P.Ny + 1);
+    const int64_t per_block = blockDim.x >> 3, stride = (int64_t)gridDim.x * per_block;
+    for (int64_t base = blockIdx.x * per_block; base < E; base += stride) {
+        const int64_t e = base + (threadIdx.x >> 3);
+        const bool valid = e < E;
+        const int64_t ex = valid ? e % P.Nx : 0, ey = valid ? (e / P.Nx) % P.Ny : 0,
+                      ez = valid ? e / ((int64_t)P.Nx * P.Ny) : 0;
+        const int64_t node = (ex + gx) + NX1 * (ey + gy) + NXY1 * (ez + gz);
+        const vec4<T> xc = valid ? load_c<T>(P.Xc + node)
+                                 : vec4<T>{gx ? T(1) : T(0), gy ? T(1) : T(0), gz ? T(1) : T(0), T(0)};
+        T out[kMapGeo];
+        mapped_geometry<false>(xc, sx, sy, sz, out);
+        if (valid)
+#pragma unroll
+            for (int k = 0; k < kMapGeo; ++k) tab[e * (kMapGeo * 8) + 8 * k + g] = geo_st(out[k]);
+    }
+}
+
+template <typename T> constexpr int geo_slot()
+{
+    return std::is_same<T, double>::value ? 0 : (std::is_same<T, float>::value ? 1 : 2);
+}
+
+// the geometry table of compute type T for the current coordinates, built on
+// first use (it allocates: not inside a stream capture)
+template <typename T> fsi_status ensure_map_geo(fsi_mesh *m, const VmsArgs<T> &P)
+{
+    void *&tab = m->map_geo[geo_slot<T>()];
+    if (tab) return FSI_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FSI_CUDA(cudaStreamIsCapturing(m->stream, &cap), "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+        return set_error(FSI_ERR_ARG, "mapped-grid geometry table: first use of this compute "
+                                      "type inside a stream capture");
+    const size_t bytes = (size_t)m->n_elems * kMapGeo * 8 * sizeof(typename GeoStore<T>::type);
+    if (cudaMalloc(&tab, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        tab = nullptr;
+        return set_error(FSI_ERR_OOM, "mapped-grid geometry table: cudaMalloc of %zu bytes failed",
+                         bytes);
+    }
+    int64_t blocks = (m->n_elems + 31) / 32;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    mapped_geo_kernel<T><<<(int)blocks, 256, 0, m->stream>>>(P, (typename GeoStore<T>::type *)tab);
+    return check_launch("mapped geometry kernel");
 }
 
 template <typename T> __global__ void vms_gather_kernel(const VmsArgs<T> P)
@@ -63,6 +122,10 @@ fsi_status launch_geo(fsi_mesh *m, const void *U, const void *A, const void *f, 
     const Brick &b = m->brick[JAC ? 1 : 0][sizeof(typename StorageOf<T>::type) == 8 ? FSI_F64 : FSI_F32];
     FSI_TRY(ensure_vms_scratch(m, b, sizeof(T)));
     VmsArgs<T> P = make_args<T>(m, b, U, A, f, x, out);
+    if constexpr (MAPPED) {
+        FSI_TRY(ensure_map_geo<T>(m, P));
+        P.geo = (const typename GeoStore<T>::type *)m->map_geo[geo_slot<T>()];
+    }
     const int nbricks = P.nbx * P.nby * P.nbz;
     const size_t smem = (size_t)b.bx * b.by * b.bz * 8 * sizeof(vec4<typename StorageOf<T>::type>);
     void (*kernel)(const VmsArgs<T>);
@@ -86,8 +149,8 @@ fsi_status launch_geo(fsi_mesh *m, const void *U, const void *A, const void *f, 
     return check_launch("vms gather kernel");
 }
 
-// the mapped-grid kernels take the geometry of every Gauss point from the
-// node coordinates (set by fsi_mesh_set_coordinates)
+// the mapped-grid kernels take the geometry of every Gauss point from a table
+// built from the node coordinates (set by fsi_mesh_set_coordinates)
 template <typename T, bool JAC>
 fsi_status launch(fsi_mesh *m, const void *U, const void *A, const void *f, const void *x,
                   void *out)

@@ -39,6 +39,30 @@ template <> __device__ __forceinline__ vec4<df64> ld4_blk<df64>(const vec4<df64>
     return ld4_df(p);
 }
 
+// Per-Gauss-point geometry of a mapped grid, built once per coordinate set and
+// compute type and read by the VMS kernels: Ji[9] (row-major), G00 G01 G02 G11
+// G12 G22, G:G, 1/tr G, det J.  Layout [element][value][Gauss point], so the 8
+// lanes of an element read 8 consecutive entries per value.  Double-float
+// entries are stored as (hi, lo) float pairs.
+constexpr int kMapGeo = 18;
+template <typename T> struct GeoStore {
+    using type = T;
+};
+template <> struct GeoStore<df64> {
+    using type = float2;
+};
+template <typename T> __device__ __forceinline__ T geo_ld(const typename GeoStore<T>::type *p)
+{
+    return __ldg(p);
+}
+template <> __device__ __forceinline__ df64 geo_ld<df64>(const float2 *p)
+{
+    const float2 v = __ldg(p);
+    return df64(v.x, v.y);
+}
+template <typename T> __device__ __forceinline__ typename GeoStore<T>::type geo_st(T v) { return v; }
+template <> __device__ __forceinline__ float2 geo_st<df64>(df64 v) { return make_float2(v.hi, v.lo); }
+
 template <typename T> struct VmsArgs {
     using S = typename StorageOf<T>::type;
     int Nx, Ny, Nz;
@@ -52,6 +76,7 @@ template <typename T> struct VmsArgs {
     T ct_dt2, CInu2;            // C_T/dt^2 and C_I (mu/rho)^2 (mapped grids: G per Gauss point)
     int has_s;
     const vec4<S> *Xc;          // mapped grids: node coordinates [n][4] (x, y, z, 0), else null
+    const typename GeoStore<T>::type *geo;  // mapped grids: [E][kMapGeo][8] Gauss-point geometry
     const vec4<S> *U, *A, *f, *x;
     vec4<T> *blocks;  // [n_bricks][(bx+1)(by+1)(bz+1)], in the compute type
     vec4<S> *out;     // [n]
@@ -195,7 +220,8 @@ __device__ __forceinline__ T project_body(T X, T Yx, T Yy, T Yz, T sx, T sy, T s
 // 4 + 4 call sites the double-float Jacobian body outgrows what the
 // instruction cache holds for its 16 warps per SM (out of line: -6 % at 64^3,
 // -12 % at 128^3); the shorter residual body is faster inlined (+3-5 %
-// out of line), except on mapped grids.  float and double always inline.
+// out of line; 6 % on mapped grids, whose geometry comes from a table).
+// float and double always inline.
 template <typename T> __device__ __noinline__ VG<T> eval_vg_ool(T u, T sx, T sy, T sz)
 {
     return eval_vg_body(u, sx, sy, sz);
@@ -358,6 +384,51 @@ __device__ __forceinline__ void to_phys(const Geo<T> &geo, VG<T> &e)
     e.gz = a * geo.Ji[0][2] + b * geo.Ji[1][2] + c * geo.Ji[2][2];
 }
 
+// Geometry at this lane's Gauss point from the node coordinates xc of the
+// element (lane = node on entry): J = dx/dxi by the butterfly (sx, sy, sz the
+// reference gradient signs +-1/2), Ji by cofactors, G = Ji^T Ji, G:G, 1/tr G.
+template <bool OUT, typename T>
+__device__ __forceinline__ void mapped_geometry(const vec4<T> &xc, T sx, T sy, T sz,
+                                                T (&out)[kMapGeo])
+{
+    VG<T> cx, cy, cz, cw;
+    eval_vg4<OUT>(xc, sx, sy, sz, cx, cy, cz, cw);
+    const T J[3][3] = {{cx.gx, cx.gy, cx.gz}, {cy.gx, cy.gy, cy.gz}, {cz.gx, cz.gy, cz.gz}};
+    const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const T c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const T det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    const T id = inv_t(det);
+    T Ji[3][3];
+    Ji[0][0] = c00 * id;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+    Ji[1][0] = c01 * id;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+    Ji[2][0] = c02 * id;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+    T G[3][3], GG = T(0);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const T gij = Ji[0][i] * Ji[0][j] + Ji[1][i] * Ji[1][j] + Ji[2][i] * Ji[2][j];
+            G[i][j] = gij;
+            GG += gij * gij;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) out[3 * i + j] = Ji[i][j];
+    out[9] = G[0][0];
+    out[10] = G[0][1];
+    out[11] = G[0][2];
+    out[12] = G[1][1];
+    out[13] = G[1][2];
+    out[14] = G[2][2];
+    out[15] = GG;
+    out[16] = inv_t(G[0][0] + G[1][1] + G[2][2]);
+    out[17] = det;
+}
+
 // Test-function coefficients of the residual at one quadrature point: X
 // multiplies N_A, Y[c][j] multiplies dN_A/dx_j for residual component c.
 template <typename T>
@@ -424,7 +495,7 @@ __device__ __forceinline__ void gp_jacobian_terms(const VmsArgs<T> &P, const GP<
 template <typename T, bool JAC, bool MAPPED = false>
 __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<T> *rel)
 {
-    constexpr bool OUT = JAC || MAPPED;  // out-of-line double-float evaluation
+    constexpr bool OUT = JAC;  // out-of-line double-float evaluation
     const int g = threadIdx.x & 7;
     const int bxi = brick % P.nbx, byi = (brick / P.nbx) % P.nby, bzi = brick / (P.nbx * P.nby);
     const int ex0 = bxi * P.bx, ey0 = byi * P.by, ez0 = bzi * P.bz;
@@ -455,37 +526,32 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
 
         Geo<T> geo;
         if constexpr (MAPPED) {
-            // dx_c/dxi_k at this lane's Gauss point; idle lanes take a unit cell
-            vec4<T> xc = valid ? load_c<T>(P.Xc + node)
-                               : vec4<T>{gx ? T(1) : T(0), gy ? T(1) : T(0), gz ? T(1) : T(0), T(0)};
-            VG<T> cx, cy, cz, cw;
-            eval_vg4<OUT>(xc, sx, sy, sz, cx, cy, cz, cw);
-            const T J[3][3] = {{cx.gx, cx.gy, cx.gz}, {cy.gx, cy.gy, cy.gz}, {cz.gx, cz.gy, cz.gz}};
-            const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-            const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-            const T c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-            geo.det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-            const T id = inv_t(geo.det);
-            geo.Ji[0][0] = c00 * id;
-            geo.Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
-            geo.Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
-            geo.Ji[1][0] = c01 * id;
-            geo.Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
-            geo.Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
-            geo.Ji[2][0] = c02 * id;
-            geo.Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
-            geo.Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
-            T trG = T(0), GG = T(0);
+            // this lane's Gauss point from the geometry table; idle lanes
+            // take the identity (their result is discarded)
+            T gt[kMapGeo];
+            if (valid) {
+                const int64_t e = ex + (int64_t)P.Nx * (ey + (int64_t)P.Ny * ez);
+                const typename GeoStore<T>::type *gp = P.geo + e * (kMapGeo * 8) + g;
+#pragma unroll
+                for (int k = 0; k < kMapGeo; ++k) gt[k] = geo_ld<T>(gp + 8 * k);
+            } else {
+#pragma unroll
+                for (int k = 0; k < kMapGeo; ++k) gt[k] = T(0);
+                gt[0] = gt[4] = gt[8] = gt[9] = gt[12] = gt[14] = gt[17] = T(1);
+                gt[15] = T(3);
+                gt[16] = T(1.0f / 3.0f);
+            }
             for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) {
-                    const T gij = geo.Ji[0][i] * geo.Ji[0][j] + geo.Ji[1][i] * geo.Ji[1][j] +
-                                  geo.Ji[2][i] * geo.Ji[2][j];
-                    geo.G[i][j] = gij;
-                    GG += gij * gij;
-                }
-            trG = geo.G[0][0] + geo.G[1][1] + geo.G[2][2];
-            geo.inv_trG = inv_t(trG);
-            geo.q0 = P.ct_dt2 + P.CInu2 * GG;
+                for (int j = 0; j < 3; ++j) geo.Ji[i][j] = gt[3 * i + j];
+            geo.G[0][0] = gt[9];
+            geo.G[0][1] = geo.G[1][0] = gt[10];
+            geo.G[0][2] = geo.G[2][0] = gt[11];
+            geo.G[1][1] = gt[12];
+            geo.G[1][2] = geo.G[2][1] = gt[13];
+            geo.G[2][2] = gt[14];
+            geo.q0 = P.ct_dt2 + P.CInu2 * gt[15];
+            geo.inv_trG = gt[16];
+            geo.det = gt[17];
         }
         GP<T> q;
         {
@@ -695,6 +761,7 @@ VmsArgs<T> make_args(const fsi_mesh *m, const Brick &b, const void *U, const voi
     P.has_s = m->phys.has_s != 0;
     using S = typename StorageOf<T>::type;
     P.Xc = (const vec4<S> *)(sizeof(S) == 8 ? m->coords64 : m->coords32);
+    P.geo = nullptr;
     P.U = (const vec4<S> *)U;
     P.A = (const vec4<S> *)A;
     P.f = (const vec4<S> *)f;

@@ -156,6 +156,31 @@ def test_uniform_coordinates_reproduce_the_uniform_kernels(fsi, oracle):
     assert rel(Ju, core.jacobian_apply(grid, p, U, A, x, c_a, c_v, f=f)) < 1e-12
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64"])
+def test_geometry_follows_new_coordinates_and_physics(fsi, oracle, prec):
+    """The per-Gauss-point geometry table is rebuilt when the coordinates
+    change and stays valid when only the physics changes."""
+    core = oracle.core
+    N = (6, 5, 7)
+    X1 = distorted(core, N, seed=31)
+    X2 = distorted(core, N, seed=32, amp=0.2)
+    mesh, p = mapped_mesh(fsi, N, X1, has_s=True)
+    n = mesh.n_nodes
+    rng = np.random.default_rng(33)
+    U, A, x = (cast(prec, rng.normal(size=(n, 4))) for _ in range(3))
+    A[:, 3] = cast(prec, rng.uniform(1.0, 3.0, n))
+    for X, phys in ((X1, {}), (X2, {}), (X2, dict(mu=0.05, dt=0.02)), (X1, dict(mu=0.05, dt=0.02))):
+        if phys:
+            mesh.set_physics(**phys)
+            p.update(phys)
+        mesh.set_coordinates(T(X))
+        grid = core.Grid(N, coords=cast(prec, X))
+        R, Jx = vms(fsi, mesh, prec, U, A, None, x)
+        c_a, c_v = oracle.timeint.chain_factors(p["rho_inf"], p["dt"])
+        assert rel(R, core.residual(grid, p, U, A)) < TOL[prec]
+        assert rel(Jx, core.jacobian_apply(grid, p, U, A, x, c_a, c_v)) < TOL[prec]
+
+
 def element_nodes(N, e):
     ex, ey, ez = e % N[0], (e // N[0]) % N[1], e // (N[0] * N[1])
     return [(ex + (a & 1)) + (N[0] + 1) * ((ey + ((a >> 1) & 1)) + (N[1] + 1) * (ez + ((a >> 2) & 1)))
