@@ -1105,11 +1105,13 @@ def tet_section(args, dev, stream):
     out["spread_df64_ms"] = timeit(lambda: fsi.fsi_tet_spread(mesh, fsi.FSI_DF64, e, lam, cs, pm,
                                                               lv, None, F, False))
     mesh.close()
-    out["newton_channel"] = tet_newton(fsi, dev, stream)
+    out["newton_channel"] = tet_newton(fsi, dev, stream,
+                                       variants=args.tet_newton_variants.split(","))
     return out
 
 
-def tet_newton(fsi, dev, stream, N=32, m=50_000):
+def tet_newton(fsi, dev, stream, N=32, m=50_000, variants=("fp64", "mixed", "schur_fp64",
+                                                          "schur_mixed")):
     """One implicit step of the channel flow (inflow 16 y(1-y) z(1-z) at x = 0,
     no-slip walls, traction-free outflow, mu = 1e-3, dt = 1e-3) on a
     tetrahedral mesh (32^3 cubes x 6, shuffled numbering) with leaflet points:
@@ -1167,6 +1169,8 @@ def tet_newton(fsi, dev, stream, N=32, m=50_000):
     runs = (("fp64", False, fsi.PRECOND_BLOCK_JACOBI), ("mixed", True, fsi.PRECOND_BLOCK_JACOBI),
             ("schur_fp64", False, fsi.PRECOND_SCHUR), ("schur_mixed", True, fsi.PRECOND_SCHUR))
     for name, mixed, precond in runs:
+        if name not in variants:
+            continue
         with torch.cuda.stream(stream):
             yv = torch.zeros((n, 4), dtype=torch.float64, device=dev)
             yv[md.bool()] = yDd[md.bool()]
@@ -1184,8 +1188,10 @@ def tet_newton(fsi, dev, stream, N=32, m=50_000):
                      "krylov_iters": rep["krylov_iters"],
                      "r_final_over_ref": rep["r_final"] / r_ref,
                      "converged": bool(rep["converged"]), "status": code}
-    out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
-    out["speedup_schur_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["schur_mixed"]["seconds"]
+    if "fp64" in out and "mixed" in out:
+        out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    if "fp64" in out and "schur_mixed" in out:
+        out["speedup_schur_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["schur_mixed"]["seconds"]
     out["pressure_levels"] = fsi.fsi_pressure_level_sizes(mesh)
     mesh.close()
     return out
@@ -1281,6 +1287,8 @@ def main():
     ap.add_argument("--newton-variants",
                     default="fp64,mixed_zero_guess,mixed,mixed_learned,mixed_block_jacobi",
                     help="comma-separated Newton variants to time")
+    ap.add_argument("--tet-newton-variants", default="fp64,mixed,schur_fp64,schur_mixed",
+                    help="comma-separated Newton runs of the tetrahedral channel step")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--batch-tune-f64", action="store_true")

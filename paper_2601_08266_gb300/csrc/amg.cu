@@ -31,8 +31,10 @@
 //               degree 8 over [hi/30, hi] when the last level is larger.
 //
 // The V-cycle is a fixed symmetric linear operator.  Each level is a CSR
-// matrix kept on the device in FP64 and FP32; one thread per row, rows in a
-// fixed order, so every result is deterministic.
+// matrix kept on the device in FP64 and FP32; a row is summed by a group of
+// w lanes (w the power of two that gives about four entries per lane, at
+// most a warp), each lane over every w-th entry, then a fixed butterfly, so
+// every result is deterministic.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -53,6 +55,7 @@ constexpr int kAmgPowerIts = 30;
 
 struct AmgCsr {
     int64_t rows = 0, nnz = 0;
+    int w = 1;  // lanes per row of the SpMV kernels: ~4 entries per lane
     int32_t *ptr = nullptr, *col = nullptr;
     double *v64 = nullptr;
     float *v32 = nullptr;
@@ -408,6 +411,8 @@ bool upload_csr(AmgCsr &D, const HostCsr &H)
 {
     D.rows = H.rows;
     D.nnz = (int64_t)H.col.size();
+    D.w = 1;
+    while (D.w < 32 && 4 * D.w * std::max<int64_t>(D.rows, 1) < D.nnz) D.w *= 2;
     std::vector<int32_t> ptr(H.ptr.begin(), H.ptr.end());
     std::vector<float> v32(H.val.begin(), H.val.end());
     int32_t dummy = 0;
@@ -452,21 +457,34 @@ template <typename T> struct Csr {
     const int32_t *__restrict__ ptr;
     const int32_t *__restrict__ col;
     const T *__restrict__ val;
+    int w;  // lanes per row
 };
 
 template <typename T> Csr<T> csr(const AmgCsr &A)
 {
     return {A.rows, A.ptr, A.col,
-            std::is_same<T, double>::value ? (const T *)A.v64 : (const T *)A.v32};
+            std::is_same<T, double>::value ? (const T *)A.v64 : (const T *)A.v32, A.w};
 }
 template <typename T> const T *dinv(const AmgLevel &L)
 {
     return std::is_same<T, double>::value ? (const T *)L.dinv64 : (const T *)L.dinv32;
 }
 
-#define AMG_ROWS(i, n)                                                              \
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n);      \
-         i += (int64_t)gridDim.x * blockDim.x)
+// Rows in groups of w lanes (w a power of two, <= 32): a warp takes 32 / w
+// consecutive rows per pass, and every lane of a warp makes the same number
+// of passes, so the shuffles of the row sums always see the whole warp.
+struct RowGroups {
+    int lane, sub;        // lane within the row's group, group within the warp
+    int64_t base0, step;  // first row of the warp's first pass, rows per pass of the grid
+};
+__device__ __forceinline__ RowGroups row_groups(int w)
+{
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int rpw = 32 / w;
+    return {(int)(threadIdx.x & (w - 1)), (int)((threadIdx.x & 31) / w), warp * rpw,
+            nwarps * rpw};
+}
 
 template <typename T>
 __device__ __forceinline__ T val(const T *__restrict__ x, const T *__restrict__ d, int64_t q)
@@ -474,14 +492,19 @@ __device__ __forceinline__ T val(const T *__restrict__ x, const T *__restrict__ 
     return x ? (d ? x[q] + d[q] : x[q]) : d[q];
 }
 
-// (A v)_i, v = x + d (x == null: v = d; d == null: v = x)
+// (A v)_i, v = x + d (x == null: v = d; d == null: v = x): the row's lanes
+// take every w-th entry, then a butterfly gives every lane the row sum (fixed
+// order for a given w)
 template <typename T>
-__device__ __forceinline__ T row_apply(const Csr<T> &A, int64_t i, const T *__restrict__ x,
-                                       const T *__restrict__ d)
+__device__ __forceinline__ T row_apply(const Csr<T> &A, int64_t i, bool valid, int lane,
+                                       const T *__restrict__ x, const T *__restrict__ d)
 {
     T s = T(0);
-    const int32_t q1 = A.ptr[i + 1];
-    for (int32_t q = A.ptr[i]; q < q1; ++q) s += A.val[q] * val(x, d, A.col[q]);
+    if (valid) {
+        const int32_t q1 = A.ptr[i + 1];
+        for (int32_t q = A.ptr[i] + lane; q < q1; q += A.w) s += A.val[q] * val(x, d, A.col[q]);
+    }
+    for (int o = A.w >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
 }
 
@@ -490,10 +513,13 @@ template <typename T>
 __global__ void csr_apply_kernel(Csr<T> A, const T *__restrict__ x, const T *__restrict__ b,
                                  T *__restrict__ y)
 {
-    AMG_ROWS(i, A.n)
-    {
-        const T ax = row_apply(A, i, x, (const T *)nullptr);
-        y[i] = b ? b[i] - ax : ax;
+    const RowGroups G = row_groups(A.w);
+    const int lane = G.lane;
+    for (int64_t base = G.base0; base < A.n; base += G.step) {
+        const int64_t i = base + G.sub;
+        const bool valid = i < A.n;
+        const T ax = row_apply(A, i, valid, lane, x, (const T *)nullptr);
+        if (valid && lane == 0) y[i] = b ? b[i] - ax : ax;
     }
 }
 
@@ -501,7 +527,14 @@ __global__ void csr_apply_kernel(Csr<T> A, const T *__restrict__ x, const T *__r
 template <typename T>
 __global__ void csr_apply_add_kernel(Csr<T> A, const T *__restrict__ x, T *__restrict__ y)
 {
-    AMG_ROWS(i, A.n) y[i] += row_apply(A, i, x, (const T *)nullptr);
+    const RowGroups G = row_groups(A.w);
+    const int lane = G.lane;
+    for (int64_t base = G.base0; base < A.n; base += G.step) {
+        const int64_t i = base + G.sub;
+        const bool valid = i < A.n;
+        const T ax = row_apply(A, i, valid, lane, x, (const T *)nullptr);
+        if (valid && lane == 0) y[i] += ax;
+    }
 }
 
 // Chebyshev, first direction d0 = D^-1 (b - A x) / theta (x == null: x = 0);
@@ -511,14 +544,20 @@ __global__ void amg_cheb0_kernel(Csr<T> A, const T *__restrict__ dinv, const T *
                                  const T *__restrict__ x, T inv_theta, T *__restrict__ d_out,
                                  T *__restrict__ x_out)
 {
-    AMG_ROWS(i, A.n)
-    {
-        const T r = x ? b[i] - row_apply(A, i, x, (const T *)nullptr) : b[i];
-        const T d0 = inv_theta * r * dinv[i];
-        if (x_out)
-            x_out[i] = x ? x[i] + d0 : d0;
-        else
-            d_out[i] = d0;
+    const RowGroups G = row_groups(A.w);
+    const int lane = G.lane;
+    for (int64_t base = G.base0; base < A.n; base += G.step) {
+        const int64_t i = base + G.sub;
+        const bool valid = i < A.n;
+        const T ax = x ? row_apply(A, i, valid, lane, x, (const T *)nullptr) : T(0);
+        if (valid && lane == 0) {
+            const T r = x ? b[i] - ax : b[i];
+            const T d0 = inv_theta * r * dinv[i];
+            if (x_out)
+                x_out[i] = x ? x[i] + d0 : d0;
+            else
+                d_out[i] = d0;
+        }
     }
 }
 
@@ -530,23 +569,31 @@ __global__ void amg_cheb_step_kernel(Csr<T> A, const T *__restrict__ dinv, const
                                      T *__restrict__ x_next, T *__restrict__ d_next,
                                      T *__restrict__ x_final)
 {
-    AMG_ROWS(i, A.n)
-    {
-        const T xk = val(x, d, i);
-        const T r = b[i] - row_apply(A, i, x, d);
-        const T dn = c1 * d[i] + c2 * (r * dinv[i]);
-        if (x_final) {
-            x_final[i] = xk + dn;
-        } else {
-            x_next[i] = xk;
-            d_next[i] = dn;
+    const RowGroups G = row_groups(A.w);
+    const int lane = G.lane;
+    for (int64_t base = G.base0; base < A.n; base += G.step) {
+        const int64_t i = base + G.sub;
+        const bool valid = i < A.n;
+        const T ax = row_apply(A, i, valid, lane, x, d);
+        if (valid && lane == 0) {
+            const T xk = val(x, d, i);
+            const T r = b[i] - ax;
+            const T dn = c1 * d[i] + c2 * (r * dinv[i]);
+            if (x_final) {
+                x_final[i] = xk + dn;
+            } else {
+                x_next[i] = xk;
+                d_next[i] = dn;
+            }
         }
     }
 }
 
 template <typename T> __global__ void amg_copy_kernel(int64_t n, const T *a, T *b)
 {
-    AMG_ROWS(i, n) b[i] = a[i];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
 }
 
 // x = Ainv b on the coarsest level: one warp per row, fixed reduction order
@@ -566,6 +613,8 @@ __global__ void amg_dense_kernel(int64_t nc, const T *__restrict__ Ainv, const T
 }
 
 int rows_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+// blocks of 256 threads for n rows in groups of w lanes
+int rows_grid(const AmgCsr &A) { return rows_grid(A.rows * A.w); }
 
 template <typename T> T *vec(void *p) { return static_cast<T *>(p); }
 
@@ -577,7 +626,7 @@ fsi_status chebyshev(fsi_mesh *m, int l, int degree, double lo, double hi, const
     const Csr<T> A = csr<T>(L.A);
     const T *di = dinv<T>(L);
     cudaStream_t s = m->stream;
-    const int g = rows_grid(L.n);
+    const int g = rows_grid(L.A);
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), s1 = theta / delta;
     if (degree == 1) {
         amg_cheb0_kernel<T><<<g, 256, 0, s>>>(A, di, b, x_in, (T)(1.0 / theta), nullptr, x_out);
@@ -623,12 +672,12 @@ template <typename T> fsi_status vcycle_level(fsi_mesh *m, int l, const T *b, T 
     const double hi = L.hi, lo = hi / kAmgLoRatio;
     T *t = vec<T>(L.t);
     FSI_TRY(chebyshev<T>(m, l, kAmgNu, lo, hi, b, (const T *)nullptr, t));
-    csr_apply_kernel<T><<<rows_grid(L.n), 256, 0, m->stream>>>(csr<T>(L.A), t, b, vec<T>(L.r));
-    csr_apply_kernel<T><<<rows_grid(Lc.n), 256, 0, m->stream>>>(csr<T>(L.R), vec<T>(L.r),
+    csr_apply_kernel<T><<<rows_grid(L.A), 256, 0, m->stream>>>(csr<T>(L.A), t, b, vec<T>(L.r));
+    csr_apply_kernel<T><<<rows_grid(L.R), 256, 0, m->stream>>>(csr<T>(L.R), vec<T>(L.r),
                                                                  (const T *)nullptr, vec<T>(Lc.b));
     FSI_TRY(check_launch("pressure AMG restrict"));
     FSI_TRY(vcycle_level<T>(m, l + 1, vec<T>(Lc.b), vec<T>(Lc.x)));
-    csr_apply_add_kernel<T><<<rows_grid(L.n), 256, 0, m->stream>>>(csr<T>(L.P), vec<T>(Lc.x), t);
+    csr_apply_add_kernel<T><<<rows_grid(L.P), 256, 0, m->stream>>>(csr<T>(L.P), vec<T>(Lc.x), t);
     FSI_TRY(check_launch("pressure AMG prolong"));
     return chebyshev<T>(m, l, kAmgNu, lo, hi, b, t, x);
 }
@@ -871,10 +920,10 @@ fsi_status amg_apply(fsi_mesh *m, fsi_prec prec, int level, const void *x, void 
     FSI_TRY(check_level(m, level, false));
     const AmgLevel &L = m->amg->lev[level];
     if (prec == FSI_F64)
-        csr_apply_kernel<double><<<rows_grid(L.n), 256, 0, m->stream>>>(
+        csr_apply_kernel<double><<<rows_grid(L.A), 256, 0, m->stream>>>(
             csr<double>(L.A), (const double *)x, nullptr, (double *)y);
     else
-        csr_apply_kernel<float><<<rows_grid(L.n), 256, 0, m->stream>>>(
+        csr_apply_kernel<float><<<rows_grid(L.A), 256, 0, m->stream>>>(
             csr<float>(L.A), (const float *)x, nullptr, (float *)y);
     return check_launch("pressure AMG apply");
 }
@@ -885,7 +934,7 @@ fsi_status amg_restrict(fsi_mesh *m, fsi_prec prec, int level, const void *r, vo
     FSI_TRY(ensure_built(m));
     FSI_TRY(check_level(m, level, true));
     const AmgLevel &L = m->amg->lev[level];
-    const int g = rows_grid(L.R.rows);
+    const int g = rows_grid(L.R);
     if (prec == FSI_F64)
         csr_apply_kernel<double><<<g, 256, 0, m->stream>>>(csr<double>(L.R), (const double *)r,
                                                            nullptr, (double *)b);
@@ -902,10 +951,10 @@ fsi_status amg_prolong_add(fsi_mesh *m, fsi_prec prec, int level, const void *xc
     FSI_TRY(check_level(m, level, true));
     const AmgLevel &L = m->amg->lev[level];
     if (prec == FSI_F64)
-        csr_apply_add_kernel<double><<<rows_grid(L.n), 256, 0, m->stream>>>(
+        csr_apply_add_kernel<double><<<rows_grid(L.P), 256, 0, m->stream>>>(
             csr<double>(L.P), (const double *)xc, (double *)x);
     else
-        csr_apply_add_kernel<float><<<rows_grid(L.n), 256, 0, m->stream>>>(
+        csr_apply_add_kernel<float><<<rows_grid(L.P), 256, 0, m->stream>>>(
             csr<float>(L.P), (const float *)xc, (float *)x);
     return check_launch("pressure AMG prolong");
 }
