@@ -1,12 +1,15 @@
 // mlp_tc.cu -- fused inference of the initial-guess network on the 5th-
 // generation tensor cores (tcgen05, TMEM accumulators).
 //
-// One persistent CTA per SM (128 threads, ~222 KB shared memory) processes
-// tiles of 128 nodes.  Thread t owns node row t of the tile, which is also
-// TMEM lane t of the accumulators.  Per tile:
+// One persistent CTA per SM (512 threads = four warpgroups, ~223 KB shared
+// memory) processes tiles of 128 nodes.  Node row r of the tile is TMEM lane
+// r of the accumulators; thread t takes row t % 128, and its warpgroup
+// t / 128 takes a quarter of every per-row phase (feature chunks, H1
+// columns, layer-3 columns), so that each SMSP has four warps to switch
+// between.  Per tile:
 //
-//   features   each thread builds its node's 112 features (27-node stencil of
-//              V_n velocity and y_n pressure, the extrapolant 2 d1 - d2),
+//   features   the 112 features of each node (27-node stencil of V_n
+//              velocity and y_n pressure, the extrapolant 2 d1 - d2),
 //              normalised and rounded to BF16, into the A tile X [128 x 112];
 //   layer 1    D1 [128 x 256] (TMEM columns 0..255) = X W1^T: 7 MMAs of
 //              M=128, N=256, K=16 (kind::f16, BF16 in, FP32 accumulate);
@@ -16,9 +19,10 @@
 //              second half is loaded from TMEM into registers while the MMAs of
 //              the first half run;
 //   layer 3    H2 = BF16(ReLU(D2 + b2)) stays in registers; the 4 outputs are
-//              FP32 dot products with the BF16 rows of W3 (+ b3), and the
-//              predictor y0 = y + e + (out_mean + out_std * out) is written in
-//              FP64.
+//              FP32 dot products with the BF16 rows of W3 (+ b3), summed per
+//              warpgroup over its 64 columns and then across warpgroups in a
+//              fixed order; the predictor y0 = y + e + (out_mean + out_std *
+//              out) is written in FP64.
 //
 // The BF16 rounding points are those of the training kernels (inputs and
 // weights of every layer).  Weights are packed once per call into the
@@ -52,6 +56,13 @@ constexpr uint32_t OFF_SW1 = 0, OFF_SW2A = OFF_SW1 + SZ_W1, OFF_SW2B = OFF_SW2A 
 constexpr uint32_t PACKED_BYTES = SZ_W1 + 2 * SZ_W2H;  // 188,416
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long kWaitLimit = 4000000;  // try_wait polls (each suspends briefly)
+// Four warpgroups share every tile: warp w reads TMEM lanes 32 (w % 4) ..
+// (the tile's node rows), so warpgroup g = w / 4 takes the same rows and its
+// share of the columns: feature chunks [kChunk[g], kChunk[g + 1]), H1
+// columns 32 g .. of each K-half, D2 columns 64 g .. of layer 3.
+constexpr int kGroups = 4;
+constexpr int kThreads = 128 * kGroups;
+__constant__ int kChunk[kGroups + 1] = {0, 4, 8, 11, 14};
 
 // byte offset of element (row, k) in a K-major canonical tile with kc chunks
 __host__ __device__ __forceinline__ uint32_t kmaj(uint32_t row, uint32_t k, uint32_t kc)
@@ -182,14 +193,14 @@ struct TcArgs {
     int *err;
 };
 
-__global__ void __launch_bounds__(128, 1) mlp_predict_tc_kernel(const TcArgs a)
+__global__ void __launch_bounds__(kThreads, 1) mlp_predict_tc_kernel(const TcArgs a)
 {
     extern __shared__ __align__(128) uint8_t sm[];
     __shared__ __align__(8) uint64_t bars[2];  // [0] weights, [1] MMA completion
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
     __shared__ float smean[NI], sistd[NI];
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, row = tid & (TM - 1), grp = tid >> 7;
     const uint32_t s0 = smem_u32(sm);
     const uint32_t bar_w = smem_u32(&bars[0]), bar_m = smem_u32(&bars[1]);
 
@@ -249,15 +260,17 @@ __global__ void __launch_bounds__(128, 1) mlp_predict_tc_kernel(const TcArgs a)
     const float os[4] = {a.out_std[0], a.out_std[1], a.out_std[2], a.out_std[3]};
     const int nx = a.Nx + 1, ny = a.Ny + 1, nz = a.Nz + 1;
     const int64_t ntiles = (a.n + TM - 1) / TM;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     uint8_t *xh = sm + OFF_SXH;
 
     for (int64_t tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
-        const int64_t node = tile * TM + tid;
+        const int64_t node = tile * TM + row;
         const bool live = node < a.n;
-        // ---- features -> X (BF16, canonical K-major, 14 chunks of 8).  The
-        // normalisation runs in FP32 ((value - mean) * (1 / std)): the result is
-        // rounded to BF16 right away, and GB300's FP64 unit is ~70x slower.
+        // ---- features -> X (BF16, canonical K-major, 14 chunks of 8 = two
+        // stencil points each, the last one point and the extrapolant).  Group
+        // g builds chunks [kChunk[g], kChunk[g + 1]).  The normalisation runs
+        // in FP32 ((value - mean) * (1 / std)): the result is rounded to BF16
+        // right away, and GB300's FP64 unit is ~70x slower.
         {
             int i = 0, j = 0, k = 0;
             if (live) {
@@ -265,43 +278,39 @@ __global__ void __launch_bounds__(128, 1) mlp_predict_tc_kernel(const TcArgs a)
                 j = (int)((node / nx) % ny);
                 k = (int)(node / ((int64_t)nx * ny));
             }
-            float f8[8];
-            int q = 0;
+            for (int c = kChunk[grp]; c < kChunk[grp + 1]; ++c) {
+                float f8[8];
 #pragma unroll
-            for (int s = 0; s < 27; ++s) {
-                const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
-                const int ii = i + dx, jj = j + dy, kk = k + dz;
-                const bool in = live && ii >= 0 && ii < nx && jj >= 0 && jj < ny && kk >= 0 && kk < nz;
-                const int64_t nb = in ? ii + (int64_t)nx * (jj + (int64_t)ny * kk) : 0;
-                double raw[4] = {0.0, 0.0, 0.0, 0.0};
-                if (in) {
-                    const double2 v01 = __ldg(reinterpret_cast<const double2 *>(a.Vn + 4 * nb));
-                    raw[0] = v01.x;
-                    raw[1] = v01.y;
-                    raw[2] = __ldg(a.Vn + 4 * nb + 2);
-                    raw[3] = __ldg(a.y + 4 * nb + 3);
-                }
+                for (int h = 0; h < 2; ++h) {
+                    const int s = 2 * c + h;
+                    double raw[4] = {0.0, 0.0, 0.0, 0.0};
+                    if (s < 27) {
+                        const int ii = i + s % 3 - 1, jj = j + (s / 3) % 3 - 1, kk = k + s / 9 - 1;
+                        const bool in = live && ii >= 0 && ii < nx && jj >= 0 && jj < ny &&
+                                        kk >= 0 && kk < nz;
+                        if (in) {
+                            const int64_t nb = ii + (int64_t)nx * (jj + (int64_t)ny * kk);
+                            const double2 v01 =
+                                __ldg(reinterpret_cast<const double2 *>(a.Vn + 4 * nb));
+                            raw[0] = v01.x;
+                            raw[1] = v01.y;
+                            raw[2] = __ldg(a.Vn + 4 * nb + 2);
+                            raw[3] = __ldg(a.y + 4 * nb + 3);
+                        }
+                    } else if (live) {  // features 108..111: the extrapolant 2 d1 - d2
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int f = 4 * s + c;
-                    f8[q++] = live ? ((float)raw[c] - smean[f]) * sistd[f] : 0.0f;
-                    if (q == 8) {
-                        const uint4 v = make_uint4(pack_bf16(f8[0], f8[1]), pack_bf16(f8[2], f8[3]),
-                                                   pack_bf16(f8[4], f8[5]), pack_bf16(f8[6], f8[7]));
-                        *reinterpret_cast<uint4 *>(xh + kmaj(tid, f - 7, KC1)) = v;
-                        q = 0;
+                        for (int q = 0; q < 4; ++q) raw[q] = 2.0 * a.d1[4 * node + q] - a.d2[4 * node + q];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int f = 4 * s + q;
+                        f8[4 * h + q] = live ? ((float)raw[q] - smean[f]) * sistd[f] : 0.0f;
                     }
                 }
+                const uint4 v = make_uint4(pack_bf16(f8[0], f8[1]), pack_bf16(f8[2], f8[3]),
+                                           pack_bf16(f8[4], f8[5]), pack_bf16(f8[6], f8[7]));
+                *reinterpret_cast<uint4 *>(xh + kmaj(row, 8 * c, KC1)) = v;
             }
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int f = 108 + c;
-                const double e = live ? 2.0 * a.d1[4 * node + c] - a.d2[4 * node + c] : 0.0;
-                f8[q++] = live ? ((float)e - smean[f]) * sistd[f] : 0.0f;
-            }
-            const uint4 v = make_uint4(pack_bf16(f8[0], f8[1]), pack_bf16(f8[2], f8[3]),
-                                       pack_bf16(f8[4], f8[5]), pack_bf16(f8[6], f8[7]));
-            *reinterpret_cast<uint4 *>(xh + kmaj(tid, 104, KC1)) = v;
         }
         fence_async_smem();
         fence_before();
@@ -325,20 +334,20 @@ __global__ void __launch_bounds__(128, 1) mlp_predict_tc_kernel(const TcArgs a)
         __syncthreads();
         if (abort_flag) break;
         fence_after();
-        // ---- H1, first K-half (columns 0..127) -> shared memory (aliases X)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        // ---- H1, first K-half (columns 0..127) -> shared memory (aliases X):
+        // group g converts columns 32 g .. 32 g + 31
+        {
             float v[32];
-            tmem_ld32(tmem + lane_base + 32 * c, v);
+            tmem_ld32(tmem + lane_base + 32 * grp, v);
 #pragma unroll
             for (int q8 = 0; q8 < 4; ++q8) {
                 float h[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
-                    const int col = 32 * c + 8 * q8 + t;
+                    const int col = 32 * grp + 8 * q8 + t;
                     h[t] = fmaxf(v[8 * q8 + t] + sb1[col], 0.0f);
                 }
-                *reinterpret_cast<uint4 *>(xh + kmaj(tid, 32 * c + 8 * q8, KC2)) =
+                *reinterpret_cast<uint4 *>(xh + kmaj(row, 32 * grp + 8 * q8, KC2)) =
                     make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
                                pack_bf16(h[6], h[7]));
             }
@@ -353,17 +362,17 @@ __global__ void __launch_bounds__(128, 1) mlp_predict_tc_kernel(const TcArgs a)
                          sdesc(s0 + OFF_SW2A + ks * 256, 128, KC2 * 128), ks > 0);
             mma_commit(bar_m);
         }
-        // second K-half of H1 into registers while those MMAs run
-        uint32_t hp[64];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        // second K-half of H1 (group g: columns 128 + 32 g ..) into registers
+        // while those MMAs run
+        uint32_t hp[16];
+        {
             float v[32];
-            tmem_ld32(tmem + lane_base + 128 + 32 * c, v);
+            tmem_ld32(tmem + lane_base + 128 + 32 * grp, v);
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
-                const int col = 128 + 32 * c + 2 * t;
-                hp[16 * c + t] = pack_bf16(fmaxf(v[2 * t] + sb1[col], 0.0f),
-                                           fmaxf(v[2 * t + 1] + sb1[col + 1], 0.0f));
+                const int col = 128 + 32 * grp + 2 * t;
+                hp[t] = pack_bf16(fmaxf(v[2 * t] + sb1[col], 0.0f),
+                                  fmaxf(v[2 * t + 1] + sb1[col + 1], 0.0f));
             }
         }
         mma_pending = true;
@@ -377,8 +386,8 @@ __global__ void __launch_bounds__(128, 1) mlp_predict_tc_kernel(const TcArgs a)
         __syncthreads();
         if (abort_flag) break;
 #pragma unroll
-        for (int q8 = 0; q8 < 16; ++q8)
-            *reinterpret_cast<uint4 *>(xh + kmaj(tid, 8 * q8, KC2)) =
+        for (int q8 = 0; q8 < 4; ++q8)
+            *reinterpret_cast<uint4 *>(xh + kmaj(row, 32 * grp + 8 * q8, KC2)) =
                 make_uint4(hp[4 * q8], hp[4 * q8 + 1], hp[4 * q8 + 2], hp[4 * q8 + 3]);
         fence_async_smem();
         fence_before();
@@ -401,15 +410,17 @@ __global__ void __launch_bounds__(128, 1) mlp_predict_tc_kernel(const TcArgs a)
         __syncthreads();
         if (abort_flag) break;
         fence_after();
-        // ---- layer 3 and the predictor
+        // ---- layer 3: group g sums D2 columns 64 g .. 64 g + 63; groups 1..3
+        // leave their partial sums in the X buffer (free now), group 0 adds
+        // them in group order and writes the predictor
         float o[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < 2; ++c) {
             float v[32];
-            tmem_ld32(tmem + lane_base + NH + 32 * c, v);
+            tmem_ld32(tmem + lane_base + NH + 64 * grp + 32 * c, v);
 #pragma unroll
             for (int t = 0; t < 32; ++t) {
-                const int col = 32 * c + t;
+                const int col = 64 * grp + 32 * c + t;
                 const float h = bf16r(fmaxf(v[t] + sb2[col], 0.0f));
                 const float4 w = sW3[col];
                 o[0] = fmaf(h, w.x, o[0]);
@@ -418,14 +429,28 @@ __global__ void __launch_bounds__(128, 1) mlp_predict_tc_kernel(const TcArgs a)
                 o[3] = fmaf(h, w.w, o[3]);
             }
         }
-        if (live)
-            for (int c = 0; c < 4; ++c) {
-                const int64_t qn = 4 * node + c;
-                const double e = 2.0 * a.d1[qn] - a.d2[qn];
-                const float out = o[c] + b3[c];
-                a.y0[qn] = a.y[qn] + e + ((double)om[c] + (double)os[c] * (double)out);
+        float4 *part = reinterpret_cast<float4 *>(xh);
+        if (grp > 0) part[(grp - 1) * TM + row] = make_float4(o[0], o[1], o[2], o[3]);
+        __syncthreads();
+        if (grp == 0) {
+#pragma unroll
+            for (int g = 1; g < kGroups; ++g) {
+                const float4 p = part[(g - 1) * TM + row];
+                o[0] += p.x;
+                o[1] += p.y;
+                o[2] += p.z;
+                o[3] += p.w;
             }
-        // the next tile overwrites X (read by the finished MMAs) and D1
+            if (live)
+                for (int c = 0; c < 4; ++c) {
+                    const int64_t qn = 4 * node + c;
+                    const double e = 2.0 * a.d1[qn] - a.d2[qn];
+                    const float out = o[c] + b3[c];
+                    a.y0[qn] = a.y[qn] + e + ((double)om[c] + (double)os[c] * (double)out);
+                }
+        }
+        // the next tile overwrites X (read by the finished MMAs and by group 0
+        // above) and D1
         fence_before();
         __syncthreads();
     }
@@ -487,7 +512,7 @@ fsi_status mlp_predict_tc(cudaStream_t s, int device, const fsi_grid &g, int64_t
              out_mean, out_std, Vn, y, d1, d2, y0, dev_err};
     const int64_t tiles = (n + TM - 1) / TM;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    mlp_predict_tc_kernel<<<grid, 128, SMEM_BYTES, s>>>(a);
+    mlp_predict_tc_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(a);
     FSI_TRY(check_launch("tensor-core predict"));
     int h = 0;
     FSI_CUDA(cudaMemcpyAsync(&h, dev_err, sizeof h, cudaMemcpyDeviceToHost, s), "memcpy");
