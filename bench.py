@@ -58,9 +58,15 @@ FLOPS_PER_ELEM = {"jacobian": 4808.0, "residual": 3008.0}
 FP32_OPS_PER_ELEM_DF64 = {"jacobian": 16075.0 + 2 * 9360.0 + 69.6,
                           "residual": 8091.0 + 2 * 6672.0 + 69.6}
 # dram__bytes_read.sum + dram__bytes_write.sum of one double-float Jacobian apply
-# at 64^3 (brick kernel 26,459,904 + 2,304 B + gather kernel 13,288,448 B; the
-# writes stay in L2 within the launch)
-TRAFFIC_JAC_DF64_64 = 39_750_656
+# at 64^3 (brick + gather kernels; the writes stay in L2 within the launch) for
+# each brick schedule (bx, by, bz, threads) of the autotuner, from one ncu
+# capture of the autotuning launches (mean of two launches per schedule)
+TRAFFIC_JAC_DF64_64 = {
+    (8, 8, 4, 256): 39_721_472, (8, 4, 4, 256): 41_196_800, (8, 8, 2, 256): 42_375_680,
+    (4, 4, 4, 256): 42_835_584, (4, 4, 8, 256): 41_209_600, (16, 4, 4, 256): 40_376_192,
+    (8, 4, 4, 128): 41_213_568, (4, 4, 4, 128): 42_842_368, (8, 4, 2, 128): 44_231_424,
+    (4, 4, 2, 128): 46_111_616,
+}
 
 
 def dist_env():
@@ -241,6 +247,16 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     mesh = fsi.Mesh(N, rho=1.0, mu=0.01, dt=1e-3, rho_inf=0.5, device=local,
                     stream=stream.cuda_stream)
+    # brick schedules of the double-float operators (shared with native FP64):
+    # the library's autotuner times its candidate shapes on this grid
+    schedule = W["schedule"] = {"autotuned": not args.no_autotune}
+    for op, name in ((0, "residual"), (1, "jacobian")):
+        if args.no_autotune:
+            schedule[name] = {"brick": [8, 8, 4], "threads": 256}
+        else:
+            t = fsi.fsi_mesh_autotune(mesh, op, fsi.FSI_DF64, reps=5)
+            schedule[name] = {"brick": list(t["brick"]), "threads": t["threads"],
+                              "ms": round(t["seconds"] * 1e3, 4)}
 
     def buffers(dtype):
         b = {}
@@ -442,7 +458,9 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
     peak_instr = fma32 / 2.0  # FMA operations/s: the probe counts an FMA as 2 flops
     # DRAM bytes of one launch (brick + gather kernels), from an ncu capture of
     # this workload; only meaningful for the 64^3 grid it was taken on
-    traffic = TRAFFIC_JAC_DF64_64 if N == N_GRID else None
+    schedule = W["schedule"]
+    jac_sched = tuple(schedule["jacobian"]["brick"]) + (schedule["jacobian"]["threads"],)
+    traffic = TRAFFIC_JAC_DF64_64.get(jac_sched) if N == N_GRID else None
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
 
@@ -526,6 +544,7 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
                      "peak_source": "measured FP32 FMA operation rate (fsi_measure_fma_peak / 2, "
                                     "this run); operations per element from ncu instruction "
                                     "counts, a paired FADD2/FMUL2/FFMA2 counted as two"},
+        "schedule": schedule,
         "cpu_baseline": cpu,
         "e2e": None if e2e_val is None else {
             "value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -1272,6 +1291,8 @@ def main():
     ap.add_argument("--grid", type=int, default=N_GRID, help="elements per axis (profiling)")
     ap.add_argument("--points", type=int, default=M_POINTS, help="solid points (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default 8x8x4 brick schedule of the VMS operators")
     ap.add_argument("--no-extras", action="store_true", help="skip Newton, batch and MLP sections")
     ap.add_argument("--sections", default="newton,batch,mlp,solid,mapped,tet",
                     help="comma-separated extra sections to run")

@@ -710,6 +710,19 @@ fsi_status fsi_batch_autotune(fsi_batch *batch, int reps, fsi_tune_report *repor
 fsi_status fsi_mesh_set_brick(fsi_mesh *mesh, int op, fsi_prec prec, int bx, int by, int bz,
                               int threads);
 
+/* Autotuner of a single structured mesh: times the VMS residual (op 0) or
+ * Jacobian apply (op 1) in compute type `prec` on scratch inputs for a fixed
+ * set of brick shapes (8x8x4, 8x4x4, 8x8x2, 4x4x4, 4x4x8, 16x4x4 at 256
+ * threads; 8x4x4, 4x4x4, 8x4x2, 4x4x2 at 128) and keeps the fastest, as
+ * fsi_mesh_set_brick would.  FSI_F64 and FSI_DF64 share one schedule per
+ * operator (both store FP64 arrays).  The report's cand_ctas holds each
+ * candidate's CTA size, ctas_per_sm is 0; seconds is per launch (brick and
+ * gather kernels, mean of reps after one warm-up).  Synchronises; results
+ * of later calls do not depend on the schedule's choice beyond rounding
+ * order (the element-to-node sums follow the bricks).                      */
+fsi_status fsi_mesh_autotune(fsi_mesh *mesh, int op, fsi_prec prec, int reps,
+                             fsi_tune_report *report);
+
 /* Measurement helper (the paper has no counterpart): the device's sustained
  * FMA throughput on the CUDA cores in `prec`, in FLOP/s (an FMA counts as 2),
  * from a dependent-chain FMA kernel over all SMs timed with CUDA events

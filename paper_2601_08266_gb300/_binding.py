@@ -177,6 +177,7 @@ _SIGS = {
     "fsi_batch_time": ([_VP, _INT, _INT, ctypes.POINTER(ctypes.c_double)], _INT),
     "fsi_batch_autotune": ([_VP, _INT, ctypes.POINTER(fsi_tune_report)], _INT),
     "fsi_mesh_set_brick": ([_VP, _INT, _INT, _INT, _INT, _INT, _INT], _INT),
+    "fsi_mesh_autotune": ([_VP, _INT, _INT, _INT, ctypes.POINTER(fsi_tune_report)], _INT),
 }
 
 
@@ -810,3 +811,15 @@ class Batch:
 
 def fsi_mesh_set_brick(mesh: Mesh, op, prec, bx, by, bz, threads):
     _check(lib().fsi_mesh_set_brick(mesh.handle, op, prec, bx, by, bz, threads))
+
+
+def fsi_mesh_autotune(mesh: Mesh, op, prec, reps=5):
+    """Time the candidate brick shapes of one VMS operator (0 residual, 1
+    Jacobian) in `prec` and keep the fastest; returns the choice and the
+    per-candidate seconds per launch."""
+    r = fsi_tune_report()
+    _check(lib().fsi_mesh_autotune(mesh.handle, int(op), int(prec), int(reps), ctypes.byref(r)))
+    cands = [((r.cand_bx[i], r.cand_by[i], r.cand_bz[i]), r.cand_ctas[i], r.cand_seconds[i])
+             for i in range(r.n_candidates)]
+    return {"brick": (r.bx, r.by, r.bz), "threads": r.threads, "seconds": r.seconds,
+            "candidates": cands}

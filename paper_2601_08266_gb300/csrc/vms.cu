@@ -20,6 +20,7 @@
 //     blocks that contain it in a fixed brick order.  The result is
 //     deterministic (bitwise reproducible) and atomic-free.
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 
 #include "fsi_internal.cuh"
@@ -159,6 +160,103 @@ fsi_status launch(fsi_mesh *m, const void *U, const void *A, const void *f, cons
     return launch_geo<T, JAC, false>(m, U, A, f, x, out);
 }
 
+// candidate brick shapes of the single-mesh autotuner: the default, smaller
+// bricks (more bricks per wave of resident CTAs on small grids), flatter and
+// longer ones, and 128-thread CTAs (more CTAs per SM)
+const Brick kMeshBricks[] = {
+    {8, 8, 4, 256}, {8, 4, 4, 256}, {8, 8, 2, 256}, {4, 4, 4, 256}, {4, 4, 8, 256},
+    {16, 4, 4, 256}, {8, 4, 4, 128}, {4, 4, 4, 128}, {8, 4, 2, 128}, {4, 4, 2, 128},
+};
+
+template <typename S> __global__ void fill_state_kernel(int64_t n, vec4<S> *U, vec4<S> *A, vec4<S> *x)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        U[i] = {S(0.5), S(-0.25), S(0.125), S(1)};
+        A[i] = {S(0), S(0), S(0), S(1)};  // s = 1
+        x[i] = {S(1), S(1), S(1), S(1)};
+    }
+}
+
+// seconds per launch of one operator with the mesh's current brick: one
+// warm-up launch, then reps launches between CUDA events
+template <typename T>
+fsi_status time_op(fsi_mesh *m, int op, int reps, const void *U, const void *A, const void *x,
+                   void *out, cudaEvent_t e0, cudaEvent_t e1, double *seconds)
+{
+    auto run = [&]() { return op ? launch<T, true>(m, U, A, nullptr, x, out)
+                                 : launch<T, false>(m, U, A, nullptr, nullptr, out); };
+    FSI_TRY(run());
+    FSI_CUDA(cudaEventRecord(e0, m->stream), "event");
+    for (int r = 0; r < reps; ++r) FSI_TRY(run());
+    FSI_CUDA(cudaEventRecord(e1, m->stream), "event");
+    FSI_CUDA(cudaEventSynchronize(e1), "event sync");
+    float ms = 0.0f;
+    FSI_CUDA(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+    *seconds = 1e-3 * ms / reps;
+    return FSI_OK;
+}
+
+template <typename T> fsi_status autotune(fsi_mesh *m, int op, int reps, fsi_tune_report *rep)
+{
+    using S = typename StorageOf<T>::type;
+    const int slot = sizeof(S) == 8 ? FSI_F64 : FSI_F32;
+    const Brick start = m->brick[op][slot];
+    const size_t bytes = (size_t)m->n_nodes * sizeof(vec4<S>);
+    void *buf[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    fsi_status st = FSI_OK;
+    for (void *&b : buf)
+        if (cudaMalloc(&b, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            st = set_error(FSI_ERR_OOM, "fsi_mesh_autotune: cudaMalloc failed");
+        }
+    if (st == FSI_OK &&
+        (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        st = set_error(FSI_ERR_CUDA, "fsi_mesh_autotune: cudaEventCreate failed");
+    double best = 1e30;
+    Brick best_brick = start;
+    int tried = 0;
+    if (st == FSI_OK) {
+        fill_state_kernel<S><<<152 * 4, 256, 0, m->stream>>>(m->n_nodes, (vec4<S> *)buf[0],
+                                                             (vec4<S> *)buf[1], (vec4<S> *)buf[2]);
+        st = check_launch("autotune fill");
+    }
+    for (const Brick &cand : kMeshBricks) {
+        if (st != FSI_OK) break;
+        m->brick[op][slot] = cand;
+        double t = 0.0;
+        st = time_op<T>(m, op, reps, buf[0], buf[1], buf[2], buf[3], e0, e1, &t);
+        if (st != FSI_OK) break;
+        if (tried < FSI_TUNE_MAX_CANDIDATES) {
+            rep->cand_bx[tried] = cand.bx;
+            rep->cand_by[tried] = cand.by;
+            rep->cand_bz[tried] = cand.bz;
+            rep->cand_ctas[tried] = cand.threads;
+            rep->cand_seconds[tried] = t;
+        }
+        ++tried;
+        if (t < best) {
+            best = t;
+            best_brick = cand;
+        }
+    }
+    m->brick[op][slot] = st == FSI_OK ? best_brick : start;
+    cudaStreamSynchronize(m->stream);
+    for (void *b : buf) cudaFree(b);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != FSI_OK) return st;
+    rep->n_candidates = tried < FSI_TUNE_MAX_CANDIDATES ? tried : FSI_TUNE_MAX_CANDIDATES;
+    rep->bx = best_brick.bx;
+    rep->by = best_brick.by;
+    rep->bz = best_brick.bz;
+    rep->threads = best_brick.threads;
+    rep->ctas_per_sm = 0;
+    rep->seconds = best;
+    return FSI_OK;
+}
+
 }  // namespace
 
 fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
@@ -180,3 +278,21 @@ fsi_status vms_jacobian(fsi_mesh *m, fsi_prec prec, const void *U, const void *A
 }
 
 }  // namespace fsi
+
+using namespace fsi;
+
+extern "C" fsi_status fsi_mesh_autotune(fsi_mesh *mesh, int op, fsi_prec prec, int reps,
+                                        fsi_tune_report *report)
+{
+    FSI_TRY(validate_mesh(mesh));
+    FSI_TRY(require_structured(mesh, "fsi_mesh_autotune"));
+    if (op < 0 || op > 1 || reps < 1 || !report ||
+        (prec != FSI_F64 && prec != FSI_F32 && prec != FSI_DF64))
+        return set_error(FSI_ERR_ARG, "fsi_mesh_autotune: bad arguments");
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    std::memset(report, 0, sizeof *report);
+    if (prec == FSI_F64) return autotune<double>(mesh, op, reps, report);
+    if (prec == FSI_DF64) return autotune<df64>(mesh, op, reps, report);
+    return autotune<float>(mesh, op, reps, report);
+}
+

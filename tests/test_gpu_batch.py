@@ -171,3 +171,41 @@ def test_mesh_brick_shapes_keep_parity(fsi, oracle):
         assert rel(H(J), ref) < 1e-12, (bx, by, bz, th)
     with pytest.raises(fsi.FsiError):
         fsi.fsi_mesh_set_brick(mesh, 1, fsi.FSI_F64, 32, 32, 4, 256)
+
+
+@pytest.mark.parametrize("prec", ["df64", "f32"])
+def test_mesh_autotune_keeps_parity(fsi, oracle, prec):
+    """The single-mesh autotuner times every candidate brick of both operators,
+    keeps the fastest, and the tuned kernels still match the oracle."""
+    import torch
+    N = (14, 9, 11)
+    mesh = fsi.Mesh(N, device=0, has_s=True)
+    P = fsi.FSI_DF64 if prec == "df64" else fsi.FSI_F32
+    dt = torch.float64 if prec == "df64" else torch.float32
+    picks = []
+    for op in (0, 1):
+        t = fsi.fsi_mesh_autotune(mesh, op, P, reps=2)
+        assert len(t["candidates"]) == 10 and t["seconds"] > 0
+        assert min(c[2] for c in t["candidates"]) == pytest.approx(t["seconds"])
+        assert (t["brick"], t["threads"]) in [(c[0], c[1]) for c in t["candidates"]]
+        picks.append(t)
+    rng = np.random.default_rng(4)
+    n = mesh.n_nodes
+    U, A, x = (rng.uniform(-1, 1, (n, 4)) for _ in range(3))
+    A[:, 3] = rng.uniform(1.0, 3.0, n)
+    if prec == "f32":
+        U, A, x = (a.astype(np.float32).astype(np.float64) for a in (U, A, x))
+    g = oracle.core.Grid(N)
+    phys = dict(rho=1.0, mu=0.01, dt=1e-3, has_s=True)
+    from oracle import timeint
+    c_a, c_v = timeint.chain_factors(0.5, 1e-3)
+    R = torch.empty((n, 4), dtype=dt, device="cuda")
+    J = torch.empty((n, 4), dtype=dt, device="cuda")
+    fsi.fsi_residual(mesh, P, T(U, dt), T(A, dt), None, R)
+    fsi.fsi_jacobian_apply(mesh, P, T(U, dt), T(A, dt), None, T(x, dt), J)
+    torch.cuda.synchronize()
+    tol = 1e-12 if prec == "df64" else 1e-5
+    assert rel(H(R), oracle.core.residual(g, phys, U, A)) < tol, picks
+    assert rel(H(J), oracle.core.jacobian_apply(g, phys, U, A, x, c_a, c_v)) < tol, picks
+    with pytest.raises(fsi.FsiError):
+        fsi.fsi_mesh_autotune(mesh, 2, P)
