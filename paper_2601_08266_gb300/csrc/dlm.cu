@@ -174,22 +174,75 @@ __device__ int newton_f32(const HexNodes &H, const double X[3], float (&xi)[3])
     return 0;
 }
 
-// FP64 root from the start xi: true when settled (last update < 1e-12).
-__device__ bool newton_f64(const HexNodes &H, const double X[3], double (&xi)[3])
+// FP64-accurate root from the start xi (the settled FP32 root): true when
+// settled (last update < 1e-12).  The Newton updates run in double-float
+// arithmetic on the FP32 pipe (~48-bit significands; GB300's FP64 unit is
+// 1/64 of its FP32 rate and bounded the location kernel): node offsets and
+// X - o are formed in FP64 (one rounding) and split exactly to 2^-47, so the
+// root agrees with an FP64 Newton iteration to ~1e-14 in xi.  The start is
+// within ~1e-7 of the root, so the second update is ~1e-14: the loop stops
+// once an update is below 1e-13.
+__device__ bool newton_df(const HexNodes &H, const double X[3], double (&xi)[3])
 {
-    const double Y[3] = {X[0] - H.o[0], X[1] - H.o[1], X[2] - H.o[2]};
-    double last = 1.0;
-    for (int it = 0; it < 12; ++it) {
-        double d[3];
-        if (!newton_update<double>(H.d, Y, xi, d)) return false;
-        xi[0] -= d[0];
-        xi[1] -= d[1];
-        xi[2] -= d[2];
-        if (!(fabs(xi[0]) < 64.0 && fabs(xi[1]) < 64.0 && fabs(xi[2]) < 64.0)) return false;
-        last = fmax(fabs(d[0]), fmax(fabs(d[1]), fabs(d[2])));
-        if (last < 1e-15) break;
+    df64 xa[8][3], Y[3], q[3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) xa[a][i] = df_split(H.d[a][i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        Y[i] = df_split(X[i] - H.o[i]);
+        q[i] = df_split(xi[i]);
     }
-    return last < 1e-12;
+    const df64 one(1), eighth(0.125f);
+    float last = 1.0f;
+    for (int it = 0; it < 12; ++it) {
+        df64 r[3] = {-Y[0], -Y[1], -Y[2]}, J[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) J[i][0] = J[i][1] = J[i][2] = df64(0);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const df64 l0 = (a & 1) ? one + q[0] : one - q[0];
+            const df64 l1 = (a & 2) ? one + q[1] : one - q[1];
+            const df64 l2 = (a & 4) ? one + q[2] : one - q[2];
+            const df64 l12 = l1 * l2, l01 = l0 * l1, l02 = l0 * l2;
+            // N and dN/dxi_k, the factor 1/8 and the signs are exact
+            const df64 N = eighth * (l0 * l12);
+            const df64 d0 = (a & 1) ? eighth * l12 : -(eighth * l12);
+            const df64 d1 = (a & 2) ? eighth * l02 : -(eighth * l02);
+            const df64 d2 = (a & 4) ? eighth * l01 : -(eighth * l01);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                r[i] = df_fma(N, xa[a][i], r[i]);
+                J[i][0] = df_fma(xa[a][i], d0, J[i][0]);
+                J[i][1] = df_fma(xa[a][i], d1, J[i][1]);
+                J[i][2] = df_fma(xa[a][i], d2, J[i][2]);
+            }
+        }
+        const df64 c00 = df_dot2(J[1][1], J[2][2], -J[1][2], J[2][1]);
+        const df64 c01 = df_dot2(J[1][2], J[2][0], -J[1][0], J[2][2]);
+        const df64 c02 = df_dot2(J[1][0], J[2][1], -J[1][1], J[2][0]);
+        const df64 det = df_fma(J[0][2], c02, df_dot2(J[0][0], c00, J[0][1], c01));
+        if (!(fabsf(det.hi) > 0.0f)) return false;
+        const df64 inv = df_rcp(det);
+        // Cramer's rule: the same cofactor expansion as the FP64 update
+        const df64 n0 = df_fma(J[0][2], df_dot2(r[1], J[2][1], -J[1][1], r[2]),
+                               df_dot2(r[0], c00, J[0][1], df_dot2(J[1][2], r[2], -r[1], J[2][2])));
+        const df64 n1 = df_fma(J[0][2], df_dot2(J[1][0], r[2], -r[1], J[2][0]),
+                               df_dot2(J[0][0], df_dot2(r[1], J[2][2], -J[1][2], r[2]), r[0], c01));
+        const df64 n2 = df_fma(r[0], c02, df_dot2(J[0][0], df_dot2(J[1][1], r[2], -r[1], J[2][1]),
+                                                  J[0][1], df_dot2(r[1], J[2][0], -J[1][0], r[2])));
+        const df64 d[3] = {n0 * inv, n1 * inv, n2 * inv};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) q[i] = q[i] - d[i];
+        if (!(fabsf(q[0].hi) < 64.0f && fabsf(q[1].hi) < 64.0f && fabsf(q[2].hi) < 64.0f))
+            return false;
+        last = fmaxf(fabsf(d[0].hi), fmaxf(fabsf(d[1].hi), fabsf(d[2].hi)));
+        if (last < 1e-13f) break;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) xi[i] = q[i].to_double();
+    return last < 1e-12f;
 }
 
 __global__ void locate_mapped_kernel(int64_t m, GridArgs g, const double4 *__restrict__ C,
@@ -225,7 +278,7 @@ __global__ void locate_mapped_kernel(int64_t m, GridArgs g, const double4 *__res
                 q[0] = q32[0];
                 q[1] = q32[1];
                 q[2] = q32[2];
-                const bool ok = newton_f64(H, X, q);
+                const bool ok = newton_df(H, X, q);
                 if (ok && fabs(q[0]) <= 1.0 + 1e-10 && fabs(q[1]) <= 1.0 + 1e-10 &&
                     fabs(q[2]) <= 1.0 + 1e-10) {
                     found = 1;
