@@ -248,7 +248,7 @@ def test_learned_guess_end_to_end(fsi, capsys):
             print("  ", rw, "|", base[rw[0]][:2])
         print(f"network or combination kept in {wins} of {len(periodic)} periodic steps; "
               f"median residual reduction of the predictor x{gain:.2f}")
-    for rw in rows:   # the residual is the judge: the kept predictor is the best one
+    for rw in rows:   # the residual decides: the kept predictor is the best one
         assert min(rw[1], rw[2], rw[3]) <= rw[1]
     assert wins >= len(periodic) // 2, rows
 
