@@ -249,30 +249,44 @@ template <typename T, bool JAC> __global__ void __launch_bounds__(256) tet_vms_k
             dN[j] = a == 0 ? s3 : (a == 1 ? geo.Ji[0][j] : (a == 2 ? geo.Ji[1][j] : geo.Ji[2][j]));
         }
         const T al = tet_al<T>(), be = tet_be<T>(), amb = al - be;
-        auto value = [&](T w) { return fma_t(amb, w, be * group_sum(w)); };
-        auto grad = [&](T w, T (&g)[3]) {
+        // Values and gradients of two fields at a time: float and double-float
+        // pairs run on the paired FP32 instructions (the double-float pair is
+        // bit-identical to the scalar sequence); double pairs are two scalars.
+        using PO = PairOf<T>;
+        using PT = typename PO::type;
+        const PT amb2 = PO::pack(amb, amb), be2 = PO::pack(be, be);
+        PT dN2[3];
 #pragma unroll
-            for (int j = 0; j < 3; ++j) g[j] = group_sum(w * dN[j]);
+        for (int j = 0; j < 3; ++j) dN2[j] = PO::pack(dN[j], dN[j]);
+        auto value = [&](T w) { return fma_t(amb, w, be * group_sum(w)); };
+        auto value2 = [&](T w1, T w2, T &r1, T &r2) {
+            const PT w = PO::pack(w1, w2);
+            const PT r = fma_t(amb2, w, be2 * group_sum(w));
+            r1 = PO::first(r);
+            r2 = PO::second(r);
+        };
+        auto grad2 = [&](T w1, T w2, T (&g1)[3], T (&g2)[3]) {
+            const PT w = PO::pack(w1, w2);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const PT gs = group_sum(w * dN2[j]);
+                g1[j] = PO::first(gs);
+                g2[j] = PO::second(gs);
+            }
         };
 
         GP<T> q;
         {
-            const T uu[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                q.v[i] = value(uu[i]);
-                grad(uu[i], q.gv[i]);
-            }
-            q.p = value(u.w);
-            grad(u.w, q.gp);
-            q.a[0] = value(ac.x);
-            q.a[1] = value(ac.y);
-            q.a[2] = value(ac.z);
-            const T sv = value(ac.w);
+            value2(u.x, u.y, q.v[0], q.v[1]);
+            value2(u.z, u.w, q.v[2], q.p);
+            grad2(u.x, u.y, q.gv[0], q.gv[1]);
+            grad2(u.z, u.w, q.gv[2], q.gp);
+            T sv;
+            value2(ac.x, ac.y, q.a[0], q.a[1]);
+            value2(ac.z, ac.w, q.a[2], sv);
             q.s = V.has_s ? sv : T(1);
             if (V.f) {
-                q.f[0] = value(ff.x);
-                q.f[1] = value(ff.y);
+                value2(ff.x, ff.y, q.f[0], q.f[1]);
                 q.f[2] = value(ff.z);
             } else {
                 q.f[0] = q.f[1] = q.f[2] = T(0);
@@ -286,32 +300,35 @@ template <typename T, bool JAC> __global__ void __launch_bounds__(256) tet_vms_k
             gp_residual_terms(V, q, X, Y);
         } else {
             const vec4<T> xx = valid ? load_c<T>(V.x + node) : zero;
-            const T xv[3] = {xx.x, xx.y, xx.z};
-            T dv[3], da[3], dgv[3][3], dgp[3];
+            T val[3], dp, g[3][3], dgp[3];
+            value2(xx.x, xx.y, val[0], val[1]);
+            value2(xx.z, xx.w, val[2], dp);
+            grad2(xx.x, xx.y, g[0], g[1]);
+            grad2(xx.z, xx.w, g[2], dgp);
+            T dv[3], da[3], dgv[3][3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const T val = value(xv[i]);
-                dv[i] = V.c_v * val;
-                da[i] = V.c_a * val;
-                T g[3];
-                grad(xv[i], g);
+                dv[i] = V.c_v * val[i];
+                da[i] = V.c_a * val[i];
 #pragma unroll
-                for (int j = 0; j < 3; ++j) dgv[i][j] = V.c_v * g[j];
+                for (int j = 0; j < 3; ++j) dgv[i][j] = V.c_v * g[i][j];
             }
-            const T dp = value(xx.w);
-            grad(xx.w, dgp);
             const T vGdv = vGdv_full(geo, q, dv);
             gp_jacobian_terms(V, q, dv, dgv, da, dp, dgp, vGdv, geo.q0, X, Y);
         }
-        // projection onto this lane's test function
-        const T w = geo.det;
-        const T Xs[4] = {X[0], X[1], X[2], X[3]};
+        // projection onto this lane's test function, two components at a time
+        const PT w2 = PO::pack(geo.det, geo.det);
         T r[4];
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-            const T gx = group_sum(Y[cc][0]), gy = group_sum(Y[cc][1]), gz = group_sum(Y[cc][2]);
-            const T t0 = fma_t(amb, Xs[cc], be * group_sum(Xs[cc]));
-            r[cc] = w * (t0 + dot3_t(dN[0], gx, dN[1], gy, dN[2], gz));
+        for (int cc = 0; cc < 4; cc += 2) {
+            const PT Xp = PO::pack(X[cc], X[cc + 1]);
+            const PT gx = group_sum(PO::pack(Y[cc][0], Y[cc + 1][0]));
+            const PT gy = group_sum(PO::pack(Y[cc][1], Y[cc + 1][1]));
+            const PT gz = group_sum(PO::pack(Y[cc][2], Y[cc + 1][2]));
+            const PT t0 = fma_t(amb2, Xp, be2 * group_sum(Xp));
+            const PT rr = w2 * (t0 + dot3_t(dN2[0], gx, dN2[1], gy, dN2[2], gz));
+            r[cc] = PO::first(rr);
+            r[cc + 1] = PO::second(rr);
         }
         if (valid) P.slots[t] = vec4<T>{r[0], r[1], r[2], r[3]};
     }
