@@ -181,3 +181,25 @@ def test_set_eliminated_refuses_a_structured_grid(fsi):
     mesh = fsi.Mesh(4, h=0.25, rho=1.0, mu=0.05, dt=0.01, rho_inf=0.5, device=0)
     with pytest.raises(fsi.FsiError):
         fsi.fsi_pressure_set_eliminated(mesh, torch.zeros(125, dtype=torch.uint8, device="cuda"))
+
+
+def test_every_node_eliminated_and_back(fsi):
+    """All nodes eliminated: the operator is its diagonal, no aggregate forms,
+    the hierarchy has one level and the V-cycle still returns a bounded
+    approximation of D^-1 b; clearing the set rebuilds the full hierarchy."""
+    import torch
+    mesh, A, _ = make(fsi, 12, seed=10, eliminate=False)
+    n = A.shape[0]
+    full = fsi.fsi_pressure_level_sizes(mesh)
+    assert len(full) >= 2
+    fsi.fsi_pressure_set_eliminated(mesh, torch.ones(n, dtype=torch.uint8, device="cuda"))
+    assert fsi.fsi_pressure_level_sizes(mesh) == [n]
+    b = T(np.random.default_rng(11).normal(size=n))
+    x = torch.empty_like(b)
+    fsi.fsi_pressure_vcycle(mesh, b, x)
+    d = A.diagonal()
+    xr = H(b) / d
+    assert np.all(np.isfinite(H(x)))
+    assert np.linalg.norm(H(x) - xr) <= 0.2 * np.linalg.norm(xr)
+    fsi.fsi_pressure_set_eliminated(mesh, None)
+    assert fsi.fsi_pressure_level_sizes(mesh) == full
