@@ -6,8 +6,9 @@ hex grid 64^3 = 262,144 elements, 274,625 nodes, 1,098,500 DOFs; smooth
 seeded Fourier velocity/pressure plus noise; three thin leaflets sampled as
 200,000 solid points):
 
-  stage (generalized alpha) -> VMS residual -> VMS Jacobian apply ->
-  locate + cell table -> interpolation C^T V -> spreading C lambda
+  stage (generalized alpha) -> VMS residual and Jacobian apply (one fused
+  pass, fsi_residual_jacobian_apply) -> locate + cell table ->
+  interpolation C^T V -> spreading C lambda
 
 with FP64 inputs and outputs: the VMS residual and Jacobian, interpolation and
 spreading in double-float arithmetic (FSI_DF64: pairs of floats on the FP32
@@ -44,9 +45,9 @@ WORKLOAD = "64^3 Q1-Q1 VMS grid + 200k leaflet points (stage, residual, Jacobian
 N_GRID = 64
 M_POINTS = 200_000
 SEED = 2026
-# Kernel launches per step issued by the library (stage 1, residual 2,
-# Jacobian 2, locate 1 + scan 3 + scatter 1 + sort 1, interp 1, spread 2).
-LAUNCHES_PER_STEP = 14
+# Kernel launches per step issued by the library (stage 1, residual + Jacobian
+# fused 2, locate 1 + scan 3 + scatter 1 + sort 1, interp 1, spread 2).
+LAUNCHES_PER_STEP = 12
 # FP64 flops per element of one VMS Jacobian apply / residual (DFMA = 2,
 # DMUL = DADD = 1), from ncu instruction counts of the native FP64 kernels.
 FLOPS_PER_ELEM = {"jacobian": 4808.0, "residual": 3008.0}
@@ -57,6 +58,17 @@ FLOPS_PER_ELEM = {"jacobian": 4808.0, "residual": 3008.0}
 # 6,672; gather 69.6 scalar.
 FP32_OPS_PER_ELEM_DF64 = {"jacobian": 16075.0 + 2 * 9360.0 + 69.6,
                           "residual": 8091.0 + 2 * 6672.0 + 69.6}
+# The same for one fused residual + Jacobian launch (brick + gather), per brick
+# schedule (bx, by, bz, threads) of op 2 (the per-element work is the same;
+# the gather's share and idle lanes differ), from one ncu capture of the
+# autotuning launches at 64^3 (sm__sass_thread_inst_executed_op_{fadd,fmul,
+# ffma}{,2}_pred_on, a paired instruction counted as two)
+FUSED_OPS_PER_ELEM_DF64 = {
+    (8, 8, 4, 256): 45_694.2, (8, 4, 4, 256): 45_712.7, (8, 8, 2, 256): 45_725.1,
+    (4, 4, 4, 256): 45_735.9, (4, 4, 8, 256): 45_712.7, (16, 4, 4, 256): 45_701.1,
+    (8, 4, 4, 128): 45_709.7, (4, 4, 4, 128): 45_729.9, (8, 4, 2, 128): 45_743.6,
+    (4, 4, 2, 128): 45_770.2,
+}
 # dram__bytes_read.sum + dram__bytes_write.sum of one double-float Jacobian apply
 # at 64^3 (brick + gather kernels; the writes stay in L2 within the launch) for
 # each brick schedule (bx, by, bz, threads) of the autotuner, from one ncu
@@ -66,6 +78,14 @@ TRAFFIC_JAC_DF64_64 = {
     (4, 4, 4, 256): 42_835_584, (4, 4, 8, 256): 41_209_600, (16, 4, 4, 256): 40_376_192,
     (8, 4, 4, 128): 41_213_568, (4, 4, 4, 128): 42_842_368, (8, 4, 2, 128): 44_231_424,
     (4, 4, 2, 128): 46_111_616,
+}
+# the same for one fused residual + Jacobian launch (brick + gather), per
+# schedule of op 2, from the same capture as FUSED_OPS_PER_ELEM_DF64
+TRAFFIC_FUSED_DF64_64 = {
+    (8, 8, 4, 256): 53_029_120, (8, 4, 4, 256): 55_985_152, (8, 8, 2, 256): 58_413_312,
+    (4, 4, 4, 256): 59_405_824, (4, 4, 8, 256): 55_988_992, (16, 4, 4, 256): 54_342_912,
+    (8, 4, 4, 128): 55_986_176, (4, 4, 4, 128): 59_353_600, (8, 4, 2, 128): 62_103_552,
+    (4, 4, 2, 128): 66_340_352,
 }
 
 
@@ -250,7 +270,7 @@ def run_ours(args):
     # brick schedules of the double-float operators (shared with native FP64):
     # the library's autotuner times its candidate shapes on this grid
     schedule = W["schedule"] = {"autotuned": not args.no_autotune}
-    for op, name in ((0, "residual"), (1, "jacobian")):
+    for op, name in ((0, "residual"), (1, "jacobian"), (2, "vms")):
         if args.no_autotune:
             schedule[name] = {"brick": [8, 8, 4], "threads": 256}
         else:
@@ -277,7 +297,8 @@ def run_ours(args):
 
     b64 = buffers(torch.float64)
     P64 = fsi.FSI_F64
-    ops = ["stage", "residual", "jacobian", "locate", "interp", "spread"]
+    # vms: the residual and the Jacobian apply, one fused pass
+    ops = ["stage", "vms", "locate", "interp", "spread"]
 
     def step(b, P, ev=None, vms=fsi.FSI_DF64, dlm=fsi.FSI_DF64):
         def mark(i):
@@ -286,17 +307,15 @@ def run_ours(args):
         mark(0)
         fsi.fsi_stage(mesh, P, b["y"], b["Vn"], b["An"], None, b["U"], b["A"])
         mark(1)
-        fsi.fsi_residual(mesh, vms, b["U"], b["A"], None, b["R"])
+        fsi.fsi_residual_jacobian_apply(mesh, vms, b["U"], b["A"], None, b["x"], b["R"], b["Jx"])
         mark(2)
-        fsi.fsi_jacobian_apply(mesh, vms, b["U"], b["A"], None, b["x"], b["Jx"])
-        mark(3)
         fsi.fsi_locate(mesh, b["X"], b["elem"], b["xi"], b["cs"], b["perm"], want_outside=False)
-        mark(4)
+        mark(3)
         fsi.fsi_dlm_interp(mesh, dlm, b["elem"], b["xi"], b["U"], b["u"])
-        mark(5)
+        mark(4)
         fsi.fsi_dlm_spread(mesh, dlm, b["elem"], b["xi"], b["cs"], b["perm"], b["lam"], None,
                            b["F"], False)
-        mark(6)
+        mark(5)
 
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
     flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device=dev)
@@ -350,7 +369,7 @@ def run_ours(args):
         fsi.fsi_dlm_spread(mesh, fsi.FSI_F32, b32["elem"], xi32, b32["cs"], b32["perm"],
                            b32["lam"], None, b32["F"], False)
         mark(4)
-        for i in range(4, 7):
+        for i in range(4, len(ops) + 1):
             mark(i)
 
     fsi.fsi_stage(mesh, fsi.FSI_F32, b32["y"], b32["Vn"], b32["An"], None, b32["U"], b32["A"])
@@ -365,10 +384,24 @@ def run_ours(args):
         fsi.fsi_residual(mesh, fsi.FSI_DF64, b64["U"], b64["A"], None, b64["R"])
         mark(1)
         fsi.fsi_jacobian_apply(mesh, fsi.FSI_DF64, b64["U"], b64["A"], None, b64["x"], b64["Jx"])
-        for i in range(2, 7):
+        for i in range(2, len(ops) + 1):
             mark(i)
     msdf, perdf = timed(stepdf, args.steps, args.warmup)
     per32 = np.concatenate([per32[:4], perdf[:2]])
+
+    # the native FP64 residual and Jacobian apply, one after the other
+    def stepnat(ev):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        fsi.fsi_residual(mesh, fsi.FSI_F64, b64["U"], b64["A"], None, b64["R"])
+        mark(1)
+        fsi.fsi_jacobian_apply(mesh, fsi.FSI_F64, b64["U"], b64["A"], None, b64["x"], b64["Jx"])
+        for i in range(2, len(ops) + 1):
+            mark(i)
+    _, pernatops = timed(stepnat, args.steps, args.warmup)
+    pernat = np.concatenate([pernat, pernatops[:2]])
     torch.cuda.synchronize()
     clocks = sampler.stop()
     if args.no_e2e:
@@ -453,14 +486,15 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
     fma64 = B.fsi_measure_fma_peak(local, fsi.FSI_F64)
     fma32 = B.fsi_measure_fma_peak(local, fsi.FSI_F32)
     E = N ** 3
-    jac_ms = per64[ops.index("jacobian")]
-    achieved = FP32_OPS_PER_ELEM_DF64["jacobian"] * E / (jac_ms * 1e-3)
+    vms_ms = per64[ops.index("vms")]
+    schedule = W["schedule"]
+    vms_sched = tuple(schedule["vms"]["brick"]) + (schedule["vms"]["threads"],)
+    ops_fused = FUSED_OPS_PER_ELEM_DF64.get(vms_sched, FUSED_OPS_PER_ELEM_DF64[(8, 8, 4, 256)])
+    achieved = ops_fused * E / (vms_ms * 1e-3)
     peak_instr = fma32 / 2.0  # FMA operations/s: the probe counts an FMA as 2 flops
     # DRAM bytes of one launch (brick + gather kernels), from an ncu capture of
     # this workload; only meaningful for the 64^3 grid it was taken on
-    schedule = W["schedule"]
-    jac_sched = tuple(schedule["jacobian"]["brick"]) + (schedule["jacobian"]["threads"],)
-    traffic = TRAFFIC_JAC_DF64_64.get(jac_sched) if N == N_GRID else None
+    traffic = TRAFFIC_FUSED_DF64_64.get(vms_sched) if N == N_GRID else None
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
 
@@ -468,11 +502,13 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
         return 4.0 * n / (ms * 1e-3) / 1e9
 
     op_tab = {o: {"ms": round(float(t), 5), "gdof_s": round(gdofs(t), 4)} for o, t in zip(ops, per64)}
+    # native FP64 residual and Jacobian apply timed one after the other
+    nat_res, nat_jac = native[1][len(ops)], native[1][len(ops) + 1]
     op_nat = {o: {"ms": round(float(t), 5), "gdof_s": round(gdofs(t), 4)}
-              for o, t in zip(("residual", "jacobian"), native[1][1:3])}
-    op_nat["residual"]["tflop_s"] = round(FLOPS_PER_ELEM["residual"] * E / (native[1][1] * 1e-3) / 1e12, 4)
-    op_nat["jacobian"]["tflop_s"] = round(FLOPS_PER_ELEM["jacobian"] * E / (native[1][2] * 1e-3) / 1e12, 4)
-    op_nat["jacobian"]["frac_of_fp64_peak"] = round(FLOPS_PER_ELEM["jacobian"] * E / (native[1][2] * 1e-3) / fma64, 4)
+              for o, t in zip(("residual", "jacobian"), (nat_res, nat_jac))}
+    op_nat["residual"]["tflop_s"] = round(FLOPS_PER_ELEM["residual"] * E / (nat_res * 1e-3) / 1e12, 4)
+    op_nat["jacobian"]["tflop_s"] = round(FLOPS_PER_ELEM["jacobian"] * E / (nat_jac * 1e-3) / 1e12, 4)
+    op_nat["jacobian"]["frac_of_fp64_peak"] = round(FLOPS_PER_ELEM["jacobian"] * E / (nat_jac * 1e-3) / fma64, 4)
     op_tab32 = {o: {"ms": round(float(t), 5), "gdof_s": round(gdofs(t), 4)}
                 for o, t in zip(ops32, per32[:4])}
     op_tabdf = {o: {"ms": round(float(t), 5), "gdof_s": round(gdofs(t), 4),
@@ -481,10 +517,9 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
     # HBM-bound DLM operators: algorithmic bytes per launch
     bytes_interp64 = m * (4 + 24 + 24)
     bytes_spread64 = m * (4 + 4 + 24 + 24) + (E + 1) * 4 + n * 24
-    op_tab["interp"]["gb_s"] = round(bytes_interp64 / (per64[4] * 1e-3) / 1e9, 1)
-    op_tab["spread"]["gb_s"] = round(bytes_spread64 / (per64[5] * 1e-3) / 1e9, 1)
-    # algorithmic bytes of the other operators (every array touched once)
-    alg_bytes = {"stage": n * 160, "residual": n * 96, "jacobian": n * 128,
+    # algorithmic bytes of the operators (every array touched once; the fused
+    # VMS pass reads U, A, x and writes R, Jx)
+    alg_bytes = {"stage": n * 160, "vms": n * 160,
                  "locate": m * (24 + 28 + 8) + (E + 1) * 4,
                  "interp": bytes_interp64, "spread": bytes_spread64}
     for o, t in zip(ops, per64):
@@ -495,8 +530,8 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
             op_tab[o]["points_per_s"] = round(m / (t * 1e-3), 1)
     op_tab32["jacobian"]["tflop_s"] = round(FLOPS_PER_ELEM["jacobian"] * E / (per32[1] * 1e-3) / 1e12, 3)
     op_tab32["jacobian"]["alu_frac"] = round(FLOPS_PER_ELEM["jacobian"] * E / (per32[1] * 1e-3) / fma32, 4)
-    op_tab["residual"]["tflop_s_fp64_equivalent"] = round(FLOPS_PER_ELEM["residual"] * E / (per64[1] * 1e-3) / 1e12, 4)
-    op_tab["jacobian"]["tflop_s_fp64_equivalent"] = round(FLOPS_PER_ELEM["jacobian"] * E / (per64[2] * 1e-3) / 1e12, 4)
+    op_tab["vms"]["tflop_s_fp64_equivalent"] = round(
+        (FLOPS_PER_ELEM["residual"] + FLOPS_PER_ELEM["jacobian"]) * E / (vms_ms * 1e-3) / 1e12, 4)
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline and N == N_GRID and m == M_POINTS:
@@ -537,7 +572,8 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
                    "grid": [N, N, N], "dofs": 4 * n, "points": m,
                    "l2": "flushed between timed steps (write of a buffer > L2)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-        "roofline": {"bound": "alu", "kernel": "vms_jacobian df64 (brick + gather)",
+        "roofline": {"bound": "alu",
+                     "kernel": "vms residual + Jacobian apply, df64, fused (brick + gather)",
                      "achieved": achieved / 1e12, "peak": peak_instr / 1e12,
                      "unit": "T FP32-pipe operations/s", "frac": achieved / peak_instr,
                      "traffic": traffic,
@@ -545,6 +581,13 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
                                     "this run); operations per element from ncu instruction "
                                     "counts, a paired FADD2/FMUL2/FFMA2 counted as two"},
         "schedule": schedule,
+        "roofline_jacobian_alone": {
+            "kernel": "vms_jacobian df64 (brick + gather), timed separately (ops_df64)",
+            "achieved": FP32_OPS_PER_ELEM_DF64["jacobian"] * E / (per32[5] * 1e-3) / 1e12,
+            "frac": FP32_OPS_PER_ELEM_DF64["jacobian"] * E / (per32[5] * 1e-3) / peak_instr,
+            "traffic": TRAFFIC_JAC_DF64_64.get(
+                tuple(schedule["jacobian"]["brick"]) + (schedule["jacobian"]["threads"],))
+            if N == N_GRID else None},
         "cpu_baseline": cpu,
         "e2e": None if e2e_val is None else {
             "value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,

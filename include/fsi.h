@@ -152,6 +152,18 @@ fsi_status fsi_residual(fsi_mesh *mesh, fsi_prec prec, const void *U, const void
 fsi_status fsi_jacobian_apply(fsi_mesh *mesh, fsi_prec prec, const void *U, const void *A,
                               const void *f, const void *x, void *Jx);
 
+/* Both operators at one stage in one pass: R as fsi_residual and Jx as
+ * fsi_jacobian_apply, from one evaluation of U and A and one base state
+ * (tau_m, tau_c, fine scales) per Gauss point.  In FSI_DF64 the results are
+ * bitwise those of the two separate calls; in FSI_F64 and FSI_F32 they agree
+ * with them to rounding (the compiler may contract differently).  The brick
+ * schedule is op 2 of fsi_mesh_set_brick / fsi_mesh_autotune.  On a
+ * tetrahedral mesh the two operators run one after the other.  Neither
+ * output may alias an input or the other output.                          */
+fsi_status fsi_residual_jacobian_apply(fsi_mesh *mesh, fsi_prec prec, const void *U,
+                                       const void *A, const void *f, const void *x, void *R,
+                                       void *Jx);
+
 /* Point location on the grid plus the cell -> points table (the point search
  * that builds C^lambda, Sec. 3 and Algorithm 1).  For each of the m points
  * X [m][3] (double):  t_k = (X_k - x0_k)/h_k; the point is outside unless
@@ -703,15 +715,17 @@ typedef struct {
  * JSON object per line.  Synchronises.                                     */
 fsi_status fsi_batch_autotune(fsi_batch *batch, int reps, fsi_tune_report *report);
 
-/* Brick schedule of a single mesh for op 0 (residual) or 1 (Jacobian) in
+/* Brick schedule of a single mesh for op 0 (residual), 1 (Jacobian) or 2
+ * (both fused; twice the shared memory) in
  * `prec`: bx*by*bz elements per CTA of `threads` threads (8 lanes per element;
  * threads a multiple of 32 and at most 256; bx*by*bz*8 >= threads not
  * required).  Scratch grows as needed.                                     */
 fsi_status fsi_mesh_set_brick(fsi_mesh *mesh, int op, fsi_prec prec, int bx, int by, int bz,
                               int threads);
 
-/* Autotuner of a single structured mesh: times the VMS residual (op 0) or
- * Jacobian apply (op 1) in compute type `prec` on scratch inputs for a fixed
+/* Autotuner of a single structured mesh: times the VMS residual (op 0),
+ * Jacobian apply (op 1) or both fused (op 2, fsi_residual_jacobian_apply) in
+ * compute type `prec` on scratch inputs for a fixed
  * set of brick shapes (8x8x4, 8x4x4, 8x8x2, 4x4x4, 4x4x8, 16x4x4 at 256
  * threads; 8x4x4, 4x4x4, 8x4x2, 4x4x2 at 128) and keeps the fastest, as
  * fsi_mesh_set_brick would.  FSI_F64 and FSI_DF64 share one schedule per

@@ -6,7 +6,7 @@ provides seeded synthetic inputs (``inputs``).
 """
 from ._binding import (FSI_BATCH_GRAPH, FSI_BATCH_PER_INSTANCE, FSI_BATCH_PERSISTENT,  # noqa: F401
                        FSI_DF64, FSI_F32, FSI_F64, Batch, FsiError, Mesh, Mlp, StepState,
-                       fsi_mesh_set_brick, fsi_mesh_autotune,
+                       fsi_mesh_set_brick, fsi_mesh_autotune, fsi_residual_jacobian_apply,
                        fsi_mlp_adam, fsi_mlp_features, fsi_mlp_forward, fsi_mlp_loss_grad,
                        fsi_mlp_num_params, fsi_mlp_predict, fsi_mlp_guess,
                        fsi_advance_history,

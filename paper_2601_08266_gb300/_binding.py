@@ -178,6 +178,7 @@ _SIGS = {
     "fsi_batch_autotune": ([_VP, _INT, ctypes.POINTER(fsi_tune_report)], _INT),
     "fsi_mesh_set_brick": ([_VP, _INT, _INT, _INT, _INT, _INT, _INT], _INT),
     "fsi_mesh_autotune": ([_VP, _INT, _INT, _INT, ctypes.POINTER(fsi_tune_report)], _INT),
+    "fsi_residual_jacobian_apply": ([_VP, _INT, _VP, _VP, _VP, _VP, _VP, _VP], _INT),
 }
 
 
@@ -294,6 +295,13 @@ def fsi_residual(mesh: Mesh, prec, U, A, f, R):
     dt = _prec_dtype(prec)
     _check(lib().fsi_residual(mesh.handle, prec, _ptr(U, dt), _ptr(A, dt), _ptr(f, dt),
                               _ptr(R, dt)))
+
+
+def fsi_residual_jacobian_apply(mesh: Mesh, prec, U, A, f, x, R, Jx):
+    dt = _prec_dtype(prec)
+    _check(lib().fsi_residual_jacobian_apply(mesh.handle, prec, _ptr(U, dt), _ptr(A, dt),
+                                             _ptr(f, dt), _ptr(x, dt), _ptr(R, dt),
+                                             _ptr(Jx, dt)))
 
 
 def fsi_jacobian_apply(mesh: Mesh, prec, U, A, f, x, Jx):

@@ -67,8 +67,8 @@ struct fsi_mesh {
     cudaStream_t stream;
     int64_t n_nodes, n_elems;
     double alpha_m, alpha_f, gamma;
-    // VMS brick schedule per [op: 0 residual, 1 jacobian][prec]
-    fsi::Brick brick[2][2];
+    // VMS brick schedule per [op: 0 residual, 1 jacobian, 2 both fused][prec]
+    fsi::Brick brick[3][2];
     // scratch: per-brick node-block partial sums of the VMS operators
     void *vms_scratch;
     size_t vms_scratch_bytes;
@@ -150,6 +150,8 @@ fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A
                         const void *f, void *R);
 fsi_status vms_jacobian(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
                         const void *f, const void *x, void *Jx);
+fsi_status vms_residual_jacobian(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
+                                 const void *f, const void *x, void *R, void *Jx);
 
 // tetrahedral meshes (tet.cu): stream and physics follow the owning fsi_mesh;
 // a distance-2 node colouring (no two nodes of one element share a colour)

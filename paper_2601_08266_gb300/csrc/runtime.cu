@@ -195,7 +195,7 @@ fsi_status fsi_mesh_create(const fsi_grid *grid, const fsi_physics *phys, int de
     m->n_nodes = n;
     m->n_elems = E;
     derive(m);
-    for (int op = 0; op < 2; ++op)
+    for (int op = 0; op < 3; ++op)
         for (int p = 0; p < 2; ++p) m->brick[op][p] = Brick{8, 8, 4, 256};
     fsi_status st = FSI_OK;
     // cell-hash scratch: fill counters [E+1], scan block sums, counters
@@ -304,11 +304,11 @@ fsi_status fsi_mesh_set_brick(fsi_mesh *m, int op, fsi_prec prec, int bx, int by
 {
     FSI_TRY(validate_mesh(m));
     FSI_TRY(require_structured(m, "fsi_mesh_set_brick"));
-    if (op < 0 || op > 1 || (prec != FSI_F64 && prec != FSI_F32))
+    if (op < 0 || op > 2 || (prec != FSI_F64 && prec != FSI_F32))
         return set_error(FSI_ERR_ARG, "bad op or precision");
     if (bx < 1 || by < 1 || bz < 1 || threads < 32 || threads > 256 || threads % 32 != 0)
         return set_error(FSI_ERR_ARG, "bad brick %dx%dx%d / %d threads", bx, by, bz, threads);
-    const size_t smem = (size_t)bx * by * bz * 8 * 4 * (prec == FSI_F64 ? 8 : 4);
+    const size_t smem = (op == 2 ? 2 : 1) * (size_t)bx * by * bz * 8 * 4 * (prec == FSI_F64 ? 8 : 4);
     if (smem > 200 * 1024)
         return set_error(FSI_ERR_ARG, "brick %dx%dx%d needs %zu bytes of shared memory", bx, by,
                          bz, smem);
@@ -378,6 +378,23 @@ fsi_status fsi_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A
         return set_error(FSI_ERR_ARG, "bad precision");
     FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
     return vms_residual(m, prec, U, A, f, R);
+}
+
+fsi_status fsi_residual_jacobian_apply(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
+                                       const void *f, const void *x, void *R, void *Jx)
+{
+    FSI_TRY(validate_mesh(m));
+    if (!U || !A || !x || !R || !Jx)
+        return set_error(FSI_ERR_ARG, "fsi_residual_jacobian_apply: NULL array argument");
+    const void *in[4] = {U, A, f, x};
+    for (const void *p : in)
+        if (p && (p == R || p == Jx))
+            return set_error(FSI_ERR_ARG, "fsi_residual_jacobian_apply: an output aliases an input");
+    if (R == Jx) return set_error(FSI_ERR_ARG, "fsi_residual_jacobian_apply: R and Jx alias");
+    if (prec != FSI_F64 && prec != FSI_F32 && prec != FSI_DF64)
+        return set_error(FSI_ERR_ARG, "bad precision");
+    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    return vms_residual_jacobian(m, prec, U, A, f, x, R, Jx);
 }
 
 fsi_status fsi_jacobian_apply(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,

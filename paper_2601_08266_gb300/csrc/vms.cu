@@ -32,21 +32,21 @@ namespace {
 
 using namespace vmsd;
 
-template <typename T, bool JAC, bool MAPPED>
+template <typename T, bool JAC, bool MAPPED, bool FUSED = false>
 __global__ void __launch_bounds__(256) vms_brick_kernel(const VmsArgs<T> P)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    brick_body<T, JAC, MAPPED>(P, blockIdx.x, reinterpret_cast<vec4<T> *>(smem_raw));
+    brick_body<T, JAC, MAPPED, FUSED>(P, blockIdx.x, reinterpret_cast<vec4<T> *>(smem_raw));
 }
 
 // The same, held to 128 registers (two 256-thread CTAs per SM): used for the
 // mapped double-float kernels, whose Jacobian otherwise takes more registers
 // and runs 1.2x slower at one CTA per SM.
-template <typename T, bool JAC, bool MAPPED>
+template <typename T, bool JAC, bool MAPPED, bool FUSED = false>
 __global__ void __launch_bounds__(256, 2) vms_brick_kernel_capped(const VmsArgs<T> P)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    brick_body<T, JAC, MAPPED>(P, blockIdx.x, reinterpret_cast<vec4<T> *>(smem_raw));
+    brick_body<T, JAC, MAPPED, FUSED>(P, blockIdx.x, reinterpret_cast<vec4<T> *>(smem_raw));
 }
 
 // Geometry table of a mapped grid: 8 lanes per element (lane = node, then
@@ -108,32 +108,40 @@ template <typename T> fsi_status ensure_map_geo(fsi_mesh *m, const VmsArgs<T> &P
     return check_launch("mapped geometry kernel");
 }
 
-template <typename T> __global__ void vms_gather_kernel(const VmsArgs<T> P)
+template <typename T, bool FUSED = false> __global__ void vms_gather_kernel(const VmsArgs<T> P)
 {
     const int n = (P.Nx + 1) * (P.Ny + 1) * (P.Nz + 1);
     for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < n;
          node += gridDim.x * blockDim.x)
-        gather_node(P, node);
+        gather_node<T, FUSED>(P, node);
 }
 
-template <typename T, bool JAC, bool MAPPED>
+// FUSED: the residual (R) and the Jacobian apply (out) at the same state in
+// one pass; the brick schedule is op 2's, the shared memory and the node-block
+// scratch hold both operators' contributions
+template <typename T, bool JAC, bool MAPPED, bool FUSED = false>
 fsi_status launch_geo(fsi_mesh *m, const void *U, const void *A, const void *f, const void *x,
-                      void *out)
+                      void *out, void *R = nullptr)
 {
-    const Brick &b = m->brick[JAC ? 1 : 0][sizeof(typename StorageOf<T>::type) == 8 ? FSI_F64 : FSI_F32];
-    FSI_TRY(ensure_vms_scratch(m, b, sizeof(T)));
+    using S = typename StorageOf<T>::type;
+    const Brick &b = m->brick[FUSED ? 2 : (JAC ? 1 : 0)][sizeof(S) == 8 ? FSI_F64 : FSI_F32];
+    FSI_TRY(ensure_vms_scratch(m, b, (FUSED ? 2 : 1) * sizeof(T)));
     VmsArgs<T> P = make_args<T>(m, b, U, A, f, x, out);
     if constexpr (MAPPED) {
         FSI_TRY(ensure_map_geo<T>(m, P));
         P.geo = (const typename GeoStore<T>::type *)m->map_geo[geo_slot<T>()];
     }
     const int nbricks = P.nbx * P.nby * P.nbz;
-    const size_t smem = (size_t)b.bx * b.by * b.bz * 8 * sizeof(vec4<typename StorageOf<T>::type>);
+    if constexpr (FUSED) {
+        P.blocks2 = P.blocks + (size_t)nbricks * (b.bx + 1) * (b.by + 1) * (b.bz + 1);
+        P.out2 = (vec4<S> *)R;
+    }
+    const size_t smem = (FUSED ? 2 : 1) * (size_t)b.bx * b.by * b.bz * 8 * sizeof(vec4<S>);
     void (*kernel)(const VmsArgs<T>);
     if constexpr (MAPPED && std::is_same<T, df64>::value)
-        kernel = vms_brick_kernel_capped<T, JAC, MAPPED>;
+        kernel = vms_brick_kernel_capped<T, JAC, MAPPED, FUSED>;
     else
-        kernel = vms_brick_kernel<T, JAC, MAPPED>;
+        kernel = vms_brick_kernel<T, JAC, MAPPED, FUSED>;
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
         FSI_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -146,7 +154,7 @@ fsi_status launch_geo(fsi_mesh *m, const void *U, const void *A, const void *f, 
     const int threads = 256;
     int64_t nb = (m->n_nodes + threads - 1) / threads;
     if (nb > 152 * 32) nb = 152 * 32;
-    vms_gather_kernel<T><<<(int)nb, threads, 0, m->stream>>>(P);
+    vms_gather_kernel<T, FUSED><<<(int)nb, threads, 0, m->stream>>>(P);
     return check_launch("vms gather kernel");
 }
 
@@ -158,6 +166,14 @@ fsi_status launch(fsi_mesh *m, const void *U, const void *A, const void *f, cons
 {
     if (m->coords64) return launch_geo<T, JAC, true>(m, U, A, f, x, out);
     return launch_geo<T, JAC, false>(m, U, A, f, x, out);
+}
+
+template <typename T>
+fsi_status launch_fused(fsi_mesh *m, const void *U, const void *A, const void *f, const void *x,
+                        void *R, void *Jx)
+{
+    if (m->coords64) return launch_geo<T, true, true, true>(m, U, A, f, x, Jx, R);
+    return launch_geo<T, true, false, true>(m, U, A, f, x, Jx, R);
 }
 
 // candidate brick shapes of the single-mesh autotuner: the default, smaller
@@ -182,10 +198,13 @@ template <typename S> __global__ void fill_state_kernel(int64_t n, vec4<S> *U, v
 // warm-up launch, then reps launches between CUDA events
 template <typename T>
 fsi_status time_op(fsi_mesh *m, int op, int reps, const void *U, const void *A, const void *x,
-                   void *out, cudaEvent_t e0, cudaEvent_t e1, double *seconds)
+                   void *out, void *R, cudaEvent_t e0, cudaEvent_t e1, double *seconds)
 {
-    auto run = [&]() { return op ? launch<T, true>(m, U, A, nullptr, x, out)
-                                 : launch<T, false>(m, U, A, nullptr, nullptr, out); };
+    auto run = [&]() {
+        if (op == 2) return launch_fused<T>(m, U, A, nullptr, x, R, out);
+        return op ? launch<T, true>(m, U, A, nullptr, x, out)
+                  : launch<T, false>(m, U, A, nullptr, nullptr, out);
+    };
     FSI_TRY(run());
     FSI_CUDA(cudaEventRecord(e0, m->stream), "event");
     for (int r = 0; r < reps; ++r) FSI_TRY(run());
@@ -203,7 +222,7 @@ template <typename T> fsi_status autotune(fsi_mesh *m, int op, int reps, fsi_tun
     const int slot = sizeof(S) == 8 ? FSI_F64 : FSI_F32;
     const Brick start = m->brick[op][slot];
     const size_t bytes = (size_t)m->n_nodes * sizeof(vec4<S>);
-    void *buf[4] = {nullptr, nullptr, nullptr, nullptr};
+    void *buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     fsi_status st = FSI_OK;
     for (void *&b : buf)
@@ -226,7 +245,7 @@ template <typename T> fsi_status autotune(fsi_mesh *m, int op, int reps, fsi_tun
         if (st != FSI_OK) break;
         m->brick[op][slot] = cand;
         double t = 0.0;
-        st = time_op<T>(m, op, reps, buf[0], buf[1], buf[2], buf[3], e0, e1, &t);
+        st = time_op<T>(m, op, reps, buf[0], buf[1], buf[2], buf[3], buf[4], e0, e1, &t);
         if (st != FSI_OK) break;
         if (tried < FSI_TUNE_MAX_CANDIDATES) {
             rep->cand_bx[tried] = cand.bx;
@@ -268,6 +287,18 @@ fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A
     return launch<float, false>(m, U, A, f, nullptr, R);
 }
 
+fsi_status vms_residual_jacobian(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
+                                 const void *f, const void *x, void *R, void *Jx)
+{
+    if (m->tet) {
+        FSI_TRY(fsi_tet_residual(m->tet, prec, U, A, f, R));
+        return fsi_tet_jacobian_apply(m->tet, prec, U, A, f, x, Jx);
+    }
+    if (prec == FSI_F64) return launch_fused<double>(m, U, A, f, x, R, Jx);
+    if (prec == FSI_DF64) return launch_fused<df64>(m, U, A, f, x, R, Jx);
+    return launch_fused<float>(m, U, A, f, x, R, Jx);
+}
+
 fsi_status vms_jacobian(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
                         const void *f, const void *x, void *Jx)
 {
@@ -286,7 +317,7 @@ extern "C" fsi_status fsi_mesh_autotune(fsi_mesh *mesh, int op, fsi_prec prec, i
 {
     FSI_TRY(validate_mesh(mesh));
     FSI_TRY(require_structured(mesh, "fsi_mesh_autotune"));
-    if (op < 0 || op > 1 || reps < 1 || !report ||
+    if (op < 0 || op > 2 || reps < 1 || !report ||
         (prec != FSI_F64 && prec != FSI_F32 && prec != FSI_DF64))
         return set_error(FSI_ERR_ARG, "fsi_mesh_autotune: bad arguments");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");

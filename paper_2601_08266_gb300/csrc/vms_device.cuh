@@ -80,6 +80,9 @@ template <typename T> struct VmsArgs {
     const vec4<S> *U, *A, *f, *x;
     vec4<T> *blocks;  // [n_bricks][(bx+1)(by+1)(bz+1)], in the compute type
     vec4<S> *out;     // [n]
+    // fused residual + Jacobian apply: the residual's node blocks and output
+    vec4<T> *blocks2;
+    vec4<S> *out2;
 };
 
 // a b + c and a b + c d: plain expressions (contracted to FMAs) for float and
@@ -492,9 +495,13 @@ __device__ __forceinline__ void gp_jacobian_terms(const VmsArgs<T> &P, const GP<
 
 // One brick of elements: element contributions into rel (shared memory,
 // [bx*by*bz][8] node records), then the brick's node block into P.blocks.
-template <typename T, bool JAC, bool MAPPED = false>
+// FUSED (with JAC): the residual at the same Gauss-point state is projected
+// too, into rel + bx*by*bz*8 and then P.blocks2; the evaluation of U and A
+// and the base state are shared by the two operators.
+template <typename T, bool JAC, bool MAPPED = false, bool FUSED = false>
 __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<T> *rel)
 {
+    static_assert(!FUSED || JAC, "the fused body computes the Jacobian apply too");
     constexpr bool OUT = JAC;  // out-of-line double-float evaluation
     const int g = threadIdx.x & 7;
     const int bxi = brick % P.nbx, byi = (brick / P.nbx) % P.nby, bzi = brick / (P.nbx * P.nby);
@@ -590,6 +597,30 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
             base_state(P, q);
 
         T X[4], Y[4][3];
+        if constexpr (FUSED) {
+            // the residual at this state, projected like the residual kernel's
+            gp_residual_terms(P, q, X, Y);
+            vec4<T> rr;
+            if constexpr (MAPPED) {
+                for (int c = 0; c < 4; ++c) {
+                    const T y0 = Y[c][0], y1 = Y[c][1], y2 = Y[c][2];
+                    Y[c][0] = geo.det * (geo.Ji[0][0] * y0 + geo.Ji[0][1] * y1 + geo.Ji[0][2] * y2);
+                    Y[c][1] = geo.det * (geo.Ji[1][0] * y0 + geo.Ji[1][1] * y1 + geo.Ji[1][2] * y2);
+                    Y[c][2] = geo.det * (geo.Ji[2][0] * y0 + geo.Ji[2][1] * y1 + geo.Ji[2][2] * y2);
+                    X[c] = geo.det * X[c];
+                }
+                project2<OUT>(X[0], Y[0], X[1], Y[1], sx, sy, sz, rr.x, rr.y);
+                project2<OUT>(X[2], Y[2], X[3], Y[3], sx, sy, sz, rr.z, rr.w);
+            } else {
+                project2<OUT>(X[0], Y[0], X[1], Y[1], sx, sy, sz, rr.x, rr.y);
+                project2<OUT>(X[2], Y[2], X[3], Y[3], sx, sy, sz, rr.z, rr.w);
+                rr.x = P.detJ * rr.x;
+                rr.y = P.detJ * rr.y;
+                rr.z = P.detJ * rr.z;
+                rr.w = P.detJ * rr.w;
+            }
+            if (slot < nel) rel[nel * 8 + slot * 8 + g] = valid ? rr : zero;
+        }
         if (!JAC) {
             gp_residual_terms(P, q, X, Y);
         } else {
@@ -652,21 +683,26 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
     // 8) brick elements around it, corner by corner in a fixed order.
     const int nx1 = P.bx + 1, ny1 = P.by + 1, nz1 = P.bz + 1;
     const int nnodes = nx1 * ny1 * nz1;
-    vec4<T> *blk = P.blocks + (size_t)brick * nnodes;
-    for (int nl = threadIdx.x; nl < nnodes; nl += blockDim.x) {
-        const int ix = nl % nx1, iy = (nl / nx1) % ny1, iz = nl / (nx1 * ny1);
-        vec4<T> acc = {T(0), T(0), T(0), T(0)};
+    constexpr int kOut = FUSED ? 2 : 1;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int lx = ix - (c & 1), ly = iy - ((c >> 1) & 1), lz = iz - ((c >> 2) & 1);
-            if (lx < 0 || ly < 0 || lz < 0 || lx >= P.bx || ly >= P.by || lz >= P.bz) continue;
-            const vec4<T> r = rel[((lz * P.by + ly) * P.bx + lx) * 8 + c];
-            acc.x += r.x;
-            acc.y += r.y;
-            acc.z += r.z;
-            acc.w += r.w;
+    for (int o = 0; o < kOut; ++o) {
+        vec4<T> *blk = (o ? P.blocks2 : P.blocks) + (size_t)brick * nnodes;
+        const vec4<T> *rl = rel + o * nel * 8;
+        for (int nl = threadIdx.x; nl < nnodes; nl += blockDim.x) {
+            const int ix = nl % nx1, iy = (nl / nx1) % ny1, iz = nl / (nx1 * ny1);
+            vec4<T> acc = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int lx = ix - (c & 1), ly = iy - ((c >> 1) & 1), lz = iz - ((c >> 2) & 1);
+                if (lx < 0 || ly < 0 || lz < 0 || lx >= P.bx || ly >= P.by || lz >= P.bz) continue;
+                const vec4<T> r = rl[((lz * P.by + ly) * P.bx + lx) * 8 + c];
+                acc.x += r.x;
+                acc.y += r.y;
+                acc.z += r.z;
+                acc.w += r.w;
+            }
+            blk[nl] = acc;
         }
-        blk[nl] = acc;
     }
 }
 
@@ -690,8 +726,9 @@ static __device__ __forceinline__ int axis_candidates(int i, int b, int nb, int 
 }
 
 // Sum, for one node, the (up to 8) brick node blocks that contain it, lower
-// bricks first.
-template <typename T> __device__ __forceinline__ void gather_node(const VmsArgs<T> &P, int node)
+// bricks first (FUSED: the residual's blocks into out2 as well).
+template <typename T, bool FUSED = false>
+__device__ __forceinline__ void gather_node(const VmsArgs<T> &P, int node)
 {
     using S = typename StorageOf<T>::type;
     const int NX1 = P.Nx + 1, NY1 = P.Ny + 1;
@@ -703,19 +740,24 @@ template <typename T> __device__ __forceinline__ void gather_node(const VmsArgs<
         const int kx = axis_candidates(i, P.bx, P.nbx, cbx, clx);
         const int ky = axis_candidates(j, P.by, P.nby, cby, cly);
         const int kz = axis_candidates(k, P.bz, P.nbz, cbz, clz);
-        vec4<T> acc = {T(0), T(0), T(0), T(0)};
-        for (int c = 0; c < kz; ++c)
-            for (int b = 0; b < ky; ++b)
-                for (int a = 0; a < kx; ++a) {
-                    const size_t brick = cbx[a] + P.nbx * (cby[b] + (size_t)P.nby * cbz[c]);
-                    const int nl = clx[a] + nx1 * (cly[b] + ny1 * clz[c]);
-                    const vec4<T> r = ld4_blk(P.blocks + brick * nnodes + nl);
-                    acc.x += r.x;
-                    acc.y += r.y;
-                    acc.z += r.z;
-                    acc.w += r.w;
-                }
-        P.out[node] = {to_s(acc.x), to_s(acc.y), to_s(acc.z), to_s(acc.w)};
+        constexpr int kOut = FUSED ? 2 : 1;
+#pragma unroll
+        for (int o = 0; o < kOut; ++o) {
+            const vec4<T> *blocks = o ? P.blocks2 : P.blocks;
+            vec4<T> acc = {T(0), T(0), T(0), T(0)};
+            for (int c = 0; c < kz; ++c)
+                for (int b = 0; b < ky; ++b)
+                    for (int a = 0; a < kx; ++a) {
+                        const size_t brick = cbx[a] + P.nbx * (cby[b] + (size_t)P.nby * cbz[c]);
+                        const int nl = clx[a] + nx1 * (cly[b] + ny1 * clz[c]);
+                        const vec4<T> r = ld4_blk(blocks + brick * nnodes + nl);
+                        acc.x += r.x;
+                        acc.y += r.y;
+                        acc.z += r.z;
+                        acc.w += r.w;
+                    }
+            (o ? P.out2 : P.out)[node] = {to_s(acc.x), to_s(acc.y), to_s(acc.z), to_s(acc.w)};
+        }
     }
 }
 
@@ -768,6 +810,8 @@ VmsArgs<T> make_args(const fsi_mesh *m, const Brick &b, const void *U, const voi
     P.x = (const vec4<S> *)x;
     P.blocks = (vec4<T> *)m->vms_scratch;
     P.out = (vec4<S> *)out;
+    P.blocks2 = nullptr;
+    P.out2 = nullptr;
     return P;
 }
 

@@ -208,4 +208,4 @@ def test_mesh_autotune_keeps_parity(fsi, oracle, prec):
     assert rel(H(R), oracle.core.residual(g, phys, U, A)) < tol, picks
     assert rel(H(J), oracle.core.jacobian_apply(g, phys, U, A, x, c_a, c_v)) < tol, picks
     with pytest.raises(fsi.FsiError):
-        fsi.fsi_mesh_autotune(mesh, 2, P)
+        fsi.fsi_mesh_autotune(mesh, 3, P)
