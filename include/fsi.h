@@ -157,7 +157,8 @@ fsi_status fsi_jacobian_apply(fsi_mesh *mesh, fsi_prec prec, const void *U, cons
  * (tau_m, tau_c, fine scales) per Gauss point.  In FSI_DF64 the results are
  * bitwise those of the two separate calls; in FSI_F64 and FSI_F32 they agree
  * with them to rounding (the compiler may contract differently).  The brick
- * schedule is op 2 of fsi_mesh_set_brick / fsi_mesh_autotune.  On a
+ * schedule is op 2 of fsi_mesh_set_brick / fsi_mesh_autotune (default 8x4x4
+ * elements, 256 threads: the pass needs twice the shared memory per brick).  On a
  * tetrahedral mesh the two operators run one after the other.  Neither
  * output may alias an input or the other output.                          */
 fsi_status fsi_residual_jacobian_apply(fsi_mesh *mesh, fsi_prec prec, const void *U,

@@ -195,8 +195,11 @@ fsi_status fsi_mesh_create(const fsi_grid *grid, const fsi_physics *phys, int de
     m->n_nodes = n;
     m->n_elems = E;
     derive(m);
+    // the fused pass keeps two element buffers in shared memory: half as many
+    // elements per brick keeps two CTAs per SM
     for (int op = 0; op < 3; ++op)
-        for (int p = 0; p < 2; ++p) m->brick[op][p] = Brick{8, 8, 4, 256};
+        for (int p = 0; p < 2; ++p)
+            m->brick[op][p] = op == 2 ? Brick{8, 4, 4, 256} : Brick{8, 8, 4, 256};
     fsi_status st = FSI_OK;
     // cell-hash scratch: fill counters [E+1], scan block sums, counters
     int64_t nblk = (E + 1 + 2047) / 2048 + 1;
