@@ -155,7 +155,8 @@ fsi_status fsi_jacobian_apply(fsi_mesh *mesh, fsi_prec prec, const void *U, cons
 /* Both operators at one stage in one pass: R as fsi_residual and Jx as
  * fsi_jacobian_apply, from one evaluation of U and A and one base state
  * (tau_m, tau_c, fine scales) per Gauss point.  In FSI_DF64 the results are
- * bitwise those of the two separate calls; in FSI_F64 and FSI_F32 they agree
+ * bitwise those of the two separate calls under the same brick schedule (the
+ * element-to-node sums follow the bricks); in FSI_F64 and FSI_F32 they agree
  * with them to rounding (the compiler may contract differently).  The brick
  * schedule is op 2 of fsi_mesh_set_brick / fsi_mesh_autotune (default 8x4x4
  * elements, 256 threads: the pass needs twice the shared memory per brick).  On a

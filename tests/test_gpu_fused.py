@@ -1,6 +1,7 @@
 """The fused residual + Jacobian apply (fsi_residual_jacobian_apply): both
 operators from one evaluation of the stage per Gauss point.  In double-float
-the outputs are bitwise those of the separate calls; in FP64 and FP32 they
+the outputs are bitwise those of the separate calls under the same brick
+schedule; in FP64 and FP32 they
 agree to rounding; both match the oracle (uniform and mapped grids, ragged
 bricks, several brick schedules, s and f present)."""
 import numpy as np
@@ -78,6 +79,10 @@ def test_fused_equals_separate_and_oracle(fsi, oracle, prec, mapped):
         mesh.set_coordinates(T(X))
         grid = core.Grid(N, coords=cast(prec, X))
     U, A, f, x = inputs_for(mesh.n_nodes, 11, prec)
+    # the element-to-node sums follow the bricks: the same schedule for all three
+    slot = fsi.FSI_F32 if prec == "f32" else fsi.FSI_F64
+    for op in (0, 1, 2):
+        fsi.fsi_mesh_set_brick(mesh, op, slot, 8, 4, 4, 256)
     R1, J1, R2, J2 = run(fsi, mesh, prec, U, A, f, x)
     if prec == "df64":
         assert torch.equal(R1, R2) and torch.equal(J1, J2)
