@@ -388,6 +388,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
+    # the two-stream step must give bitwise the one-stream step's results
+    keys = ("U", "A", "R", "Jx", "elem", "xi", "cs", "perm", "u", "F")
+    step(b64, P64)
+    stream.synchronize()
+    ref = [b64[k].clone() for k in keys]
+    step_cc(b64, P64)
+    stream.synchronize()
+    for k, r in zip(keys, ref):
+        if not torch.equal(b64[k], r):
+            raise RuntimeError(f"two-stream step: {k} differs from the one-stream step")
     ms64 = timed_total(lambda: step_cc(b64, P64), args.steps, args.warmup)
     # the operators one after the other on one stream, for the per-operator split
     ms64_seq, per64 = timed(lambda ev: step(b64, P64, ev), args.steps, args.warmup)
