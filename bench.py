@@ -850,13 +850,21 @@ def newton_section(args, dev, stream):
     train_s = time.perf_counter() - t0
     # 3) the evaluation grid: warm steps, then one step four ways
     ch = Channel(fsi, dev, stream, args.newton_grid, args.newton_points, SEED + 60)
+    # brick schedules of the operators the mixed step runs most: the FP32
+    # Jacobian apply of the Krylov iterations and the double-float residual
+    schedule = {}
+    if not args.no_autotune:
+        for op, prec, name in ((1, fsi.FSI_F32, "jacobian_f32"), (0, fsi.FSI_DF64, "residual_df64")):
+            t = fsi.fsi_mesh_autotune(ch.mesh, op, prec, reps=3)
+            schedule[name] = {"brick": list(t["brick"]), "threads": t["threads"],
+                              "ms": round(t["seconds"] * 1e3, 4)}
     for _ in range(args.newton_warm):
         y, st = ch.state()
         fsi.fsi_newton_step(ch.mesh, st, mixed=True, residual_prec=fsi.FSI_DF64, **solve)
         ch.advance(y)
     work = torch.empty((5, ch.n, 4), dtype=torch.float64, device=dev)
     out = {"grid": [ch.N] * 3, "dofs": 4 * ch.n, "points": ch.m, "dt": ch.dt, "mu": 1e-3,
-           "history_steps": ch.k,
+           "history_steps": ch.k, "schedule": schedule,
            "training": {"grid": [args.train_grid] * 3, "points": args.train_points,
                         "runs": runs, "steps_per_run": steps,
                         "samples": int(Xn.shape[0]), "generate_seconds": gen_s,
