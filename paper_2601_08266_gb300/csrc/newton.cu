@@ -93,6 +93,21 @@ __global__ void solid_force_kernel(int64_t m, const int32_t *elem, const double 
     }
 }
 
+// y[i].xyz += f[i].xyz (the coupling's nodal forces into the Jacobian apply)
+template <typename T>
+__global__ void add_xyz_kernel(int64_t n, const vec4<T> *__restrict__ f, vec4<T> *__restrict__ y)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const vec4<T> a = f[i];
+        vec4<T> b = y[i];
+        b.x += a.x;
+        b.y += a.y;
+        b.z += a.z;
+        y[i] = b;
+    }
+}
+
 template <typename T> __global__ void scale_kernel(int64_t n, T alpha, const T *x, T *y)
 {
     GRID_STRIDE(i, n) y[i] = alpha * x[i];
@@ -459,6 +474,12 @@ struct Work {
     double *hcol = nullptr, *h2 = nullptr;  // [restart+2]
     double *hhost = nullptr;                // pinned
     int precond = 0;                        // 0 block-Jacobi, 1 Schur (pmg.cu)
+    // the point-mass coupling of the Jacobian apply runs on a side stream
+    // while the VMS Jacobian runs on the mesh's stream; its spread goes to
+    // ftmp [n][4] (components 0..2), added to Jx after the join
+    void *ftmp = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t reorth = 0;                     // second Gram-Schmidt passes taken
 };
 
@@ -468,6 +489,10 @@ void free_work(Work &W)
                     W.bu, W.bv, W.ba, W.buw, W.pw,
                     W.Vk, W.w, W.z, W.x, W.b, W.blocks, W.inv, W.partial, W.hcol, W.h2};
     for (void *p : ptrs) cudaFree(p);
+    cudaFree(W.ftmp);
+    if (W.side) cudaStreamDestroy(W.side);
+    if (W.ev_fork) cudaEventDestroy(W.ev_fork);
+    if (W.ev_join) cudaEventDestroy(W.ev_join);
     if (W.hhost) cudaFreeHost(W.hhost);
     W = Work();
 }
@@ -513,7 +538,7 @@ fsi_status ensure_work(fsi_mesh *mesh, int64_t m_pts, int restart)
         {(void **)&W.bu, pm}, {(void **)&W.bv, pm}, {(void **)&W.ba, pm}, {&W.buw, pm},
         {&W.pw, pm},
         {&W.Vk, v * (size_t)(restart + 1)}, {&W.w, v}, {&W.z, v}, {&W.x, v}, {&W.b, v},
-        {&W.blocks, v * 4}, {&W.inv, v * 4},
+        {&W.blocks, v * 4}, {&W.inv, v * 4}, {&W.ftmp, v},
         {(void **)&W.partial, (size_t)(restart + 2) * kRedGrid * sizeof(double)},
         {(void **)&W.hcol, (size_t)(restart + 2) * sizeof(double)},
         {(void **)&W.h2, (size_t)(restart + 2) * sizeof(double)},
@@ -529,6 +554,15 @@ fsi_status ensure_work(fsi_mesh *mesh, int64_t m_pts, int restart)
     if (e != cudaSuccess) {
         free_work(W);
         return check_cuda(e, "pinned host buffer");
+    }
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&W.side, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W.ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W.ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        free_work(W);
+        return check_cuda(e, "coupling side stream");
     }
     W.have = true;
     return FSI_OK;
@@ -601,6 +635,13 @@ fsi_status coupled_jacobian_impl(fsi_mesh *mesh, const fsi_step_state *st, const
     cudaStream_t s = mesh->stream;
     const int64_t n = mesh->n_nodes;
     const fsi_prec P = prec_of<T>();
+    // point masses on a structured grid: the coupling overlaps the VMS Jacobian
+    const bool overlap = st->m > 0 && !st->body && !mesh->tet;
+    if (overlap) {
+        // x is ready on s: the side stream may start the coupling
+        FSI_CUDA(cudaEventRecord(W.ev_fork, s), "event record");
+        FSI_CUDA(cudaStreamWaitEvent(W.side, W.ev_fork, 0), "stream wait");
+    }
     FSI_TRY(vms_jacobian(mesh, P, W.Uw, W.Aw, st->f ? W.fw : nullptr, x, Jx));
     if (st->m > 0 && st->body) {
         FSI_TRY(fsi_dlm_interp(mesh, P, st->m, st->elem, W.xiw, x, W.pu));
@@ -608,7 +649,7 @@ fsi_status coupled_jacobian_impl(fsi_mesh *mesh, const fsi_step_state *st, const
                                       (T *)W.pw));
         FSI_TRY(fsi_dlm_spread(mesh, P, st->m, st->elem, W.xiw, st->cell_start, st->perm, W.pw,
                                nullptr, Jx, 1));
-    } else if (st->m > 0) {
+    } else if (st->m > 0 && !overlap) {
         FSI_TRY(fsi_dlm_interp(mesh, P, st->m, st->elem, W.xiw, x, W.pu));
         const double D = st->drho_s + st->k_s * mesh->gamma * mesh->phys.dt * mesh->phys.dt;
         scale_kernel<T><<<grid1d(3 * st->m), 256, 0, s>>>(3 * st->m, (T)D, (const T *)W.pu,
@@ -616,6 +657,25 @@ fsi_status coupled_jacobian_impl(fsi_mesh *mesh, const fsi_step_state *st, const
         FSI_TRY(check_launch("scale kernel"));
         FSI_TRY(fsi_dlm_spread(mesh, P, st->m, st->elem, W.xiw, st->cell_start, st->perm, W.pu,
                                st->w ? W.ww : nullptr, Jx, 1));
+    } else if (st->m > 0) {
+        // C D C^T x on the side stream (D = w (drho + k gamma dt^2)): it needs
+        // only x, so it overlaps the VMS Jacobian issued above on s
+        const double D = st->drho_s + st->k_s * mesh->gamma * mesh->phys.dt * mesh->phys.dt;
+        mesh->stream = W.side;
+        const fsi_status cs = [&]() -> fsi_status {
+            FSI_TRY(fsi_dlm_interp(mesh, P, st->m, st->elem, W.xiw, x, W.pu));
+            scale_kernel<T><<<grid1d(3 * st->m), 256, 0, W.side>>>(3 * st->m, (T)D,
+                                                                  (const T *)W.pu, (T *)W.pu);
+            FSI_TRY(check_launch("scale kernel"));
+            return fsi_dlm_spread(mesh, P, st->m, st->elem, W.xiw, st->cell_start, st->perm,
+                                  W.pu, st->w ? W.ww : nullptr, W.ftmp, 0);
+        }();
+        mesh->stream = s;
+        FSI_TRY(cs);
+        FSI_CUDA(cudaEventRecord(W.ev_join, W.side), "event record");
+        FSI_CUDA(cudaStreamWaitEvent(s, W.ev_join, 0), "stream wait");
+        add_xyz_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const vec4<T> *)W.ftmp, (vec4<T> *)Jx);
+        FSI_TRY(check_launch("coupling add kernel"));
     }
     if (st->mask) {
         dirichlet_rows_kernel<T><<<grid1d(4 * n), 256, 0, s>>>(4 * n, st->mask, x, Jx);
