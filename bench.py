@@ -1077,8 +1077,10 @@ def mapped_section(args, dev, stream):
     """Mapped (curvilinear) structured grids: the VMS kernels with per-Gauss-point
     geometry against the uniform kernels on the same 128^3 grid, point location
     by the element walk, and the mixed Newton step of the 64^3 channel on a
-    bubble-mapped grid (the Schur preconditioner keeps the nominal uniform
-    pressure operator there)."""
+    bubble-mapped grid, with the Schur preconditioner's pressure block either
+    the geometric multigrid of the nominal uniform operator or the algebraic
+    multigrid of the exact operator assembled on the mapped grid (its host
+    set-up timed apart)."""
     import torch
     import paper_2601_08266_gb300 as fsi
     N = 128
@@ -1145,9 +1147,17 @@ def mapped_section(args, dev, stream):
     mesh.close()
     # the mixed Newton step of the 64^3 channel, uniform against mapped
     solve = dict(restart=50, max_newton=10, max_krylov=4000, newton_rtol=1e-8, krylov_rtol=1e-3)
-    for name, bub in (("uniform", 0.0), ("mapped", 0.02)):
+    for name, bub, amg in (("uniform", 0.0, False), ("mapped", 0.02, False),
+                           ("mapped_amg", 0.02, True)):
         ch = Channel(fsi, dev, stream, 64, M_POINTS, SEED + 81, bubble=bub)
         y, st = ch.state(guess="zero")
+        setup = None
+        if amg:
+            fsi.fsi_pressure_use_amg(ch.mesh, True)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            fsi.fsi_pressure_level_sizes(ch.mesh)  # builds the hierarchy
+            setup = time.perf_counter() - t0
         stream.synchronize()
         t0 = time.perf_counter()
         code, rep = fsi.fsi_newton_step(ch.mesh, st, mixed=True, check=False,
@@ -1157,6 +1167,9 @@ def mapped_section(args, dev, stream):
             "seconds": time.perf_counter() - t0, "newton_iters": rep["newton_iters"],
             "krylov_iters": rep["krylov_iters"], "r_final_over_r0": rep["r_final"] / rep["r0"],
             "converged": bool(rep["converged"]), "status": code}
+        if amg:
+            out["newton_mixed_64cubed_" + name]["amg_setup_seconds"] = setup
+            out["newton_mixed_64cubed_" + name]["amg_levels"] = fsi.fsi_pressure_level_sizes(ch.mesh)
         ch.close()
     return out
 

@@ -254,8 +254,9 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
  * most Nx + Ny + Nz + 8 elements, 30 Newton iterations each; a point counts
  * as inside when |xi_k| <= 1 + 1e-10).  Interpolation and spreading only
  * need (elem, xi) and work unchanged.  The nominal N, x0, h of the mesh stay
- * in use for the walk's start and the Schur preconditioner's pressure
- * operator (an approximation there).  Synchronises the mesh stream.  The
+ * in use for the walk's start and the Schur preconditioner's geometric
+ * multigrid (an approximation there; fsi_pressure_use_amg assembles the
+ * exact pressure operator from the coordinates instead).  Synchronises the mesh stream.  The
  * geometry of the Gauss points (J^-1, G, G:G, 1/tr G, det J: 18 values per
  * point) is computed once per compute type, on the first residual or
  * Jacobian apply in it, into a table kept with the mesh (E x 144 values:
@@ -554,13 +555,32 @@ fsi_status fsi_solid_positions(fsi_solid *body, const double *u, double *x);
  * by default.  fsi_newton_step eliminates the nodes on the mesh boundary
  * whose three velocity components are free and the nodes whose pressure is
  * fixed.  fsi_pressure_levels and fsi_pressure_set_faces are for the
- * structured grid only (FSI_ERR_ARG here).                                  */
+ * geometric multigrid of the structured grid only (FSI_ERR_ARG here).
+ *
+ * A structured grid takes the same algebraic multigrid after
+ * fsi_pressure_use_amg(mesh, 1): K + kappa M is then assembled from the Q1
+ * element matrices of the grid's hexahedra (corner a of element (i, j, k) at
+ * node (i + (a&1), j + ((a>>1)&1), k + ((a>>2)&1)); eight Gauss points
+ * +-1/sqrt(3), exact for both matrices on a trilinear map) at the mapped node
+ * coordinates when fsi_mesh_set_coordinates gave some, else on the uniform
+ * grid (where it equals the geometric multigrid's level-0 operator); L is
+ * the largest extent of the nodes' bounding box; boundary nodes are those on
+ * the box's faces.  This is the exact pressure operator of a mapped grid,
+ * where the geometric multigrid uses the nominal uniform one.               */
 /* number of levels and the unknowns per level n[l] ([16] or NULL); either
  * mesh kind */
 fsi_status fsi_pressure_level_sizes(fsi_mesh *mesh, int32_t *n_levels, int64_t *n);
-/* tetrahedral mesh only: eliminated[n] device flags (nonzero = eliminated),
- * NULL = none.  Synchronises the mesh stream; rebuilds the hierarchy when
- * the set changes.  FSI_ERR_ARG on a structured grid.                      */
+/* select the pressure block of a structured grid: on != 0 the algebraic
+ * multigrid from the assembled element matrices, 0 the geometric multigrid
+ * (the default).  Synchronises the mesh stream when the choice changes; the
+ * hierarchy is built on first use and dropped (with its elimination set) by
+ * a change of choice or of coordinates.  On a tetrahedral mesh on = 0 is
+ * FSI_ERR_ARG and on != 0 does nothing.                                     */
+fsi_status fsi_pressure_use_amg(fsi_mesh *mesh, int32_t on);
+/* algebraic multigrid only (tetrahedral mesh, or fsi_pressure_use_amg):
+ * eliminated[n] device flags (nonzero = eliminated), NULL = none.
+ * Synchronises the mesh stream; rebuilds the hierarchy when the set changes.
+ * FSI_ERR_ARG with the geometric multigrid.                                 */
 fsi_status fsi_pressure_set_eliminated(fsi_mesh *mesh, const uint8_t *eliminated);
 /* faces[6] (x0, x1, y0, y1, z0, z1), nonzero = eliminated; none by default.
  * Synchronises the mesh stream when the set changes (the coarse inverse is

@@ -280,3 +280,48 @@ def sigma_of(rho, dt, rho_inf=0.5):
     from . import timeint
     am, af, gm = timeint.alphas(rho_inf)
     return af * gm * dt / (am * rho)
+
+
+def mapped_pressure_operator(N, X, kappa=None, eliminated=None):
+    """K + kappa M of the Q1 pressure space of a structured grid whose node
+    (i, j, k) (number i + (Nx+1)(j + (Ny+1)k)) sits at X[node] (a trilinear
+    map per element), as a scipy CSR matrix: the exact pressure Schur
+    approximation sigma (K + kappa M) of a mapped grid (Sec. 2.4; the module
+    docstring's operator with the true geometry in place of the nominal box).
+    Per element and Gauss point xi in {-1/sqrt3, 1/sqrt3}^3 (weight 1):
+    J = sum_a x_a (grad_xi N_a)^T, grad N_a = J^-T grad_xi N_a,
+    K_ab += |det J| grad N_a . grad N_b, M_ab += |det J| N_a N_b.  kappa
+    defaults to (pi / (2 L))^2, L the largest extent of the nodes' bounding
+    box.  Nodes flagged in `eliminated` keep only their diagonal entry.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    if kappa is None:
+        L = float(np.max(X.max(axis=0) - X.min(axis=0)))
+        kappa = (math.pi / (2.0 * L)) ** 2
+    conn = _connectivity(N)
+    g = 1.0 / math.sqrt(3.0)
+    s = np.array([[2 * ((a >> d) & 1) - 1 for d in range(3)] for a in range(8)], dtype=float)
+    xe = X[conn]                                   # [E, 8, 3]
+    Ae = np.zeros((conn.shape[0], 8, 8))
+    for q in range(8):
+        xi = np.array([(-g, g)[(q >> d) & 1] for d in range(3)])
+        f = 0.5 * (1.0 + s * xi[None, :])          # [8, 3] 1D factors
+        Nq = f.prod(axis=1)                        # [8]
+        dN = np.empty((8, 3))                      # d N_a / d xi_d
+        for d in range(3):
+            dN[:, d] = 0.5 * s[:, d] * np.prod(np.delete(f, d, axis=1), axis=1)
+        J = np.einsum("eai,ad->eid", xe, dN)       # J[e, i, d] = dx_i / dxi_d
+        Jinv = np.linalg.inv(J)                    # [e, d, i]
+        G = np.einsum("ad,edi->eai", dN, Jinv)     # grad N_a
+        w = np.abs(np.linalg.det(J))[:, None, None]
+        Ae += w * (np.einsum("eai,ebi->eab", G, G) + kappa * np.outer(Nq, Nq)[None])
+    rows = np.repeat(conn, 8, axis=1).ravel()
+    cols = np.tile(conn, (1, 8)).ravel()
+    A = sp.csr_matrix((Ae.ravel(), (rows, cols)), shape=(n, n))
+    if eliminated is not None:
+        el = np.asarray(eliminated, dtype=bool)
+        A = A.tocoo()
+        keep = (A.row == A.col) | ~(el[A.row] | el[A.col])
+        A = sp.csr_matrix((A.data[keep], (A.row[keep], A.col[keep])), shape=A.shape)
+    return A

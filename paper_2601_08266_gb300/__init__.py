@@ -21,4 +21,5 @@ from ._binding import (FSI_BATCH_GRAPH, FSI_BATCH_PER_INSTANCE, FSI_BATCH_PERSIS
                        fsi_solid_advance, fsi_solid_positions,
                        fsi_pressure_levels, fsi_pressure_set_faces, fsi_pressure_apply, fsi_pressure_restrict,
                        fsi_pressure_prolong_add, fsi_pressure_smooth, fsi_pressure_vcycle,
-                       fsi_pressure_level_sizes, fsi_pressure_set_eliminated)
+                       fsi_pressure_level_sizes, fsi_pressure_set_eliminated,
+                       fsi_pressure_use_amg)

@@ -151,6 +151,7 @@ _SIGS = {
     "fsi_pressure_level_sizes": ([_VP, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_int64)], _INT),
     "fsi_pressure_set_eliminated": ([_VP, _VP], _INT),
+    "fsi_pressure_use_amg": ([_VP, ctypes.c_int32], _INT),
     "fsi_pressure_apply": ([_VP, _INT, _INT, _VP, _VP], _INT),
     "fsi_pressure_restrict": ([_VP, _INT, _INT, _VP, _VP], _INT),
     "fsi_pressure_prolong_add": ([_VP, _INT, _INT, _VP, _VP], _INT),
@@ -724,9 +725,15 @@ def fsi_pressure_level_sizes(mesh: Mesh):
     return [int(buf[l]) for l in range(n.value)]
 
 
+def fsi_pressure_use_amg(mesh: Mesh, on=True):
+    """Structured grid: pressure block from the algebraic multigrid of the
+    assembled Q1 element matrices (on) or the geometric multigrid (off)."""
+    _check(lib().fsi_pressure_use_amg(mesh.handle, int(bool(on))))
+
+
 def fsi_pressure_set_eliminated(mesh: Mesh, eliminated=None):
-    """Tetrahedral mesh: per-node uint8 device flags of eliminated pressure
-    nodes (None: none)."""
+    """Algebraic multigrid (tetrahedral mesh or fsi_pressure_use_amg):
+    per-node uint8 device flags of eliminated pressure nodes (None: none)."""
     if eliminated is None:
         _check(lib().fsi_pressure_set_eliminated(mesh.handle, None))
         return

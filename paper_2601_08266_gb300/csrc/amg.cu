@@ -1,10 +1,13 @@
 // amg.cu -- pressure block of the Schur-complement block preconditioner on a
-// tetrahedral mesh (Sec. 2.4 solves the reduced system with block
-// preconditioners built from its sub-matrices).  The approximation is the
-// one of the structured grid: the pressure Schur complement acts like
-// sigma (K + kappa M), K and M now the P1 stiffness and mass matrices of the
-// tetrahedral pressure space, kappa = (pi / (2 L))^2 with L the largest
-// extent of the mesh's bounding box.  Eliminated nodes (boundary nodes where
+// tetrahedral mesh, and on a structured grid that asks for it (Sec. 2.4
+// solves the reduced system with block preconditioners built from its
+// sub-matrices).  The approximation is the one of the structured grid: the
+// pressure Schur complement acts like sigma (K + kappa M), K and M now the
+// stiffness and mass matrices of the pressure space as assembled from the
+// elements (P1 on tetrahedra; Q1 on the hexahedra of the grid, through its
+// mapped node coordinates when it has them, 2x2x2 Gauss points -- exact for
+// both matrices on any trilinear map), kappa = (pi / (2 L))^2 with L the
+// largest extent of the mesh's bounding box.  Eliminated nodes (boundary nodes where
 // the velocity is free, and nodes with a Dirichlet pressure) keep only their
 // diagonal entry and drop out of every other row.  With no grid hierarchy,
 // the inverse is one V-cycle of smoothed-aggregation algebraic multigrid
@@ -84,8 +87,9 @@ struct TetAmg {
     bool built = false;
     std::vector<uint8_t> elim;      // elimination set of the built hierarchy
     std::vector<uint8_t> boundary;  // nodes on a boundary face
-    std::vector<double> Ae;         // per element 4x4 K + kappa M
-    std::vector<int32_t> tets;      // [E][4]
+    int nv = 4;                     // corners per element: 4 tetrahedron, 8 hexahedron
+    std::vector<double> Ae;         // per element nv x nv K + kappa M
+    std::vector<int32_t> conn;      // [E][nv]
     std::vector<int64_t> nstart;    // node -> (element, corner) lists
     std::vector<int64_t> nslot;
 };
@@ -130,6 +134,56 @@ void element_matrix(const double x[4][3], double kappa, double *Ae)
                             kappa * V * (a == b ? 2.0 : 1.0) / 20.0;
 }
 
+// K + kappa M of one trilinear hexahedron, corner a at parent vertex
+// (s_0, s_1, s_2) = (2(a&1)-1, 2((a>>1)&1)-1, 2((a>>2)&1)-1) of [-1, 1]^3,
+// N_a = prod_k (1 + s_k xi_k) / 8: the integrals over the eight Gauss points
+// xi_k = +-1/sqrt(3) (weights 1) with J_ik = dx_i/dxi_k,
+// grad N_a = J^-T grad_xi N_a and dV = |det J| dxi
+void hex_element_matrix(const double x[8][3], double kappa, double *Ae)
+{
+    const double g = 1.0 / std::sqrt(3.0);
+    for (int q = 0; q < 64; ++q) Ae[q] = 0.0;
+    for (int gp = 0; gp < 8; ++gp) {
+        const double xi[3] = {(gp & 1) ? g : -g, (gp & 2) ? g : -g, (gp & 4) ? g : -g};
+        double N[8], dN[8][3];
+        for (int a = 0; a < 8; ++a) {
+            double f[3], s[3];
+            for (int k = 0; k < 3; ++k) {
+                s[k] = ((a >> k) & 1) ? 1.0 : -1.0;
+                f[k] = 0.5 * (1.0 + s[k] * xi[k]);
+            }
+            N[a] = f[0] * f[1] * f[2];
+            dN[a][0] = 0.5 * s[0] * f[1] * f[2];
+            dN[a][1] = 0.5 * s[1] * f[0] * f[2];
+            dN[a][2] = 0.5 * s[2] * f[0] * f[1];
+        }
+        double J[3][3] = {};
+        for (int a = 0; a < 8; ++a)
+            for (int i = 0; i < 3; ++i)
+                for (int k = 0; k < 3; ++k) J[i][k] += x[a][i] * dN[a][k];
+        double C[3][3];  // cofactors: (J^-1)_{ki} = C_ik / det
+        C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+        C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+        C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+        C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+        C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+        C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+        double gx[8][3];  // (grad N_a)_i = sum_k (J^-1)_{ki} dN_a/dxi_k
+        for (int a = 0; a < 8; ++a)
+            for (int i = 0; i < 3; ++i)
+                gx[a][i] = (C[i][0] * dN[a][0] + C[i][1] * dN[a][1] + C[i][2] * dN[a][2]) / det;
+        const double w = std::fabs(det);
+        for (int a = 0; a < 8; ++a)
+            for (int b = 0; b < 8; ++b)
+                Ae[8 * a + b] += w * (gx[a][0] * gx[b][0] + gx[a][1] * gx[b][1] +
+                                      gx[a][2] * gx[b][2] + kappa * N[a] * N[b]);
+    }
+}
+
 // level-0 operator: rows assembled node by node from the node's element
 // list (increasing element number), columns sorted; eliminated rows and
 // columns keep only the diagonal
@@ -145,12 +199,13 @@ HostCsr assemble(const TetAmg &H, int64_t n)
         cols.clear();
         vals.clear();
         for (int64_t q = H.nstart[i]; q < H.nstart[i + 1]; ++q) {
-            const int64_t e = H.nslot[q] >> 2;
-            const int a = (int)(H.nslot[q] & 3);
-            for (int b = 0; b < 4; ++b) {
-                const int32_t j = H.tets[4 * e + b];
+            const int nv = H.nv;
+            const int64_t e = H.nslot[q] / nv;
+            const int a = (int)(H.nslot[q] % nv);
+            for (int b = 0; b < nv; ++b) {
+                const int32_t j = H.conn[nv * e + b];
                 if (j != i && (H.elim[i] || H.elim[j])) continue;
-                const double v = H.Ae[16 * e + 4 * a + b];
+                const double v = H.Ae[(int64_t)nv * nv * e + nv * a + b];
                 if (where[j] < 0) {
                     where[j] = (int64_t)cols.size();
                     cols.push_back(j);
@@ -682,30 +737,105 @@ template <typename T> fsi_status vcycle_level(fsi_mesh *m, int l, const T *b, T 
     return chebyshev<T>(m, l, kAmgNu, lo, hi, b, t, x);
 }
 
-// host data of the mesh: element matrices, node lists, boundary nodes
+// node -> (element, corner) lists of the connectivity, elements in
+// increasing order
+void node_lists(TetAmg &H, int64_t n)
+{
+    H.nstart.assign((size_t)n + 1, 0);
+    for (int32_t v : H.conn) ++H.nstart[v + 1];
+    for (int64_t i = 0; i < n; ++i) H.nstart[i + 1] += H.nstart[i];
+    H.nslot.resize(H.conn.size());
+    std::vector<int64_t> cur(H.nstart.begin(), H.nstart.end() - 1);
+    for (int64_t s = 0; s < (int64_t)H.conn.size(); ++s) H.nslot[cur[H.conn[s]]++] = s;
+}
+
+double shift_for(const double lo[3], const double hi[3])
+{
+    double Lmax = 0.0;
+    for (int d = 0; d < 3; ++d) Lmax = std::max(Lmax, hi[d] - lo[d]);
+    const double q = 3.14159265358979323846 / (2.0 * Lmax);
+    return q * q;
+}
+
+// host data of the structured grid: node (i, j, k) is i + (Nx+1)(j + (Ny+1)k),
+// element (i, j, k) is i + Nx(j + Ny k) with corner a at node
+// (i + (a&1), j + ((a>>1)&1), k + ((a>>2)&1)); coordinates from the mapped
+// table when set, else x0 + i h; boundary nodes lie on the box's faces
+fsi_status load_grid(fsi_mesh *m, TetAmg &H)
+{
+    const int32_t *N = m->grid.N;
+    const int64_t NX1 = N[0] + 1, NY1 = N[1] + 1, NZ1 = N[2] + 1;
+    const int64_t n = m->n_nodes, E = m->n_elems;
+    std::vector<double> X((size_t)n * 3);
+    if (m->coords64) {
+        std::vector<double> C4((size_t)n * 4);
+        FSI_CUDA(cudaMemcpyAsync(C4.data(), m->coords64, C4.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, m->stream),
+                 "memcpy");
+        FSI_CUDA(cudaStreamSynchronize(m->stream), "sync");
+        for (int64_t v = 0; v < n; ++v)
+            for (int d = 0; d < 3; ++d) X[3 * v + d] = C4[4 * v + d];
+    } else {
+        for (int64_t k = 0; k < NZ1; ++k)
+            for (int64_t j = 0; j < NY1; ++j)
+                for (int64_t i = 0; i < NX1; ++i) {
+                    const int64_t v = i + NX1 * (j + NY1 * k);
+                    X[3 * v] = m->grid.x0[0] + (double)i * m->grid.h[0];
+                    X[3 * v + 1] = m->grid.x0[1] + (double)j * m->grid.h[1];
+                    X[3 * v + 2] = m->grid.x0[2] + (double)k * m->grid.h[2];
+                }
+    }
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) lo[d] = hi[d] = X[d];
+    for (int64_t v = 0; v < n; ++v)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], X[3 * v + d]);
+            hi[d] = std::max(hi[d], X[3 * v + d]);
+        }
+    H.kappa = shift_for(lo, hi);
+    H.nv = 8;
+    H.conn.resize((size_t)E * 8);
+    H.Ae.resize((size_t)E * 64);
+    for (int64_t k = 0; k < N[2]; ++k)
+        for (int64_t j = 0; j < N[1]; ++j)
+            for (int64_t i = 0; i < N[0]; ++i) {
+                const int64_t e = i + N[0] * (j + N[1] * k);
+                double x[8][3];
+                for (int a = 0; a < 8; ++a) {
+                    const int64_t v = (i + (a & 1)) + NX1 * ((j + ((a >> 1) & 1)) +
+                                                             NY1 * (k + ((a >> 2) & 1)));
+                    H.conn[8 * e + a] = (int32_t)v;
+                    for (int d = 0; d < 3; ++d) x[a][d] = X[3 * v + d];
+                }
+                hex_element_matrix(x, H.kappa, &H.Ae[64 * e]);
+            }
+    node_lists(H, n);
+    H.boundary.assign((size_t)n, 0);
+    for (int64_t k = 0; k < NZ1; ++k)
+        for (int64_t j = 0; j < NY1; ++j)
+            for (int64_t i = 0; i < NX1; ++i)
+                H.boundary[i + NX1 * (j + NY1 * k)] = i == 0 || i == N[0] || j == 0 ||
+                                                      j == N[1] || k == 0 || k == N[2];
+    return FSI_OK;
+}
+
+// host data of the tetrahedral mesh: element matrices, node lists, boundary nodes
 fsi_status load_mesh(fsi_mesh *m, TetAmg &H)
 {
     std::vector<double> X;
     double lo[3], hi[3];
-    FSI_TRY(tet_download(m->tet, X, H.tets, lo, hi));
-    const int64_t n = m->n_nodes, E = (int64_t)H.tets.size() / 4;
-    double Lmax = 0.0;
-    for (int d = 0; d < 3; ++d) Lmax = std::max(Lmax, hi[d] - lo[d]);
-    const double q = 3.14159265358979323846 / (2.0 * Lmax);
-    H.kappa = q * q;
+    FSI_TRY(tet_download(m->tet, X, H.conn, lo, hi));
+    const int64_t n = m->n_nodes, E = (int64_t)H.conn.size() / 4;
+    H.kappa = shift_for(lo, hi);
+    H.nv = 4;
     H.Ae.resize((size_t)E * 16);
     for (int64_t e = 0; e < E; ++e) {
         double x[4][3];
         for (int a = 0; a < 4; ++a)
-            for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)H.tets[4 * e + a] + i];
+            for (int i = 0; i < 3; ++i) x[a][i] = X[3 * (int64_t)H.conn[4 * e + a] + i];
         element_matrix(x, H.kappa, &H.Ae[16 * e]);
     }
-    H.nstart.assign((size_t)n + 1, 0);
-    for (int32_t v : H.tets) ++H.nstart[v + 1];
-    for (int64_t i = 0; i < n; ++i) H.nstart[i + 1] += H.nstart[i];
-    H.nslot.resize(H.tets.size());
-    std::vector<int64_t> cur(H.nstart.begin(), H.nstart.end() - 1);
-    for (int64_t s = 0; s < (int64_t)H.tets.size(); ++s) H.nslot[cur[H.tets[s]]++] = s;
+    node_lists(H, n);
     // boundary faces: the faces (sorted node triples) that one element holds
     struct Face {
         int32_t v[3];
@@ -724,7 +854,7 @@ fsi_status load_mesh(fsi_mesh *m, TetAmg &H)
             Face F;
             int k = 0;
             for (int a = 0; a < 4; ++a)
-                if (a != f) F.v[k++] = H.tets[4 * e + a];
+                if (a != f) F.v[k++] = H.conn[4 * e + a];
             std::sort(F.v, F.v + 3);
             faces[4 * e + f] = F;
         }
@@ -743,12 +873,14 @@ fsi_status load_mesh(fsi_mesh *m, TetAmg &H)
 fsi_status ensure_host(fsi_mesh *m)
 {
     FSI_TRY(validate_mesh(m));
-    if (!m->tet) return set_error(FSI_ERR_ARG, "pressure AMG: the mesh is not tetrahedral");
+    if (!uses_amg(m))
+        return set_error(FSI_ERR_ARG, "pressure AMG: not selected for this structured grid "
+                                      "(fsi_pressure_use_amg)");
     if (m->amg) return FSI_OK;
     TetAmg *H = new (std::nothrow) TetAmg();
     if (!H) return set_error(FSI_ERR_OOM, "host allocation of the pressure AMG failed");
     m->amg = H;
-    fsi_status st = load_mesh(m, *H);
+    fsi_status st = m->tet ? load_mesh(m, *H) : load_grid(m, *H);
     if (st != FSI_OK) {
         delete H;
         m->amg = nullptr;

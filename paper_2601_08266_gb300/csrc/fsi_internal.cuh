@@ -94,11 +94,16 @@ struct fsi_mesh {
     // null for the structured grid
     fsi_tetmesh *tet;
     // algebraic multigrid of the pressure Schur approximation on the
-    // tetrahedral mesh (amg.cu)
+    // tetrahedral mesh, or on the structured grid when pressure_amg is set
+    // (amg.cu); built on first use, dropped when the coordinates change
     fsi::TetAmg *amg;
+    bool pressure_amg;
 };
 
 namespace fsi {
+
+// the pressure block of the Schur preconditioner is the algebraic multigrid
+inline bool uses_amg(const fsi_mesh *m) { return m->tet != nullptr || m->pressure_amg; }
 
 fsi_status validate_mesh(const fsi_mesh *m);
 fsi_status ensure_vms_scratch(fsi_mesh *m, const Brick &b, size_t elem_bytes);

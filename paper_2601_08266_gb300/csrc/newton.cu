@@ -713,7 +713,7 @@ fsi_status build_block_jacobi(fsi_mesh *mesh, const fsi_step_state *st, int prec
         FSI_TRY(check_launch("block invert"));
         // tetrahedral mesh: the algebraic multigrid eliminates boundary nodes
         // with free velocity and nodes with fixed pressure
-        if (mesh->tet) return amg_set_from_mask(mesh, st->mask);
+        if (uses_amg(mesh)) return amg_set_from_mask(mesh, st->mask);
         // faces where the velocity is free (more than half of the face's inner
         // nodes, or of all its nodes when it has none inside) get Dirichlet
         // pressure in the Schur approximation
@@ -791,12 +791,12 @@ fsi_status apply_precond(fsi_mesh *mesh, const fsi_step_state *st, const T *in, 
         block_apply_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, in, out);
         return check_launch("block apply");
     }
-    const bool tet = mesh->tet != nullptr;
-    T *bp = (T *)(tet ? amg_fine_buffer(mesh, 0) : pmg_fine_buffer(mesh, 0));
-    T *xp = (T *)(tet ? amg_fine_buffer(mesh, 1) : pmg_fine_buffer(mesh, 1));
+    const bool amg = uses_amg(mesh);
+    T *bp = (T *)(amg ? amg_fine_buffer(mesh, 0) : pmg_fine_buffer(mesh, 0));
+    T *xp = (T *)(amg ? amg_fine_buffer(mesh, 1) : pmg_fine_buffer(mesh, 1));
     schur_split_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, in, out, bp);
     FSI_TRY(check_launch("Schur split"));
-    FSI_TRY(tet ? amg_vcycle<T>(mesh, bp, xp) : pmg_vcycle<T>(mesh, bp, xp));
+    FSI_TRY(amg ? amg_vcycle<T>(mesh, bp, xp) : pmg_vcycle<T>(mesh, bp, xp));
     const double sigma = mesh->alpha_f * mesh->gamma * mesh->phys.dt / (mesh->alpha_m * mesh->phys.rho);
     schur_merge_kernel<T><<<grid1d(n), 256, 0, s>>>(n, in, xp, st->mask, (T)(1.0 / sigma), out);
     return check_launch("Schur merge");

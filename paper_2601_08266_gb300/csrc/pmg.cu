@@ -630,6 +630,9 @@ fsi_status fsi_pressure_levels(fsi_mesh *mesh, int32_t *n_levels, int32_t *N)
 {
     FSI_TRY(validate_mesh(mesh));
     if (!n_levels) return set_error(FSI_ERR_ARG, "fsi_pressure_levels: n_levels is NULL");
+    if (mesh->pressure_amg)
+        return set_error(FSI_ERR_ARG, "fsi_pressure_levels: the pressure block is the algebraic "
+                                      "multigrid (fsi_pressure_level_sizes)");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
     FSI_TRY(pmg_ensure(mesh));
     *n_levels = mesh->pmg->nlev;
@@ -644,7 +647,7 @@ fsi_status fsi_pressure_level_sizes(fsi_mesh *mesh, int32_t *n_levels, int64_t *
     FSI_TRY(validate_mesh(mesh));
     if (!n_levels) return set_error(FSI_ERR_ARG, "fsi_pressure_level_sizes: n_levels is NULL");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
-    if (mesh->tet) return amg_level_sizes(mesh, n_levels, n);
+    if (uses_amg(mesh)) return amg_level_sizes(mesh, n_levels, n);
     FSI_TRY(pmg_ensure(mesh));
     *n_levels = mesh->pmg->nlev;
     if (n)
@@ -655,10 +658,10 @@ fsi_status fsi_pressure_level_sizes(fsi_mesh *mesh, int32_t *n_levels, int64_t *
 fsi_status fsi_pressure_set_eliminated(fsi_mesh *mesh, const uint8_t *eliminated)
 {
     FSI_TRY(validate_mesh(mesh));
-    if (!mesh->tet)
-        return set_error(FSI_ERR_ARG, "fsi_pressure_set_eliminated: the mesh is not tetrahedral "
-                                      "(a structured grid eliminates faces: "
-                                      "fsi_pressure_set_faces)");
+    if (!uses_amg(mesh))
+        return set_error(FSI_ERR_ARG, "fsi_pressure_set_eliminated: the pressure block is the "
+                                      "geometric multigrid (it eliminates faces: "
+                                      "fsi_pressure_set_faces; or fsi_pressure_use_amg)");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
     std::vector<uint8_t> e((size_t)mesh->n_nodes, 0);
     if (eliminated) {
@@ -671,10 +674,31 @@ fsi_status fsi_pressure_set_eliminated(fsi_mesh *mesh, const uint8_t *eliminated
     return amg_set_eliminated(mesh, e);
 }
 
+fsi_status fsi_pressure_use_amg(fsi_mesh *mesh, int32_t on)
+{
+    FSI_TRY(validate_mesh(mesh));
+    if (mesh->tet) {
+        if (!on)
+            return set_error(FSI_ERR_ARG, "fsi_pressure_use_amg: a tetrahedral mesh has only the "
+                                          "algebraic multigrid");
+        return FSI_OK;
+    }
+    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    if ((on != 0) == mesh->pressure_amg) return FSI_OK;
+    // the hierarchy may be in use by work already queued on the stream
+    FSI_CUDA(cudaStreamSynchronize(mesh->stream), "sync");
+    destroy_amg(mesh);
+    mesh->pressure_amg = on != 0;
+    return FSI_OK;
+}
+
 fsi_status fsi_pressure_set_faces(fsi_mesh *mesh, const int32_t *faces)
 {
     FSI_TRY(validate_mesh(mesh));
     if (!faces) return set_error(FSI_ERR_ARG, "fsi_pressure_set_faces: faces is NULL");
+    if (mesh->pressure_amg)
+        return set_error(FSI_ERR_ARG, "fsi_pressure_set_faces: the pressure block is the "
+                                      "algebraic multigrid (fsi_pressure_set_eliminated)");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
     int f[6];
     for (int q = 0; q < 6; ++q) f[q] = faces[q] != 0;
@@ -687,7 +711,7 @@ fsi_status fsi_pressure_apply(fsi_mesh *mesh, fsi_prec prec, int32_t level, cons
     FSI_TRY(check_prec(prec));
     if (!x || !y) return set_error(FSI_ERR_ARG, "fsi_pressure_apply: NULL argument");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
-    if (mesh->tet) return amg_apply(mesh, prec, level, x, y);
+    if (uses_amg(mesh)) return amg_apply(mesh, prec, level, x, y);
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, false));
     const dim3 g = grid3(mesh->pmg->lev[level]);
@@ -707,7 +731,7 @@ fsi_status fsi_pressure_restrict(fsi_mesh *mesh, fsi_prec prec, int32_t level, c
     FSI_TRY(check_prec(prec));
     if (!r || !b) return set_error(FSI_ERR_ARG, "fsi_pressure_restrict: NULL argument");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
-    if (mesh->tet) return amg_restrict(mesh, prec, level, r, b);
+    if (uses_amg(mesh)) return amg_restrict(mesh, prec, level, r, b);
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, true));
     PressureMG &P = *mesh->pmg;
@@ -730,7 +754,7 @@ fsi_status fsi_pressure_prolong_add(fsi_mesh *mesh, fsi_prec prec, int32_t level
     FSI_TRY(check_prec(prec));
     if (!xc || !x) return set_error(FSI_ERR_ARG, "fsi_pressure_prolong_add: NULL argument");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
-    if (mesh->tet) return amg_prolong_add(mesh, prec, level, xc, x);
+    if (uses_amg(mesh)) return amg_prolong_add(mesh, prec, level, xc, x);
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, true));
     PressureMG &P = *mesh->pmg;
@@ -754,7 +778,7 @@ fsi_status fsi_pressure_smooth(fsi_mesh *mesh, fsi_prec prec, int32_t level, int
     if (!b || !x) return set_error(FSI_ERR_ARG, "fsi_pressure_smooth: NULL argument");
     if (degree < 1 || degree > 64) return set_error(FSI_ERR_ARG, "fsi_pressure_smooth: degree 1..64");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
-    if (mesh->tet) return amg_smooth(mesh, prec, level, degree, b, x, from_zero);
+    if (uses_amg(mesh)) return amg_smooth(mesh, prec, level, degree, b, x, from_zero);
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, false));
     const double hi = mesh->pmg->lev[level].hi;
@@ -787,7 +811,7 @@ fsi_status fsi_pressure_vcycle(fsi_mesh *mesh, fsi_prec prec, const void *b, voi
     if (!b || !x) return set_error(FSI_ERR_ARG, "fsi_pressure_vcycle: NULL argument");
     if (b == x) return set_error(FSI_ERR_ARG, "fsi_pressure_vcycle: b and x must not alias");
     FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
-    if (mesh->tet) {
+    if (uses_amg(mesh)) {
         if (prec == FSI_F64) return amg_vcycle<double>(mesh, (const double *)b, (double *)x);
         return amg_vcycle<float>(mesh, (const float *)b, (float *)x);
     }

@@ -270,6 +270,7 @@ fsi_status fsi_mesh_set_coordinates(fsi_mesh *m, const double *X)
         cudaFree(g);
         g = nullptr;
     }
+    destroy_amg(m);  // assembled from the old coordinates
     if (!X) {
         cudaFree(m->coords64);
         cudaFree(m->coords32);

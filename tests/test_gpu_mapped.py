@@ -295,8 +295,8 @@ def test_mapped_locate_faces_and_nodes_are_valid(fsi, oracle):
     assert np.abs(map_points(core, grid, X, eg, xg) - P).max() < 1e-12
 
 
-@pytest.mark.parametrize("mixed", [False, True])
-def test_mapped_newton_step(fsi, oracle, mixed):
+@pytest.mark.parametrize("mixed,amg", [(False, False), (True, False), (True, True)])
+def test_mapped_newton_step(fsi, oracle, mixed, amg):
     """The implicit step on a mapped grid with immersed points: the GPU Newton
     step reaches ||R|| <= 1e-8 ||R0|| by the oracle's mapped-grid residual and
     lands on the oracle's direct-solve solution."""
@@ -328,6 +328,8 @@ def test_mapped_newton_step(fsi, oracle, mixed):
     y0 = rng.normal(size=(n, 4))
     y0[mask] = yD[mask]
     mesh, _ = mapped_mesh(fsi, N, X, rho=1.0, mu=0.05, dt=0.01, rho_inf=0.5, has_s=True)
+    if amg:  # the Schur preconditioner's pressure block from the mapped grid's exact operator
+        fsi.fsi_pressure_use_amg(mesh, True)
     e_d = torch.empty(m, dtype=torch.int32, device="cuda")
     xi_d = torch.empty((m, 3), dtype=torch.float64, device="cuda")
     cs_d = torch.empty(mesh.n_elems + 1, dtype=torch.int32, device="cuda")
