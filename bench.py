@@ -1079,7 +1079,7 @@ def mapped_section(args, dev, stream):
     by the element walk, and the mixed Newton step of the 64^3 channel on a
     bubble-mapped grid, with the Schur preconditioner's pressure block either
     the geometric multigrid of the nominal uniform operator or the algebraic
-    multigrid of the exact operator assembled on the mapped grid (its host
+    multigrid of the operator assembled on the mapped grid (its host
     set-up timed apart)."""
     import torch
     import paper_2601_08266_gb300 as fsi
@@ -1153,11 +1153,16 @@ def mapped_section(args, dev, stream):
         y, st = ch.state(guess="zero")
         setup = None
         if amg:
+            # one untimed step builds the hierarchy for the step's elimination
+            # set (the host set-up, timed apart); the timed step reuses it
             fsi.fsi_pressure_use_amg(ch.mesh, True)
             stream.synchronize()
             t0 = time.perf_counter()
-            fsi.fsi_pressure_level_sizes(ch.mesh)  # builds the hierarchy
+            fsi.fsi_newton_step(ch.mesh, st, mixed=True, check=False,
+                                residual_prec=fsi.FSI_DF64, **solve)
+            stream.synchronize()
             setup = time.perf_counter() - t0
+            y, st = ch.state(guess="zero")
         stream.synchronize()
         t0 = time.perf_counter()
         code, rep = fsi.fsi_newton_step(ch.mesh, st, mixed=True, check=False,
@@ -1168,7 +1173,7 @@ def mapped_section(args, dev, stream):
             "krylov_iters": rep["krylov_iters"], "r_final_over_r0": rep["r_final"] / rep["r0"],
             "converged": bool(rep["converged"]), "status": code}
         if amg:
-            out["newton_mixed_64cubed_" + name]["amg_setup_seconds"] = setup
+            out["newton_mixed_64cubed_" + name]["first_step_with_amg_setup_seconds"] = setup
             out["newton_mixed_64cubed_" + name]["amg_levels"] = fsi.fsi_pressure_level_sizes(ch.mesh)
         ch.close()
     return out

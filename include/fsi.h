@@ -256,7 +256,7 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
  * need (elem, xi) and work unchanged.  The nominal N, x0, h of the mesh stay
  * in use for the walk's start and the Schur preconditioner's geometric
  * multigrid (an approximation there; fsi_pressure_use_amg assembles the
- * exact pressure operator from the coordinates instead).  Synchronises the mesh stream.  The
+ * pressure operator from the coordinates instead).  Synchronises the mesh stream.  The
  * geometry of the Gauss points (J^-1, G, G:G, 1/tr G, det J: 18 values per
  * point) is computed once per compute type, on the first residual or
  * Jacobian apply in it, into a table kept with the mesh (E x 144 values:
@@ -561,12 +561,16 @@ fsi_status fsi_solid_positions(fsi_solid *body, const double *u, double *x);
  * fsi_pressure_use_amg(mesh, 1): K + kappa M is then assembled from the Q1
  * element matrices of the grid's hexahedra (corner a of element (i, j, k) at
  * node (i + (a&1), j + ((a>>1)&1), k + ((a>>2)&1)); eight Gauss points
- * +-1/sqrt(3), exact for both matrices on a trilinear map) at the mapped node
+ * +-1/sqrt(3), the quadrature of the VMS operators: exact on affine maps,
+ * and on a trilinear map K still annihilates linear fields at interior
+ * nodes) at the mapped node
  * coordinates when fsi_mesh_set_coordinates gave some, else on the uniform
  * grid (where it equals the geometric multigrid's level-0 operator); L is
  * the largest extent of the nodes' bounding box; boundary nodes are those on
- * the box's faces.  This is the exact pressure operator of a mapped grid,
- * where the geometric multigrid uses the nominal uniform one.               */
+ * the box's faces; the strength threshold is 0.02 (the Q1 stiffness couples
+ * a near-cubic element's edge and corner neighbours by 1/16 and 1/32 of the
+ * diagonal).  This is the pressure operator assembled on the mapped
+ * geometry, where the geometric multigrid uses the nominal uniform one.     */
 /* number of levels and the unknowns per level n[l] ([16] or NULL); either
  * mesh kind */
 fsi_status fsi_pressure_level_sizes(fsi_mesh *mesh, int32_t *n_levels, int64_t *n);

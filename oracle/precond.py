@@ -285,8 +285,8 @@ def sigma_of(rho, dt, rho_inf=0.5):
 def mapped_pressure_operator(N, X, kappa=None, eliminated=None):
     """K + kappa M of the Q1 pressure space of a structured grid whose node
     (i, j, k) (number i + (Nx+1)(j + (Ny+1)k)) sits at X[node] (a trilinear
-    map per element), as a scipy CSR matrix: the exact pressure Schur
-    approximation sigma (K + kappa M) of a mapped grid (Sec. 2.4; the module
+    map per element), as a scipy CSR matrix: the pressure Schur
+    approximation sigma (K + kappa M) assembled on a mapped grid (Sec. 2.4; the module
     docstring's operator with the true geometry in place of the nominal box).
     Per element and Gauss point xi in {-1/sqrt3, 1/sqrt3}^3 (weight 1):
     J = sum_a x_a (grad_xi N_a)^T, grad N_a = J^-T grad_xi N_a,

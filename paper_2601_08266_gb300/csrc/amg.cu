@@ -5,8 +5,9 @@
 // pressure Schur complement acts like sigma (K + kappa M), K and M now the
 // stiffness and mass matrices of the pressure space as assembled from the
 // elements (P1 on tetrahedra; Q1 on the hexahedra of the grid, through its
-// mapped node coordinates when it has them, 2x2x2 Gauss points -- exact for
-// both matrices on any trilinear map), kappa = (pi / (2 L))^2 with L the
+// mapped node coordinates when it has them, 2x2x2 Gauss points -- exact on
+// affine maps; on a trilinear map K still passes the linear patch test and
+// M integrates volume and first moments exactly), kappa = (pi / (2 L))^2 with L the
 // largest extent of the mesh's bounding box.  Eliminated nodes (boundary nodes where
 // the velocity is free, and nodes with a Dirichlet pressure) keep only their
 // diagonal entry and drop out of every other row.  With no grid hierarchy,
@@ -15,7 +16,10 @@
 // FP64 once per elimination set:
 //
 //   strength    j is a strong neighbour of i if |a_ij| >= theta sqrt(a_ii a_jj),
-//               theta = 0.08;
+//               theta = 0.08 on tetrahedra, 0.02 on hexahedra (the Q1
+//               stiffness of a near-cubic element couples face neighbours by
+//               ~0 and edge and corner neighbours by 1/16 and 1/32 of the
+//               diagonal: 0.02 keeps all 26 neighbours strong);
 //   aggregates  three greedy passes in node order: a node whose strong
 //               neighbours are all free starts an aggregate with them; a free
 //               node joins the first-pass aggregate of its strongest
@@ -50,7 +54,7 @@ namespace fsi {
 
 constexpr int kAmgMaxLevels = 16;
 constexpr int64_t kAmgDirectMax = 600;
-constexpr double kAmgTheta = 0.08;
+constexpr double kAmgThetaTet = 0.08, kAmgThetaHex = 0.02;
 constexpr int kAmgNu = 2;
 constexpr double kAmgLoRatio = 10.0;
 constexpr int kAmgCoarseDegree = 8;
@@ -342,7 +346,8 @@ double spectral_radius(const HostCsr &A, const std::vector<double> &d)
 }
 
 // aggregate number per node (-1: in none); returns the number of aggregates
-int64_t aggregate(const HostCsr &A, const std::vector<double> &d, std::vector<int32_t> &agg)
+int64_t aggregate(const HostCsr &A, const std::vector<double> &d, double theta,
+                  std::vector<int32_t> &agg)
 {
     const int64_t n = A.rows;
     std::vector<int64_t> sptr((size_t)n + 1, 0);
@@ -352,7 +357,7 @@ int64_t aggregate(const HostCsr &A, const std::vector<double> &d, std::vector<in
         for (int64_t q = A.ptr[i]; q < A.ptr[i + 1]; ++q) {
             const int32_t j = A.col[q];
             if (j == i) continue;
-            if (std::fabs(A.val[q]) >= kAmgTheta * std::sqrt(std::fabs(d[i] * d[j]))) {
+            if (std::fabs(A.val[q]) >= theta * std::sqrt(std::fabs(d[i] * d[j]))) {
                 scol.push_back(j);
                 sval.push_back(std::fabs(A.val[q]));
             }
@@ -904,7 +909,7 @@ fsi_status build(fsi_mesh *m)
     while ((int)A.size() < kAmgMaxLevels && A.back().rows > kAmgDirectMax) {
         const HostCsr &Af = A.back();
         std::vector<int32_t> agg;
-        const int64_t na = aggregate(Af, D.back(), agg);
+        const int64_t na = aggregate(Af, D.back(), H.nv == 8 ? kAmgThetaHex : kAmgThetaTet, agg);
         if (na == 0 || (double)na * 1.25 > (double)Af.rows) break;
         HostCsr Pl = smoothed_prolongator(Af, D.back(), rho.back(), agg, na);
         HostCsr Rl = transpose(Pl);

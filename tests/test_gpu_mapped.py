@@ -328,7 +328,7 @@ def test_mapped_newton_step(fsi, oracle, mixed, amg):
     y0 = rng.normal(size=(n, 4))
     y0[mask] = yD[mask]
     mesh, _ = mapped_mesh(fsi, N, X, rho=1.0, mu=0.05, dt=0.01, rho_inf=0.5, has_s=True)
-    if amg:  # the Schur preconditioner's pressure block from the mapped grid's exact operator
+    if amg:  # the Schur preconditioner's pressure block assembled on the mapped grid
         fsi.fsi_pressure_use_amg(mesh, True)
     e_d = torch.empty(m, dtype=torch.int32, device="cuda")
     xi_d = torch.empty((m, 3), dtype=torch.float64, device="cuda")

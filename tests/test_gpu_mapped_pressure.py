@@ -1,6 +1,6 @@
 """The algebraic-multigrid pressure block on a structured grid
-(fsi_pressure_use_amg; Sec. 2.4's Schur approximation with the exact
-operator of a mapped grid): the level-0 operator against the oracle's Q1
+(fsi_pressure_use_amg; Sec. 2.4's Schur approximation with the operator
+assembled on a mapped grid): the level-0 operator against the oracle's Q1
 assembly at the mapped coordinates, with and without eliminated nodes; on a
 uniform grid it equals the geometric multigrid's operator; the V-cycle as a
 symmetric positive definite preconditioner; the switch and its invalidation
