@@ -45,6 +45,15 @@ MUTATIONS = {
     "tet_pressure_elimination_rows_only": (
         "tet.py", "keep = (A.row == A.col) | ~(el[A.row] | el[A.col])",
         "keep = (A.row == A.col) | ~el[A.row]", "test_oracle_tet_pressure.py"),
+    "mapped_pressure_jacobian_transposed": (
+        "precond.py", 'G = np.einsum("ad,edi->eai", dN, Jinv)',
+        'G = np.einsum("ad,eid->eai", dN, Jinv)', "test_oracle_mapped_pressure.py"),
+    "mapped_pressure_no_det": (
+        "precond.py", "w = np.abs(np.linalg.det(J))[:, None, None]",
+        "w = np.ones((J.shape[0], 1, 1))", "test_oracle_mapped_pressure.py"),
+    "mapped_pressure_mass_diagonal": (
+        "precond.py", "kappa * np.outer(Nq, Nq)[None])",
+        "kappa * np.diag(Nq * Nq)[None])", "test_oracle_mapped_pressure.py"),
     "band_dilation_short": ("interface.py", "max(0, i - layers):min(Nx, i + layers + 1)",
                             "max(0, i - layers):min(Nx, i + layers)", "test_oracle_interface.py"),
     "band_lower_corner_only": ("interface.py", "on[dk:dk + Nz, dj:dj + Ny, di:di + Nx] |= band",
