@@ -10,14 +10,15 @@ seeded Fourier velocity/pressure plus noise; three thin leaflets sampled as
   pass, fsi_residual_jacobian_apply) -> locate + cell table ->
   interpolation C^T V -> spreading C lambda
 
-with FP64 inputs and outputs (the location, interpolation and spreading run on a second
-stream, concurrently with the VMS pass; "ms_per_step_one_stream" and "ops_step" time the
-operators one after the other): the VMS residual and Jacobian, interpolation and
-spreading in double-float arithmetic (FSI_DF64: pairs of floats on the FP32
-pipe, agreeing with FP64 to ~1e-14), locate and stage in FP64.  The same step
-with native FP64 operators ("step_native_f64"), and the operators in FP32
-("ops_f32"), are timed in further loops.  value = DOFs (4 per node) passed through the step per
-second, in GDOF/s.
+in native FP64 arithmetic throughout, on FP64 arrays (the location,
+interpolation and spreading run on a second stream, concurrently with the VMS
+pass; "ms_per_step_one_stream" and "ops_step" time the operators one after the
+other).  value = DOFs (4 per node) passed through the step per second, in
+GDOF/s.  The same step with the VMS operators, interpolation and spreading in
+double-float arithmetic (pairs of floats on the FP32 pipe; "step_df64", with
+its difference from the FP64 step), the operators in FP32 ("ops_f32") and the
+extra sections (Newton step, ensemble, network, solid, mapped and tetrahedral
+meshes) are timed in further loops.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank runs its own replica (weak scaling, no collective on
@@ -50,45 +51,10 @@ SEED = 2026
 # Kernel launches per step issued by the library (stage 1, residual + Jacobian
 # fused 2, locate 1 + scan 3 + scatter 1 + sort 1, interp 1, spread 2).
 LAUNCHES_PER_STEP = 12
-# FP64 flops per element of one VMS Jacobian apply / residual (DFMA = 2,
-# DMUL = DADD = 1), from ncu instruction counts of the native FP64 kernels.
-FLOPS_PER_ELEM = {"jacobian": 4808.0, "residual": 3008.0}
-# FP32-pipe operations per element of the double-float kernels, brick + gather:
-# FADD + FMUL + FFMA + 2 x (FADD2 + FMUL2 + FFMA2) (a paired instruction does two
-# lanes of work), from ncu's sm__sass_thread_inst_executed_op_*_pred_on counters
-# (64^3 capture).  Jacobian: 16,075 scalar + 9,360 paired; residual: 8,091 +
-# 6,672; gather 69.6 scalar.
-FP32_OPS_PER_ELEM_DF64 = {"jacobian": 16075.0 + 2 * 9360.0 + 69.6,
-                          "residual": 8091.0 + 2 * 6672.0 + 69.6}
-# The same for one fused residual + Jacobian launch (brick + gather), per brick
-# schedule (bx, by, bz, threads) of op 2 (the per-element work is the same;
-# the gather's share and idle lanes differ), from one ncu capture of the
-# autotuning launches at 64^3 (sm__sass_thread_inst_executed_op_{fadd,fmul,
-# ffma}{,2}_pred_on, a paired instruction counted as two)
-FUSED_OPS_PER_ELEM_DF64 = {
-    (8, 8, 4, 256): 45_694.2, (8, 4, 4, 256): 45_712.7, (8, 8, 2, 256): 45_725.1,
-    (4, 4, 4, 256): 45_735.9, (4, 4, 8, 256): 45_712.7, (16, 4, 4, 256): 45_701.1,
-    (8, 4, 4, 128): 45_709.7, (4, 4, 4, 128): 45_729.9, (8, 4, 2, 128): 45_743.6,
-    (4, 4, 2, 128): 45_770.2,
-}
-# dram__bytes_read.sum + dram__bytes_write.sum of one double-float Jacobian apply
-# at 64^3 (brick + gather kernels; the writes stay in L2 within the launch) for
-# each brick schedule (bx, by, bz, threads) of the autotuner, from one ncu
-# capture of the autotuning launches (mean of two launches per schedule)
-TRAFFIC_JAC_DF64_64 = {
-    (8, 8, 4, 256): 39_721_472, (8, 4, 4, 256): 41_196_800, (8, 8, 2, 256): 42_375_680,
-    (4, 4, 4, 256): 42_835_584, (4, 4, 8, 256): 41_209_600, (16, 4, 4, 256): 40_376_192,
-    (8, 4, 4, 128): 41_213_568, (4, 4, 4, 128): 42_842_368, (8, 4, 2, 128): 44_231_424,
-    (4, 4, 2, 128): 46_111_616,
-}
-# the same for one fused residual + Jacobian launch (brick + gather), per
-# schedule of op 2, from the same capture as FUSED_OPS_PER_ELEM_DF64
-TRAFFIC_FUSED_DF64_64 = {
-    (8, 8, 4, 256): 53_029_120, (8, 4, 4, 256): 55_985_152, (8, 8, 2, 256): 58_413_312,
-    (4, 4, 4, 256): 59_405_824, (4, 4, 8, 256): 55_988_992, (16, 4, 4, 256): 54_342_912,
-    (8, 4, 4, 128): 55_986_176, (4, 4, 4, 128): 59_353_600, (8, 4, 2, 128): 62_103_552,
-    (4, 4, 2, 128): 66_340_352,
-}
+# dram__bytes_read.sum + dram__bytes_write.sum of one fused native FP64
+# residual + Jacobian launch (brick + gather kernels) on the 64^3 workload,
+# from an ncu capture (None until captured for the current kernels)
+TRAFFIC_FUSED_F64_64 = None
 
 
 def dist_env():
@@ -176,6 +142,30 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def local_rel(a, b):
+    """Largest relative difference of a from b over the momentum and the
+    continuity slots of a nodal field (or the whole of a point array), both
+    norm-wise and for the largest entry."""
+    a, b = a.double(), b.double()
+    groups = [slice(0, 3), slice(3, 4)] if b.shape[-1] == 4 else [slice(None)]
+    worst = 0.0
+    for g in groups:
+        r = b[..., g]
+        n2 = float(r.norm())
+        if n2 == 0.0:
+            continue
+        d = a[..., g] - r
+        worst = max(worst, float(d.norm()) / n2, float(d.abs().max()) / float(r.abs().max()))
+    return worst
+
+
+def vms_flops():
+    """The oracle's operation count per element of the VMS operators, stored
+    by tests/golden/make_vms_flops.py (read here as data)."""
+    with open(os.path.join(ROOT, "tests", "golden", "vms_flops.json")) as f:
+        return json.load(f)
 
 
 def measured_peaks():
@@ -269,16 +259,18 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     mesh = fsi.Mesh(N, rho=1.0, mu=0.01, dt=1e-3, rho_inf=0.5, device=local,
                     stream=stream.cuda_stream)
-    # brick schedules of the double-float operators (shared with native FP64):
-    # the library's autotuner times its candidate shapes on this grid
+    # brick schedules of the VMS operators, one per compute type: the
+    # library's autotuner times its candidate shapes on this grid
     schedule = W["schedule"] = {"autotuned": not args.no_autotune}
-    for op, name in ((0, "residual"), (1, "jacobian"), (2, "vms")):
-        if args.no_autotune:
-            schedule[name] = {"brick": [8, 4, 4] if op == 2 else [8, 8, 4], "threads": 256}
-        else:
-            t = fsi.fsi_mesh_autotune(mesh, op, fsi.FSI_DF64, reps=5)
-            schedule[name] = {"brick": list(t["brick"]), "threads": t["threads"],
-                              "ms": round(t["seconds"] * 1e3, 4)}
+    for prec, tag in ((fsi.FSI_F64, "f64"), (fsi.FSI_DF64, "df64")):
+        for op, name in ((0, "residual"), (1, "jacobian"), (2, "vms")):
+            key = f"{name}_{tag}"
+            if args.no_autotune:
+                schedule[key] = {"brick": [8, 4, 4] if op == 2 else [8, 8, 4], "threads": 256}
+            else:
+                t = fsi.fsi_mesh_autotune(mesh, op, prec, reps=3 if tag == "f64" else 5)
+                schedule[key] = {"brick": list(t["brick"]), "threads": t["threads"],
+                                 "ms": round(t["seconds"] * 1e3, 4)}
 
     def buffers(dtype):
         b = {}
@@ -302,7 +294,7 @@ def run_ours(args):
     # vms: the residual and the Jacobian apply, one fused pass
     ops = ["stage", "vms", "locate", "interp", "spread"]
 
-    def step(b, P, ev=None, vms=fsi.FSI_DF64, dlm=fsi.FSI_DF64):
+    def step(b, P, ev=None, vms=fsi.FSI_F64, dlm=fsi.FSI_F64):
         def mark(i):
             if ev is not None:
                 ev[i].record(stream)
@@ -328,7 +320,7 @@ def run_ours(args):
     side = torch.cuda.Stream(device=dev, priority=-1)
     ev_start, ev_staged, ev_side = (torch.cuda.Event() for _ in range(3))
 
-    def step_cc(b, P, vms=fsi.FSI_DF64, dlm=fsi.FSI_DF64):
+    def step_cc(b, P, vms=fsi.FSI_F64, dlm=fsi.FSI_F64):
         ev_start.record(stream)
         fsi.fsi_stage(mesh, P, b["y"], b["Vn"], b["An"], None, b["U"], b["A"])
         ev_staged.record(stream)
@@ -398,15 +390,20 @@ def run_ours(args):
     for k, r in zip(keys, ref):
         if not torch.equal(b64[k], r):
             raise RuntimeError(f"two-stream step: {k} differs from the one-stream step")
+    # the headline: the step in native FP64 arithmetic throughout
     ms64 = timed_total(lambda: step_cc(b64, P64), args.steps, args.warmup)
     # the operators one after the other on one stream, for the per-operator split
     ms64_seq, per64 = timed(lambda ev: step(b64, P64, ev), args.steps, args.warmup)
     W["ms_seq"] = ms64_seq
     torch.cuda.synchronize()
-    # the same step with native FP64 VMS operators
-    msnat = timed_total(lambda: step_cc(b64, P64, vms=fsi.FSI_F64, dlm=fsi.FSI_F64), args.steps,
-                        args.warmup)
-    pernat = np.zeros(len(ops))
+    fp64_out = {k: b64[k].clone() for k in ("R", "Jx", "u", "F")}
+    # the same step with the VMS operators, interpolation and spreading in
+    # double-float arithmetic (FP64 arrays), and how far it is from FP64
+    df = dict(vms=fsi.FSI_DF64, dlm=fsi.FSI_DF64)
+    msnat = timed_total(lambda: step_cc(b64, P64, **df), args.steps, args.warmup)
+    _, pernat = timed(lambda ev: step(b64, P64, ev, **df), args.steps, args.warmup)
+    torch.cuda.synchronize()
+    W["df64_vs_f64"] = {k: local_rel(b64[k], fp64_out[k]) for k in fp64_out}
     # FP32 operators (xi cast once outside the timed loop)
     b32 = buffers(torch.float32)
     fsi.fsi_locate(mesh, b32["X"], b32["elem"], b32["xi"], b32["cs"], b32["perm"],
@@ -461,6 +458,7 @@ def run_ours(args):
             mark(i)
     _, pernatops = timed(stepnat, args.steps, args.warmup)
     pernat = np.concatenate([pernat, pernatops[:2]])
+    # the e2e arm below runs the headline (native FP64) step
     torch.cuda.synchronize()
     clocks = sampler.stop()
     if args.no_e2e:
@@ -540,20 +538,26 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
             torch.distributed.barrier()
         return 0
 
-    # roofline of the dominant kernel: the double-float Jacobian apply, bound
-    # by the FP32 pipe (plain ALU arithmetic, no tensor cores, no HBM limit)
+    # roofline of the dominant kernel of the FP64 step: the fused native FP64
+    # residual + Jacobian pass (brick + gather), bound by the FP64 pipe (plain
+    # ALU arithmetic, no tensor cores; the HBM bytes take microseconds).
+    # achieved = the oracle's operation count per element (one element's
+    # computation, constants folded, common subexpressions merged) x elements
+    # / the pass's CUDA-event time; peak = the FP64 FMA rate probed in this run
+    # (MEASURED_PEAKS.json has no FP64 figure)
     fma64 = B.fsi_measure_fma_peak(local, fsi.FSI_F64)
     fma32 = B.fsi_measure_fma_peak(local, fsi.FSI_F32)
     E = N ** 3
+    fl = vms_flops()
+    asm_ = (32.0 * E - 4.0 * n) / E
+    flops_elem = {k: fl["per_element"][k]["element"] + (2 if k == "fused" else 1) * asm_
+                  for k in ("residual", "jacobian", "fused")}
     vms_ms = per64[ops.index("vms")]
     schedule = W["schedule"]
-    vms_sched = tuple(schedule["vms"]["brick"]) + (schedule["vms"]["threads"],)
-    ops_fused = FUSED_OPS_PER_ELEM_DF64.get(vms_sched, FUSED_OPS_PER_ELEM_DF64[(8, 8, 4, 256)])
-    achieved = ops_fused * E / (vms_ms * 1e-3)
-    peak_instr = fma32 / 2.0  # FMA operations/s: the probe counts an FMA as 2 flops
-    # DRAM bytes of one launch (brick + gather kernels), from an ncu capture of
-    # this workload; only meaningful for the 64^3 grid it was taken on
-    traffic = TRAFFIC_FUSED_DF64_64.get(vms_sched) if N == N_GRID else None
+    achieved = flops_elem["fused"] * E / (vms_ms * 1e-3)
+    # DRAM bytes of one fused FP64 launch (brick + gather kernels), from an
+    # ncu capture of this workload; only meaningful for the 64^3 grid
+    traffic = TRAFFIC_FUSED_F64_64 if N == N_GRID else None
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
 
@@ -561,17 +565,20 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
         return 4.0 * n / (ms * 1e-3) / 1e9
 
     op_tab = {o: {"ms": round(float(t), 5), "gdof_s": round(gdofs(t), 4)} for o, t in zip(ops, per64)}
-    # native FP64 residual and Jacobian apply timed one after the other
+    # the double-float step: per-operator split and native residual / Jacobian alone
+    df_step_ops = {o: {"ms": round(float(t), 5)} for o, t in zip(ops, native[1][:len(ops)])}
     nat_res, nat_jac = native[1][len(ops)], native[1][len(ops) + 1]
     op_nat = {o: {"ms": round(float(t), 5), "gdof_s": round(gdofs(t), 4)}
               for o, t in zip(("residual", "jacobian"), (nat_res, nat_jac))}
-    op_nat["residual"]["tflop_s"] = round(FLOPS_PER_ELEM["residual"] * E / (nat_res * 1e-3) / 1e12, 4)
-    op_nat["jacobian"]["tflop_s"] = round(FLOPS_PER_ELEM["jacobian"] * E / (nat_jac * 1e-3) / 1e12, 4)
-    op_nat["jacobian"]["frac_of_fp64_peak"] = round(FLOPS_PER_ELEM["jacobian"] * E / (nat_jac * 1e-3) / fma64, 4)
+    for o, t in (("residual", nat_res), ("jacobian", nat_jac)):
+        r = flops_elem[o] * E / (t * 1e-3)
+        op_nat[o]["method_tflop_s"] = round(r / 1e12, 4)
+        op_nat[o]["frac_of_fp64_fma_peak"] = round(r / fma64, 4)
     op_tab32 = {o: {"ms": round(float(t), 5), "gdof_s": round(gdofs(t), 4)}
                 for o, t in zip(ops32, per32[:4])}
     op_tabdf = {o: {"ms": round(float(t), 5), "gdof_s": round(gdofs(t), 4),
-                    "tflop_s_fp64_equivalent": round(FLOPS_PER_ELEM[o] * E / (t * 1e-3) / 1e12, 3)}
+                    "method_tflop_s": round(flops_elem[o] * E / (t * 1e-3) / 1e12, 3),
+                    "frac_of_fp32_fma_peak": round(flops_elem[o] * E / (t * 1e-3) / fma32, 4)}
                 for o, t in zip(("residual", "jacobian"), per32[4:6])}
     # HBM-bound DLM operators: algorithmic bytes per launch
     bytes_interp64 = m * (4 + 24 + 24)
@@ -587,10 +594,15 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
         op_tab[o]["hbm_frac"] = round(gbs / hbm, 4)
         if o in ("locate", "interp", "spread"):
             op_tab[o]["points_per_s"] = round(m / (t * 1e-3), 1)
-    op_tab32["jacobian"]["tflop_s"] = round(FLOPS_PER_ELEM["jacobian"] * E / (per32[1] * 1e-3) / 1e12, 3)
-    op_tab32["jacobian"]["alu_frac"] = round(FLOPS_PER_ELEM["jacobian"] * E / (per32[1] * 1e-3) / fma32, 4)
-    op_tab["vms"]["tflop_s_fp64_equivalent"] = round(
-        (FLOPS_PER_ELEM["residual"] + FLOPS_PER_ELEM["jacobian"]) * E / (vms_ms * 1e-3) / 1e12, 4)
+    for o, t in zip(ops, native[1][:len(ops)]):
+        if o in ("locate", "interp", "spread"):
+            df_step_ops[o]["hbm_frac"] = round(alg_bytes[o] / (t * 1e-3) / 1e9 / hbm, 4)
+    op_tab32["jacobian"]["method_tflop_s"] = round(flops_elem["jacobian"] * E / (per32[1] * 1e-3) / 1e12, 3)
+    op_tab32["jacobian"]["frac_of_fp32_fma_peak"] = round(
+        flops_elem["jacobian"] * E / (per32[1] * 1e-3) / fma32, 4)
+    op_tab["vms"]["method_tflop_s"] = round(achieved / 1e12, 4)
+    df_vms_ms = native[1][ops.index("vms")]
+    df_rate = flops_elem["fused"] * E / (df_vms_ms * 1e-3)
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline and N == N_GRID and m == M_POINTS:
@@ -623,31 +635,38 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
         "ms_per_step_one_stream": W.get("ms_seq"),
-        "scaling": "weak", "vs_baseline": None, "dtype": "df64", "data": "synthetic",
-        "arithmetic": "FP64 arrays; VMS residual/Jacobian, interp and spread in double-float "
-                      "(2 x FP32, ~48-bit significand) on the FP32 pipe, parity ~1e-14 vs the "
-                      "FP64 oracle; locate and stage in FP64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "arithmetic": "native IEEE FP64 throughout: stage, VMS residual + Jacobian apply (one "
+                      "fused pass), location, interpolation, spreading",
         "config": {"workload": WORKLOAD if (N, m) == (N_GRID, M_POINTS) else
                    f"{N}^3 grid + {m} leaflet points (profiling case)",
                    "grid": [N, N, N], "dofs": 4 * n, "points": m,
                    "l2": "flushed between timed steps (write of a buffer > L2)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "roofline": {"bound": "alu",
-                     "kernel": "vms residual + Jacobian apply, df64, fused (brick + gather)",
-                     "achieved": achieved / 1e12, "peak": peak_instr / 1e12,
-                     "unit": "T FP32-pipe operations/s", "frac": achieved / peak_instr,
+                     "kernel": "vms residual + Jacobian apply, native FP64, fused (brick + gather)",
+                     "achieved": achieved / 1e12, "peak": fma64 / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / fma64,
                      "traffic": traffic,
-                     "peak_source": "measured FP32 FMA operation rate (fsi_measure_fma_peak / 2, "
-                                    "this run); operations per element from ncu instruction "
-                                    "counts, a paired FADD2/FMUL2/FFMA2 counted as two"},
+                     "flops_per_element": flops_elem["fused"],
+                     "flops_source": "tests/golden/vms_flops.json: the oracle's operations for one "
+                                     "element's residual and Jacobian apply (oracle/flops.cpp: "
+                                     "constants folded, common subexpressions merged) + the "
+                                     "assembly additions; the oracle sums over the 8 nodes where "
+                                     "the kernel uses the tensor-product butterflies, so the "
+                                     "kernel executes fewer operations than this count",
+                     "peak_source": "FP64 FMA rate probed in this run (fsi_measure_fma_peak; "
+                                    "MEASURED_PEAKS.json has no FP64 figure)"},
         "schedule": schedule,
-        "roofline_jacobian_alone": {
-            "kernel": "vms_jacobian df64 (brick + gather), timed separately (ops_df64)",
-            "achieved": FP32_OPS_PER_ELEM_DF64["jacobian"] * E / (per32[5] * 1e-3) / 1e12,
-            "frac": FP32_OPS_PER_ELEM_DF64["jacobian"] * E / (per32[5] * 1e-3) / peak_instr,
-            "traffic": TRAFFIC_JAC_DF64_64.get(
-                tuple(schedule["jacobian"]["brick"]) + (schedule["jacobian"]["threads"],))
-            if N == N_GRID else None},
+        "step_df64": {
+            "ms": native[0], "gdof_s": gdofs(native[0]),
+            "arithmetic": "VMS, interpolation and spreading in double-float (pairs of FP32, "
+                          "~48-bit significand, FP32 exponent range) on FP64 arrays; stage and "
+                          "location in FP64",
+            "rel_diff_vs_f64_step": W.get("df64_vs_f64"),
+            "ops": df_step_ops,
+            "vms_method_tflop_s": df_rate / 1e12,
+            "vms_frac_of_fp32_fma_peak": df_rate / fma32},
         "cpu_baseline": cpu,
         "e2e": None if e2e_val is None else {
             "value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -658,8 +677,7 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clocks,
         "ops_step": op_tab,
-        "step_native_f64": {"ms": native[0], "gdof_s": 4.0 * n / (native[0] * 1e-3) / 1e9,
-                            "ops": op_nat},
+        "ops_native_f64_alone": op_nat,
         "ops_f32": op_tab32,
         "ops_df64": op_tabdf,
         "ms_per_step_f32_ops": ms32,

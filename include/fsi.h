@@ -196,7 +196,12 @@ fsi_status fsi_locate(fsi_mesh *mesh, int64_t m, const double *X, int32_t *elem,
  * cells are rejected with FSI_ERR_ARG before anything is launched.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture
- * begins.  All calls share the array and it keeps the last call's
+ * begins.  The address is kept per device for the life of the process: it
+ * is not valid across a reset of the device's primary context
+ * (cudaDeviceReset), after which this entry point must not be called.
+ * Grids are checked against the limit factor by factor, so extents whose
+ * product would overflow are refused too.  All calls share the array and it
+ * keeps the last call's
  * contents (each call clears what must start at zero): calls that overlap on
  * the GPU (on different streams, or from different host threads) race and
  * must be ordered by the caller.  No cudaMalloc, cudaFree or allocating
@@ -742,8 +747,8 @@ typedef struct {
 fsi_status fsi_batch_autotune(fsi_batch *batch, int reps, fsi_tune_report *report);
 
 /* Brick schedule of a single mesh for op 0 (residual), 1 (Jacobian) or 2
- * (both fused; twice the shared memory) in
- * `prec`: bx*by*bz elements per CTA of `threads` threads (8 lanes per element;
+ * (both fused; twice the shared memory) in compute type
+ * `prec` (FSI_F64, FSI_F32 or FSI_DF64, each its own): bx*by*bz elements per CTA of `threads` threads (8 lanes per element;
  * threads a multiple of 32 and at most 256; bx*by*bz*8 >= threads not
  * required).  Scratch grows as needed.                                     */
 fsi_status fsi_mesh_set_brick(fsi_mesh *mesh, int op, fsi_prec prec, int bx, int by, int bz,
@@ -754,8 +759,8 @@ fsi_status fsi_mesh_set_brick(fsi_mesh *mesh, int op, fsi_prec prec, int bx, int
  * compute type `prec` on scratch inputs for a fixed
  * set of brick shapes (8x8x4, 8x4x4, 8x8x2, 4x4x4, 4x4x8, 16x4x4 at 256
  * threads; 8x4x4, 4x4x4, 8x4x2, 4x4x2 at 128) and keeps the fastest, as
- * fsi_mesh_set_brick would.  FSI_F64 and FSI_DF64 share one schedule per
- * operator (both store FP64 arrays).  The report's cand_ctas holds each
+ * fsi_mesh_set_brick would.  Each compute type (FSI_F64, FSI_F32,
+ * FSI_DF64) has its own schedule per operator.  The report's cand_ctas holds each
  * candidate's CTA size, ctas_per_sm is 0; seconds is per launch (brick and
  * gather kernels, mean of reps after one warm-up).  Synchronises; results
  * of later calls do not depend on the schedule's choice beyond rounding

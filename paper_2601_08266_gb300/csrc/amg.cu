@@ -672,7 +672,7 @@ __global__ void amg_dense_kernel(int64_t nc, const T *__restrict__ Ainv, const T
     }
 }
 
-int rows_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+int rows_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sm_count() * 16)); }
 // blocks of 256 threads for n rows in groups of w lanes
 int rows_grid(const AmgCsr &A) { return rows_grid(A.rows * A.w); }
 
@@ -717,7 +717,7 @@ template <typename T> fsi_status coarse_solve(fsi_mesh *m, const T *b, T *x)
     const int l = H.nlev - 1;
     if (H.direct) {
         const T *inv = std::is_same<T, double>::value ? (const T *)H.inv64 : (const T *)H.inv32;
-        const int blocks = (int)std::min<int64_t>((H.nc + 7) / 8, 152 * 8);
+        const int blocks = (int)std::min<int64_t>((H.nc + 7) / 8, sm_count() * 8);
         amg_dense_kernel<T><<<blocks, 256, 0, m->stream>>>(H.nc, inv, b, x);
         return check_launch("pressure AMG coarse solve");
     }

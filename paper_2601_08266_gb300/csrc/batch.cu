@@ -393,7 +393,7 @@ fsi_status fsi_batch_create(fsi_mesh *const *meshes, const fsi_batch_item *items
         if (it.m < 0 || (it.m > 0 && (!it.elem || !it.xi || !it.perm || !it.lam || !it.u)))
             return set_error(FSI_ERR_ARG, "batch item %d: bad point arrays", i);
     }
-    FSI_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    FSI_DEVICE(device);
     fsi_batch *b = new (std::nothrow) fsi_batch();
     if (!b) return set_error(FSI_ERR_OOM, "host allocation failed");
     b->device = device;
@@ -424,7 +424,7 @@ fsi_status fsi_batch_create(fsi_mesh *const *meshes, const fsi_batch_item *items
 void fsi_batch_destroy(fsi_batch *b)
 {
     if (!b) return;
-    cudaSetDevice(b->device);
+    fsi::DeviceGuard _fsi_device_guard(b->device);
     cudaStreamSynchronize(b->stream);
     if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
     if (b->graph) cudaGraphDestroy(b->graph);
@@ -442,14 +442,14 @@ fsi_status fsi_batch_run(fsi_batch *b, int mode)
     if (!b) return set_error(FSI_ERR_ARG, "batch is NULL");
     if (mode < FSI_BATCH_PER_INSTANCE || mode > FSI_BATCH_GRAPH)
         return set_error(FSI_ERR_ARG, "bad batch mode %d", mode);
-    FSI_CUDA(cudaSetDevice(b->device), "cudaSetDevice");
+    FSI_DEVICE(b->device);
     return run_mode(b, mode, 7);
 }
 
 fsi_status fsi_batch_autotune(fsi_batch *b, int reps, fsi_tune_report *rep)
 {
     if (!b || !rep || reps < 1) return set_error(FSI_ERR_ARG, "bad autotune arguments");
-    FSI_CUDA(cudaSetDevice(b->device), "cudaSetDevice");
+    FSI_DEVICE(b->device);
     std::memset(rep, 0, sizeof *rep);
     const Brick start = b->brick;
     const int start_ctas = b->ctas_per_sm;
@@ -511,7 +511,7 @@ fsi_status fsi_batch_time(fsi_batch *b, int mode, int reps, double *seconds)
     if (!b || !seconds || reps < 1) return set_error(FSI_ERR_ARG, "bad arguments");
     if (mode < FSI_BATCH_PER_INSTANCE || mode > FSI_BATCH_GRAPH)
         return set_error(FSI_ERR_ARG, "bad batch mode %d", mode);
-    FSI_CUDA(cudaSetDevice(b->device), "cudaSetDevice");
+    FSI_DEVICE(b->device);
     return time_mode(b, mode, 7, reps, seconds);
 }
 

@@ -39,7 +39,7 @@ GridArgs grid_args(const fsi_mesh *m)
     return g;
 }
 
-int blocks_for(int64_t n, int threads, int cap = 152 * 16)
+int blocks_for(int64_t n, int threads, int cap = sm_count() * 16)
 {
     int64_t b = (n + threads - 1) / threads;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
@@ -672,7 +672,7 @@ fsi_status build_cell_table(cudaStream_t s, int64_t E, int64_t m, const int32_t 
         FSI_CUDA(cudaMemsetAsync(fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
         scatter_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, E, elem, cell_start, fill, perm);
         FSI_TRY(check_launch("scatter kernel"));
-        cell_sort_kernel<<<blocks_for((E + 32) / 32 * 32, 256, 152 * 64), 256, 0, s>>>(
+        cell_sort_kernel<<<blocks_for((E + 32) / 32 * 32, 256, sm_count() * 64), 256, 0, s>>>(
             E, m, cell_start, perm);
         FSI_TRY(check_launch("cell sort kernel"));
     }
@@ -696,7 +696,7 @@ fsi_status fsi_locate(fsi_mesh *mesh, int64_t m, const double *X, int32_t *elem,
         return set_error(FSI_ERR_ARG, "fsi_locate: perm given without cell_start");
     if (cell_start != nullptr && perm == nullptr && m > 0)
         return set_error(FSI_ERR_ARG, "fsi_locate: cell_start given without perm");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     if (mesh->tet) {
         int64_t h = 0;
         FSI_TRY(fsi_tet_locate(mesh->tet, m, X, elem, xi, cell_start, perm,
@@ -746,7 +746,7 @@ fsi_status fsi_dlm_interp(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
         return set_error(FSI_ERR_ARG, "bad precision");
     if (m == 0) return FSI_OK;
     if (!elem || !xi || !U || !u) return set_error(FSI_ERR_ARG, "fsi_dlm_interp: NULL argument");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     if (mesh->tet) return fsi_tet_interp(mesh->tet, prec, m, elem, xi, U, u);
     GridArgs g = grid_args(mesh);
     if (prec == FSI_F64)
@@ -773,7 +773,7 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
     if (!F || !cell_start) return set_error(FSI_ERR_ARG, "fsi_dlm_spread: NULL F or cell_start");
     if (m > 0 && (!xi || !perm || !lam))
         return set_error(FSI_ERR_ARG, "fsi_dlm_spread: NULL xi, perm or lam");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     if (mesh->tet)
         return fsi_tet_spread(mesh->tet, prec, m, elem, xi, cell_start, perm, lam, w, F,
                               accumulate);
@@ -782,8 +782,8 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
     const size_t esz = prec == FSI_F32 ? sizeof(float) : sizeof(double);
     FSI_TRY(ensure_spread_scratch(mesh, (size_t)mesh->n_elems * 24 * esz));
     const int64_t E = mesh->n_elems;
-    const int cgrid = blocks_for((E + kSpreadSeg - 1) / kSpreadSeg * 32, 256, 152 * 64);
-    const int ngrid = blocks_for(mesh->n_nodes, 256, 152 * 32);
+    const int cgrid = blocks_for((E + kSpreadSeg - 1) / kSpreadSeg * 32, 256, sm_count() * 64);
+    const int ngrid = blocks_for(mesh->n_nodes, 256, sm_count() * 32);
     if (prec == FSI_F64) {
         spread_cells_kernel<double><<<cgrid, 256, 0, mesh->stream>>>(
             E, (const double *)xi, cell_start, perm, (const double *)lam, (const double *)w,
@@ -819,7 +819,7 @@ fsi_status fsi_interface_scaling(fsi_mesh *mesh, const int32_t *cell_start, doub
         return set_error(FSI_ERR_ARG, "fsi_interface_scaling: s_band must be positive and finite");
     if (layers < 0 || layers > 64)
         return set_error(FSI_ERR_ARG, "fsi_interface_scaling: layers must be in [0, 64]");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     const fsi_grid &g = mesh->grid;
     interface_scaling_kernel<<<blocks_for(mesh->n_nodes, 256), 256, 0, mesh->stream>>>(
         g.N[0], g.N[1], g.N[2], cell_start, s_band, layers, s);
@@ -831,18 +831,21 @@ fsi_status fsi_locate_noalloc(const fsi_grid *grid, int64_t m, const double *X, 
                               int strict, int device, void *cuda_stream)
 {
     if (!grid) return set_error(FSI_ERR_ARG, "fsi_locate_noalloc: grid is NULL");
+    // The cell count bounds every index into the static scratch, so it is
+    // checked after each factor: a product of three large int32 extents
+    // could otherwise wrap around and pass the limit.
     int64_t E = 1;
     for (int k = 0; k < 3; ++k) {
         if (grid->N[k] < 1 || !(grid->h[k] > 0.0) || !std::isfinite(grid->h[k]) ||
             !std::isfinite(grid->x0[k]))
             return set_error(FSI_ERR_ARG, "fsi_locate_noalloc: invalid grid");
+        if (grid->N[k] > kNoAllocMaxCells || E * grid->N[k] > kNoAllocMaxCells)
+            return set_error(FSI_ERR_ARG,
+                             "fsi_locate_noalloc: grid %d x %d x %d has more cells than the "
+                             "static scratch maximum of %lld; use fsi_locate with a mesh instead",
+                             grid->N[0], grid->N[1], grid->N[2], (long long)kNoAllocMaxCells);
         E *= grid->N[k];
     }
-    if (E > kNoAllocMaxCells)
-        return set_error(FSI_ERR_ARG,
-                         "fsi_locate_noalloc: grid has %lld cells, more than the static "
-                         "scratch maximum of %lld; use fsi_locate with a mesh instead",
-                         (long long)E, (long long)kNoAllocMaxCells);
     if (m < 0 || m >= INT32_MAX) return set_error(FSI_ERR_ARG, "fsi_locate_noalloc: m out of range");
     if (m > 0 && (!X || !elem || !xi))
         return set_error(FSI_ERR_ARG, "fsi_locate_noalloc: NULL X, elem or xi");
@@ -850,7 +853,7 @@ fsi_status fsi_locate_noalloc(const fsi_grid *grid, int64_t m, const double *X, 
         return set_error(FSI_ERR_ARG, "fsi_locate_noalloc: perm given without cell_start");
     if (cell_start != nullptr && perm == nullptr && m > 0)
         return set_error(FSI_ERR_ARG, "fsi_locate_noalloc: cell_start given without perm");
-    FSI_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    FSI_DEVICE(device);
     int32_t *scratch = nullptr;
     FSI_TRY(noalloc_scratch(device, &scratch));
     unsigned long long *nout = (unsigned long long *)scratch;
@@ -867,23 +870,7 @@ fsi_status fsi_locate_noalloc(const fsi_grid *grid, int64_t m, const double *X, 
                                                          nout);
         FSI_TRY(check_launch("locate kernel"));
     }
-    if (table) {
-        const int64_t ntiles = (E + kScanTile - 1) / kScanTile;
-        scan_tiles_kernel<<<(int)ntiles, 1024, 0, s>>>(E, fill, cell_start, tiles);
-        FSI_TRY(check_launch("scan tiles kernel"));
-        scan_totals_kernel<<<1, 1024, 0, s>>>(ntiles, tiles);
-        FSI_TRY(check_launch("scan totals kernel"));
-        scan_add_kernel<<<(int)ntiles, 256, 0, s>>>(E, cell_start, tiles);
-        FSI_TRY(check_launch("scan add kernel"));
-        if (m > 0) {
-            FSI_CUDA(cudaMemsetAsync(fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
-            scatter_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, E, elem, cell_start, fill, perm);
-            FSI_TRY(check_launch("scatter kernel"));
-            cell_sort_kernel<<<blocks_for((E + 32) / 32 * 32, 256, 152 * 64), 256, 0, s>>>(
-                E, m, cell_start, perm);
-            FSI_TRY(check_launch("cell sort kernel"));
-        }
-    }
+    if (table) FSI_TRY(build_cell_table(s, E, m, elem, fill, tiles, cell_start, perm));
     if (n_outside || strict) {
         unsigned long long h = 0;
         FSI_CUDA(cudaMemcpyAsync(&h, nout, sizeof h, cudaMemcpyDeviceToHost, s), "memcpy");

@@ -26,6 +26,31 @@ fsi_status check_launch(const char *what);
 
 #define FSI_CUDA(expr, what) FSI_TRY(::fsi::check_cuda((expr), (what)))
 
+// ---------------------------------------------------------------- devices
+// Makes `device` the calling thread's current device for the guard's
+// lifetime and gives the caller's current device back when it ends, so that
+// no entry point leaves the thread on another device.
+class DeviceGuard {
+public:
+    explicit DeviceGuard(int device);
+    ~DeviceGuard();
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+    fsi_status status() const { return st_; }
+
+private:
+    int prev_ = -1;
+    fsi_status st_ = FSI_OK;
+};
+
+#define FSI_DEVICE(dev)                      \
+    ::fsi::DeviceGuard _fsi_device_guard(dev); \
+    FSI_TRY(_fsi_device_guard.status())
+
+// Number of SMs of the current device (queried once per device).  Grid caps
+// are multiples of it, so that they follow the GPU the library runs on.
+int sm_count();
+
 // ---------------------------------------------------------------- 4-vectors
 // 16/32-byte aligned node records so that one node is one vector load.
 template <typename T> struct alignas(4 * sizeof(T)) vec4 {
@@ -67,8 +92,9 @@ struct fsi_mesh {
     cudaStream_t stream;
     int64_t n_nodes, n_elems;
     double alpha_m, alpha_f, gamma;
-    // VMS brick schedule per [op: 0 residual, 1 jacobian, 2 both fused][prec]
-    fsi::Brick brick[3][2];
+    // VMS brick schedule per [op: 0 residual, 1 jacobian, 2 both fused]
+    // [compute type: FSI_F64, FSI_F32, FSI_DF64]
+    fsi::Brick brick[3][3];
     // scratch: per-brick node-block partial sums of the VMS operators
     void *vms_scratch;
     size_t vms_scratch_bytes;

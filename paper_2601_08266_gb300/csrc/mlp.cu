@@ -330,7 +330,7 @@ __global__ void dots3_kernel(int64_t n, const double *x, const double *y, const 
     if (threadIdx.x < 6) partial[6 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
 }
 
-int blocks(int64_t n, int threads = 256, int cap = 152 * 16)
+int blocks(int64_t n, int threads = 256, int cap = sm_count() * 16)
 {
     int64_t b = (n + threads - 1) / threads;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
@@ -387,7 +387,7 @@ fsi_status fsi_mlp_create(int device, void *cuda_stream, int64_t max_batch, fsi_
     *out = nullptr;
     if (max_batch < 1 || max_batch > (1 << 24))
         return set_error(FSI_ERR_ARG, "max_batch must be in [1, 2^24]");
-    FSI_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    FSI_DEVICE(device);
     fsi_mlp *h = new (std::nothrow) fsi_mlp();
     if (!h) return set_error(FSI_ERR_OOM, "host allocation failed");
     h->device = device;
@@ -419,7 +419,7 @@ fsi_status fsi_mlp_create(int device, void *cuda_stream, int64_t max_batch, fsi_
 void fsi_mlp_destroy(fsi_mlp *h)
 {
     if (!h) return;
-    cudaSetDevice(h->device);
+    fsi::DeviceGuard _fsi_device_guard(h->device);
     cudaStreamSynchronize(h->stream);
     float *ptrs[] = {h->Z1, h->H1, h->Z2, h->H2, h->O, h->dO, h->dZ1, h->dZ2, h->X};
     for (float *p : ptrs) cudaFree(p);
@@ -435,7 +435,7 @@ fsi_status fsi_mlp_forward(fsi_mlp *h, const float *params, const float *X, int6
 {
     FSI_TRY(check_mlp(h, B));
     if (!params || !X || !out) return set_error(FSI_ERR_ARG, "NULL argument");
-    FSI_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    FSI_DEVICE(h->device);
     FSI_TRY(forward_impl(h, params, X, B, false));
     FSI_CUDA(cudaMemcpyAsync(out, h->O, B * NO * sizeof(float), cudaMemcpyDeviceToDevice,
                              h->stream),
@@ -448,7 +448,7 @@ fsi_status fsi_mlp_loss_grad(fsi_mlp *h, const float *params, const float *X, co
 {
     FSI_TRY(check_mlp(h, B));
     if (!params || !X || !T || !loss || !grad) return set_error(FSI_ERR_ARG, "NULL argument");
-    FSI_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    FSI_DEVICE(h->device);
     cudaStream_t s = h->stream;
     const float *P = params;
     FSI_TRY(forward_impl(h, P, X, B, true));
@@ -478,7 +478,7 @@ fsi_status fsi_mlp_adam(fsi_mlp *h, float *params, const float *grad, float *m, 
 {
     if (!h) return set_error(FSI_ERR_ARG, "mlp handle is NULL");
     if (!params || !grad || !m || !v || step < 1) return set_error(FSI_ERR_ARG, "bad argument");
-    FSI_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    FSI_DEVICE(h->device);
     const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
     adam_kernel<<<blocks(N_PARAMS), 256, 0, h->stream>>>(N_PARAMS, params, grad, m, v, lr, beta1,
                                                         beta2, eps, c1, c2);
@@ -496,7 +496,7 @@ fsi_status fsi_mlp_features(fsi_mesh *mesh, const double *Vn, const double *y, c
     if (!idx) k = mesh->n_nodes;
     if (k < 0) return set_error(FSI_ERR_ARG, "k < 0");
     if (k == 0) return FSI_OK;
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     features_kernel<<<blocks(k), 256, 0, mesh->stream>>>(mesh->grid.N[0], mesh->grid.N[1],
                                                         mesh->grid.N[2], 0, k, idx, Vn, y, d1,
                                                         d2, in_mean, in_std, X);
@@ -514,7 +514,7 @@ fsi_status fsi_mlp_predict(fsi_mlp *h, fsi_mesh *mesh, const float *params, cons
     if (!params || !in_mean || !in_std || !out_mean || !out_std || !Vn || !y || !d1 || !d2 || !y0)
         return set_error(FSI_ERR_ARG, "NULL argument");
     if (h->device != mesh->device) return set_error(FSI_ERR_ARG, "mlp and mesh on other devices");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     // fused features -> network -> predictor on the tcgen05 tensor cores
     return mlp_predict_tc(mesh->stream, mesh->device, mesh->grid, mesh->n_nodes, params, in_mean,
                           in_std, out_mean, out_std, Vn, y, d1, d2, y0, h->packed, h->tc_err);
@@ -534,7 +534,7 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
     if (judge_prec != FSI_F64 && judge_prec != FSI_DF64)
         return set_error(FSI_ERR_ARG, "judge_prec must be FSI_F64 or FSI_DF64");
     if (st->y == yn) return set_error(FSI_ERR_ARG, "st->y must not alias yn");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     cudaStream_t s = mesh->stream;
     const int64_t n4 = 4 * mesh->n_nodes;
     double *ml = work, *trial = work + n4, *R0 = work + 2 * n4, *Rv = work + 3 * n4,

@@ -32,6 +32,7 @@
 // asynchronous copies.  Every wait is bounded: a wait that runs out sets an
 // error flag that the host reads, the CTA stops issuing work, waits (bounded)
 // for what it issued, frees its TMEM and returns.
+#include <atomic>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -496,16 +497,17 @@ fsi_status mlp_predict_tc(cudaStream_t s, int device, const fsi_grid &g, int64_t
                           void *packed, int *dev_err)
 {
     if (n <= 0) return FSI_OK;
-    static bool attr_set[64] = {};
-    if (device >= 0 && device < 64 && !attr_set[device]) {
+    // the attribute is per device; setting it twice (two threads racing on
+    // the first call) is harmless, the flags only skip later calls
+    static std::atomic<bool> attr_set[64];
+    if (device < 0 || device >= 64 || !attr_set[device].load(std::memory_order_acquire)) {
         FSI_CUDA(cudaFuncSetAttribute(mlp_predict_tc_kernel,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
                  "cudaFuncSetAttribute");
-        attr_set[device] = true;
+        if (device >= 0 && device < 64) attr_set[device].store(true, std::memory_order_release);
     }
-    int sms = 0;
-    FSI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device), "attribute");
-    pack_weights_kernel<<<152 * 4, 256, 0, s>>>(params, (uint8_t *)packed);
+    const int sms = sm_count();
+    pack_weights_kernel<<<sm_count() * 4, 256, 0, s>>>(params, (uint8_t *)packed);
     FSI_TRY(check_launch("pack weights"));
     FSI_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(int), s), "memset");
     TcArgs a{g.N[0], g.N[1], g.N[2], n, params, (const uint8_t *)packed, in_mean, in_std,
@@ -527,7 +529,7 @@ extern "C" fsi_status fsi_wait_selftest(int device, int *timed_out, double *seco
 {
     using namespace fsi;
     if (!timed_out || !seconds) return set_error(FSI_ERR_ARG, "fsi_wait_selftest: NULL output");
-    FSI_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    FSI_DEVICE(device);
     int *err = nullptr;
     FSI_CUDA(cudaMalloc(&err, sizeof(int)), "cudaMalloc");
     cudaEvent_t e0, e1;

@@ -21,7 +21,7 @@ constexpr int kRedGrid = 608;   // fixed partial-sum grid (4 CTAs per SM): deter
 constexpr int kRedThreads = 256;
 constexpr int kDotGroup = 8;    // vectors per multi-dot pass
 
-int grid1d(int64_t n, int threads = 256, int cap = 152 * 16)
+int grid1d(int64_t n, int threads = 256, int cap = sm_count() * 16)
 {
     int64_t b = (n + threads - 1) / threads;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
@@ -999,7 +999,7 @@ fsi_status fsi_coupled_residual(fsi_mesh *mesh, fsi_prec prec, const fsi_step_st
     if (!R) return set_error(FSI_ERR_ARG, "R is NULL");
     if (prec != FSI_F64 && prec != FSI_DF64)
         return set_error(FSI_ERR_ARG, "fsi_coupled_residual: precision must be FSI_F64 or FSI_DF64");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     FSI_TRY(ensure_work(mesh, st->m, 1));
     return coupled_residual_impl(mesh, st, R, prec);
 }
@@ -1011,7 +1011,7 @@ fsi_status fsi_coupled_jacobian_apply(fsi_mesh *mesh, fsi_prec prec, const fsi_s
     FSI_TRY(validate_state(mesh, st));
     if (!x || !Jx || x == Jx) return set_error(FSI_ERR_ARG, "bad x / Jx");
     if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     FSI_TRY(ensure_work(mesh, st->m, 1));
     Work &W = mesh->newton->w;
     FSI_TRY(coupled_residual_impl(mesh, st, W.R));
@@ -1030,7 +1030,7 @@ fsi_status fsi_block_diagonal(fsi_mesh *mesh, fsi_prec prec, const fsi_step_stat
     FSI_TRY(validate_state(mesh, st));
     if (!blocks) return set_error(FSI_ERR_ARG, "blocks is NULL");
     if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     FSI_TRY(ensure_work(mesh, st->m, 1));
     Work &W = mesh->newton->w;
     FSI_TRY(coupled_residual_impl(mesh, st, W.R));
@@ -1060,7 +1060,7 @@ fsi_status fsi_newton_step(fsi_mesh *mesh, const fsi_newton_opts *opts, const fs
         return set_error(FSI_ERR_ARG, "invalid Newton options");
     std::memset(report, 0, sizeof *report);
     const auto t0 = std::chrono::steady_clock::now();
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     FSI_TRY(ensure_work(mesh, st->m, opts->restart));
     mesh->newton->w.precond = opts->precond;
     fsi_status stt = opts->mixed ? newton_impl<float>(mesh, opts, st, report)

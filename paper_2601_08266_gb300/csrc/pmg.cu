@@ -309,7 +309,7 @@ __global__ void dense_apply_kernel(int64_t nc, const T *__restrict__ Ainv, const
     }
 }
 
-int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sm_count() * 16)); }
 
 constexpr int kRowThreads = 128;
 dim3 grid3(const PmgLevel &L)
@@ -456,7 +456,7 @@ template <typename T> fsi_status coarse_solve(fsi_mesh *m, const T *b, T *x)
     if (P.direct) {
         const T *inv = std::is_same<T, double>::value ? (const T *)P.inv64 : (const T *)P.inv32;
         const int warps_per_block = 8;
-        const int blocks = (int)std::min<int64_t>((P.nc + warps_per_block - 1) / warps_per_block, 152 * 8);
+        const int blocks = (int)std::min<int64_t>((P.nc + warps_per_block - 1) / warps_per_block, sm_count() * 8);
         dense_apply_kernel<T><<<blocks, 32 * warps_per_block, 0, m->stream>>>(P.nc, inv, b, x);
         return check_launch("pressure coarse solve");
     }
@@ -633,7 +633,7 @@ fsi_status fsi_pressure_levels(fsi_mesh *mesh, int32_t *n_levels, int32_t *N)
     if (mesh->pressure_amg)
         return set_error(FSI_ERR_ARG, "fsi_pressure_levels: the pressure block is the algebraic "
                                       "multigrid (fsi_pressure_level_sizes)");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     FSI_TRY(pmg_ensure(mesh));
     *n_levels = mesh->pmg->nlev;
     if (N)
@@ -646,7 +646,7 @@ fsi_status fsi_pressure_level_sizes(fsi_mesh *mesh, int32_t *n_levels, int64_t *
 {
     FSI_TRY(validate_mesh(mesh));
     if (!n_levels) return set_error(FSI_ERR_ARG, "fsi_pressure_level_sizes: n_levels is NULL");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     if (uses_amg(mesh)) return amg_level_sizes(mesh, n_levels, n);
     FSI_TRY(pmg_ensure(mesh));
     *n_levels = mesh->pmg->nlev;
@@ -662,7 +662,7 @@ fsi_status fsi_pressure_set_eliminated(fsi_mesh *mesh, const uint8_t *eliminated
         return set_error(FSI_ERR_ARG, "fsi_pressure_set_eliminated: the pressure block is the "
                                       "geometric multigrid (it eliminates faces: "
                                       "fsi_pressure_set_faces; or fsi_pressure_use_amg)");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     std::vector<uint8_t> e((size_t)mesh->n_nodes, 0);
     if (eliminated) {
         FSI_CUDA(cudaMemcpyAsync(e.data(), eliminated, e.size(), cudaMemcpyDeviceToHost,
@@ -683,7 +683,7 @@ fsi_status fsi_pressure_use_amg(fsi_mesh *mesh, int32_t on)
                                           "algebraic multigrid");
         return FSI_OK;
     }
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     if ((on != 0) == mesh->pressure_amg) return FSI_OK;
     // the hierarchy may be in use by work already queued on the stream
     FSI_CUDA(cudaStreamSynchronize(mesh->stream), "sync");
@@ -699,7 +699,7 @@ fsi_status fsi_pressure_set_faces(fsi_mesh *mesh, const int32_t *faces)
     if (mesh->pressure_amg)
         return set_error(FSI_ERR_ARG, "fsi_pressure_set_faces: the pressure block is the "
                                       "algebraic multigrid (fsi_pressure_set_eliminated)");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     int f[6];
     for (int q = 0; q < 6; ++q) f[q] = faces[q] != 0;
     return pmg_set_faces(mesh, f);
@@ -710,7 +710,7 @@ fsi_status fsi_pressure_apply(fsi_mesh *mesh, fsi_prec prec, int32_t level, cons
     FSI_TRY(validate_mesh(mesh));
     FSI_TRY(check_prec(prec));
     if (!x || !y) return set_error(FSI_ERR_ARG, "fsi_pressure_apply: NULL argument");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     if (uses_amg(mesh)) return amg_apply(mesh, prec, level, x, y);
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, false));
@@ -730,7 +730,7 @@ fsi_status fsi_pressure_restrict(fsi_mesh *mesh, fsi_prec prec, int32_t level, c
     FSI_TRY(validate_mesh(mesh));
     FSI_TRY(check_prec(prec));
     if (!r || !b) return set_error(FSI_ERR_ARG, "fsi_pressure_restrict: NULL argument");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     if (uses_amg(mesh)) return amg_restrict(mesh, prec, level, r, b);
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, true));
@@ -753,7 +753,7 @@ fsi_status fsi_pressure_prolong_add(fsi_mesh *mesh, fsi_prec prec, int32_t level
     FSI_TRY(validate_mesh(mesh));
     FSI_TRY(check_prec(prec));
     if (!xc || !x) return set_error(FSI_ERR_ARG, "fsi_pressure_prolong_add: NULL argument");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     if (uses_amg(mesh)) return amg_prolong_add(mesh, prec, level, xc, x);
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, true));
@@ -777,7 +777,7 @@ fsi_status fsi_pressure_smooth(fsi_mesh *mesh, fsi_prec prec, int32_t level, int
     FSI_TRY(check_prec(prec));
     if (!b || !x) return set_error(FSI_ERR_ARG, "fsi_pressure_smooth: NULL argument");
     if (degree < 1 || degree > 64) return set_error(FSI_ERR_ARG, "fsi_pressure_smooth: degree 1..64");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     if (uses_amg(mesh)) return amg_smooth(mesh, prec, level, degree, b, x, from_zero);
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, false));
@@ -810,7 +810,7 @@ fsi_status fsi_pressure_vcycle(fsi_mesh *mesh, fsi_prec prec, const void *b, voi
     FSI_TRY(check_prec(prec));
     if (!b || !x) return set_error(FSI_ERR_ARG, "fsi_pressure_vcycle: NULL argument");
     if (b == x) return set_error(FSI_ERR_ARG, "fsi_pressure_vcycle: b and x must not alias");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     if (uses_amg(mesh)) {
         if (prec == FSI_F64) return amg_vcycle<double>(mesh, (const double *)b, (double *)x);
         return amg_vcycle<float>(mesh, (const float *)b, (float *)x);

@@ -26,7 +26,7 @@ template <typename T> __global__ void fma_peak_kernel(int iters, T *out)
 
 template <typename T> fsi_status run(int device, double *rate)
 {
-    FSI_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    FSI_DEVICE(device);
     cudaDeviceProp prop;
     FSI_CUDA(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
     const int threads = 256, blocks = prop.multiProcessorCount * 8;

@@ -1,5 +1,6 @@
 // runtime.cu -- handles, errors, validation and the generalized-alpha stage
 // kernel of libfsi (C ABI in include/fsi.h).
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -31,6 +32,35 @@ fsi_status check_cuda(cudaError_t e, const char *what)
 }
 
 fsi_status check_launch(const char *what) { return check_cuda(cudaGetLastError(), what); }
+
+DeviceGuard::DeviceGuard(int device)
+{
+    if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+    if (prev_ != device) st_ = check_cuda(cudaSetDevice(device), "cudaSetDevice");
+}
+
+DeviceGuard::~DeviceGuard()
+{
+    int cur = -1;
+    if (prev_ >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev_) cudaSetDevice(prev_);
+}
+
+int sm_count()
+{
+    constexpr int kMaxDevices = 64;
+    static std::atomic<int> cached[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 152;
+    if (dev < kMaxDevices) {
+        int v = cached[dev].load(std::memory_order_relaxed);
+        if (v > 0) return v;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+        n = 152;
+    if (dev < kMaxDevices) cached[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
 
 static fsi_status validate_physics(const fsi_physics *p)
 {
@@ -153,7 +183,7 @@ __global__ void advance_kernel(int64_t n, T dt, T gamma, const vec4<T> *__restri
 static int grid_for(int64_t n, int threads)
 {
     int64_t b = (n + threads - 1) / threads;
-    const int cap = 152 * 16;
+    const int cap = sm_count() * 16;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
@@ -185,7 +215,7 @@ fsi_status fsi_mesh_create(const fsi_grid *grid, const fsi_physics *phys, int de
     FSI_CUDA(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
     if (device < 0 || device >= ndev)
         return set_error(FSI_ERR_ARG, "device %d out of range (%d devices)", device, ndev);
-    FSI_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    FSI_DEVICE(device);
     fsi_mesh *m = new (std::nothrow) fsi_mesh();
     if (!m) return set_error(FSI_ERR_OOM, "host allocation of the mesh handle failed");
     m->grid = *grid;
@@ -198,7 +228,7 @@ fsi_status fsi_mesh_create(const fsi_grid *grid, const fsi_physics *phys, int de
     // the fused pass keeps two element buffers in shared memory: half as many
     // elements per brick keeps two CTAs per SM
     for (int op = 0; op < 3; ++op)
-        for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < 3; ++p)
             m->brick[op][p] = op == 2 ? Brick{8, 4, 4, 256} : Brick{8, 8, 4, 256};
     fsi_status st = FSI_OK;
     // cell-hash scratch: fill counters [E+1], scan block sums, counters
@@ -223,7 +253,7 @@ fsi_status fsi_mesh_create(const fsi_grid *grid, const fsi_physics *phys, int de
 void fsi_mesh_destroy(fsi_mesh *m)
 {
     if (!m) return;
-    cudaSetDevice(m->device);
+    fsi::DeviceGuard _fsi_device_guard(m->device);
     cudaStreamSynchronize(m->stream);
     cudaFree(m->vms_scratch);
     cudaFree(m->hash_fill);
@@ -264,7 +294,7 @@ fsi_status fsi_mesh_set_coordinates(fsi_mesh *m, const double *X)
 {
     FSI_TRY(validate_mesh(m));
     FSI_TRY(require_structured(m, "fsi_mesh_set_coordinates"));
-    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    FSI_DEVICE(m->device);
     FSI_CUDA(cudaStreamSynchronize(m->stream), "sync");
     for (void *&g : m->map_geo) {
         cudaFree(g);
@@ -287,7 +317,7 @@ fsi_status fsi_mesh_set_coordinates(fsi_mesh *m, const double *X)
         }
     }
     int64_t blocks = (m->n_nodes + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > sm_count() * 16) blocks = sm_count() * 16;
     pad_coords_kernel<<<(int)blocks, 256, 0, m->stream>>>(m->n_nodes, X, (double4 *)m->coords64,
                                                           (float4 *)m->coords32);
     return check_launch("pad coordinates kernel");
@@ -308,11 +338,11 @@ fsi_status fsi_mesh_set_brick(fsi_mesh *m, int op, fsi_prec prec, int bx, int by
 {
     FSI_TRY(validate_mesh(m));
     FSI_TRY(require_structured(m, "fsi_mesh_set_brick"));
-    if (op < 0 || op > 2 || (prec != FSI_F64 && prec != FSI_F32))
+    if (op < 0 || op > 2 || (prec != FSI_F64 && prec != FSI_F32 && prec != FSI_DF64))
         return set_error(FSI_ERR_ARG, "bad op or precision");
     if (bx < 1 || by < 1 || bz < 1 || threads < 32 || threads > 256 || threads % 32 != 0)
         return set_error(FSI_ERR_ARG, "bad brick %dx%dx%d / %d threads", bx, by, bz, threads);
-    const size_t smem = (op == 2 ? 2 : 1) * (size_t)bx * by * bz * 8 * 4 * (prec == FSI_F64 ? 8 : 4);
+    const size_t smem = (op == 2 ? 2 : 1) * (size_t)bx * by * bz * 8 * 4 * (prec == FSI_F32 ? 4 : 8);
     if (smem > 200 * 1024)
         return set_error(FSI_ERR_ARG, "brick %dx%dx%d needs %zu bytes of shared memory", bx, by,
                          bz, smem);
@@ -335,7 +365,7 @@ fsi_status fsi_stage(fsi_mesh *m, fsi_prec prec, const void *y, const void *Vn, 
     if (!y || !Vn || !An || !U || !A)
         return set_error(FSI_ERR_ARG, "fsi_stage: NULL array argument");
     if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
-    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    FSI_DEVICE(m->device);
     const int threads = 256;
     const int blocks = grid_for(m->n_nodes, threads);
     const double dt = m->phys.dt;
@@ -357,7 +387,7 @@ fsi_status fsi_advance_history(fsi_mesh *m, fsi_prec prec, const void *y, void *
     FSI_TRY(validate_mesh(m));
     if (!y || !Vn || !An) return set_error(FSI_ERR_ARG, "fsi_advance_history: NULL argument");
     if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
-    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    FSI_DEVICE(m->device);
     const int threads = 256;
     const int blocks = grid_for(m->n_nodes, threads);
     if (prec == FSI_F64)
@@ -380,7 +410,7 @@ fsi_status fsi_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A
         return set_error(FSI_ERR_ARG, "fsi_residual: R aliases an input");
     if (prec != FSI_F64 && prec != FSI_F32 && prec != FSI_DF64)
         return set_error(FSI_ERR_ARG, "bad precision");
-    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    FSI_DEVICE(m->device);
     return vms_residual(m, prec, U, A, f, R);
 }
 
@@ -397,7 +427,7 @@ fsi_status fsi_residual_jacobian_apply(fsi_mesh *m, fsi_prec prec, const void *U
     if (R == Jx) return set_error(FSI_ERR_ARG, "fsi_residual_jacobian_apply: R and Jx alias");
     if (prec != FSI_F64 && prec != FSI_F32 && prec != FSI_DF64)
         return set_error(FSI_ERR_ARG, "bad precision");
-    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    FSI_DEVICE(m->device);
     return vms_residual_jacobian(m, prec, U, A, f, x, R, Jx);
 }
 
@@ -411,7 +441,7 @@ fsi_status fsi_jacobian_apply(fsi_mesh *m, fsi_prec prec, const void *U, const v
         return set_error(FSI_ERR_ARG, "fsi_jacobian_apply: Jx aliases an input");
     if (prec != FSI_F64 && prec != FSI_F32 && prec != FSI_DF64)
         return set_error(FSI_ERR_ARG, "bad precision");
-    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    FSI_DEVICE(m->device);
     return vms_jacobian(m, prec, U, A, f, x, Jx);
 }
 

@@ -315,7 +315,7 @@ __global__ void positions_kernel(int64_t n3, const double *X, const double *u, d
 int grid_of(int64_t n, int threads = 128)
 {
     const int64_t b = (n + threads - 1) / threads;
-    return (int)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
+    return (int)(b < 1 ? 1 : (b > sm_count() * 32 ? sm_count() * 32 : b));
 }
 
 SolidArgs args_of(const fsi_solid *b, const double g[3])
@@ -401,7 +401,7 @@ fsi_status fsi_solid_create(fsi_mesh *mesh, int64_t n_nodes, int64_t n_elems, co
     if (!X || !conn) return set_error(FSI_ERR_ARG, "fsi_solid_create: NULL array");
     if (!(rho_s > 0.0) || !(mu_s > 0.0) || !(lambda_s >= 0.0))
         return set_error(FSI_ERR_ARG, "fsi_solid_create: rho_s, mu_s > 0 and lambda_s >= 0");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     // node -> element-slot table, built on the host from the connectivity
     std::vector<int32_t> hconn((size_t)n_elems * 8);
     FSI_CUDA(cudaMemcpy(hconn.data(), conn, hconn.size() * sizeof(int32_t), cudaMemcpyDeviceToHost),
@@ -460,7 +460,7 @@ fsi_status fsi_solid_create(fsi_mesh *mesh, int64_t n_nodes, int64_t n_elems, co
 void fsi_solid_destroy(fsi_solid *b)
 {
     if (!b) return;
-    cudaSetDevice(b->mesh->device);
+    fsi::DeviceGuard _fsi_device_guard(b->mesh->device);
     cudaStreamSynchronize(b->mesh->stream);
     cudaFree(b->X);
     cudaFree(b->conn);
@@ -476,7 +476,7 @@ fsi_status fsi_solid_residual(fsi_solid *b, const double *u_af, const double *v_
     if (!b) return set_error(FSI_ERR_ARG, "fsi_solid_residual: solid is NULL");
     if (!u_af || !v_af || !a_am || !u_n || !R)
         return set_error(FSI_ERR_ARG, "fsi_solid_residual: NULL argument");
-    FSI_CUDA(cudaSetDevice(b->mesh->device), "cudaSetDevice");
+    FSI_DEVICE(b->mesh->device);
     return solid_residual_impl(b, u_af, v_af, a_am, u_n, g, R);
 }
 
@@ -487,7 +487,7 @@ fsi_status fsi_solid_tangent_apply(fsi_solid *b, fsi_prec prec, const void *u_af
     if (!u_af || !u_n || !x || !Jx)
         return set_error(FSI_ERR_ARG, "fsi_solid_tangent_apply: NULL argument");
     if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
-    FSI_CUDA(cudaSetDevice(b->mesh->device), "cudaSetDevice");
+    FSI_DEVICE(b->mesh->device);
     if (prec == FSI_F64)
         return solid_tangent_impl<double>(b, (const double *)u_af, u_n, (const double *)x,
                                           (double *)Jx);
@@ -499,7 +499,7 @@ fsi_status fsi_solid_stage(fsi_solid *b, const double *u, const double *v, const
 {
     if (!b || !u || !v || !a || !a_next || !u_af || !v_af || !a_am)
         return set_error(FSI_ERR_ARG, "fsi_solid_stage: NULL argument");
-    FSI_CUDA(cudaSetDevice(b->mesh->device), "cudaSetDevice");
+    FSI_DEVICE(b->mesh->device);
     return solid_stage_impl(b, u, v, a, a_next, u_af, v_af, a_am);
 }
 
@@ -507,7 +507,7 @@ fsi_status fsi_solid_advance(fsi_solid *b, double *u, double *v, double *a, cons
 {
     if (!b || !u || !v || !a || !a_next)
         return set_error(FSI_ERR_ARG, "fsi_solid_advance: NULL argument");
-    FSI_CUDA(cudaSetDevice(b->mesh->device), "cudaSetDevice");
+    FSI_DEVICE(b->mesh->device);
     const fsi_mesh *m = b->mesh;
     const double beta = 0.25 * (1.0 + m->alpha_m - m->alpha_f) * (1.0 + m->alpha_m - m->alpha_f);
     solid_advance_kernel<<<grid_of(3 * b->ns, 256), 256, 0, m->stream>>>(
@@ -518,7 +518,7 @@ fsi_status fsi_solid_advance(fsi_solid *b, double *u, double *v, double *a, cons
 fsi_status fsi_solid_positions(fsi_solid *b, const double *u, double *x)
 {
     if (!b || !u || !x) return set_error(FSI_ERR_ARG, "fsi_solid_positions: NULL argument");
-    FSI_CUDA(cudaSetDevice(b->mesh->device), "cudaSetDevice");
+    FSI_DEVICE(b->mesh->device);
     positions_kernel<<<grid_of(3 * b->ns, 256), 256, 0, b->mesh->stream>>>(3 * b->ns, b->X, u, x);
     return check_launch("solid positions kernel");
 }

@@ -617,7 +617,7 @@ __global__ void pad_tet_coords_kernel(int64_t n, const double *X, double4 *X64, 
     }
 }
 
-int grid_for(int64_t n, int threads, int cap = 152 * 32)
+int grid_for(int64_t n, int threads, int cap = sm_count() * 32)
 {
     int64_t b = (n + threads - 1) / threads;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
@@ -692,7 +692,7 @@ fsi_status tet_vms(fsi_tetmesh *m, const void *U, const void *A, const void *f, 
     TetArgs<T> P = tet_args<T>(m, U, A, f, x);
     P.geo = (const T *)m->geo[geo_slot<T>()];
     const int64_t threads = 4 * m->n_elems;
-    tet_vms_kernel<T, JAC><<<grid_for(threads, 256, 152 * 64), 256, 0, m->stream>>>(P);
+    tet_vms_kernel<T, JAC><<<grid_for(threads, 256, sm_count() * 64), 256, 0, m->stream>>>(P);
     FSI_TRY(check_launch("tet vms kernel"));
     tet_gather_kernel<T><<<grid_for(m->n_nodes, 256), 256, 0, m->stream>>>(
         m->n_nodes, m->node_start, m->node_slot, P.slots, (vec4<S> *)out);
@@ -796,7 +796,7 @@ fsi_status fsi_tetmesh_create(int64_t n_nodes, const double *X, int64_t n_tets,
     if (!(phys->rho > 0.0) || !(phys->mu >= 0.0) || !(phys->dt > 0.0) || !(phys->C_I >= 0.0) ||
         !(phys->C_T >= 0.0) || !(phys->rho_inf >= 0.0 && phys->rho_inf <= 1.0))
         return set_error(FSI_ERR_ARG, "invalid physics");
-    FSI_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    FSI_DEVICE(device);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     // host copies for the set-up structures
     std::vector<int32_t> ht((size_t)n_tets * 4);
@@ -963,7 +963,7 @@ fsi_status fsi_tetmesh_create(int64_t n_nodes, const double *X, int64_t n_tets,
 void fsi_tetmesh_destroy(fsi_tetmesh *m)
 {
     if (!m) return;
-    cudaSetDevice(m->device);
+    fsi::DeviceGuard _fsi_device_guard(m->device);
     if (m->stream) cudaStreamSynchronize(m->stream);
     cudaFree(m->X64);
     cudaFree(m->X32);
@@ -987,7 +987,7 @@ fsi_status fsi_tet_residual(fsi_tetmesh *m, fsi_prec prec, const void *U, const 
 {
     FSI_TRY(validate_tetmesh(m));
     if (!U || !A || !R) return set_error(FSI_ERR_ARG, "fsi_tet_residual: NULL argument");
-    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    FSI_DEVICE(m->device);
     if (prec == FSI_F64) return tet_vms<double, false>(m, U, A, f, nullptr, R);
     if (prec == FSI_DF64) return tet_vms<df64, false>(m, U, A, f, nullptr, R);
     if (prec == FSI_F32) return tet_vms<float, false>(m, U, A, f, nullptr, R);
@@ -999,7 +999,7 @@ fsi_status fsi_tet_jacobian_apply(fsi_tetmesh *m, fsi_prec prec, const void *U, 
 {
     FSI_TRY(validate_tetmesh(m));
     if (!U || !A || !x || !Jx) return set_error(FSI_ERR_ARG, "fsi_tet_jacobian_apply: NULL argument");
-    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    FSI_DEVICE(m->device);
     if (prec == FSI_F64) return tet_vms<double, true>(m, U, A, f, x, Jx);
     if (prec == FSI_DF64) return tet_vms<df64, true>(m, U, A, f, x, Jx);
     if (prec == FSI_F32) return tet_vms<float, true>(m, U, A, f, x, Jx);
@@ -1017,7 +1017,7 @@ fsi_status fsi_tet_locate(fsi_tetmesh *m, int64_t np, const double *P, int32_t *
         return set_error(FSI_ERR_ARG, "fsi_tet_locate: perm given without cell_start");
     if (cell_start != nullptr && perm == nullptr && np > 0)
         return set_error(FSI_ERR_ARG, "fsi_tet_locate: cell_start given without perm");
-    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    FSI_DEVICE(m->device);
     cudaStream_t s = m->stream;
     const int64_t E = m->n_elems;
     const bool table = cell_start != nullptr;
@@ -1054,7 +1054,7 @@ fsi_status fsi_tet_interp(fsi_tetmesh *m, fsi_prec prec, int64_t np, const int32
     if (np < 0 || np >= INT32_MAX) return set_error(FSI_ERR_ARG, "fsi_tet_interp: bad m");
     if (np == 0) return FSI_OK;
     if (!elem || !lam || !U || !u) return set_error(FSI_ERR_ARG, "fsi_tet_interp: NULL argument");
-    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    FSI_DEVICE(m->device);
     const int g = grid_for(np, 256);
     if (prec == FSI_F64)
         tet_interp_kernel<double><<<g, 256, 0, m->stream>>>(np, m->n_elems, m->tets, elem,
@@ -1083,9 +1083,9 @@ fsi_status fsi_tet_spread(fsi_tetmesh *m, fsi_prec prec, int64_t np, const int32
     if (!F || !cell_start) return set_error(FSI_ERR_ARG, "fsi_tet_spread: NULL F or cell_start");
     if (np > 0 && (!lam || !perm || !lamv))
         return set_error(FSI_ERR_ARG, "fsi_tet_spread: NULL lam, perm or forces");
-    FSI_CUDA(cudaSetDevice(m->device), "cudaSetDevice");
+    FSI_DEVICE(m->device);
     const int64_t E = m->n_elems;
-    const int cg = grid_for((E + 7) / 8 * 32, 256, 152 * 64);
+    const int cg = grid_for((E + 7) / 8 * 32, 256, sm_count() * 64);
     const int ng = grid_for(m->n_nodes, 256);
     cudaStream_t s = m->stream;
     if (prec == FSI_F64) {

@@ -79,6 +79,13 @@ __global__ void __launch_bounds__(256) mapped_geo_kernel(const VmsArgs<T> P,
     }
 }
 
+// index of the compute type in fsi_mesh::brick (its fsi_prec)
+template <typename T> constexpr int prec_slot()
+{
+    return std::is_same<T, double>::value ? FSI_F64
+                                          : (std::is_same<T, float>::value ? FSI_F32 : FSI_DF64);
+}
+
 template <typename T> constexpr int geo_slot()
 {
     return std::is_same<T, double>::value ? 0 : (std::is_same<T, float>::value ? 1 : 2);
@@ -103,7 +110,7 @@ template <typename T> fsi_status ensure_map_geo(fsi_mesh *m, const VmsArgs<T> &P
                          bytes);
     }
     int64_t blocks = (m->n_elems + 31) / 32;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > sm_count() * 8) blocks = sm_count() * 8;
     mapped_geo_kernel<T><<<(int)blocks, 256, 0, m->stream>>>(P, (typename GeoStore<T>::type *)tab);
     return check_launch("mapped geometry kernel");
 }
@@ -124,7 +131,7 @@ fsi_status launch_geo(fsi_mesh *m, const void *U, const void *A, const void *f, 
                       void *out, void *R = nullptr)
 {
     using S = typename StorageOf<T>::type;
-    const Brick &b = m->brick[FUSED ? 2 : (JAC ? 1 : 0)][sizeof(S) == 8 ? FSI_F64 : FSI_F32];
+    const Brick &b = m->brick[FUSED ? 2 : (JAC ? 1 : 0)][prec_slot<T>()];
     FSI_TRY(ensure_vms_scratch(m, b, (FUSED ? 2 : 1) * sizeof(T)));
     VmsArgs<T> P = make_args<T>(m, b, U, A, f, x, out);
     if constexpr (MAPPED) {
@@ -153,7 +160,7 @@ fsi_status launch_geo(fsi_mesh *m, const void *U, const void *A, const void *f, 
     FSI_TRY(check_launch("vms brick kernel"));
     const int threads = 256;
     int64_t nb = (m->n_nodes + threads - 1) / threads;
-    if (nb > 152 * 32) nb = 152 * 32;
+    if (nb > sm_count() * 32) nb = sm_count() * 32;
     vms_gather_kernel<T, FUSED><<<(int)nb, threads, 0, m->stream>>>(P);
     return check_launch("vms gather kernel");
 }
@@ -219,7 +226,7 @@ fsi_status time_op(fsi_mesh *m, int op, int reps, const void *U, const void *A, 
 template <typename T> fsi_status autotune(fsi_mesh *m, int op, int reps, fsi_tune_report *rep)
 {
     using S = typename StorageOf<T>::type;
-    const int slot = sizeof(S) == 8 ? FSI_F64 : FSI_F32;
+    const int slot = prec_slot<T>();
     const Brick start = m->brick[op][slot];
     const size_t bytes = (size_t)m->n_nodes * sizeof(vec4<S>);
     void *buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -237,7 +244,7 @@ template <typename T> fsi_status autotune(fsi_mesh *m, int op, int reps, fsi_tun
     Brick best_brick = start;
     int tried = 0;
     if (st == FSI_OK) {
-        fill_state_kernel<S><<<152 * 4, 256, 0, m->stream>>>(m->n_nodes, (vec4<S> *)buf[0],
+        fill_state_kernel<S><<<sm_count() * 4, 256, 0, m->stream>>>(m->n_nodes, (vec4<S> *)buf[0],
                                                              (vec4<S> *)buf[1], (vec4<S> *)buf[2]);
         st = check_launch("autotune fill");
     }
@@ -320,7 +327,7 @@ extern "C" fsi_status fsi_mesh_autotune(fsi_mesh *mesh, int op, fsi_prec prec, i
     if (op < 0 || op > 2 || reps < 1 || !report ||
         (prec != FSI_F64 && prec != FSI_F32 && prec != FSI_DF64))
         return set_error(FSI_ERR_ARG, "fsi_mesh_autotune: bad arguments");
-    FSI_CUDA(cudaSetDevice(mesh->device), "cudaSetDevice");
+    FSI_DEVICE(mesh->device);
     std::memset(report, 0, sizeof *report);
     if (prec == FSI_F64) return autotune<double>(mesh, op, reps, report);
     if (prec == FSI_DF64) return autotune<df64>(mesh, op, reps, report);

@@ -1,13 +1,17 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on
 the same seeded inputs.
 
-Tolerances (norm-wise relative error ||gpu - oracle|| / ||oracle|| per operator
-output): 1e-12 in FP64, 1e-5 in FP32 (FP32 inputs rounded from the FP64 data;
-the oracle runs in FP64 on the rounded values).  Location indices and the cell
+Tolerances: 1e-12 in FP64 and double-float, 1e-5 in FP32 (FP32 inputs rounded
+from the FP64 data; the oracle runs in FP64 on the rounded values), held by
+every part of an output (tests/parity.py): the momentum and continuity rows
+apart, the boundary and interior nodes apart, norm-wise and for the largest
+entry error.  Location indices and the cell
 table are compared bit for bit.
 """
 import numpy as np
 import pytest
+
+import parity
 
 from paper_2601_08266_gb300 import inputs
 
@@ -35,7 +39,15 @@ def H(t):
     return t.detach().cpu().numpy().astype(np.float64)
 
 
-def rel(a, b):
+def rel(a, b, grid=None):
+    """Worst local relative error of a against b: momentum and continuity
+    rows, boundary and interior nodes (when grid is given) apart, norm-wise
+    and largest entry (tests/parity.py)."""
+    return parity.rel_local(np.asarray(a), b, grid)
+
+
+def rel_norm(a, b):
+    """Norm-wise distance of a whole solution vector from a reference one."""
     nb = np.linalg.norm(b)
     return np.linalg.norm(np.asarray(a) - b) / (nb if nb > 0 else 1.0)
 
@@ -74,7 +86,7 @@ def vms_case(fsi, oracle, mesh, grid, p, U, A, f, x, prec):
     c_a, c_v = oracle.timeint.chain_factors(p["rho_inf"], p["dt"])
     Ro = oracle.core.residual(grid, p, U, A, f=f)
     Jo = oracle.core.jacobian_apply(grid, p, U, A, x, c_a, c_v, f=f)
-    return rel(H(R), Ro), rel(H(Jx), Jo), (R, Jx)
+    return rel(H(R), Ro, grid.N), rel(H(Jx), Jo, grid.N), (R, Jx)
 
 
 # ---------------------------------------------------------------- stage
@@ -203,7 +215,7 @@ def dlm_check(fsi, oracle, N, X, prec, weighted, accumulate, seed=0, h=None, x0=
     uo = oracle.core.interp(grid, eo, xiw, U)
     Fo = oracle.core.spread(grid, eo, xiw, lam, w=w, F=F0, accumulate=accumulate)
     assert rel(g["u"], uo) < TOL[prec]
-    assert rel(g["F"][:, :3], Fo[:, :3]) < TOL[prec]
+    assert rel(g["F"][:, :3], Fo[:, :3], grid.N) < TOL[prec]
     # slot 3 is never written
     assert np.array_equal(g["F"][:, 3], F0[:, 3].astype(np.float32).astype(np.float64)
                           if prec == "f32" else F0[:, 3])
@@ -310,3 +322,119 @@ def test_interface_scaling_matches_oracle(fsi, oracle, layers):
     x = rng.uniform(-1, 1, (mesh.n_nodes, 4))
     eR, eJ, _ = vms_case(fsi, oracle, mesh, grid, p, U, A, None, x, "df64")
     assert eR < 1e-12 and eJ < 1e-12
+
+
+# ---------------------------------------------------------------- full sizes
+_C3 = {}
+
+
+def config3_inputs():
+    """128^3 channel-like state (8.6 M DOFs): inflow profile
+    v_x = 16 y(1-y) z(1-z) plus 0.01 x a seeded Fourier field, Fourier
+    pressure, acceleration and direction; 1 M points on three leaflets."""
+    if not _C3:
+        N = 128
+        ax = np.arange(N + 1) / N
+        z, y, _ = np.meshgrid(ax, ax, ax, indexing="ij")
+        U = 0.01 * inputs.fourier_field(N, seed=40)
+        U[:, 0] += (16.0 * y * (1 - y) * z * (1 - z)).ravel()
+        A = np.zeros_like(U)
+        A[:, :3] = inputs.fourier_field(N, seed=41, ncomp=3)
+        A[:, 3] = 1.0
+        _C3.update(N=N, U=U, A=A, x=inputs.uniform_nodal(N, seed=42),
+                   X=inputs.leaflet_points(1_000_000, seed=43))
+    return _C3
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64"])
+def test_vms_config3_full_size(fsi, oracle, prec):
+    """128^3 grid (2.1 M elements, 8.6 M DOFs, mu = 1e-3): the whole residual
+    and Jacobian apply against the oracle, part by part (32-bit index
+    products of the brick and gather kernels are largest here)."""
+    W = config3_inputs()
+    mesh, grid, p = make(fsi, oracle, W["N"], mu=1e-3)
+    eR, eJ, _ = vms_case(fsi, oracle, mesh, grid, p, W["U"], W["A"], None, W["x"], prec)
+    print(f"\n128^3 {prec}: residual {eR:.2e}, Jacobian {eJ:.2e}")
+    assert eR < TOL[prec], eR
+    assert eJ < TOL[prec], eJ
+    mesh.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64"])
+def test_dlm_config3_full_size(fsi, oracle, prec):
+    """128^3 grid, 1 M leaflet points: location and cell table bit for bit,
+    interpolation and weighted accumulating spreading part by part."""
+    W = config3_inputs()
+    g = dlm_check(fsi, oracle, W["N"], W["X"], prec, True, True, seed=44)
+    assert g["nout"] == 0
+
+
+def test_fused_config3_full_size(fsi, oracle):
+    """The fused residual + Jacobian pass of the benchmark step at 128^3 in
+    native FP64 and double-float against the oracle."""
+    import torch
+    W = config3_inputs()
+    mesh, grid, p = make(fsi, oracle, W["N"], mu=1e-3)
+    Ud, Ad, xd = T(W["U"]), T(W["A"]), T(W["x"])
+    c_a, c_v = oracle.timeint.chain_factors(p["rho_inf"], p["dt"])
+    Ro = oracle.core.residual(grid, p, W["U"], W["A"])
+    Jo = oracle.core.jacobian_apply(grid, p, W["U"], W["A"], W["x"], c_a, c_v)
+    for P in (fsi.FSI_F64, fsi.FSI_DF64):
+        R = torch.empty_like(Ud)
+        J = torch.empty_like(Ud)
+        fsi.fsi_residual_jacobian_apply(mesh, P, Ud, Ad, None, xd, R, J)
+        torch.cuda.synchronize()
+        assert rel(H(R), Ro, grid.N) < 1e-12 and rel(H(J), Jo, grid.N) < 1e-12
+    mesh.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
+def test_vms_paper_scales(fsi, oracle, prec):
+    """Inputs at the scales of the paper's problems (CGS units): element size
+    1e-3 cm, time step 1e-5 s (free-falling sphere), blood-like viscosity
+    0.035 P, velocities up to 100 cm/s, accelerations up to 1e6 cm/s^2 and a
+    pressure of 3e5 dyn/cm^2 with +-10 % variation (closed valve).  tau_M is
+    ~6e-7 here and the metric G ~ 4e6, far from the unit scales of the other
+    cases; double-float must still agree with the oracle to 1e-12."""
+    N, h = (20, 14, 23), (1e-3, 1e-3, 1e-3)
+    mesh, grid, p = make(fsi, oracle, N, h=h, x0=(0.51, -0.013, 0.2), rho=1.06, mu=0.035,
+                         dt=1e-5, has_s=True)
+    n = mesh.n_nodes
+    rng = np.random.default_rng(77)
+    U = np.empty((n, 4))
+    U[:, :3] = rng.uniform(-100.0, 100.0, (n, 3))
+    U[:, 3] = 3e5 * (1.0 + rng.uniform(-0.1, 0.1, n))
+    A = np.empty((n, 4))
+    A[:, :3] = rng.uniform(-1e6, 1e6, (n, 3))
+    A[:, 3] = rng.uniform(1.0, 100.0, n)
+    f = np.zeros((n, 4))
+    f[:, 2] = -981.0
+    x = np.empty((n, 4))
+    x[:, :3] = rng.uniform(-1e6, 1e6, (n, 3))
+    x[:, 3] = rng.uniform(-3e4, 3e4, n)
+    eR, eJ, _ = vms_case(fsi, oracle, mesh, grid, p, U, A, f, x, prec)
+    print(f"\npaper scales {prec}: residual {eR:.2e}, Jacobian {eJ:.2e}")
+    assert eR < TOL[prec], eR
+    assert eJ < TOL[prec], eJ
+
+
+def test_dlm_paper_scales(fsi, oracle):
+    """Location, interpolation and spreading on a 1e-3 cm grid away from the
+    origin (x0 ~ 0.5 cm: t = (X - x0)/h loses ~10 bits to the offset),
+    velocities ~100 cm/s and multipliers ~1e5: FP64 and double-float against
+    the oracle."""
+    N, h, x0 = (30, 24, 28), (1e-3,) * 3, (0.5, 0.25, -0.75)
+    rng = np.random.default_rng(5)
+    X = np.array(x0) + rng.uniform(-0.001, 1.001, (20_000, 3)) * np.array(N) * 1e-3
+    for prec in ("f64", "df64"):
+        mesh, grid, _ = make(fsi, oracle, N, h=h, x0=x0)
+        m = X.shape[0]
+        lam = 1e5 * rng.normal(size=(m, 3))
+        U = 100.0 * rng.normal(size=(mesh.n_nodes, 4))
+        g = dlm_run(fsi, mesh, X, prec, lam, None, U, np.zeros((mesh.n_nodes, 4)), False)
+        eo, xio, nouto = oracle.core.locate(grid, X)
+        assert g["nout"] == nouto and np.array_equal(g["elem"], eo)
+        assert np.array_equal(g["xi"], xio)
+        assert rel(g["u"], oracle.core.interp(grid, eo, xio, U)) < 1e-12
+        Fo = oracle.core.spread(grid, eo, xio, lam)
+        assert rel(g["F"][:, :3], Fo[:, :3], grid.N) < 1e-12

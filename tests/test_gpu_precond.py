@@ -5,6 +5,8 @@ Newton step."""
 import numpy as np
 import pytest
 
+import parity
+
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32": 1e-5}
@@ -28,8 +30,17 @@ def H(t):
     return t.detach().cpu().numpy().astype(np.float64)
 
 
-def rel(a, b):
-    return np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300)
+def rel(a, b, grid=None):
+    """Worst local relative error of a against b: momentum and continuity
+    rows, boundary and interior nodes (when grid is given) apart, norm-wise
+    and largest entry (tests/parity.py)."""
+    return parity.rel_local(np.asarray(a), b, grid)
+
+
+def rel_norm(a, b):
+    """Norm-wise distance of a whole solution vector from a reference one."""
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a) - b) / (nb if nb > 0 else 1.0)
 
 
 def dtype_of(prec):

@@ -5,6 +5,8 @@ against the tetrahedral oracle on the same seeded, shuffled meshes."""
 import numpy as np
 import pytest
 
+import parity
+
 from paper_2601_08266_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -37,7 +39,15 @@ def H(t):
     return t.detach().cpu().numpy().astype(np.float64)
 
 
-def rel(a, b):
+def rel(a, b, grid=None):
+    """Worst local relative error of a against b: momentum and continuity
+    rows, boundary and interior nodes (when grid is given) apart, norm-wise
+    and largest entry (tests/parity.py)."""
+    return parity.rel_local(np.asarray(a), b, grid)
+
+
+def rel_norm(a, b):
+    """Norm-wise distance of a whole solution vector from a reference one."""
     nb = np.linalg.norm(b)
     return np.linalg.norm(np.asarray(a) - b) / (nb if nb > 0 else 1.0)
 
