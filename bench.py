@@ -944,7 +944,9 @@ def newton_section(args, dev, stream):
 def batch_section(args, dev, stream):
     """64 independent instances (N ~ U{16..48}, mu ~ logU[1e-3, 1e-1], 10k-150k
     leaflet points each): per-instance launches vs persistent grids vs the CUDA
-    graph of the persistent step, FP32 and FP64."""
+    graph of the persistent step, FP32 and FP64.  One step = location and cell
+    table of the raw points, residual, Jacobian apply, interpolation and
+    spreading of every instance."""
     import torch
     import paper_2601_08266_gb300 as fsi
     from paper_2601_08266_gb300 import inputs
@@ -954,7 +956,8 @@ def batch_section(args, dev, stream):
     mus = np.exp(rng.uniform(np.log(1e-3), np.log(1e-1), size=count))
     ms = rng.integers(10_000, 150_001, size=count)
     out = {"instances": count, "dofs_total": int(sum(4 * (N + 1) ** 3 for N in Ns)),
-           "points_total": int(ms.sum())}
+           "points_total": int(ms.sum()),
+           "step": "locate + cell table, residual, Jacobian apply, interp, spread"}
     for prec_name, dt_t, P in (("f32", torch.float32, fsi.FSI_F32), ("f64", torch.float64, fsi.FSI_F64)):
         meshes, items = [], []
         for i in range(count):
@@ -974,12 +977,12 @@ def batch_section(args, dev, stream):
                           perm=torch.empty(m, dtype=torch.int32, device=dev),
                           lam=torch.randn((m, 3), device=dev, generator=g).to(dt_t),
                           u=torch.empty((m, 3), dtype=dt_t, device=dev))
-                xi64 = torch.empty((m, 3), dtype=torch.float64, device=dev)
-                Xp = torch.as_tensor(inputs.leaflet_points(m, seed=SEED + 100 + i), device=dev)
-            fsi.fsi_locate(mesh, Xp, it["elem"], xi64, it["cell_start"], it["perm"],
-                           want_outside=False)
-            with torch.cuda.stream(stream):
-                it["xi"] = xi64.to(dt_t).contiguous()
+                # raw points: every batched step locates them and builds the
+                # instance's cell table itself (elem, xi, cell_start, perm are
+                # outputs of the step)
+                it["X"] = torch.as_tensor(inputs.leaflet_points(m, seed=SEED + 100 + i),
+                                          device=dev)
+                it["xi"] = torch.empty((m, 3), dtype=dt_t, device=dev)
             meshes.append(mesh)
             items.append(it)
         stream.synchronize()

@@ -692,9 +692,16 @@ fsi_status fsi_mlp_guess(fsi_mlp *mlp, fsi_mesh *mesh, const float *params, cons
  * size.  One item per instance: device arrays in the batch's precision,
  * contiguous, owned by the caller and kept valid (same pointers) for the
  * batch's lifetime: U, A, f (or NULL), x, R, Jx [n_i][4]; points (m may be
- * 0): elem, cell_start, perm from fsi_locate, xi [m][3], lam [m][3], w [m]
- * (or NULL), u [m][3]; spreading writes F [n_i][4] (slots 0..2, overwrite).
- * One batched step = for every instance R = residual(U, A, f),
+ * 0, m < 2^31): elem [m], cell_start [E_i+1], perm [m], xi [m][3],
+ * lam [m][3], w [m] (or NULL), u [m][3]; spreading writes F [n_i][4]
+ * (slots 0..2, overwrite).
+ * X [m][3] (FP64) are the instance's raw solid points, or NULL.  With X the
+ * step locates them itself (Sec. 3, Algorithm 1's point search; the rule of
+ * fsi_locate): elem, xi, cell_start and perm are OUTPUTS of every step,
+ * written bit for bit as fsi_locate writes them (xi rounded to FP32 in an
+ * FP32 batch), so they must point to writable memory.  Without X they are
+ * inputs from an earlier fsi_locate.
+ * One batched step = for every instance (locate X), R = residual(U, A, f),
  * Jx = J(U, A, f) x, u = C^T U, F = C lambda.                              */
 typedef struct {
     const void *U, *A, *f, *x;
@@ -703,6 +710,7 @@ typedef struct {
     const int32_t *elem, *cell_start, *perm;
     const void *xi, *lam, *w;
     void *u, *F;
+    const double *X;
 } fsi_batch_item;
 
 typedef struct fsi_batch fsi_batch;

@@ -82,7 +82,7 @@ class fsi_batch_item(ctypes.Structure):
                 ("m", ctypes.c_int64), ("elem", ctypes.c_void_p),
                 ("cell_start", ctypes.c_void_p), ("perm", ctypes.c_void_p),
                 ("xi", ctypes.c_void_p), ("lam", ctypes.c_void_p), ("w", ctypes.c_void_p),
-                ("u", ctypes.c_void_p), ("F", ctypes.c_void_p)]
+                ("u", ctypes.c_void_p), ("F", ctypes.c_void_p), ("X", ctypes.c_void_p)]
 
 
 _NT = 64
@@ -789,7 +789,7 @@ class Batch:
                 _ptr(it["R"], dt), _ptr(it["Jx"], dt), m, _ptr(it.get("elem"), torch.int32),
                 _ptr(it["cell_start"], torch.int32), _ptr(it.get("perm"), torch.int32),
                 _ptr(it.get("xi"), dt), _ptr(it.get("lam"), dt), _ptr(it.get("w"), dt),
-                _ptr(it.get("u"), dt), _ptr(it["F"], dt))
+                _ptr(it.get("u"), dt), _ptr(it["F"], dt), _ptr(it.get("X"), torch.float64))
         handles = (ctypes.c_void_p * len(meshes))(*[mm.handle.value for mm in meshes])
         out = ctypes.c_void_p()
         _check(lib().fsi_batch_create(handles, arr, len(items), prec, ctypes.c_void_p(stream),

@@ -1,10 +1,11 @@
 // batch.cu -- many independent instances of uneven size in one pass (an
-// extension; the paper has no counterpart): the residual, the Jacobian apply,
-// interpolation and spreading of every instance run as persistent grids that
-// walk a prefix sum of (instance, work item) pairs, so small grids no longer
-// leave SMs idle and the whole step is a handful of launches, which one CUDA
-// graph replays.  A native autotuner picks the brick shape and the persistent
-// grid size by timing candidates on the actual batch.
+// extension; the paper has no counterpart): the point location and cell
+// table, the residual, the Jacobian apply, interpolation and spreading of
+// every instance run as persistent grids that walk a prefix sum of
+// (instance, work item) pairs, so small grids no longer leave SMs idle and the
+// whole step is a handful of launches, which one CUDA graph replays.  A
+// native autotuner picks the brick shape and the persistent grid size by
+// timing candidates on the actual batch.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -25,6 +26,12 @@ template <typename T> struct DlmDesc {
     const T *xi, *lam, *w;
     const vec4<T> *U;
     T *u, *F, *S;
+    // batched location: raw points (null when the item brings its own
+    // table), per-cell counters [E+1] and scan tile sums [ntiles]; the step
+    // then writes elem, xi, start and perm
+    const double *X;
+    int32_t *fill, *tiles;
+    int64_t ntiles;
 };
 
 constexpr int kChunk = 256;  // nodes / points per work item; 8 cell segments per item
@@ -65,6 +72,114 @@ __global__ void batch_gather_kernel(const vmsd::VmsArgs<T> *desc, const int64_t 
         const int64_t node = (item - prefix[inst]) * kChunk + threadIdx.x;
         if (node < n) vmsd::gather_node(P, (int)node);
     }
+}
+
+// ---- batched location and cell table (the bodies of dlm_device.cuh over
+// the instances' prefix sums; instances without raw points are skipped)
+template <typename T>
+__global__ void batch_clear_kernel(const DlmDesc<T> *desc, const int64_t *prefix, int count)
+{
+    const int64_t total = prefix[count];
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const int inst = find_instance(prefix, count, item);
+        const DlmDesc<T> &D = desc[inst];
+        const int64_t c = (item - prefix[inst]) * kChunk + threadIdx.x;
+        if (D.X && c <= D.E) D.fill[c] = 0;
+    }
+}
+
+template <typename T>
+__global__ void batch_locate_kernel(const DlmDesc<T> *desc, const int64_t *prefix, int count)
+{
+    const int64_t total = prefix[count];
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const int inst = find_instance(prefix, count, item);
+        const DlmDesc<T> &D = desc[inst];
+        const int64_t b = (item - prefix[inst]) * kChunk + threadIdx.x;
+        if (D.X && b < D.m) {
+            const int e = dlmd::locate_point<T>(D.g, b, D.X, const_cast<int32_t *>(D.elem),
+                                                const_cast<T *>(D.xi));
+            if (e >= 0) atomicAdd(D.fill + e, 1);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) batch_scan_tiles_kernel(const DlmDesc<T> *desc,
+                                                                const int64_t *prefix, int count)
+{
+    __shared__ int warp_sums[32];
+    const int64_t total = prefix[count];
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const int inst = find_instance(prefix, count, item);
+        const DlmDesc<T> &D = desc[inst];
+        if (D.X)  // uniform over the block
+            dlmd::scan_tile(D.E, D.fill, const_cast<int32_t *>(D.start), D.tiles,
+                            item - prefix[inst], warp_sums);
+        __syncthreads();  // warp_sums is reused by the next tile
+    }
+}
+
+// one CTA per instance scans that instance's tile sums
+template <typename T>
+__global__ void __launch_bounds__(1024) batch_scan_totals_kernel(const DlmDesc<T> *desc, int count)
+{
+    __shared__ int warp_sums[32];
+    __shared__ int carry;
+    for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
+        const DlmDesc<T> &D = desc[inst];
+        if (D.X) dlmd::scan_totals_block(D.ntiles, D.tiles, warp_sums, &carry);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void batch_scan_add_kernel(const DlmDesc<T> *desc, const int64_t *prefix, int count)
+{
+    const int64_t total = prefix[count];
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const int inst = find_instance(prefix, count, item);
+        const DlmDesc<T> &D = desc[inst];
+        if (D.X)
+            dlmd::scan_add_tile(D.E, const_cast<int32_t *>(D.start), D.tiles, item - prefix[inst]);
+    }
+}
+
+template <typename T>
+__global__ void batch_scatter_kernel(const DlmDesc<T> *desc, const int64_t *prefix, int count)
+{
+    const int64_t total = prefix[count];
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const int inst = find_instance(prefix, count, item);
+        const DlmDesc<T> &D = desc[inst];
+        const int64_t b = (item - prefix[inst]) * kChunk + threadIdx.x;
+        if (D.X && b < D.m)
+            dlmd::scatter_point(b, D.E, D.elem, D.start, D.fill, const_cast<int32_t *>(D.perm));
+    }
+}
+
+// kChunk cells per item: one warp per 32 consecutive cells (cell E = the tail
+// of outside points)
+template <typename T>
+__global__ void batch_cell_sort_kernel(const DlmDesc<T> *desc, const int64_t *prefix, int count)
+{
+    const int64_t total = prefix[count];
+    const int warp = threadIdx.x >> 5;
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const int inst = find_instance(prefix, count, item);
+        const DlmDesc<T> &D = desc[inst];
+        const int64_t c0 = (item - prefix[inst]) * kChunk + 32 * warp;
+        if (D.X && c0 <= D.E)
+            dlmd::cell_sort_segment(D.E, D.m, D.start, const_cast<int32_t *>(D.perm), c0);
+    }
+}
+
+template <typename T>
+__global__ void cast_xi_kernel(int64_t n, const double *src, T *dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (T)src[i];
 }
 
 template <typename T>
@@ -122,12 +237,22 @@ struct fsi_batch {
     int sms;
     // device data
     void *desc_res, *desc_jac, *desc_dlm;                      // descriptors
-    int64_t *prefix;  // [5][count+1]: bricks, node chunks, point chunks, cell items, (spare)
+    // [kRows][count+1]: bricks, node chunks, point chunks, spreading cell items,
+    // counter chunks (E+1 cells), scan tiles, cell-sort items (E+1 cells)
+    int64_t *prefix;
     void *blocks;
     size_t blocks_bytes;
     void *spread;
     size_t spread_bytes;
-    int64_t totals[4];
+    // batched location: per-cell counters and scan tile sums of every
+    // instance that brings raw points; FP64 xi of one instance for the
+    // per-instance path of an FP32 batch
+    void *loc;
+    size_t loc_bytes;
+    double *xi64;
+    size_t xi64_bytes;
+    bool locate;
+    int64_t totals[7];
     // CUDA graph of one batched step
     cudaGraph_t graph;
     cudaGraphExec_t graph_exec;
@@ -136,15 +261,17 @@ struct fsi_batch {
 namespace fsi {
 namespace {
 
+constexpr int kRows = 7;
+
 // (Re)build descriptors and scratch for the batch's current brick shape.
 template <typename T> fsi_status build_batch(fsi_batch *b)
 {
     const int C = b->count;
     std::vector<vmsd::VmsArgs<T>> res(C), jac(C);
     std::vector<DlmDesc<T>> dlm(C);
-    std::vector<int64_t> pre(5 * (C + 1), 0);
-    size_t blocks_need = 0, spread_need = 0;
-    std::vector<size_t> boff(C), soff(C);
+    std::vector<int64_t> pre(kRows * (C + 1), 0);
+    size_t blocks_need = 0, spread_need = 0, loc_need = 0, xi64_need = 0;
+    std::vector<size_t> boff(C), soff(C), loff(C);
     for (int i = 0; i < C; ++i) {
         fsi_mesh *m = b->meshes[i];
         boff[i] = blocks_need;
@@ -153,6 +280,26 @@ template <typename T> fsi_status build_batch(fsi_batch *b)
         soff[i] = spread_need;
         spread_need += (size_t)m->n_elems * 24 * sizeof(T);
         spread_need = (spread_need + 255) / 256 * 256;
+        loff[i] = loc_need;
+        if (b->items[i].X) {
+            loc_need += (size_t)(m->n_elems + 1 + dlmd::cell_tiles(m->n_elems)) * sizeof(int32_t);
+            loc_need = (loc_need + 255) / 256 * 256;
+            xi64_need = std::max(xi64_need, (size_t)b->items[i].m * 3 * sizeof(double));
+        }
+    }
+    if (loc_need > b->loc_bytes) {
+        cudaFree(b->loc);
+        b->loc = nullptr;
+        b->loc_bytes = 0;
+        FSI_CUDA(cudaMalloc(&b->loc, loc_need), "batch location scratch");
+        b->loc_bytes = loc_need;
+    }
+    if (sizeof(T) != sizeof(double) && xi64_need > b->xi64_bytes) {
+        cudaFree(b->xi64);
+        b->xi64 = nullptr;
+        b->xi64_bytes = 0;
+        FSI_CUDA(cudaMalloc(&b->xi64, xi64_need), "batch xi scratch");
+        b->xi64_bytes = xi64_need;
     }
     if (blocks_need > b->blocks_bytes) {
         cudaFree(b->blocks);
@@ -196,6 +343,10 @@ template <typename T> fsi_status build_batch(fsi_batch *b)
         D.u = (T *)it.u;
         D.F = (T *)it.F;
         D.S = (T *)((char *)b->spread + soff[i]);
+        D.X = it.X;
+        D.ntiles = dlmd::cell_tiles(m->n_elems);
+        D.fill = it.X ? (int32_t *)((char *)b->loc + loff[i]) : nullptr;
+        D.tiles = it.X ? D.fill + m->n_elems + 1 : nullptr;
         const int64_t nb = (int64_t)res[i].nbx * res[i].nby * res[i].nbz;
         pre[0 * (C + 1) + i + 1] = pre[0 * (C + 1) + i] + nb;
         pre[1 * (C + 1) + i + 1] = pre[1 * (C + 1) + i] + (m->n_nodes + kChunk - 1) / kChunk;
@@ -203,8 +354,12 @@ template <typename T> fsi_status build_batch(fsi_batch *b)
         pre[3 * (C + 1) + i + 1] =
             pre[3 * (C + 1) + i] +
             ((m->n_elems + dlmd::kSpreadSeg - 1) / dlmd::kSpreadSeg + 7) / 8;  // 8 segments per item
+        const int64_t cells = it.X ? (m->n_elems + 1 + kChunk - 1) / kChunk : 0;
+        pre[4 * (C + 1) + i + 1] = pre[4 * (C + 1) + i] + cells;
+        pre[5 * (C + 1) + i + 1] = pre[5 * (C + 1) + i] + (it.X ? D.ntiles : 0);
+        pre[6 * (C + 1) + i + 1] = pre[6 * (C + 1) + i] + cells;
     }
-    for (int k = 0; k < 4; ++k) b->totals[k] = pre[k * (C + 1) + C];
+    for (int k = 0; k < kRows; ++k) b->totals[k] = pre[k * (C + 1) + C];
     cudaStream_t s = b->stream;
     FSI_CUDA(cudaMemcpyAsync(b->desc_res, res.data(), C * sizeof(res[0]), cudaMemcpyHostToDevice, s),
              "descriptor upload");
@@ -227,6 +382,10 @@ template <typename T> fsi_status build_batch(fsi_batch *b)
     return FSI_OK;
 }
 
+// phases of a batched step: 1 residual, 2 Jacobian apply, 4 interpolation and
+// spreading, 8 location and cell table (instances with raw points)
+constexpr int kAllPhases = 15;
+
 int persistent_grid(const fsi_batch *b, int64_t items)
 {
     int64_t g = (int64_t)b->sms * b->ctas_per_sm;
@@ -241,6 +400,28 @@ template <typename T> fsi_status run_batched(fsi_batch *b, int phases)
     const int C = b->count;
     const int64_t *pre = b->prefix;
     const size_t smem = (size_t)b->brick.bx * b->brick.by * b->brick.bz * 8 * sizeof(vec4<T>);
+    if ((phases & 8) && b->locate) {
+        const DlmDesc<T> *dd = (const DlmDesc<T> *)b->desc_dlm;
+        batch_clear_kernel<T><<<persistent_grid(b, b->totals[4]), kChunk, 0, s>>>(
+            dd, pre + 4 * (C + 1), C);
+        if (b->totals[2] > 0)
+            batch_locate_kernel<T><<<persistent_grid(b, b->totals[2]), kChunk, 0, s>>>(
+                dd, pre + 2 * (C + 1), C);
+        batch_scan_tiles_kernel<T><<<persistent_grid(b, b->totals[5]), 1024, 0, s>>>(
+            dd, pre + 5 * (C + 1), C);
+        batch_scan_totals_kernel<T><<<std::min(C, b->sms * 2), 1024, 0, s>>>(dd, C);
+        batch_scan_add_kernel<T><<<persistent_grid(b, b->totals[5]), 256, 0, s>>>(
+            dd, pre + 5 * (C + 1), C);
+        if (b->totals[2] > 0) {
+            batch_clear_kernel<T><<<persistent_grid(b, b->totals[4]), kChunk, 0, s>>>(
+                dd, pre + 4 * (C + 1), C);
+            batch_scatter_kernel<T><<<persistent_grid(b, b->totals[2]), kChunk, 0, s>>>(
+                dd, pre + 2 * (C + 1), C);
+            batch_cell_sort_kernel<T><<<persistent_grid(b, b->totals[6]), kChunk, 0, s>>>(
+                dd, pre + 6 * (C + 1), C);
+        }
+        FSI_TRY(check_launch("batched location kernels"));
+    }
     if (phases & 1) {
         batch_brick_kernel<T, false><<<persistent_grid(b, b->totals[0]), b->brick.threads, smem, s>>>(
             (const vmsd::VmsArgs<T> *)b->desc_res, pre, C);
@@ -275,7 +456,20 @@ fsi_status run_per_instance(fsi_batch *b, int phases)
         fsi::Brick bsaved[2] = {m->brick[0][b->prec], m->brick[1][b->prec]};
         m->brick[0][b->prec] = m->brick[1][b->prec] = b->brick;
         fsi_status st = FSI_OK;
-        if (phases & 1) st = fsi_residual(m, b->prec, it.U, it.A, it.f, it.R);
+        if ((phases & 8) && it.X) {
+            // FP64 xi straight into the item, or through the batch's FP64
+            // scratch and a rounding copy for an FP32 batch
+            double *xi = b->prec == FSI_F64 ? (double *)it.xi : b->xi64;
+            st = fsi_locate(m, it.m, it.X, const_cast<int32_t *>(it.elem), xi,
+                            const_cast<int32_t *>(it.cell_start), const_cast<int32_t *>(it.perm),
+                            nullptr, 0);
+            if (st == FSI_OK && b->prec != FSI_F64 && it.m > 0) {
+                cast_xi_kernel<float><<<sm_count() * 4, 256, 0, m->stream>>>(
+                    3 * it.m, b->xi64, (float *)const_cast<void *>(it.xi));
+                st = check_launch("xi rounding kernel");
+            }
+        }
+        if (st == FSI_OK && (phases & 1)) st = fsi_residual(m, b->prec, it.U, it.A, it.f, it.R);
         if (st == FSI_OK && (phases & 2))
             st = fsi_jacobian_apply(m, b->prec, it.U, it.A, it.f, it.x, it.Jx);
         if (st == FSI_OK && (phases & 4)) {
@@ -327,7 +521,8 @@ fsi_status run_mode(fsi_batch *b, int mode, int phases)
             return set_error(FSI_ERR_ARG, "graph mode needs a non-default stream");
         FSI_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
                  "begin capture");
-        fsi_status st = b->prec == FSI_F64 ? run_batched<double>(b, 7) : run_batched<float>(b, 7);
+        fsi_status st = b->prec == FSI_F64 ? run_batched<double>(b, kAllPhases)
+                                           : run_batched<float>(b, kAllPhases);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(b->stream, &g);
         FSI_TRY(st);
@@ -390,7 +585,8 @@ fsi_status fsi_batch_create(fsi_mesh *const *meshes, const fsi_batch_item *items
         const fsi_batch_item &it = items[i];
         if (!it.U || !it.A || !it.x || !it.R || !it.Jx || !it.F || !it.cell_start)
             return set_error(FSI_ERR_ARG, "batch item %d: NULL array", i);
-        if (it.m < 0 || (it.m > 0 && (!it.elem || !it.xi || !it.perm || !it.lam || !it.u)))
+        if (it.m < 0 || it.m >= INT32_MAX ||
+            (it.m > 0 && (!it.elem || !it.xi || !it.perm || !it.lam || !it.u)))
             return set_error(FSI_ERR_ARG, "batch item %d: bad point arrays", i);
     }
     FSI_DEVICE(device);
@@ -402,6 +598,7 @@ fsi_status fsi_batch_create(fsi_mesh *const *meshes, const fsi_batch_item *items
     b->count = count;
     b->meshes.assign(meshes, meshes + count);
     b->items.assign(items, items + count);
+    for (int i = 0; i < count; ++i) b->locate = b->locate || items[i].X != nullptr;
     b->brick = Brick{8, 8, 4, 256};
     b->ctas_per_sm = 2;
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, device);
@@ -411,7 +608,7 @@ fsi_status fsi_batch_create(fsi_mesh *const *meshes, const fsi_batch_item *items
     if (st == FSI_OK) st = check_cuda(cudaMalloc(&b->desc_jac, count * vsz), "descriptors");
     if (st == FSI_OK) st = check_cuda(cudaMalloc(&b->desc_dlm, count * dsz), "descriptors");
     if (st == FSI_OK)
-        st = check_cuda(cudaMalloc(&b->prefix, 5 * (count + 1) * sizeof(int64_t)), "prefix");
+        st = check_cuda(cudaMalloc(&b->prefix, kRows * (count + 1) * sizeof(int64_t)), "prefix");
     if (st == FSI_OK) st = prec == FSI_F64 ? build_batch<double>(b) : build_batch<float>(b);
     if (st != FSI_OK) {
         fsi_batch_destroy(b);
@@ -434,6 +631,8 @@ void fsi_batch_destroy(fsi_batch *b)
     cudaFree(b->prefix);
     cudaFree(b->blocks);
     cudaFree(b->spread);
+    cudaFree(b->loc);
+    cudaFree(b->xi64);
     delete b;
 }
 
@@ -443,7 +642,7 @@ fsi_status fsi_batch_run(fsi_batch *b, int mode)
     if (mode < FSI_BATCH_PER_INSTANCE || mode > FSI_BATCH_GRAPH)
         return set_error(FSI_ERR_ARG, "bad batch mode %d", mode);
     FSI_DEVICE(b->device);
-    return run_mode(b, mode, 7);
+    return run_mode(b, mode, kAllPhases);
 }
 
 fsi_status fsi_batch_autotune(fsi_batch *b, int reps, fsi_tune_report *rep)
@@ -512,7 +711,7 @@ fsi_status fsi_batch_time(fsi_batch *b, int mode, int reps, double *seconds)
     if (mode < FSI_BATCH_PER_INSTANCE || mode > FSI_BATCH_GRAPH)
         return set_error(FSI_ERR_ARG, "bad batch mode %d", mode);
     FSI_DEVICE(b->device);
-    return time_mode(b, mode, 7, reps, seconds);
+    return time_mode(b, mode, kAllPhases, reps, seconds);
 }
 
 }  // extern "C"

@@ -52,28 +52,11 @@ __global__ void locate_kernel(int64_t m, GridArgs g, const double *__restrict__ 
 {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
          b += (int64_t)gridDim.x * blockDim.x) {
-        const double tx = (X[3 * b + 0] - g.x0) / g.hx;
-        const double ty = (X[3 * b + 1] - g.y0) / g.hy;
-        const double tz = (X[3 * b + 2] - g.z0) / g.hz;
-        const bool in = (tx >= 0.0 && tx <= (double)g.Nx) && (ty >= 0.0 && ty <= (double)g.Ny) &&
-                        (tz >= 0.0 && tz <= (double)g.Nz);
-        if (!in) {
-            elem[b] = -1;
-            xi[3 * b + 0] = 0.0;
-            xi[3 * b + 1] = 0.0;
-            xi[3 * b + 2] = 0.0;
+        const int e = locate_point<double>(g, b, X, elem, xi);
+        if (e < 0)
             atomicAdd(n_out, 1ull);
-            continue;
-        }
-        const int ex = min((int)floor(tx), g.Nx - 1);
-        const int ey = min((int)floor(ty), g.Ny - 1);
-        const int ez = min((int)floor(tz), g.Nz - 1);
-        xi[3 * b + 0] = 2.0 * (tx - (double)ex) - 1.0;
-        xi[3 * b + 1] = 2.0 * (ty - (double)ey) - 1.0;
-        xi[3 * b + 2] = 2.0 * (tz - (double)ez) - 1.0;
-        const int e = ex + g.Nx * (ey + g.Ny * ez);
-        elem[b] = e;
-        if (count) atomicAdd(count + e, 1);
+        else if (count)
+            atomicAdd(count + e, 1);
     }
 }
 
@@ -331,204 +314,42 @@ __global__ void locate_mapped_kernel(int64_t m, GridArgs g, const double4 *__res
     }
 }
 
-// --------------------------------------------------------------- scan
-// Exclusive scan of count[0..E) into start[0..E] (start[E] = total) with
-// 2048-entry tiles: (1) tile-local inclusive scan + tile totals, (2) one CTA
-// scans the tile totals, (3) tiles add their offset.
-constexpr int kScanTile = 2048;
-
-__device__ __forceinline__ int block_inclusive_scan(int v, int *warp_sums)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-    }
-    if (lane == 31) warp_sums[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        int s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += t;
-        }
-        warp_sums[lane] = s;
-    }
-    __syncthreads();
-    if (wid > 0) v += warp_sums[wid - 1];
-    return v;
-}
-
+// --------------------------------------------------------------- cell table
+// (the per-work-item bodies are in dlm_device.cuh, shared with the batch)
 __global__ void __launch_bounds__(1024) scan_tiles_kernel(int64_t E, const int32_t *count,
                                                           int32_t *start, int32_t *tile_sum)
 {
     __shared__ int warp_sums[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + 2 * threadIdx.x;
-    const int a = base < E ? count[base] : 0;
-    const int b = base + 1 < E ? count[base + 1] : 0;
-    const int incl = block_inclusive_scan(a + b, warp_sums);
-    if (base < E) start[base + 1] = incl - b;
-    if (base + 1 < E) start[base + 2] = incl;
-    if (threadIdx.x == blockDim.x - 1) tile_sum[blockIdx.x] = incl;
+    scan_tile(E, count, start, tile_sum, blockIdx.x, warp_sums);
 }
 
 __global__ void __launch_bounds__(1024) scan_totals_kernel(int64_t ntiles, int32_t *tile_sum)
 {
     __shared__ int warp_sums[32];
     __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < ntiles; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        const int v = i < ntiles ? tile_sum[i] : 0;
-        const int incl = block_inclusive_scan(v, warp_sums);
-        const int c = carry;
-        __syncthreads();
-        if (i < ntiles) tile_sum[i] = c + incl - v;  // exclusive
-        if (threadIdx.x == blockDim.x - 1) carry = c + incl;
-        __syncthreads();
-    }
+    scan_totals_block(ntiles, tile_sum, warp_sums, &carry);
 }
 
 __global__ void scan_add_kernel(int64_t E, int32_t *start, const int32_t *tile_sum)
 {
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    const int off = tile_sum[blockIdx.x];
-    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
-        const int64_t k = base + i;
-        if (k < E) start[k + 1] += off;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) start[0] = 0;
+    scan_add_tile(E, start, tile_sum, blockIdx.x);
 }
 
-// --------------------------------------------------------------- scatter + sort
 __global__ void scatter_kernel(int64_t m, int64_t E, const int32_t *__restrict__ elem,
                                const int32_t *__restrict__ start, int32_t *fill,
                                int32_t *__restrict__ perm)
 {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
-         b += (int64_t)gridDim.x * blockDim.x) {
-        const int e = elem[b];
-        const int64_t cell = e >= 0 ? e : E;  // outside points form the tail "cell" E
-        const int pos = start[cell] + atomicAdd(fill + cell, 1);
-        perm[pos] = (int32_t)b;
-    }
-}
-
-// Sort every cell's slice of perm ascending (restores the stable order).
-// Cell E is the tail of outside points [start[E], m).  One warp per segment of
-// 32 consecutive cells; each slice is sorted by ranks (values are distinct
-// point indices, so rank_i = #{j : v_j < v_i} is a permutation) held in
-// registers for slices of up to 128 points, and a single-lane shell sort
-// beyond (rare: very dense cells).
-__device__ void shell_sort(int32_t *s, int len)
-{
-    int gap = 1;
-    while (gap * 9 / 4 + 1 < len) gap = gap * 9 / 4 + 1;
-    for (;;) {
-        for (int i = gap; i < len; ++i) {
-            const int v = s[i];
-            int j = i;
-            while (j >= gap && s[j - gap] > v) {
-                s[j] = s[j - gap];
-                j -= gap;
-            }
-            s[j] = v;
-        }
-        if (gap == 1) break;
-        gap = gap * 4 / 9;
-        if (gap < 1) gap = 1;
-    }
-}
-
-// Ascending bitonic sorting network over N values in registers (all indices
-// compile-time constants, so nothing goes to local memory).
-template <int N> __device__ __forceinline__ void bitonic(int (&v)[N])
-{
-#pragma unroll
-    for (int k = 2; k <= N; k <<= 1)
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1)
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const int a = v[i], b = v[l];
-                    const bool up = (i & k) == 0;
-                    v[i] = up ? min(a, b) : max(a, b);
-                    v[l] = up ? max(a, b) : min(a, b);
-                }
-            }
-}
-
-// one lane sorts a slice of len <= N values in place
-template <int N> __device__ __forceinline__ void sort_slice(int32_t *sl, int len)
-{
-    int v[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) v[i] = i < len ? sl[i] : INT32_MAX;
-    bitonic<N>(v);
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-        if (i < len) sl[i] = v[i];
+         b += (int64_t)gridDim.x * blockDim.x)
+        scatter_point(b, E, elem, start, fill, perm);
 }
 
 __global__ void cell_sort_kernel(int64_t E, int64_t m, const int32_t *__restrict__ start,
                                  int32_t *__restrict__ perm)
 {
-    const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c0 = warp * 32; c0 <= E; c0 += nwarps * 32) {
-        const int64_t c = c0 + lane;
-        int lo = 0, len = 0;
-        if (c <= E) {
-            lo = start[c];
-            len = (c < E ? start[c + 1] : (int)m) - lo;
-        }
-        // up to 64 points: each lane sorts its own cell's slice in registers
-        if (len >= 2 && len <= 32)
-            sort_slice<32>(perm + lo, len);
-        else if (len > 32 && len <= 64)
-            sort_slice<64>(perm + lo, len);
-        // fuller cells: the warp together
-        unsigned todo = __ballot_sync(0xffffffffu, len > 64);
-        while (todo) {
-            const int l = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int base = __shfl_sync(0xffffffffu, lo, l);
-            const int n = __shfl_sync(0xffffffffu, len, l);
-            int32_t *sl = perm + base;
-            __syncwarp();
-            if (n <= 128) {
-                // four values per lane, all in registers
-                int own[4], rk[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    own[k] = (lane + 32 * k < n) ? sl[lane + 32 * k] : INT32_MAX;
-                    rk[k] = 0;
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-#pragma unroll 8
-                    for (int j = 0; j < 32; ++j) {
-                        const int wj = __shfl_sync(0xffffffffu, own[c], j);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) rk[k] += wj < own[k];
-                    }
-                __syncwarp();
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (lane + 32 * k < n) sl[rk[k]] = own[k];
-                __syncwarp();
-            } else {
-                if (lane == 0) shell_sort(sl, n);
-                __syncwarp();
-            }
-        }
-    }
+    for (int64_t c0 = warp * 32; c0 <= E; c0 += nwarps * 32) cell_sort_segment(E, m, start, perm, c0);
 }
 
 // --------------------------------------------------------------- interp / spread
@@ -656,7 +477,7 @@ GridArgs grid_args_of(const fsi_grid &gr)
 
 }  // namespace
 
-int64_t cell_table_scan_ints(int64_t E) { return (E + kScanTile - 1) / kScanTile; }
+int64_t cell_table_scan_ints(int64_t E) { return cell_tiles(E); }
 
 fsi_status build_cell_table(cudaStream_t s, int64_t E, int64_t m, const int32_t *elem,
                             int32_t *fill, int32_t *scan_tmp, int32_t *cell_start, int32_t *perm)

@@ -220,3 +220,80 @@ def test_mesh_autotune_keeps_parity(fsi, oracle, prec):
     assert rel(H(J), oracle.core.jacobian_apply(g, phys, U, A, x, c_a, c_v)) < tol, picks
     with pytest.raises(fsi.FsiError):
         fsi.fsi_mesh_autotune(mesh, 3, P)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batch_locates_its_points(fsi, oracle, prec):
+    """Items that bring raw points: the batched step (per instance, persistent
+    grids and the CUDA graph) locates them and builds every instance's cell
+    table itself.  elem, cell_start and perm equal fsi_locate's bit for bit,
+    xi equals fsi_locate's (rounded to FP32 in an FP32 batch), and R, Jx, u, F
+    equal those of the same batch fed fsi_locate's tables.  The points include
+    outside points, points on the far faces and an instance without points."""
+    import torch
+    s = torch.cuda.Stream()
+    _streams[s.cuda_stream] = s
+    meshes, items, host, P = build(fsi, prec, s.cuda_stream)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    ref_tables = []
+    loc_items = []
+    for i, (mesh, it, hst) in enumerate(zip(meshes, items, host)):
+        X = hst["X"]
+        if len(X):
+            ext = np.asarray(mesh.h) * np.asarray(hst["N"])
+            X = np.concatenate([X, inputs.edge_points(hst["N"], seed=len(X), m_random=20)
+                                * ext[None, :]])
+            X[::7] *= 1.05           # some outside the box
+        m = X.shape[0]
+        Xd = T(X, torch.float64)
+        e = torch.empty(m, dtype=torch.int32, device="cuda")
+        xi = torch.empty((m, 3), dtype=torch.float64, device="cuda")
+        cs = torch.empty(mesh.n_elems + 1, dtype=torch.int32, device="cuda")
+        pm = torch.empty(m, dtype=torch.int32, device="cuda")
+        with torch.cuda.stream(s):
+            fsi.fsi_locate(mesh, Xd, e, xi, cs, pm)
+        s.synchronize()
+        ref_tables.append((e.cpu().numpy(), xi.to(dt).cpu().numpy(), cs.cpu().numpy(),
+                           pm.cpu().numpy()))
+        lam = T(np.random.default_rng(m).normal(size=(m, 3)), dt)
+        base = {k: it[k] for k in ("U", "A", "x")}
+        fed = dict(base, R=torch.zeros_like(it["R"]), Jx=torch.zeros_like(it["R"]),
+                   F=torch.zeros_like(it["F"]), cell_start=cs, elem=e, xi=xi.to(dt).contiguous(),
+                   perm=pm, lam=lam, u=torch.zeros((m, 3), dtype=dt, device="cuda"))
+        own = dict(base, R=torch.zeros_like(it["R"]), Jx=torch.zeros_like(it["R"]),
+                   F=torch.zeros_like(it["F"]),
+                   cell_start=torch.full_like(cs, -7) if m else cs.clone(),
+                   elem=torch.full_like(e, 9),
+                   xi=torch.full((m, 3), 5.0, dtype=dt, device="cuda"),
+                   perm=torch.full_like(pm, -3), lam=lam,
+                   u=torch.zeros((m, 3), dtype=dt, device="cuda"), X=Xd)
+        items[i] = fed
+        loc_items.append(own)
+    b_fed = fsi.Batch(meshes, items, P, s.cuda_stream)
+    b_fed.run(fsi.FSI_BATCH_PERSISTENT)
+    s.synchronize()
+    want = outputs(items)
+    b_own = fsi.Batch(meshes, loc_items, P, s.cuda_stream)
+    for mode in (fsi.FSI_BATCH_PER_INSTANCE, fsi.FSI_BATCH_PERSISTENT, fsi.FSI_BATCH_GRAPH):
+        for it in loc_items:
+            if it["elem"].shape[0]:   # an empty X is NULL: that item keeps its table
+                it["cell_start"].fill_(-7)
+            it["elem"].fill_(9)
+            it["perm"].fill_(-3)
+            it["xi"].fill_(5.0)
+            for k in ("R", "Jx", "u", "F"):
+                it[k].fill_(float("nan"))
+        for _ in range(2):           # the second step starts from the first's tables
+            b_own.run(mode)
+        s.synchronize()
+        for it, (e, xi, cs, pm) in zip(loc_items, ref_tables):
+            assert np.array_equal(it["elem"].cpu().numpy(), e), mode
+            assert np.array_equal(it["cell_start"].cpu().numpy(), cs), mode
+            assert np.array_equal(it["perm"].cpu().numpy(), pm), mode
+            assert np.array_equal(it["xi"].cpu().numpy(), xi), mode
+        for a, c in zip(outputs(loc_items), want):
+            for x, y in zip(a, c):
+                assert np.array_equal(x[..., :3] if x.shape[-1] == 4 else x,
+                                      y[..., :3] if y.shape[-1] == 4 else y), mode
+    b_own.close()
+    b_fed.close()
