@@ -809,7 +809,7 @@ def train_network(args, dev, stream, fsi, feats, targs, gen):
         if it in (1, args.mlp_iters):
             stream.synchronize()
             losses.append(float(loss.item()))
-    stream.synchronize()
+    h.check()  # no tensor-core wait ran out
     return h, P, im, isd, om, osd, Xn, losses
 
 

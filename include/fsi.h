@@ -624,8 +624,14 @@ fsi_status fsi_pressure_vcycle(fsi_mesh *mesh, fsi_prec prec, const void *b, voi
  * c = out_mean + out_std * o.
  * Parameters: one FP32 device vector of fsi_mlp_num_params() values laid out
  * W1 [112][256], b1 [256], W2 [256][256], b2 [256], W3 [256][4], b3 [4]
- * (row = input unit).  The GEMMs run on the tensor cores with BF16 operands
- * and FP32 accumulation.  Loss = (1/B) sum_rows 1/2 |o - t|^2.             */
+ * (row = input unit).  The GEMMs run on the 5th-generation tensor cores
+ * (tcgen05, TMEM accumulators) with BF16 operands and FP32 accumulation; the
+ * weight-gradient GEMMs sum split-K partial tiles in a fixed order, so
+ * results are deterministic.  Loss = (1/B) sum_rows 1/2 |o - t|^2.
+ * forward, loss_grad, adam and predict are asynchronous on their streams.
+ * The tensor-core kernels bound every wait; a wait that runs out (which only
+ * a stuck tensor-core pipeline would cause) leaves an error flag on the
+ * handle that fsi_mlp_check and fsi_mlp_guess report as FSI_ERR_TIMEOUT.   */
 typedef struct fsi_mlp fsi_mlp;
 
 /* Handle with activation scratch for batches of up to max_batch rows. */
@@ -652,8 +658,14 @@ fsi_status fsi_mlp_features(fsi_mesh *mesh, const double *Vn, const double *y, c
                             const double *d2, const int32_t *idx, int64_t k,
                             const float *in_mean, const float *in_std, float *X);
 
-/* Newton predictor y0 [n][4] = y + e + c for every node, in chunks of the
- * handle's max_batch, on the mesh's stream.                                */
+/* Reports and clears the handle's tensor-core error flag (see above):
+ * FSI_ERR_TIMEOUT if a wait of an earlier call ran out, else FSI_OK.
+ * Synchronises the device.                                                 */
+fsi_status fsi_mlp_check(fsi_mlp *mlp);
+
+/* Newton predictor y0 [n][4] = y + e + c for every node, on the mesh's
+ * stream, by one fused tensor-core kernel (features, three layers,
+ * predictor).  Asynchronous.                                               */
 fsi_status fsi_mlp_predict(fsi_mlp *mlp, fsi_mesh *mesh, const float *params,
                            const float *in_mean, const float *in_std, const float *out_mean,
                            const float *out_std, const double *Vn, const double *y,

@@ -161,6 +161,7 @@ _SIGS = {
                             ctypes.POINTER(_I64), _INT, _INT, _VP], _INT),
     "fsi_mlp_create": ([_INT, _VP, _I64, ctypes.POINTER(_VP)], _INT),
     "fsi_mlp_destroy": ([_VP], None),
+    "fsi_mlp_check": ([_VP], _INT),
     "fsi_mlp_num_params": ([], _I64),
     "fsi_mlp_forward": ([_VP, _VP, _VP, _I64, _VP], _INT),
     "fsi_mlp_loss_grad": ([_VP, _VP, _VP, _VP, _I64, _VP, _VP], _INT),
@@ -546,6 +547,11 @@ class Mlp:
                                     ctypes.byref(out)))
         self.handle = out
         self.max_batch = int(max_batch)
+
+    def check(self):
+        """Raise FsiError(FSI_ERR_TIMEOUT) if a tensor-core wait of an earlier
+        call ran out (synchronises the device)."""
+        _check(lib().fsi_mlp_check(self.handle))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -85,6 +85,7 @@ __global__ void batch_clear_kernel(const DlmDesc<T> *desc, const int64_t *prefix
         const DlmDesc<T> &D = desc[inst];
         const int64_t c = (item - prefix[inst]) * kChunk + threadIdx.x;
         if (D.X && c <= D.E) D.fill[c] = 0;
+        if (D.X && c == 0) D.tiles[D.ntiles] = 0;  // count of CTA-sorted cells
     }
 }
 
@@ -170,7 +171,24 @@ __global__ void batch_cell_sort_kernel(const DlmDesc<T> *desc, const int64_t *pr
         const DlmDesc<T> &D = desc[inst];
         const int64_t c0 = (item - prefix[inst]) * kChunk + 32 * warp;
         if (D.X && c0 <= D.E)
-            dlmd::cell_sort_segment(D.E, D.m, D.start, const_cast<int32_t *>(D.perm), c0);
+            dlmd::cell_sort_segment(D.E, D.m, D.start, const_cast<int32_t *>(D.perm), c0, D.fill,
+                                    D.tiles + D.ntiles);
+    }
+}
+
+// the cells too full for a warp, listed per instance by the kernel above,
+// one CTA per cell
+template <typename T>
+__global__ void __launch_bounds__(1024) batch_dense_sort_kernel(const DlmDesc<T> *desc, int count)
+{
+    extern __shared__ int32_t sort_sh[];
+    for (int inst = 0; inst < count; ++inst) {
+        const DlmDesc<T> &D = desc[inst];
+        if (!D.X) continue;
+        const int n = D.tiles[D.ntiles];
+        for (int k = blockIdx.x; k < n; k += gridDim.x)
+            dlmd::block_sort_cell(D.E, D.m, D.start, const_cast<int32_t *>(D.perm), D.fill[k],
+                                  sort_sh);
     }
 }
 
@@ -282,7 +300,7 @@ template <typename T> fsi_status build_batch(fsi_batch *b)
         spread_need = (spread_need + 255) / 256 * 256;
         loff[i] = loc_need;
         if (b->items[i].X) {
-            loc_need += (size_t)(m->n_elems + 1 + dlmd::cell_tiles(m->n_elems)) * sizeof(int32_t);
+            loc_need += (size_t)(m->n_elems + 1 + dlmd::cell_tiles(m->n_elems) + 1) * sizeof(int32_t);
             loc_need = (loc_need + 255) / 256 * 256;
             xi64_need = std::max(xi64_need, (size_t)b->items[i].m * 3 * sizeof(double));
         }
@@ -419,6 +437,9 @@ template <typename T> fsi_status run_batched(fsi_batch *b, int phases)
                 dd, pre + 2 * (C + 1), C);
             batch_cell_sort_kernel<T><<<persistent_grid(b, b->totals[6]), kChunk, 0, s>>>(
                 dd, pre + 6 * (C + 1), C);
+            const int smem = dlmd::kBlockSortMax * (int)sizeof(int32_t);
+            FSI_TRY(set_smem_limit((const void *)batch_dense_sort_kernel<T>, smem));
+            batch_dense_sort_kernel<T><<<b->sms, 1024, smem, s>>>(dd, C);
         }
         FSI_TRY(check_launch("batched location kernels"));
     }
@@ -488,24 +509,14 @@ fsi_status run_per_instance(fsi_batch *b, int phases)
 
 fsi_status set_smem_attr(fsi_prec prec)
 {
-    static bool done[2] = {false, false};
-    if (done[prec]) return FSI_OK;
+    const int bytes = 200 * 1024;
     if (prec == FSI_F64) {
-        FSI_CUDA(cudaFuncSetAttribute(batch_brick_kernel<double, false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
-                 "attr");
-        FSI_CUDA(cudaFuncSetAttribute(batch_brick_kernel<double, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
-                 "attr");
+        FSI_TRY(set_smem_limit((const void *)batch_brick_kernel<double, false>, bytes));
+        FSI_TRY(set_smem_limit((const void *)batch_brick_kernel<double, true>, bytes));
     } else {
-        FSI_CUDA(cudaFuncSetAttribute(batch_brick_kernel<float, false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
-                 "attr");
-        FSI_CUDA(cudaFuncSetAttribute(batch_brick_kernel<float, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
-                 "attr");
+        FSI_TRY(set_smem_limit((const void *)batch_brick_kernel<float, false>, bytes));
+        FSI_TRY(set_smem_limit((const void *)batch_brick_kernel<float, true>, bytes));
     }
-    done[prec] = true;
     return FSI_OK;
 }
 

@@ -345,11 +345,25 @@ __global__ void scatter_kernel(int64_t m, int64_t E, const int32_t *__restrict__
 }
 
 __global__ void cell_sort_kernel(int64_t E, int64_t m, const int32_t *__restrict__ start,
-                                 int32_t *__restrict__ perm)
+                                 int32_t *__restrict__ perm, int32_t *dense, int32_t *dense_count)
 {
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c0 = warp * 32; c0 <= E; c0 += nwarps * 32) cell_sort_segment(E, m, start, perm, c0);
+    for (int64_t c0 = warp * 32; c0 <= E; c0 += nwarps * 32)
+        cell_sort_segment(E, m, start, perm, c0, dense, dense_count);
+}
+
+// the cells listed by cell_sort_kernel, one CTA per cell
+__global__ void __launch_bounds__(1024) dense_sort_kernel(int64_t E, int64_t m,
+                                                          const int32_t *__restrict__ start,
+                                                          int32_t *__restrict__ perm,
+                                                          const int32_t *dense,
+                                                          const int32_t *dense_count)
+{
+    extern __shared__ int32_t sort_sh[];
+    const int n = *dense_count;
+    for (int k = blockIdx.x; k < n; k += gridDim.x)
+        block_sort_cell(E, m, start, perm, dense[k], sort_sh);
 }
 
 // --------------------------------------------------------------- interp / spread
@@ -477,12 +491,13 @@ GridArgs grid_args_of(const fsi_grid &gr)
 
 }  // namespace
 
-int64_t cell_table_scan_ints(int64_t E) { return cell_tiles(E); }
+// the scan's tile sums and, after them, the count of CTA-sorted cells
+int64_t cell_table_scan_ints(int64_t E) { return cell_tiles(E) + 1; }
 
 fsi_status build_cell_table(cudaStream_t s, int64_t E, int64_t m, const int32_t *elem,
                             int32_t *fill, int32_t *scan_tmp, int32_t *cell_start, int32_t *perm)
 {
-    const int64_t ntiles = cell_table_scan_ints(E);
+    const int64_t ntiles = cell_tiles(E);
     scan_tiles_kernel<<<(int)ntiles, 1024, 0, s>>>(E, fill, cell_start, scan_tmp);
     FSI_TRY(check_launch("scan tiles kernel"));
     scan_totals_kernel<<<1, 1024, 0, s>>>(ntiles, scan_tmp);
@@ -493,9 +508,20 @@ fsi_status build_cell_table(cudaStream_t s, int64_t E, int64_t m, const int32_t 
         FSI_CUDA(cudaMemsetAsync(fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
         scatter_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, E, elem, cell_start, fill, perm);
         FSI_TRY(check_launch("scatter kernel"));
+        // the cursors in fill are spent: fill lists the cells too full for a
+        // warp, scan_tmp[ntiles] counts them
+        int32_t *dense_count = scan_tmp + ntiles;
+        FSI_CUDA(cudaMemsetAsync(dense_count, 0, sizeof(int32_t), s), "memset");
         cell_sort_kernel<<<blocks_for((E + 32) / 32 * 32, 256, sm_count() * 64), 256, 0, s>>>(
-            E, m, cell_start, perm);
+            E, m, cell_start, perm, fill, dense_count);
         FSI_TRY(check_launch("cell sort kernel"));
+        if (m > kWarpSortMax) {
+            const int smem = kBlockSortMax * (int)sizeof(int32_t);
+            FSI_TRY(set_smem_limit((const void *)dense_sort_kernel, smem));
+            dense_sort_kernel<<<sm_count(), 1024, smem, s>>>(E, m, cell_start, perm, fill,
+                                                            dense_count);
+            FSI_TRY(check_launch("dense cell sort kernel"));
+        }
     }
     return FSI_OK;
 }

@@ -193,10 +193,20 @@ template <int N> __device__ __forceinline__ void sort_slice(int32_t *sl, int len
         if (i < len) sl[i] = v[i];
 }
 
-// the cells [c0, c0 + 32) (all 32 lanes of the warp call it)
+// Slices of up to kWarpSortMax points are sorted by the warp that owns the
+// cell's segment; fuller cells are put on a list (when the caller gives one)
+// and sorted by a whole CTA in shared memory (block_sort_cell), up to
+// kBlockSortMax points, beyond which one lane shell-sorts the slice.
+constexpr int kWarpSortMax = 128;
+constexpr int kBlockSortMax = 32768;
+
+// the cells [c0, c0 + 32) (all 32 lanes of the warp call it); dense cells go
+// to dense[atomicAdd(dense_count, 1)] when dense is not null
 __device__ __forceinline__ void cell_sort_segment(int64_t E, int64_t m,
                                                   const int32_t *__restrict__ start,
-                                                  int32_t *__restrict__ perm, int64_t c0)
+                                                  int32_t *__restrict__ perm, int64_t c0,
+                                                  int32_t *dense = nullptr,
+                                                  int32_t *dense_count = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int64_t c = c0 + lane;
@@ -210,8 +220,10 @@ __device__ __forceinline__ void cell_sort_segment(int64_t E, int64_t m,
         sort_slice<32>(perm + lo, len);
     else if (len > 32 && len <= 64)
         sort_slice<64>(perm + lo, len);
+    // the CTA-sorted cells
+    if (dense && len > kWarpSortMax) dense[atomicAdd(dense_count, 1)] = (int32_t)c;
     // fuller cells: the warp together
-    unsigned todo = __ballot_sync(0xffffffffu, len > 64);
+    unsigned todo = __ballot_sync(0xffffffffu, len > 64 && (len <= kWarpSortMax || !dense));
     while (todo) {
         const int l = __ffs(todo) - 1;
         todo &= todo - 1;
@@ -219,7 +231,7 @@ __device__ __forceinline__ void cell_sort_segment(int64_t E, int64_t m,
         const int n = __shfl_sync(0xffffffffu, len, l);
         int32_t *sl = perm + base;
         __syncwarp();
-        if (n <= 128) {
+        if (n <= kWarpSortMax) {
             // four values per lane, all in registers
             int own[4], rk[4];
 #pragma unroll
@@ -245,6 +257,43 @@ __device__ __forceinline__ void cell_sort_segment(int64_t E, int64_t m,
             __syncwarp();
         }
     }
+}
+
+// Sort the slice of cell c (cell E: the outside points) with the whole CTA: a
+// bitonic network over the slice padded with INT32_MAX to a power of two, in
+// shared memory sh (kBlockSortMax ints).  Every thread of the CTA calls it.
+__device__ __forceinline__ void block_sort_cell(int64_t E, int64_t m,
+                                                const int32_t *__restrict__ start,
+                                                int32_t *__restrict__ perm, int64_t c, int32_t *sh)
+{
+    const int lo = start[c];
+    const int len = (c < E ? start[c + 1] : (int)m) - lo;
+    if (len > kBlockSortMax) {
+        if (threadIdx.x == 0) shell_sort(perm + lo, len);
+        __syncthreads();
+        return;
+    }
+    int P = 1;
+    while (P < len) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < len ? perm[lo + i] : INT32_MAX;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const int a = sh[i], b = sh[l];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        sh[i] = b;
+                        sh[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < len; i += blockDim.x) perm[lo + i] = sh[i];
+    __syncthreads();
 }
 
 template <typename T> __device__ __forceinline__ T shape_1d(T xi, int side)

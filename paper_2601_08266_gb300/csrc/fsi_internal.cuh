@@ -51,6 +51,10 @@ private:
 // are multiples of it, so that they follow the GPU the library runs on.
 int sm_count();
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device (once per kernel and device; thread-safe).
+fsi_status set_smem_limit(const void *kernel, int bytes);
+
 // ---------------------------------------------------------------- 4-vectors
 // 16/32-byte aligned node records so that one node is one vector load.
 template <typename T> struct alignas(4 * sizeof(T)) vec4 {
@@ -167,6 +171,32 @@ fsi_status solid_tangent_impl(fsi_solid *b, const T *u_af, const double *u_n, co
 fsi_status solid_stage_impl(fsi_solid *b, const double *u, const double *v, const double *a,
                             const double *a1, double *u_af, double *v_af, double *a_am);
 int64_t solid_nodes(const fsi_solid *b);
+
+// tensor-core GEMM of the network's training (mlp_gemm.cu):
+// C[M x N] = epi(op(A) op(B)), FP32 operands rounded to BF16, FP32 accumulation;
+// op(A) = A [M][K] (lda) or, with transA, A^T of A [K][M]; op(B) = B [K][N]
+// (ldb) or, with transB, B^T of B [N][K].  N <= 256.  work: the split-K
+// workspace (tc_gemm_work_floats() floats); err: a device flag raised when a
+// tensor-core wait runs out.
+enum TcEpi { TC_EPI_STORE = 0, TC_EPI_BIAS = 1, TC_EPI_BIAS_RELU = 2, TC_EPI_MASK = 3 };
+struct TcGemm {
+    int M, N, K;
+    const float *A;
+    int64_t lda;
+    int transA;
+    const float *B;
+    int64_t ldb;
+    int transB;
+    float *C;
+    int64_t ldc;
+    int epi;
+    const float *bias;  // [N] for TC_EPI_BIAS / TC_EPI_BIAS_RELU
+    float *Cpre;        // pre-activation output for TC_EPI_BIAS_RELU (may be null)
+    const float *mask;  // [M x N] (ldc) for TC_EPI_MASK: C *= (mask > 0)
+    int BN;             // set by tc_gemm: N rounded up to a multiple of 16
+};
+size_t tc_gemm_work_floats();
+fsi_status tc_gemm(cudaStream_t s, const TcGemm &g, float *work, int *err);
 
 // fused tensor-core inference of the initial-guess network (mlp_tc.cu)
 size_t mlp_tc_packed_bytes();

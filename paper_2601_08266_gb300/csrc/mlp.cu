@@ -4,10 +4,9 @@
 // kernels (forward, backward, Adam) and applied per node to predict the
 // Newton predictor y^(0) = y_n + e + c, e = 2 d_{n-1} - d_{n-2}.
 //
-// GEMM: C[M x N] = op(A)[M x K] op(B)[K x N] with FP32 operands in global
-// memory rounded to BF16 when staged into shared memory, mma.sync m16n8k16
-// (BF16 x BF16 -> FP32), 64x64 CTA tiles, 4 warps of 32x32, fused epilogues
-// (bias, ReLU keeping the pre-activation, multiply by a ReLU mask).
+// GEMMs: the tcgen05 tensor-core kernel of mlp_gemm.cu (BF16 operands, FP32
+// accumulation in TMEM, fused epilogues: bias, ReLU keeping the
+// pre-activation, the ReLU mask of the backward pass).
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -25,7 +24,8 @@ struct fsi_mlp {
     float *X;       // features of a predict chunk [max_batch][112]
     double *loss_partial;
     void *packed;   // BF16 weights in the tensor-core operand layout (mlp_tc.cu)
-    int *tc_err;    // wait-timeout flag of the tensor-core predict kernel
+    int *tc_err;    // wait-timeout flag of the tensor-core kernels (predict and GEMMs)
+    float *gemm_work;  // split-K partial tiles of the weight-gradient GEMMs
 };
 
 namespace fsi {
@@ -36,138 +36,24 @@ constexpr int64_t OFF_W1 = 0, OFF_b1 = OFF_W1 + NI * NH, OFF_W2 = OFF_b1 + NH,
                   OFF_b2 = OFF_W2 + NH * NH, OFF_W3 = OFF_b2 + NH, OFF_b3 = OFF_W3 + NH * NO,
                   N_PARAMS = OFF_b3 + NO;
 
-constexpr int BM = 64, BN = 64, BK = 32, SK = BK + 8;  // SK: padded smem row (bf16)
+enum Epi { EPI_STORE = TC_EPI_STORE, EPI_BIAS = TC_EPI_BIAS, EPI_BIAS_RELU = TC_EPI_BIAS_RELU,
+           EPI_MASK = TC_EPI_MASK };
 
-enum Epi { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_RELU = 2, EPI_MASK = 3 };
-
-struct GemmArgs {
-    int M, N, K;
-    const float *A;
-    int64_t lda;
-    int transA;
-    const float *B;
-    int64_t ldb;
-    int transB;
-    float *C;
-    int64_t ldc;
-    int epi;
-    const float *bias;  // [N] for EPI_BIAS / EPI_BIAS_RELU
-    float *Cpre;        // pre-activation output for EPI_BIAS_RELU (may be null)
-    const float *mask;  // [M x N] (ldc) for EPI_MASK: C *= (mask > 0)
-};
-
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
+fsi_status gemm(const fsi_mlp *h, const TcGemm &g)
 {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    return tc_gemm(h->stream, g, h->gemm_work, h->tc_err);
 }
 
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
+TcGemm ga(int M, int N, int K, const float *A, int64_t lda, int tA, const float *B, int64_t ldb,
+          int tB, float *C, int64_t ldc, int epi = EPI_STORE, const float *bias = nullptr,
+          float *Cpre = nullptr, const float *mask = nullptr)
 {
-    __shared__ __align__(16) __nv_bfloat16 As[BM][SK];  // [m][k]
-    __shared__ __align__(16) __nv_bfloat16 Bs[BN][SK];  // [n][k]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 1, wn = warp & 1;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int gq = lane >> 2, tq = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-
-    for (int k0 = 0; k0 < g.K; k0 += BK) {
-        // stage A (BM x BK) and B (BK x BN) as BF16; zero outside the matrices
-        for (int e = tid; e < BM * BK; e += 128) {
-            int r, kk;
-            if (!g.transA) { r = e / BK; kk = e % BK; }   // k fastest: coalesced
-            else { kk = e / BM; r = e % BM; }             // m fastest: coalesced
-            const int gi = m0 + r, gk = k0 + kk;
-            float v = 0.f;
-            if (gi < g.M && gk < g.K)
-                v = g.transA ? g.A[(int64_t)gk * g.lda + gi] : g.A[(int64_t)gi * g.lda + gk];
-            As[r][kk] = __float2bfloat16_rn(v);
-        }
-        for (int e = tid; e < BN * BK; e += 128) {
-            int c, kk;
-            if (!g.transB) { kk = e / BN; c = e % BN; }   // n fastest
-            else { c = e / BK; kk = e % BK; }             // k fastest
-            const int gj = n0 + c, gk = k0 + kk;
-            float v = 0.f;
-            if (gj < g.N && gk < g.K)
-                v = g.transB ? g.B[(int64_t)gj * g.ldb + gk] : g.B[(int64_t)gk * g.ldb + gj];
-            Bs[c][kk] = __float2bfloat16_rn(v);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[2][4], bf[4][2];
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                const int r = wm * 32 + mi * 16 + gq;
-                af[mi][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * tq]);
-                af[mi][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * tq]);
-                af[mi][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * tq + 8]);
-                af[mi][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * tq + 8]);
-            }
-#pragma unroll
-            for (int ni = 0; ni < 4; ++ni) {
-                const int c = wn * 32 + ni * 8 + gq;
-                bf[ni][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + 2 * tq]);
-                bf[ni][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + 2 * tq + 8]);
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bf[ni]);
-        }
-        __syncthreads();
-    }
-    // epilogue
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const int i = m0 + wm * 32 + mi * 16 + gq + 8 * h;
-                    const int j = n0 + wn * 32 + ni * 8 + 2 * tq + t;
-                    if (i >= g.M || j >= g.N) continue;
-                    float v = acc[mi][ni][2 * h + t];
-                    const int64_t o = (int64_t)i * g.ldc + j;
-                    if (g.epi == EPI_BIAS || g.epi == EPI_BIAS_RELU) v += g.bias[j];
-                    if (g.epi == EPI_BIAS_RELU) {
-                        if (g.Cpre) g.Cpre[o] = v;
-                        v = v > 0.f ? v : 0.f;
-                    }
-                    if (g.epi == EPI_MASK) v = g.mask[o] > 0.f ? v : 0.f;
-                    g.C[o] = v;
-                }
-}
-
-fsi_status gemm(cudaStream_t s, GemmArgs g)
-{
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-    gemm_bf16_kernel<<<grid, 128, 0, s>>>(g);
-    return check_launch("bf16 gemm");
-}
-
-GemmArgs ga(int M, int N, int K, const float *A, int64_t lda, int tA, const float *B, int64_t ldb,
-            int tB, float *C, int64_t ldc, int epi = EPI_STORE, const float *bias = nullptr,
-            float *Cpre = nullptr, const float *mask = nullptr)
-{
-    GemmArgs g;
+    TcGemm g;
     g.M = M; g.N = N; g.K = K;
     g.A = A; g.lda = lda; g.transA = tA;
     g.B = B; g.ldb = ldb; g.transB = tB;
     g.C = C; g.ldc = ldc; g.epi = epi; g.bias = bias; g.Cpre = Cpre; g.mask = mask;
+    g.BN = 0;
     return g;
 }
 
@@ -356,13 +242,23 @@ fsi_status dots3(cudaStream_t s, int64_t n, const double *x, const double *y, co
 
 fsi_status forward_impl(fsi_mlp *h, const float *P, const float *X, int64_t B, bool keep)
 {
-    cudaStream_t s = h->stream;
-    FSI_TRY(gemm(s, ga((int)B, NH, NI, X, NI, 0, P + OFF_W1, NH, 0, h->H1, NH, EPI_BIAS_RELU,
+    FSI_TRY(gemm(h, ga((int)B, NH, NI, X, NI, 0, P + OFF_W1, NH, 0, h->H1, NH, EPI_BIAS_RELU,
                        P + OFF_b1, keep ? h->Z1 : nullptr)));
-    FSI_TRY(gemm(s, ga((int)B, NH, NH, h->H1, NH, 0, P + OFF_W2, NH, 0, h->H2, NH, EPI_BIAS_RELU,
+    FSI_TRY(gemm(h, ga((int)B, NH, NH, h->H1, NH, 0, P + OFF_W2, NH, 0, h->H2, NH, EPI_BIAS_RELU,
                        P + OFF_b2, keep ? h->Z2 : nullptr)));
-    return gemm(s, ga((int)B, NO, NH, h->H2, NH, 0, P + OFF_W3, NO, 0, h->O, NO, EPI_BIAS,
+    return gemm(h, ga((int)B, NO, NH, h->H2, NH, 0, P + OFF_W3, NO, 0, h->O, NO, EPI_BIAS,
                       P + OFF_b3));
+}
+
+// the tensor-core kernels' wait-timeout flag, read (after the caller's
+// synchronisation) and cleared
+fsi_status take_tc_error(fsi_mlp *h)
+{
+    int f = 0;
+    FSI_CUDA(cudaMemcpy(&f, h->tc_err, sizeof f, cudaMemcpyDeviceToHost), "memcpy");
+    if (!f) return FSI_OK;
+    FSI_CUDA(cudaMemset(h->tc_err, 0, sizeof(int)), "memset");
+    return set_error(FSI_ERR_TIMEOUT, "a tensor-core wait ran out (network kernels)");
 }
 
 fsi_status check_mlp(const fsi_mlp *h, int64_t B)
@@ -408,6 +304,8 @@ fsi_status fsi_mlp_create(int device, void *cuda_stream, int64_t max_batch, fsi_
     cudaError_t e = cudaMalloc(&h->loss_partial, 1024 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->packed, mlp_tc_packed_bytes());
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->tc_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->gemm_work, tc_gemm_work_floats() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(h->tc_err, 0, sizeof(int));
     if (e != cudaSuccess) {
         fsi_mlp_destroy(h);
         return check_cuda(e, "mlp allocation");
@@ -426,6 +324,7 @@ void fsi_mlp_destroy(fsi_mlp *h)
     cudaFree(h->loss_partial);
     cudaFree(h->packed);
     cudaFree(h->tc_err);
+    cudaFree(h->gemm_work);
     delete h;
 }
 
@@ -458,17 +357,17 @@ fsi_status fsi_mlp_loss_grad(fsi_mlp *h, const float *params, const float *X, co
     FSI_TRY(check_launch("loss kernels"));
     const int M = (int)B;
     // layer 3: dW3 = H2^T dO, db3 = colsum(dO), dZ2 = (dO W3^T) * (Z2 > 0)
-    FSI_TRY(gemm(s, ga(NH, NO, M, h->H2, NH, 1, h->dO, NO, 0, grad + OFF_W3, NO)));
+    FSI_TRY(gemm(h, ga(NH, NO, M, h->H2, NH, 1, h->dO, NO, 0, grad + OFF_W3, NO)));
     colsum_kernel<<<1, 32, 0, s>>>(B, NO, h->dO, grad + OFF_b3);
-    FSI_TRY(gemm(s, ga(M, NH, NO, h->dO, NO, 0, P + OFF_W3, NO, 1, h->dZ2, NH, EPI_MASK,
+    FSI_TRY(gemm(h, ga(M, NH, NO, h->dO, NO, 0, P + OFF_W3, NO, 1, h->dZ2, NH, EPI_MASK,
                        nullptr, nullptr, h->Z2)));
     // layer 2: dW2 = H1^T dZ2, db2, dZ1 = (dZ2 W2^T) * (Z1 > 0)
-    FSI_TRY(gemm(s, ga(NH, NH, M, h->H1, NH, 1, h->dZ2, NH, 0, grad + OFF_W2, NH)));
+    FSI_TRY(gemm(h, ga(NH, NH, M, h->H1, NH, 1, h->dZ2, NH, 0, grad + OFF_W2, NH)));
     colsum_kernel<<<1, 256, 0, s>>>(B, NH, h->dZ2, grad + OFF_b2);
-    FSI_TRY(gemm(s, ga(M, NH, NH, h->dZ2, NH, 0, P + OFF_W2, NH, 1, h->dZ1, NH, EPI_MASK,
+    FSI_TRY(gemm(h, ga(M, NH, NH, h->dZ2, NH, 0, P + OFF_W2, NH, 1, h->dZ1, NH, EPI_MASK,
                        nullptr, nullptr, h->Z1)));
     // layer 1: dW1 = X^T dZ1, db1
-    FSI_TRY(gemm(s, ga(NI, NH, M, X, NI, 1, h->dZ1, NH, 0, grad + OFF_W1, NH)));
+    FSI_TRY(gemm(h, ga(NI, NH, M, X, NI, 1, h->dZ1, NH, 0, grad + OFF_W1, NH)));
     colsum_kernel<<<1, 256, 0, s>>>(B, NH, h->dZ1, grad + OFF_b1);
     return check_launch("bias gradients");
 }
@@ -602,7 +501,15 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
         FSI_CUDA(cudaMemcpyAsync(st->y, trial, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s),
                  "memcpy");
     FSI_CUDA(cudaStreamSynchronize(s), "sync");
-    return FSI_OK;
+    return take_tc_error(h);
+}
+
+fsi_status fsi_mlp_check(fsi_mlp *h)
+{
+    if (!h) return set_error(FSI_ERR_ARG, "mlp handle is NULL");
+    FSI_DEVICE(h->device);
+    FSI_CUDA(cudaDeviceSynchronize(), "device sync");
+    return take_tc_error(h);
 }
 
 }  // extern "C"

@@ -37,6 +37,7 @@
 #include <stdint.h>
 
 #include "fsi_internal.cuh"
+#include "tc_common.cuh"
 
 namespace fsi {
 namespace {
@@ -56,7 +57,6 @@ constexpr uint32_t OFF_SW1 = 0, OFF_SW2A = OFF_SW1 + SZ_W1, OFF_SW2B = OFF_SW2A 
                    SMEM_BYTES = OFF_SB2 + NH * 4;  // 227,328
 constexpr uint32_t PACKED_BYTES = SZ_W1 + 2 * SZ_W2H;  // 188,416
 constexpr uint32_t TMEM_COLS = 512;
-constexpr long long kWaitLimit = 4000000;  // try_wait polls (each suspends briefly)
 // Four warpgroups share every tile: warp w reads TMEM lanes 32 (w % 4) ..
 // (the tile's node rows), so warpgroup g = w / 4 takes the same rows and its
 // share of the columns: feature chunks [kChunk[g], kChunk[g + 1]), H1
@@ -65,100 +65,14 @@ constexpr int kGroups = 4;
 constexpr int kThreads = 128 * kGroups;
 __constant__ int kChunk[kGroups + 1] = {0, 4, 8, 11, 14};
 
-// byte offset of element (row, k) in a K-major canonical tile with kc chunks
-__host__ __device__ __forceinline__ uint32_t kmaj(uint32_t row, uint32_t k, uint32_t kc)
-{
-    return (row >> 3) * (kc * 128u) + (k >> 3) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
-}
+using namespace tc;
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// UMMA shared-memory descriptor: start, LBO, SBO (all >> 4), version 1 at
-// bit 46, no swizzle (layout type 0 in bits 61..63), base offset 0
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
-{
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// instruction descriptor, kind::f16: D FP32 (bit 4), A and B BF16 (bits 7, 10),
-// both K-major, N >> 3 at bit 17, M >> 4 at bit 24
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NH >> 3) << 17) |
-                            ((uint32_t)(TM >> 4) << 24);
+constexpr uint32_t kIdesc = idesc_bf16(TM, NH);
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc)
 {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
-        : "memory");
+    tc::mma_bf16(d_tmem, a, b, kIdesc, acc);
 }
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait; false when the limit ran out
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    for (long long it = 0; it < kWaitLimit; ++it)
-        if (mbar_try(bar, parity)) return true;
-    return false;
-}
-
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
-{
-    const __nv_bfloat16 lo = __float2bfloat16_rn(a), hi = __float2bfloat16_rn(b);
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-__device__ __forceinline__ float bf16r(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
 
 // W1 [NI][NH] and W2 [NH][NH] (input-major, as trained) -> B operands
 // [N = out][K = in] BF16 in the canonical layout: W1 (K = 112), then the two
@@ -509,18 +423,14 @@ fsi_status mlp_predict_tc(cudaStream_t s, int device, const fsi_grid &g, int64_t
     const int sms = sm_count();
     pack_weights_kernel<<<sm_count() * 4, 256, 0, s>>>(params, (uint8_t *)packed);
     FSI_TRY(check_launch("pack weights"));
-    FSI_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(int), s), "memset");
     TcArgs a{g.N[0], g.N[1], g.N[2], n, params, (const uint8_t *)packed, in_mean, in_std,
              out_mean, out_std, Vn, y, d1, d2, y0, dev_err};
     const int64_t tiles = (n + TM - 1) / TM;
     const int grid = (int)(tiles < sms ? tiles : sms);
     mlp_predict_tc_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(a);
-    FSI_TRY(check_launch("tensor-core predict"));
-    int h = 0;
-    FSI_CUDA(cudaMemcpyAsync(&h, dev_err, sizeof h, cudaMemcpyDeviceToHost, s), "memcpy");
-    FSI_CUDA(cudaStreamSynchronize(s), "sync");
-    if (h) return set_error(FSI_ERR_TIMEOUT, "tensor-core predict: a wait ran out");
-    return FSI_OK;
+    // asynchronous: a wait that ran out stays flagged in dev_err until the
+    // handle's next check (fsi_mlp_check, fsi_mlp_guess)
+    return check_launch("tensor-core predict");
 }
 
 }  // namespace fsi

@@ -1,6 +1,9 @@
 // runtime.cu -- handles, errors, validation and the generalized-alpha stage
 // kernel of libfsi (C ABI in include/fsi.h).
 #include <atomic>
+#include <mutex>
+#include <set>
+#include <tuple>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -43,6 +46,21 @@ DeviceGuard::~DeviceGuard()
 {
     int cur = -1;
     if (prev_ >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev_) cudaSetDevice(prev_);
+}
+
+fsi_status set_smem_limit(const void *kernel, int bytes)
+{
+    static std::mutex mu;
+    static std::set<std::tuple<const void *, int, int>> done;
+    int dev = 0;
+    FSI_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(kernel, dev, bytes);
+    if (done.count(key)) return FSI_OK;
+    FSI_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+             "cudaFuncSetAttribute");
+    done.insert(key);
+    return FSI_OK;
 }
 
 int sm_count()

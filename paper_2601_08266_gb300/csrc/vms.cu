@@ -149,13 +149,7 @@ fsi_status launch_geo(fsi_mesh *m, const void *U, const void *A, const void *f, 
         kernel = vms_brick_kernel_capped<T, JAC, MAPPED, FUSED>;
     else
         kernel = vms_brick_kernel<T, JAC, MAPPED, FUSED>;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        FSI_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      200 * 1024),
-                 "cudaFuncSetAttribute");
-        attr_set = true;
-    }
+    FSI_TRY(set_smem_limit((const void *)kernel, 200 * 1024));
     kernel<<<nbricks, b.threads, smem, m->stream>>>(P);
     FSI_TRY(check_launch("vms brick kernel"));
     const int threads = 256;

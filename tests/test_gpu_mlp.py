@@ -33,7 +33,11 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300)
 
 
-def test_forward_and_gradients_match_oracle(fsi):
+@pytest.mark.parametrize("B", [300, 4096 + 77])
+def test_forward_and_gradients_match_oracle(fsi, B):
+    """The tcgen05 GEMMs of the forward and backward passes: one ragged row
+    tile, and a batch whose weight gradients take the split-K path (K = B);
+    bitwise repeatable, no wait ran out."""
     import torch
     from oracle import mlp as om
     rng = np.random.default_rng(0)
@@ -43,17 +47,19 @@ def test_forward_and_gradients_match_oracle(fsi):
             p[k] = rng.normal(scale=0.1, size=p[k].shape)
     theta = om.flatten(p).astype(np.float32).astype(np.float64)
     p = om.unflatten(theta)
-    B = 300
     X = rng.normal(size=(B, om.N_IN)).astype(np.float32).astype(np.float64)
     Tt = rng.normal(size=(B, om.N_OUT)).astype(np.float32).astype(np.float64)
-    h = fsi.Mlp(512)
+    h = fsi.Mlp(8192)
     P = T(theta, torch.float32)
     out = torch.empty((B, 4), dtype=torch.float32, device="cuda")
     fsi.fsi_mlp_forward(h, P, T(X, torch.float32), out)
     loss = torch.empty(1, dtype=torch.float32, device="cuda")
     grad = torch.empty_like(P)
     fsi.fsi_mlp_loss_grad(h, P, T(X, torch.float32), T(Tt, torch.float32), loss, grad)
-    torch.cuda.synchronize()
+    grad2 = torch.empty_like(P)
+    fsi.fsi_mlp_loss_grad(h, P, T(X, torch.float32), T(Tt, torch.float32), loss, grad2)
+    h.check()
+    assert torch.equal(grad, grad2)
     # against the oracle with the kernels' BF16 operand rounding: FP32
     # accumulation is the only remaining difference
     O_b, _ = om.forward(p, X, bf16=True)
@@ -228,6 +234,7 @@ def test_learned_guess_end_to_end(fsi, capsys):
         fsi.fsi_mlp_adam(h, P, G, Mo, Vo, it, lr=lr)
         if it in (1, iters):
             losses.append(float(loss.item()))
+    h.check()
     assert losses[-1] < 0.3 * losses[0], losses
     learn = {"h": h, "P": P, "im": T(im.astype(np.float32)), "is": T(isd.astype(np.float32)),
              "om": T(om_.astype(np.float32)), "os": T(osd.astype(np.float32))}
