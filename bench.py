@@ -936,6 +936,21 @@ def newton_section(args, dev, stream):
                                                   out["mixed_learned"]["seconds"])
     if h is not None:
         h.close()
+    # the Krylov BLAS-1 kernels on vectors of this grid's size (FP32, as in the
+    # mixed solve): algorithmic bytes per call / CUDA-event time
+    from paper_2601_08266_gb300 import _binding as B
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    length = 4 * ch.n
+    blas = {"vector_mb_f32": length * 4 / 1e6}
+    for nvec in (8, 24, 48):
+        td, ta = B.fsi_measure_blas1(dev.index, fsi.FSI_F32, length, nvec, reps=10)
+        bd = (nvec + -(-nvec // 8)) * length * 4
+        ba = (nvec + 2) * length * 4
+        blas[str(nvec)] = {"dot_ms": td * 1e3, "dot_gb_s": bd / td / 1e9,
+                           "dot_hbm_frac": bd / td / 1e9 / hbm,
+                           "update_ms": ta * 1e3, "update_gb_s": ba / ta / 1e9,
+                           "update_hbm_frac": ba / ta / 1e9 / hbm}
+    out["krylov_blas1"] = blas
     ch.close()
     return out
 
@@ -1371,13 +1386,43 @@ def mlp_section(args, dev, stream, W):
     """Per-node inference of the initial-guess network over whole grids: the
     fused tcgen05 predictor (features, three layers, predictor in one
     persistent kernel) against the unfused path of the training kernels
-    (features to HBM, then mma.sync GEMMs per chunk)."""
+    (features to HBM, then the training GEMMs per chunk); and one training
+    step (forward, loss, backward) on a batch of 4096 samples."""
     import torch
     import paper_2601_08266_gb300 as fsi
     out = {"kernel": "fused: tcgen05.mma kind::f16 (BF16 in, FP32 accumulate in TMEM), weights "
-                     "resident in shared memory via cp.async.bulk; unfused: mma.sync m16n8k16"}
+                     "resident in shared memory via cp.async.bulk; unfused and training: the "
+                     "tcgen05 GEMM kernel (BF16 operands staged from FP32, TMEM accumulators, "
+                     "split-K weight gradients)"}
     peaks = measured_peaks()
     bf16_peak = peaks.get("bf16_tflops", 1865.6)
+    # one training step: 3 forward GEMMs, 5 backward GEMMs (2 x the forward
+    # flops), bias sums and the loss; CUDA events over 20 steps
+    B = 4096
+    g = torch.Generator(device=dev).manual_seed(SEED + 7)
+    with torch.cuda.stream(stream):
+        P = torch.randn(fsi.fsi_mlp_num_params(), device=dev, generator=g) * 0.05
+        Xb = torch.randn((B, 112), device=dev, generator=g)
+        Tb = torch.randn((B, 4), device=dev, generator=g)
+        G = torch.empty_like(P)
+        loss = torch.empty(1, device=dev)
+    h = fsi.Mlp(B, device=dev.index, stream=stream.cuda_stream)
+    for _ in range(3):
+        fsi.fsi_mlp_loss_grad(h, P, Xb, Tb, loss, G)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(20):
+        fsi.fsi_mlp_loss_grad(h, P, Xb, Tb, loss, G)
+    e1.record(stream)
+    stream.synchronize()
+    h.check()
+    ms = e0.elapsed_time(e1) / 20
+    tflop = 3 * 2.0 * B * (112 * 256 + 256 * 256 + 256 * 4) / 1e12
+    out["training_step"] = {"batch": B, "ms": ms, "tflop_s": tflop / (ms * 1e-3),
+                            "frac_of_bf16_peak": tflop / (ms * 1e-3) / bf16_peak,
+                            "flops": "3 x 2 B (112 x 256 + 256 x 256 + 256 x 4)"}
+    h.close()
     for N in (64, 128):
         mesh = fsi.Mesh(N, device=dev.index, stream=stream.cuda_stream)
         n = mesh.n_nodes
@@ -1409,7 +1454,7 @@ def mlp_section(args, dev, stream, W):
                                      Xc[:k])
                 fsi.fsi_mlp_forward(h, P, Xc[:k], Oc[:k])
         res = {"nodes": n}
-        for name, fn in (("fused_tcgen05", fused), ("unfused_mma_sync", unfused)):
+        for name, fn in (("fused_tcgen05", fused), ("unfused", unfused)):
             for _ in range(2):
                 fn()
             stream.synchronize()

@@ -795,6 +795,18 @@ fsi_status fsi_mesh_autotune(fsi_mesh *mesh, int op, fsi_prec prec, int reps,
  * stream and a small buffer it allocates and frees; synchronises.          */
 fsi_status fsi_measure_fma_peak(int device, fsi_prec prec, double *flops_per_second);
 
+/* Measurement helper (the paper has no counterpart): seconds per call of the
+ * Krylov solver's BLAS-1 kernels on vectors of `len` entries (a multiple of
+ * 4) in `prec` (FSI_F64, or FSI_F32 as in the mixed mode): the multi-dot of
+ * nvec basis vectors with one vector (partial sums and their fixed-order
+ * final sums; the reads are nvec + ceil(nvec / 8) vectors), and the
+ * multi-update w -= V h over nvec vectors with the fused |w|^2 (nvec + 1
+ * reads, 1 write).  1 <= nvec <= 256.  CUDA events over reps calls after one
+ * warm-up, on its own stream and buffers, which it allocates and frees;
+ * synchronises.                                                            */
+fsi_status fsi_measure_blas1(int device, fsi_prec prec, int64_t len, int nvec, int reps,
+                             double *dot_seconds, double *axpy_seconds);
+
 #ifdef __cplusplus
 }
 #endif

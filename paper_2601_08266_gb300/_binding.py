@@ -120,6 +120,8 @@ _SIGS = {
     "fsi_dlm_interp": ([_VP, _INT, _I64, _VP, _VP, _VP, _VP], _INT),
     "fsi_dlm_spread": ([_VP, _INT, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _INT], _INT),
     "fsi_measure_fma_peak": ([_INT, _INT, ctypes.POINTER(ctypes.c_double)], _INT),
+    "fsi_measure_blas1": ([_INT, _INT, _I64, _INT, _INT, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double)], _INT),
     "fsi_coupled_residual": ([_VP, _INT, ctypes.POINTER(fsi_step_state), _VP], _INT),
     "fsi_coupled_jacobian_apply": ([_VP, _INT, ctypes.POINTER(fsi_step_state), _VP, _VP], _INT),
     "fsi_block_diagonal": ([_VP, _INT, ctypes.POINTER(fsi_step_state), _VP], _INT),
@@ -459,6 +461,15 @@ def fsi_measure_fma_peak(device, prec):
     out = ctypes.c_double(0.0)
     _check(lib().fsi_measure_fma_peak(device, prec, ctypes.byref(out)))
     return out.value
+
+
+def fsi_measure_blas1(device, prec, length, nvec, reps=10):
+    """(seconds per multi-dot, seconds per multi-update) of the Krylov
+    BLAS-1 kernels on nvec basis vectors of `length` entries."""
+    d, a = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().fsi_measure_blas1(device, prec, int(length), int(nvec), int(reps),
+                                   ctypes.byref(d), ctypes.byref(a)))
+    return d.value, a.value
 
 
 class StepState:

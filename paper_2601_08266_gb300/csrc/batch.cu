@@ -349,6 +349,7 @@ template <typename T> fsi_status build_batch(fsi_batch *b)
         D.g.hx = m->grid.h[0];
         D.g.hy = m->grid.h[1];
         D.g.hz = m->grid.h[2];
+        dlmd::set_reciprocals(D.g);
         D.m = it.m;
         D.E = m->n_elems;
         D.elem = it.elem;

@@ -36,6 +36,7 @@ GridArgs grid_args(const fsi_mesh *m)
     g.hx = m->grid.h[0];
     g.hy = m->grid.h[1];
     g.hz = m->grid.h[2];
+    set_reciprocals(g);
     return g;
 }
 
@@ -486,6 +487,7 @@ GridArgs grid_args_of(const fsi_grid &gr)
     g.hx = gr.h[0];
     g.hy = gr.h[1];
     g.hz = gr.h[2];
+    set_reciprocals(g);
     return g;
 }
 

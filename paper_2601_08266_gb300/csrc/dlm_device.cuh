@@ -3,6 +3,8 @@
 // kernels (batch.cu).  See dlm.cu for the design.
 #pragma once
 
+#include <cmath>
+
 #include "df64.cuh"
 #include "fsi_internal.cuh"
 
@@ -12,7 +14,35 @@ namespace dlmd {
 struct GridArgs {
     int Nx, Ny, Nz;
     double x0, y0, z0, hx, hy, hz;
+    // 1/h_k when h_k is an exact power of two (then d * (1/h_k) is the
+    // correctly rounded d / h_k: both round the same real number d 2^-e), else 0
+    double rx, ry, rz;
 };
+
+// the exact reciprocal of h when h = 2^e (with 1/h a normal double), else 0
+inline double pow2_reciprocal(double h)
+{
+    int e = 0;
+    const double f = std::frexp(h, &e);  // h = f 2^e, f in [0.5, 1)
+    if (!(h > 0.0) || f != 0.5) return 0.0;
+    const double r = std::ldexp(1.0, 1 - e);
+    return (std::isnormal(r) && r * h == 1.0) ? r : 0.0;
+}
+
+inline void set_reciprocals(GridArgs &g)
+{
+    g.rx = pow2_reciprocal(g.hx);
+    g.ry = pow2_reciprocal(g.hy);
+    g.rz = pow2_reciprocal(g.hz);
+}
+
+// (X - x0) / h as IEEE FP64 division, by the exact multiply when h is a
+// power of two (GB300's FP64 division is a long dependent sequence)
+__device__ __forceinline__ double grid_coord(double X, double x0, double h, double r)
+{
+    const double d = X - x0;
+    return r != 0.0 ? d * r : d / h;
+}
 
 // ------------------------------------------------------------ location
 // Location of point b on the uniform grid: t_k = (X_k - x0_k)/h_k, outside
@@ -24,9 +54,9 @@ __device__ __forceinline__ int locate_point(const GridArgs &g, int64_t b,
                                             const double *__restrict__ X,
                                             int32_t *__restrict__ elem, S *__restrict__ xi)
 {
-    const double tx = (X[3 * b + 0] - g.x0) / g.hx;
-    const double ty = (X[3 * b + 1] - g.y0) / g.hy;
-    const double tz = (X[3 * b + 2] - g.z0) / g.hz;
+    const double tx = grid_coord(X[3 * b + 0], g.x0, g.hx, g.rx);
+    const double ty = grid_coord(X[3 * b + 1], g.y0, g.hy, g.ry);
+    const double tz = grid_coord(X[3 * b + 2], g.z0, g.hz, g.rz);
     const bool in = (tx >= 0.0 && tx <= (double)g.Nx) && (ty >= 0.0 && ty <= (double)g.Ny) &&
                     (tz >= 0.0 && tz <= (double)g.Nz);
     if (!in) {

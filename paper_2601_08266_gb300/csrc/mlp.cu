@@ -87,14 +87,38 @@ __global__ void loss_final_kernel(int nb, const double *partial, float *loss)
     }
 }
 
-// db[j] = sum_i dZ[i][j] (fixed order over i)
-__global__ void colsum_kernel(int64_t M, int N, const float *dZ, float *db)
+// db[j] = sum_i dZ[i][j] in two passes with a fixed order: CTA (cx, r) sums
+// its row slice of columns 32 cx .. 32 cx + 31 (thread (x, y): rows y, y + 8,
+// ... of the slice, then a tree over y) into part[r][j]; then the slices are
+// added in order.  FP32 sums of at most a few thousand rows.
+constexpr int kColSlices = 16;
+
+__global__ void colsum_partial_kernel(int64_t M, int N, const float *dZ, float *part)
+{
+    __shared__ float red[8][33];
+    const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + x;
+    const int64_t per = (M + gridDim.y - 1) / gridDim.y;
+    const int64_t r0 = blockIdx.y * per, r1 = min(M, r0 + per);
+    float acc = 0.f;
+    if (j < N)
+        for (int64_t i = r0 + y; i < r1; i += 8) acc += dZ[i * N + j];
+    red[y][x] = acc;
+    __syncthreads();
+    for (int st = 4; st > 0; st >>= 1) {
+        if (y < st) red[y][x] += red[y + st][x];
+        __syncthreads();
+    }
+    if (y == 0 && j < N) part[(int64_t)blockIdx.y * N + j] = red[0][x];
+}
+
+__global__ void colsum_final_kernel(int N, int slices, const float *part, float *db)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
-    double s = 0.0;
-    for (int64_t i = 0; i < M; ++i) s += dZ[i * N + j];
-    db[j] = (float)s;
+    float s = 0.f;
+    for (int r = 0; r < slices; ++r) s += part[(int64_t)r * N + j];
+    db[j] = s;
 }
 
 __global__ void adam_kernel(int64_t n, float *p, const float *g, float *m, float *v, float lr,
@@ -240,6 +264,16 @@ fsi_status dots3(cudaStream_t s, int64_t n, const double *x, const double *y, co
     return FSI_OK;
 }
 
+// db = column sums of dZ [M][N] (the bias gradient), through the split-K
+// workspace (free between GEMMs in stream order)
+fsi_status colsum(const fsi_mlp *h, int64_t M, int N, const float *dZ, float *db)
+{
+    dim3 grid((N + 31) / 32, kColSlices);
+    colsum_partial_kernel<<<grid, 256, 0, h->stream>>>(M, N, dZ, h->gemm_work);
+    colsum_final_kernel<<<(N + 255) / 256, 256, 0, h->stream>>>(N, kColSlices, h->gemm_work, db);
+    return check_launch("bias gradient");
+}
+
 fsi_status forward_impl(fsi_mlp *h, const float *P, const float *X, int64_t B, bool keep)
 {
     FSI_TRY(gemm(h, ga((int)B, NH, NI, X, NI, 0, P + OFF_W1, NH, 0, h->H1, NH, EPI_BIAS_RELU,
@@ -358,18 +392,17 @@ fsi_status fsi_mlp_loss_grad(fsi_mlp *h, const float *params, const float *X, co
     const int M = (int)B;
     // layer 3: dW3 = H2^T dO, db3 = colsum(dO), dZ2 = (dO W3^T) * (Z2 > 0)
     FSI_TRY(gemm(h, ga(NH, NO, M, h->H2, NH, 1, h->dO, NO, 0, grad + OFF_W3, NO)));
-    colsum_kernel<<<1, 32, 0, s>>>(B, NO, h->dO, grad + OFF_b3);
+    FSI_TRY(colsum(h, B, NO, h->dO, grad + OFF_b3));
     FSI_TRY(gemm(h, ga(M, NH, NO, h->dO, NO, 0, P + OFF_W3, NO, 1, h->dZ2, NH, EPI_MASK,
                        nullptr, nullptr, h->Z2)));
     // layer 2: dW2 = H1^T dZ2, db2, dZ1 = (dZ2 W2^T) * (Z1 > 0)
     FSI_TRY(gemm(h, ga(NH, NH, M, h->H1, NH, 1, h->dZ2, NH, 0, grad + OFF_W2, NH)));
-    colsum_kernel<<<1, 256, 0, s>>>(B, NH, h->dZ2, grad + OFF_b2);
+    FSI_TRY(colsum(h, B, NH, h->dZ2, grad + OFF_b2));
     FSI_TRY(gemm(h, ga(M, NH, NH, h->dZ2, NH, 0, P + OFF_W2, NH, 1, h->dZ1, NH, EPI_MASK,
                        nullptr, nullptr, h->Z1)));
     // layer 1: dW1 = X^T dZ1, db1
     FSI_TRY(gemm(h, ga(NI, NH, M, X, NI, 1, h->dZ1, NH, 0, grad + OFF_W1, NH)));
-    colsum_kernel<<<1, 256, 0, s>>>(B, NH, h->dZ1, grad + OFF_b1);
-    return check_launch("bias gradients");
+    return colsum(h, B, NH, h->dZ1, grad + OFF_b1);
 }
 
 fsi_status fsi_mlp_adam(fsi_mlp *h, float *params, const float *grad, float *m, float *v,

@@ -150,11 +150,13 @@ template <> struct DotAcc<float> {
 };
 
 // (index self_k, when in [k0, k0+cnt), stands for w itself: w . w)
+// (cond, when not null, is a device flag: the kernel does nothing when it is 0)
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) multi_dot_partial_kernel(
     int k0, int cnt, int64_t len4, const vec4<T> *V, int64_t vstride, const vec4<T> *w,
-    double *partial, int self_k)
+    double *partial, int self_k, const double *cond)
 {
+    if (cond && *cond == 0.0) return;
     using Acc = typename DotAcc<T>::type;
     __shared__ double red[kDotGroup][kRedThreads / 32];
     Acc acc[kDotGroup];
@@ -193,8 +195,10 @@ __global__ void __launch_bounds__(kRedThreads) multi_dot_partial_kernel(
 
 // out[k] (+)= sum_b partial[k][b] for k < cnt; one block per k, fixed tree.
 // mode 0: store, 1: add, 2: store sqrt (norm)
-__global__ void multi_dot_final_kernel(int cnt, const double *partial, double *out, int mode)
+__global__ void multi_dot_final_kernel(int cnt, const double *partial, double *out, int mode,
+                                       const double *cond = nullptr)
 {
+    if (cond && *cond == 0.0) return;
     __shared__ double red[kRedThreads];
     const int k = blockIdx.x;
     double v = 0.0;
@@ -216,12 +220,20 @@ __global__ void multi_dot_final_kernel(int cnt, const double *partial, double *o
 // w_i -= sum_k V_k[i] h[k], k < cnt: FP64 vectors in FP64; FP32 vectors
 // (the mixed mode's Krylov basis) with FP32 FMAs and h rounded to FP32.  One
 // 4-value record per thread and step, four basis vectors loaded ahead of their
-// FMAs (the FMA order per entry is k = 0, 1, 2, ...).
+// FMAs (the FMA order per entry is k = 0, 1, 2, ...).  With norm_partial the
+// same pass sums |w_new|^2 (like the dots: FP64, or exact FP32 products in
+// double-float) per CTA into norm_partial[block] (launch on the fixed
+// kRedGrid x kRedThreads grid); with cond, nothing happens when *cond is 0.
 constexpr int kMaxAxpy = 256;
 template <typename T>
-__global__ void multi_axpy_kernel(int cnt, int64_t len4, const vec4<T> *V, int64_t vstride,
-                                  const double *h, vec4<T> *w)
+__global__ void __launch_bounds__(kRedThreads)
+    multi_axpy_kernel(int cnt, int64_t len4, const vec4<T> *V, int64_t vstride, const double *h,
+                      vec4<T> *w, double *norm_partial, const double *cond)
 {
+    if (cond && *cond == 0.0) return;
+    using Acc = typename DotAcc<T>::type;
+    Acc nacc = Acc(0);
+    __shared__ double red[kRedThreads / 32];
     __shared__ T hs[kMaxAxpy];
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) hs[k] = (T)h[k];
     __syncthreads();
@@ -251,7 +263,44 @@ __global__ void multi_axpy_kernel(int cnt, int64_t len4, const vec4<T> *V, int64
             acc.w = fma_rn(-v.w, hk, acc.w);
         }
         w[i] = acc;
+        if (norm_partial) {
+            dot_acc(nacc, acc.x, acc.x);
+            dot_acc(nacc, acc.y, acc.y);
+            dot_acc(nacc, acc.z, acc.z);
+            dot_acc(nacc, acc.w, acc.w);
+        }
     }
+    if (norm_partial) {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        double v = dot_value(nacc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < kRedThreads / 32; ++q) t += red[q];
+            norm_partial[blockIdx.x] = t;
+        }
+    }
+}
+
+// Kahan's test on the device: flag = 1 when |h[0..j]|^2 > |w|^2 / 2 (w . w in
+// h[j + 1]), i.e. the classical Gram-Schmidt pass lost orthogonality and a
+// second pass is due; lanes sum in a fixed order
+__global__ void kahan_flag_kernel(int j, const double *h, double *flag)
+{
+    double v = 0.0;
+    for (int i = threadIdx.x; i <= j; i += 32) v += h[i] * h[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) *flag = (v <= 0.5 * h[j + 1]) ? 0.0 : 1.0;
+}
+
+__global__ void add_if_kernel(int n, const double *x, double *y, const double *cond)
+{
+    if (*cond == 0.0) return;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] += x[i];
 }
 
 // y = x / *den (0 when the norm vanished: lucky breakdown), in the vector's
@@ -739,7 +788,7 @@ fsi_status build_block_jacobi(fsi_mesh *mesh, const fsi_step_state *st, int prec
 // out[k] = V_k . w for k < cnt (with self_k: out[self_k] = w . w)
 template <typename T>
 fsi_status multi_dot(fsi_mesh *mesh, int cnt, const T *V, int64_t ld, const T *w, double *out,
-                     int mode, int self_k = -1)
+                     int mode, int self_k = -1, const double *cond = nullptr)
 {
     Work &W = mesh->newton->w;
     cudaStream_t s = mesh->stream;
@@ -747,20 +796,24 @@ fsi_status multi_dot(fsi_mesh *mesh, int cnt, const T *V, int64_t ld, const T *w
     for (int k0 = 0; k0 < cnt; k0 += kDotGroup) {
         const int c = cnt - k0 < kDotGroup ? cnt - k0 : kDotGroup;
         multi_dot_partial_kernel<T><<<kRedGrid, kRedThreads, 0, s>>>(
-            k0, c, len / 4, (const vec4<T> *)V, ld / 4, (const vec4<T> *)w, W.partial, self_k);
+            k0, c, len / 4, (const vec4<T> *)V, ld / 4, (const vec4<T> *)w, W.partial, self_k,
+            cond);
     }
     FSI_TRY(check_launch("multi-dot partial"));
-    multi_dot_final_kernel<<<cnt, kRedThreads, 0, s>>>(cnt, W.partial, out, mode);
+    multi_dot_final_kernel<<<cnt, kRedThreads, 0, s>>>(cnt, W.partial, out, mode, cond);
     return check_launch("multi-dot final");
 }
 
-// w -= V[:, :cnt] h (vectors of len = 4n entries, 16/32-byte aligned records)
+// w -= V[:, :cnt] h (vectors of len = 4n entries, 16/32-byte aligned records);
+// with norm_partial also the CTA partial sums of |w|^2 (fixed grid); with
+// cond only when the device flag is set
 template <typename T>
 void multi_axpy(cudaStream_t s, int cnt, int64_t len, const T *V, int64_t ld, const double *h,
-                T *w)
+                T *w, double *norm_partial = nullptr, const double *cond = nullptr)
 {
-    multi_axpy_kernel<T><<<grid1d(len / 4), 256, 0, s>>>(cnt, len / 4, (const vec4<T> *)V,
-                                                         ld / 4, h, (vec4<T> *)w);
+    multi_axpy_kernel<T><<<kRedGrid, kRedThreads, 0, s>>>(cnt, len / 4, (const vec4<T> *)V,
+                                                          ld / 4, h, (vec4<T> *)w, norm_partial,
+                                                          cond);
 }
 
 template <typename T> fsi_status norm2(fsi_mesh *mesh, const T *x, double *dev_out)
@@ -842,28 +895,30 @@ fsi_status gmres(fsi_mesh *mesh, const fsi_step_state *st, int restart, int max_
             // classical Gram-Schmidt, h = V^T w (and |w|^2 in the same pass), with
             // a second pass only when Kahan's criterion flags a loss of
             // orthogonality: |h|^2 > |w|^2 / 2, i.e. |w - V h| < |w| / sqrt(2)
+            // Kahan's test runs on the device and the second pass (when it is
+            // due) is launched conditionally, so the iteration needs one host
+            // synchronisation, at its end; |w|^2 of the orthogonalised vector is
+            // summed by the update pass itself
+            double *flag = W.h2 + restart + 1;
+            double *npart = W.partial + (int64_t)(restart + 1) * kRedGrid;
             FSI_TRY(multi_dot<T>(mesh, j + 2, V, ld, w, W.hcol, 0, j + 1));
-            FSI_CUDA(cudaMemcpyAsync(W.hhost, W.hcol, (j + 2) * sizeof(double),
-                                     cudaMemcpyDeviceToHost, s),
-                     "memcpy");
-            FSI_CUDA(cudaStreamSynchronize(s), "GMRES sync");
-            double hh = 0.0;
-            for (int i = 0; i <= j; ++i) hh += W.hhost[i] * W.hhost[i];
-            const bool reorth = !(hh <= 0.5 * W.hhost[j + 1]);
-            multi_axpy<T>(s, j + 1, len, V, ld, W.hcol, w);
-            if (reorth) {
-                FSI_TRY(multi_dot<T>(mesh, j + 1, V, ld, w, W.h2, 0));
-                multi_axpy<T>(s, j + 1, len, V, ld, W.h2, w);
-                add_kernel<double><<<1, 64, 0, s>>>(j + 1, W.h2, W.hcol);
-                ++W.reorth;
-            }
-            FSI_TRY(norm2<T>(mesh, w, W.hcol + j + 1));
+            kahan_flag_kernel<<<1, 32, 0, s>>>(j, W.hcol, flag);
+            multi_axpy<T>(s, j + 1, len, V, ld, W.hcol, w, npart);
+            FSI_TRY(multi_dot<T>(mesh, j + 1, V, ld, w, W.h2, 0, -1, flag));
+            multi_axpy<T>(s, j + 1, len, V, ld, W.h2, w, npart, flag);
+            add_if_kernel<<<1, 64, 0, s>>>(j + 1, W.h2, W.hcol, flag);
+            multi_dot_final_kernel<<<1, kRedThreads, 0, s>>>(1, npart, W.hcol + j + 1, 2);
+            FSI_TRY(check_launch("Gram-Schmidt"));
             scale_by_inv_kernel<T><<<grid1d(len), 256, 0, s>>>(len, W.hcol + j + 1, w,
                                                               V + (int64_t)(j + 1) * ld);
             FSI_CUDA(cudaMemcpyAsync(W.hhost, W.hcol, (j + 2) * sizeof(double),
                                      cudaMemcpyDeviceToHost, s),
                      "memcpy");
+            FSI_CUDA(cudaMemcpyAsync(W.hhost + j + 2, flag, sizeof(double),
+                                     cudaMemcpyDeviceToHost, s),
+                     "memcpy");
             FSI_CUDA(cudaStreamSynchronize(s), "GMRES sync");
+            if (W.hhost[j + 2] != 0.0) ++W.reorth;
             ++its;
             double *h = &H[(size_t)j * (restart + 1)];
             for (int i = 0; i <= j + 1; ++i) h[i] = W.hhost[i];
@@ -1069,6 +1124,76 @@ fsi_status fsi_newton_step(fsi_mesh *mesh, const fsi_newton_opts *opts, const fs
     report->seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return stt;
+}
+
+fsi_status fsi_measure_blas1(int device, fsi_prec prec, int64_t len, int nvec, int reps,
+                             double *dot_seconds, double *axpy_seconds)
+{
+    if (!dot_seconds || !axpy_seconds) return set_error(FSI_ERR_ARG, "NULL output");
+    if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
+    if (len < 4 || len % 4 != 0 || nvec < 1 || nvec > kMaxAxpy || reps < 1)
+        return set_error(FSI_ERR_ARG, "fsi_measure_blas1: bad sizes");
+    FSI_DEVICE(device);
+    const size_t esz = prec == FSI_F64 ? sizeof(double) : sizeof(float);
+    void *V = nullptr, *w = nullptr;
+    double *partial = nullptr, *h = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    fsi_status st = check_cuda(cudaMalloc(&V, (size_t)nvec * len * esz), "buffers");
+    if (st == FSI_OK) st = check_cuda(cudaMalloc(&w, (size_t)len * esz), "buffers");
+    if (st == FSI_OK)
+        st = check_cuda(cudaMalloc(&partial, (size_t)(nvec + 1) * kRedGrid * sizeof(double)),
+                        "buffers");
+    if (st == FSI_OK) st = check_cuda(cudaMalloc(&h, (size_t)(nvec + 1) * sizeof(double)), "buffers");
+    if (st == FSI_OK) st = check_cuda(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
+    if (st == FSI_OK) st = check_cuda(cudaEventCreate(&e0), "event");
+    if (st == FSI_OK) st = check_cuda(cudaEventCreate(&e1), "event");
+    if (st == FSI_OK) st = check_cuda(cudaMemsetAsync(V, 0, (size_t)nvec * len * esz, s), "memset");
+    if (st == FSI_OK) st = check_cuda(cudaMemsetAsync(w, 0, (size_t)len * esz, s), "memset");
+    if (st == FSI_OK) st = check_cuda(cudaMemsetAsync(h, 0, (size_t)(nvec + 1) * sizeof(double), s),
+                                      "memset");
+    auto dots = [&]() {
+        for (int k0 = 0; k0 < nvec; k0 += kDotGroup) {
+            const int c = nvec - k0 < kDotGroup ? nvec - k0 : kDotGroup;
+            if (prec == FSI_F64)
+                multi_dot_partial_kernel<double><<<kRedGrid, kRedThreads, 0, s>>>(
+                    k0, c, len / 4, (const vec4<double> *)V, len / 4, (const vec4<double> *)w,
+                    partial, -1, nullptr);
+            else
+                multi_dot_partial_kernel<float><<<kRedGrid, kRedThreads, 0, s>>>(
+                    k0, c, len / 4, (const vec4<float> *)V, len / 4, (const vec4<float> *)w,
+                    partial, -1, nullptr);
+        }
+        multi_dot_final_kernel<<<nvec, kRedThreads, 0, s>>>(nvec, partial, h, 0);
+    };
+    auto axpy = [&]() {
+        if (prec == FSI_F64)
+            multi_axpy<double>(s, nvec, len, (const double *)V, len, h, (double *)w, partial);
+        else
+            multi_axpy<float>(s, nvec, len, (const float *)V, len, h, (float *)w, partial);
+    };
+    float ms = 0.f;
+    for (int which = 0; st == FSI_OK && which < 2; ++which) {
+        auto run = [&]() {
+            if (which == 0) dots();
+            else axpy();
+        };
+        run();
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; ++r) run();
+        cudaEventRecord(e1, s);
+        st = check_cuda(cudaEventSynchronize(e1), "BLAS-1 kernels");
+        if (st == FSI_OK) st = check_cuda(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+        if (st == FSI_OK) (which == 0 ? *dot_seconds : *axpy_seconds) = 1e-3 * ms / reps;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(V);
+    cudaFree(w);
+    cudaFree(partial);
+    cudaFree(h);
+    return st;
 }
 
 }  // extern "C"
