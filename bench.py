@@ -52,9 +52,14 @@ SEED = 2026
 # fused 2, locate 1 + scan 3 + scatter 1 + sort 1, interp 1, spread 2).
 LAUNCHES_PER_STEP = 12
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused native FP64
-# residual + Jacobian launch (brick + gather kernels) on the 64^3 workload,
-# from an ncu capture (None until captured for the current kernels)
-TRAFFIC_FUSED_F64_64 = None
+# residual + Jacobian launch on the 64^3 workload (4x4x4 bricks, 128
+# threads: brick 26.43 + 0.20 MB, gather 32.79 + 0.04 MB), from one ncu
+# capture with a cache flush between the two kernels
+TRAFFIC_FUSED_F64_64 = {(4, 4, 4, 128): 26_429_952 + 204_800 + 32_786_176 + 39_680}
+# FP64 operations the fused FP64 brick kernel executes per element (ncu,
+# same capture: DFMA 1,712 (x2), DMUL 1,368, DADD 1,070): context for the
+# roofline, whose achieved rate counts the oracle's operations
+KERNEL_FP64_FLOPS_PER_ELEM = 2 * 1712 + 1368 + 1070
 
 
 def dist_env():
@@ -557,7 +562,8 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
     achieved = flops_elem["fused"] * E / (vms_ms * 1e-3)
     # DRAM bytes of one fused FP64 launch (brick + gather kernels), from an
     # ncu capture of this workload; only meaningful for the 64^3 grid
-    traffic = TRAFFIC_FUSED_F64_64 if N == N_GRID else None
+    vms_sched = tuple(schedule["vms_f64"]["brick"]) + (schedule["vms_f64"]["threads"],)
+    traffic = TRAFFIC_FUSED_F64_64.get(vms_sched) if N == N_GRID else None
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
 
@@ -656,7 +662,12 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
                                      "the kernel uses the tensor-product butterflies, so the "
                                      "kernel executes fewer operations than this count",
                      "peak_source": "FP64 FMA rate probed in this run (fsi_measure_fma_peak; "
-                                    "MEASURED_PEAKS.json has no FP64 figure)"},
+                                    "MEASURED_PEAKS.json has no FP64 figure)",
+                     "kernel_flops_per_element": KERNEL_FP64_FLOPS_PER_ELEM,
+                     "kernel_flop_frac": KERNEL_FP64_FLOPS_PER_ELEM * E / (vms_ms * 1e-3) / fma64,
+                     "kernel_flops_source": "ncu FP64 instruction counts of the fused brick kernel "
+                                            "at 64^3 (DFMA x 2 + DMUL + DADD); its FP64 pipe is "
+                                            "85 % active"},
         "schedule": schedule,
         "step_df64": {
             "ms": native[0], "gdof_s": gdofs(native[0]),
@@ -823,7 +834,9 @@ def newton_section(args, dev, stream):
     mixed solver from the learned guess."""
     import torch
     import paper_2601_08266_gb300 as fsi
-    solve = dict(restart=50, max_newton=10, max_krylov=4000, newton_rtol=1e-8, krylov_rtol=1e-3)
+    # krylov_rtol is the floor of the target-aware forcing (see fsi_newton_step)
+    solve = dict(restart=50, max_newton=10, max_krylov=4000, newton_rtol=1e-8,
+                 krylov_rtol=args.krylov_floor)
     wanted = set(args.newton_variants.split(","))
     learned = "mixed_learned" in wanted
     zeros = torch.zeros(112, dtype=torch.float32, device=dev)
@@ -908,7 +921,7 @@ def newton_section(args, dev, stream):
         if guess_kind == "learned":
             guess = fsi.fsi_mlp_guess(h, ch.mesh, P, im.float().contiguous(),
                                       isd.float().contiguous(), om.contiguous(), osd.contiguous(),
-                                      st, ch.yn, ch.d1, ch.d2, 1, work,
+                                      st, ch.yn, ch.d1, ch.d2, 0, work,
                                       judge_prec=fsi.FSI_DF64)
         code, rep = fsi.fsi_newton_step(ch.mesh, st, mixed=mixed, r_ref=r_ref or 0.0,
                                         check=False, precond=pc,
@@ -924,8 +937,9 @@ def newton_section(args, dev, stream):
                      "r_final_over_ref": rep["r_final"] / r_ref,
                      "converged": bool(rep["converged"]), "status": code}
         if guess is not None:
-            out[name]["predictor"] = {k2: guess[k2] for k2 in ("r_fallback", "r_learned",
-                                                               "r_combined", "used")}
+            out[name]["predictor"] = {k2: guess[k2] for k2 in (
+                "r_fallback", "r_learned", "r_combined", "used", "c_extrapolant", "a_velocity",
+                "b_pressure")}
     if {"fp64", "mixed"} <= wanted:
         out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
     if {"fp64", "mixed_learned"} <= wanted:
@@ -934,6 +948,9 @@ def newton_section(args, dev, stream):
     if {"mixed", "mixed_learned"} <= wanted:
         out["speedup_learned_vs_extrapolated"] = (out["mixed"]["seconds"] /
                                                   out["mixed_learned"]["seconds"])
+    if {"mixed_zero_guess", "mixed_learned"} <= wanted:
+        out["speedup_learned_vs_zero"] = (out["mixed_zero_guess"]["seconds"] /
+                                          out["mixed_learned"]["seconds"])
     if h is not None:
         h.close()
     # the Krylov BLAS-1 kernels on vectors of this grid's size (FP32, as in the
@@ -1495,6 +1512,8 @@ def main():
     ap.add_argument("--newton-grid", type=int, default=128)
     ap.add_argument("--newton-points", type=int, default=1_000_000)
     ap.add_argument("--newton-warm", type=int, default=3)
+    ap.add_argument("--krylov-floor", type=float, default=1e-4,
+                    help="floor of the Newton solver's target-aware inner tolerance")
     ap.add_argument("--train-grid", type=int, default=64)
     ap.add_argument("--train-points", type=int, default=200_000)
     ap.add_argument("--train-runs", type=int, default=2)

@@ -671,24 +671,32 @@ fsi_status fsi_mlp_predict(fsi_mlp *mlp, fsi_mesh *mesh, const float *params,
                            const float *out_std, const double *Vn, const double *y,
                            const double *d1, const double *d2, double *y0);
 
-/* The FP64 residual judges the network.  Builds the fallback predictor
- * y_fb (fallback 0: y_n, the zero increment; 1: y_n + e) and the network's
- * predictor y_ml; Dirichlet rows (st->mask) of both take st->yD.  With
- * d = y_ml - y_fb split into its velocity part d_v and pressure part d_p it
- * evaluates the coupled FP64 residual (fsi_coupled_residual) of y_fb,
- * y_fb + d_v, y_fb + d_p, y_ml and y_c = y_fb + a d_v + b d_p, where (a, b)
- * minimise |R(y_fb) + a (R(y_fb+d_v) - R(y_fb)) + b (R(y_fb+d_p) - R(y_fb))|
- * (R is close to linear in y over a predictor's error), and leaves in st->y
- * whichever of y_fb, y_ml, y_c has the smallest residual norm.  judge_prec
- * (FSI_F64 or FSI_DF64) is the residual's arithmetic (fsi_coupled_residual).
- * work: caller-owned FP64 device array [5][n][4].  yn [n][4] is y_n (must not
- * alias st->y).  Synchronises.                                             */
+/* The FP64 residual judges the network.  With e = 2 d1 - d2 (the linear
+ * extrapolant of the increment) and c = y_ml - y_n - e the network's
+ * correction (fsi_mlp_predict), split into its velocity part c_v and
+ * pressure part c_p, the predictor is the best member of the family
+ *     y = y_fb + alpha e + beta c_v + gamma c_p
+ * around the fallback y_fb (fallback 0: y_n, the zero increment; 1: y_n + e),
+ * all Dirichlet rows (st->mask) held at st->yD: the coefficients minimise
+ * |R(y_fb) + J (alpha e + beta c_v + gamma c_p)|, R the coupled residual
+ * (fsi_coupled_residual) of y_fb in judge_prec and J its Jacobian at y_fb
+ * applied in FP32 (fsi_coupled_jacobian_apply; R is close to linear in y
+ * over a predictor's error), by the 3 x 3 normal equations in FP64 (a
+ * direction that adds nothing is dropped).  The family holds both
+ * fallbacks (alpha = 0 or 1 from y_n) and the network's own predictor, so the
+ * fit is at least as good as each of them in the linear model.  The
+ * candidate's residual is then evaluated in judge_prec, and st->y keeps the
+ * candidate if its residual norm is below the fallback's, else y_fb.  Cost:
+ * two residuals, three FP32 Jacobian applies and the network.  judge_prec:
+ * FSI_F64 or FSI_DF64.  work: caller-owned FP64 device array [5][n][4].
+ * yn [n][4] is y_n (must not alias st->y).  Synchronises; a tensor-core wait
+ * that ran out in this or an earlier call of the handle is FSI_ERR_TIMEOUT. */
 typedef struct {
-    double r_fallback;  /* ||R(y_fb)||_2                     */
-    double r_learned;   /* ||R(y_ml)||_2                     */
-    double r_combined;  /* ||R(y_c)||_2                      */
-    double a_velocity, b_pressure;
-    int32_t used;       /* 0 fallback, 1 network, 2 combined */
+    double r_fallback;   /* ||R(y_fb)||_2, judge_prec                               */
+    double r_learned;    /* the linear model's ||R|| at the network's own predictor */
+    double r_combined;   /* ||R(y_c)||_2 of the fitted candidate, judge_prec         */
+    double a_velocity, b_pressure, c_extrapolant;  /* beta, gamma, alpha            */
+    int32_t used;        /* 0 fallback, 2 fitted candidate                           */
     int32_t reserved;
 } fsi_guess_report;
 

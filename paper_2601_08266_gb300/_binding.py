@@ -72,8 +72,8 @@ class fsi_newton_report(ctypes.Structure):
 class fsi_guess_report(ctypes.Structure):
     _fields_ = [("r_fallback", ctypes.c_double), ("r_learned", ctypes.c_double),
                 ("r_combined", ctypes.c_double), ("a_velocity", ctypes.c_double),
-                ("b_pressure", ctypes.c_double), ("used", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("b_pressure", ctypes.c_double), ("c_extrapolant", ctypes.c_double),
+                ("used", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class fsi_batch_item(ctypes.Structure):

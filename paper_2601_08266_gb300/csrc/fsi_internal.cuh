@@ -206,6 +206,11 @@ fsi_status mlp_predict_tc(cudaStream_t s, int device, const fsi_grid &g, int64_t
                           const double *y, const double *d1, const double *d2, double *y0,
                           void *packed, int *dev_err);
 
+// the coupled Jacobian (newton.cu) at st->y applied to k FP32 vectors after
+// one linearisation; used by the learned guess's fitted predictor
+fsi_status coupled_jacobian_f32(fsi_mesh *mesh, const fsi_step_state *st, int k,
+                                const float *const *x, float *const *Jx);
+
 // VMS operators (vms.cu)
 fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,
                         const void *f, void *R);

@@ -9,6 +9,7 @@
 // pre-activation, the ReLU mask of the backward pass).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -203,65 +204,88 @@ __global__ void apply_dirichlet_kernel(int64_t n4, const uint8_t *mask, const do
         if (mask[q]) y[q] = yD[q];
 }
 
-// y = yf + a (ml - yf) on velocity slots + b (ml - yf) on the pressure slot
-__global__ void combine_kernel(int64_t n4, const double *yf, const double *ml, double a, double b,
-                               double *y)
+// One search direction of the fitted predictor, in FP32 (which: 0 the
+// extrapolant e = 2 d1 - d2; 1 the network's velocity correction c_v; 2 its
+// pressure correction c_p, c = ml - yn - e); zero on Dirichlet rows
+__global__ void direction_kernel(int64_t n4, int which, const double *ml, const double *yn,
+                                 const double *d1, const double *d2, const uint8_t *mask,
+                                 float *out)
 {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const double c = (q & 3) == 3 ? b : a;
-        y[q] = yf[q] + c * (ml[q] - yf[q]);
+        const double e = 2.0 * d1[q] - d2[q];
+        const bool pslot = (q & 3) == 3;
+        double v = which == 0 ? e : ((which == 1) != pslot ? ml[q] - yn[q] - e : 0.0);
+        if (mask && mask[q]) v = 0.0;
+        out[q] = (float)v;
     }
 }
 
-// per-block partial sums of the 6 pairwise dot products of x, y, z (FP64)
-__global__ void dots3_kernel(int64_t n, const double *x, const double *y, const double *z,
-                             double *partial)
+// y = yfb + a e + b c_v + c c_p (Dirichlet rows = yD)
+__global__ void fitted_kernel(int64_t n4, const double *yfb, const double *ml, const double *yn,
+                              const double *d1, const double *d2, const uint8_t *mask,
+                              const double *yD, double a, double b, double c, double *y)
 {
-    __shared__ double red[6][256];
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const double e = 2.0 * d1[q] - d2[q];
+        const double corr = ml[q] - yn[q] - e;
+        y[q] = (mask && mask[q]) ? yD[q] : yfb[q] + a * e + ((q & 3) == 3 ? c : b) * corr;
+    }
+}
+
+// per-block partial sums of the normal equations of the fit: G_ij = J_i . J_j
+// (6 values) and r_i = J_i . R (3 values), FP32 products summed in FP64
+constexpr int kFitBlocks = 96;
+__global__ void fit_dots_kernel(int64_t n4, const float *J0, const float *J1, const float *J2,
+                                const double *R, double *partial)
+{
+    __shared__ double red[9][256];
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double a = x[i], b = y[i], c = z[i];
+        const double a = J0[i], b = J1[i], c = J2[i], r = R[i];
         acc[0] += a * a;
         acc[1] += a * b;
         acc[2] += a * c;
         acc[3] += b * b;
         acc[4] += b * c;
         acc[5] += c * c;
+        acc[6] += a * r;
+        acc[7] += b * r;
+        acc[8] += c * r;
     }
-    for (int k = 0; k < 6; ++k) red[k][threadIdx.x] = acc[k];
+    for (int k = 0; k < 9; ++k) red[k][threadIdx.x] = acc[k];
     __syncthreads();
     for (int st = 128; st > 0; st >>= 1) {
         if (threadIdx.x < st)
-            for (int k = 0; k < 6; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
+            for (int k = 0; k < 9; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
         __syncthreads();
     }
-    if (threadIdx.x < 6) partial[6 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+    if (threadIdx.x < 9) partial[9 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// per-block partial sums of |x|^2 (FP64)
+__global__ void sumsq_kernel(int64_t n, const double *x, double *partial)
+{
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc += x[i] * x[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
 int blocks(int64_t n, int threads = 256, int cap = sm_count() * 16)
 {
     int64_t b = (n + threads - 1) / threads;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
-}
-
-// The 6 pairwise dot products of three device vectors (fixed grid: deterministic).
-fsi_status dots3(cudaStream_t s, int64_t n, const double *x, const double *y, const double *z,
-                 double *partial, double out[6])
-{
-    const int nb = 128;  // partial holds 1024 doubles >= 6 * nb
-    dots3_kernel<<<nb, 256, 0, s>>>(n, x, y, z, partial);
-    FSI_TRY(check_launch("dots kernel"));
-    double host[6 * nb];
-    FSI_CUDA(cudaMemcpyAsync(host, partial, sizeof host, cudaMemcpyDeviceToHost, s), "memcpy");
-    FSI_CUDA(cudaStreamSynchronize(s), "sync");
-    for (int k = 0; k < 6; ++k) {
-        double acc = 0.0;
-        for (int b = 0; b < nb; ++b) acc += host[6 * b + k];
-        out[k] = acc;
-    }
-    return FSI_OK;
 }
 
 // db = column sums of dZ [M][N] (the bias gradient), through the split-K
@@ -469,8 +493,11 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
     FSI_DEVICE(mesh->device);
     cudaStream_t s = mesh->stream;
     const int64_t n4 = 4 * mesh->n_nodes;
-    double *ml = work, *trial = work + n4, *R0 = work + 2 * n4, *Rv = work + 3 * n4,
-           *Rp = work + 4 * n4;
+    // work: [0] the network's predictor, [1] R(y_fb), [2..4] FP32: the three
+    // directions and their J d_i; once the fit is done [2] holds the fitted
+    // candidate and [3] its residual
+    double *ml = work, *Rfb = work + n4, *cand = work + 2 * n4, *Rc = work + 3 * n4;
+    float *dir = (float *)(work + 2 * n4), *Jd = dir + 3 * n4;
     // the fallback predictor (in st->y) and the network's predictor (in ml)
     fallback_kernel<<<blocks(n4), 256, 0, s>>>(n4, fallback, yn, d1, d2, st->y);
     FSI_TRY(check_launch("fallback kernel"));
@@ -478,60 +505,96 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
                             d2, ml));
     if (st->mask) {
         apply_dirichlet_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->mask, st->yD, st->y);
-        apply_dirichlet_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->mask, st->yD, ml);
         FSI_TRY(check_launch("dirichlet kernel"));
     }
-    fsi_step_state tmp = *st;
-    auto residual = [&](const double *y, double *R) -> fsi_status {
-        tmp.y = const_cast<double *>(y);
-        return fsi_coupled_residual(mesh, judge_prec, &tmp, R);
-    };
-    // residuals of y_fb, y_fb + d_v and y_fb + d_p (d = ml - y_fb split into
-    // its velocity and pressure slots)
-    FSI_TRY(residual(st->y, R0));
-    combine_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->y, ml, 1.0, 0.0, trial);
-    FSI_TRY(residual(trial, Rv));
-    combine_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->y, ml, 0.0, 1.0, trial);
-    FSI_TRY(residual(trial, Rp));
-    FSI_TRY(check_launch("combine kernel"));
-    double G[6];  // <R0,R0> <R0,Rv> <R0,Rp> <Rv,Rv> <Rv,Rp> <Rp,Rp>
-    FSI_TRY(dots3(s, n4, R0, Rv, Rp, h->loss_partial, G));
-    const double r0 = sqrt(G[0]);
-    // Av = Rv - R0, Ap = Rp - R0: minimise |R0 + a Av + b Ap|^2 (R is close to
-    // linear in y over a predictor's error)
-    const double vv = G[3] - 2 * G[1] + G[0], pp = G[5] - 2 * G[2] + G[0];
-    const double vp = G[4] - G[1] - G[2] + G[0];
-    const double rv = G[1] - G[0], rp = G[2] - G[0];
-    double a = 0.0, b = 0.0;
-    const double det = vv * pp - vp * vp;
-    if (det > 1e-14 * (vv * pp) && vv > 0 && pp > 0) {
-        a = (-rv * pp + rp * vp) / det;
-        b = (-rp * vv + rv * vp) / det;
-    } else if (vv > 0) {
-        a = -rv / vv;
+    // the fallback's residual, and J at y_fb applied to e, c_v, c_p (FP32,
+    // one linearisation)
+    FSI_TRY(fsi_coupled_residual(mesh, judge_prec, st, Rfb));
+    for (int i = 0; i < 3; ++i)
+        direction_kernel<<<blocks(n4), 256, 0, s>>>(n4, i, ml, yn, d1, d2, st->mask, dir + i * n4);
+    FSI_TRY(check_launch("direction kernel"));
+    {
+        const float *xs[3] = {dir, dir + n4, dir + 2 * n4};
+        float *js[3] = {Jd, Jd + n4, Jd + 2 * n4};
+        FSI_TRY(coupled_jacobian_f32(mesh, st, 3, xs, js));
     }
-    // pure network predictor (a = b = 1) and the combination (a, b)
-    FSI_TRY(residual(ml, Rv));
-    combine_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->y, ml, a, b, trial);
-    FSI_TRY(residual(trial, Rp));
-    double G2[6];
-    FSI_TRY(dots3(s, n4, R0, Rv, Rp, h->loss_partial, G2));
-    const double r_ml = sqrt(G2[3]), r_comb = sqrt(G2[5]);
-    rep->r_fallback = r0;
-    rep->r_learned = r_ml;
-    rep->r_combined = r_comb;
-    rep->a_velocity = a;
-    rep->b_pressure = b;
-    int use = 0;
-    double best = r0;
-    if (std::isfinite(r_ml) && r_ml < best) { use = 1; best = r_ml; }
-    if (std::isfinite(r_comb) && r_comb < best) { use = 2; best = r_comb; }
-    rep->used = use;
-    if (use == 1)
-        FSI_CUDA(cudaMemcpyAsync(st->y, ml, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s),
-                 "memcpy");
-    else if (use == 2)
-        FSI_CUDA(cudaMemcpyAsync(st->y, trial, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s),
+    // normal equations G x = -r of min |R_fb + sum_i x_i J d_i|
+    fit_dots_kernel<<<kFitBlocks, 256, 0, s>>>(n4, Jd, Jd + n4, Jd + 2 * n4, Rfb,
+                                              h->loss_partial);
+    sumsq_kernel<<<kFitBlocks, 256, 0, s>>>(n4, Rfb, h->loss_partial + 9 * kFitBlocks);
+    FSI_TRY(check_launch("fit dots"));
+    double hp[10 * kFitBlocks];
+    FSI_CUDA(cudaMemcpyAsync(hp, h->loss_partial, sizeof hp, cudaMemcpyDeviceToHost, s), "memcpy");
+    FSI_CUDA(cudaStreamSynchronize(s), "sync");
+    double q[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, rr = 0.0;
+    for (int b = 0; b < kFitBlocks; ++b) {
+        for (int k = 0; k < 9; ++k) q[k] += hp[9 * b + k];
+        rr += hp[9 * kFitBlocks + b];
+    }
+    const double r_fb = std::sqrt(rr);
+    double G[3][3] = {{q[0], q[1], q[2]}, {q[1], q[3], q[4]}, {q[2], q[4], q[5]}};
+    double r[3] = {q[6], q[7], q[8]};
+    // Cholesky with pivot tolerance: a direction whose Schur pivot is below
+    // 1e-12 of its own norm adds nothing and keeps coefficient 0
+    double x[3] = {0.0, 0.0, 0.0};
+    {
+        bool use[3];
+        double L[3][3] = {{0}};
+        for (int i = 0; i < 3; ++i) {
+            double d = G[i][i];
+            for (int k = 0; k < i; ++k) d -= L[i][k] * L[i][k];
+            use[i] = G[i][i] > 0.0 && d > 1e-12 * G[i][i];
+            L[i][i] = use[i] ? std::sqrt(d) : 0.0;
+            for (int j = i + 1; j < 3; ++j) {
+                double t = G[j][i];
+                for (int k = 0; k < i; ++k) t -= L[j][k] * L[i][k];
+                L[j][i] = use[i] ? t / L[i][i] : 0.0;
+            }
+        }
+        double z[3];
+        for (int i = 0; i < 3; ++i) {
+            double t = -r[i];
+            for (int k = 0; k < i; ++k) t -= L[i][k] * z[k];
+            z[i] = use[i] ? t / L[i][i] : 0.0;
+        }
+        for (int i = 2; i >= 0; --i) {
+            double t = z[i];
+            for (int k = i + 1; k < 3; ++k) t -= L[k][i] * x[k];
+            x[i] = use[i] ? t / L[i][i] : 0.0;
+        }
+    }
+    // the linear model's residual at the network's own predictor y_n + e + c
+    {
+        const double xm[3] = {fallback == 1 ? 0.0 : 1.0, 1.0, 1.0};
+        double v = rr;
+        for (int i = 0; i < 3; ++i) {
+            v += 2.0 * xm[i] * r[i];
+            for (int j = 0; j < 3; ++j) v += xm[i] * G[i][j] * xm[j];
+        }
+        rep->r_learned = std::sqrt(std::max(v, 0.0));
+    }
+    rep->r_fallback = r_fb;
+    rep->c_extrapolant = x[0];
+    rep->a_velocity = x[1];
+    rep->b_pressure = x[2];
+    // the candidate, judged by its own residual in judge_prec
+    fitted_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->y, ml, yn, d1, d2, st->mask, st->yD, x[0],
+                                            x[1], x[2], cand);
+    FSI_TRY(check_launch("fitted kernel"));
+    fsi_step_state tmp = *st;
+    tmp.y = cand;
+    FSI_TRY(fsi_coupled_residual(mesh, judge_prec, &tmp, Rc));
+    sumsq_kernel<<<kFitBlocks, 256, 0, s>>>(n4, Rc, h->loss_partial);
+    FSI_TRY(check_launch("norm kernel"));
+    double hn[kFitBlocks];
+    FSI_CUDA(cudaMemcpyAsync(hn, h->loss_partial, sizeof hn, cudaMemcpyDeviceToHost, s), "memcpy");
+    FSI_CUDA(cudaStreamSynchronize(s), "sync");
+    double rc = 0.0;
+    for (int b = 0; b < kFitBlocks; ++b) rc += hn[b];
+    rep->r_combined = std::sqrt(rc);
+    rep->used = std::isfinite(rep->r_combined) && rep->r_combined < r_fb ? 2 : 0;
+    if (rep->used == 2)
+        FSI_CUDA(cudaMemcpyAsync(st->y, cand, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s),
                  "memcpy");
     FSI_CUDA(cudaStreamSynchronize(s), "sync");
     return take_tc_error(h);

@@ -995,11 +995,19 @@ fsi_status newton_impl(fsi_mesh *mesh, const fsi_newton_opts *o, const fsi_step_
             rep->precond_builds++;
         }
         neg_cast_kernel<T><<<grid1d(len), 256, 0, s>>>(len, W.R, (T *)W.b);
-        // inexact Newton without oversolving: the linear solve need not go
-        // below what the absolute target asks of this iteration
+        // inexact Newton without oversolving: plan the fewest iterations n
+        // whose linear reductions, each no tighter than the floor
+        // krylov_rtol, reach half the absolute target from r, and ask this
+        // solve for the n-th root of that reduction (n = 1: 0.5 target / r)
+        const double need = 0.5 * target / r;
         double eta = o->krylov_rtol;
-        const double loose = 0.5 * target / r;
-        if (loose > eta) eta = loose < 0.5 ? loose : 0.5;
+        if (need >= eta) {
+            eta = need < 0.5 ? need : 0.5;
+        } else if (o->krylov_rtol < 0.5) {
+            const int nn = (int)std::ceil(std::log(need) / std::log(o->krylov_rtol) - 1e-9);
+            const double root = std::pow(need, 1.0 / std::max(nn, 1));
+            if (root > eta) eta = root;
+        }
         int its = 0;
         FSI_TRY(gmres<T>(mesh, st, o->restart, o->max_krylov, eta, &its));
         rep->krylov_iters += its;
@@ -1019,6 +1027,24 @@ fsi_status newton_impl(fsi_mesh *mesh, const fsi_newton_opts *o, const fsi_step_
                          target, it);
     return FSI_OK;
 }
+
+}  // namespace
+
+// one linearisation at st->y (stage values, and for a hyperelastic body its
+// stage values through the coupled residual), then J x_i for k FP32 vectors
+fsi_status coupled_jacobian_f32(fsi_mesh *mesh, const fsi_step_state *st, int k,
+                                const float *const *x, float *const *Jx)
+{
+    FSI_TRY(ensure_work(mesh, st->m, 1));
+    Work &W = mesh->newton->w;
+    if (st->m > 0 && st->body) FSI_TRY(coupled_residual_impl(mesh, st, W.R));
+    else FSI_TRY(fsi_stage(mesh, FSI_F64, st->y, st->Vn, st->An, st->s, W.U, W.A));
+    FSI_TRY(prepare_linearisation<float>(mesh, st));
+    for (int i = 0; i < k; ++i) FSI_TRY(coupled_jacobian_impl<float>(mesh, st, x[i], Jx[i]));
+    return FSI_OK;
+}
+
+namespace {
 
 fsi_status validate_state(const fsi_mesh *mesh, const fsi_step_state *st)
 {

@@ -183,8 +183,10 @@ def run_series(fsi, N, steps, dt=0.01, period=0.12, learn=None, seed=0):
             rec["X"] = Xf.cpu().numpy()
         # same absolute target with or without the network: the fallback's residual
         r_ref = rec["guess"]["r_fallback"] if "guess" in rec else 0.0
+        # target-aware forcing with a floor of 1e-4: a start with a smaller
+        # residual may meet the same absolute target in fewer Newton iterations
         code, rep = fsi.fsi_newton_step(mesh, st, mixed=True, restart=50, max_newton=8,
-                                        max_krylov=3000, newton_rtol=1e-8, krylov_rtol=1e-3,
+                                        max_krylov=3000, newton_rtol=1e-8, krylov_rtol=1e-4,
                                         r_ref=r_ref)
         rec["rep"] = rep
         d_new = y - yn
@@ -201,8 +203,11 @@ def run_series(fsi, N, steps, dt=0.01, period=0.12, learn=None, seed=0):
 def test_learned_guess_end_to_end(fsi, capsys):
     """Train on GPU-generated steps of a pulsatile channel (interior rows, after
     the start-up transient), then predict the Newton predictor on a run with
-    other leaflets.  The FP64 residual judges each step's predictor; the test
-    records what the network gains over the extrapolated fallback."""
+    other leaflets.  The FP64 residual judges each step's predictor (the fit
+    of the extrapolant and the network's corrections, kept only when its
+    residual is below the fallback's); over the periodic steps the learned
+    guess must take fewer Newton iterations in total than the extrapolated
+    fallback alone (the same steps, the same absolute target)."""
     import torch
     N, skip = 14, 5
     recs = run_series(fsi, N, steps=26)
@@ -247,17 +252,25 @@ def test_learned_guess_end_to_end(fsi, capsys):
             for r in run_series(fsi, N, steps=16, seed=1)}
     periodic = [rw for rw in rows if rw[0] >= skip + 1]
     wins = sum(1 for rw in periodic if rw[4] != 0)
-    gain = np.median([rw[1] / min(rw[1], rw[2], rw[3]) for rw in periodic])
+    gain = np.median([rw[1] / min(rw[1], rw[3]) for rw in periodic])
+    newton_l = sum(rw[6] for rw in periodic)
+    newton_f = sum(base[rw[0]][1] for rw in periodic)
+    krylov_l = sum(rw[5] for rw in periodic)
+    krylov_f = sum(base[rw[0]][0] for rw in periodic)
     with capsys.disabled():
         print("\nloss", losses)
         print("(step, r_fallback, r_network, r_combined, used, krylov, newton | fallback-only krylov, newton)")
         for rw in rows:
             print("  ", rw, "|", base[rw[0]][:2])
-        print(f"network or combination kept in {wins} of {len(periodic)} periodic steps; "
-              f"median residual reduction of the predictor x{gain:.2f}")
-    for rw in rows:   # the residual decides: the kept predictor is the best one
-        assert min(rw[1], rw[2], rw[3]) <= rw[1]
+        print(f"fitted predictor kept in {wins} of {len(periodic)} periodic steps; "
+              f"median residual reduction of the predictor x{gain:.2f}; Newton iterations "
+              f"{newton_l} vs {newton_f} (fallback), Krylov {krylov_l} vs {krylov_f}")
+    for rw in rows:   # the residual decides: the candidate is kept only when it is better
+        assert rw[4] in (0, 2)
+        assert rw[4] == 0 or rw[3] < rw[1]
     assert wins >= len(periodic) // 2, rows
+    # what the trained network gains over the method without it
+    assert newton_l < newton_f, (newton_l, newton_f, rows)
 
 
 def test_predict_matches_oracle(fsi):
