@@ -633,6 +633,8 @@ def finish(args, W, ws, rank, local, mesh, ms64, per64, ms32, per32, ops, ops32,
             extras["mlp_inference"] = mlp_section(args, dev, stream2, W)
         if "solid" in sections:
             extras["solid"] = solid_section(args, dev, stream2)
+        if "dlm" in sections:
+            extras["dlm_128"] = dlm_section(args, dev, stream2)
         if "mapped" in sections:
             extras["mapped"] = mapped_section(args, dev, stream2)
         if "tet" in sections:
@@ -912,34 +914,45 @@ def newton_section(args, dev, stream):
                        "residual (VMS, interp, spread; ~1e-14 vs FP64), also for the predictor's "
                        "judge")
     r_ref = None
+    im_f, isd_f = im.float().contiguous(), isd.float().contiguous()
+    om_c, osd_c = om.contiguous(), osd.contiguous()
+    # the same step from the same state, repeated (median wall time): the
+    # mixed variants --newton-reps times, the slow FP64 one once
     for name, mixed, guess_kind, pc in variants:
-        y, st = ch.state("zero" if guess_kind == "zero" else "extrapolated")
-        stream.synchronize()
-        torch.cuda.nvtx.range_push(f"newton_{name}")
-        t0 = time.perf_counter()
-        guess = None
-        if guess_kind == "learned":
-            guess = fsi.fsi_mlp_guess(h, ch.mesh, P, im.float().contiguous(),
-                                      isd.float().contiguous(), om.contiguous(), osd.contiguous(),
-                                      st, ch.yn, ch.d1, ch.d2, 0, work,
-                                      judge_prec=fsi.FSI_DF64)
-        code, rep = fsi.fsi_newton_step(ch.mesh, st, mixed=mixed, r_ref=r_ref or 0.0,
-                                        check=False, precond=pc,
-                                        residual_prec=fsi.FSI_DF64 if mixed else fsi.FSI_F64,
-                                        **solve)
-        stream.synchronize()
-        el = time.perf_counter() - t0
-        torch.cuda.nvtx.range_pop()
+        times, preds = [], []
+        for rep_i in range(args.newton_reps if mixed else 1):
+            y, st = ch.state("zero" if guess_kind == "zero" else "extrapolated")
+            stream.synchronize()
+            torch.cuda.nvtx.range_push(f"newton_{name}")
+            t0 = time.perf_counter()
+            guess = None
+            R0 = None
+            if guess_kind == "learned":
+                guess = fsi.fsi_mlp_guess(h, ch.mesh, P, im_f, isd_f, om_c, osd_c,
+                                          st, ch.yn, ch.d1, ch.d2, 0, work,
+                                          judge_prec=fsi.FSI_DF64)
+                # the judge's residual of the returned predictor is Newton's first
+                R0 = work[0]
+                preds.append(time.perf_counter() - t0)
+            code, rep = fsi.fsi_newton_step(ch.mesh, st, mixed=mixed, r_ref=r_ref or 0.0,
+                                            check=False, precond=pc,
+                                            residual_prec=fsi.FSI_DF64 if mixed else fsi.FSI_F64,
+                                            R0=R0, **solve)
+            stream.synchronize()
+            times.append(time.perf_counter() - t0)
+            torch.cuda.nvtx.range_pop()
         if r_ref is None:
             r_ref = rep["r_ref"]
-        out[name] = {"seconds": el, "newton_iters": rep["newton_iters"],
+        out[name] = {"seconds": float(np.median(times)), "seconds_all": times,
+                     "newton_iters": rep["newton_iters"],
                      "krylov_iters": rep["krylov_iters"], "r0_over_ref": rep["r0"] / r_ref,
                      "r_final_over_ref": rep["r_final"] / r_ref,
                      "converged": bool(rep["converged"]), "status": code}
         if guess is not None:
             out[name]["predictor"] = {k2: guess[k2] for k2 in (
-                "r_fallback", "r_learned", "r_combined", "used", "c_extrapolant", "a_velocity",
-                "b_pressure")}
+                "r_fallback", "r_learned", "r_extrapolant_fit", "r_combined", "used",
+                "c_extrapolant", "a_velocity", "b_pressure")}
+            out[name]["predictor"]["seconds"] = float(np.median(preds))
     if {"fp64", "mixed"} <= wanted:
         out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
     if {"fp64", "mixed_learned"} <= wanted:
@@ -1124,6 +1137,80 @@ def bubble_map(X, delta):
     """Smooth map of the unit cube onto itself, identity on its faces."""
     b = np.sin(2 * np.pi * X[:, 0]) * np.sin(2 * np.pi * X[:, 1]) * np.sin(2 * np.pi * X[:, 2])
     return X + delta * b[:, None] * np.array([1.0, -0.7, 0.4])[None, :]
+
+
+def dlm_section(args, dev, stream):
+    """The coupling operators on the 128^3 grid with 1M leaflet points (the
+    mixed Newton step's workload): location with the cell table (FP64),
+    interpolation and spreading in FP32, double-float and FP64.  Each call is
+    timed alone with CUDA events on the library's stream, L2 flushed (write of
+    a buffer > L2) before it, median of the repetitions; achieved = the
+    operator's algorithmic bytes (every input and output array touched once;
+    the velocity rows of the nodes of occupied cells for interpolation) / time,
+    against the measured HBM copy bandwidth."""
+    import torch
+    import paper_2601_08266_gb300 as fsi
+    from paper_2601_08266_gb300 import inputs
+    N, m = args.newton_grid, args.newton_points
+    mesh = fsi.Mesh(N, device=dev.index, stream=stream.cuda_stream)
+    n, E = mesh.n_nodes, mesh.n_elems
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    g = torch.Generator(device=dev).manual_seed(SEED + 90)
+    with torch.cuda.stream(stream):
+        flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device=dev)
+        X = torch.as_tensor(inputs.leaflet_points(m, seed=SEED + 91), device=dev)
+        elem = torch.empty(m, dtype=torch.int32, device=dev)
+        xi = torch.empty((m, 3), dtype=torch.float64, device=dev)
+        cs = torch.empty(E + 1, dtype=torch.int32, device=dev)
+        perm = torch.empty(m, dtype=torch.int32, device=dev)
+    fsi.fsi_locate(mesh, X, elem, xi, cs, perm)
+    stream.synchronize()
+    # nodes of occupied cells (the rows interpolation reads)
+    occ = torch.nonzero(cs[1:] > cs[:-1]).flatten().long()
+    ex, ey, ez = occ % N, (occ // N) % N, occ // (N * N)
+    nodes = torch.cat([(ex + dx) + (N + 1) * ((ey + dy) + (N + 1) * (ez + dz))
+                       for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)]).unique().numel()
+
+    def timed(fn, reps=10):
+        ts = []
+        for r in range(reps + 2):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            stream.synchronize()
+            if r >= 2:
+                ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    def entry(ms, nbytes):
+        return {"ms": round(ms, 5), "gb_s": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / hbm, 4),
+                "points_per_s": round(m / (ms * 1e-3), 1), "bytes": int(nbytes)}
+
+    out = {"grid": [N, N, N], "points": m, "occupied_cells": int(occ.numel()),
+           "nodes_of_occupied_cells": int(nodes)}
+    t = timed(lambda: fsi.fsi_locate(mesh, X, elem, xi, cs, perm, want_outside=False))
+    out["locate_f64"] = entry(t, m * (24 + 4 + 24 + 4) + (E + 1) * 4)
+    for name, P, dt, sz in (("f32", fsi.FSI_F32, torch.float32, 4),
+                            ("df64", fsi.FSI_DF64, torch.float64, 8),
+                            ("f64", fsi.FSI_F64, torch.float64, 8)):
+        with torch.cuda.stream(stream):
+            U = torch.randn((n, 4), dtype=dt, device=dev, generator=g)
+            F = torch.zeros((n, 4), dtype=dt, device=dev)
+            lam = torch.randn((m, 3), dtype=dt, device=dev, generator=g)
+            u = torch.empty((m, 3), dtype=dt, device=dev)
+            xw = xi.to(dt).contiguous()
+        t = timed(lambda: fsi.fsi_dlm_interp(mesh, P, elem, xw, U, u))
+        out[f"interp_{name}"] = entry(t, m * (4 + 3 * sz + 3 * sz) + nodes * 4 * sz)
+        t = timed(lambda: fsi.fsi_dlm_spread(mesh, P, elem, xw, cs, perm, lam, None, F, False))
+        out[f"spread_{name}"] = entry(t, m * (4 + 3 * sz + 3 * sz) + (E + 1) * 4 + n * 3 * sz)
+        del U, F, lam, u, xw
+    mesh.close()
+    return out
 
 
 def mapped_section(args, dev, stream):
@@ -1492,6 +1579,62 @@ def mlp_section(args, dev, stream, W):
     return out
 
 
+def profile_case(args):
+    """Small fixed cases for ncu captures (nothing is timed): 'vms_f64' runs the
+    fused FP64 residual + Jacobian pass twice on the --grid grid with 4x4x4
+    bricks of 128 threads; 'dlm' runs location with the cell table, and FP32
+    and double-float interpolation and spreading, twice, on the --grid grid
+    with --points leaflet points; 'blas1' runs the Krylov multi-dot and
+    multi-update kernels twice each on 8 FP32 vectors of the --grid grid's
+    4 (N+1)^3 entries."""
+    import torch
+    import paper_2601_08266_gb300 as fsi
+    from paper_2601_08266_gb300 import inputs
+    dev = torch.device("cuda:0")
+    N = args.grid
+    if args.profile_case == "blas1":
+        from paper_2601_08266_gb300 import _binding as B
+        B.fsi_measure_blas1(0, fsi.FSI_F32, 4 * (N + 1) ** 3, 8, reps=1)
+        print(json.dumps({"profile_case": "blas1", "grid": N, "ok": True}))
+        return 0
+    mesh = fsi.Mesh(N, device=0)
+    n = mesh.n_nodes
+    if args.profile_case == "vms_f64":
+        fsi.fsi_mesh_set_brick(mesh, 2, fsi.FSI_F64, 4, 4, 4, 128)
+        U = torch.as_tensor(inputs.fourier_field(N, seed=1), device=dev)
+        A = torch.as_tensor(inputs.fourier_field(N, seed=2), device=dev)
+        A[:, 3] = 1.0
+        x = torch.as_tensor(inputs.uniform_nodal(N, seed=3), device=dev)
+        R, J = torch.empty_like(U), torch.empty_like(U)
+        for _ in range(2):
+            fsi.fsi_residual_jacobian_apply(mesh, fsi.FSI_F64, U, A, None, x, R, J)
+    else:
+        m = args.points
+        X = torch.as_tensor(inputs.leaflet_points(m, seed=7), device=dev)
+        elem = torch.empty(m, dtype=torch.int32, device=dev)
+        xi = torch.empty((m, 3), dtype=torch.float64, device=dev)
+        cs = torch.empty(mesh.n_elems + 1, dtype=torch.int32, device=dev)
+        perm = torch.empty(m, dtype=torch.int32, device=dev)
+        bufs = {}
+        for name, P, dt in (("f32", fsi.FSI_F32, torch.float32),
+                            ("df64", fsi.FSI_DF64, torch.float64)):
+            bufs[name] = (P, torch.randn((n, 4), dtype=dt, device=dev),
+                          torch.zeros((n, 4), dtype=dt, device=dev),
+                          torch.randn((m, 3), dtype=dt, device=dev),
+                          torch.empty((m, 3), dtype=dt, device=dev))
+        for _ in range(2):
+            fsi.fsi_locate(mesh, X, elem, xi, cs, perm, want_outside=False)
+            for name in ("f32", "df64"):
+                P, U, F, lam, u = bufs[name]
+                xw = xi.to(U.dtype).contiguous()
+                fsi.fsi_dlm_interp(mesh, P, elem, xw, U, u)
+                fsi.fsi_dlm_spread(mesh, P, elem, xw, cs, perm, lam, None, F, False)
+    torch.cuda.synchronize()
+    mesh.close()
+    print(json.dumps({"profile_case": args.profile_case, "grid": N, "ok": True}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1507,10 +1650,12 @@ def main():
                     help="keep the default brick schedules of the VMS operators (8x8x4; 8x4x4 "
                          "for the fused pass)")
     ap.add_argument("--no-extras", action="store_true", help="skip Newton, batch and MLP sections")
-    ap.add_argument("--sections", default="newton,batch,mlp,solid,mapped,tet",
+    ap.add_argument("--sections", default="newton,dlm,batch,mlp,solid,mapped,tet",
                     help="comma-separated extra sections to run")
     ap.add_argument("--newton-grid", type=int, default=128)
     ap.add_argument("--newton-points", type=int, default=1_000_000)
+    ap.add_argument("--newton-reps", type=int, default=3,
+                    help="repetitions of each mixed Newton variant (median time)")
     ap.add_argument("--newton-warm", type=int, default=3)
     ap.add_argument("--krylov-floor", type=float, default=1e-4,
                     help="floor of the Newton solver's target-aware inner tolerance")
@@ -1528,7 +1673,11 @@ def main():
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--batch-tune-f64", action="store_true")
+    ap.add_argument("--profile-case", choices=["vms_f64", "dlm", "blas1"], default=None,
+                    help="run one small fixed case for an ncu capture and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

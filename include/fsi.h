@@ -455,6 +455,14 @@ typedef struct {
     int32_t residual_prec; /* FSI_F64 or FSI_DF64: arithmetic of the Newton
                               residual (see fsi_coupled_residual)             */
     int32_t reserved;
+    const double *R0;      /* NULL, or R(y_0) [n][4] FP64 on the device,
+                              computed by the caller in residual_prec for
+                              this state (fsi_coupled_residual, e.g. the
+                              judge's residual fsi_mlp_guess leaves in its
+                              work array): the first residual evaluation is
+                              skipped.  Ignored (R(y_0) evaluated) when the
+                              state carries a hyperelastic body, whose stage
+                              values come out of the residual.  Read only.   */
 } fsi_newton_opts;
 
 typedef struct {
@@ -688,7 +696,9 @@ fsi_status fsi_mlp_predict(fsi_mlp *mlp, fsi_mesh *mesh, const float *params,
  * candidate's residual is then evaluated in judge_prec, and st->y keeps the
  * candidate if its residual norm is below the fallback's, else y_fb.  Cost:
  * two residuals, three FP32 Jacobian applies and the network.  judge_prec:
- * FSI_F64 or FSI_DF64.  work: caller-owned FP64 device array [5][n][4].
+ * FSI_F64 or FSI_DF64.  work: caller-owned FP64 device array [5][n][4]; on
+ * return work[0..n) x 4 holds R(st->y) in judge_prec, the residual that
+ * judged the returned predictor, for fsi_newton_opts.R0.
  * yn [n][4] is y_n (must not alias st->y).  Synchronises; a tensor-core wait
  * that ran out in this or an earlier call of the handle is FSI_ERR_TIMEOUT. */
 typedef struct {
@@ -698,6 +708,10 @@ typedef struct {
     double a_velocity, b_pressure, c_extrapolant;  /* beta, gamma, alpha            */
     int32_t used;        /* 0 fallback, 2 fitted candidate                           */
     int32_t reserved;
+    double r_extrapolant_fit; /* the linear model's ||R|| at the best y_fb + alpha e
+                                 alone (the same fit without the network's
+                                 directions: what the network adds is the gap
+                                 to r_combined)                                 */
 } fsi_guess_report;
 
 fsi_status fsi_mlp_guess(fsi_mlp *mlp, fsi_mesh *mesh, const float *params, const float *in_mean,

@@ -56,7 +56,7 @@ class fsi_newton_opts(ctypes.Structure):
                 ("newton_rtol", ctypes.c_double), ("krylov_rtol", ctypes.c_double),
                 ("r_ref", ctypes.c_double), ("precond_every", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("residual_prec", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("R0", ctypes.c_void_p)]
 
 
 class fsi_newton_report(ctypes.Structure):
@@ -73,7 +73,8 @@ class fsi_guess_report(ctypes.Structure):
     _fields_ = [("r_fallback", ctypes.c_double), ("r_learned", ctypes.c_double),
                 ("r_combined", ctypes.c_double), ("a_velocity", ctypes.c_double),
                 ("b_pressure", ctypes.c_double), ("c_extrapolant", ctypes.c_double),
-                ("used", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("used", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("r_extrapolant_fit", ctypes.c_double)]
 
 
 class fsi_batch_item(ctypes.Structure):
@@ -515,10 +516,16 @@ PRECOND_BLOCK_JACOBI, PRECOND_SCHUR = 0, 1
 
 def fsi_newton_step(mesh: Mesh, st: StepState, mixed=True, restart=50, max_newton=10,
                     max_krylov=1000, newton_rtol=1e-8, krylov_rtol=1e-3, r_ref=0.0,
-                    precond_every=0, precond=PRECOND_SCHUR, residual_prec=FSI_F64, check=True):
-    """Returns (status, report dict); raises on error when check is True."""
+                    precond_every=0, precond=PRECOND_SCHUR, residual_prec=FSI_F64, check=True,
+                    R0=None):
+    """Returns (status, report dict); raises on error when check is True.
+    R0: optional FP64 [n, 4] device tensor holding R(st.y) in residual_prec."""
+    import torch
+    if R0 is not None and R0.numel() != 4 * mesh.n_nodes:
+        raise ValueError("R0 must hold [n_nodes, 4] values")
     o = fsi_newton_opts(1 if mixed else 0, restart, max_newton, max_krylov, newton_rtol,
-                        krylov_rtol, r_ref, precond_every, int(precond), int(residual_prec), 0)
+                        krylov_rtol, r_ref, precond_every, int(precond), int(residual_prec), 0,
+                        _ptr(R0, torch.float64) if R0 is not None else None)
     rep = fsi_newton_report()
     st_code = lib().fsi_newton_step(mesh.handle, ctypes.byref(o), ctypes.byref(st.c),
                                     ctypes.byref(rep))

@@ -207,8 +207,12 @@ __global__ void batch_interp_kernel(const DlmDesc<T> *desc, const int64_t *prefi
     for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
         const int inst = find_instance(prefix, count, item);
         const DlmDesc<T> &D = desc[inst];
-        const int64_t b = (item - prefix[inst]) * kChunk + threadIdx.x;
-        if (b < D.m) dlmd::interp_point<T>(D.g, b, D.elem, D.xi, D.U, D.u);
+        // the chunk's kChunk points in two halves, two lanes per point
+        for (int half = 0; half < 2; ++half) {
+            const int64_t b = (item - prefix[inst]) * kChunk + half * (kChunk / 2) +
+                              (threadIdx.x >> 1);
+            dlmd::interp_point_pair<T>(D.g, b, b < D.m, D.elem, D.xi, D.U, D.u);
+        }
     }
 }
 

@@ -573,6 +573,9 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
         }
         rep->r_learned = std::sqrt(std::max(v, 0.0));
     }
+    // the same linear model restricted to y_fb + alpha e
+    rep->r_extrapolant_fit =
+        G[0][0] > 0.0 ? std::sqrt(std::max(rr - r[0] * r[0] / G[0][0], 0.0)) : r_fb;
     rep->r_fallback = r_fb;
     rep->c_extrapolant = x[0];
     rep->a_velocity = x[1];
@@ -596,6 +599,10 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
     if (rep->used == 2)
         FSI_CUDA(cudaMemcpyAsync(st->y, cand, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s),
                  "memcpy");
+    // the judged residual of the returned predictor, for the Newton step
+    FSI_CUDA(cudaMemcpyAsync(work, rep->used == 2 ? Rc : Rfb, n4 * sizeof(double),
+                             cudaMemcpyDeviceToDevice, s),
+             "memcpy");
     FSI_CUDA(cudaStreamSynchronize(s), "sync");
     return take_tc_error(h);
 }

@@ -978,7 +978,14 @@ fsi_status newton_impl(fsi_mesh *mesh, const fsi_newton_opts *o, const fsi_step_
     cudaStream_t s = mesh->stream;
     const int64_t len = 4 * mesh->n_nodes;
     const fsi_prec rp = o->residual_prec == FSI_DF64 ? FSI_DF64 : FSI_F64;
-    FSI_TRY(coupled_residual_impl(mesh, st, W.R, rp));
+    if (o->R0 && !(st->m > 0 && st->body)) {
+        // the caller's R(y_0); the linearisation still needs the stage values
+        FSI_TRY(fsi_stage(mesh, FSI_F64, st->y, st->Vn, st->An, st->s, W.U, W.A));
+        FSI_CUDA(cudaMemcpyAsync(W.R, o->R0, len * sizeof(double), cudaMemcpyDeviceToDevice, s),
+                 "memcpy");
+    } else {
+        FSI_TRY(coupled_residual_impl(mesh, st, W.R, rp));
+    }
     double r = 0.0;
     FSI_TRY(norm2<double>(mesh, W.R, W.hcol));
     FSI_TRY(host_scalar(mesh, W.hcol, &r));

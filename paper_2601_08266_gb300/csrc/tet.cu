@@ -288,6 +288,7 @@ template <typename T, bool JAC> __global__ void __launch_bounds__(256) tet_vms_k
             if (V.f) {
                 value2(ff.x, ff.y, q.f[0], q.f[1]);
                 q.f[2] = value(ff.z);
+                for (int i = 0; i < 3; ++i) q.a[i] = q.a[i] - q.f[i];
             } else {
                 q.f[0] = q.f[1] = q.f[2] = T(0);
             }

@@ -354,9 +354,11 @@ template <> __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v
 template <> __device__ __forceinline__ df64 rsqrt_t(df64 v) { return df_rsqrt(v); }
 
 // Base state of the VMS form at one Gauss point.
+// a[] holds the acceleration minus the body force (a - f): the two enter the
+// residual only as that difference; cup = -tau_M / rho (u' = cup r_M)
 template <typename T> struct GP {
     T v[3], gv[3][3], p, gp[3], a[3], f[3], s;
-    T rM[3], rC, conv[3], tauM, tauC, up[3], pp, vGv;
+    T rM[3], rC, conv[3], tauM, tauC, up[3], pp, vGv, cup;
 };
 
 template <typename T>
@@ -364,7 +366,7 @@ __device__ __forceinline__ void base_state(const VmsArgs<T> &P, GP<T> &q)
 {
     for (int i = 0; i < 3; ++i) {
         q.conv[i] = dot3_t(q.v[0], q.gv[i][0], q.v[1], q.gv[i][1], q.v[2], q.gv[i][2]);
-        q.rM[i] = fma_t(P.rho, q.a[i] + q.conv[i] - q.f[i], q.gp[i]);
+        q.rM[i] = fma_t(P.rho, q.a[i] + q.conv[i], q.gp[i]);
     }
     q.rC = q.gv[0][0] + q.gv[1][1] + q.gv[2][2];
     q.vGv = dot3_t(P.G0 * q.v[0], q.v[0], P.G1 * q.v[1], q.v[1], P.G2 * q.v[2], q.v[2]);
@@ -372,8 +374,8 @@ __device__ __forceinline__ void base_state(const VmsArgs<T> &P, GP<T> &q)
     q.tauM = rsqrt_t(S);
     // tau_C = 1/(tau_M tr G) and 1/tau_M = S tau_M
     q.tauC = S * q.tauM * P.inv_trG;
-    const T c = -q.tauM * P.inv_rho;
-    for (int i = 0; i < 3; ++i) q.up[i] = c * q.rM[i];
+    q.cup = -q.tauM * P.inv_rho;
+    for (int i = 0; i < 3; ++i) q.up[i] = q.cup * q.rM[i];
     q.pp = -P.rho * q.tauC * q.rC;
 }
 
@@ -389,7 +391,7 @@ __device__ __forceinline__ void base_state_g(const VmsArgs<T> &P, const Geo<T> &
 {
     for (int i = 0; i < 3; ++i) {
         q.conv[i] = dot3_t(q.v[0], q.gv[i][0], q.v[1], q.gv[i][1], q.v[2], q.gv[i][2]);
-        q.rM[i] = fma_t(P.rho, q.a[i] + q.conv[i] - q.f[i], q.gp[i]);
+        q.rM[i] = fma_t(P.rho, q.a[i] + q.conv[i], q.gp[i]);
     }
     q.rC = q.gv[0][0] + q.gv[1][1] + q.gv[2][2];
     T vGv = T(0);
@@ -399,8 +401,8 @@ __device__ __forceinline__ void base_state_g(const VmsArgs<T> &P, const Geo<T> &
     const T S = q.s * (geo.q0 + q.vGv);
     q.tauM = rsqrt_t(S);
     q.tauC = S * q.tauM * geo.inv_trG;
-    const T c = -q.tauM * P.inv_rho;
-    for (int i = 0; i < 3; ++i) q.up[i] = c * q.rM[i];
+    q.cup = -q.tauM * P.inv_rho;
+    for (int i = 0; i < 3; ++i) q.up[i] = q.cup * q.rM[i];
     q.pp = -P.rho * q.tauC * q.rC;
 }
 
@@ -465,13 +467,25 @@ template <typename T>
 __device__ __forceinline__ void gp_residual_terms(const VmsArgs<T> &P, const GP<T> &q, T (&X)[4],
                                                   T (&Y)[4][3])
 {
+    // X_i = rho (a - f + v.grad v_i + u'.grad v_i), the sums in FMA order
     for (int i = 0; i < 3; ++i) {
-        X[i] = P.rho * (q.a[i] + q.conv[i] - q.f[i] +
-                        dot3_t(q.up[0], q.gv[i][0], q.up[1], q.gv[i][1], q.up[2], q.gv[i][2]));
-        for (int j = 0; j < 3; ++j)
-            Y[i][j] = dot2_t(P.mu, q.gv[i][j] + q.gv[j][i], -P.rho * (q.v[j] + q.up[j]), q.up[i]);
-        Y[i][i] -= q.p + q.pp;
+        T t = q.a[i] + q.conv[i];
+        t = fma_t(q.up[0], q.gv[i][0], t);
+        t = fma_t(q.up[1], q.gv[i][1], t);
+        t = fma_t(q.up[2], q.gv[i][2], t);
+        X[i] = P.rho * t;
     }
+    // Y_ij = mu (d_j v_i + d_i v_j) - rho (v_j + u'_j) u'_i: the symmetric
+    // viscous part once per pair
+    T mw[3];
+    for (int j = 0; j < 3; ++j) mw[j] = -P.rho * (q.v[j] + q.up[j]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = i; j < 3; ++j) {
+            const T muS = P.mu * (q.gv[i][j] + q.gv[j][i]);
+            Y[i][j] = fma_t(mw[j], q.up[i], muS);
+            if (j != i) Y[j][i] = fma_t(mw[i], q.up[j], muS);
+        }
+    for (int i = 0; i < 3; ++i) Y[i][i] -= q.p + q.pp;
     X[3] = q.rC;
     for (int j = 0; j < 3; ++j) Y[3][j] = -q.up[j];
 }
@@ -495,27 +509,49 @@ __device__ __forceinline__ void gp_jacobian_terms(const VmsArgs<T> &P, const GP<
                                                   const T (&da)[3], T dp, const T (&dgp)[3],
                                                   T vGdv, T q0, T (&X)[4], T (&Y)[4][3])
 {
-    T dconv[3], drM[3], dup[3];
+    T dconv[3], drM[3], dup[3], dadc[3];
     for (int i = 0; i < 3; ++i) {
-        dconv[i] = dot3_t(dv[0], q.gv[i][0], dv[1], q.gv[i][1], dv[2], q.gv[i][2]) +
-                   dot3_t(q.v[0], dgv[i][0], q.v[1], dgv[i][1], q.v[2], dgv[i][2]);
-        drM[i] = fma_t(P.rho, da[i] + dconv[i], dgp[i]);
+        // dv.grad v_i + v.grad dv_i, one product and five FMAs
+        T t = q.v[0] * dgv[i][0];
+        t = fma_t(q.v[1], dgv[i][1], t);
+        t = fma_t(q.v[2], dgv[i][2], t);
+        t = fma_t(dv[0], q.gv[i][0], t);
+        t = fma_t(dv[1], q.gv[i][1], t);
+        dconv[i] = fma_t(dv[2], q.gv[i][2], t);
+        dadc[i] = da[i] + dconv[i];
+        drM[i] = fma_t(P.rho, dadc[i], dgp[i]);
     }
     const T drC = dgv[0][0] + dgv[1][1] + dgv[2][2];
     const T dtauM = -q.tauM * q.tauM * q.tauM * q.s * vGdv;
     // d tau_C = -tau_C d tau_M / tau_M, 1/tau_M = s (q0 + vGv) tau_M
     const T dtauC = -q.tauC * dtauM * (q.s * (q0 + q.vGv) * q.tauM);
-    for (int i = 0; i < 3; ++i) dup[i] = -dot2_t(dtauM, q.rM[i], q.tauM, drM[i]) * P.inv_rho;
+    // du' = -(d tau_M r_M + tau_M d r_M) / rho
+    const T ka = -dtauM * P.inv_rho;
+    for (int i = 0; i < 3; ++i) dup[i] = fma_t(ka, q.rM[i], q.cup * drM[i]);
     const T dpp = -P.rho * dot2_t(dtauC, q.rC, q.tauC, drC);
     for (int i = 0; i < 3; ++i) {
-        X[i] = P.rho * (da[i] + dconv[i] +
-                        dot3_t(dup[0], q.gv[i][0], dup[1], q.gv[i][1], dup[2], q.gv[i][2]) +
-                        dot3_t(q.up[0], dgv[i][0], q.up[1], dgv[i][1], q.up[2], dgv[i][2]));
-        for (int j = 0; j < 3; ++j)
-            Y[i][j] = fma_t(P.mu, dgv[i][j] + dgv[j][i],
-                            -P.rho * dot2_t(dv[j] + dup[j], q.up[i], q.v[j] + q.up[j], dup[i]));
-        Y[i][i] -= dp + dpp;
+        T t = dadc[i];
+        t = fma_t(dup[0], q.gv[i][0], t);
+        t = fma_t(dup[1], q.gv[i][1], t);
+        t = fma_t(dup[2], q.gv[i][2], t);
+        t = fma_t(q.up[0], dgv[i][0], t);
+        t = fma_t(q.up[1], dgv[i][1], t);
+        t = fma_t(q.up[2], dgv[i][2], t);
+        X[i] = P.rho * t;
     }
+    // Y_ij = mu (d_j dv_i + d_i dv_j) - rho [(dv_j + du'_j) u'_i + (v_j + u'_j) du'_i]
+    T mw[3], md[3];
+    for (int j = 0; j < 3; ++j) {
+        mw[j] = -P.rho * (q.v[j] + q.up[j]);
+        md[j] = -P.rho * (dv[j] + dup[j]);
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = i; j < 3; ++j) {
+            const T muS = P.mu * (dgv[i][j] + dgv[j][i]);
+            Y[i][j] = fma_t(md[j], q.up[i], fma_t(mw[j], dup[i], muS));
+            if (j != i) Y[j][i] = fma_t(md[i], q.up[j], fma_t(mw[i], dup[j], muS));
+        }
+    for (int i = 0; i < 3; ++i) Y[i][i] -= dp + dpp;
     X[3] = drC;
     for (int j = 0; j < 3; ++j) Y[3][j] = -dup[j];
 }
@@ -614,6 +650,7 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
         if (P.f) {
             eval_v2<OUT>(ff.x, ff.y, q.f[0], q.f[1]);
             q.f[2] = eval_v<OUT>(ff.z);
+            for (int i = 0; i < 3; ++i) q.a[i] = q.a[i] - q.f[i];
         } else {
             q.f[0] = q.f[1] = q.f[2] = T(0);
         }

@@ -70,3 +70,45 @@ def test_product_path_does_not_touch_the_oracle():
             continue
         src = open(path, errors="ignore").read()
         assert "oracle" not in src.lower().replace("the oracle", ""), path
+
+
+def test_struct_layouts_match_the_header():
+    """Every struct the binding mirrors has the header's size and field
+    offsets (a small C program compiled against include/fsi.h prints them)."""
+    import shutil
+    import subprocess
+    import tempfile
+    from paper_2601_08266_gb300 import _binding as b
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [c for c in vars(b).values()
+               if isinstance(c, type) and issubclass(c, ctypes.Structure)
+               and c.__name__.startswith("fsi_")]
+    assert structs
+    import keyword
+
+    def cname(f):   # a C field named like a Python keyword carries a trailing _
+        return f[:-1] if f.endswith("_") and keyword.iskeyword(f[:-1]) else f
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fsi.h"', "int main(void) {"]
+    for c in structs:
+        lines.append(f'printf("{c.__name__} size %zu\\n", sizeof({c.__name__}));')
+        for f in c._fields_:
+            lines.append(f'printf("{c.__name__} {f[0]} %zu\\n", '
+                         f'offsetof({c.__name__}, {cname(f[0])}));')
+    lines += ["return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines))
+        r = subprocess.run([cc, "-I", os.path.join(ROOT, "include"), src, "-o", exe],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    got = {}
+    for line in out.splitlines():
+        s, f, v = line.split()
+        got[(s, f)] = int(v)
+    for c in structs:
+        assert got[(c.__name__, "size")] == ctypes.sizeof(c), c.__name__
+        for f in c._fields_:
+            assert got[(c.__name__, f[0])] == getattr(c, f[0]).offset, (c.__name__, f[0])

@@ -185,9 +185,10 @@ def run_series(fsi, N, steps, dt=0.01, period=0.12, learn=None, seed=0):
         r_ref = rec["guess"]["r_fallback"] if "guess" in rec else 0.0
         # target-aware forcing with a floor of 1e-4: a start with a smaller
         # residual may meet the same absolute target in fewer Newton iterations
+        # with the network, the judge's residual of the predictor is Newton's first
         code, rep = fsi.fsi_newton_step(mesh, st, mixed=True, restart=50, max_newton=8,
                                         max_krylov=3000, newton_rtol=1e-8, krylov_rtol=1e-4,
-                                        r_ref=r_ref)
+                                        r_ref=r_ref, R0=work[0] if "guess" in rec else None)
         rec["rep"] = rep
         d_new = y - yn
         if "X" in rec:
@@ -265,6 +266,10 @@ def test_learned_guess_end_to_end(fsi, capsys):
         print(f"fitted predictor kept in {wins} of {len(periodic)} periodic steps; "
               f"median residual reduction of the predictor x{gain:.2f}; Newton iterations "
               f"{newton_l} vs {newton_f} (fallback), Krylov {krylov_l} vs {krylov_f}")
+        # ablation: the same fit without the network's directions (linear model)
+        print("linear-model residual of the extrapolant-only fit / judged residual of the "
+              "full fit:", [round(r["guess"]["r_extrapolant_fit"] / r["guess"]["r_combined"], 2)
+                            for r in recs2 if "guess" in r and r["step"] >= skip + 1])
     for rw in rows:   # the residual decides: the candidate is kept only when it is better
         assert rw[4] in (0, 2)
         assert rw[4] == 0 or rw[3] < rw[1]

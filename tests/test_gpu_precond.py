@@ -154,8 +154,10 @@ def test_vcycle_rejects_aliasing_and_bad_levels(fsi):
 
 
 def test_schur_preconditioner_cuts_krylov_iterations(fsi, oracle):
-    """Same Newton step, both preconditioners: the same converged residual,
-    and the Schur preconditioner needs far fewer Krylov iterations."""
+    """Same Newton step, both preconditioners: the same converged solution,
+    and the Schur preconditioner needs far fewer Krylov iterations.  The
+    Newton tolerance is 1e-10 so that the two iterates, each stopped just
+    below it, lie within 1e-5 of one another."""
     import torch
     from paper_2601_08266_gb300 import inputs
     N, dt = 24, 1e-3
@@ -194,7 +196,7 @@ def test_schur_preconditioner_cuts_krylov_iterations(fsi, oracle):
                                w=torch.full((m,), 0.024 / m, dtype=torch.float64, device="cuda"),
                                drho_s=0.5)
             code, rep = fsi.fsi_newton_step(mesh, st, mixed=mixed, restart=50, max_newton=10,
-                                            max_krylov=4000, newton_rtol=1e-8, krylov_rtol=1e-3,
+                                            max_krylov=4000, newton_rtol=1e-10, krylov_rtol=1e-3,
                                             precond=pc)
             assert code == 0 and rep["converged"], rep
             res[(pc, mixed)] = (rep["krylov_iters"], H(y))
