@@ -207,11 +207,17 @@ __global__ void batch_interp_kernel(const DlmDesc<T> *desc, const int64_t *prefi
     for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
         const int inst = find_instance(prefix, count, item);
         const DlmDesc<T> &D = desc[inst];
-        // the chunk's kChunk points in two halves, two lanes per point
-        for (int half = 0; half < 2; ++half) {
-            const int64_t b = (item - prefix[inst]) * kChunk + half * (kChunk / 2) +
-                              (threadIdx.x >> 1);
-            dlmd::interp_point_pair<T>(D.g, b, b < D.m, D.elem, D.xi, D.U, D.u);
+        if constexpr (std::is_same<T, float>::value) {
+            // the chunk's kChunk points in two halves, two lanes per point
+            // (the single-mesh FP32 kernel's arithmetic)
+            for (int half = 0; half < 2; ++half) {
+                const int64_t b = (item - prefix[inst]) * kChunk + half * (kChunk / 2) +
+                                  (threadIdx.x >> 1);
+                dlmd::interp_point_pair<T>(D.g, b, b < D.m, D.elem, D.xi, D.U, D.u);
+            }
+        } else {
+            const int64_t b = (item - prefix[inst]) * kChunk + threadIdx.x;
+            if (b < D.m) dlmd::interp_point<T>(D.g, b, D.elem, D.xi, D.U, D.u);
         }
     }
 }
@@ -238,9 +244,14 @@ __global__ void batch_spread_nodes_kernel(const DlmDesc<T> *desc, const int64_t 
     for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
         const int inst = find_instance(prefix, count, item);
         const DlmDesc<T> &D = desc[inst];
-        const int n = (D.g.Nx + 1) * (D.g.Ny + 1) * (D.g.Nz + 1);
+        const int NX1 = D.g.Nx + 1, NY1 = D.g.Ny + 1;
+        const int n = NX1 * NY1 * (D.g.Nz + 1);
         const int64_t node = (item - prefix[inst]) * kChunk + threadIdx.x;
-        if (node < n) dlmd::spread_node<T>(D.g, (int)node, D.start, D.S, D.F, 0);
+        if (node < n) {
+            const int nd = (int)node;
+            dlmd::spread_node<T>(D.g, nd % NX1, (nd / NX1) % NY1, nd / (NX1 * NY1), D.start, D.S,
+                                 D.F, 0);
+        }
     }
 }
 

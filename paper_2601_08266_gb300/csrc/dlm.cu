@@ -13,7 +13,9 @@
 // fuller cells, fixed transpose-reduce trees), then a node gather over the
 // (up to) eight cells of each node in a fixed order.  No races, no atomics,
 // and the result does not depend on scheduling.
+#include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <mutex>
 
 #include "fsi_internal.cuh"
@@ -368,17 +370,24 @@ __global__ void __launch_bounds__(1024) dense_sort_kernel(int64_t E, int64_t m,
 }
 
 // --------------------------------------------------------------- interp / spread
-// two lanes per point (interp_point_pair); the loop bound is warp-uniform
+// FP32: two lanes per point (interp_point_pair; the loop bound is
+// warp-uniform); double-float and FP64: one lane per point
 template <typename T, typename S = typename StorageOf<T>::type>
 __global__ void interp_kernel(int64_t m, GridArgs g, const int32_t *__restrict__ elem,
                               const S *__restrict__ xi, const vec4<S> *__restrict__ U,
                               S *__restrict__ u)
 {
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int pair = (threadIdx.x & 31) >> 1;
-    for (int64_t b0 = warp * 16; b0 < m; b0 += nwarps * 16)
-        interp_point_pair<T>(g, b0 + pair, b0 + pair < m, elem, xi, U, u);
+    if constexpr (std::is_same<T, float>::value) {
+        const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+        const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        const int pair = (threadIdx.x & 31) >> 1;
+        for (int64_t b0 = warp * 16; b0 < m; b0 += nwarps * 16)
+            interp_point_pair<T>(g, b0 + pair, b0 + pair < m, elem, xi, U, u);
+    } else {
+        for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
+             b += (int64_t)gridDim.x * blockDim.x)
+            interp_point<T>(g, b, elem, xi, U, u);
+    }
 }
 
 // Spreading, pass 1: one warp per segment of kSpreadSeg consecutive cells
@@ -399,17 +408,19 @@ __global__ void spread_cells_kernel(int64_t E, const typename StorageOf<T>::type
         spread_cells_segment<T>(E, c0, xi, start, perm, lam, w, S);
 }
 
-// Spreading, pass 2: every node sums the corner sums of its occupied cells,
-// four consecutive nodes of an x-row per thread (spread_node_quad).
+// Spreading, pass 2: every node sums the corner sums of its occupied cells.
+// 3D launch: x over the row's nodes, y over j, z (strided) over k: no index
+// division.
 template <typename T>
 __global__ void spread_nodes_kernel(GridArgs g, const int32_t *__restrict__ start,
                                     const T *__restrict__ S,
                                     typename StorageOf<T>::type *__restrict__ F, int accumulate)
 {
-    const int64_t nq = (int64_t)((g.Nx + 4) / 4) * (g.Ny + 1) * (g.Nz + 1);
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
-         q += (int64_t)gridDim.x * blockDim.x)
-        spread_node_quad<T>(g, q, start, S, F, accumulate);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > g.Nx || j > g.Ny) return;
+    for (int k = blockIdx.z; k <= g.Nz; k += gridDim.z)
+        spread_node<T>(g, i, j, k, start, S, F, accumulate);
 }
 
 // ------------------------------------------------------------- interface scaling
@@ -603,10 +614,10 @@ fsi_status fsi_dlm_interp(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
     if (mesh->tet) return fsi_tet_interp(mesh->tet, prec, m, elem, xi, U, u);
     GridArgs g = grid_args(mesh);
     if (prec == FSI_F64)
-        interp_kernel<double><<<blocks_for(2 * m, 256), 256, 0, mesh->stream>>>(
+        interp_kernel<double><<<blocks_for(m, 256), 256, 0, mesh->stream>>>(
             m, g, elem, (const double *)xi, (const vec4<double> *)U, (double *)u);
     else if (prec == FSI_DF64)
-        interp_kernel<df64><<<blocks_for(2 * m, 256), 256, 0, mesh->stream>>>(
+        interp_kernel<df64><<<blocks_for(m, 256), 256, 0, mesh->stream>>>(
             m, g, elem, (const double *)xi, (const vec4<double> *)U, (double *)u);
     else
         interp_kernel<float><<<blocks_for(2 * m, 256), 256, 0, mesh->stream>>>(
@@ -636,28 +647,31 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
     FSI_TRY(ensure_spread_scratch(mesh, (size_t)mesh->n_elems * 24 * esz));
     const int64_t E = mesh->n_elems;
     const int cgrid = blocks_for((E + kSpreadSeg - 1) / kSpreadSeg * 32, 256, sm_count() * 64);
-    const int64_t nquads = (int64_t)((g.Nx + 4) / 4) * (g.Ny + 1) * (g.Nz + 1);
-    const int ngrid = blocks_for(nquads, 256, sm_count() * 32);
+    // nodes: 32 x 8 threads per CTA over (i, j), one grid layer per k
+    const dim3 nblock(32, 8);
+    const dim3 ngrid((g.Nx + 32) / 32, std::min((g.Ny + 8) / 8, 65535), std::min(g.Nz + 1, 65535));
+    if ((g.Ny + 8) / 8 > 65535)
+        return set_error(FSI_ERR_ARG, "fsi_dlm_spread: more than 524,280 nodes along y");
     if (prec == FSI_F64) {
         spread_cells_kernel<double><<<cgrid, 256, 0, mesh->stream>>>(
             E, (const double *)xi, cell_start, perm, (const double *)lam, (const double *)w,
             (double *)mesh->spread_scratch);
         FSI_TRY(check_launch("spread cells kernel"));
-        spread_nodes_kernel<double><<<ngrid, 256, 0, mesh->stream>>>(
+        spread_nodes_kernel<double><<<ngrid, nblock, 0, mesh->stream>>>(
             g, cell_start, (const double *)mesh->spread_scratch, (double *)F, accumulate);
     } else if (prec == FSI_DF64) {
         spread_cells_kernel<df64><<<cgrid, 256, 0, mesh->stream>>>(
             E, (const double *)xi, cell_start, perm, (const double *)lam, (const double *)w,
             (df64 *)mesh->spread_scratch);
         FSI_TRY(check_launch("spread cells kernel"));
-        spread_nodes_kernel<df64><<<ngrid, 256, 0, mesh->stream>>>(
+        spread_nodes_kernel<df64><<<ngrid, nblock, 0, mesh->stream>>>(
             g, cell_start, (const df64 *)mesh->spread_scratch, (double *)F, accumulate);
     } else {
         spread_cells_kernel<float><<<cgrid, 256, 0, mesh->stream>>>(
             E, (const float *)xi, cell_start, perm, (const float *)lam, (const float *)w,
             (float *)mesh->spread_scratch);
         FSI_TRY(check_launch("spread cells kernel"));
-        spread_nodes_kernel<float><<<ngrid, 256, 0, mesh->stream>>>(
+        spread_nodes_kernel<float><<<ngrid, nblock, 0, mesh->stream>>>(
             g, cell_start, (const float *)mesh->spread_scratch, (float *)F, accumulate);
     }
     return check_launch("spread nodes kernel");

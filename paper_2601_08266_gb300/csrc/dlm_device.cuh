@@ -331,8 +331,42 @@ template <typename T> __device__ __forceinline__ T shape_1d(T xi, int side)
     return side ? (T(1) + xi) : (T(1) - xi);
 }
 
-// Interpolation for one point b (u = C^T V, Eq. nodal_solid_velo) by two
-// adjacent lanes of a warp: lane ax (= lane & 1) sums the 4 nodes of the
+// Interpolation for one point b (u = C^T V, Eq. nodal_solid_velo) by one
+// lane (the double-float and FP64 kernels: issue-bound, so no work is
+// duplicated).  T is the compute type; xi, U and u are in StorageOf<T>.
+template <typename T>
+__device__ __forceinline__ void interp_point(
+    const GridArgs &g, int64_t b, const int32_t *__restrict__ elem,
+    const typename StorageOf<T>::type *__restrict__ xi,
+    const vec4<typename StorageOf<T>::type> *__restrict__ U,
+    typename StorageOf<T>::type *__restrict__ u)
+{
+    const int NX1 = g.Nx + 1, NXY1 = (g.Nx + 1) * (g.Ny + 1);
+    const int E = g.Nx * g.Ny * g.Nz;
+    const int e = elem[b];
+    T ux = T(0), uy = T(0), uz = T(0);
+    if (e >= 0 && e < E) {
+        const int ex = e % g.Nx, ey = (e / g.Nx) % g.Ny, ez = e / (g.Nx * g.Ny);
+        const T x0 = to_c<T>(xi[3 * b]), x1 = to_c<T>(xi[3 * b + 1]),
+                x2 = to_c<T>(xi[3 * b + 2]);
+        const int n0 = ex + NX1 * ey + NXY1 * ez;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+            const T Na = shape_1d(x0, ax) * shape_1d(x1, ay) * shape_1d(x2, az) * T(0.125f);
+            const auto v = ld4(U + n0 + ax + NX1 * ay + NXY1 * az);
+            ux = madd(Na, to_c<T>(v.x), ux);
+            uy = madd(Na, to_c<T>(v.y), uy);
+            uz = madd(Na, to_c<T>(v.z), uz);
+        }
+    }
+    u[3 * b] = to_s(ux);
+    u[3 * b + 1] = to_s(uy);
+    u[3 * b + 2] = to_s(uz);
+}
+
+// The same by two adjacent lanes of a warp (the FP32 kernels: bound by the
+// number of memory lines their node loads touch): lane ax (= lane & 1) sums the 4 nodes of the
 // element with x-offset ax (in a = 2 (ay + 2 az) + ax order), so that the two
 // lanes' loads of an x-adjacent node pair fall in one memory line; the ax = 0
 // lane adds the other half and writes u.  Every lane of the warp calls this
@@ -431,17 +465,8 @@ __device__ __forceinline__ void spread_cells_segment(
         T acc[24];
 #pragma unroll
         for (int k = 0; k < 24; ++k) acc[k] = T(0);
-        if (group) {
-            // two points per trip: both perm entries are read before either
-            // point's inputs, the accumulation order stays p, p+4, p+8, ...
-            int p = lo + (lane & 3);
-            for (; p + 4 < hi; p += 8) {
-                const int b0 = perm[p], b1 = perm[p + 4];
-                spread_accumulate<T>(b0, xi, lam, w, acc);
-                spread_accumulate<T>(b1, xi, lam, w, acc);
-            }
-            if (p < hi) spread_accumulate<T>(perm[p], xi, lam, w, acc);
-        }
+        if (group)
+            for (int p = lo + (lane & 3); p < hi; p += 4) spread_accumulate<T>(perm[p], xi, lam, w, acc);
         const bool b1 = lane & 2, b0 = lane & 1;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
@@ -508,113 +533,58 @@ __device__ __forceinline__ void spread_cells_segment(
     }
 }
 
-// Spreading, pass 2: every node sums the corner sums of its (up to 8)
-// occupied cells in a fixed order.
+// Spreading, pass 2: node (i, j, k) sums the corner sums of its (up to 8)
+// occupied cells in a fixed order (c = 0..7, cx fastest).  The node is
+// corner (cx, cy, cz) of cell (i - cx, j - cy, k - cz); the two cells of a
+// row pair (i - 1, i) are tested with three cell-table entries.
 template <typename T>
-__device__ __forceinline__ void spread_node(const GridArgs &g, int node,
+__device__ __forceinline__ void spread_node(const GridArgs &g, int i, int j, int k,
                                             const int32_t *__restrict__ start,
                                             const T *__restrict__ S,
                                             typename StorageOf<T>::type *__restrict__ F,
                                             int accumulate)
 {
-    const int NX1 = g.Nx + 1, NY1 = g.Ny + 1;
-    {
-        const int i = node % NX1, j = (node / NX1) % NY1, k = node / (NX1 * NY1);
-        T fx = T(0), fy = T(0), fz = T(0);
-        bool touched = false;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            // this node is local corner (cx,cy,cz) of cell (i-cx, j-cy, k-cz)
-            const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
-            const int ex = i - cx, ey = j - cy, ez = k - cz;
-            if (ex < 0 || ey < 0 || ez < 0 || ex >= g.Nx || ey >= g.Ny || ez >= g.Nz) continue;
-            const int cell = ex + g.Nx * (ey + g.Ny * ez);
-            if (start[cell + 1] == start[cell]) continue;
-            const T *sc = S + (size_t)cell * 24 + 3 * c;
-            fx = fx + sc[0];
-            fy = fy + sc[1];
-            fz = fz + sc[2];
-            touched = true;
-        }
-        auto *o = F + 4 * (size_t)node;
-        if (accumulate) {
-            if (touched) {
-                o[0] = to_s(to_c<T>(o[0]) + fx);
-                o[1] = to_s(to_c<T>(o[1]) + fy);
-                o[2] = to_s(to_c<T>(o[2]) + fz);
-            }
-        } else {
-            o[0] = to_s(fx);
-            o[1] = to_s(fy);
-            o[2] = to_s(fz);
-        }
-    }
-}
-
-// Spreading, pass 2, for four consecutive nodes i0 .. i0+3 of the x-row
-// (j, k) (quad q of the rows' ceil((Nx+1)/4) quads): the occupancy of the
-// 5 x 2 x 2 cells around them is read once from the cell table (at most 24
-// entries instead of 64 for four spread_node calls), then every node adds the
-// corner sums of its occupied cells in spread_node's order, so the results
-// are bitwise those of spread_node.
-template <typename T>
-__device__ __forceinline__ void spread_node_quad(const GridArgs &g, int64_t q,
-                                                 const int32_t *__restrict__ start,
-                                                 const T *__restrict__ S,
-                                                 typename StorageOf<T>::type *__restrict__ F,
-                                                 int accumulate)
-{
-    const int NX1 = g.Nx + 1, NY1 = g.Ny + 1;
-    const int nq = (NX1 + 3) >> 2;
-    const int i0 = (int)(q % nq) * 4;
-    const int64_t row = q / nq;
-    const int j = (int)(row % NY1), k = (int)(row / NY1);
-    // occ[cy + 2 cz] bit (ex - i0 + 1): cell (ex, j - cy, k - cz) holds points
-    unsigned occ[4];
+    bool occ[8];
 #pragma unroll
     for (int rc = 0; rc < 4; ++rc) {
-        occ[rc] = 0u;
         const int ey = j - (rc & 1), ez = k - (rc >> 1);
+        occ[2 * rc] = occ[2 * rc + 1] = false;
         if (ey < 0 || ez < 0 || ey >= g.Ny || ez >= g.Nz) continue;
-        const int lo = i0 > 0 ? i0 - 1 : 0, hi = i0 + 3 < g.Nx - 1 ? i0 + 3 : g.Nx - 1;
-        const int32_t *st = start + (size_t)g.Nx * (ey + (size_t)g.Ny * ez);
-        int prev = st[lo];
-        for (int ex = lo; ex <= hi; ++ex) {
-            const int nxt = st[ex + 1];
-            if (nxt > prev) occ[rc] |= 1u << (ex - i0 + 1);
-            prev = nxt;
-        }
+        // a row of cells without points (most rows, for thin leaflets) is
+        // skipped on two entries that every node of the row reads alike
+        const int32_t *row = start + (size_t)g.Nx * (ey + (size_t)g.Ny * ez);
+        if (row[g.Nx] == row[0]) continue;
+        // st[0] = start of cell i of the row (for i = Nx the entry after the
+        // row's last cell, still inside the table's E + 1 entries)
+        const int32_t *st = row + i;
+        const int s0 = st[0];
+        if (i < g.Nx) occ[2 * rc] = st[1] > s0;      // cell i     (cx = 0)
+        if (i > 0) occ[2 * rc + 1] = s0 > st[-1];    // cell i - 1 (cx = 1)
     }
+    T fx = T(0), fy = T(0), fz = T(0);
+    bool touched = false;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const int i = i0 + t;
-        if (i >= NX1) break;
-        T fx = T(0), fy = T(0), fz = T(0);
-        bool touched = false;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int cx = c & 1, rc = c >> 1;
-            const int ex = i - cx;
-            if (ex < 0 || ex >= g.Nx || !((occ[rc] >> (ex - i0 + 1)) & 1u)) continue;
-            const int cell = ex + g.Nx * ((j - (rc & 1)) + g.Ny * (k - (rc >> 1)));
-            const T *sc = S + (size_t)cell * 24 + 3 * c;
-            fx = fx + sc[0];
-            fy = fy + sc[1];
-            fz = fz + sc[2];
-            touched = true;
+    for (int c = 0; c < 8; ++c) {
+        if (!occ[c]) continue;
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+        const int cell = (i - cx) + g.Nx * ((j - cy) + g.Ny * (k - cz));
+        const T *sc = S + (size_t)cell * 24 + 3 * c;
+        fx = fx + sc[0];
+        fy = fy + sc[1];
+        fz = fz + sc[2];
+        touched = true;
+    }
+    auto *o = F + 4 * ((size_t)i + (size_t)(g.Nx + 1) * (j + (size_t)(g.Ny + 1) * k));
+    if (accumulate) {
+        if (touched) {
+            o[0] = to_s(to_c<T>(o[0]) + fx);
+            o[1] = to_s(to_c<T>(o[1]) + fy);
+            o[2] = to_s(to_c<T>(o[2]) + fz);
         }
-        auto *o = F + 4 * ((size_t)row * NX1 + i);
-        if (accumulate) {
-            if (touched) {
-                o[0] = to_s(to_c<T>(o[0]) + fx);
-                o[1] = to_s(to_c<T>(o[1]) + fy);
-                o[2] = to_s(to_c<T>(o[2]) + fz);
-            }
-        } else {
-            o[0] = to_s(fx);
-            o[1] = to_s(fy);
-            o[2] = to_s(fz);
-        }
+    } else {
+        o[0] = to_s(fx);
+        o[1] = to_s(fy);
+        o[2] = to_s(fz);
     }
 }
 

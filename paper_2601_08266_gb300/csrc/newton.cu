@@ -17,7 +17,7 @@
 namespace fsi {
 namespace {
 
-constexpr int kRedGrid = 608;   // fixed partial-sum grid (4 CTAs per SM): deterministic dots
+constexpr int kRedGrid = 456;   // fixed partial-sum grid (3 CTAs per SM): deterministic dots
 constexpr int kRedThreads = 256;
 constexpr int kDotGroup = 8;    // vectors per multi-dot pass
 
@@ -152,7 +152,7 @@ template <> struct DotAcc<float> {
 // (index self_k, when in [k0, k0+cnt), stands for w itself: w . w)
 // (cond, when not null, is a device flag: the kernel does nothing when it is 0)
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) multi_dot_partial_kernel(
+__global__ void __launch_bounds__(kRedThreads, 3) multi_dot_partial_kernel(
     int k0, int cnt, int64_t len4, const vec4<T> *V, int64_t vstride, const vec4<T> *w,
     double *partial, int self_k, const double *cond)
 {
@@ -162,20 +162,40 @@ __global__ void __launch_bounds__(kRedThreads) multi_dot_partial_kernel(
     Acc acc[kDotGroup];
 #pragma unroll
     for (int j = 0; j < kDotGroup; ++j) acc[j] = Acc(0);
-    // one 4-value record per thread and step: the loads of all cnt vectors are
-    // independent, so each thread keeps up to 9 vector loads in flight
+    // one 4-value record per thread and step: all cnt + 1 vector loads are
+    // issued before the first product (up to 9 loads in flight per thread;
+    // with the products between the loads, the loads waited one by one)
+    // (FP64 vectors, twice the registers per record and bound by the FP64
+    // pipe, keep the loads next to their products)
     GRID_STRIDE(i, len4)
     {
         const vec4<T> wi = ld4(w + i);
+        if constexpr (sizeof(T) == 4) {
+            vec4<T> v[kDotGroup];
 #pragma unroll
-        for (int j = 0; j < kDotGroup; ++j)
-            if (j < cnt) {
-                const vec4<T> v = k0 + j == self_k ? wi : ld4(V + (int64_t)(k0 + j) * vstride + i);
-                dot_acc(acc[j], v.x, wi.x);
-                dot_acc(acc[j], v.y, wi.y);
-                dot_acc(acc[j], v.z, wi.z);
-                dot_acc(acc[j], v.w, wi.w);
-            }
+            for (int j = 0; j < kDotGroup; ++j)
+                if (j < cnt)
+                    v[j] = ld4((k0 + j == self_k ? w : V + (int64_t)(k0 + j) * vstride) + i);
+#pragma unroll
+            for (int j = 0; j < kDotGroup; ++j)
+                if (j < cnt) {
+                    dot_acc(acc[j], v[j].x, wi.x);
+                    dot_acc(acc[j], v[j].y, wi.y);
+                    dot_acc(acc[j], v[j].z, wi.z);
+                    dot_acc(acc[j], v[j].w, wi.w);
+                }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kDotGroup; ++j)
+                if (j < cnt) {
+                    const vec4<T> v =
+                        k0 + j == self_k ? wi : ld4(V + (int64_t)(k0 + j) * vstride + i);
+                    dot_acc(acc[j], v.x, wi.x);
+                    dot_acc(acc[j], v.y, wi.y);
+                    dot_acc(acc[j], v.z, wi.z);
+                    dot_acc(acc[j], v.w, wi.w);
+                }
+        }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
