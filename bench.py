@@ -53,13 +53,14 @@ SEED = 2026
 LAUNCHES_PER_STEP = 12
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused native FP64
 # residual + Jacobian launch on the 64^3 workload (4x4x4 bricks, 128
-# threads: brick 26.43 + 0.20 MB, gather 32.79 + 0.04 MB), from one ncu
+# threads: brick 26.43 + 0.35 MB, gather 32.79 + 0.06 MB), from one ncu
 # capture with a cache flush between the two kernels
-TRAFFIC_FUSED_F64_64 = {(4, 4, 4, 128): 26_429_952 + 204_800 + 32_786_176 + 39_680}
+# (profiles/vms_fused_f64_64cubed_ncu.md)
+TRAFFIC_FUSED_F64_64 = {(4, 4, 4, 128): 26_427_136 + 353_280 + 32_786_176 + 58_112}
 # FP64 operations the fused FP64 brick kernel executes per element (ncu,
-# same capture: DFMA 1,712 (x2), DMUL 1,368, DADD 1,070): context for the
+# same capture: DFMA 1,808 (x2), DMUL 1,232, DADD 950): context for the
 # roofline, whose achieved rate counts the oracle's operations
-KERNEL_FP64_FLOPS_PER_ELEM = 2 * 1712 + 1368 + 1070
+KERNEL_FP64_FLOPS_PER_ELEM = 2 * 1808 + 1232 + 950
 
 
 def dist_env():

@@ -394,18 +394,19 @@ __global__ void interp_kernel(int64_t m, GridArgs g, const int32_t *__restrict__
 // (see spread_cells_segment).
 // T is the compute type (double, float or double-float); xi, lam, w and F are
 // in its storage type, the corner sums S in T.
-template <typename T>
+// (SQ: w N^2 dsq instead of w N lambda, see spread_accumulate)
+template <typename T, bool SQ = false>
 __global__ void spread_cells_kernel(int64_t E, const typename StorageOf<T>::type *__restrict__ xi,
                                     const int32_t *__restrict__ start,
                                     const int32_t *__restrict__ perm,
                                     const typename StorageOf<T>::type *__restrict__ lam,
                                     const typename StorageOf<T>::type *__restrict__ w,
-                                    T *__restrict__ S)
+                                    T *__restrict__ S, T dsq = T(0))
 {
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c0 = warp * kSpreadSeg; c0 < E; c0 += nwarps * kSpreadSeg)
-        spread_cells_segment<T>(E, c0, xi, start, perm, lam, w, S);
+        spread_cells_segment<T, SQ>(E, c0, xi, start, perm, lam, w, S, dsq);
 }
 
 // Spreading, pass 2: every node sums the corner sums of its occupied cells.
@@ -542,6 +543,33 @@ fsi_status build_cell_table(cudaStream_t s, int64_t E, int64_t m, const int32_t 
     }
     return FSI_OK;
 }
+
+template <typename T>
+fsi_status spread_mass_diag(fsi_mesh *mesh, int64_t m, const T *xi, const int32_t *cell_start,
+                            const int32_t *perm, const T *w, double dsq, T *F)
+{
+    (void)m;  // the cell table lists the points
+    FSI_DEVICE(mesh->device);
+    const GridArgs g = grid_args(mesh);
+    const int64_t E = mesh->n_elems;
+    FSI_TRY(ensure_spread_scratch(mesh, (size_t)E * 24 * sizeof(T)));
+    const int cgrid = blocks_for((E + kSpreadSeg - 1) / kSpreadSeg * 32, 256, sm_count() * 64);
+    spread_cells_kernel<T, true><<<cgrid, 256, 0, mesh->stream>>>(
+        E, xi, cell_start, perm, nullptr, w, (T *)mesh->spread_scratch, (T)dsq);
+    FSI_TRY(check_launch("spread cells kernel"));
+    const dim3 nblock(32, 8);
+    const dim3 ngrid((g.Nx + 32) / 32, std::min((g.Ny + 8) / 8, 65535), std::min(g.Nz + 1, 65535));
+    if ((g.Ny + 8) / 8 > 65535)
+        return set_error(FSI_ERR_ARG, "spreading: more than 524,280 nodes along y");
+    spread_nodes_kernel<T><<<ngrid, nblock, 0, mesh->stream>>>(g, cell_start,
+                                                              (const T *)mesh->spread_scratch, F, 0);
+    return check_launch("spread nodes kernel");
+}
+template fsi_status spread_mass_diag<float>(fsi_mesh *, int64_t, const float *, const int32_t *,
+                                            const int32_t *, const float *, double, float *);
+template fsi_status spread_mass_diag<double>(fsi_mesh *, int64_t, const double *,
+                                             const int32_t *, const int32_t *, const double *,
+                                             double, double *);
 
 }  // namespace fsi
 

@@ -411,20 +411,29 @@ __device__ __forceinline__ void interp_point_pair(
 }
 
 // Corner contributions w_B N_a(xi_B) lambda_B of one point B added to acc
-// (T the compute type; inputs in StorageOf<T>).
-template <typename T>
+// (T the compute type; inputs in StorageOf<T>).  SQ: w_B N_a(xi_B)^2 dsq
+// instead (lam unused): the diagonal of C W C^T scaled by dsq.
+template <typename T, bool SQ = false>
 __device__ __forceinline__ void spread_accumulate(
     int b, const typename StorageOf<T>::type *__restrict__ xi,
     const typename StorageOf<T>::type *__restrict__ lam,
-    const typename StorageOf<T>::type *__restrict__ w, T (&acc)[24])
+    const typename StorageOf<T>::type *__restrict__ w, T (&acc)[24], T dsq = T(0))
 {
     const T x0 = to_c<T>(xi[3 * b]), x1 = to_c<T>(xi[3 * b + 1]), x2 = to_c<T>(xi[3 * b + 2]);
     const T s = w ? to_c<T>(w[b]) * T(0.125f) : T(0.125f);
-    const T l0 = to_c<T>(lam[3 * b]), l1 = to_c<T>(lam[3 * b + 1]), l2 = to_c<T>(lam[3 * b + 2]);
+    T l0, l1, l2;
+    if constexpr (SQ) {
+        l0 = l1 = l2 = dsq;
+    } else {
+        l0 = to_c<T>(lam[3 * b]);
+        l1 = to_c<T>(lam[3 * b + 1]);
+        l2 = to_c<T>(lam[3 * b + 2]);
+    }
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-        const T Na = shape_1d(x0, a & 1) * shape_1d(x1, (a >> 1) & 1) *
-                     shape_1d(x2, (a >> 2) & 1) * s;
+        const T sh = shape_1d(x0, a & 1) * shape_1d(x1, (a >> 1) & 1) * shape_1d(x2, (a >> 2) & 1);
+        // N_a = sh / 8: w N_a = sh s, w N_a^2 = sh s (sh / 8)
+        const T Na = SQ ? sh * s * (sh * T(0.125f)) : sh * s;
         acc[3 * a] = madd(Na, l0, acc[3 * a]);
         acc[3 * a + 1] = madd(Na, l1, acc[3 * a + 1]);
         acc[3 * a + 2] = madd(Na, l2, acc[3 * a + 2]);
@@ -445,12 +454,12 @@ __device__ __forceinline__ void spread_accumulate(
 constexpr int kSpreadSeg = 8;
 constexpr int kGroupCell = 128;
 
-template <typename T>
+template <typename T, bool SQ = false>
 __device__ __forceinline__ void spread_cells_segment(
     int64_t E, int64_t c0, const typename StorageOf<T>::type *__restrict__ xi,
     const int32_t *__restrict__ start, const int32_t *__restrict__ perm,
     const typename StorageOf<T>::type *__restrict__ lam,
-    const typename StorageOf<T>::type *__restrict__ w, T *__restrict__ S)
+    const typename StorageOf<T>::type *__restrict__ w, T *__restrict__ S, T dsq = T(0))
 {
     const int lane = threadIdx.x & 31;
     const int64_t myc = c0 + (lane >> 2);
@@ -466,7 +475,7 @@ __device__ __forceinline__ void spread_cells_segment(
 #pragma unroll
         for (int k = 0; k < 24; ++k) acc[k] = T(0);
         if (group)
-            for (int p = lo + (lane & 3); p < hi; p += 4) spread_accumulate<T>(perm[p], xi, lam, w, acc);
+            for (int p = lo + (lane & 3); p < hi; p += 4) spread_accumulate<T, SQ>(perm[p], xi, lam, w, acc, dsq);
         const bool b1 = lane & 2, b0 = lane & 1;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
@@ -496,7 +505,7 @@ __device__ __forceinline__ void spread_cells_segment(
         T acc[24];
 #pragma unroll
         for (int k = 0; k < 24; ++k) acc[k] = T(0);
-        for (int p = plo + lane; p < phi; p += 32) spread_accumulate<T>(perm[p], xi, lam, w, acc);
+        for (int p = plo + lane; p < phi; p += 32) spread_accumulate<T, SQ>(perm[p], xi, lam, w, acc, dsq);
         // each level halves the values a lane carries (12, 6, 3), then a
         // butterfly over the last two bits
         const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;

@@ -208,6 +208,19 @@ fsi_status mlp_predict_tc(cudaStream_t s, int device, const fsi_grid &g, int64_t
 
 // the coupled Jacobian (newton.cu) at st->y applied to k FP32 vectors after
 // one linearisation; used by the learned guess's fitted predictor
+// Nodal diagonal blocks of the VMS Jacobian at (U, A, f) on the uniform
+// grid (diag.cu): blocks [n][4][4] row-major in the compute type (FSI_F64 or
+// FSI_F32 arrays), rows and columns 0..ncols-1 (3: velocity, 4: with
+// pressure) overwritten, the rest zero.  Mesh's stream.
+fsi_status vms_diag_blocks(fsi_mesh *m, fsi_prec prec, int ncols, const void *U, const void *A,
+                           const void *f, void *blocks);
+
+// F[a].xyz = dsq sum_B w_B N_a(xi_B)^2 (the diagonal of C W C^T scaled by
+// dsq; dlm.cu), over the points of the cell table, deterministic.
+template <typename T>
+fsi_status spread_mass_diag(fsi_mesh *mesh, int64_t m, const T *xi, const int32_t *cell_start,
+                            const int32_t *perm, const T *w, double dsq, T *F);
+
 fsi_status coupled_jacobian_f32(fsi_mesh *mesh, const fsi_step_state *st, int k,
                                 const float *const *x, float *const *Jx);
 

@@ -367,6 +367,27 @@ __global__ void probe_extract_kernel(int n, int NX1, int NY1, const int32_t *col
         for (int r = 0; r < 4; ++r) blocks[16 * node + 4 * r + comp] = Jx[4 * node + r];
 }
 
+// Direct diagonal blocks, last step: the point masses' diagonal
+// (cpl[node].x = D sum_B w_B N_a(xi_B)^2, or null) on the velocity diagonal,
+// then the Dirichlet rows (mask) as unit rows, like the Jacobian's.
+template <typename T>
+__global__ void diag_finish_kernel(int64_t n, int ncols, const vec4<T> *cpl, const uint8_t *mask,
+                                   T *blocks)
+{
+    GRID_STRIDE(node, n)
+    {
+        T *b = blocks + 16 * node;
+        if (cpl) {
+            const T d = cpl[node].x;
+            for (int r = 0; r < 3; ++r) b[5 * r] += d;
+        }
+        if (mask)
+            for (int r = 0; r < ncols; ++r)
+                if (mask[4 * node + r])
+                    for (int c = 0; c < ncols; ++c) b[4 * r + c] = r == c ? T(1) : T(0);
+    }
+}
+
 // 4x4 inverse per node, Gauss-Jordan with partial pivoting in FP64; a
 // singular block is replaced by the identity (no preconditioning there).
 template <typename T> __global__ void block_invert_kernel(int n, const T *blocks, T *inv)
@@ -768,6 +789,24 @@ fsi_status build_block_jacobi(fsi_mesh *mesh, const fsi_step_state *st, int prec
     int ncolors = 8;
     const int32_t *colors = nullptr;
     if (mesh->tet) colors = tet_colors(mesh->tet, &ncolors);
+    // uniform grid without a hyperelastic body: the blocks from their
+    // definition (diag.cu), the point masses' diagonal by a squared spread;
+    // otherwise by probing the coupled Jacobian
+    const bool direct = !mesh->tet && !mesh->coords64 && !(st->m > 0 && st->body);
+    if (direct) {
+        FSI_TRY(vms_diag_blocks(mesh, prec_of<T>(), ncomp, W.Uw, W.Aw, st->f ? W.fw : nullptr,
+                                W.blocks));
+        const vec4<T> *cpl = nullptr;
+        if (st->m > 0) {
+            const double D = st->drho_s + st->k_s * mesh->gamma * mesh->phys.dt * mesh->phys.dt;
+            FSI_TRY(spread_mass_diag<T>(mesh, st->m, (const T *)W.xiw, st->cell_start, st->perm,
+                                        st->w ? (const T *)W.ww : nullptr, D, (T *)W.ftmp));
+            cpl = (const vec4<T> *)W.ftmp;
+        }
+        diag_finish_kernel<T><<<grid1d(n), 256, 0, s>>>(n, ncomp, cpl, st->mask, (T *)W.blocks);
+        FSI_TRY(check_launch("diagonal blocks finish"));
+        ncolors = 0;  // no probing
+    }
     for (int color = 0; color < ncolors; ++color)
         for (int comp = 0; comp < ncomp; ++comp) {
             probe_fill_kernel<T><<<grid1d(n), 256, 0, s>>>(n, NX1, NY1, colors, color, comp, px);
