@@ -1587,12 +1587,23 @@ def profile_case(args):
     and double-float interpolation and spreading, twice, on the --grid grid
     with --points leaflet points; 'blas1' runs the Krylov multi-dot and
     multi-update kernels twice each on 8 FP32 vectors of the --grid grid's
-    4 (N+1)^3 entries."""
+    4 (N+1)^3 entries; 'pmg' runs two FP32 pressure V-cycles on the --grid
+    grid (no eliminated faces)."""
     import torch
     import paper_2601_08266_gb300 as fsi
     from paper_2601_08266_gb300 import inputs
     dev = torch.device("cuda:0")
     N = args.grid
+    if args.profile_case == "pmg":
+        mesh = fsi.Mesh(N, device=0)
+        bp = torch.randn(mesh.n_nodes, dtype=torch.float32, device=dev)
+        xp = torch.empty_like(bp)
+        for _ in range(2):
+            fsi.fsi_pressure_vcycle(mesh, bp, xp)
+        torch.cuda.synchronize()
+        mesh.close()
+        print(json.dumps({"profile_case": "pmg", "grid": N, "ok": True}))
+        return 0
     if args.profile_case == "blas1":
         from paper_2601_08266_gb300 import _binding as B
         B.fsi_measure_blas1(0, fsi.FSI_F32, 4 * (N + 1) ** 3, 8, reps=1)
@@ -1674,7 +1685,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--batch-tune-f64", action="store_true")
-    ap.add_argument("--profile-case", choices=["vms_f64", "dlm", "blas1"], default=None,
+    ap.add_argument("--profile-case", choices=["vms_f64", "dlm", "blas1", "pmg"], default=None,
                     help="run one small fixed case for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile_case:

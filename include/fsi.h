@@ -686,23 +686,28 @@ fsi_status fsi_mlp_predict(fsi_mlp *mlp, fsi_mesh *mesh, const float *params,
  *     y = y_fb + alpha e + beta c_v + gamma c_p
  * around the fallback y_fb (fallback 0: y_n, the zero increment; 1: y_n + e),
  * all Dirichlet rows (st->mask) held at st->yD: the coefficients minimise
- * |R(y_fb) + J (alpha e + beta c_v + gamma c_p)|, R the coupled residual
- * (fsi_coupled_residual) of y_fb in judge_prec and J its Jacobian at y_fb
+ * |R(y_fb) + J (alpha e + beta c_v + gamma c_p)|, R the coupled residual of
+ * y_fb (its VMS part in FP32 from the FP32 linearisation, the coupling and
+ * the Dirichlet rows double-float: the fit needs R far better than the
+ * reduction a predictor brings, not to FP64) and J its Jacobian at y_fb
  * applied in FP32 (fsi_coupled_jacobian_apply; R is close to linear in y
  * over a predictor's error), by the 3 x 3 normal equations in FP64 (a
  * direction that adds nothing is dropped).  The family holds both
  * fallbacks (alpha = 0 or 1 from y_n) and the network's own predictor, so the
  * fit is at least as good as each of them in the linear model.  The
  * candidate's residual is then evaluated in judge_prec, and st->y keeps the
- * candidate if its residual norm is below the fallback's, else y_fb.  Cost:
- * two residuals, three FP32 Jacobian applies and the network.  judge_prec:
+ * candidate if its norm is below the fallback's (r_fallback), else y_fb.
+ * Cost: the network, one FP32 linearisation with the FP32 residual and three
+ * FP32 Jacobian applies, and the candidate's residual in judge_prec (which a
+ * Newton step can take as its first, fsi_newton_opts.R0; when the fallback
+ * is kept, its residual in judge_prec is evaluated instead).  judge_prec:
  * FSI_F64 or FSI_DF64.  work: caller-owned FP64 device array [5][n][4]; on
- * return work[0..n) x 4 holds R(st->y) in judge_prec, the residual that
- * judged the returned predictor, for fsi_newton_opts.R0.
+ * return work[0..n) x 4 holds R(st->y) in judge_prec, for
+ * fsi_newton_opts.R0.
  * yn [n][4] is y_n (must not alias st->y).  Synchronises; a tensor-core wait
  * that ran out in this or an earlier call of the handle is FSI_ERR_TIMEOUT. */
 typedef struct {
-    double r_fallback;   /* ||R(y_fb)||_2, judge_prec                               */
+    double r_fallback;   /* ||R(y_fb)||_2, the fit's residual (VMS part FP32)      */
     double r_learned;    /* the linear model's ||R|| at the network's own predictor */
     double r_combined;   /* ||R(y_c)||_2 of the fitted candidate, judge_prec         */
     double a_velocity, b_pressure, c_extrapolant;  /* beta, gamma, alpha            */

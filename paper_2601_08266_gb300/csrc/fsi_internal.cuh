@@ -221,8 +221,11 @@ template <typename T>
 fsi_status spread_mass_diag(fsi_mesh *mesh, int64_t m, const T *xi, const int32_t *cell_start,
                             const int32_t *perm, const T *w, double dsq, T *F);
 
+// the checks fsi_newton_step makes of a step state (newton.cu)
+fsi_status validate_step_state(const fsi_mesh *mesh, const fsi_step_state *st);
+
 fsi_status coupled_jacobian_f32(fsi_mesh *mesh, const fsi_step_state *st, int k,
-                                const float *const *x, float *const *Jx);
+                                const float *const *x, float *const *Jx, double *R_fit = nullptr);
 
 // VMS operators (vms.cu)
 fsi_status vms_residual(fsi_mesh *m, fsi_prec prec, const void *U, const void *A,

@@ -490,6 +490,7 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
     if (judge_prec != FSI_F64 && judge_prec != FSI_DF64)
         return set_error(FSI_ERR_ARG, "judge_prec must be FSI_F64 or FSI_DF64");
     if (st->y == yn) return set_error(FSI_ERR_ARG, "st->y must not alias yn");
+    FSI_TRY(validate_step_state(mesh, st));
     FSI_DEVICE(mesh->device);
     cudaStream_t s = mesh->stream;
     const int64_t n4 = 4 * mesh->n_nodes;
@@ -507,16 +508,17 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
         apply_dirichlet_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->mask, st->yD, st->y);
         FSI_TRY(check_launch("dirichlet kernel"));
     }
-    // the fallback's residual, and J at y_fb applied to e, c_v, c_p (FP32,
-    // one linearisation)
-    FSI_TRY(fsi_coupled_residual(mesh, judge_prec, st, Rfb));
+    // one FP32 linearisation at y_fb: the fallback's residual for the fit
+    // (its VMS part in FP32: the fit needs it to far less than the 1e-3 of
+    // ||R|| that a predictor gains; coupling and Dirichlet rows double-float)
+    // and J applied to e, c_v, c_p
     for (int i = 0; i < 3; ++i)
         direction_kernel<<<blocks(n4), 256, 0, s>>>(n4, i, ml, yn, d1, d2, st->mask, dir + i * n4);
     FSI_TRY(check_launch("direction kernel"));
     {
         const float *xs[3] = {dir, dir + n4, dir + 2 * n4};
         float *js[3] = {Jd, Jd + n4, Jd + 2 * n4};
-        FSI_TRY(coupled_jacobian_f32(mesh, st, 3, xs, js));
+        FSI_TRY(coupled_jacobian_f32(mesh, st, 3, xs, js, Rfb));
     }
     // normal equations G x = -r of min |R_fb + sum_i x_i J d_i|
     fit_dots_kernel<<<kFitBlocks, 256, 0, s>>>(n4, Jd, Jd + n4, Jd + 2 * n4, Rfb,
@@ -599,10 +601,13 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
     if (rep->used == 2)
         FSI_CUDA(cudaMemcpyAsync(st->y, cand, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s),
                  "memcpy");
-    // the judged residual of the returned predictor, for the Newton step
-    FSI_CUDA(cudaMemcpyAsync(work, rep->used == 2 ? Rc : Rfb, n4 * sizeof(double),
-                             cudaMemcpyDeviceToDevice, s),
-             "memcpy");
+    // the judged residual of the returned predictor, for the Newton step (the
+    // fallback's in judge_prec when it is kept)
+    if (rep->used == 2)
+        FSI_CUDA(cudaMemcpyAsync(work, Rc, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s),
+                 "memcpy");
+    else
+        FSI_TRY(fsi_coupled_residual(mesh, judge_prec, st, work));
     FSI_CUDA(cudaStreamSynchronize(s), "sync");
     return take_tc_error(h);
 }

@@ -325,12 +325,23 @@ __global__ void add_if_kernel(int n, const double *x, double *y, const double *c
 
 // y = x / *den (0 when the norm vanished: lucky breakdown), in the vector's
 // own precision (the scale is rounded once; GB300's FP64 unit is ~70x slower)
+// (len a multiple of 4: one 4-value record per thread and step)
 template <typename T>
 __global__ void scale_by_inv_kernel(int64_t len, const double *den, const T *x, T *y)
 {
     const double d = *den;
     const T s = (T)(d > 0.0 ? 1.0 / d : 0.0);
-    GRID_STRIDE(i, len) y[i] = x[i] * s;
+    const vec4<T> *x4 = (const vec4<T> *)x;
+    vec4<T> *y4 = (vec4<T> *)y;
+    GRID_STRIDE(i, len / 4)
+    {
+        vec4<T> v = ld4(x4 + i);
+        v.x *= s;
+        v.y *= s;
+        v.z *= s;
+        v.w *= s;
+        y4[i] = v;
+    }
 }
 
 // ------------------------------------------------------------ block Jacobi
@@ -527,11 +538,18 @@ __global__ void schur_split_kernel(int n, const T *inv, const T *v, T *z, T *bp)
 {
     GRID_STRIDE(node, n)
     {
-        const T x0 = v[4 * node], x1 = v[4 * node + 1], x2 = v[4 * node + 2];
-        const T *M = inv + 16 * node;
-        for (int r = 0; r < 3; ++r)
-            z[4 * node + r] = M[4 * r] * x0 + M[4 * r + 1] * x1 + M[4 * r + 2] * x2;
-        bp[node] = v[4 * node + 3];
+        // vector loads of the node record and the block's three rows; z's
+        // pressure slot is written by schur_merge_kernel afterwards
+        const vec4<T> x = ld4((const vec4<T> *)v + node);
+        const vec4<T> *M = (const vec4<T> *)(inv + 16 * node);
+        vec4<T> zr;
+        const vec4<T> m0 = ld4(M), m1 = ld4(M + 1), m2 = ld4(M + 2);
+        zr.x = m0.x * x.x + m0.y * x.y + m0.z * x.z;
+        zr.y = m1.x * x.x + m1.y * x.y + m1.z * x.z;
+        zr.z = m2.x * x.x + m2.y * x.y + m2.z * x.z;
+        zr.w = T(0);
+        ((vec4<T> *)z)[node] = zr;
+        bp[node] = x.w;
     }
 }
 
@@ -664,23 +682,15 @@ template <typename T> fsi_prec prec_of() { return sizeof(T) == 8 ? FSI_F64 : FSI
 // FP64 coupled residual at st->y; leaves the FP64 stage in W.U, W.A.
 // prec: FSI_F64 (native FP64) or FSI_DF64 (double-float VMS and coupling
 // arithmetic on FP64 arrays, FP64-accurate to ~1e-14); stage and solid force in FP64
-fsi_status coupled_residual_impl(fsi_mesh *mesh, const fsi_step_state *st, double *R,
-                                 fsi_prec prec = FSI_F64)
+// R += the point masses' spread forces (no hyperelastic body), then the
+// Dirichlet rows R = y - y_D; coupling in prec
+fsi_status point_mass_residual_add(fsi_mesh *mesh, const fsi_step_state *st, double *R,
+                                   fsi_prec prec)
 {
     Work &W = mesh->newton->w;
     cudaStream_t s = mesh->stream;
     const int64_t n = mesh->n_nodes;
-    FSI_TRY(fsi_stage(mesh, FSI_F64, st->y, st->Vn, st->An, st->s, W.U, W.A));
-    FSI_TRY(vms_residual(mesh, prec, W.U, W.A, st->f, R));
-    if (st->m > 0 && st->body) {
-        // hyperelastic body: uddot_{n+1} = C^T Vdot_{n+1} at its nodes, stage
-        // values, nodal residual R^s, spread without weights
-        FSI_TRY(fsi_dlm_interp(mesh, prec, st->m, st->elem, st->xi, st->y, W.pa));
-        FSI_TRY(solid_stage_impl(st->body, st->us, st->vs, st->as, W.pa, W.bu, W.bv, W.ba));
-        FSI_TRY(solid_residual_impl(st->body, W.bu, W.bv, W.ba, st->us, st->g_s, W.prs));
-        FSI_TRY(fsi_dlm_spread(mesh, prec, st->m, st->elem, st->xi, st->cell_start, st->perm,
-                               W.prs, nullptr, R, 1));
-    } else if (st->m > 0) {
+    if (st->m > 0) {
         velocity_next_kernel<<<grid1d(n), 256, 0, s>>>(n, mesh->phys.dt, mesh->gamma, st->y,
                                                       st->Vn, st->An, W.V1);
         FSI_TRY(check_launch("velocity_next kernel"));
@@ -698,6 +708,32 @@ fsi_status coupled_residual_impl(fsi_mesh *mesh, const fsi_step_state *st, doubl
         FSI_TRY(check_launch("dirichlet residual kernel"));
     }
     return FSI_OK;
+}
+
+fsi_status coupled_residual_impl(fsi_mesh *mesh, const fsi_step_state *st, double *R,
+                                 fsi_prec prec = FSI_F64)
+{
+    Work &W = mesh->newton->w;
+    cudaStream_t s = mesh->stream;
+    const int64_t n = mesh->n_nodes;
+    FSI_TRY(fsi_stage(mesh, FSI_F64, st->y, st->Vn, st->An, st->s, W.U, W.A));
+    FSI_TRY(vms_residual(mesh, prec, W.U, W.A, st->f, R));
+    if (st->m > 0 && st->body) {
+        // hyperelastic body: uddot_{n+1} = C^T Vdot_{n+1} at its nodes, stage
+        // values, nodal residual R^s, spread without weights
+        FSI_TRY(fsi_dlm_interp(mesh, prec, st->m, st->elem, st->xi, st->y, W.pa));
+        FSI_TRY(solid_stage_impl(st->body, st->us, st->vs, st->as, W.pa, W.bu, W.bv, W.ba));
+        FSI_TRY(solid_residual_impl(st->body, W.bu, W.bv, W.ba, st->us, st->g_s, W.prs));
+        FSI_TRY(fsi_dlm_spread(mesh, prec, st->m, st->elem, st->xi, st->cell_start, st->perm,
+                               W.prs, nullptr, R, 1));
+        if (st->mask) {
+            dirichlet_residual_kernel<<<grid1d(4 * n), 256, 0, s>>>(4 * n, st->mask, st->y, st->yD,
+                                                                    R);
+            FSI_TRY(check_launch("dirichlet residual kernel"));
+        }
+        return FSI_OK;
+    }
+    return point_mass_residual_add(mesh, st, R, prec);
 }
 
 // Working-precision copies of the linearisation point (after a residual).
@@ -892,7 +928,9 @@ fsi_status host_scalar(fsi_mesh *mesh, const double *dev, double *out)
 
 // out = M^{-1} in: nodal 4x4 block-Jacobi (precond 0), or the block-diagonal
 // Schur-complement preconditioner (precond 1): 3x3 velocity blocks and
-// sigma^{-1} x one pressure V-cycle, sigma = alpha_f gamma dt / (alpha_m rho)
+// sigma^{-1} x one pressure V-cycle, sigma = alpha_f gamma dt / (alpha_m rho);
+// in and out must not alias (the split writes all of out's records before the
+// merge reads in's pressure slots)
 template <typename T>
 fsi_status apply_precond(fsi_mesh *mesh, const fsi_step_state *st, const T *in, T *out)
 {
@@ -1097,15 +1135,27 @@ fsi_status newton_impl(fsi_mesh *mesh, const fsi_newton_opts *o, const fsi_step_
 }  // namespace
 
 // one linearisation at st->y (stage values, and for a hyperelastic body its
-// stage values through the coupled residual), then J x_i for k FP32 vectors
+// stage values through the coupled residual), then J x_i for k FP32 vectors;
+// with R_fit the residual at st->y too: the VMS part in FP32 from the
+// linearisation's FP32 copies, the coupling and the Dirichlet rows
+// double-float (a body's residual entirely double-float)
 fsi_status coupled_jacobian_f32(fsi_mesh *mesh, const fsi_step_state *st, int k,
-                                const float *const *x, float *const *Jx)
+                                const float *const *x, float *const *Jx, double *R_fit)
 {
     FSI_TRY(ensure_work(mesh, st->m, 1));
     Work &W = mesh->newton->w;
-    if (st->m > 0 && st->body) FSI_TRY(coupled_residual_impl(mesh, st, W.R));
+    const bool body = st->m > 0 && st->body;
+    if (body) FSI_TRY(coupled_residual_impl(mesh, st, R_fit ? R_fit : W.R, R_fit ? FSI_DF64 : FSI_F64));
     else FSI_TRY(fsi_stage(mesh, FSI_F64, st->y, st->Vn, st->An, st->s, W.U, W.A));
     FSI_TRY(prepare_linearisation<float>(mesh, st));
+    if (R_fit && !body) {
+        const int64_t n4 = 4 * mesh->n_nodes;
+        float *r32 = (float *)W.z;
+        FSI_TRY(vms_residual(mesh, FSI_F32, W.Uw, W.Aw, st->f ? W.fw : nullptr, r32));
+        cast_kernel<float, double><<<grid1d(n4), 256, 0, mesh->stream>>>(n4, r32, R_fit);
+        FSI_TRY(check_launch("residual cast"));
+        FSI_TRY(point_mass_residual_add(mesh, st, R_fit, FSI_DF64));
+    }
     for (int i = 0; i < k; ++i) FSI_TRY(coupled_jacobian_impl<float>(mesh, st, x[i], Jx[i]));
     return FSI_OK;
 }
@@ -1132,6 +1182,12 @@ fsi_status validate_state(const fsi_mesh *mesh, const fsi_step_state *st)
 }
 
 }  // namespace
+
+fsi_status validate_step_state(const fsi_mesh *mesh, const fsi_step_state *st)
+{
+    return validate_state(mesh, st);
+}
+
 }  // namespace fsi
 
 using namespace fsi;

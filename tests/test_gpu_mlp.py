@@ -278,6 +278,68 @@ def test_learned_guess_end_to_end(fsi, capsys):
     assert newton_l < newton_f, (newton_l, newton_f, rows)
 
 
+@pytest.mark.parametrize("judge", [0, 2])
+def test_guess_contract(fsi, judge):
+    """fsi_mlp_guess on a small coupled state with an untrained network: the
+    returned predictor keeps its Dirichlet rows, r_fallback is the norm of
+    the fallback's residual (its VMS part in FP32: within 1e-5), the kept
+    candidate's judged residual is below it, and work[0] is R(st.y) in the
+    judge's precision bit for bit (what a Newton step takes as opts.R0)."""
+    import torch
+    from oracle import mlp as om
+    from paper_2601_08266_gb300 import inputs
+    N = 8
+    mesh = fsi.Mesh(N, rho=1.0, mu=0.01, dt=0.01, rho_inf=0.5, device=0)
+    n = mesh.n_nodes
+    rng = np.random.default_rng(21)
+    Vn, An = T(rng.normal(size=(n, 4))), T(0.5 * rng.normal(size=(n, 4)))
+    yn = T(rng.normal(size=(n, 4)))
+    d1, d2 = T(0.1 * rng.normal(size=(n, 4))), T(0.1 * rng.normal(size=(n, 4)))
+    mask = np.zeros((n, 4), np.uint8)
+    mask[:40, :3] = 1
+    yD = T(rng.normal(size=(n, 4)))
+    m = 300
+    X = inputs.ball_points(m, seed=22, radius=0.3)
+    e = torch.empty(m, dtype=torch.int32, device="cuda")
+    xi = torch.empty((m, 3), dtype=torch.float64, device="cuda")
+    cs = torch.empty(mesh.n_elems + 1, dtype=torch.int32, device="cuda")
+    pm = torch.empty(m, dtype=torch.int32, device="cuda")
+    fsi.fsi_locate(mesh, T(X), e, xi, cs, pm)
+    y = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+    st = fsi.StepState(y, Vn, An, mask=T(mask), yD=yD, elem=e, xi=xi, cell_start=cs, perm=pm,
+                       w=T(rng.uniform(0.5, 1.5, m) * 1e-3), drho_s=0.5)
+    P = T(om.flatten(om.init_params(4)), torch.float32)
+    f32 = torch.float32
+    h = fsi.Mlp(1024)
+    work = torch.empty((5, n, 4), dtype=torch.float64, device="cuda")
+    rep = fsi.fsi_mlp_guess(h, mesh, P, torch.zeros(112, dtype=f32, device="cuda"),
+                            torch.ones(112, dtype=f32, device="cuda"),
+                            torch.zeros(4, dtype=f32, device="cuda"),
+                            torch.full((4,), 1e-2, dtype=f32, device="cuda"),
+                            st, yn, d1, d2, 0, work, judge_prec=judge)
+    torch.cuda.synchronize()
+    assert rep["used"] in (0, 2)
+    mb = mask.astype(bool)
+    assert np.array_equal(H(y)[mb], H(yD)[mb])
+    # the fallback y_n (Dirichlet rows at y_D) and its FP64 residual
+    yfb = yn.clone()
+    yfb[T(mb)] = yD[T(mb)]
+    R = torch.empty_like(y)
+    st_fb = fsi.StepState(yfb, Vn, An, mask=T(mask), yD=yD, elem=e, xi=xi, cell_start=cs,
+                          perm=pm, w=st.t["w"], drho_s=0.5)
+    fsi.fsi_coupled_residual(mesh, st_fb, R, prec=fsi.FSI_F64)
+    r_fb = float(R.norm())
+    assert abs(rep["r_fallback"] - r_fb) <= 1e-5 * r_fb, (rep["r_fallback"], r_fb)
+    fsi.fsi_coupled_residual(mesh, st, R, prec=judge)
+    torch.cuda.synchronize()
+    assert np.array_equal(H(work[0]), H(R))
+    if rep["used"] == 2:
+        assert abs(rep["r_combined"] - float(R.norm())) <= 1e-12 * rep["r_combined"]
+        assert rep["r_combined"] < rep["r_fallback"]
+    h.close()
+    mesh.close()
+
+
 def test_predict_matches_oracle(fsi):
     """y0 = y + e + (out_mean + out_std * net((features - in_mean) / in_std))."""
     import torch
