@@ -135,132 +135,241 @@ template <typename T> __device__ __forceinline__ T diag_of(const LevelArgs<T> &L
     return kx * my * mz + mx * ky * mz + mx * my * kz + L.kappa * mx * my * mz;
 }
 
-// (A v)_node for node (i, j, k), v = x + d (x == null: v = d; d == null:
-// v = x): nine x-lines, each reduced with the 1D stiffness and mass rows, then
-// combined with the y/z coefficients.  Rows of eliminated nodes keep only the
-// diagonal; their columns are skipped.
+// v = x + d at a node (x == null: v = d; d == null: v = x)
 template <typename T>
 __device__ __forceinline__ T val(const T *__restrict__ x, const T *__restrict__ d, int64_t q)
 {
     return x ? (d ? x[q] + d[q] : x[q]) : d[q];
 }
 
-template <typename T>
-__device__ __forceinline__ T apply_row(const LevelArgs<T> &L, const T *__restrict__ x,
-                                       const T *__restrict__ d, int i, int j, int k)
-{
-    const int64_t node = i + (int64_t)L.NX1 * (j + (int64_t)L.NY1 * k);
-    if (i >= 2 && j >= 2 && k >= 2 && i <= L.NX1 - 3 && j <= L.NY1 - 3 && k <= L.NZ1 - 3) {
-        // interior node two or more planes from every face: all 27 neighbours
-        // exist, none is eliminated, every 1D coefficient is an interior one;
-        // the same sums in the same order as the general path below
-        const Axis<T> &ax = L.a[0], &ay = L.a[1], &az = L.a[2];
-        T acc = T(0);
-#pragma unroll
-        for (int dk = -1; dk <= 1; ++dk) {
-            const T mz = dk ? az.m_off : az.m_in, kz = dk ? az.k_off : az.k_in;
-#pragma unroll
-            for (int dj = -1; dj <= 1; ++dj) {
-                const T my = dj ? ay.m_off : ay.m_in, ky = dj ? ay.k_off : ay.k_in;
-                const int64_t row = (int64_t)L.NX1 * ((j + dj) + (int64_t)L.NY1 * (k + dk)) + i;
-                const T vm = val(x, d, row - 1), v0 = val(x, d, row), vp = val(x, d, row + 1);
-                T sK = T(0), sM = T(0);
-                sK += ax.k_off * vm;
-                sM += ax.m_off * vm;
-                sK += ax.k_in * v0;
-                sM += ax.m_in * v0;
-                sK += ax.k_off * vp;
-                sM += ax.m_off * vp;
-                acc += sK * (my * mz) + sM * (ky * mz + my * kz + L.kappa * my * mz);
-            }
-        }
-        return acc;
-    }
-    if (eliminated(L, i, j, k)) return diag_of(L, i, j, k) * val(x, d, node);
-    // the eliminated neighbours lie on faces: the lines that would touch them
-    // are cut at i/j/k = 0 or N when the face is eliminated
-    const int ilo = L.faces[0] ? 1 : 0, ihi = L.faces[1] ? L.NX1 - 2 : L.NX1 - 1;
-    const int jlo = L.faces[2] ? 1 : 0, jhi = L.faces[3] ? L.NY1 - 2 : L.NY1 - 1;
-    const int klo = L.faces[4] ? 1 : 0, khi = L.faces[5] ? L.NZ1 - 2 : L.NZ1 - 1;
-    T acc = T(0);
-    for (int dk = -1; dk <= 1; ++dk) {
-        const int kk = k + dk;
-        if (kk < klo || kk > khi) continue;
-        T mz, kz;
-        coef(L.a[2], k, dk, mz, kz);
-        for (int dj = -1; dj <= 1; ++dj) {
-            const int jj = j + dj;
-            if (jj < jlo || jj > jhi) continue;
-            T my, ky;
-            coef(L.a[1], j, dj, my, ky);
-            const int64_t row = (int64_t)L.NX1 * (jj + (int64_t)L.NY1 * kk);
-            T sK = T(0), sM = T(0);
-            for (int di = -1; di <= 1; ++di) {
-                const int ii = i + di;
-                if (ii < ilo || ii > ihi) continue;
-                T mx, kx;
-                coef(L.a[0], i, di, mx, kx);
-                const T v = val(x, d, row + ii);
-                sK += kx * v;
-                sM += mx * v;
-            }
-            acc += sK * (my * mz) + sM * (ky * mz + my * kz + L.kappa * my * mz);
-        }
-    }
-    return acc;
-}
-
-// One thread per node on a 3D launch: x and y from the block and thread
-// indices, z from the grid (no per-node division).
+// One thread per (i, j) column on a 3D launch, x and y from the block and
+// thread indices, striding over the planes k from the grid's z index (no
+// per-node division; a CTA does several planes, so tiny CTAs do not make the
+// CTA launches the limit).
 #define NODE3(L, i, j, k)                                                                   \
     const int i = blockIdx.x * blockDim.x + threadIdx.x;                                 \
-    const int j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;                 \
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;                                 \
     if (i >= (L).NX1 || j >= (L).NY1) return;                                            \
-    const int64_t node = i + (int64_t)(L).NX1 * (j + (int64_t)(L).NY1 * k)
+    for (int k = blockIdx.z; k < (L).NZ1; k += gridDim.z)
 
-// y = A x (b == null) or y = b - A x
+// Chebyshev, first direction from x = 0: d0 = D^{-1} b / theta, or with
+// x_out (degree 1) x_out = d0.  (From a nonzero x the first direction needs
+// A x: march_kernel in kMarchCheb0 mode.)
 template <typename T>
-__global__ void apply_kernel(LevelArgs<T> L, const T *__restrict__ x, const T *__restrict__ b,
-                             T *__restrict__ y)
+__global__ void cheb0_kernel(LevelArgs<T> L, const T *__restrict__ b, T inv_theta,
+                             T *__restrict__ d_out, T *__restrict__ x_out)
 {
-    NODE3(L, i, j, k);
-    const T ax = apply_row(L, x, (const T *)nullptr, i, j, k);
-    y[node] = b ? b[node] - ax : ax;
-}
-
-// Chebyshev, first direction d0 = D^{-1} (b - A x) / theta (x == null: x = 0).
-// With x_out != null (degree 1) it writes x_out = x + d0 instead of d0.
-template <typename T>
-__global__ void cheb0_kernel(LevelArgs<T> L, const T *__restrict__ b, const T *__restrict__ x,
-                             T inv_theta, T *__restrict__ d_out, T *__restrict__ x_out)
-{
-    NODE3(L, i, j, k);
-    const T r = x ? b[node] - apply_row(L, x, (const T *)nullptr, i, j, k) : b[node];
-    const T d0 = inv_theta * r / diag_of(L, i, j, k);
-    if (x_out)
-        x_out[node] = x ? x[node] + d0 : d0;
-    else
-        d_out[node] = d0;
-}
-
-// One Chebyshev step from (x, d) of the previous step: x' = x + d,
-// d' = c1 d + c2 D^{-1} (b - A x'); writes (x', d'), or x' + d' into x_final
-// on the last step.  x == null stands for x = 0.
-template <typename T>
-__global__ void cheb_step_kernel(LevelArgs<T> L, const T *__restrict__ b, const T *__restrict__ x,
-                                 const T *__restrict__ d, T c1, T c2, T *__restrict__ x_next,
-                                 T *__restrict__ d_next, T *__restrict__ x_final)
-{
-    NODE3(L, i, j, k);
-    const T xk = val(x, d, node);
-    const T r = b[node] - apply_row(L, x, d, i, j, k);
-    const T dn = c1 * d[node] + c2 * (r / diag_of(L, i, j, k));
-    if (x_final) {
-        x_final[node] = xk + dn;
-    } else {
-        x_next[node] = xk;
-        d_next[node] = dn;
+    NODE3(L, i, j, k)
+    {
+        const int64_t node = i + (int64_t)L.NX1 * (j + (int64_t)L.NY1 * k);
+        const T d0 = inv_theta * b[node] / diag_of(L, i, j, k);
+        if (x_out)
+            x_out[node] = d0;
+        else
+            d_out[node] = d0;
     }
+}
+
+// ---------------------------------------------------------------- z-marching stencil
+// The operator A = K + kappa M of a level is a tensor product of 1D Q1 rows
+// (stiffness k, mass m per axis), so (A v)_node = sum_dk [P(k+dk) mz(dk) +
+// Q(k+dk) kz(dk)] with, per plane k', P = Ax + By + kappa C and Q = C, where
+// Ax = sum_dj sK_x(j+dj) my(dj), By = sum_dj sM_x(j+dj) ky(dj), C = sum_dj
+// sM_x(j+dj) my(dj), and sK_x / sM_x the 1D stiffness / mass rows along x.
+// A CTA owns a 32 x 8 column of nodes and marches up kz planes (as many as
+// leave about 16 CTAs per SM, 2 to 16): per plane it stages v (with a one-node
+// halo, zero outside the grid and on eliminated nodes, whose columns A does
+// not have) in shared memory, forms the x rows once per position, and each
+// thread folds its 3 x 3 neighbourhood into (P, Q) for the plane; the z fold
+// uses the three most recent planes held in registers.  The next plane's
+// loads are issued before the current plane is folded, so their latency
+// overlaps the work.  Every v is read once per plane (plus halos) instead of
+// 27 times, and the per-node work is ~30 operations.  Rows of eliminated
+// nodes keep only the diagonal.  The sums run in a fixed order
+// (deterministic).  (One thread per column marching without shared memory,
+// reading its 3 x 3 neighbourhood through L1, measured 1.8x slower.)
+constexpr int kMarchX = 32, kMarchY = 8;
+constexpr int kStage = (kMarchY + 2) * (kMarchX + 2);                            // per plane
+constexpr int kStagePer = (kStage + kMarchX * kMarchY - 1) / (kMarchX * kMarchY);  // per thread
+
+template <typename T> struct March {
+    const T *x, *d;  // v = x + d (either may be null: 0)
+    const T *b;
+    T c1, c2, inv_theta;
+    T *y, *x_next, *d_next, *x_final;
+    int kz;          // planes per CTA
+};
+
+enum MarchMode { kMarchApply = 0, kMarchCheb0 = 1, kMarchStep = 2 };
+
+template <typename T>
+__device__ __forceinline__ T md_of(const Axis<T> &a, int i)
+{
+    return (i == 0 || i == a.N) ? a.m_bd : a.m_in;
+}
+template <typename T>
+__device__ __forceinline__ T kd_of(const Axis<T> &a, int i)
+{
+    return (i == 0 || i == a.N) ? a.k_bd : a.k_in;
+}
+
+// this thread's staged values of plane kk (zero outside the grid and on
+// eliminated nodes)
+template <typename T>
+__device__ __forceinline__ void stage_load(const LevelArgs<T> &L, const March<T> &M, int i0,
+                                           int j0, int kk, int tid, T (&v)[kStagePer])
+{
+#pragma unroll
+    for (int r = 0; r < kStagePer; ++r) {
+        const int q = tid + r * kMarchX * kMarchY;
+        const int hx = q % (kMarchX + 2), hy = q / (kMarchX + 2);
+        const int gi = i0 - 1 + hx, gj = j0 - 1 + hy;
+        v[r] = T(0);
+        if (q < kStage && gi >= 0 && gj >= 0 && kk >= 0 && gi < L.NX1 && gj < L.NY1 &&
+            kk < L.NZ1 && !eliminated(L, gi, gj, kk))
+            v[r] = val(M.x, M.d, gi + (int64_t)L.NX1 * (gj + (int64_t)L.NY1 * kk));
+    }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kMarchX *kMarchY) march_kernel(LevelArgs<T> L, March<T> M)
+{
+    __shared__ T vt[kMarchY + 2][kMarchX + 2];
+    __shared__ T sk[kMarchY + 2][kMarchX], sm[kMarchY + 2][kMarchX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kMarchX * ty;
+    const int i0 = blockIdx.x * kMarchX, j0 = blockIdx.y * kMarchY, k0 = blockIdx.z * M.kz;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool own = i < L.NX1 && j < L.NY1;
+    const Axis<T> &ax = L.a[0], &ay = L.a[1], &az = L.a[2];
+    const T mdx = md_of(ax, i), kdx = kd_of(ax, i);
+    const T mdy = md_of(ay, j), kdy = kd_of(ay, j);
+    T Pm = T(0), P0 = T(0), Qm = T(0), Q0 = T(0);  // planes k-1, k (after the shift)
+    const int klast = min(k0 + M.kz, L.NZ1);        // planes k0 .. klast-1 are output
+    // the node inputs of the next output plane (b, d and v there), loaded one
+    // iteration ahead; the staged planes two iterations ahead
+    T b_nx = T(0), d_nx = T(0), v_nx = T(0), b_cur = T(0), d_cur = T(0), v_cur = T(0);
+    auto plane = [&](int kk, T (&cur)[kStagePer]) {
+#pragma unroll
+        for (int r = 0; r < kStagePer; ++r) {
+            const int q = tid + r * kMarchX * kMarchY;
+            if (q < kStage) vt[q / (kMarchX + 2)][q % (kMarchX + 2)] = cur[r];
+        }
+        __syncthreads();
+        b_cur = b_nx;
+        d_cur = d_nx;
+        v_cur = v_nx;
+        // the loads two planes ahead are in flight while this plane is folded
+        if (kk + 2 <= klast) stage_load(L, M, i0, j0, kk + 2, tid, cur);
+        if (own && kk >= k0 && kk < klast) {
+            const int64_t nd = i + (int64_t)L.NX1 * (j + (int64_t)L.NY1 * kk);
+            if (M.b) b_nx = M.b[nd];
+            if (MODE == kMarchStep) d_nx = M.d[nd];
+            // v at the node: the staged value unless the node is eliminated
+            // (staged as 0)
+            v_nx = eliminated(L, i, j, kk) ? val(M.x, M.d, nd) : vt[ty + 1][tx + 1];
+        }
+        // the x rows of the plane at the CTA's columns, rows j0-1 .. j0+kMarchY
+        for (int q = tid; q < (kMarchY + 2) * kMarchX; q += kMarchX * kMarchY) {
+            const int cx = q % kMarchX, cy = q / kMarchX;
+            const T vm = vt[cy][cx], v0 = vt[cy][cx + 1], vp = vt[cy][cx + 2];
+            const int gi = i0 + cx;
+            T a = T(0), c = T(0);
+            a += ax.k_off * vm;
+            c += ax.m_off * vm;
+            a += kd_of(ax, gi) * v0;
+            c += md_of(ax, gi) * v0;
+            a += ax.k_off * vp;
+            c += ax.m_off * vp;
+            sk[cy][cx] = a;
+            sm[cy][cx] = c;
+        }
+        __syncthreads();
+        // y fold for this thread's column on plane kk
+        T Ax = T(0), By = T(0), C = T(0);
+        Ax += sk[ty][tx] * ay.m_off;
+        By += sm[ty][tx] * ay.k_off;
+        C += sm[ty][tx] * ay.m_off;
+        Ax += sk[ty + 1][tx] * mdy;
+        By += sm[ty + 1][tx] * kdy;
+        C += sm[ty + 1][tx] * mdy;
+        Ax += sk[ty + 2][tx] * ay.m_off;
+        By += sm[ty + 2][tx] * ay.k_off;
+        C += sm[ty + 2][tx] * ay.m_off;
+        const T Pp = Ax + By + L.kappa * C, Qp = C;
+        const int k = kk - 1;  // output plane: k-1, k, k+1 = (Pm, P0, Pp)
+        if (k >= k0 && k < klast && own) {
+            const int64_t node = i + (int64_t)L.NX1 * (j + (int64_t)L.NY1 * k);
+            const T mdz = md_of(az, k), kdz = kd_of(az, k);
+            T Av = T(0);
+            Av += Pm * az.m_off;
+            Av += Qm * az.k_off;
+            Av += P0 * mdz;
+            Av += Q0 * kdz;
+            Av += Pp * az.m_off;
+            Av += Qp * az.k_off;
+            const T D = kdx * mdy * mdz + mdx * kdy * mdz + mdx * mdy * kdz + L.kappa * mdx * mdy * mdz;
+            const T vown = v_cur;
+            if (eliminated(L, i, j, k)) Av = D * vown;
+            if constexpr (MODE == kMarchApply) {
+                M.y[node] = M.b ? b_cur - Av : Av;
+            } else if constexpr (MODE == kMarchCheb0) {
+                // first Chebyshev direction from x (not null here)
+                const T d0 = M.inv_theta * (b_cur - Av) / D;
+                if (M.x_final)
+                    M.x_final[node] = vown + d0;
+                else
+                    M.d_next[node] = d0;
+            } else {
+                const T dn = M.c1 * d_cur + M.c2 * ((b_cur - Av) / D);
+                if (M.x_final) {
+                    M.x_final[node] = vown + dn;
+                } else {
+                    M.x_next[node] = vown;
+                    M.d_next[node] = dn;
+                }
+            }
+        }
+        Pm = P0;
+        Qm = Q0;
+        P0 = Pp;
+        Q0 = Qp;
+        __syncthreads();
+    };
+    T pa[kStagePer], pb[kStagePer];
+    stage_load(L, M, i0, j0, k0 - 1, tid, pa);
+    stage_load(L, M, i0, j0, k0, tid, pb);
+    for (int kk = k0 - 1; kk <= klast; kk += 2) {
+        plane(kk, pa);
+        if (kk + 1 <= klast) plane(kk + 1, pb);
+    }
+}
+
+const dim3 kMarchBlock(kMarchX, kMarchY);
+
+template <typename T, int MODE>
+fsi_status march(const PressureMG &P, int l, cudaStream_t s, March<T> M)
+{
+    const PmgLevel &L = P.lev[l];
+    const int nz1 = L.N[2] + 1;
+    const int gx = (L.N[0] + 1 + kMarchX - 1) / kMarchX, gy = (L.N[1] + 1 + kMarchY - 1) / kMarchY;
+    // planes per CTA: about 16 CTAs per SM in all (each CTA's planes are a
+    // serial chain of shared-memory passes), at least 2, at most 16
+    const int64_t cols = (int64_t)gx * gy;
+    M.kz = (int)std::max<int64_t>(2, std::min<int64_t>(16, nz1 * cols / (16 * sm_count())));
+    const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)((nz1 + M.kz - 1) / M.kz));
+    march_kernel<T, MODE><<<grid, kMarchBlock, 0, s>>>(level_args<T>(P, l), M);
+    return check_launch("pressure stencil");
+}
+
+// y = A x (b == null) or y = b - A x on level l
+template <typename T>
+fsi_status level_apply(const PressureMG &P, int l, cudaStream_t s, const T *x, const T *b, T *y)
+{
+    March<T> M{};
+    M.x = x;
+    M.b = b;
+    M.y = y;
+    return march<T, kMarchApply>(P, l, s, M);
 }
 
 // b_c = P^T r: each coarse node gathers the fine nodes within one fine cell,
@@ -269,27 +378,30 @@ template <typename T>
 __global__ void restrict_kernel(LevelArgs<T> F, LevelArgs<T> C, const T *__restrict__ r,
                                 T *__restrict__ bc)
 {
-    NODE3(C, I, J, K);
-    T acc = T(0);
-    for (int dk = -1; dk <= 1; ++dk) {
-        const int k = 2 * K + dk;
-        if (k < 0 || k >= F.NZ1) continue;
-        const T wk = dk ? T(0.5) : T(1);
-        for (int dj = -1; dj <= 1; ++dj) {
-            const int j = 2 * J + dj;
-            if (j < 0 || j >= F.NY1) continue;
-            const T wjk = (dj ? T(0.5) : T(1)) * wk;
-            const T *row = r + (int64_t)F.NX1 * (j + (int64_t)F.NY1 * k);
-            T s = T(0);
-            for (int di = -1; di <= 1; ++di) {
-                const int i = 2 * I + di;
-                if (i < 0 || i >= F.NX1) continue;
-                s += (di ? T(0.5) : T(1)) * row[i];
+    NODE3(C, I, J, K)
+    {
+        const int64_t node = I + (int64_t)C.NX1 * (J + (int64_t)C.NY1 * K);
+        T acc = T(0);
+        for (int dk = -1; dk <= 1; ++dk) {
+            const int k = 2 * K + dk;
+            if (k < 0 || k >= F.NZ1) continue;
+            const T wk = dk ? T(0.5) : T(1);
+            for (int dj = -1; dj <= 1; ++dj) {
+                const int j = 2 * J + dj;
+                if (j < 0 || j >= F.NY1) continue;
+                const T wjk = (dj ? T(0.5) : T(1)) * wk;
+                const T *row = r + (int64_t)F.NX1 * (j + (int64_t)F.NY1 * k);
+                T s = T(0);
+                for (int di = -1; di <= 1; ++di) {
+                    const int i = 2 * I + di;
+                    if (i < 0 || i >= F.NX1) continue;
+                    s += (di ? T(0.5) : T(1)) * row[i];
+                }
+                acc += wjk * s;
             }
-            acc += wjk * s;
         }
+        bc[node] = eliminated(C, I, J, K) ? T(0) : acc;
     }
-    bc[node] = eliminated(C, I, J, K) ? T(0) : acc;
 }
 
 // x += P x_c: trilinear interpolation of the coarse correction
@@ -297,20 +409,23 @@ template <typename T>
 __global__ void prolong_kernel(LevelArgs<T> F, LevelArgs<T> C, const T *__restrict__ xc,
                                T *__restrict__ x)
 {
-    NODE3(F, i, j, k);
-    const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
-    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
-    const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1),
-            wk = (k & 1) ? T(0.5) : T(1);
-    T acc = T(0);
-    for (int c = 0; c < nk; ++c)
-        for (int bb = 0; bb < nj; ++bb) {
-            const T *row = xc + (int64_t)C.NX1 * ((j0 + bb) + (int64_t)C.NY1 * (k0 + c));
-            T s = T(0);
-            for (int a = 0; a < ni; ++a) s += row[i0 + a];
-            acc += (wj * wk) * (wi * s);
-        }
-    x[node] += acc;
+    NODE3(F, i, j, k)
+    {
+        const int64_t node = i + (int64_t)F.NX1 * (j + (int64_t)F.NY1 * k);
+        const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+        const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+        const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1),
+                wk = (k & 1) ? T(0.5) : T(1);
+        T acc = T(0);
+        for (int c = 0; c < nk; ++c)
+            for (int bb = 0; bb < nj; ++bb) {
+                const T *row = xc + (int64_t)C.NX1 * ((j0 + bb) + (int64_t)C.NY1 * (k0 + c));
+                T s = T(0);
+                for (int a = 0; a < ni; ++a) s += row[i0 + a];
+                acc += (wj * wk) * (wi * s);
+            }
+        x[node] += acc;
+    }
 }
 
 template <typename T> __global__ void copy_kernel(int64_t n, const T *a, T *b)
@@ -338,14 +453,24 @@ __global__ void dense_apply_kernel(int64_t nc, const T *__restrict__ Ainv, const
 
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sm_count() * 16)); }
 
-// node kernels: CTAs of 32 nodes along x by 4 along y, one grid layer per z
-// (at 129 nodes per row: 81 % of the lanes busy, against 50 % for 128-node
-// rows of CTAs)
+// node kernels: CTAs of 32 nodes along x by 4 along y (at 129 nodes per row:
+// 81 % of the lanes busy, against 50 % for 128-node rows of CTAs), one plane
+// per grid layer
 const dim3 kRowBlock(32, 4);
 dim3 grid3(const PmgLevel &L)
 {
     return dim3((unsigned)((L.N[0] + 1 + 31) / 32), (unsigned)((L.N[1] + 1 + 3) / 4),
                 (unsigned)(L.N[2] + 1));
+}
+// the same with about 16 CTAs per SM in all, each striding over planes (for
+// the purely pointwise first smoother direction: 13 -> 8 us at 129^3; the
+// transfers are faster one plane per CTA)
+dim3 grid3_strided(const PmgLevel &L)
+{
+    const int gx = (L.N[0] + 1 + 31) / 32, gy = (L.N[1] + 1 + 3) / 4;
+    const int64_t gz = std::max<int64_t>(1, std::min<int64_t>(L.N[2] + 1,
+                                                              16 * sm_count() / ((int64_t)gx * gy)));
+    return dim3((unsigned)gx, (unsigned)gy, (unsigned)gz);
 }
 
 double spectrum_bound(const double h[3], double kappa)
@@ -454,14 +579,23 @@ fsi_status chebyshev(fsi_mesh *m, int l, int degree, double lo, double hi, const
     PmgLevel &L = P.lev[l];
     const LevelArgs<T> A = level_args<T>(P, l);
     cudaStream_t s = m->stream;
-    const dim3 g = grid3(L);
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), s1 = theta / delta;
-    if (degree == 1) {
-        cheb0_kernel<T><<<g, kRowBlock, 0, s>>>(A, b, x_in, (T)(1.0 / theta), nullptr, x_out);
-        return check_launch("pressure smoother");
-    }
     T *dbuf[2] = {vec<T>(L.d0), vec<T>(L.d1)}, *xbuf[2] = {vec<T>(L.xa), vec<T>(L.r)};
-    cheb0_kernel<T><<<g, kRowBlock, 0, s>>>(A, b, x_in, (T)(1.0 / theta), dbuf[0], nullptr);
+    // first direction (degree 1: x_out = x + d0 directly)
+    if (x_in) {
+        March<T> M{};
+        M.x = x_in;
+        M.b = b;
+        M.inv_theta = (T)(1.0 / theta);
+        M.d_next = degree == 1 ? nullptr : dbuf[0];
+        M.x_final = degree == 1 ? x_out : nullptr;
+        FSI_TRY((march<T, kMarchCheb0>(P, l, s, M)));
+    } else {
+        cheb0_kernel<T><<<grid3_strided(L), kRowBlock, 0, s>>>(
+            A, b, (T)(1.0 / theta), degree == 1 ? nullptr : dbuf[0], degree == 1 ? x_out : nullptr);
+        FSI_TRY(check_launch("pressure smoother"));
+    }
+    if (degree == 1) return FSI_OK;
     const T *xc = x_in;
     const T *dc = dbuf[0];
     double rho = 1.0 / s1;
@@ -470,8 +604,16 @@ fsi_status chebyshev(fsi_mesh *m, int l, int degree, double lo, double hi, const
         const T c1 = (T)(rho_new * rho), c2 = (T)(2.0 * rho_new / delta);
         const bool last = it == degree - 1;
         T *xn = xbuf[it & 1], *dn = dbuf[it & 1];
-        cheb_step_kernel<T><<<g, kRowBlock, 0, s>>>(A, b, xc, dc, c1, c2, last ? nullptr : xn,
-                                                      last ? nullptr : dn, last ? x_out : nullptr);
+        March<T> M{};
+        M.x = xc;
+        M.d = dc;
+        M.b = b;
+        M.c1 = c1;
+        M.c2 = c2;
+        M.x_next = last ? nullptr : xn;
+        M.d_next = last ? nullptr : dn;
+        M.x_final = last ? x_out : nullptr;
+        FSI_TRY((march<T, kMarchStep>(P, l, s, M)));
         xc = xn;
         dc = dn;
         rho = rho_new;
@@ -504,7 +646,7 @@ template <typename T> fsi_status vcycle_level(fsi_mesh *m, int l, const T *b, T 
     T *t = vec<T>(L.t);
     FSI_TRY(chebyshev<T>(m, l, kPmgNu, hi / 4.0, hi, b, (const T *)nullptr, t));
     const LevelArgs<T> A = level_args<T>(P, l), Ac = level_args<T>(P, l + 1);
-    apply_kernel<T><<<grid3(L), kRowBlock, 0, m->stream>>>(A, t, b, vec<T>(L.r));
+    FSI_TRY(level_apply<T>(P, l, m->stream, t, b, vec<T>(L.r)));
     restrict_kernel<T><<<grid3(Lc), kRowBlock, 0, m->stream>>>(A, Ac, vec<T>(L.r), vec<T>(Lc.b));
     FSI_TRY(check_launch("pressure restrict"));
     FSI_TRY(vcycle_level<T>(m, l + 1, vec<T>(Lc.b), vec<T>(Lc.x)));
@@ -744,14 +886,11 @@ fsi_status fsi_pressure_apply(fsi_mesh *mesh, fsi_prec prec, int32_t level, cons
     if (uses_amg(mesh)) return amg_apply(mesh, prec, level, x, y);
     FSI_TRY(pmg_ensure(mesh));
     FSI_TRY(check_level(mesh, level, false));
-    const dim3 g = grid3(mesh->pmg->lev[level]);
     if (prec == FSI_F64)
-        apply_kernel<double><<<g, kRowBlock, 0, mesh->stream>>>(
-            level_args<double>(*mesh->pmg, level), (const double *)x, nullptr, (double *)y);
-    else
-        apply_kernel<float><<<g, kRowBlock, 0, mesh->stream>>>(
-            level_args<float>(*mesh->pmg, level), (const float *)x, nullptr, (float *)y);
-    return check_launch("pressure apply");
+        return level_apply<double>(*mesh->pmg, level, mesh->stream, (const double *)x, nullptr,
+                                   (double *)y);
+    return level_apply<float>(*mesh->pmg, level, mesh->stream, (const float *)x, nullptr,
+                              (float *)y);
 }
 
 fsi_status fsi_pressure_restrict(fsi_mesh *mesh, fsi_prec prec, int32_t level, const void *r,
