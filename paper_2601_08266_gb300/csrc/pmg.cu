@@ -213,93 +213,121 @@ __device__ __forceinline__ T kd_of(const Axis<T> &a, int i)
     return (i == 0 || i == a.N) ? a.k_bd : a.k_in;
 }
 
-// this thread's staged values of plane kk (zero outside the grid and on
-// eliminated nodes)
-template <typename T>
-__device__ __forceinline__ void stage_load(const LevelArgs<T> &L, const March<T> &M, int i0,
-                                           int j0, int kk, int tid, T (&v)[kStagePer])
-{
-#pragma unroll
-    for (int r = 0; r < kStagePer; ++r) {
-        const int q = tid + r * kMarchX * kMarchY;
-        const int hx = q % (kMarchX + 2), hy = q / (kMarchX + 2);
-        const int gi = i0 - 1 + hx, gj = j0 - 1 + hy;
-        v[r] = T(0);
-        if (q < kStage && gi >= 0 && gj >= 0 && kk >= 0 && gi < L.NX1 && gj < L.NY1 &&
-            kk < L.NZ1 && !eliminated(L, gi, gj, kk))
-            v[r] = val(M.x, M.d, gi + (int64_t)L.NX1 * (gj + (int64_t)L.NY1 * kk));
-    }
-}
-
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kMarchX *kMarchY) march_kernel(LevelArgs<T> L, March<T> M)
 {
-    __shared__ T vt[kMarchY + 2][kMarchX + 2];
-    __shared__ T sk[kMarchY + 2][kMarchX], sm[kMarchY + 2][kMarchX];
+    __shared__ T vt[kStage];                      // [kMarchY + 2][kMarchX + 2]
+    __shared__ T sk[(kMarchY + 2) * kMarchX], sm[(kMarchY + 2) * kMarchX];
+    constexpr int kThreads = kMarchX * kMarchY;
+    constexpr int kRows = (kMarchY + 2) * kMarchX;  // x-row positions per plane
+    constexpr int kRowPer = (kRows + kThreads - 1) / kThreads;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kMarchX * ty;
     const int i0 = blockIdx.x * kMarchX, j0 = blockIdx.y * kMarchY, k0 = blockIdx.z * M.kz;
     const int i = i0 + tx, j = j0 + ty;
     const bool own = i < L.NX1 && j < L.NY1;
     const Axis<T> &ax = L.a[0], &ay = L.a[1], &az = L.a[2];
+    const int64_t plane_n = (int64_t)L.NX1 * L.NY1;
+    // everything that does not change from plane to plane, once per thread:
+    // the staged slots' in-plane offsets and masks (x, y faces),
+    int64_t s_off[kStagePer];
+    bool s_in[kStagePer];
+#pragma unroll
+    for (int r = 0; r < kStagePer; ++r) {
+        const int q = tid + r * kThreads;
+        const int gi = i0 - 1 + q % (kMarchX + 2), gj = j0 - 1 + q / (kMarchX + 2);
+        s_in[r] = q < kStage && gi >= 0 && gj >= 0 && gi < L.NX1 && gj < L.NY1 &&
+                  !((L.faces[0] && gi == 0) || (L.faces[1] && gi == L.NX1 - 1) ||
+                    (L.faces[2] && gj == 0) || (L.faces[3] && gj == L.NY1 - 1));
+        s_off[r] = gi + (int64_t)L.NX1 * gj;
+    }
+    // the x-row slots' centre coefficients and staged indices,
+    T r_k[kRowPer], r_m[kRowPer];
+    int r_v[kRowPer];
+#pragma unroll
+    for (int r = 0; r < kRowPer; ++r) {
+        const int q = tid + r * kThreads;
+        const int cx = q % kMarchX, cy = q / kMarchX;
+        r_k[r] = kd_of(ax, i0 + cx);
+        r_m[r] = md_of(ax, i0 + cx);
+        r_v[r] = cy * (kMarchX + 2) + cx;
+    }
+    // this node's coefficients: D = A1 mz(0) + A2 kz(0), with mz(0), kz(0)
+    // the boundary or interior entries of plane k
     const T mdx = md_of(ax, i), kdx = kd_of(ax, i);
     const T mdy = md_of(ay, j), kdy = kd_of(ay, j);
+    const T A1 = kdx * mdy + mdx * kdy + L.kappa * mdx * mdy, A2 = mdx * mdy;
+    const T inv_D_bd = T(1) / (A1 * az.m_bd + A2 * az.k_bd);
+    const T inv_D_in = T(1) / (A1 * az.m_in + A2 * az.k_in);
+    const bool elim_xy = own && ((L.faces[0] && i == 0) || (L.faces[1] && i == L.NX1 - 1) ||
+                                 (L.faces[2] && j == 0) || (L.faces[3] && j == L.NY1 - 1));
+    const int64_t own_off = i + (int64_t)L.NX1 * j;
+    const int klast = min(k0 + M.kz, L.NZ1);  // planes k0 .. klast-1 are output
+
+    auto stage = [&](int kk, T (&v)[kStagePer]) {
+        const bool zcut = kk < 0 || kk >= L.NZ1 || (L.faces[4] && kk == 0) ||
+                          (L.faces[5] && kk == L.NZ1 - 1);
+#pragma unroll
+        for (int r = 0; r < kStagePer; ++r)
+            v[r] = (s_in[r] && !zcut) ? val(M.x, M.d, s_off[r] + plane_n * kk) : T(0);
+    };
     T Pm = T(0), P0 = T(0), Qm = T(0), Q0 = T(0);  // planes k-1, k (after the shift)
-    const int klast = min(k0 + M.kz, L.NZ1);        // planes k0 .. klast-1 are output
     // the node inputs of the next output plane (b, d and v there), loaded one
     // iteration ahead; the staged planes two iterations ahead
-    T b_nx = T(0), d_nx = T(0), v_nx = T(0), b_cur = T(0), d_cur = T(0), v_cur = T(0);
+    T b_nx = T(0), d_nx = T(0), v_nx = T(0);
     auto plane = [&](int kk, T (&cur)[kStagePer]) {
 #pragma unroll
-        for (int r = 0; r < kStagePer; ++r) {
-            const int q = tid + r * kMarchX * kMarchY;
-            if (q < kStage) vt[q / (kMarchX + 2)][q % (kMarchX + 2)] = cur[r];
-        }
+        for (int r = 0; r < kStagePer; ++r)
+            if (tid + r * kThreads < kStage) vt[tid + r * kThreads] = cur[r];
         __syncthreads();
-        b_cur = b_nx;
-        d_cur = d_nx;
-        v_cur = v_nx;
+        const T b_cur = b_nx, d_cur = d_nx, v_cur = v_nx;
         // the loads two planes ahead are in flight while this plane is folded
-        if (kk + 2 <= klast) stage_load(L, M, i0, j0, kk + 2, tid, cur);
+        if (kk + 2 <= klast) stage(kk + 2, cur);
+        const bool elim_k = elim_xy || (L.faces[4] && kk == 0) || (L.faces[5] && kk == L.NZ1 - 1);
         if (own && kk >= k0 && kk < klast) {
-            const int64_t nd = i + (int64_t)L.NX1 * (j + (int64_t)L.NY1 * kk);
+            const int64_t nd = own_off + plane_n * kk;
             if (M.b) b_nx = M.b[nd];
             if (MODE == kMarchStep) d_nx = M.d[nd];
             // v at the node: the staged value unless the node is eliminated
             // (staged as 0)
-            v_nx = eliminated(L, i, j, kk) ? val(M.x, M.d, nd) : vt[ty + 1][tx + 1];
+            v_nx = elim_k ? val(M.x, M.d, nd) : vt[(ty + 1) * (kMarchX + 2) + tx + 1];
         }
         // the x rows of the plane at the CTA's columns, rows j0-1 .. j0+kMarchY
-        for (int q = tid; q < (kMarchY + 2) * kMarchX; q += kMarchX * kMarchY) {
-            const int cx = q % kMarchX, cy = q / kMarchX;
-            const T vm = vt[cy][cx], v0 = vt[cy][cx + 1], vp = vt[cy][cx + 2];
-            const int gi = i0 + cx;
-            T a = T(0), c = T(0);
-            a += ax.k_off * vm;
-            c += ax.m_off * vm;
-            a += kd_of(ax, gi) * v0;
-            c += md_of(ax, gi) * v0;
-            a += ax.k_off * vp;
-            c += ax.m_off * vp;
-            sk[cy][cx] = a;
-            sm[cy][cx] = c;
+#pragma unroll
+        for (int r = 0; r < kRowPer; ++r) {
+            const int q = tid + r * kThreads;
+            if (q < kRows) {
+                const T vm = vt[r_v[r]], v0 = vt[r_v[r] + 1], vp = vt[r_v[r] + 2];
+                T a = T(0), c = T(0);
+                a += ax.k_off * vm;
+                c += ax.m_off * vm;
+                a += r_k[r] * v0;
+                c += r_m[r] * v0;
+                a += ax.k_off * vp;
+                c += ax.m_off * vp;
+                sk[q] = a;
+                sm[q] = c;
+            }
         }
         __syncthreads();
         // y fold for this thread's column on plane kk
         T Ax = T(0), By = T(0), C = T(0);
-        Ax += sk[ty][tx] * ay.m_off;
-        By += sm[ty][tx] * ay.k_off;
-        C += sm[ty][tx] * ay.m_off;
-        Ax += sk[ty + 1][tx] * mdy;
-        By += sm[ty + 1][tx] * kdy;
-        C += sm[ty + 1][tx] * mdy;
-        Ax += sk[ty + 2][tx] * ay.m_off;
-        By += sm[ty + 2][tx] * ay.k_off;
-        C += sm[ty + 2][tx] * ay.m_off;
+        const int c0 = ty * kMarchX + tx;
+        Ax += sk[c0] * ay.m_off;
+        By += sm[c0] * ay.k_off;
+        C += sm[c0] * ay.m_off;
+        Ax += sk[c0 + kMarchX] * mdy;
+        By += sm[c0 + kMarchX] * kdy;
+        C += sm[c0 + kMarchX] * mdy;
+        Ax += sk[c0 + 2 * kMarchX] * ay.m_off;
+        By += sm[c0 + 2 * kMarchX] * ay.k_off;
+        C += sm[c0 + 2 * kMarchX] * ay.m_off;
         const T Pp = Ax + By + L.kappa * C, Qp = C;
         const int k = kk - 1;  // output plane: k-1, k, k+1 = (Pm, P0, Pp)
         if (k >= k0 && k < klast && own) {
-            const int64_t node = i + (int64_t)L.NX1 * (j + (int64_t)L.NY1 * k);
-            const T mdz = md_of(az, k), kdz = kd_of(az, k);
+            const int64_t node = own_off + plane_n * k;
+            const bool bd = k == 0 || k == L.NZ1 - 1;
+            const T mdz = bd ? az.m_bd : az.m_in, kdz = bd ? az.k_bd : az.k_in;
+            const T inv_D = bd ? inv_D_bd : inv_D_in;
             T Av = T(0);
             Av += Pm * az.m_off;
             Av += Qm * az.k_off;
@@ -307,24 +335,23 @@ __global__ void __launch_bounds__(kMarchX *kMarchY) march_kernel(LevelArgs<T> L,
             Av += Q0 * kdz;
             Av += Pp * az.m_off;
             Av += Qp * az.k_off;
-            const T D = kdx * mdy * mdz + mdx * kdy * mdz + mdx * mdy * kdz + L.kappa * mdx * mdy * mdz;
-            const T vown = v_cur;
-            if (eliminated(L, i, j, k)) Av = D * vown;
+            const bool elim = elim_xy || (L.faces[4] && k == 0) || (L.faces[5] && k == L.NZ1 - 1);
+            if (elim) Av = (A1 * mdz + A2 * kdz) * v_cur;
             if constexpr (MODE == kMarchApply) {
                 M.y[node] = M.b ? b_cur - Av : Av;
             } else if constexpr (MODE == kMarchCheb0) {
                 // first Chebyshev direction from x (not null here)
-                const T d0 = M.inv_theta * (b_cur - Av) / D;
+                const T d0 = M.inv_theta * (b_cur - Av) * inv_D;
                 if (M.x_final)
-                    M.x_final[node] = vown + d0;
+                    M.x_final[node] = v_cur + d0;
                 else
                     M.d_next[node] = d0;
             } else {
-                const T dn = M.c1 * d_cur + M.c2 * ((b_cur - Av) / D);
+                const T dn = M.c1 * d_cur + M.c2 * ((b_cur - Av) * inv_D);
                 if (M.x_final) {
-                    M.x_final[node] = vown + dn;
+                    M.x_final[node] = v_cur + dn;
                 } else {
-                    M.x_next[node] = vown;
+                    M.x_next[node] = v_cur;
                     M.d_next[node] = dn;
                 }
             }
@@ -336,8 +363,8 @@ __global__ void __launch_bounds__(kMarchX *kMarchY) march_kernel(LevelArgs<T> L,
         __syncthreads();
     };
     T pa[kStagePer], pb[kStagePer];
-    stage_load(L, M, i0, j0, k0 - 1, tid, pa);
-    stage_load(L, M, i0, j0, k0, tid, pb);
+    stage(k0 - 1, pa);
+    stage(k0, pb);
     for (int kk = k0 - 1; kk <= klast; kk += 2) {
         plane(kk, pa);
         if (kk + 1 <= klast) plane(kk + 1, pb);
