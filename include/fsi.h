@@ -834,6 +834,18 @@ fsi_status fsi_measure_fma_peak(int device, fsi_prec prec, double *flops_per_sec
 fsi_status fsi_measure_blas1(int device, fsi_prec prec, int64_t len, int nvec, int reps,
                              double *dot_seconds, double *axpy_seconds);
 
+/* The Krylov solver's multi-dot by itself (the paper has no counterpart;
+ * Sec. 2.4 keeps the Gram-Schmidt dot products in FP64): out[k] = V_k . w
+ * for k < nvec, V_k = V + k * ldv, each of `len` entries (len and ldv
+ * multiples of 4, V and w 16-byte aligned), in `prec`: FSI_F64 sums in FP64;
+ * FSI_F32 forms each product exactly (TwoProd) and sums on the FP32 pipe
+ * with a compensated float pair, to the FP64 level (error a few units of
+ * 2^-44 of the sum of |V_k[i] w[i]|).  out: FP64 device array [nvec].  The
+ * sums follow a fixed grid, so the results are bitwise repeatable.  1 <=
+ * nvec <= 256.  Asynchronous on the default stream of `device`.             */
+fsi_status fsi_multi_dot(int device, fsi_prec prec, int64_t len, int nvec, const void *V,
+                         int64_t ldv, const void *w, double *out);
+
 #ifdef __cplusplus
 }
 #endif

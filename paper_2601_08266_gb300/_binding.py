@@ -121,6 +121,7 @@ _SIGS = {
     "fsi_dlm_interp": ([_VP, _INT, _I64, _VP, _VP, _VP, _VP], _INT),
     "fsi_dlm_spread": ([_VP, _INT, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _INT], _INT),
     "fsi_measure_fma_peak": ([_INT, _INT, ctypes.POINTER(ctypes.c_double)], _INT),
+    "fsi_multi_dot": ([_INT, _INT, _I64, _INT, _VP, _I64, _VP, _VP], _INT),
     "fsi_measure_blas1": ([_INT, _INT, _I64, _INT, _INT, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double)], _INT),
     "fsi_coupled_residual": ([_VP, _INT, ctypes.POINTER(fsi_step_state), _VP], _INT),
@@ -462,6 +463,16 @@ def fsi_measure_fma_peak(device, prec):
     out = ctypes.c_double(0.0)
     _check(lib().fsi_measure_fma_peak(device, prec, ctypes.byref(out)))
     return out.value
+
+
+def fsi_multi_dot(prec, V, w, out, device=0):
+    """out[k] = V[k] . w (the Krylov multi-dot; V [nvec, len], w [len], out
+    float64 [nvec], all device tensors)."""
+    import torch
+    dt = _prec_dtype(prec)
+    nvec, length = V.shape
+    _check(lib().fsi_multi_dot(device, prec, int(length), int(nvec), _ptr(V, dt), int(length),
+                               _ptr(w, dt), _ptr(out, torch.float64)))
 
 
 def fsi_measure_blas1(device, prec, length, nvec, reps=10):

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 
@@ -130,23 +131,43 @@ __global__ void dirichlet_rows_kernel(int64_t n4, const uint8_t *mask, const T *
 // ------------------------------------------------------------ reductions
 // partial[k][block] = sum over the block's grid-stride range of V_k . w, for
 // k in [k0, k0+cnt); fixed grid and block size (deterministic).  FP64 vectors
-// accumulate in FP64.  FP32 vectors accumulate FP64-grade on the FP32 pipe:
-// each product is exact as the pair (p, e) of an FMA-based TwoProd and is
-// added into a double-float accumulator (GB300's FP64 unit is ~70x slower).
+// accumulate in FP64.  FP32 vectors accumulate FP64-grade on the FP32 pipe
+// (GB300's FP64 unit is ~70x slower): each product is exact as the pair
+// (p, e) of an FMA-based TwoProd; p joins the running float sum s by Knuth's
+// TwoSum, whose rounding error t and e go to a float compensation c, and
+// (s, c) is renormalised (Fast2Sum) once per 4-value record: 10 FP32
+// instructions per product against 13 for a full double-float addition, with
+// |c| kept below a few ulp(s) so the error stays at the double-float level.
+struct Comp {
+    float s, c;
+    __device__ Comp() {}
+    __device__ explicit Comp(int) : s(0.0f), c(0.0f) {}
+};
 __device__ __forceinline__ void dot_acc(double &acc, double v, double w) { acc += v * w; }
-__device__ __forceinline__ void dot_acc(df64 &acc, float v, float w)
+__device__ __forceinline__ void dot_acc(Comp &acc, float v, float w)
 {
     const float p = __fmul_rn(v, w);
     const float e = __fmaf_rn(v, w, -p);
-    acc = acc + df64(p, e);
+    const float s = __fadd_rn(acc.s, p);
+    const float bb = __fsub_rn(s, acc.s);
+    const float t = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    acc.s = s;
+    acc.c = __fadd_rn(acc.c, __fadd_rn(e, t));
+}
+__device__ __forceinline__ void dot_renorm(double &) {}
+__device__ __forceinline__ void dot_renorm(Comp &acc)
+{
+    const float s = __fadd_rn(acc.s, acc.c);
+    acc.c = __fsub_rn(acc.c, __fsub_rn(s, acc.s));
+    acc.s = s;
 }
 __device__ __forceinline__ double dot_value(double a) { return a; }
-__device__ __forceinline__ double dot_value(df64 a) { return a.to_double(); }
+__device__ __forceinline__ double dot_value(Comp a) { return (double)a.s + (double)a.c; }
 template <typename T> struct DotAcc {
     using type = double;
 };
 template <> struct DotAcc<float> {
-    using type = df64;
+    using type = Comp;
 };
 
 // (index self_k, when in [k0, k0+cnt), stands for w itself: w . w)
@@ -183,6 +204,7 @@ __global__ void __launch_bounds__(kRedThreads, 3) multi_dot_partial_kernel(
                     dot_acc(acc[j], v[j].y, wi.y);
                     dot_acc(acc[j], v[j].z, wi.z);
                     dot_acc(acc[j], v[j].w, wi.w);
+                    dot_renorm(acc[j]);
                 }
         } else {
 #pragma unroll
@@ -194,6 +216,7 @@ __global__ void __launch_bounds__(kRedThreads, 3) multi_dot_partial_kernel(
                     dot_acc(acc[j], v.y, wi.y);
                     dot_acc(acc[j], v.z, wi.z);
                     dot_acc(acc[j], v.w, wi.w);
+                    dot_renorm(acc[j]);
                 }
         }
     }
@@ -288,6 +311,7 @@ __global__ void __launch_bounds__(kRedThreads)
             dot_acc(nacc, acc.y, acc.y);
             dot_acc(nacc, acc.z, acc.z);
             dot_acc(nacc, acc.w, acc.w);
+            dot_renorm(nacc);
         }
     }
     if (norm_partial) {
@@ -1272,6 +1296,37 @@ fsi_status fsi_newton_step(fsi_mesh *mesh, const fsi_newton_opts *opts, const fs
     report->seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return stt;
+}
+
+fsi_status fsi_multi_dot(int device, fsi_prec prec, int64_t len, int nvec, const void *V,
+                         int64_t ldv, const void *w, double *out)
+{
+    if (!V || !w || !out) return set_error(FSI_ERR_ARG, "fsi_multi_dot: NULL argument");
+    if (prec != FSI_F64 && prec != FSI_F32) return set_error(FSI_ERR_ARG, "bad precision");
+    if (len < 4 || len % 4 != 0 || ldv < len || ldv % 4 != 0 || nvec < 1 || nvec > kMaxAxpy)
+        return set_error(FSI_ERR_ARG, "fsi_multi_dot: bad sizes");
+    const size_t esz = prec == FSI_F64 ? sizeof(double) : sizeof(float);
+    if (((uintptr_t)V | (uintptr_t)w) % (4 * esz) != 0)
+        return set_error(FSI_ERR_ARG, "fsi_multi_dot: V and w must be aligned to 4 entries");
+    FSI_DEVICE(device);
+    double *partial = nullptr;
+    FSI_CUDA(cudaMallocAsync((void **)&partial, (size_t)nvec * kRedGrid * sizeof(double), 0),
+             "partial sums");
+    for (int k0 = 0; k0 < nvec; k0 += kDotGroup) {
+        const int c = nvec - k0 < kDotGroup ? nvec - k0 : kDotGroup;
+        if (prec == FSI_F64)
+            multi_dot_partial_kernel<double><<<kRedGrid, kRedThreads, 0, 0>>>(
+                k0, c, len / 4, (const vec4<double> *)V, ldv / 4, (const vec4<double> *)w, partial,
+                -1, nullptr);
+        else
+            multi_dot_partial_kernel<float><<<kRedGrid, kRedThreads, 0, 0>>>(
+                k0, c, len / 4, (const vec4<float> *)V, ldv / 4, (const vec4<float> *)w, partial,
+                -1, nullptr);
+    }
+    multi_dot_final_kernel<<<nvec, kRedThreads, 0, 0>>>(nvec, partial, out, 0);
+    const fsi_status st = check_launch("multi-dot kernels");
+    cudaFreeAsync(partial, 0);
+    return st;
 }
 
 fsi_status fsi_measure_blas1(int device, fsi_prec prec, int64_t len, int nvec, int reps,
