@@ -48,6 +48,17 @@ int blocks_for(int64_t n, int threads, int cap = sm_count() * 16)
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
+// grid of the node pass (32 x 8 CTAs over (i, j)): about 16 CTAs per SM in
+// all, the z index striding over the planes (one plane per CTA made the CTA
+// launches the limit at 2.1 M nodes)
+dim3 node_grid(const GridArgs &g)
+{
+    const int gx = (g.Nx + 32) / 32, gy = std::min((g.Ny + 8) / 8, 65535);
+    const int64_t gz = std::max<int64_t>(
+        1, std::min<int64_t>(std::min(g.Nz + 1, 65535), 16 * sm_count() / ((int64_t)gx * gy)));
+    return dim3((unsigned)gx, (unsigned)gy, (unsigned)gz);
+}
+
 // --------------------------------------------------------------- locate
 __global__ void locate_kernel(int64_t m, GridArgs g, const double *__restrict__ X,
                               int32_t *__restrict__ elem, double *__restrict__ xi,
@@ -557,8 +568,7 @@ fsi_status spread_mass_diag(fsi_mesh *mesh, int64_t m, const T *xi, const int32_
     spread_cells_kernel<T, true><<<cgrid, 256, 0, mesh->stream>>>(
         E, xi, cell_start, perm, nullptr, w, (T *)mesh->spread_scratch, (T)dsq);
     FSI_TRY(check_launch("spread cells kernel"));
-    const dim3 nblock(32, 8);
-    const dim3 ngrid((g.Nx + 32) / 32, std::min((g.Ny + 8) / 8, 65535), std::min(g.Nz + 1, 65535));
+    const dim3 nblock(32, 8), ngrid = node_grid(g);
     if ((g.Ny + 8) / 8 > 65535)
         return set_error(FSI_ERR_ARG, "spreading: more than 524,280 nodes along y");
     spread_nodes_kernel<T><<<ngrid, nblock, 0, mesh->stream>>>(g, cell_start,
@@ -676,8 +686,7 @@ fsi_status fsi_dlm_spread(fsi_mesh *mesh, fsi_prec prec, int64_t m, const int32_
     const int64_t E = mesh->n_elems;
     const int cgrid = blocks_for((E + kSpreadSeg - 1) / kSpreadSeg * 32, 256, sm_count() * 64);
     // nodes: 32 x 8 threads per CTA over (i, j), one grid layer per k
-    const dim3 nblock(32, 8);
-    const dim3 ngrid((g.Nx + 32) / 32, std::min((g.Ny + 8) / 8, 65535), std::min(g.Nz + 1, 65535));
+    const dim3 nblock(32, 8), ngrid = node_grid(g);
     if ((g.Ny + 8) / 8 > 65535)
         return set_error(FSI_ERR_ARG, "fsi_dlm_spread: more than 524,280 nodes along y");
     if (prec == FSI_F64) {
