@@ -951,8 +951,8 @@ def newton_section(args, dev, stream):
                      "converged": bool(rep["converged"]), "status": code}
         if guess is not None:
             out[name]["predictor"] = {k2: guess[k2] for k2 in (
-                "r_fallback", "r_learned", "r_extrapolant_fit", "r_combined", "used",
-                "c_extrapolant", "a_velocity", "b_pressure")}
+                "r_fallback", "r_learned", "r_history_fit", "r_combined", "used",
+                "c_d1", "c_d2", "c_net")}
             out[name]["predictor"]["seconds"] = float(np.median(preds))
     if {"fp64", "mixed"} <= wanted:
         out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]

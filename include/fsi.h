@@ -679,26 +679,26 @@ fsi_status fsi_mlp_predict(fsi_mlp *mlp, fsi_mesh *mesh, const float *params,
                            const float *out_std, const double *Vn, const double *y,
                            const double *d1, const double *d2, double *y0);
 
-/* The FP64 residual judges the network.  With e = 2 d1 - d2 (the linear
- * extrapolant of the increment) and c = y_ml - y_n - e the network's
- * correction (fsi_mlp_predict), split into its velocity part c_v and
- * pressure part c_p, the predictor is the best member of the family
- *     y = y_fb + alpha e + beta c_v + gamma c_p
+/* The FP64 residual judges the network.  With d1, d2 the last two
+ * increments, e = 2 d1 - d2 their linear extrapolant and c = y_ml - y_n - e
+ * the network's correction (fsi_mlp_predict), the predictor is the best
+ * member of the family
+ *     y = y_fb + x1 d1 + x2 d2 + x3 c
  * around the fallback y_fb (fallback 0: y_n, the zero increment; 1: y_n + e),
  * all Dirichlet rows (st->mask) held at st->yD: the coefficients minimise
- * |R(y_fb) + J (alpha e + beta c_v + gamma c_p)|, R the coupled residual of
- * y_fb (its VMS part in FP32 from the FP32 linearisation, the coupling and
- * the Dirichlet rows double-float: the fit needs R far better than the
- * reduction a predictor brings, not to FP64) and J its Jacobian at y_fb
- * applied in FP32 (fsi_coupled_jacobian_apply; R is close to linear in y
+ * |R(y_fb) + J (x1 d1 + x2 d2 + x3 c)|, R the coupled
+ * residual of y_fb (its VMS part in FP32 from the FP32 linearisation, the
+ * coupling and the Dirichlet rows double-float: the fit needs R far better
+ * than the reduction a predictor brings, not to FP64) and J its Jacobian at
+ * y_fb applied in FP32 (fsi_coupled_jacobian_apply; R is close to linear in y
  * over a predictor's error), by the 3 x 3 normal equations in FP64 (a
- * direction that adds nothing is dropped).  The family holds both
- * fallbacks (alpha = 0 or 1 from y_n) and the network's own predictor, so the
- * fit is at least as good as each of them in the linear model.  The
- * candidate's residual is then evaluated in judge_prec, and st->y keeps the
- * candidate if its norm is below the fallback's (r_fallback), else y_fb.
- * Cost: the network, one FP32 linearisation with the FP32 residual and three
- * FP32 Jacobian applies, and the candidate's residual in judge_prec (which a
+ * direction that adds nothing is dropped).  The family holds both fallbacks
+ * (the zero increment and e) and the network's own predictor, so the fit is
+ * at least as good as each of them in the linear model.  The candidate's
+ * residual is then evaluated in judge_prec, and st->y keeps the candidate if
+ * its norm is below the fallback's (r_fallback), else y_fb.  Cost: the
+ * network, one FP32 linearisation with the FP32 residual and three FP32
+ * Jacobian applies, and the candidate's residual in judge_prec (which a
  * Newton step can take as its first, fsi_newton_opts.R0; when the fallback
  * is kept, its residual in judge_prec is evaluated instead).  judge_prec:
  * FSI_F64 or FSI_DF64.  work: caller-owned FP64 device array [5][n][4]; on
@@ -710,13 +710,13 @@ typedef struct {
     double r_fallback;   /* ||R(y_fb)||_2, the fit's residual (VMS part FP32)      */
     double r_learned;    /* the linear model's ||R|| at the network's own predictor */
     double r_combined;   /* ||R(y_c)||_2 of the fitted candidate, judge_prec         */
-    double a_velocity, b_pressure, c_extrapolant;  /* beta, gamma, alpha            */
+    double c_d1, c_d2, c_net;  /* x1, x2, x3                                      */
     int32_t used;        /* 0 fallback, 2 fitted candidate                           */
     int32_t reserved;
-    double r_extrapolant_fit; /* the linear model's ||R|| at the best y_fb + alpha e
-                                 alone (the same fit without the network's
-                                 directions: what the network adds is the gap
-                                 to r_combined)                                 */
+    double r_history_fit; /* the linear model's ||R|| at the best y_fb + x1 d1 +
+                             x2 d2 alone (the same fit without the network's
+                             direction: what the network adds is the gap to
+                             r_combined)                                       */
 } fsi_guess_report;
 
 fsi_status fsi_mlp_guess(fsi_mlp *mlp, fsi_mesh *mesh, const float *params, const float *in_mean,

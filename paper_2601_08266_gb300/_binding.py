@@ -71,10 +71,10 @@ class fsi_newton_report(ctypes.Structure):
 
 class fsi_guess_report(ctypes.Structure):
     _fields_ = [("r_fallback", ctypes.c_double), ("r_learned", ctypes.c_double),
-                ("r_combined", ctypes.c_double), ("a_velocity", ctypes.c_double),
-                ("b_pressure", ctypes.c_double), ("c_extrapolant", ctypes.c_double),
+                ("r_combined", ctypes.c_double), ("c_d1", ctypes.c_double),
+                ("c_d2", ctypes.c_double), ("c_net", ctypes.c_double),
                 ("used", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("r_extrapolant_fit", ctypes.c_double)]
+                ("r_history_fit", ctypes.c_double)]
 
 
 class fsi_batch_item(ctypes.Structure):
@@ -646,6 +646,8 @@ def fsi_mlp_guess(mlp: Mlp, mesh: Mesh, params, in_mean, in_std, out_mean, out_s
                   st: "StepState", yn, d1, d2, fallback, work, judge_prec=FSI_F64):
     import torch
     d, f = torch.float64, torch.float32
+    if work.numel() < 5 * 4 * mesh.n_nodes:
+        raise ValueError("fsi_mlp_guess: work must hold [5, n_nodes, 4] float64 values")
     rep = fsi_guess_report()
     _check(lib().fsi_mlp_guess(mlp.handle, mesh.handle, _ptr(params, f), _ptr(in_mean, f),
                                _ptr(in_std, f), _ptr(out_mean, f), _ptr(out_std, f),

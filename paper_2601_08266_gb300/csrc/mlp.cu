@@ -204,65 +204,74 @@ __global__ void apply_dirichlet_kernel(int64_t n4, const uint8_t *mask, const do
         if (mask[q]) y[q] = yD[q];
 }
 
-// One search direction of the fitted predictor, in FP32 (which: 0 the
-// extrapolant e = 2 d1 - d2; 1 the network's velocity correction c_v; 2 its
-// pressure correction c_p, c = ml - yn - e); zero on Dirichlet rows
+// One search direction of the fitted predictor, in FP32 (which: 0 the last
+// increment d1; 1 the one before, d2; 2 the network's correction
+// c = ml - yn - (2 d1 - d2)); zero on Dirichlet rows
+constexpr int kFitDirs = 3;
 __global__ void direction_kernel(int64_t n4, int which, const double *ml, const double *yn,
                                  const double *d1, const double *d2, const uint8_t *mask,
                                  float *out)
 {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const double e = 2.0 * d1[q] - d2[q];
-        const bool pslot = (q & 3) == 3;
-        double v = which == 0 ? e : ((which == 1) != pslot ? ml[q] - yn[q] - e : 0.0);
+        double v;
+        if (which == 0)
+            v = d1[q];
+        else if (which == 1)
+            v = d2[q];
+        else
+            v = ml[q] - yn[q] - (2.0 * d1[q] - d2[q]);
         if (mask && mask[q]) v = 0.0;
         out[q] = (float)v;
     }
 }
 
-// y = yfb + a e + b c_v + c c_p (Dirichlet rows = yD)
+// y = yfb + x0 d1 + x1 d2 + x2 c (Dirichlet rows = yD)
 __global__ void fitted_kernel(int64_t n4, const double *yfb, const double *ml, const double *yn,
                               const double *d1, const double *d2, const uint8_t *mask,
-                              const double *yD, double a, double b, double c, double *y)
+                              const double *yD, double x0, double x1, double x2, double *y)
 {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const double e = 2.0 * d1[q] - d2[q];
-        const double corr = ml[q] - yn[q] - e;
-        y[q] = (mask && mask[q]) ? yD[q] : yfb[q] + a * e + ((q & 3) == 3 ? c : b) * corr;
+        const double corr = ml[q] - yn[q] - (2.0 * d1[q] - d2[q]);
+        y[q] = (mask && mask[q]) ? yD[q] : yfb[q] + x0 * d1[q] + x1 * d2[q] + x2 * corr;
     }
 }
 
 // per-block partial sums of the normal equations of the fit: G_ij = J_i . J_j
-// (6 values) and r_i = J_i . R (3 values), FP32 products summed in FP64
+// (i <= j, 6 values, row by row) and r_i = J_i . R (3 values), FP32 products
+// summed in FP64
 constexpr int kFitBlocks = 96;
-__global__ void fit_dots_kernel(int64_t n4, const float *J0, const float *J1, const float *J2,
-                                const double *R, double *partial)
+constexpr int kFitSums = kFitDirs * (kFitDirs + 1) / 2 + kFitDirs;
+__global__ void fit_dots_kernel(int64_t n4, const float *Jd, const double *R, double *partial)
 {
-    __shared__ double red[9][256];
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    __shared__ double red[kFitSums][128];
+    double acc[kFitSums];
+#pragma unroll
+    for (int k = 0; k < kFitSums; ++k) acc[k] = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double a = J0[i], b = J1[i], c = J2[i], r = R[i];
-        acc[0] += a * a;
-        acc[1] += a * b;
-        acc[2] += a * c;
-        acc[3] += b * b;
-        acc[4] += b * c;
-        acc[5] += c * c;
-        acc[6] += a * r;
-        acc[7] += b * r;
-        acc[8] += c * r;
+        double a[kFitDirs];
+#pragma unroll
+        for (int d = 0; d < kFitDirs; ++d) a[d] = Jd[d * n4 + i];
+        const double r = R[i];
+        int k = 0;
+#pragma unroll
+        for (int d = 0; d < kFitDirs; ++d)
+#pragma unroll
+            for (int e = d; e < kFitDirs; ++e) acc[k++] += a[d] * a[e];
+#pragma unroll
+        for (int d = 0; d < kFitDirs; ++d) acc[k++] += a[d] * r;
     }
-    for (int k = 0; k < 9; ++k) red[k][threadIdx.x] = acc[k];
+#pragma unroll
+    for (int k = 0; k < kFitSums; ++k) red[k][threadIdx.x] = acc[k];
     __syncthreads();
-    for (int st = 128; st > 0; st >>= 1) {
+    for (int st = 64; st > 0; st >>= 1) {
         if (threadIdx.x < st)
-            for (int k = 0; k < 9; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
+            for (int k = 0; k < kFitSums; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
         __syncthreads();
     }
-    if (threadIdx.x < 9) partial[9 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+    if (threadIdx.x < kFitSums) partial[kFitSums * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
 }
 
 // per-block partial sums of |x|^2 (FP64)
@@ -359,7 +368,7 @@ fsi_status fsi_mlp_create(int device, void *cuda_stream, int64_t max_batch, fsi_
             return check_cuda(e, "mlp activation allocation");
         }
     }
-    cudaError_t e = cudaMalloc(&h->loss_partial, 1024 * sizeof(double));
+    cudaError_t e = cudaMalloc(&h->loss_partial, 2048 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->packed, mlp_tc_packed_bytes());
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->tc_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&h->gemm_work, tc_gemm_work_floats() * sizeof(float));
@@ -498,7 +507,7 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
     // directions and their J d_i; once the fit is done [2] holds the fitted
     // candidate and [3] its residual
     double *ml = work, *Rfb = work + n4, *cand = work + 2 * n4, *Rc = work + 3 * n4;
-    float *dir = (float *)(work + 2 * n4), *Jd = dir + 3 * n4;
+    float *dir = (float *)(work + 2 * n4), *Jd = dir + kFitDirs * n4;
     // the fallback predictor (in st->y) and the network's predictor (in ml)
     fallback_kernel<<<blocks(n4), 256, 0, s>>>(n4, fallback, yn, d1, d2, st->y);
     FSI_TRY(check_launch("fallback kernel"));
@@ -511,77 +520,95 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
     // one FP32 linearisation at y_fb: the fallback's residual for the fit
     // (its VMS part in FP32: the fit needs it to far less than the 1e-3 of
     // ||R|| that a predictor gains; coupling and Dirichlet rows double-float)
-    // and J applied to e, c_v, c_p
-    for (int i = 0; i < 3; ++i)
+    // and J applied to d1, d2, c
+    for (int i = 0; i < kFitDirs; ++i)
         direction_kernel<<<blocks(n4), 256, 0, s>>>(n4, i, ml, yn, d1, d2, st->mask, dir + i * n4);
     FSI_TRY(check_launch("direction kernel"));
     {
-        const float *xs[3] = {dir, dir + n4, dir + 2 * n4};
-        float *js[3] = {Jd, Jd + n4, Jd + 2 * n4};
-        FSI_TRY(coupled_jacobian_f32(mesh, st, 3, xs, js, Rfb));
+        const float *xs[kFitDirs];
+        float *js[kFitDirs];
+        for (int i = 0; i < kFitDirs; ++i) {
+            xs[i] = dir + i * n4;
+            js[i] = Jd + i * n4;
+        }
+        FSI_TRY(coupled_jacobian_f32(mesh, st, kFitDirs, xs, js, Rfb));
     }
     // normal equations G x = -r of min |R_fb + sum_i x_i J d_i|
-    fit_dots_kernel<<<kFitBlocks, 256, 0, s>>>(n4, Jd, Jd + n4, Jd + 2 * n4, Rfb,
-                                              h->loss_partial);
-    sumsq_kernel<<<kFitBlocks, 256, 0, s>>>(n4, Rfb, h->loss_partial + 9 * kFitBlocks);
+    fit_dots_kernel<<<kFitBlocks, 128, 0, s>>>(n4, Jd, Rfb, h->loss_partial);
+    sumsq_kernel<<<kFitBlocks, 256, 0, s>>>(n4, Rfb, h->loss_partial + kFitSums * kFitBlocks);
     FSI_TRY(check_launch("fit dots"));
-    double hp[10 * kFitBlocks];
+    double hp[(kFitSums + 1) * kFitBlocks];
     FSI_CUDA(cudaMemcpyAsync(hp, h->loss_partial, sizeof hp, cudaMemcpyDeviceToHost, s), "memcpy");
     FSI_CUDA(cudaStreamSynchronize(s), "sync");
-    double q[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, rr = 0.0;
+    double q[kFitSums] = {}, rr = 0.0;
     for (int b = 0; b < kFitBlocks; ++b) {
-        for (int k = 0; k < 9; ++k) q[k] += hp[9 * b + k];
-        rr += hp[9 * kFitBlocks + b];
+        for (int k = 0; k < kFitSums; ++k) q[k] += hp[kFitSums * b + k];
+        rr += hp[kFitSums * kFitBlocks + b];
     }
     const double r_fb = std::sqrt(rr);
-    double G[3][3] = {{q[0], q[1], q[2]}, {q[1], q[3], q[4]}, {q[2], q[4], q[5]}};
-    double r[3] = {q[6], q[7], q[8]};
-    // Cholesky with pivot tolerance: a direction whose Schur pivot is below
-    // 1e-12 of its own norm adds nothing and keeps coefficient 0
-    double x[3] = {0.0, 0.0, 0.0};
+    constexpr int K = kFitDirs;
+    double G[K][K], r[K];
     {
-        bool use[3];
-        double L[3][3] = {{0}};
-        for (int i = 0; i < 3; ++i) {
+        int k = 0;
+        for (int i = 0; i < K; ++i)
+            for (int j = i; j < K; ++j) G[i][j] = G[j][i] = q[k++];
+        for (int i = 0; i < K; ++i) r[i] = q[k++];
+    }
+    // min over the directions in `sel` (a bit mask) of the linear model
+    // |R_fb + sum x_i J d_i|^2: Cholesky with pivot tolerance (a direction
+    // whose Schur pivot is below 1e-12 of its own norm adds nothing and keeps
+    // coefficient 0); returns the model's |R|^2
+    auto fit = [&](unsigned sel, double (&x)[K]) {
+        bool use[K];
+        double L[K][K] = {};
+        for (int i = 0; i < K; ++i) {
             double d = G[i][i];
             for (int k = 0; k < i; ++k) d -= L[i][k] * L[i][k];
-            use[i] = G[i][i] > 0.0 && d > 1e-12 * G[i][i];
+            use[i] = ((sel >> i) & 1u) && G[i][i] > 0.0 && d > 1e-12 * G[i][i];
             L[i][i] = use[i] ? std::sqrt(d) : 0.0;
-            for (int j = i + 1; j < 3; ++j) {
+            for (int j = i + 1; j < K; ++j) {
                 double t = G[j][i];
                 for (int k = 0; k < i; ++k) t -= L[j][k] * L[i][k];
                 L[j][i] = use[i] ? t / L[i][i] : 0.0;
             }
         }
-        double z[3];
-        for (int i = 0; i < 3; ++i) {
+        double z[K];
+        for (int i = 0; i < K; ++i) {
             double t = -r[i];
             for (int k = 0; k < i; ++k) t -= L[i][k] * z[k];
             z[i] = use[i] ? t / L[i][i] : 0.0;
         }
-        for (int i = 2; i >= 0; --i) {
+        for (int i = K - 1; i >= 0; --i) {
             double t = z[i];
-            for (int k = i + 1; k < 3; ++k) t -= L[k][i] * x[k];
+            for (int k = i + 1; k < K; ++k) t -= L[k][i] * x[k];
             x[i] = use[i] ? t / L[i][i] : 0.0;
         }
-    }
-    // the linear model's residual at the network's own predictor y_n + e + c
-    {
-        const double xm[3] = {fallback == 1 ? 0.0 : 1.0, 1.0, 1.0};
         double v = rr;
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < K; ++i) {
+            v += 2.0 * x[i] * r[i];
+            for (int j = 0; j < K; ++j) v += x[i] * G[i][j] * x[j];
+        }
+        return std::max(v, 0.0);
+    };
+    double x[K];
+    fit(0x7u, x);
+    // the same model over the history directions alone (the fit without the
+    // network), and at the network's own predictor y_n + e + c (e = 2 d1 - d2)
+    {
+        double xh[K];
+        rep->r_history_fit = std::sqrt(fit(0x3u, xh));
+        const double xm[K] = {fallback == 1 ? 0.0 : 2.0, fallback == 1 ? 0.0 : -1.0, 1.0};
+        double v = rr;
+        for (int i = 0; i < K; ++i) {
             v += 2.0 * xm[i] * r[i];
-            for (int j = 0; j < 3; ++j) v += xm[i] * G[i][j] * xm[j];
+            for (int j = 0; j < K; ++j) v += xm[i] * G[i][j] * xm[j];
         }
         rep->r_learned = std::sqrt(std::max(v, 0.0));
     }
-    // the same linear model restricted to y_fb + alpha e
-    rep->r_extrapolant_fit =
-        G[0][0] > 0.0 ? std::sqrt(std::max(rr - r[0] * r[0] / G[0][0], 0.0)) : r_fb;
     rep->r_fallback = r_fb;
-    rep->c_extrapolant = x[0];
-    rep->a_velocity = x[1];
-    rep->b_pressure = x[2];
+    rep->c_d1 = x[0];
+    rep->c_d2 = x[1];
+    rep->c_net = x[2];
     // the candidate, judged by its own residual in judge_prec
     fitted_kernel<<<blocks(n4), 256, 0, s>>>(n4, st->y, ml, yn, d1, d2, st->mask, st->yD, x[0],
                                             x[1], x[2], cand);

@@ -267,9 +267,9 @@ def test_learned_guess_end_to_end(fsi, capsys):
               f"median residual reduction of the predictor x{gain:.2f}; Newton iterations "
               f"{newton_l} vs {newton_f} (fallback), Krylov {krylov_l} vs {krylov_f}")
         # ablation: the same fit without the network's directions (linear model)
-        print("linear-model residual of the extrapolant-only fit / judged residual of the "
-              "full fit:", [round(r["guess"]["r_extrapolant_fit"] / r["guess"]["r_combined"], 2)
-                            for r in recs2 if "guess" in r and r["step"] >= skip + 1])
+        print("linear-model residual of the history-only fit (d1, d2) / judged residual of "
+              "the full fit:", [round(r["guess"]["r_history_fit"] / r["guess"]["r_combined"], 2)
+                                for r in recs2 if "guess" in r and r["step"] >= skip + 1])
     for rw in rows:   # the residual decides: the candidate is kept only when it is better
         assert rw[4] in (0, 2)
         assert rw[4] == 0 or rw[3] < rw[1]
