@@ -176,8 +176,9 @@ __global__ void cheb0_kernel(LevelArgs<T> L, const T *__restrict__ b, T inv_thet
 // Q(k+dk) kz(dk)] with, per plane k', P = Ax + By + kappa C and Q = C, where
 // Ax = sum_dj sK_x(j+dj) my(dj), By = sum_dj sM_x(j+dj) ky(dj), C = sum_dj
 // sM_x(j+dj) my(dj), and sK_x / sM_x the 1D stiffness / mass rows along x.
-// A CTA owns a 32 x 8 column of nodes and marches up kz planes (as many as
-// leave about 16 CTAs per SM, 2 to 16): per plane it stages v (with a one-node
+// A CTA of 32 x 8 threads owns a 32 x 8 column of nodes and marches up kz
+// planes (as many as leave about 16 CTAs per SM, 2 to 16): per plane it
+// stages v (with a one-node
 // halo, zero outside the grid and on eliminated nodes, whose columns A does
 // not have) in shared memory, forms the x rows once per position, and each
 // thread folds its 3 x 3 neighbourhood into (P, Q) for the plane; the z fold
@@ -187,13 +188,20 @@ __global__ void cheb0_kernel(LevelArgs<T> L, const T *__restrict__ b, T inv_thet
 // 27 times, and the per-node work is ~30 operations.  Rows of eliminated
 // nodes keep only the diagonal.  The sums run in a fixed order
 // (deterministic).  (One thread per column marching without shared memory,
-// reading its 3 x 3 neighbourhood through L1, measured 1.8x slower.)
-constexpr int kMarchX = 32, kMarchY = 8;
-constexpr int kStage = (kMarchY + 2) * (kMarchX + 2);                            // per plane
-constexpr int kStagePer = (kStage + kMarchX * kMarchY - 1) / (kMarchX * kMarchY);  // per thread
+// reading its 3 x 3 neighbourhood through L1, measured 1.8x slower; two
+// rows per thread, 8 apart, measured 1.3x slower at 129^3: 88-94 registers
+// leave 2 CTAs per SM.)  The source of v (x, d or x + d) is a template
+// parameter, so no pass tests for null vectors per load.
+constexpr int kMarchX = 32, kMarchTY = 8, kMarchRows = 1;    // threads x, threads y, rows per thread
+constexpr int kMarchY = kMarchTY * kMarchRows;                   // node rows per CTA
+constexpr int kMarchThreads = kMarchX * kMarchTY;
+constexpr int kStage = (kMarchY + 2) * (kMarchX + 2);            // staged values per plane
+constexpr int kStagePer = (kStage + kMarchThreads - 1) / kMarchThreads;
+constexpr int kXRows = (kMarchY + 2) * kMarchX;                  // x-row positions per plane
+constexpr int kXRowPer = (kXRows + kMarchThreads - 1) / kMarchThreads;
 
 template <typename T> struct March {
-    const T *x, *d;  // v = x + d (either may be null: 0)
+    const T *x, *d;  // v = x + d (VX selects which are present)
     const T *b;
     T c1, c2, inv_theta;
     T *y, *x_next, *d_next, *x_final;
@@ -201,6 +209,8 @@ template <typename T> struct March {
 };
 
 enum MarchMode { kMarchApply = 0, kMarchCheb0 = 1, kMarchStep = 2 };
+// the vector v the stencil acts on: d alone, x alone, or x + d
+enum MarchSource { kVd = 0, kVx = 1, kVxd = 2 };
 
 template <typename T>
 __device__ __forceinline__ T md_of(const Axis<T> &a, int i)
@@ -212,96 +222,120 @@ __device__ __forceinline__ T kd_of(const Axis<T> &a, int i)
 {
     return (i == 0 || i == a.N) ? a.k_bd : a.k_in;
 }
+template <typename T, int VX> __device__ __forceinline__ T vsrc(const March<T> &M, int64_t q)
+{
+    if constexpr (VX == kVd) return M.d[q];
+    else if constexpr (VX == kVx) return M.x[q];
+    else return M.x[q] + M.d[q];
+}
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kMarchX *kMarchY) march_kernel(LevelArgs<T> L, March<T> M)
+template <typename T, int MODE, int VX>
+__global__ void __launch_bounds__(kMarchThreads) march_kernel(LevelArgs<T> L, March<T> M)
 {
     __shared__ T vt[kStage];                      // [kMarchY + 2][kMarchX + 2]
-    __shared__ T sk[(kMarchY + 2) * kMarchX], sm[(kMarchY + 2) * kMarchX];
-    constexpr int kThreads = kMarchX * kMarchY;
-    constexpr int kRows = (kMarchY + 2) * kMarchX;  // x-row positions per plane
-    constexpr int kRowPer = (kRows + kThreads - 1) / kThreads;
+    __shared__ T sk[kXRows], sm[kXRows];          // [kMarchY + 2][kMarchX]
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kMarchX * ty;
     const int i0 = blockIdx.x * kMarchX, j0 = blockIdx.y * kMarchY, k0 = blockIdx.z * M.kz;
-    const int i = i0 + tx, j = j0 + ty;
-    const bool own = i < L.NX1 && j < L.NY1;
+    const int i = i0 + tx;
     const Axis<T> &ax = L.a[0], &ay = L.a[1], &az = L.a[2];
     const int64_t plane_n = (int64_t)L.NX1 * L.NY1;
-    // everything that does not change from plane to plane, once per thread:
-    // the staged slots' in-plane offsets and masks (x, y faces),
+    // per thread, once: the staged slots' in-plane offsets and masks (x, y
+    // faces), the x-row slots' centre coefficients and staged indices
     int64_t s_off[kStagePer];
     bool s_in[kStagePer];
 #pragma unroll
     for (int r = 0; r < kStagePer; ++r) {
-        const int q = tid + r * kThreads;
+        const int q = tid + r * kMarchThreads;
         const int gi = i0 - 1 + q % (kMarchX + 2), gj = j0 - 1 + q / (kMarchX + 2);
         s_in[r] = q < kStage && gi >= 0 && gj >= 0 && gi < L.NX1 && gj < L.NY1 &&
                   !((L.faces[0] && gi == 0) || (L.faces[1] && gi == L.NX1 - 1) ||
                     (L.faces[2] && gj == 0) || (L.faces[3] && gj == L.NY1 - 1));
         s_off[r] = gi + (int64_t)L.NX1 * gj;
     }
-    // the x-row slots' centre coefficients and staged indices,
-    T r_k[kRowPer], r_m[kRowPer];
-    int r_v[kRowPer];
+    T x_k[kXRowPer], x_m[kXRowPer];
+    int x_v[kXRowPer];
 #pragma unroll
-    for (int r = 0; r < kRowPer; ++r) {
-        const int q = tid + r * kThreads;
+    for (int r = 0; r < kXRowPer; ++r) {
+        const int q = tid + r * kMarchThreads;
         const int cx = q % kMarchX, cy = q / kMarchX;
-        r_k[r] = kd_of(ax, i0 + cx);
-        r_m[r] = md_of(ax, i0 + cx);
-        r_v[r] = cy * (kMarchX + 2) + cx;
+        x_k[r] = kd_of(ax, i0 + cx);
+        x_m[r] = md_of(ax, i0 + cx);
+        x_v[r] = cy * (kMarchX + 2) + cx;
     }
-    // this node's coefficients: D = A1 mz(0) + A2 kz(0), with mz(0), kz(0)
-    // the boundary or interior entries of plane k
+    // this thread's nodes (i, j0 + ty + kMarchTY * rr): D = A1 mz(0) + A2 kz(0)
     const T mdx = md_of(ax, i), kdx = kd_of(ax, i);
-    const T mdy = md_of(ay, j), kdy = kd_of(ay, j);
-    const T A1 = kdx * mdy + mdx * kdy + L.kappa * mdx * mdy, A2 = mdx * mdy;
-    const T inv_D_bd = T(1) / (A1 * az.m_bd + A2 * az.k_bd);
-    const T inv_D_in = T(1) / (A1 * az.m_in + A2 * az.k_in);
-    const bool elim_xy = own && ((L.faces[0] && i == 0) || (L.faces[1] && i == L.NX1 - 1) ||
-                                 (L.faces[2] && j == 0) || (L.faces[3] && j == L.NY1 - 1));
-    const int64_t own_off = i + (int64_t)L.NX1 * j;
+    T mdy[kMarchRows], kdy[kMarchRows], A1[kMarchRows], A2[kMarchRows], iDb[kMarchRows],
+        iDi[kMarchRows];
+    bool own[kMarchRows], exy[kMarchRows];
+    int64_t off[kMarchRows];
+#pragma unroll
+    for (int rr = 0; rr < kMarchRows; ++rr) {
+        const int j = j0 + ty + kMarchTY * rr;
+        own[rr] = i < L.NX1 && j < L.NY1;
+        mdy[rr] = md_of(ay, j);
+        kdy[rr] = kd_of(ay, j);
+        A1[rr] = kdx * mdy[rr] + mdx * kdy[rr] + L.kappa * mdx * mdy[rr];
+        A2[rr] = mdx * mdy[rr];
+        iDb[rr] = T(1) / (A1[rr] * az.m_bd + A2[rr] * az.k_bd);
+        iDi[rr] = T(1) / (A1[rr] * az.m_in + A2[rr] * az.k_in);
+        exy[rr] = (L.faces[0] && i == 0) || (L.faces[1] && i == L.NX1 - 1) ||
+                  (L.faces[2] && j == 0) || (L.faces[3] && j == L.NY1 - 1);
+        off[rr] = i + (int64_t)L.NX1 * j;
+    }
     const int klast = min(k0 + M.kz, L.NZ1);  // planes k0 .. klast-1 are output
-
     auto stage = [&](int kk, T (&v)[kStagePer]) {
         const bool zcut = kk < 0 || kk >= L.NZ1 || (L.faces[4] && kk == 0) ||
                           (L.faces[5] && kk == L.NZ1 - 1);
 #pragma unroll
         for (int r = 0; r < kStagePer; ++r)
-            v[r] = (s_in[r] && !zcut) ? val(M.x, M.d, s_off[r] + plane_n * kk) : T(0);
+            v[r] = (s_in[r] && !zcut) ? vsrc<T, VX>(M, s_off[r] + plane_n * kk) : T(0);
     };
-    T Pm = T(0), P0 = T(0), Qm = T(0), Q0 = T(0);  // planes k-1, k (after the shift)
-    // the node inputs of the next output plane (b, d and v there), loaded one
-    // iteration ahead; the staged planes two iterations ahead
-    T b_nx = T(0), d_nx = T(0), v_nx = T(0);
+    // per row: (P, Q) of planes k-1, k; the node inputs of the next output
+    // plane (b, d, v) loaded one plane ahead, the staged planes two ahead
+    T Pm[kMarchRows], P0[kMarchRows], Qm[kMarchRows], Q0[kMarchRows];
+    T b_nx[kMarchRows], d_nx[kMarchRows], v_nx[kMarchRows];
+#pragma unroll
+    for (int rr = 0; rr < kMarchRows; ++rr)
+        Pm[rr] = P0[rr] = Qm[rr] = Q0[rr] = b_nx[rr] = d_nx[rr] = v_nx[rr] = T(0);
     auto plane = [&](int kk, T (&cur)[kStagePer]) {
 #pragma unroll
         for (int r = 0; r < kStagePer; ++r)
-            if (tid + r * kThreads < kStage) vt[tid + r * kThreads] = cur[r];
+            if (tid + r * kMarchThreads < kStage) vt[tid + r * kMarchThreads] = cur[r];
         __syncthreads();
-        const T b_cur = b_nx, d_cur = d_nx, v_cur = v_nx;
+        T b_cur[kMarchRows], d_cur[kMarchRows], v_cur[kMarchRows];
+#pragma unroll
+        for (int rr = 0; rr < kMarchRows; ++rr) {
+            b_cur[rr] = b_nx[rr];
+            d_cur[rr] = d_nx[rr];
+            v_cur[rr] = v_nx[rr];
+        }
         // the loads two planes ahead are in flight while this plane is folded
         if (kk + 2 <= klast) stage(kk + 2, cur);
-        const bool elim_k = elim_xy || (L.faces[4] && kk == 0) || (L.faces[5] && kk == L.NZ1 - 1);
-        if (own && kk >= k0 && kk < klast) {
-            const int64_t nd = own_off + plane_n * kk;
-            if (M.b) b_nx = M.b[nd];
-            if (MODE == kMarchStep) d_nx = M.d[nd];
-            // v at the node: the staged value unless the node is eliminated
-            // (staged as 0)
-            v_nx = elim_k ? val(M.x, M.d, nd) : vt[(ty + 1) * (kMarchX + 2) + tx + 1];
+        const bool ez = (L.faces[4] && kk == 0) || (L.faces[5] && kk == L.NZ1 - 1);
+        if (kk >= k0 && kk < klast) {
+#pragma unroll
+            for (int rr = 0; rr < kMarchRows; ++rr)
+                if (own[rr]) {
+                    const int64_t nd = off[rr] + plane_n * kk;
+                    if (M.b) b_nx[rr] = M.b[nd];
+                    if (MODE == kMarchStep) d_nx[rr] = M.d[nd];
+                    // v at the node: staged, unless eliminated (staged as 0)
+                    v_nx[rr] = (exy[rr] || ez)
+                                   ? vsrc<T, VX>(M, nd)
+                                   : vt[(ty + kMarchTY * rr + 1) * (kMarchX + 2) + tx + 1];
+                }
         }
         // the x rows of the plane at the CTA's columns, rows j0-1 .. j0+kMarchY
 #pragma unroll
-        for (int r = 0; r < kRowPer; ++r) {
-            const int q = tid + r * kThreads;
-            if (q < kRows) {
-                const T vm = vt[r_v[r]], v0 = vt[r_v[r] + 1], vp = vt[r_v[r] + 2];
+        for (int r = 0; r < kXRowPer; ++r) {
+            const int q = tid + r * kMarchThreads;
+            if (q < kXRows) {
+                const T vm = vt[x_v[r]], v0 = vt[x_v[r] + 1], vp = vt[x_v[r] + 2];
                 T a = T(0), c = T(0);
                 a += ax.k_off * vm;
                 c += ax.m_off * vm;
-                a += r_k[r] * v0;
-                c += r_m[r] * v0;
+                a += x_k[r] * v0;
+                c += x_m[r] * v0;
                 a += ax.k_off * vp;
                 c += ax.m_off * vp;
                 sk[q] = a;
@@ -309,57 +343,61 @@ __global__ void __launch_bounds__(kMarchX *kMarchY) march_kernel(LevelArgs<T> L,
             }
         }
         __syncthreads();
-        // y fold for this thread's column on plane kk
-        T Ax = T(0), By = T(0), C = T(0);
-        const int c0 = ty * kMarchX + tx;
-        Ax += sk[c0] * ay.m_off;
-        By += sm[c0] * ay.k_off;
-        C += sm[c0] * ay.m_off;
-        Ax += sk[c0 + kMarchX] * mdy;
-        By += sm[c0 + kMarchX] * kdy;
-        C += sm[c0 + kMarchX] * mdy;
-        Ax += sk[c0 + 2 * kMarchX] * ay.m_off;
-        By += sm[c0 + 2 * kMarchX] * ay.k_off;
-        C += sm[c0 + 2 * kMarchX] * ay.m_off;
-        const T Pp = Ax + By + L.kappa * C, Qp = C;
         const int k = kk - 1;  // output plane: k-1, k, k+1 = (Pm, P0, Pp)
-        if (k >= k0 && k < klast && own) {
-            const int64_t node = own_off + plane_n * k;
-            const bool bd = k == 0 || k == L.NZ1 - 1;
-            const T mdz = bd ? az.m_bd : az.m_in, kdz = bd ? az.k_bd : az.k_in;
-            const T inv_D = bd ? inv_D_bd : inv_D_in;
-            T Av = T(0);
-            Av += Pm * az.m_off;
-            Av += Qm * az.k_off;
-            Av += P0 * mdz;
-            Av += Q0 * kdz;
-            Av += Pp * az.m_off;
-            Av += Qp * az.k_off;
-            const bool elim = elim_xy || (L.faces[4] && k == 0) || (L.faces[5] && k == L.NZ1 - 1);
-            if (elim) Av = (A1 * mdz + A2 * kdz) * v_cur;
-            if constexpr (MODE == kMarchApply) {
-                M.y[node] = M.b ? b_cur - Av : Av;
-            } else if constexpr (MODE == kMarchCheb0) {
-                // first Chebyshev direction from x (not null here)
-                const T d0 = M.inv_theta * (b_cur - Av) * inv_D;
-                if (M.x_final)
-                    M.x_final[node] = v_cur + d0;
-                else
-                    M.d_next[node] = d0;
-            } else {
-                const T dn = M.c1 * d_cur + M.c2 * ((b_cur - Av) * inv_D);
-                if (M.x_final) {
-                    M.x_final[node] = v_cur + dn;
+        const bool out = k >= k0 && k < klast;
+        const bool bd = k == 0 || k == L.NZ1 - 1;
+        const bool elim_z = (L.faces[4] && k == 0) || (L.faces[5] && k == L.NZ1 - 1);
+        const T mdz = bd ? az.m_bd : az.m_in, kdz = bd ? az.k_bd : az.k_in;
+#pragma unroll
+        for (int rr = 0; rr < kMarchRows; ++rr) {
+            // y fold for this row's column on plane kk
+            const int c0 = (ty + kMarchTY * rr) * kMarchX + tx;
+            T Ax = T(0), By = T(0), C = T(0);
+            Ax += sk[c0] * ay.m_off;
+            By += sm[c0] * ay.k_off;
+            C += sm[c0] * ay.m_off;
+            Ax += sk[c0 + kMarchX] * mdy[rr];
+            By += sm[c0 + kMarchX] * kdy[rr];
+            C += sm[c0 + kMarchX] * mdy[rr];
+            Ax += sk[c0 + 2 * kMarchX] * ay.m_off;
+            By += sm[c0 + 2 * kMarchX] * ay.k_off;
+            C += sm[c0 + 2 * kMarchX] * ay.m_off;
+            const T Pp = Ax + By + L.kappa * C, Qp = C;
+            if (out && own[rr]) {
+                const int64_t node = off[rr] + plane_n * k;
+                T Av = T(0);
+                Av += Pm[rr] * az.m_off;
+                Av += Qm[rr] * az.k_off;
+                Av += P0[rr] * mdz;
+                Av += Q0[rr] * kdz;
+                Av += Pp * az.m_off;
+                Av += Qp * az.k_off;
+                const T inv_D = bd ? iDb[rr] : iDi[rr];
+                if (exy[rr] || elim_z) Av = (A1[rr] * mdz + A2[rr] * kdz) * v_cur[rr];
+                if constexpr (MODE == kMarchApply) {
+                    M.y[node] = M.b ? b_cur[rr] - Av : Av;
+                } else if constexpr (MODE == kMarchCheb0) {
+                    // first Chebyshev direction from x (not null here)
+                    const T d0 = M.inv_theta * (b_cur[rr] - Av) * inv_D;
+                    if (M.x_final)
+                        M.x_final[node] = v_cur[rr] + d0;
+                    else
+                        M.d_next[node] = d0;
                 } else {
-                    M.x_next[node] = v_cur;
-                    M.d_next[node] = dn;
+                    const T dn = M.c1 * d_cur[rr] + M.c2 * ((b_cur[rr] - Av) * inv_D);
+                    if (M.x_final) {
+                        M.x_final[node] = v_cur[rr] + dn;
+                    } else {
+                        M.x_next[node] = v_cur[rr];
+                        M.d_next[node] = dn;
+                    }
                 }
             }
+            Pm[rr] = P0[rr];
+            Qm[rr] = Q0[rr];
+            P0[rr] = Pp;
+            Q0[rr] = Qp;
         }
-        Pm = P0;
-        Qm = Q0;
-        P0 = Pp;
-        Q0 = Qp;
         __syncthreads();
     };
     T pa[kStagePer], pb[kStagePer];
@@ -371,21 +409,35 @@ __global__ void __launch_bounds__(kMarchX *kMarchY) march_kernel(LevelArgs<T> L,
     }
 }
 
-const dim3 kMarchBlock(kMarchX, kMarchY);
+const dim3 kMarchBlock(kMarchX, kMarchTY);
 
-template <typename T, int MODE>
-fsi_status march(const PressureMG &P, int l, cudaStream_t s, March<T> M)
+template <typename T, int MODE, int VX>
+fsi_status march_launch(const PressureMG &P, int l, cudaStream_t s, March<T> M)
 {
     const PmgLevel &L = P.lev[l];
     const int nz1 = L.N[2] + 1;
     const int gx = (L.N[0] + 1 + kMarchX - 1) / kMarchX, gy = (L.N[1] + 1 + kMarchY - 1) / kMarchY;
-    // planes per CTA: about 16 CTAs per SM in all (each CTA's planes are a
+    // planes per CTA: about 8 CTAs per SM in all (each CTA's planes are a
     // serial chain of shared-memory passes), at least 2, at most 16
     const int64_t cols = (int64_t)gx * gy;
     M.kz = (int)std::max<int64_t>(2, std::min<int64_t>(16, nz1 * cols / (16 * sm_count())));
     const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)((nz1 + M.kz - 1) / M.kz));
-    march_kernel<T, MODE><<<grid, kMarchBlock, 0, s>>>(level_args<T>(P, l), M);
+    march_kernel<T, MODE, VX><<<grid, kMarchBlock, 0, s>>>(level_args<T>(P, l), M);
     return check_launch("pressure stencil");
+}
+
+// the stencil pass in MODE: on v = M.x (apply, first Chebyshev direction) or
+// v = M.x + M.d (Chebyshev step; M.x null after a zero start)
+template <typename T, int MODE>
+fsi_status march(const PressureMG &P, int l, cudaStream_t s, const March<T> &M)
+{
+    if constexpr (MODE == kMarchStep) {
+        if (M.x) return march_launch<T, MODE, kVxd>(P, l, s, M);
+        return march_launch<T, MODE, kVd>(P, l, s, M);
+    } else {
+        if (!M.x) return FSI_ERR_ARG;
+        return march_launch<T, MODE, kVx>(P, l, s, M);
+    }
 }
 
 // y = A x (b == null) or y = b - A x on level l
