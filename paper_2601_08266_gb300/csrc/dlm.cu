@@ -2,13 +2,15 @@
 // point location with a cell -> points table, interpolation u = C^T V
 // (Eq. nodal_solid_velo) and spreading F = C lambda (Eq. fsi_constraint_matrix).
 //
-// Location is closed-form on the uniform grid (a bounded element walk with
-// Newton inversion on a mapped grid).  The cell table is a stable counting
-// sort: histogram (integer atomics, order-free), a three-kernel exclusive
-// scan, a scatter through per-cell cursors, and a per-cell sort of each
-// cell's slice by point index, which restores the stable order exactly (a
-// bitonic network in one lane's registers up to 64 points, a warp rank sort
-// up to 128, a shell sort beyond).  Spreading is atomic-free in two passes:
+// Location is closed-form on the uniform grid (integer work on the bits of
+// the coordinates when the spacings are powers of two; a bounded element
+// walk with Newton inversion on a mapped grid).  The cell table is a stable
+// counting sort: histogram (integer atomics, order-free), a single-pass
+// exclusive scan with decoupled look-back, a scatter that counts the
+// per-cell counters back down, and a per-cell sort of each cell's slice by
+// point index, which restores the stable order exactly (a warp rank sort up
+// to 128 points, a CTA bitonic network or a shell sort beyond).  Spreading
+// is atomic-free in two passes:
 // per-cell corner sums (four lanes per cell of up to 128 points, the warp for
 // fuller cells, fixed transpose-reduce trees), then a node gather over the
 // (up to) eight cells of each node in a fixed order.  No races, no atomics,
@@ -60,17 +62,48 @@ dim3 node_grid(const GridArgs &g)
 }
 
 // --------------------------------------------------------------- locate
+template <bool ZERO_ORIGIN>
 __global__ void locate_kernel(int64_t m, GridArgs g, const double *__restrict__ X,
                               int32_t *__restrict__ elem, double *__restrict__ xi,
-                              int32_t *__restrict__ count, unsigned long long *n_out)
+                              int32_t *__restrict__ count, unsigned long long *n_out,
+                              int32_t *__restrict__ arrival);
+
+fsi_status launch_locate(cudaStream_t s, int64_t m, const GridArgs &g, const double *X,
+                         int32_t *elem, double *xi, int32_t *count, unsigned long long *n_out,
+                         int32_t *arrival = nullptr)
 {
+    if (g.shifted && g.zero_origin)
+        locate_kernel<true><<<blocks_for(m, 256), 256, 0, s>>>(m, g, X, elem, xi, count, n_out,
+                                                               arrival);
+    else
+        locate_kernel<false><<<blocks_for(m, 256), 256, 0, s>>>(m, g, X, elem, xi, count, n_out,
+                                                                arrival);
+    return check_launch("locate kernel");
+}
+
+// One atomic per point: leaflet points arrive in no spatial order, so the
+// points of a warp almost never share a cell (a __match_any_sync grouping
+// measured no fewer atomics and kept the address unit busy).  With arrival,
+// each point keeps the count its cell had before it (outside points count in
+// the tail cell E): its slot in the cell's slice, so the scatter needs no
+// atomics.
+template <bool ZERO_ORIGIN>
+__global__ void locate_kernel(int64_t m, GridArgs g, const double *__restrict__ X,
+                              int32_t *__restrict__ elem, double *__restrict__ xi,
+                              int32_t *__restrict__ count, unsigned long long *n_out,
+                              int32_t *__restrict__ arrival)
+{
+    const int64_t E = (int64_t)g.Nx * g.Ny * g.Nz;
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
          b += (int64_t)gridDim.x * blockDim.x) {
-        const int e = locate_point<double>(g, b, X, elem, xi);
-        if (e < 0)
-            atomicAdd(n_out, 1ull);
-        else if (count)
+        const int e = locate_point<double, ZERO_ORIGIN>(g, b, X, elem, xi);
+        if (arrival) {
+            arrival[b] = atomicAdd(count + (e >= 0 ? (int64_t)e : E), 1);
+        } else if (e < 0) {
+            if (n_out) atomicAdd(n_out, 1ull);
+        } else if (count) {
             atomicAdd(count + e, 1);
+        }
     }
 }
 
@@ -245,8 +278,9 @@ __device__ bool newton_df(const HexNodes &H, const double X[3], double (&xi)[3])
 __global__ void locate_mapped_kernel(int64_t m, GridArgs g, const double4 *__restrict__ C,
                                      const double *__restrict__ Xp, int32_t *__restrict__ elem,
                                      double *__restrict__ xi, int32_t *__restrict__ count,
-                                     unsigned long long *n_out)
+                                     unsigned long long *n_out, int32_t *__restrict__ arrival)
 {
+    const int64_t E = (int64_t)g.Nx * g.Ny * g.Nz;
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
          b += (int64_t)gridDim.x * blockDim.x) {
         const double X[3] = {Xp[3 * b], Xp[3 * b + 1], Xp[3 * b + 2]};
@@ -316,7 +350,8 @@ __global__ void locate_mapped_kernel(int64_t m, GridArgs g, const double4 *__res
         if (!found) {
             elem[b] = -1;
             xi[3 * b] = xi[3 * b + 1] = xi[3 * b + 2] = 0.0;
-            atomicAdd(n_out, 1ull);
+            if (n_out) atomicAdd(n_out, 1ull);
+            if (arrival) arrival[b] = atomicAdd(count + E, 1);
             continue;
         }
         const int e = e3[0] + g.Nx * (e3[1] + g.Ny * e3[2]);
@@ -324,60 +359,369 @@ __global__ void locate_mapped_kernel(int64_t m, GridArgs g, const double4 *__res
         xi[3 * b] = q[0];
         xi[3 * b + 1] = q[1];
         xi[3 * b + 2] = q[2];
-        if (count) atomicAdd(count + e, 1);
+        if (arrival)
+            arrival[b] = atomicAdd(count + e, 1);
+        else if (count)
+            atomicAdd(count + e, 1);
     }
 }
 
 // --------------------------------------------------------------- cell table
-// (the per-work-item bodies are in dlm_device.cuh, shared with the batch)
-__global__ void __launch_bounds__(1024) scan_tiles_kernel(int64_t E, const int32_t *count,
-                                                          int32_t *start, int32_t *tile_sum)
+// Launches, none of them a memset: (1) the counts come from the locate
+// kernel; (2) per-tile sums of the counts (2048 cells a tile); (3) the scan
+// proper: each tile adds up the sums of the tiles before it (read from L2;
+// beyond kDirectTiles tiles one CTA first scans the tile sums in place, an
+// extra launch) and scans its own cells into start; (4) a scatter that counts
+// each cell's counter back down to zero while it hands out the cell's slots
+// (outside points take slots of the tail from a cursor); (5) a sort of every
+// 32-cell segment's slices by point index, which restores the stable order
+// exactly; cells of more than kWarpSortMax points are listed and sorted by a
+// whole CTA (6, only when m > kWarpSortMax).  No kernel waits on another CTA.
+// The counters and the scratch are left all zero, so the next call starts
+// without clearing them.
+//
+// Scan scratch, int32 words: [0] count of CTA-sorted cells, [5] cursor of
+// the outside points, [1..5) and [6, 8) unused, then the tile sums.
+constexpr int kScanHdr = 8;
+constexpr int kLbThreads = 256, kLbPer = kScanTile / kLbThreads;
+constexpr int64_t kDirectTiles = 1024;
+
+// this thread's kLbPer counts of tile t (zero past E)
+__device__ __forceinline__ void tile_counts(int64_t E, const int32_t *__restrict__ count, int t,
+                                            int (&v)[kLbPer])
 {
-    __shared__ int warp_sums[32];
-    scan_tile(E, count, start, tile_sum, blockIdx.x, warp_sums);
+    const int64_t base = (int64_t)t * kScanTile + (int64_t)threadIdx.x * kLbPer;
+    if (base + kLbPer <= E) {
+        const int4 a = *(const int4 *)(count + base), c = *(const int4 *)(count + base + 4);
+        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = c.x, v[5] = c.y, v[6] = c.z,
+        v[7] = c.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < kLbPer; ++i) v[i] = base + i < E ? count[base + i] : 0;
+    }
 }
 
-__global__ void __launch_bounds__(1024) scan_totals_kernel(int64_t ntiles, int32_t *tile_sum)
+__device__ __forceinline__ int block_sum(int x, int *warp_sums)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();  // warp_sums may still be read by a previous call
+    if (lane == 0) warp_sums[wid] = x;
+    __syncthreads();
+    int s = 0;
+#pragma unroll
+    for (int w = 0; w < kLbThreads / 32; ++w) s += warp_sums[w];
+    return s;
+}
+
+__global__ void __launch_bounds__(kLbThreads) tile_sums_kernel(int64_t E,
+                                                               const int32_t *__restrict__ count,
+                                                               int32_t *__restrict__ tile_sum)
+{
+    __shared__ int warp_sums[kLbThreads / 32];
+    int v[kLbPer];
+    tile_counts(E, count, blockIdx.x, v);
+    int own = 0;
+#pragma unroll
+    for (int i = 0; i < kLbPer; ++i) own += v[i];
+    const int s = block_sum(own, warp_sums);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = s;
+}
+
+// exclusive scan of the tile sums in place (one CTA; many tiles only)
+__global__ void __launch_bounds__(1024) tile_prefix_kernel(int64_t ntiles, int32_t *tile_sum)
 {
     __shared__ int warp_sums[32];
     __shared__ int carry;
     scan_totals_block(ntiles, tile_sum, warp_sums, &carry);
 }
 
-__global__ void scan_add_kernel(int64_t E, int32_t *start, const int32_t *tile_sum)
+// DIRECT: the tile's prefix is the sum of tile_sum[0, t); else tile_sum[t]
+template <bool DIRECT>
+__global__ void __launch_bounds__(kLbThreads) tile_scan_kernel(int64_t E,
+                                                               const int32_t *__restrict__ count,
+                                                               const int32_t *__restrict__ tile_sum,
+                                                               int32_t *__restrict__ start)
 {
-    scan_add_tile(E, start, tile_sum, blockIdx.x);
+    __shared__ int warp_sums[kLbThreads / 32];
+    const int t = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int v[kLbPer];
+    tile_counts(E, count, t, v);
+    int prefix;
+    if constexpr (DIRECT) {
+        int p = 0;
+        for (int u = threadIdx.x; u < t; u += kLbThreads) p += tile_sum[u];
+        prefix = block_sum(p, warp_sums);
+    } else {
+        prefix = tile_sum[t];
+    }
+    int own = 0;
+#pragma unroll
+    for (int i = 0; i < kLbPer; ++i) own += v[i];
+    int incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    int before = 0;
+#pragma unroll
+    for (int w = 0; w < kLbThreads / 32; ++w) before += w < wid ? warp_sums[w] : 0;
+    int run = prefix + before + incl - own;
+    // through shared memory (a row of kLbPer + 1 ints per thread: no bank
+    // conflicts) to stores of consecutive cells by consecutive threads
+    __shared__ int out[kLbThreads * (kLbPer + 1)];
+#pragma unroll
+    for (int i = 0; i < kLbPer; ++i) {
+        run += v[i];
+        out[threadIdx.x * (kLbPer + 1) + i] = run;
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)t * kScanTile;
+#pragma unroll
+    for (int i = 0; i < kLbPer; ++i) {
+        const int c = threadIdx.x + kLbThreads * i;
+        if (base + c < E) start[base + c + 1] = out[(c / kLbPer) * (kLbPer + 1) + c % kLbPer];
+    }
+    if (t == 0 && threadIdx.x == 0) start[0] = 0;
 }
 
-__global__ void scatter_kernel(int64_t m, int64_t E, const int32_t *__restrict__ elem,
-                               const int32_t *__restrict__ start, int32_t *fill,
-                               int32_t *__restrict__ perm)
+// point b into a slot of its cell's slice: the cell's counter counts down,
+// outside points count the tail cursor up (a slot outside [0, m), impossible
+// with counts from this call's locate, is dropped rather than written)
+__global__ void scatter_down_kernel(int64_t m, int64_t E, const int32_t *__restrict__ elem,
+                                    const int32_t *__restrict__ start, int32_t *fill,
+                                    int32_t *scr, int32_t *__restrict__ perm)
 {
+    if (blockIdx.x == 0 && threadIdx.x == 0) scr[0] = 0;  // the sort lists dense cells afresh
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
-         b += (int64_t)gridDim.x * blockDim.x)
-        scatter_point(b, E, elem, start, fill, perm);
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int e = elem[b];
+        const int64_t pos = e >= 0 ? (int64_t)start[e] + atomicSub(fill + e, 1) - 1
+                                   : (int64_t)start[E] + atomicAdd(scr + 5, 1);
+        if (pos >= 0 && pos < m) perm[pos] = (int32_t)b;
+    }
 }
 
-__global__ void cell_sort_kernel(int64_t E, int64_t m, const int32_t *__restrict__ start,
-                                 int32_t *__restrict__ perm, int32_t *dense, int32_t *dense_count)
+// Sort the slices of the cells [c0, c0 + 32) (one warp).  The slices are
+// contiguous in perm, [S0, S0 + T) with S0 = start[c0] (the tail cell E
+// holds the outside points).  A segment of at most 32 points is sorted at
+// once by the key (cell, point index): lane k holds element k, finds its
+// cell by a binary search over the 32 slice starts held in the lanes, and
+// its new place is the number of the segment's elements with a smaller key
+// (the keys are distinct).  A segment of up to kSegStage points is staged in
+// shared memory with one coalesced load, and its cells of 2 to kWarpSortMax
+// points are rank-sorted from there one at a time (so no cell waits for a
+// load of its own); cells of more points go to the dense list (or, without
+// one, to a single-lane shell sort).  Fuller segments sort their cells from
+// global memory.
+constexpr int kSegStage = 512;
+
+__device__ __forceinline__ void sort_segment_small(int32_t *__restrict__ perm, int S0, int T,
+                                                   int lo)
 {
+    const int lane = threadIdx.x & 31;
+    const int v = lane < T ? perm[S0 + lane] : INT32_MAX;
+    int q = 0;  // the last lane whose slice starts at or before S0 + lane
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+        if (__shfl_sync(0xffffffffu, lo, q + step) <= S0 + lane) q += step;
+    const int cl = lane < T ? q : 32;
+    int rk = 0;
+    for (int j = 0; j < T; ++j) {
+        const int vj = __shfl_sync(0xffffffffu, v, j);
+        const int cj = __shfl_sync(0xffffffffu, cl, j);
+        rk += (cj < cl) | ((cj == cl) & (vj < v));
+    }
+    __syncwarp();
+    if (lane < T) perm[S0 + rk] = v;
+}
+
+// rank sort of one slice of n (2..kWarpSortMax) values read from src, written
+// to dst (src may be dst: every value is read before the first write)
+__device__ __forceinline__ void rank_sort_slice(const int32_t *src, int32_t *dst, int n)
+{
+    const int lane = threadIdx.x & 31;
+    if (n <= 32) {
+        const int v = lane < n ? src[lane] : INT32_MAX;
+        int rk = 0;
+        for (int j = 0; j < n; ++j) rk += __shfl_sync(0xffffffffu, v, j) < v;
+        __syncwarp();
+        if (lane < n) dst[rk] = v;
+        return;
+    }
+    int own[4], rk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        own[k] = (lane + 32 * k < n) ? src[lane + 32 * k] : INT32_MAX;
+        rk[k] = 0;
+    }
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+        const int jn = min(32, n - 32 * cc);  // warp-uniform
+        for (int j = 0; j < jn; ++j) {
+            const int wj = __shfl_sync(0xffffffffu, own[cc], j);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) rk[k] += wj < own[k];
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (lane + 32 * k < n) dst[rk[k]] = own[k];
+}
+
+__device__ __forceinline__ void cell_sort_warp(int64_t E, int64_t m,
+                                               const int32_t *__restrict__ start,
+                                               int32_t *__restrict__ perm, int64_t c0,
+                                               int32_t *dense, int32_t *dense_count,
+                                               int32_t *stage)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t c = c0 + lane;
+    int lo = (int)m, len = 0;
+    if (c <= E) {
+        lo = start[c];
+        len = (c < E ? start[c + 1] : (int)m) - lo;
+    }
+    const int S0 = __shfl_sync(0xffffffffu, lo, 0);
+    const int T = __shfl_sync(0xffffffffu, lo + len, 31) - S0;
+    if (!__any_sync(0xffffffffu, len >= 2)) return;
+    if (T <= 32) {
+        sort_segment_small(perm, S0, T, lo);
+        return;
+    }
+    if (dense && len > kWarpSortMax) dense[atomicAdd(dense_count, 1)] = (int32_t)c;
+    const bool staged = stage != nullptr && T <= kSegStage;
+    if (staged) {
+        for (int k = lane; k < T; k += 32) stage[k] = perm[S0 + k];
+        __syncwarp();
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, len >= 2 && (len <= kWarpSortMax || !dense));
+    while (todo) {
+        const int l = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int base = __shfl_sync(0xffffffffu, lo, l);
+        const int n = __shfl_sync(0xffffffffu, len, l);
+        if (n <= kWarpSortMax) {
+            rank_sort_slice(staged ? stage + (base - S0) : perm + base, perm + base, n);
+        } else {
+            __syncwarp();
+            if (lane == 0) shell_sort(perm + base, n);
+        }
+        __syncwarp();
+    }
+}
+
+constexpr int kSortThreads = 256;
+
+__global__ void __launch_bounds__(kSortThreads) cell_sort_kernel(int64_t E, int64_t m,
+                                                                 const int32_t *__restrict__ start,
+                                                                 int32_t *__restrict__ perm,
+                                                                 int32_t *dense, int32_t *scr)
+{
+    __shared__ int32_t stage[kSortThreads / 32][kSegStage];
+    if (blockIdx.x == 0 && threadIdx.x == 0) scr[5] = 0;  // the outside cursor is spent
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c0 = warp * 32; c0 <= E; c0 += nwarps * 32)
-        cell_sort_segment(E, m, start, perm, c0, dense, dense_count);
+        cell_sort_warp(E, m, start, perm, c0, dense, scr, stage[threadIdx.x >> 5]);
 }
 
-// the cells listed by cell_sort_kernel, one CTA per cell
+// the cells listed by cell_sort_kernel, one CTA per cell; each list entry is
+// cleared once its cell is sorted (the list lives in the zeroed counters)
 __global__ void __launch_bounds__(1024) dense_sort_kernel(int64_t E, int64_t m,
                                                           const int32_t *__restrict__ start,
                                                           int32_t *__restrict__ perm,
-                                                          const int32_t *dense,
+                                                          int32_t *dense,
                                                           const int32_t *dense_count)
 {
     extern __shared__ int32_t sort_sh[];
     const int n = *dense_count;
-    for (int k = blockIdx.x; k < n; k += gridDim.x)
-        block_sort_cell(E, m, start, perm, dense[k], sort_sh);
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int c = dense[k];
+        block_sort_cell(E, m, start, perm, c, sort_sh);  // ends with __syncthreads
+        if (threadIdx.x == 0) dense[k] = 0;
+    }
+}
+
+// With point scratch (the mesh path): the scatter writes (point, cell) pairs
+// into tmp, and every slot finds its point's final place in one pass: the
+// number of points of its cell's slice with a smaller index (reads of the
+// slice hit L1: the lanes of a warp mostly share a cell).  Cells of more than
+// kWarpSortMax points are listed (by their first slot) and sorted by a CTA
+// from tmp into perm.
+// the points into (point, cell) pairs at their arrival slots; the point
+// that arrived first at a cell clears the cell's counter
+__global__ void scatter_arrival_kernel(int64_t m, int64_t E, const int32_t *__restrict__ elem,
+                                       const int32_t *__restrict__ arrival,
+                                       const int32_t *__restrict__ start, int32_t *fill,
+                                       int32_t *scr, int2 *__restrict__ tmp)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) scr[0] = 0;  // the dense list starts empty
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int e = elem[b];
+        const int c = e >= 0 ? e : (int)E;
+        const int r = arrival[b];
+        const int64_t pos = (int64_t)start[c] + r;
+        if (pos >= 0 && pos < m) tmp[pos] = make_int2((int)b, c);
+        if (r == 0) fill[c] = 0;
+    }
+}
+
+__global__ void rank_place_kernel(int64_t m, int64_t E, const int32_t *__restrict__ start,
+                                  const int2 *__restrict__ tmp, int32_t *__restrict__ perm,
+                                  int32_t *dense, int32_t *scr)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int2 p = tmp[k];
+        const int lo = start[p.y];
+        const int hi = p.y < E ? start[p.y + 1] : (int)m;
+        if (hi - lo > kWarpSortMax) {
+            if (k == lo) dense[atomicAdd(scr, 1)] = p.y;
+            continue;
+        }
+        // two pairs per 16-byte load from an even slot on
+        int r = 0, j = lo;
+        if ((j & 1) && j < hi) r += tmp[j++].x < p.x;
+#pragma unroll 2
+        for (; j + 1 < hi; j += 2) {
+            const int4 q = *reinterpret_cast<const int4 *>(tmp + j);
+            r += (q.x < p.x) + (q.z < p.x);
+        }
+        if (j < hi) r += tmp[j].x < p.x;
+        perm[lo + r] = p.x;
+    }
+}
+
+// the listed cells, one CTA per cell, from tmp into perm (bitonic network
+// in shared memory, or one lane's shell sort beyond kBlockSortMax points);
+// each list entry is cleared once its cell is sorted
+__global__ void __launch_bounds__(1024) dense_pairs_kernel(int64_t E, int64_t m,
+                                                           const int32_t *__restrict__ start,
+                                                           const int2 *__restrict__ tmp,
+                                                           int32_t *__restrict__ perm,
+                                                           int32_t *dense,
+                                                           const int32_t *dense_count)
+{
+    extern __shared__ int32_t sort_sh[];
+    const int n = *dense_count;
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int c = dense[k];
+        const int lo = start[c];
+        const int len = (c < E ? start[c + 1] : (int)m) - lo;
+        for (int i = threadIdx.x; i < len; i += blockDim.x) perm[lo + i] = tmp[lo + i].x;
+        __syncthreads();
+        block_sort_cell(E, m, start, perm, c, sort_sh);  // ends with __syncthreads
+        if (threadIdx.x == 0) dense[k] = 0;
+    }
 }
 
 // --------------------------------------------------------------- interp / spread
@@ -477,7 +821,7 @@ constexpr int64_t kNoAllocFillOffset = 64;
 constexpr int64_t kNoAllocTileOffset =
     kNoAllocFillOffset + ((kNoAllocMaxCells + 1 + 63) / 64) * 64;
 constexpr int64_t kNoAllocInts =
-    kNoAllocTileOffset + ((kNoAllocMaxCells + kScanTile - 1) / kScanTile + 64);
+    kNoAllocTileOffset + kScanHdr + ((kNoAllocMaxCells + kScanTile - 1) / kScanTile) + 64;
 static __device__ __align__(256) int32_t g_locate_scratch[kNoAllocInts];
 
 constexpr int kNoAllocMaxDevices = 64;
@@ -520,35 +864,54 @@ GridArgs grid_args_of(const fsi_grid &gr)
 
 }  // namespace
 
-// the scan's tile sums and, after them, the count of CTA-sorted cells
-int64_t cell_table_scan_ints(int64_t E) { return cell_tiles(E) + 1; }
+// the scan's header and the tile sums (see the cell table)
+int64_t cell_table_scan_ints(int64_t E) { return kScanHdr + cell_tiles(E) + 8; }
 
 fsi_status build_cell_table(cudaStream_t s, int64_t E, int64_t m, const int32_t *elem,
-                            int32_t *fill, int32_t *scan_tmp, int32_t *cell_start, int32_t *perm)
+                            int32_t *fill, int32_t *scan_tmp, int32_t *cell_start, int32_t *perm,
+                            int2 *tmp)
 {
     const int64_t ntiles = cell_tiles(E);
-    scan_tiles_kernel<<<(int)ntiles, 1024, 0, s>>>(E, fill, cell_start, scan_tmp);
-    FSI_TRY(check_launch("scan tiles kernel"));
-    scan_totals_kernel<<<1, 1024, 0, s>>>(ntiles, scan_tmp);
-    FSI_TRY(check_launch("scan totals kernel"));
-    scan_add_kernel<<<(int)ntiles, 256, 0, s>>>(E, cell_start, scan_tmp);
-    FSI_TRY(check_launch("scan add kernel"));
-    if (m > 0) {
-        FSI_CUDA(cudaMemsetAsync(fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
-        scatter_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, E, elem, cell_start, fill, perm);
+    if (ntiles > INT32_MAX) return set_error(FSI_ERR_ARG, "cell table: too many cells");
+    int32_t *tile_sum = scan_tmp + kScanHdr;
+    tile_sums_kernel<<<(int)ntiles, kLbThreads, 0, s>>>(E, fill, tile_sum);
+    FSI_TRY(check_launch("cell tile sums kernel"));
+    if (ntiles <= kDirectTiles) {
+        tile_scan_kernel<true><<<(int)ntiles, kLbThreads, 0, s>>>(E, fill, tile_sum, cell_start);
+    } else {
+        tile_prefix_kernel<<<1, 1024, 0, s>>>(ntiles, tile_sum);
+        FSI_TRY(check_launch("cell tile prefix kernel"));
+        tile_scan_kernel<false><<<(int)ntiles, kLbThreads, 0, s>>>(E, fill, tile_sum, cell_start);
+    }
+    FSI_TRY(check_launch("cell scan kernel"));
+    if (m > 0 && tmp) {
+        scatter_arrival_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, E, elem, perm, cell_start,
+                                                                  fill, scan_tmp, tmp);
         FSI_TRY(check_launch("scatter kernel"));
-        // the cursors in fill are spent: fill lists the cells too full for a
-        // warp, scan_tmp[ntiles] counts them
-        int32_t *dense_count = scan_tmp + ntiles;
-        FSI_CUDA(cudaMemsetAsync(dense_count, 0, sizeof(int32_t), s), "memset");
-        cell_sort_kernel<<<blocks_for((E + 32) / 32 * 32, 256, sm_count() * 64), 256, 0, s>>>(
-            E, m, cell_start, perm, fill, dense_count);
+        rank_place_kernel<<<blocks_for(m, 256, sm_count() * 32), 256, 0, s>>>(
+            m, E, cell_start, tmp, perm, fill, scan_tmp);
+        FSI_TRY(check_launch("rank place kernel"));
+        if (m > kWarpSortMax) {
+            const int smem = kBlockSortMax * (int)sizeof(int32_t);
+            FSI_TRY(set_smem_limit((const void *)dense_pairs_kernel, smem));
+            dense_pairs_kernel<<<sm_count(), 1024, smem, s>>>(E, m, cell_start, tmp, perm, fill,
+                                                             scan_tmp);
+            FSI_TRY(check_launch("dense cell sort kernel"));
+        }
+    } else if (m > 0) {
+        scatter_down_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, E, elem, cell_start, fill,
+                                                               scan_tmp, perm);
+        FSI_TRY(check_launch("scatter kernel"));
+        // the counters are back to zero: their head lists the cells too full
+        // for a warp, scan_tmp[0] counts them
+        cell_sort_kernel<<<blocks_for((E + 32) / 32 * 32, kSortThreads, sm_count() * 16),
+                           kSortThreads, 0, s>>>(E, m, cell_start, perm, fill, scan_tmp);
         FSI_TRY(check_launch("cell sort kernel"));
         if (m > kWarpSortMax) {
             const int smem = kBlockSortMax * (int)sizeof(int32_t);
             FSI_TRY(set_smem_limit((const void *)dense_sort_kernel, smem));
             dense_sort_kernel<<<sm_count(), 1024, smem, s>>>(E, m, cell_start, perm, fill,
-                                                            dense_count);
+                                                            scan_tmp);
             FSI_TRY(check_launch("dense cell sort kernel"));
         }
     }
@@ -611,27 +974,53 @@ fsi_status fsi_locate(fsi_mesh *mesh, int64_t m, const double *X, int32_t *elem,
     }
     const int64_t E = mesh->n_elems;
     cudaStream_t s = mesh->stream;
-    unsigned long long *nout = (unsigned long long *)mesh->dev_counters;
-    FSI_CUDA(cudaMemsetAsync(nout, 0, sizeof(unsigned long long), s), "memset");
     const bool table = cell_start != nullptr;
-    if (table) FSI_CUDA(cudaMemsetAsync(mesh->hash_fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
+    // with a table the outside points are its tail [cell_start[E], m): no
+    // separate counter (and no clearing launch) is needed
+    unsigned long long *nout = nullptr;
+    if (!table && (n_outside || strict)) {
+        nout = (unsigned long long *)mesh->dev_counters;
+        FSI_CUDA(cudaMemsetAsync(nout, 0, sizeof(unsigned long long), s), "memset");
+    }
+    if (table && !mesh->hash_clean)
+        FSI_CUDA(cudaMemsetAsync(mesh->hash_fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
+    if (table) mesh->hash_clean = false;
+    if (table && m > mesh->pt_tmp_cap) {
+        // grow-only point scratch of the cell table: (point, cell) pairs
+        cudaFree(mesh->pt_tmp);
+        mesh->pt_tmp = nullptr;
+        mesh->pt_tmp_cap = 0;
+        const int64_t cap = std::max<int64_t>(m, 1024);
+        FSI_CUDA(cudaMalloc(&mesh->pt_tmp, cap * sizeof(int2)), "point scratch");
+        mesh->pt_tmp_cap = cap;
+    }
     GridArgs g = grid_args(mesh);
     if (m > 0 && mesh->coords64) {
         locate_mapped_kernel<<<blocks_for(m, 128), 128, 0, s>>>(
             m, g, (const double4 *)mesh->coords64, X, elem, xi,
-            table ? mesh->hash_fill : nullptr, nout);
+            table ? mesh->hash_fill : nullptr, nout, table ? perm : nullptr);
         FSI_TRY(check_launch("locate kernel"));
     } else if (m > 0) {
-        locate_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, g, X, elem, xi,
-                                                         table ? mesh->hash_fill : nullptr, nout);
-        FSI_TRY(check_launch("locate kernel"));
+        FSI_TRY(launch_locate(s, m, g, X, elem, xi, table ? mesh->hash_fill : nullptr, nout,
+                              table ? perm : nullptr));
     }
-    if (table)
-        FSI_TRY(build_cell_table(s, E, m, elem, mesh->hash_fill, mesh->scan_tmp, cell_start, perm));
+    if (table) {
+        FSI_TRY(build_cell_table(s, E, m, elem, mesh->hash_fill, mesh->scan_tmp, cell_start, perm,
+                                 mesh->pt_tmp));
+        mesh->hash_clean = true;
+    }
     if (n_outside || strict) {
         unsigned long long h = 0;
-        FSI_CUDA(cudaMemcpyAsync(&h, nout, sizeof h, cudaMemcpyDeviceToHost, s), "memcpy");
-        FSI_CUDA(cudaStreamSynchronize(s), "stream sync");
+        if (table) {
+            int32_t inside = 0;
+            FSI_CUDA(cudaMemcpyAsync(&inside, cell_start + E, sizeof inside,
+                                     cudaMemcpyDeviceToHost, s), "memcpy");
+            FSI_CUDA(cudaStreamSynchronize(s), "stream sync");
+            h = (unsigned long long)(m - inside);
+        } else {
+            FSI_CUDA(cudaMemcpyAsync(&h, nout, sizeof h, cudaMemcpyDeviceToHost, s), "memcpy");
+            FSI_CUDA(cudaStreamSynchronize(s), "stream sync");
+        }
         if (n_outside) *n_outside = (int64_t)h;
         if (strict && h > 0)
             return set_error(FSI_ERR_OUTSIDE, "fsi_locate: %llu points outside the grid", h);
@@ -771,9 +1160,7 @@ fsi_status fsi_locate_noalloc(const fsi_grid *grid, int64_t m, const double *X, 
     if (table) FSI_CUDA(cudaMemsetAsync(fill, 0, (E + 1) * sizeof(int32_t), s), "memset");
     GridArgs g = grid_args_of(*grid);
     if (m > 0) {
-        locate_kernel<<<blocks_for(m, 256), 256, 0, s>>>(m, g, X, elem, xi, table ? fill : nullptr,
-                                                         nout);
-        FSI_TRY(check_launch("locate kernel"));
+        FSI_TRY(launch_locate(s, m, g, X, elem, xi, table ? fill : nullptr, nout));
     }
     if (table) FSI_TRY(build_cell_table(s, E, m, elem, fill, tiles, cell_start, perm));
     if (n_outside || strict) {

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cmath>
+#include <cstring>
 
 #include "df64.cuh"
 #include "fsi_internal.cuh"
@@ -17,6 +18,12 @@ struct GridArgs {
     // 1/h_k when h_k is an exact power of two (then d * (1/h_k) is the
     // correctly rounded d / h_k: both round the same real number d 2^-e), else 0
     double rx, ry, rz;
+    // shifted: every 1/h_k = 2^s_k with 0 <= s_k <= 1000, and then the bit
+    // patterns of d_max_k = N_k h_k (exact; see locate_point)
+    int shifted;
+    int sx, sy, sz;
+    long long dmax_bits[3];
+    int zero_origin;  // x0_k == 0 (either sign) on every axis
 };
 
 // the exact reciprocal of h when h = 2^e (with 1/h a normal double), else 0
@@ -34,6 +41,22 @@ inline void set_reciprocals(GridArgs &g)
     g.rx = pow2_reciprocal(g.hx);
     g.ry = pow2_reciprocal(g.hy);
     g.rz = pow2_reciprocal(g.hz);
+    const double r[3] = {g.rx, g.ry, g.rz}, h[3] = {g.hx, g.hy, g.hz};
+    const int N[3] = {g.Nx, g.Ny, g.Nz};
+    int sh[3] = {0, 0, 0};
+    g.shifted = 1;
+    for (int k = 0; k < 3; ++k) {
+        int e = 0;
+        std::frexp(r[k], &e);  // r = 0.5 * 2^e = 2^(e-1) when r is a power of two
+        sh[k] = e - 1;
+        if (!(r[k] >= 1.0) || sh[k] > 1000) g.shifted = 0;
+        const double dmax = (double)N[k] * h[k];  // exact: N < 2^31 times 2^-s
+        std::memcpy(&g.dmax_bits[k], &dmax, sizeof dmax);
+    }
+    g.zero_origin = g.x0 == 0.0 && g.y0 == 0.0 && g.z0 == 0.0;
+    g.sx = sh[0];
+    g.sy = sh[1];
+    g.sz = sh[2];
 }
 
 // (X - x0) / h as IEEE FP64 division, by the exact multiply when h is a
@@ -49,11 +72,129 @@ __device__ __forceinline__ double grid_coord(double X, double x0, double h, doub
 // unless 0 <= t_k <= N_k (NaN is outside), e_k = min(floor(t_k), N_k - 1),
 // xi_k = 2 (t_k - e_k) - 1, all in FP64 (xi stored in S).  Writes elem[b]
 // and xi[b]; returns the element, or -1 for an outside point (xi = 0).
-template <typename S>
+//
+// With every h_k = 2^-s_k (s_k >= 0), t_k = d_k 2^s_k is exact, so the same
+// results follow from integer work on the bits of d_k = X_k - x0_k (GB300's
+// FP64 unit issues two operations per SM and clock): 0 <= t_k <= N_k is 0 <=
+// d_k <= N_k h_k (an exact double) compared as ordered bit patterns;
+// floor(t_k) is the integer part of d_k's significand shifted by its
+// exponent + s_k; for floor(t_k) >= 1, xi_k = 2 (t_k - e_k) - 1 is exactly
+// Z 2^(u-52), u the exponent of t_k and Z = 2 F - 2^(52-u) (F the fraction
+// bits of t_k, |Z| < 2^53); in the first cell (t_k < 1), 2 t_k - 1 is
+// rounded to nearest, ties to even, from its exact integer form, as the FP64
+// subtraction of the definition rounds it.  Only a non-zero origin costs an
+// FP64 subtraction per coordinate.
+
+// the double of a non-zero integer Z (|Z| <= 2^53) times 2^p, from its bits
+// (the result is normal)
+__host__ __device__ __forceinline__ double exact_scaled(long long Z, int p)
+{
+    const long long a = Z < 0 ? -Z : Z;
+#ifdef __CUDA_ARCH__
+    const int msb = 63 - __clzll(a);
+#else
+    const int msb = 63 - __builtin_clzll((unsigned long long)a);
+#endif
+    const long long b = ((long long)(Z < 0) << 63) | ((long long)(1023 + msb + p) << 52) |
+                        ((a << (52 - msb)) & 0xfffffffffffffLL);
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(b);
+#else
+    double r;
+    std::memcpy(&r, &b, sizeof r);
+    return r;
+#endif
+}
+
+// 2 t - 1 rounded to nearest (ties to even) for t = d 2^s in [0, 1), from
+// the bits of d (d >= 0 or -0; s <= 1000)
+__host__ __device__ __forceinline__ double first_cell_xi(long long bits, int s)
+{
+    const int be = (int)((bits >> 52) & 0x7ff);
+    long long sig = bits & 0xfffffffffffffLL;
+    int u;  // t = sig 2^(u - 52)
+    if (be == 0) {
+        u = -1022 + s;
+    } else {
+        sig |= 1LL << 52;
+        u = be - 1023 + s;
+    }
+    if (sig == 0) return -1.0;
+    if (be != 0 && u == -1) {  // t in [1/2, 1): 2t - 1 = (sig - 2^52) 2^-52, exact
+        const long long Z = sig - (1LL << 52);
+        return Z == 0 ? 0.0 : exact_scaled(Z, -52);
+    }
+    // t < 1/2: 2t - 1 = -(2^53 - y) 2^-53, y = sig 2^(u+2) = sig / 2^j < 2^52
+    const int j = -u - 2;
+    long long M;
+    if (j <= 0) {
+        M = (1LL << 53) - (sig << (-j));
+    } else if (j >= 60) {
+        M = 1LL << 53;  // y < 2^-7
+    } else {
+        const long long q = sig >> j, r = sig & ((1LL << j) - 1), half = 1LL << (j - 1);
+        const long long B = (1LL << 53) - q, A = B - 1;  // 2^53 - y lies in (A, B]
+        M = r == 0 ? B : (r < half ? B : (r > half ? A : ((B & 1) ? A : B)));
+    }
+    return M == (1LL << 53) ? -1.0 : exact_scaled(-M, -53);
+}
+
+// axis k of the shifted path: returns false when the point is outside on it
+template <bool ZERO_ORIGIN>
+__device__ __forceinline__ bool shifted_axis(double X, double x0, int s, long long dmax_bits,
+                                             int N, int &e, double &q)
+{
+    const double d = ZERO_ORIGIN ? X : X - x0;  // X - (+-0) is X up to the sign of a zero
+    const long long bits = __double_as_longlong(d);
+    if (!(bits <= dmax_bits && (bits >= 0 || bits == (long long)0x8000000000000000ULL)))
+        return false;
+    const int be = (int)((bits >> 52) & 0x7ff);  // biased exponent of d
+    const int u = be - 1023 + s;                 // exponent of t = d 2^s
+    if (be == 0 || u < 0) {                      // t < 1
+        e = 0;
+        q = first_cell_xi(bits, s);
+        return true;
+    }
+    const long long sig = (bits & 0xfffffffffffffLL) | (1LL << 52);
+    const int f = (int)(sig >> (52 - u));  // floor(t) >= 1, u <= 30
+    if (f >= N) {                          // t = N: the last cell's far face
+        e = N - 1;
+        q = 1.0;
+        return true;
+    }
+    e = f;
+    const long long Z = 2 * (sig & ((1LL << (52 - u)) - 1)) - (1LL << (52 - u));
+    q = Z == 0 ? 0.0 : exact_scaled(Z, u - 52);
+    return true;
+}
+
+// ZERO_ORIGIN: the caller has checked g.zero_origin (x0 = 0 on every axis)
+template <typename S, bool ZERO_ORIGIN = false>
 __device__ __forceinline__ int locate_point(const GridArgs &g, int64_t b,
                                             const double *__restrict__ X,
                                             int32_t *__restrict__ elem, S *__restrict__ xi)
 {
+    if (g.shifted) {
+        int ex = 0, ey = 0, ez = 0;
+        double qx = 0.0, qy = 0.0, qz = 0.0;
+        const bool in =
+            shifted_axis<ZERO_ORIGIN>(X[3 * b + 0], g.x0, g.sx, g.dmax_bits[0], g.Nx, ex, qx) &
+            shifted_axis<ZERO_ORIGIN>(X[3 * b + 1], g.y0, g.sy, g.dmax_bits[1], g.Ny, ey, qy) &
+            shifted_axis<ZERO_ORIGIN>(X[3 * b + 2], g.z0, g.sz, g.dmax_bits[2], g.Nz, ez, qz);
+        if (!in) {
+            elem[b] = -1;
+            xi[3 * b + 0] = S(0);
+            xi[3 * b + 1] = S(0);
+            xi[3 * b + 2] = S(0);
+            return -1;
+        }
+        xi[3 * b + 0] = (S)qx;
+        xi[3 * b + 1] = (S)qy;
+        xi[3 * b + 2] = (S)qz;
+        const int e = ex + g.Nx * (ey + g.Ny * ez);
+        elem[b] = e;
+        return e;
+    }
     const double tx = grid_coord(X[3 * b + 0], g.x0, g.hx, g.rx);
     const double ty = grid_coord(X[3 * b + 1], g.y0, g.hy, g.ry);
     const double tz = grid_coord(X[3 * b + 2], g.z0, g.hz, g.rz);

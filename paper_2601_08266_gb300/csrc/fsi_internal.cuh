@@ -102,10 +102,15 @@ struct fsi_mesh {
     // scratch: per-brick node-block partial sums of the VMS operators
     void *vms_scratch;
     size_t vms_scratch_bytes;
-    // scratch: cell fill counters [E+1] + scan block sums + misc counters
+    // scratch: cell fill counters [E+1] + scan scratch + misc counters;
+    // hash_clean: the counters are known to be all zero
     int32_t *hash_fill;
     int32_t *scan_tmp;
     int64_t scan_tmp_len;
+    bool hash_clean;
+    // grow-only point scratch of the cell table ((point, cell) pairs)
+    int2 *pt_tmp;
+    int64_t pt_tmp_cap;
     int64_t *dev_counters;  // [0] outside count, [1] error flag
     // scratch: per-cell corner sums of the spreading operator [E][8][3]
     void *spread_scratch;
@@ -249,10 +254,17 @@ fsi_status require_structured(const fsi_mesh *m, const char *what);
 
 // cell -> points table (dlm.cu): from per-cell counts in fill[0..E), an
 // exclusive scan into cell_start[E+1], a scatter of the points into perm and
-// a per-cell sort by point index (outside points last).  fill is reused as
-// cursors; scan_tmp holds cell_table_scan_ints(E) ints.
+// a per-cell sort by point index (outside points last).  fill is counted
+// back down as the slots are handed out and is all zero again on return;
+// scan_tmp holds cell_table_scan_ints(E) ints, all zero before the first
+// call, which every call leaves so.
 int64_t cell_table_scan_ints(int64_t E);
+// With tmp (m (point, cell) pairs of scratch), the locate kernel has left
+// each point's arrival slot in perm and counted outside points in fill[E];
+// the slices are then ordered by a rank pass from tmp into perm.  Without
+// tmp, fill[E] is unused and the slices are sorted in place in perm.
 fsi_status build_cell_table(cudaStream_t s, int64_t E, int64_t m, const int32_t *elem,
-                            int32_t *fill, int32_t *scan_tmp, int32_t *cell_start, int32_t *perm);
+                            int32_t *fill, int32_t *scan_tmp, int32_t *cell_start, int32_t *perm,
+                            int2 *tmp = nullptr);
 
 }  // namespace fsi

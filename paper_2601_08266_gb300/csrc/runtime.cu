@@ -249,13 +249,19 @@ fsi_status fsi_mesh_create(const fsi_grid *grid, const fsi_physics *phys, int de
         for (int p = 0; p < 3; ++p)
             m->brick[op][p] = op == 2 ? Brick{8, 4, 4, 256} : Brick{8, 8, 4, 256};
     fsi_status st = FSI_OK;
-    // cell-hash scratch: fill counters [E+1], scan block sums, counters
-    int64_t nblk = (E + 1 + 2047) / 2048 + 1;
+    // cell-hash scratch: fill counters [E+1], scan scratch, counters; both
+    // start at zero and every cell-table build leaves them so
+    int64_t nblk = cell_table_scan_ints(E);
     m->scan_tmp_len = nblk;
     if (st == FSI_OK)
         st = check_cuda(cudaMalloc(&m->hash_fill, (E + 1) * sizeof(int32_t)), "hash scratch");
     if (st == FSI_OK)
         st = check_cuda(cudaMalloc(&m->scan_tmp, nblk * sizeof(int32_t)), "scan scratch");
+    if (st == FSI_OK)
+        st = check_cuda(cudaMemset(m->hash_fill, 0, (E + 1) * sizeof(int32_t)), "hash scratch");
+    if (st == FSI_OK)
+        st = check_cuda(cudaMemset(m->scan_tmp, 0, nblk * sizeof(int32_t)), "scan scratch");
+    m->hash_clean = st == FSI_OK;
     if (st == FSI_OK)
         st = check_cuda(cudaMalloc(&m->dev_counters, 8 * sizeof(int64_t)), "counter scratch");
     if (st == FSI_OK) st = ensure_vms_scratch(m, m->brick[1][0], sizeof(double));
@@ -276,6 +282,7 @@ void fsi_mesh_destroy(fsi_mesh *m)
     cudaFree(m->vms_scratch);
     cudaFree(m->hash_fill);
     cudaFree(m->scan_tmp);
+    cudaFree(m->pt_tmp);
     cudaFree(m->dev_counters);
     cudaFree(m->spread_scratch);
     destroy_newton_workspace(m);

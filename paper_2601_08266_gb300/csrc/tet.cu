@@ -940,6 +940,7 @@ fsi_status fsi_tetmesh_create(int64_t n_nodes, const double *X, int64_t n_tets,
     };
     ok = cudaMemcpyAsync(m->tets, tets, n_tets * sizeof(int4), cudaMemcpyDeviceToDevice, s) ==
              cudaSuccess &&
+         cudaMemsetAsync(m->scan_tmp, 0, (size_t)ntmp * sizeof(int32_t), s) == cudaSuccess &&
          up(m->node_start, nstart.data(), nstart.size() * sizeof(int32_t)) &&
          up(m->node_slot, nslot.data(), nslot.size() * sizeof(int32_t)) &&
          up(m->bucket_start, bstart.data(), bstart.size() * sizeof(int32_t)) &&
