@@ -24,7 +24,22 @@ struct GridArgs {
     int sx, sy, sz;
     long long dmax_bits[3];
     int zero_origin;  // x0_k == 0 (either sign) on every axis
+    // exact division of an element index e < 2^31 by Nx and by Ny:
+    // e / N = (e * div_m) >> div_k (see division_magic)
+    unsigned long long div_mx, div_my;
+    int div_kx, div_ky;
 };
+
+// multiplier and shift of the exact division by d (1 <= d < 2^31) of every
+// n < 2^31: k = 31 + ceil(log2 d), M = ceil(2^k / d); then M d - 2^k < d and
+// n M / 2^k < n/d + 2^(31-k) <= n/d + 1/d, which cannot pass the next integer
+inline void division_magic(int d, unsigned long long &M, int &k)
+{
+    int l = 0;
+    while ((1LL << l) < d) ++l;
+    k = 31 + l;
+    M = ((1ULL << k) + (unsigned long long)d - 1) / (unsigned long long)d;
+}
 
 // the exact reciprocal of h when h = 2^e (with 1/h a normal double), else 0
 inline double pow2_reciprocal(double h)
@@ -54,6 +69,8 @@ inline void set_reciprocals(GridArgs &g)
         std::memcpy(&g.dmax_bits[k], &dmax, sizeof dmax);
     }
     g.zero_origin = g.x0 == 0.0 && g.y0 == 0.0 && g.z0 == 0.0;
+    division_magic(g.Nx, g.div_mx, g.div_kx);
+    division_magic(g.Ny, g.div_my, g.div_ky);
     g.sx = sh[0];
     g.sy = sh[1];
     g.sz = sh[2];
@@ -467,6 +484,15 @@ __device__ __forceinline__ void block_sort_cell(int64_t E, int64_t m,
     __syncthreads();
 }
 
+// (ex, ey, ez) of element e = ex + Nx (ey + Ny ez), 0 <= e < 2^31
+__device__ __forceinline__ void elem_coords(const GridArgs &g, int e, int &ex, int &ey, int &ez)
+{
+    const int q = (int)(((unsigned long long)e * g.div_mx) >> g.div_kx);  // e / Nx
+    ez = (int)(((unsigned long long)q * g.div_my) >> g.div_ky);          // q / Ny
+    ex = e - q * g.Nx;
+    ey = q - ez * g.Ny;
+}
+
 template <typename T> __device__ __forceinline__ T shape_1d(T xi, int side)
 {
     return side ? (T(1) + xi) : (T(1) - xi);
@@ -487,7 +513,8 @@ __device__ __forceinline__ void interp_point(
     const int e = elem[b];
     T ux = T(0), uy = T(0), uz = T(0);
     if (e >= 0 && e < E) {
-        const int ex = e % g.Nx, ey = (e / g.Nx) % g.Ny, ez = e / (g.Nx * g.Ny);
+        int ex, ey, ez;
+        elem_coords(g, e, ex, ey, ez);
         const T x0 = to_c<T>(xi[3 * b]), x1 = to_c<T>(xi[3 * b + 1]),
                 x2 = to_c<T>(xi[3 * b + 2]);
         const int n0 = ex + NX1 * ey + NXY1 * ez;
@@ -526,7 +553,8 @@ __device__ __forceinline__ void interp_point_pair(
     const int e = valid ? elem[b] : -1;
     T ux = T(0), uy = T(0), uz = T(0);
     if (e >= 0 && e < E) {
-        const int ex = e % g.Nx, ey = (e / g.Nx) % g.Ny, ez = e / (g.Nx * g.Ny);
+        int ex, ey, ez;
+        elem_coords(g, e, ex, ey, ez);
         const T x0 = to_c<T>(xi[3 * b]), x1 = to_c<T>(xi[3 * b + 1]),
                 x2 = to_c<T>(xi[3 * b + 2]);
         const int n0 = ex + ax + NX1 * ey + NXY1 * ez;
