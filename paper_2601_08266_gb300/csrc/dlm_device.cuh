@@ -722,19 +722,39 @@ __device__ __forceinline__ void spread_node(const GridArgs &g, int i, int j, int
                                             typename StorageOf<T>::type *__restrict__ F,
                                             int accumulate)
 {
-    bool occ[8];
+    using St = typename StorageOf<T>::type;
+    St *o = F + 4 * ((size_t)i + (size_t)(g.Nx + 1) * (j + (size_t)(g.Ny + 1) * k));
+    // the (up to) four rows of cells around the node; a row without points
+    // (most rows, for thin leaflets) is told by two entries that every node
+    // of the row reads alike, and a node with no such row is done at once
+    // (a branch the lanes of a warp, one node row, take alike)
+    const int32_t *row[4];
+    bool rocc[4];
 #pragma unroll
     for (int rc = 0; rc < 4; ++rc) {
         const int ey = j - (rc & 1), ez = k - (rc >> 1);
-        occ[2 * rc] = occ[2 * rc + 1] = false;
+        rocc[rc] = false;
+        row[rc] = start;
         if (ey < 0 || ez < 0 || ey >= g.Ny || ez >= g.Nz) continue;
-        // a row of cells without points (most rows, for thin leaflets) is
-        // skipped on two entries that every node of the row reads alike
-        const int32_t *row = start + (size_t)g.Nx * (ey + (size_t)g.Ny * ez);
-        if (row[g.Nx] == row[0]) continue;
+        row[rc] = start + (size_t)g.Nx * (ey + (size_t)g.Ny * ez);
+        rocc[rc] = row[rc][g.Nx] != row[rc][0];
+    }
+    if (!(rocc[0] | rocc[1] | rocc[2] | rocc[3])) {
+        if (!accumulate) {
+            o[0] = St(0);
+            o[1] = St(0);
+            o[2] = St(0);
+        }
+        return;
+    }
+    bool occ[8];
+#pragma unroll
+    for (int rc = 0; rc < 4; ++rc) {
+        occ[2 * rc] = occ[2 * rc + 1] = false;
+        if (!rocc[rc]) continue;
         // st[0] = start of cell i of the row (for i = Nx the entry after the
         // row's last cell, still inside the table's E + 1 entries)
-        const int32_t *st = row + i;
+        const int32_t *st = row[rc] + i;
         const int s0 = st[0];
         if (i < g.Nx) occ[2 * rc] = st[1] > s0;      // cell i     (cx = 0)
         if (i > 0) occ[2 * rc + 1] = s0 > st[-1];    // cell i - 1 (cx = 1)
@@ -752,7 +772,6 @@ __device__ __forceinline__ void spread_node(const GridArgs &g, int i, int j, int
         fz = fz + sc[2];
         touched = true;
     }
-    auto *o = F + 4 * ((size_t)i + (size_t)(g.Nx + 1) * (j + (size_t)(g.Ny + 1) * k));
     if (accumulate) {
         if (touched) {
             o[0] = to_s(to_c<T>(o[0]) + fx);
