@@ -7,8 +7,10 @@ against the oracle, on the cases the uniform-grid kernels branch on:
   infinities and NaN;
 - grids of more than 1024 scan tiles (2048 cells each: the tile sums are
   scanned by one CTA first) and of fewer;
-- cell segments (32 consecutive cells) holding at most 32 points, 33 to 128
-  points, and more (cells sorted one at a time, the CTA-sorted dense list);
+- cells of one point, 2 to 128 points (placed by the rank pass) and more
+  (the CTA-sorted dense list), the tail of outside points among them (the
+  in-place variant of the table, without point scratch, is covered through
+  fsi_locate_noalloc and the tetrahedral mesh);
 - repeated calls on one mesh with changing point sets (the per-cell counters
   and the scan scratch are left at zero by every call).
 """
@@ -112,15 +114,14 @@ def clustered_points(N, rng):
 
     parts = [
         in_cell(3, 4, 5, 200),        # a dense cell (CTA sort)
-        in_cell(4, 4, 5, 129),        # just over a warp's limit
+        in_cell(4, 4, 5, 129),        # just over the rank pass's limit
         in_cell(9, 2, 2, 128),        # exactly 128
-        in_cell(10, 2, 2, 40),        # same segment: 168 points, cells one at a time
+        in_cell(10, 2, 2, 40),
         in_cell(20, 7, 3, 33),
     ]
-    # a segment of 33..128 points spread over several cells (composite sort)
+    # neighbouring cells of a few points each
     for i in range(0, 24, 3):
         parts.append(in_cell(i, 11, 6, 9))
-    # segments of <= 32 points
     for i in range(0, 32, 4):
         parts.append(in_cell(i, 13, 1, 3))
     parts.append(rng.uniform(0, 1, (20000, 3)))
@@ -165,3 +166,4 @@ def test_cell_table_fewer_tiles(fsi, oracle):
         X = rng.uniform(-0.02, 1.02, (60_000, 3))
         check(fsi, oracle, mesh, grid, X)
         check(fsi, oracle, mesh, grid, X[:5000])
+
