@@ -27,12 +27,18 @@ template <typename T> struct DlmDesc {
     const vec4<T> *U;
     T *u, *F, *S;
     // batched location: raw points (null when the item brings its own
-    // table), per-cell counters [E+1] and scan tile sums [ntiles]; the step
-    // then writes elem, xi, start and perm
+    // table), per-cell counters [E+1], scan tile sums [ntiles] (+ the count
+    // of CTA-sorted cells) and (point, cell) pairs [m]; the step then writes
+    // elem, xi, start and perm
     const double *X;
     int32_t *fill, *tiles;
+    int2 *pairs;
     int64_t ntiles;
 };
+
+// cells of more points than this are sorted by a CTA instead of the rank
+// pass (whose work per point grows with its cell's size)
+constexpr int kBatchRankMax = 512;
 
 constexpr int kChunk = 256;  // nodes / points per work item; 8 cell segments per item
 
@@ -100,7 +106,9 @@ __global__ void batch_locate_kernel(const DlmDesc<T> *desc, const int64_t *prefi
         if (D.X && b < D.m) {
             const int e = dlmd::locate_point<T>(D.g, b, D.X, const_cast<int32_t *>(D.elem),
                                                 const_cast<T *>(D.xi));
-            if (e >= 0) atomicAdd(D.fill + e, 1);
+            // the count the cell had before this point (outside points count
+            // in the tail cell E): the point's slot in its cell's slice
+            const_cast<int32_t *>(D.perm)[b] = atomicAdd(D.fill + (e >= 0 ? (int64_t)e : D.E), 1);
         }
     }
 }
@@ -146,6 +154,8 @@ __global__ void batch_scan_add_kernel(const DlmDesc<T> *desc, const int64_t *pre
     }
 }
 
+// (point, cell) pairs at their arrival slots (the single-mesh table's
+// scatter, per instance)
 template <typename T>
 __global__ void batch_scatter_kernel(const DlmDesc<T> *desc, const int64_t *prefix, int count)
 {
@@ -154,41 +164,63 @@ __global__ void batch_scatter_kernel(const DlmDesc<T> *desc, const int64_t *pref
         const int inst = find_instance(prefix, count, item);
         const DlmDesc<T> &D = desc[inst];
         const int64_t b = (item - prefix[inst]) * kChunk + threadIdx.x;
-        if (D.X && b < D.m)
-            dlmd::scatter_point(b, D.E, D.elem, D.start, D.fill, const_cast<int32_t *>(D.perm));
+        if (D.X && b < D.m) {
+            const int e = D.elem[b];
+            const int c = e >= 0 ? e : (int)D.E;
+            const int64_t pos = (int64_t)D.start[c] + D.perm[b];
+            if (pos >= 0 && pos < D.m) D.pairs[pos] = make_int2((int)b, c);
+        }
     }
 }
 
-// kChunk cells per item: one warp per 32 consecutive cells (cell E = the tail
-// of outside points)
+// each slot's final place: the number of its cell's points with a smaller
+// index (cells of more than kBatchRankMax points go to the dense list in the
+// spent counters, counted in tiles[ntiles])
 template <typename T>
-__global__ void batch_cell_sort_kernel(const DlmDesc<T> *desc, const int64_t *prefix, int count)
+__global__ void batch_rank_kernel(const DlmDesc<T> *desc, const int64_t *prefix, int count)
 {
     const int64_t total = prefix[count];
-    const int warp = threadIdx.x >> 5;
     for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
         const int inst = find_instance(prefix, count, item);
         const DlmDesc<T> &D = desc[inst];
-        const int64_t c0 = (item - prefix[inst]) * kChunk + 32 * warp;
-        if (D.X && c0 <= D.E)
-            dlmd::cell_sort_segment(D.E, D.m, D.start, const_cast<int32_t *>(D.perm), c0, D.fill,
-                                    D.tiles + D.ntiles);
+        const int64_t k = (item - prefix[inst]) * kChunk + threadIdx.x;
+        if (!D.X || k >= D.m) continue;
+        const int2 p = D.pairs[k];
+        const int lo = D.start[p.y];
+        const int hi = p.y < D.E ? D.start[p.y + 1] : (int)D.m;
+        if (hi - lo > kBatchRankMax) {
+            if (k == lo) D.fill[atomicAdd(D.tiles + D.ntiles, 1)] = p.y;
+            continue;
+        }
+        int r = 0;
+        for (int j = lo; j < hi; ++j) r += D.pairs[j].x < p.x;
+        const_cast<int32_t *>(D.perm)[lo + r] = p.x;
     }
 }
 
-// the cells too full for a warp, listed per instance by the kernel above,
-// one CTA per cell
+// the listed cells, one CTA per cell: the pairs' points into perm, then a
+// bitonic sort in shared memory (or one lane's shell sort beyond
+// kBlockSortMax points)
 template <typename T>
 __global__ void __launch_bounds__(1024) batch_dense_sort_kernel(const DlmDesc<T> *desc, int count)
 {
     extern __shared__ int32_t sort_sh[];
+    // the instances' lists read as one: CTA b takes entries b, b + grid, ...
+    int64_t g = blockIdx.x, base = 0;
     for (int inst = 0; inst < count; ++inst) {
         const DlmDesc<T> &D = desc[inst];
         if (!D.X) continue;
         const int n = D.tiles[D.ntiles];
-        for (int k = blockIdx.x; k < n; k += gridDim.x)
-            dlmd::block_sort_cell(D.E, D.m, D.start, const_cast<int32_t *>(D.perm), D.fill[k],
-                                  sort_sh);
+        for (; g < base + n; g += gridDim.x) {
+            const int c = D.fill[g - base];
+            const int lo = D.start[c];
+            const int len = (c < D.E ? D.start[c + 1] : (int)D.m) - lo;
+            int32_t *perm = const_cast<int32_t *>(D.perm);
+            for (int i = threadIdx.x; i < len; i += blockDim.x) perm[lo + i] = D.pairs[lo + i].x;
+            __syncthreads();
+            dlmd::block_sort_cell(D.E, D.m, D.start, perm, c, sort_sh);
+        }
+        base += n;
     }
 }
 
@@ -271,7 +303,7 @@ struct fsi_batch {
     // device data
     void *desc_res, *desc_jac, *desc_dlm;                      // descriptors
     // [kRows][count+1]: bricks, node chunks, point chunks, spreading cell items,
-    // counter chunks (E+1 cells), scan tiles, cell-sort items (E+1 cells)
+    // counter chunks (E+1 cells), scan tiles
     int64_t *prefix;
     void *blocks;
     size_t blocks_bytes;
@@ -285,7 +317,7 @@ struct fsi_batch {
     double *xi64;
     size_t xi64_bytes;
     bool locate;
-    int64_t totals[7];
+    int64_t totals[6];
     // CUDA graph of one batched step
     cudaGraph_t graph;
     cudaGraphExec_t graph_exec;
@@ -294,7 +326,7 @@ struct fsi_batch {
 namespace fsi {
 namespace {
 
-constexpr int kRows = 7;
+constexpr int kRows = 6;
 
 // (Re)build descriptors and scratch for the batch's current brick shape.
 template <typename T> fsi_status build_batch(fsi_batch *b)
@@ -316,6 +348,8 @@ template <typename T> fsi_status build_batch(fsi_batch *b)
         loff[i] = loc_need;
         if (b->items[i].X) {
             loc_need += (size_t)(m->n_elems + 1 + dlmd::cell_tiles(m->n_elems) + 1) * sizeof(int32_t);
+            loc_need = (loc_need + 255) / 256 * 256;
+            loc_need += (size_t)b->items[i].m * sizeof(int2);  // the pairs
             loc_need = (loc_need + 255) / 256 * 256;
             xi64_need = std::max(xi64_need, (size_t)b->items[i].m * 3 * sizeof(double));
         }
@@ -381,6 +415,13 @@ template <typename T> fsi_status build_batch(fsi_batch *b)
         D.ntiles = dlmd::cell_tiles(m->n_elems);
         D.fill = it.X ? (int32_t *)((char *)b->loc + loff[i]) : nullptr;
         D.tiles = it.X ? D.fill + m->n_elems + 1 : nullptr;
+        if (it.X) {
+            const size_t off = ((size_t)(m->n_elems + 1 + D.ntiles + 1) * sizeof(int32_t) + 255) /
+                               256 * 256;
+            D.pairs = (int2 *)((char *)b->loc + loff[i] + off);
+        } else {
+            D.pairs = nullptr;
+        }
         const int64_t nb = (int64_t)res[i].nbx * res[i].nby * res[i].nbz;
         pre[0 * (C + 1) + i + 1] = pre[0 * (C + 1) + i] + nb;
         pre[1 * (C + 1) + i + 1] = pre[1 * (C + 1) + i] + (m->n_nodes + kChunk - 1) / kChunk;
@@ -391,7 +432,6 @@ template <typename T> fsi_status build_batch(fsi_batch *b)
         const int64_t cells = it.X ? (m->n_elems + 1 + kChunk - 1) / kChunk : 0;
         pre[4 * (C + 1) + i + 1] = pre[4 * (C + 1) + i] + cells;
         pre[5 * (C + 1) + i + 1] = pre[5 * (C + 1) + i] + (it.X ? D.ntiles : 0);
-        pre[6 * (C + 1) + i + 1] = pre[6 * (C + 1) + i] + cells;
     }
     for (int k = 0; k < kRows; ++k) b->totals[k] = pre[k * (C + 1) + C];
     cudaStream_t s = b->stream;
@@ -447,12 +487,10 @@ template <typename T> fsi_status run_batched(fsi_batch *b, int phases)
         batch_scan_add_kernel<T><<<persistent_grid(b, b->totals[5]), 256, 0, s>>>(
             dd, pre + 5 * (C + 1), C);
         if (b->totals[2] > 0) {
-            batch_clear_kernel<T><<<persistent_grid(b, b->totals[4]), kChunk, 0, s>>>(
-                dd, pre + 4 * (C + 1), C);
             batch_scatter_kernel<T><<<persistent_grid(b, b->totals[2]), kChunk, 0, s>>>(
                 dd, pre + 2 * (C + 1), C);
-            batch_cell_sort_kernel<T><<<persistent_grid(b, b->totals[6]), kChunk, 0, s>>>(
-                dd, pre + 6 * (C + 1), C);
+            batch_rank_kernel<T><<<persistent_grid(b, b->totals[2]), kChunk, 0, s>>>(
+                dd, pre + 2 * (C + 1), C);
             const int smem = dlmd::kBlockSortMax * (int)sizeof(int32_t);
             FSI_TRY(set_smem_limit((const void *)batch_dense_sort_kernel<T>, smem));
             batch_dense_sort_kernel<T><<<b->sms, 1024, smem, s>>>(dd, C);
