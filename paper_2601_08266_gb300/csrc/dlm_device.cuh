@@ -310,25 +310,9 @@ __device__ __forceinline__ void scan_add_tile(int64_t E, int32_t *start, const i
     if (tile == 0 && threadIdx.x == 0) start[0] = 0;
 }
 
-// Point b into its cell's slice of perm through the per-cell cursors fill
-// (outside points form the tail "cell" E).
-__device__ __forceinline__ void scatter_point(int64_t b, int64_t E,
-                                              const int32_t *__restrict__ elem,
-                                              const int32_t *__restrict__ start, int32_t *fill,
-                                              int32_t *__restrict__ perm)
-{
-    const int e = elem[b];
-    const int64_t cell = e >= 0 ? e : E;
-    const int pos = start[cell] + atomicAdd(fill + cell, 1);
-    perm[pos] = (int32_t)b;
-}
-
-// Sort every cell's slice of perm ascending (restores the stable order).
-// Cell E is the tail of outside points [start[E], m).  One warp per segment of
-// 32 consecutive cells; each slice is sorted by ranks (values are distinct
-// point indices, so rank_i = #{j : v_j < v_i} is a permutation) held in
-// registers for slices of up to 128 points, and a single-lane shell sort
-// beyond (rare: very dense cells).
+// Sorting a cell's slice of perm ascending (restores the stable order; cell
+// E is the tail of outside points [start[E], m)): one lane's shell sort, the
+// fallback for slices too long for a CTA's shared memory.
 __device__ inline void shell_sort(int32_t *s, int len)
 {
     int gap = 1;
@@ -349,103 +333,13 @@ __device__ inline void shell_sort(int32_t *s, int len)
     }
 }
 
-// Ascending bitonic sorting network over N values in registers (all indices
-// compile-time constants, so nothing goes to local memory).
-template <int N> __device__ __forceinline__ void bitonic(int (&v)[N])
-{
-#pragma unroll
-    for (int k = 2; k <= N; k <<= 1)
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1)
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const int a = v[i], b = v[l];
-                    const bool up = (i & k) == 0;
-                    v[i] = up ? min(a, b) : max(a, b);
-                    v[l] = up ? max(a, b) : min(a, b);
-                }
-            }
-}
-
-// one lane sorts a slice of len <= N values in place
-template <int N> __device__ __forceinline__ void sort_slice(int32_t *sl, int len)
-{
-    int v[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) v[i] = i < len ? sl[i] : INT32_MAX;
-    bitonic<N>(v);
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-        if (i < len) sl[i] = v[i];
-}
-
-// Slices of up to kWarpSortMax points are sorted by the warp that owns the
-// cell's segment; fuller cells are put on a list (when the caller gives one)
-// and sorted by a whole CTA in shared memory (block_sort_cell), up to
-// kBlockSortMax points, beyond which one lane shell-sorts the slice.
+// Slices of up to kWarpSortMax points are ordered by a warp (the in-place
+// table) or the rank pass (the single-mesh table with point scratch); fuller
+// cells are listed and sorted by a whole CTA in shared memory
+// (block_sort_cell), up to kBlockSortMax points, beyond which one lane
+// shell-sorts the slice.
 constexpr int kWarpSortMax = 128;
 constexpr int kBlockSortMax = 32768;
-
-// the cells [c0, c0 + 32) (all 32 lanes of the warp call it); dense cells go
-// to dense[atomicAdd(dense_count, 1)] when dense is not null
-__device__ __forceinline__ void cell_sort_segment(int64_t E, int64_t m,
-                                                  const int32_t *__restrict__ start,
-                                                  int32_t *__restrict__ perm, int64_t c0,
-                                                  int32_t *dense = nullptr,
-                                                  int32_t *dense_count = nullptr)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t c = c0 + lane;
-    int lo = 0, len = 0;
-    if (c <= E) {
-        lo = start[c];
-        len = (c < E ? start[c + 1] : (int)m) - lo;
-    }
-    // up to 64 points: each lane sorts its own cell's slice in registers
-    if (len >= 2 && len <= 32)
-        sort_slice<32>(perm + lo, len);
-    else if (len > 32 && len <= 64)
-        sort_slice<64>(perm + lo, len);
-    // the CTA-sorted cells
-    if (dense && len > kWarpSortMax) dense[atomicAdd(dense_count, 1)] = (int32_t)c;
-    // fuller cells: the warp together
-    unsigned todo = __ballot_sync(0xffffffffu, len > 64 && (len <= kWarpSortMax || !dense));
-    while (todo) {
-        const int l = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int base = __shfl_sync(0xffffffffu, lo, l);
-        const int n = __shfl_sync(0xffffffffu, len, l);
-        int32_t *sl = perm + base;
-        __syncwarp();
-        if (n <= kWarpSortMax) {
-            // four values per lane, all in registers
-            int own[4], rk[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                own[k] = (lane + 32 * k < n) ? sl[lane + 32 * k] : INT32_MAX;
-                rk[k] = 0;
-            }
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc)
-#pragma unroll 8
-                for (int j = 0; j < 32; ++j) {
-                    const int wj = __shfl_sync(0xffffffffu, own[cc], j);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) rk[k] += wj < own[k];
-                }
-            __syncwarp();
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (lane + 32 * k < n) sl[rk[k]] = own[k];
-            __syncwarp();
-        } else {
-            if (lane == 0) shell_sort(sl, n);
-            __syncwarp();
-        }
-    }
-}
 
 // Sort the slice of cell c (cell E: the outside points) with the whole CTA: a
 // bitonic network over the slice padded with INT32_MAX to a power of two, in
