@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "fsi_internal.cuh"
 
@@ -238,53 +239,113 @@ __global__ void fitted_kernel(int64_t n4, const double *yfb, const double *ml, c
     }
 }
 
-// per-block partial sums of the normal equations of the fit: G_ij = J_i . J_j
-// (i <= j, 6 values, row by row) and r_i = J_i . R (3 values), FP32 products
-// summed in FP64
-constexpr int kFitBlocks = 96;
-constexpr int kFitSums = kFitDirs * (kFitDirs + 1) / 2 + kFitDirs;
-__global__ void fit_dots_kernel(int64_t n4, const float *Jd, const double *R, double *partial)
+// The fit's sums on the FP32 pipe: each product is split exactly (TwoProd:
+// p = x y rounded, e = fma(x, y, -p)) and added into a compensated pair
+// (s, c) (TwoSum of s and p, the errors gathered in c), about 2^-44 relative
+// per thread's sum; the CTA sums the pairs in FP64.  The residual's doubles
+// enter truncated to float (2^-23 relative per entry; the fit is a
+// least-squares model of three coefficients, judged afterwards by the true
+// residual of its candidate), formed from their bits by integer operations.
+// (FP64 products and sums took 555 us at 128^3: GB300's FP64 unit issues two
+// operations per SM and clock, and a double -> float conversion is one.)
+struct FitAcc {
+    float s, c;
+};
+__device__ __forceinline__ void fit_add(FitAcc &a, float p, float e)
 {
-    __shared__ double red[kFitSums][128];
-    double acc[kFitSums];
+    const float s = __fadd_rn(a.s, p);
+    const float bb = __fsub_rn(s, a.s);
+    const float t = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    a.s = s;
+    a.c = __fadd_rn(a.c, __fadd_rn(e, t));
+}
+// a += x y
+__device__ __forceinline__ void fit_mul(FitAcc &a, float x, float y)
+{
+    const float p = __fmul_rn(x, y);
+    fit_add(a, p, __fmaf_rn(x, y, -p));
+}
+// the float of a double with its significand truncated to 24 bits, from the
+// bits (no FP64 operation): zero below the float range, infinite above it,
+// NaN stays NaN
+__device__ __forceinline__ float trunc_to_float(double r)
+{
+    const long long b = __double_as_longlong(r);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ff);
+    const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (mant | ((b & 0xfffffffffffffLL) != 0)));
+    const int fe = e - 1023 + 127;
+    if (fe <= 0) return __uint_as_float(sign);
+    if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)fe << 23) | mant);
+}
+
+// per-block partial sums (FP64) of kSums compensated pairs in red
+template <int kSums, int kThreads>
+__device__ __forceinline__ void fit_block_sums(const FitAcc (&acc)[kSums], double (*red)[kThreads],
+                                               double *partial)
+{
 #pragma unroll
-    for (int k = 0; k < kFitSums; ++k) acc[k] = 0.0;
+    for (int k = 0; k < kSums; ++k) red[k][threadIdx.x] = (double)acc[k].s + (double)acc[k].c;
+    __syncthreads();
+    for (int st = kThreads / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int k = 0; k < kSums; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x < kSums) partial[kSums * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// per-block partial sums of the normal equations of the fit: G_ij = J_i . J_j
+// (i <= j, 6 values, row by row), r_i = J_i . R (3 values) and |R|^2 (the
+// model's; the fallback's reported norm is within 1e-6 of the FP64 one)
+constexpr int kFitBlocks = 608, kFitThreads = 256;  // 4 per SM of a GB300
+// doubles of per-block partial sums the handle keeps (the fit's 10 per block,
+// the training loss's one per block)
+constexpr int kPartialDoubles = 8192;
+static_assert((kFitDirs * (kFitDirs + 1) / 2 + kFitDirs + 1) * kFitBlocks <= kPartialDoubles,
+              "partial sums of the fit");
+constexpr int kFitSums = kFitDirs * (kFitDirs + 1) / 2 + kFitDirs;
+__global__ void __launch_bounds__(kFitThreads) fit_dots_kernel(int64_t n4, const float *Jd,
+                                                               const double *R, double *partial)
+{
+    __shared__ double red[kFitSums + 1][kFitThreads];
+    FitAcc acc[kFitSums + 1];
+#pragma unroll
+    for (int k = 0; k <= kFitSums; ++k) acc[k] = {0.0f, 0.0f};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double a[kFitDirs];
+        float a[kFitDirs];
 #pragma unroll
         for (int d = 0; d < kFitDirs; ++d) a[d] = Jd[d * n4 + i];
-        const double r = R[i];
+        const float r = trunc_to_float(R[i]);
         int k = 0;
 #pragma unroll
         for (int d = 0; d < kFitDirs; ++d)
 #pragma unroll
-            for (int e = d; e < kFitDirs; ++e) acc[k++] += a[d] * a[e];
+            for (int e = d; e < kFitDirs; ++e) fit_mul(acc[k++], a[d], a[e]);
 #pragma unroll
-        for (int d = 0; d < kFitDirs; ++d) acc[k++] += a[d] * r;
+        for (int d = 0; d < kFitDirs; ++d) fit_mul(acc[k++], a[d], r);
+        fit_mul(acc[k], r, r);
     }
-#pragma unroll
-    for (int k = 0; k < kFitSums; ++k) red[k][threadIdx.x] = acc[k];
-    __syncthreads();
-    for (int st = 64; st > 0; st >>= 1) {
-        if (threadIdx.x < st)
-            for (int k = 0; k < kFitSums; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
-        __syncthreads();
-    }
-    if (threadIdx.x < kFitSums) partial[kFitSums * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+    fit_block_sums<kFitSums + 1, kFitThreads>(acc, red, partial);
 }
 
-// per-block partial sums of |x|^2 (FP64)
-__global__ void sumsq_kernel(int64_t n, const double *x, double *partial)
+// per-block partial sums of |x|^2 in FP64 (the reported norm of a judged
+// residual: to FP64 accuracy), on a grid that keeps the FP64 unit busy
+__global__ void __launch_bounds__(kFitThreads) sumsq_kernel(int64_t n, const double *x,
+                                                            double *partial)
 {
-    __shared__ double red[256];
+    __shared__ double red[kFitThreads];
     double acc = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        acc += x[i] * x[i];
+        acc = fma(x[i], x[i], acc);
     red[threadIdx.x] = acc;
     __syncthreads();
-    for (int st = 128; st > 0; st >>= 1) {
+    for (int st = kFitThreads / 2; st > 0; st >>= 1) {
         if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
         __syncthreads();
     }
@@ -368,7 +429,7 @@ fsi_status fsi_mlp_create(int device, void *cuda_stream, int64_t max_batch, fsi_
             return check_cuda(e, "mlp activation allocation");
         }
     }
-    cudaError_t e = cudaMalloc(&h->loss_partial, 2048 * sizeof(double));
+    cudaError_t e = cudaMalloc(&h->loss_partial, kPartialDoubles * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->packed, mlp_tc_packed_bytes());
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->tc_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&h->gemm_work, tc_gemm_work_floats() * sizeof(float));
@@ -534,16 +595,17 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
         FSI_TRY(coupled_jacobian_f32(mesh, st, kFitDirs, xs, js, Rfb));
     }
     // normal equations G x = -r of min |R_fb + sum_i x_i J d_i|
-    fit_dots_kernel<<<kFitBlocks, 128, 0, s>>>(n4, Jd, Rfb, h->loss_partial);
-    sumsq_kernel<<<kFitBlocks, 256, 0, s>>>(n4, Rfb, h->loss_partial + kFitSums * kFitBlocks);
+    fit_dots_kernel<<<kFitBlocks, kFitThreads, 0, s>>>(n4, Jd, Rfb, h->loss_partial);
     FSI_TRY(check_launch("fit dots"));
-    double hp[(kFitSums + 1) * kFitBlocks];
-    FSI_CUDA(cudaMemcpyAsync(hp, h->loss_partial, sizeof hp, cudaMemcpyDeviceToHost, s), "memcpy");
+    std::vector<double> hp((kFitSums + 1) * kFitBlocks);
+    FSI_CUDA(cudaMemcpyAsync(hp.data(), h->loss_partial, hp.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, s),
+             "memcpy");
     FSI_CUDA(cudaStreamSynchronize(s), "sync");
     double q[kFitSums] = {}, rr = 0.0;
     for (int b = 0; b < kFitBlocks; ++b) {
-        for (int k = 0; k < kFitSums; ++k) q[k] += hp[kFitSums * b + k];
-        rr += hp[kFitSums * kFitBlocks + b];
+        for (int k = 0; k < kFitSums; ++k) q[k] += hp[(kFitSums + 1) * b + k];
+        rr += hp[(kFitSums + 1) * b + kFitSums];
     }
     const double r_fb = std::sqrt(rr);
     constexpr int K = kFitDirs;
@@ -616,10 +678,12 @@ fsi_status fsi_mlp_guess(fsi_mlp *h, fsi_mesh *mesh, const float *params, const 
     fsi_step_state tmp = *st;
     tmp.y = cand;
     FSI_TRY(fsi_coupled_residual(mesh, judge_prec, &tmp, Rc));
-    sumsq_kernel<<<kFitBlocks, 256, 0, s>>>(n4, Rc, h->loss_partial);
+    sumsq_kernel<<<kFitBlocks, kFitThreads, 0, s>>>(n4, Rc, h->loss_partial);
     FSI_TRY(check_launch("norm kernel"));
-    double hn[kFitBlocks];
-    FSI_CUDA(cudaMemcpyAsync(hn, h->loss_partial, sizeof hn, cudaMemcpyDeviceToHost, s), "memcpy");
+    std::vector<double> hn(kFitBlocks);
+    FSI_CUDA(cudaMemcpyAsync(hn.data(), h->loss_partial, hn.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, s),
+             "memcpy");
     FSI_CUDA(cudaStreamSynchronize(s), "sync");
     double rc = 0.0;
     for (int b = 0; b < kFitBlocks; ++b) rc += hn[b];
