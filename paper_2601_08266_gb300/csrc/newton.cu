@@ -19,8 +19,12 @@ namespace fsi {
 namespace {
 
 constexpr int kRedGrid = 456;   // fixed partial-sum grid (3 CTAs per SM): deterministic dots
+// fixed grid of the multi-update pass (4 CTAs per SM: its |w|^2 partials,
+// one row of kAxpyGrid; the multi-dot's 76 registers keep it at 3)
+constexpr int kAxpyGrid = 608;
 constexpr int kRedThreads = 256;
 constexpr int kDotGroup = 8;    // vectors per multi-dot pass
+static_assert(kDotGroup % 2 == 0, "the FP32 multi-dot pairs vectors");
 
 int grid1d(int64_t n, int threads = 256, int cap = sm_count() * 16)
 {
@@ -154,6 +158,31 @@ __device__ __forceinline__ void dot_acc(Comp &acc, float v, float w)
     acc.s = s;
     acc.c = __fadd_rn(acc.c, __fadd_rn(e, t));
 }
+// the same for two accumulators at once on the paired FP32 instructions
+// (FMUL2, FFMA2, FADD2): each half rounds exactly like the scalar
+// operation, so the two sums equal two scalar Comp sums bit for bit, at half
+// the issue slots
+struct Comp2 {
+    float2 s, c;
+};
+__device__ __forceinline__ float2 negf2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void dot_acc2(Comp2 &acc, float2 v, float2 w)
+{
+    const float2 p = __fmul2_rn(v, w);
+    const float2 e = __ffma2_rn(v, w, negf2(p));
+    const float2 s = __fadd2_rn(acc.s, p);
+    const float2 bb = __fadd2_rn(s, negf2(acc.s));
+    const float2 t = __fadd2_rn(__fadd2_rn(acc.s, negf2(__fadd2_rn(s, negf2(bb)))),
+                                __fadd2_rn(p, negf2(bb)));
+    acc.s = s;
+    acc.c = __fadd2_rn(acc.c, __fadd2_rn(e, t));
+}
+__device__ __forceinline__ void dot_renorm2(Comp2 &acc)
+{
+    const float2 s = __fadd2_rn(acc.s, acc.c);
+    acc.c = __fadd2_rn(acc.c, negf2(__fadd2_rn(s, negf2(acc.s))));
+    acc.s = s;
+}
 __device__ __forceinline__ void dot_renorm(double &) {}
 __device__ __forceinline__ void dot_renorm(Comp &acc)
 {
@@ -197,14 +226,24 @@ __global__ void __launch_bounds__(kRedThreads, 3) multi_dot_partial_kernel(
             for (int j = 0; j < kDotGroup; ++j)
                 if (j < cnt)
                     v[j] = ld4((k0 + j == self_k ? w : V + (int64_t)(k0 + j) * vstride) + i);
+                else
+                    v[j] = vec4<T>{T(0), T(0), T(0), T(0)};
+            // vectors j and j + 1 on the two halves of the paired
+            // instructions (a missing j + 1 sums zeros, unused)
 #pragma unroll
-            for (int j = 0; j < kDotGroup; ++j)
+            for (int j = 0; j < kDotGroup; j += 2)
                 if (j < cnt) {
-                    dot_acc(acc[j], v[j].x, wi.x);
-                    dot_acc(acc[j], v[j].y, wi.y);
-                    dot_acc(acc[j], v[j].z, wi.z);
-                    dot_acc(acc[j], v[j].w, wi.w);
-                    dot_renorm(acc[j]);
+                    Comp2 a2{make_float2(acc[j].s, acc[j + 1].s),
+                             make_float2(acc[j].c, acc[j + 1].c)};
+                    dot_acc2(a2, make_float2(v[j].x, v[j + 1].x), make_float2(wi.x, wi.x));
+                    dot_acc2(a2, make_float2(v[j].y, v[j + 1].y), make_float2(wi.y, wi.y));
+                    dot_acc2(a2, make_float2(v[j].z, v[j + 1].z), make_float2(wi.z, wi.z));
+                    dot_acc2(a2, make_float2(v[j].w, v[j + 1].w), make_float2(wi.w, wi.w));
+                    dot_renorm2(a2);
+                    acc[j].s = a2.s.x;
+                    acc[j].c = a2.c.x;
+                    acc[j + 1].s = a2.s.y;
+                    acc[j + 1].c = a2.c.y;
                 }
         } else {
 #pragma unroll
@@ -238,14 +277,15 @@ __global__ void __launch_bounds__(kRedThreads, 3) multi_dot_partial_kernel(
 
 // out[k] (+)= sum_b partial[k][b] for k < cnt; one block per k, fixed tree.
 // mode 0: store, 1: add, 2: store sqrt (norm)
+// (nb partials per k, rows kRedGrid apart)
 __global__ void multi_dot_final_kernel(int cnt, const double *partial, double *out, int mode,
-                                       const double *cond = nullptr)
+                                       const double *cond = nullptr, int nb = kRedGrid)
 {
     if (cond && *cond == 0.0) return;
     __shared__ double red[kRedThreads];
     const int k = blockIdx.x;
     double v = 0.0;
-    for (int b = threadIdx.x; b < kRedGrid; b += blockDim.x) v += partial[(int64_t)k * kRedGrid + b];
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partial[(int64_t)k * kRedGrid + b];
     red[threadIdx.x] = v;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -266,7 +306,7 @@ __global__ void multi_dot_final_kernel(int cnt, const double *partial, double *o
 // FMAs (the FMA order per entry is k = 0, 1, 2, ...).  With norm_partial the
 // same pass sums |w_new|^2 (like the dots: FP64, or exact FP32 products in
 // double-float) per CTA into norm_partial[block] (launch on the fixed
-// kRedGrid x kRedThreads grid); with cond, nothing happens when *cond is 0.
+// kAxpyGrid x kRedThreads grid); with cond, nothing happens when *cond is 0.
 constexpr int kMaxAxpy = 256;
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
@@ -602,7 +642,7 @@ struct Work {
     void *Vk = nullptr;                    // [restart+1][4n]
     void *w = nullptr, *z = nullptr, *x = nullptr, *b = nullptr;
     void *blocks = nullptr, *inv = nullptr;  // [n][16]
-    double *partial = nullptr;              // [restart+2][kRedGrid]
+    double *partial = nullptr;              // [restart+1][kRedGrid] + [kAxpyGrid]
     double *hcol = nullptr, *h2 = nullptr;  // [restart+2]
     double *hhost = nullptr;                // pinned
     int precond = 0;                        // 0 block-Jacobi, 1 Schur (pmg.cu)
@@ -671,7 +711,7 @@ fsi_status ensure_work(fsi_mesh *mesh, int64_t m_pts, int restart)
         {&W.pw, pm},
         {&W.Vk, v * (size_t)(restart + 1)}, {&W.w, v}, {&W.z, v}, {&W.x, v}, {&W.b, v},
         {&W.blocks, v * 4}, {&W.inv, v * 4}, {&W.ftmp, v},
-        {(void **)&W.partial, (size_t)(restart + 2) * kRedGrid * sizeof(double)},
+        {(void **)&W.partial, ((size_t)(restart + 1) * kRedGrid + kAxpyGrid) * sizeof(double)},
         {(void **)&W.hcol, (size_t)(restart + 2) * sizeof(double)},
         {(void **)&W.h2, (size_t)(restart + 2) * sizeof(double)},
     };
@@ -930,7 +970,7 @@ template <typename T>
 void multi_axpy(cudaStream_t s, int cnt, int64_t len, const T *V, int64_t ld, const double *h,
                 T *w, double *norm_partial = nullptr, const double *cond = nullptr)
 {
-    multi_axpy_kernel<T><<<kRedGrid, kRedThreads, 0, s>>>(cnt, len / 4, (const vec4<T> *)V,
+    multi_axpy_kernel<T><<<kAxpyGrid, kRedThreads, 0, s>>>(cnt, len / 4, (const vec4<T> *)V,
                                                           ld / 4, h, (vec4<T> *)w, norm_partial,
                                                           cond);
 }
@@ -1028,7 +1068,8 @@ fsi_status gmres(fsi_mesh *mesh, const fsi_step_state *st, int restart, int max_
             FSI_TRY(multi_dot<T>(mesh, j + 1, V, ld, w, W.h2, 0, -1, flag));
             multi_axpy<T>(s, j + 1, len, V, ld, W.h2, w, npart, flag);
             add_if_kernel<<<1, 64, 0, s>>>(j + 1, W.h2, W.hcol, flag);
-            multi_dot_final_kernel<<<1, kRedThreads, 0, s>>>(1, npart, W.hcol + j + 1, 2);
+            multi_dot_final_kernel<<<1, kRedThreads, 0, s>>>(1, npart, W.hcol + j + 1, 2, nullptr,
+                                                             kAxpyGrid);
             FSI_TRY(check_launch("Gram-Schmidt"));
             scale_by_inv_kernel<T><<<grid1d(len), 256, 0, s>>>(len, W.hcol + j + 1, w,
                                                               V + (int64_t)(j + 1) * ld);
