@@ -113,6 +113,31 @@ __global__ void add_xyz_kernel(int64_t n, const vec4<T> *__restrict__ f, vec4<T>
     }
 }
 
+// the same followed by the Dirichlet rows (Jx = x where mask), one pass
+template <typename T>
+__global__ void add_xyz_rows_kernel(int64_t n, const vec4<T> *__restrict__ f,
+                                    const uchar4 *__restrict__ mask, const vec4<T> *__restrict__ x,
+                                    vec4<T> *__restrict__ y)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const vec4<T> a = f[i];
+        const uchar4 mk = mask[i];
+        vec4<T> b = y[i];
+        b.x += a.x;
+        b.y += a.y;
+        b.z += a.z;
+        if (mk.x | mk.y | mk.z | mk.w) {
+            const vec4<T> xv = x[i];
+            if (mk.x) b.x = xv.x;
+            if (mk.y) b.y = xv.y;
+            if (mk.z) b.z = xv.z;
+            if (mk.w) b.w = xv.w;
+        }
+        y[i] = b;
+    }
+}
+
 template <typename T> __global__ void scale_kernel(int64_t n, T alpha, const T *x, T *y)
 {
     GRID_STRIDE(i, n) y[i] = alpha * x[i];
@@ -864,6 +889,13 @@ fsi_status coupled_jacobian_impl(fsi_mesh *mesh, const fsi_step_state *st, const
         FSI_TRY(cs);
         FSI_CUDA(cudaEventRecord(W.ev_join, W.side), "event record");
         FSI_CUDA(cudaStreamWaitEvent(s, W.ev_join, 0), "stream wait");
+        if (st->mask && (reinterpret_cast<uintptr_t>(st->mask) & 3) == 0) {
+            // the coupling's forces and the Dirichlet rows in one pass
+            add_xyz_rows_kernel<T><<<grid1d(n), 256, 0, s>>>(
+                n, (const vec4<T> *)W.ftmp, (const uchar4 *)st->mask, (const vec4<T> *)x,
+                (vec4<T> *)Jx);
+            return check_launch("coupling add kernel");
+        }
         add_xyz_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const vec4<T> *)W.ftmp, (vec4<T> *)Jx);
         FSI_TRY(check_launch("coupling add kernel"));
     }
