@@ -1583,7 +1583,8 @@ def mlp_section(args, dev, stream, W):
 def profile_case(args):
     """Small fixed cases for ncu captures (nothing is timed): 'vms_f64' runs the
     fused FP64 residual + Jacobian pass twice on the --grid grid with 4x4x4
-    bricks of 128 threads; 'dlm' runs location with the cell table, and FP32
+    bricks of 128 threads; 'vms_f32' runs the FP32 Jacobian apply twice on
+    the --grid grid with the default schedule; 'dlm' runs location with the cell table, and FP32
     and double-float interpolation and spreading, twice, on the --grid grid
     with --points leaflet points; 'blas1' runs the Krylov multi-dot and
     multi-update kernels twice each on 8 FP32 vectors of the --grid grid's
@@ -1611,7 +1612,16 @@ def profile_case(args):
         return 0
     mesh = fsi.Mesh(N, device=0)
     n = mesh.n_nodes
-    if args.profile_case == "vms_f64":
+    if args.profile_case == "vms_f32":
+        # the FP32 Jacobian apply of the mixed Newton step, default schedule
+        U = torch.as_tensor(inputs.fourier_field(N, seed=1), device=dev).float()
+        A = torch.as_tensor(inputs.fourier_field(N, seed=2), device=dev).float()
+        A[:, 3] = 1.0
+        x = torch.as_tensor(inputs.uniform_nodal(N, seed=3), device=dev).float()
+        J = torch.empty_like(U)
+        for _ in range(2):
+            fsi.fsi_jacobian_apply(mesh, fsi.FSI_F32, U, A, None, x, J)
+    elif args.profile_case == "vms_f64":
         fsi.fsi_mesh_set_brick(mesh, 2, fsi.FSI_F64, 4, 4, 4, 128)
         U = torch.as_tensor(inputs.fourier_field(N, seed=1), device=dev)
         A = torch.as_tensor(inputs.fourier_field(N, seed=2), device=dev)
@@ -1685,7 +1695,8 @@ def main():
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--batch-tune-f64", action="store_true")
-    ap.add_argument("--profile-case", choices=["vms_f64", "dlm", "blas1", "pmg"], default=None,
+    ap.add_argument("--profile-case", choices=["vms_f64", "vms_f32", "dlm", "blas1", "pmg"],
+                    default=None,
                     help="run one small fixed case for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile_case:

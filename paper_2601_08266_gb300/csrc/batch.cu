@@ -473,7 +473,8 @@ template <typename T> fsi_status run_batched(fsi_batch *b, int phases)
     cudaStream_t s = b->stream;
     const int C = b->count;
     const int64_t *pre = b->prefix;
-    const size_t smem = (size_t)b->brick.bx * b->brick.by * b->brick.bz * 8 * sizeof(vec4<T>);
+    const size_t smem = (size_t)vmsd::rel_records(b->brick.bx * b->brick.by * b->brick.bz) *
+                        sizeof(vec4<T>);
     if ((phases & 8) && b->locate) {
         const DlmDesc<T> *dd = (const DlmDesc<T> *)b->desc_dlm;
         batch_clear_kernel<T><<<persistent_grid(b, b->totals[4]), kChunk, 0, s>>>(

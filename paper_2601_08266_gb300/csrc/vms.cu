@@ -143,7 +143,7 @@ fsi_status launch_geo(fsi_mesh *m, const void *U, const void *A, const void *f, 
         P.blocks2 = P.blocks + (size_t)nbricks * (b.bx + 1) * (b.by + 1) * (b.bz + 1);
         P.out2 = (vec4<S> *)R;
     }
-    const size_t smem = (FUSED ? 2 : 1) * (size_t)b.bx * b.by * b.bz * 8 * sizeof(vec4<S>);
+    const size_t smem = (FUSED ? 2 : 1) * (size_t)vmsd::rel_records(b.bx * b.by * b.bz) * sizeof(vec4<S>);
     void (*kernel)(const VmsArgs<T>);
     if constexpr (MAPPED && std::is_same<T, df64>::value)
         kernel = vms_brick_kernel_capped<T, JAC, MAPPED, FUSED>;

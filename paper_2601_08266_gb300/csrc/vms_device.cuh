@@ -559,8 +559,16 @@ __device__ __forceinline__ void gp_jacobian_terms(const VmsArgs<T> &P, const GP<
 // One brick of elements: element contributions into rel (shared memory,
 // [bx*by*bz][8] node records), then the brick's node block into P.blocks.
 // FUSED (with JAC): the residual at the same Gauss-point state is projected
-// too, into rel + bx*by*bz*8 and then P.blocks2; the evaluation of U and A
+// too, into rel + rel_records(bx*by*bz) and then P.blocks2; the evaluation of U and A
 // and the base state are shared by the two operators.
+// Element records in shared memory, corner-major with one padding record
+// per corner row: corner c of brick element `slot` at c (nel + 1) + slot.
+// The 8 lanes of an element then store to 8 different bank groups, and the
+// node sums read consecutive elements from consecutive threads (element-major
+// records, 8 apart, put a warp's 32 reads on the same banks: 8-way conflicts).
+__host__ __device__ __forceinline__ int rel_records(int nel) { return 8 * (nel + 1); }
+__device__ __forceinline__ int rel_at(int nel, int slot, int c) { return c * (nel + 1) + slot; }
+
 template <typename T, bool JAC, bool MAPPED = false, bool FUSED = false>
 __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<T> *rel)
 {
@@ -683,7 +691,7 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
                 rr.z = P.detJ * rr.z;
                 rr.w = P.detJ * rr.w;
             }
-            if (slot < nel) rel[nel * 8 + slot * 8 + g] = valid ? rr : zero;
+            if (slot < nel) rel[rel_records(nel) + rel_at(nel, slot, g)] = valid ? rr : zero;
         }
         if (!JAC) {
             gp_residual_terms(P, q, X, Y);
@@ -757,7 +765,7 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
             r.z = P.detJ * r.z;
             r.w = P.detJ * r.w;
         }
-        if (slot < nel) rel[slot * 8 + g] = valid ? r : zero;
+        if (slot < nel) rel[rel_at(nel, slot, g)] = valid ? r : zero;
     }
     __syncthreads();
 
@@ -769,7 +777,7 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
 #pragma unroll
     for (int o = 0; o < kOut; ++o) {
         vec4<T> *blk = (o ? P.blocks2 : P.blocks) + (size_t)brick * nnodes;
-        const vec4<T> *rl = rel + o * nel * 8;
+        const vec4<T> *rl = rel + o * rel_records(nel);
         for (int nl = threadIdx.x; nl < nnodes; nl += blockDim.x) {
             const int ix = nl % nx1, iy = (nl / nx1) % ny1, iz = nl / (nx1 * ny1);
             vec4<T> acc = {T(0), T(0), T(0), T(0)};
@@ -777,7 +785,7 @@ __device__ __forceinline__ void brick_body(const VmsArgs<T> &P, int brick, vec4<
             for (int c = 0; c < 8; ++c) {
                 const int lx = ix - (c & 1), ly = iy - ((c >> 1) & 1), lz = iz - ((c >> 2) & 1);
                 if (lx < 0 || ly < 0 || lz < 0 || lx >= P.bx || ly >= P.by || lz >= P.bz) continue;
-                const vec4<T> r = rl[((lz * P.by + ly) * P.bx + lx) * 8 + c];
+                const vec4<T> r = rl[rel_at(nel, (lz * P.by + ly) * P.bx + lx, c)];
                 acc.x += r.x;
                 acc.y += r.y;
                 acc.z += r.z;
