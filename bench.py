@@ -915,8 +915,10 @@ def newton_section(args, dev, stream):
                        "residual (VMS, interp, spread; ~1e-14 vs FP64), also for the predictor's "
                        "judge")
     r_ref = None
-    im_f, isd_f = im.float().contiguous(), isd.float().contiguous()
-    om_c, osd_c = om.contiguous(), osd.contiguous()
+    im_f = isd_f = om_c = osd_c = None
+    if im is not None:  # the network was trained (the learned variant is wanted)
+        im_f, isd_f = im.float().contiguous(), isd.float().contiguous()
+        om_c, osd_c = om.contiguous(), osd.contiguous()
     # the same step from the same state, repeated (median wall time): the
     # mixed variants --newton-reps times, the slow FP64 one once
     for name, mixed, guess_kind, pc in variants:
