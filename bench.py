@@ -52,11 +52,13 @@ SEED = 2026
 # fused 2, locate 1 + scan 3 + scatter 1 + sort 1, interp 1, spread 2).
 LAUNCHES_PER_STEP = 12
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused native FP64
-# residual + Jacobian launch on the 64^3 workload (4x4x4 bricks, 128
-# threads: brick 26.43 + 0.35 MB, gather 32.79 + 0.06 MB), from one ncu
-# capture with a cache flush between the two kernels
-# (profiles/vms_fused_f64_64cubed_ncu.md)
-TRAFFIC_FUSED_F64_64 = {(4, 4, 4, 128): 26_427_136 + 353_280 + 32_786_176 + 58_112}
+# residual + Jacobian launch on the 64^3 workload, per brick schedule the
+# autotuner picks (4x4x4 bricks, 128 threads: brick 26.43 + 0.23 MB, gather
+# 32.79 + 0 MB; 8x4x2, 128 threads: brick 26.43 + 0.40 MB, gather 35.41 +
+# 0.004 MB), from ncu captures of the current kernels with a cache flush
+# between the two (profiles/vms_fused_f64_64cubed_ncu.md)
+TRAFFIC_FUSED_F64_64 = {(4, 4, 4, 128): 26_429_696 + 226_304 + 32_786_432 + 0,
+                        (8, 4, 2, 128): 26_429_952 + 403_712 + 35_407_616 + 4_096}
 # FP64 operations the fused FP64 brick kernel executes per element (ncu,
 # same capture: DFMA 1,808 (x2), DMUL 1,232, DADD 950): context for the
 # roofline, whose achieved rate counts the oracle's operations
@@ -1584,8 +1586,8 @@ def mlp_section(args, dev, stream, W):
 
 def profile_case(args):
     """Small fixed cases for ncu captures (nothing is timed): 'vms_f64' runs the
-    fused FP64 residual + Jacobian pass twice on the --grid grid with 4x4x4
-    bricks of 128 threads; 'vms_f32' runs the FP32 Jacobian apply twice on
+    fused FP64 residual + Jacobian pass twice on the --grid grid with the
+    --profile-brick schedule (default 4x4x4 bricks of 128 threads); 'vms_f32' runs the FP32 Jacobian apply twice on
     the --grid grid with the default schedule; 'dlm' runs location with the cell table, and FP32
     and double-float interpolation and spreading, twice, on the --grid grid
     with --points leaflet points; 'blas1' runs the Krylov multi-dot and
@@ -1624,7 +1626,8 @@ def profile_case(args):
         for _ in range(2):
             fsi.fsi_jacobian_apply(mesh, fsi.FSI_F32, U, A, None, x, J)
     elif args.profile_case == "vms_f64":
-        fsi.fsi_mesh_set_brick(mesh, 2, fsi.FSI_F64, 4, 4, 4, 128)
+        bx, by, bz, th = (int(v) for v in args.profile_brick.split(","))
+        fsi.fsi_mesh_set_brick(mesh, 2, fsi.FSI_F64, bx, by, bz, th)
         U = torch.as_tensor(inputs.fourier_field(N, seed=1), device=dev)
         A = torch.as_tensor(inputs.fourier_field(N, seed=2), device=dev)
         A[:, 3] = 1.0
@@ -1697,6 +1700,8 @@ def main():
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--batch-tune-f64", action="store_true")
+    ap.add_argument("--profile-brick", default="4,4,4,128",
+                    help="brick schedule bx,by,bz,threads of the vms_f64 profile case")
     ap.add_argument("--profile-case", choices=["vms_f64", "vms_f32", "dlm", "blas1", "pmg"],
                     default=None,
                     help="run one small fixed case for an ncu capture and exit")
