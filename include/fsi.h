@@ -179,7 +179,14 @@ fsi_status fsi_residual_jacobian_apply(fsi_mesh *mesh, fsi_prec prec, const void
  * increasing index order.  n_outside (HOST pointer, may be NULL) receives
  * the number of outside points; passing it makes the call synchronise.
  * strict != 0 returns FSI_ERR_OUTSIDE (after completing all outputs) when
- * some point is outside.  m may be 0.  m must be < 2^31.                   */
+ * some point is outside.  m may be 0.  m must be < 2^31.
+ * On a structured mesh the table uses a point scratch of the mesh (8 bytes
+ * per point) that grows on the first call with a table and on any later call
+ * with more points than before: that call allocates (cudaMalloc, FSI_ERR_OOM
+ * if it fails) and so must not be the first such call inside a stream
+ * capture.  Calls with at most as many points as an earlier one allocate
+ * nothing.  Between calls perm's contents are the caller's; during the call
+ * perm also serves as scratch before receiving the table.                  */
 fsi_status fsi_locate(fsi_mesh *mesh, int64_t m, const double *X, int32_t *elem, double *xi,
                       int32_t *cell_start, int32_t *perm, int64_t *n_outside, int strict);
 
