@@ -209,8 +209,10 @@ template <typename T> struct March {
 };
 
 enum MarchMode { kMarchApply = 0, kMarchCheb0 = 1, kMarchStep = 2 };
-// the vector v the stencil acts on: d alone, x alone, or x + d
-enum MarchSource { kVd = 0, kVx = 1, kVxd = 2 };
+// the vector v the stencil acts on: d alone, x alone, x + d, or (kVb) the
+// first Chebyshev direction from x = 0, d0 = b / (theta D), formed from b at
+// every staged node (so no pass writes d0 first)
+enum MarchSource { kVd = 0, kVx = 1, kVxd = 2, kVb = 3 };
 
 template <typename T>
 __device__ __forceinline__ T md_of(const Axis<T> &a, int i)
@@ -243,6 +245,8 @@ __global__ void __launch_bounds__(kMarchThreads) march_kernel(LevelArgs<T> L, Ma
     // faces), the x-row slots' centre coefficients and staged indices
     int64_t s_off[kStagePer];
     bool s_in[kStagePer];
+    // kVb: 1/D of the staged column's nodes on an interior / boundary plane
+    T s_iDi[kStagePer], s_iDb[kStagePer];
 #pragma unroll
     for (int r = 0; r < kStagePer; ++r) {
         const int q = tid + r * kMarchThreads;
@@ -251,6 +255,13 @@ __global__ void __launch_bounds__(kMarchThreads) march_kernel(LevelArgs<T> L, Ma
                   !((L.faces[0] && gi == 0) || (L.faces[1] && gi == L.NX1 - 1) ||
                     (L.faces[2] && gj == 0) || (L.faces[3] && gj == L.NY1 - 1));
         s_off[r] = gi + (int64_t)L.NX1 * gj;
+        if constexpr (VX == kVb) {
+            const T mx = md_of(L.a[0], gi), kx = kd_of(L.a[0], gi);
+            const T my = md_of(L.a[1], gj), ky = kd_of(L.a[1], gj);
+            const T a1 = kx * my + mx * ky + L.kappa * mx * my, a2 = mx * my;
+            s_iDi[r] = T(1) / (a1 * L.a[2].m_in + a2 * L.a[2].k_in);
+            s_iDb[r] = T(1) / (a1 * L.a[2].m_bd + a2 * L.a[2].k_bd);
+        }
     }
     T x_k[kXRowPer], x_m[kXRowPer];
     int x_v[kXRowPer];
@@ -286,9 +297,18 @@ __global__ void __launch_bounds__(kMarchThreads) march_kernel(LevelArgs<T> L, Ma
     auto stage = [&](int kk, T (&v)[kStagePer]) {
         const bool zcut = kk < 0 || kk >= L.NZ1 || (L.faces[4] && kk == 0) ||
                           (L.faces[5] && kk == L.NZ1 - 1);
+        if constexpr (VX == kVb) {
+            const bool zb = kk == 0 || kk == L.NZ1 - 1;
 #pragma unroll
-        for (int r = 0; r < kStagePer; ++r)
-            v[r] = (s_in[r] && !zcut) ? vsrc<T, VX>(M, s_off[r] + plane_n * kk) : T(0);
+            for (int r = 0; r < kStagePer; ++r)
+                v[r] = (s_in[r] && !zcut) ? M.inv_theta * M.b[s_off[r] + plane_n * kk] *
+                                                (zb ? s_iDb[r] : s_iDi[r])
+                                          : T(0);
+        } else {
+#pragma unroll
+            for (int r = 0; r < kStagePer; ++r)
+                v[r] = (s_in[r] && !zcut) ? vsrc<T, VX>(M, s_off[r] + plane_n * kk) : T(0);
+        }
     };
     // per row: (P, Q) of planes k-1, k; the node inputs of the next output
     // plane (b, d, v) loaded one plane ahead, the staged planes two ahead
@@ -318,11 +338,20 @@ __global__ void __launch_bounds__(kMarchThreads) march_kernel(LevelArgs<T> L, Ma
                 if (own[rr]) {
                     const int64_t nd = off[rr] + plane_n * kk;
                     if (M.b) b_nx[rr] = M.b[nd];
-                    if (MODE == kMarchStep) d_nx[rr] = M.d[nd];
-                    // v at the node: staged, unless eliminated (staged as 0)
-                    v_nx[rr] = (exy[rr] || ez)
-                                   ? vsrc<T, VX>(M, nd)
-                                   : vt[(ty + kMarchTY * rr + 1) * (kMarchX + 2) + tx + 1];
+                    if constexpr (VX == kVb) {
+                        // v = d0 at the node (staged, unless eliminated)
+                        const bool zb = kk == 0 || kk == L.NZ1 - 1;
+                        v_nx[rr] = (exy[rr] || ez)
+                                       ? M.inv_theta * b_nx[rr] * (zb ? iDb[rr] : iDi[rr])
+                                       : vt[(ty + kMarchTY * rr + 1) * (kMarchX + 2) + tx + 1];
+                        d_nx[rr] = v_nx[rr];
+                    } else {
+                        if (MODE == kMarchStep) d_nx[rr] = M.d[nd];
+                        // v at the node: staged, unless eliminated (staged as 0)
+                        v_nx[rr] = (exy[rr] || ez)
+                                       ? vsrc<T, VX>(M, nd)
+                                       : vt[(ty + kMarchTY * rr + 1) * (kMarchX + 2) + tx + 1];
+                    }
                 }
         }
         // the x rows of the plane at the CTA's columns, rows j0-1 .. j0+kMarchY
@@ -427,13 +456,16 @@ fsi_status march_launch(const PressureMG &P, int l, cudaStream_t s, March<T> M)
 }
 
 // the stencil pass in MODE: on v = M.x (apply, first Chebyshev direction) or
-// v = M.x + M.d (Chebyshev step; M.x null after a zero start)
+// v = M.x + M.d (Chebyshev step; M.x null after a zero start; both null: the
+// first step from x = 0, v = d0 = b / (theta D) formed in the pass)
 template <typename T, int MODE>
 fsi_status march(const PressureMG &P, int l, cudaStream_t s, const March<T> &M)
 {
     if constexpr (MODE == kMarchStep) {
         if (M.x) return march_launch<T, MODE, kVxd>(P, l, s, M);
-        return march_launch<T, MODE, kVd>(P, l, s, M);
+        if (M.d) return march_launch<T, MODE, kVd>(P, l, s, M);
+        if (!M.b) return FSI_ERR_ARG;
+        return march_launch<T, MODE, kVb>(P, l, s, M);  // the first step from x = 0
     } else {
         if (!M.x) return FSI_ERR_ARG;
         return march_launch<T, MODE, kVx>(P, l, s, M);
@@ -669,14 +701,15 @@ fsi_status chebyshev(fsi_mesh *m, int l, int degree, double lo, double hi, const
         M.d_next = degree == 1 ? nullptr : dbuf[0];
         M.x_final = degree == 1 ? x_out : nullptr;
         FSI_TRY((march<T, kMarchCheb0>(P, l, s, M)));
-    } else {
-        cheb0_kernel<T><<<grid3_strided(L), kRowBlock, 0, s>>>(
-            A, b, (T)(1.0 / theta), degree == 1 ? nullptr : dbuf[0], degree == 1 ? x_out : nullptr);
+    } else if (degree == 1) {
+        cheb0_kernel<T><<<grid3_strided(L), kRowBlock, 0, s>>>(A, b, (T)(1.0 / theta), nullptr,
+                                                               x_out);
         FSI_TRY(check_launch("pressure smoother"));
     }
     if (degree == 1) return FSI_OK;
+    // from x = 0 the first step forms d0 = b / (theta D) itself (no d0 pass)
     const T *xc = x_in;
-    const T *dc = dbuf[0];
+    const T *dc = x_in ? dbuf[0] : nullptr;
     double rho = 1.0 / s1;
     for (int it = 1; it < degree; ++it) {
         const double rho_new = 1.0 / (2.0 * s1 - rho);
@@ -689,6 +722,7 @@ fsi_status chebyshev(fsi_mesh *m, int l, int degree, double lo, double hi, const
         M.b = b;
         M.c1 = c1;
         M.c2 = c2;
+        M.inv_theta = (T)(1.0 / theta);
         M.x_next = last ? nullptr : xn;
         M.d_next = last ? nullptr : dn;
         M.x_final = last ? x_out : nullptr;
