@@ -150,6 +150,13 @@ void destroy_newton_workspace(fsi_mesh *m);
 fsi_status pmg_ensure(fsi_mesh *m);
 fsi_status pmg_set_faces(fsi_mesh *m, const int faces[6]);
 template <typename T> fsi_status pmg_vcycle(fsi_mesh *m, const T *b, T *x);
+// the V-cycle as the pressure block of the Schur preconditioner: the result
+// x goes straight into the pressure slot of z [n][4] as x / sigma, or
+// v [n][4]'s pressure where mask [n][4] (uint8, may be null) fixes it; false
+// (nothing launched) when the hierarchy has a single level
+template <typename T>
+fsi_status pmg_vcycle_schur(fsi_mesh *m, const T *b, T *z, const T *v, const uint8_t *mask,
+                            T inv_sigma, bool *done);
 void *pmg_fine_buffer(fsi_mesh *m, int which);
 void destroy_pmg(fsi_mesh *m);
 

@@ -1042,8 +1042,14 @@ fsi_status apply_precond(fsi_mesh *mesh, const fsi_step_state *st, const T *in, 
     T *xp = (T *)(amg ? amg_fine_buffer(mesh, 1) : pmg_fine_buffer(mesh, 1));
     schur_split_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, in, out, bp);
     FSI_TRY(check_launch("Schur split"));
-    FSI_TRY(amg ? amg_vcycle<T>(mesh, bp, xp) : pmg_vcycle<T>(mesh, bp, xp));
     const double sigma = mesh->alpha_f * mesh->gamma * mesh->phys.dt / (mesh->alpha_m * mesh->phys.rho);
+    if (!amg) {
+        // the V-cycle's last smoothing step writes z_p itself (no merge pass)
+        bool done = false;
+        FSI_TRY(pmg_vcycle_schur<T>(mesh, bp, out, in, st->mask, (T)(1.0 / sigma), &done));
+        if (done) return FSI_OK;
+    }
+    FSI_TRY(amg ? amg_vcycle<T>(mesh, bp, xp) : pmg_vcycle<T>(mesh, bp, xp));
     schur_merge_kernel<T><<<grid1d(n), 256, 0, s>>>(n, in, xp, st->mask, (T)(1.0 / sigma), out);
     return check_launch("Schur merge");
 }

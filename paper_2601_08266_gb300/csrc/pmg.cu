@@ -206,6 +206,12 @@ template <typename T> struct March {
     T c1, c2, inv_theta;
     T *y, *x_next, *d_next, *x_final;
     int kz;          // planes per CTA
+    // with z4 (a step's x_final): the result goes to z4[4 node + 3] as
+    // x_final * inv_sigma, or v4[4 node + 3] where m4[4 node + 3] is set
+    T *z4;
+    const T *v4;
+    const uint8_t *m4;
+    T inv_sigma;
 };
 
 enum MarchMode { kMarchApply = 0, kMarchCheb0 = 1, kMarchStep = 2 };
@@ -414,7 +420,11 @@ __global__ void __launch_bounds__(kMarchThreads) march_kernel(LevelArgs<T> L, Ma
                         M.d_next[node] = d0;
                 } else {
                     const T dn = M.c1 * d_cur[rr] + M.c2 * ((b_cur[rr] - Av) * inv_D);
-                    if (M.x_final) {
+                    if (M.z4) {
+                        M.z4[4 * node + 3] = (M.m4 && M.m4[4 * node + 3])
+                                                 ? M.v4[4 * node + 3]
+                                                 : (v_cur[rr] + dn) * M.inv_sigma;
+                    } else if (M.x_final) {
                         M.x_final[node] = v_cur[rr] + dn;
                     } else {
                         M.x_next[node] = v_cur[rr];
@@ -682,9 +692,17 @@ template <typename T> T *vec(void *p) { return static_cast<T *>(p); }
 // One kernel per step: step k reads (x_{k-1}, d_{k-1}) and writes
 // (x_k, d_k) to the other buffers of a ping-pong pair; the last step writes
 // x_m = x_{m-1} + d_{m-1} straight into x_out.
+// the Schur preconditioner's output of the V-cycle (see March::z4)
+template <typename T> struct SchurOut {
+    T *z4;
+    const T *v4;
+    const uint8_t *m4;
+    T inv_sigma;
+};
+
 template <typename T>
 fsi_status chebyshev(fsi_mesh *m, int l, int degree, double lo, double hi, const T *b,
-                     const T *x_in, T *x_out)
+                     const T *x_in, T *x_out, const SchurOut<T> *so = nullptr)
 {
     PressureMG &P = *m->pmg;
     PmgLevel &L = P.lev[l];
@@ -726,6 +744,12 @@ fsi_status chebyshev(fsi_mesh *m, int l, int degree, double lo, double hi, const
         M.x_next = last ? nullptr : xn;
         M.d_next = last ? nullptr : dn;
         M.x_final = last ? x_out : nullptr;
+        if (last && so) {
+            M.z4 = so->z4;
+            M.v4 = so->v4;
+            M.m4 = so->m4;
+            M.inv_sigma = so->inv_sigma;
+        }
         FSI_TRY((march<T, kMarchStep>(P, l, s, M)));
         xc = xn;
         dc = dn;
@@ -750,7 +774,10 @@ template <typename T> fsi_status coarse_solve(fsi_mesh *m, const T *b, T *x)
 
 // x = V_l(b): pre-smoothing from zero into t, residual, restriction, the
 // coarse cycle, prolongation into t, post-smoothing from t into x
-template <typename T> fsi_status vcycle_level(fsi_mesh *m, int l, const T *b, T *x)
+// (so: level l's result goes to the Schur preconditioner's output instead of
+// x; not on the coarsest level)
+template <typename T>
+fsi_status vcycle_level(fsi_mesh *m, int l, const T *b, T *x, const SchurOut<T> *so = nullptr)
 {
     PressureMG &P = *m->pmg;
     if (l == P.nlev - 1) return coarse_solve<T>(m, b, x);
@@ -765,7 +792,7 @@ template <typename T> fsi_status vcycle_level(fsi_mesh *m, int l, const T *b, T 
     FSI_TRY(vcycle_level<T>(m, l + 1, vec<T>(Lc.b), vec<T>(Lc.x)));
     prolong_kernel<T><<<grid3(L), kRowBlock, 0, m->stream>>>(A, Ac, vec<T>(Lc.x), t);
     FSI_TRY(check_launch("pressure prolong"));
-    return chebyshev<T>(m, l, kPmgNu, hi / 4.0, hi, b, t, x);
+    return chebyshev<T>(m, l, kPmgNu, hi / 4.0, hi, b, t, x, so);
 }
 
 fsi_status check_prec(fsi_prec p)
@@ -899,6 +926,24 @@ template <typename T> fsi_status pmg_vcycle(fsi_mesh *m, const T *b, T *x)
 }
 template fsi_status pmg_vcycle<double>(fsi_mesh *, const double *, double *);
 template fsi_status pmg_vcycle<float>(fsi_mesh *, const float *, float *);
+
+template <typename T>
+fsi_status pmg_vcycle_schur(fsi_mesh *m, const T *b, T *z, const T *v, const uint8_t *mask,
+                            T inv_sigma, bool *done)
+{
+    FSI_TRY(pmg_ensure(m));
+    *done = false;
+    PressureMG &P = *m->pmg;
+    if (P.nlev < 2) return FSI_OK;
+    const SchurOut<T> so{z, v, mask, inv_sigma};
+    FSI_TRY(vcycle_level<T>(m, 0, b, vec<T>(P.lev[0].x), &so));
+    *done = true;
+    return FSI_OK;
+}
+template fsi_status pmg_vcycle_schur<double>(fsi_mesh *, const double *, double *, const double *,
+                                             const uint8_t *, double, bool *);
+template fsi_status pmg_vcycle_schur<float>(fsi_mesh *, const float *, float *, const float *,
+                                            const uint8_t *, float, bool *);
 
 // level-0 right-hand side (which = 0) and solution (which = 1) buffers, n
 // entries of either precision; the Newton preconditioner gathers into them
