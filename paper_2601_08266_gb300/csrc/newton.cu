@@ -642,6 +642,35 @@ __global__ void schur_split_kernel(int n, const T *inv, const T *v, T *z, T *bp)
     }
 }
 
+// The GMRES basis scaling V = w / den fused with the Schur split of V for
+// the next preconditioner application (the arithmetic of scale_by_inv_kernel
+// and schur_split_kernel, one pass)
+template <typename T>
+__global__ void scale_split_kernel(int n, const double *den, const T *w, T *V, const T *inv, T *z,
+                                   T *bp)
+{
+    const double dd = *den;
+    const T sc = (T)(dd > 0.0 ? 1.0 / dd : 0.0);
+    GRID_STRIDE(node, n)
+    {
+        vec4<T> x = ld4((const vec4<T> *)w + node);
+        x.x *= sc;
+        x.y *= sc;
+        x.z *= sc;
+        x.w *= sc;
+        ((vec4<T> *)V)[node] = x;
+        const vec4<T> *M = (const vec4<T> *)(inv + 16 * node);
+        vec4<T> zr;
+        const vec4<T> m0 = ld4(M), m1 = ld4(M + 1), m2 = ld4(M + 2);
+        zr.x = m0.x * x.x + m0.y * x.y + m0.z * x.z;
+        zr.y = m1.x * x.x + m1.y * x.y + m1.z * x.z;
+        zr.z = m2.x * x.x + m2.y * x.y + m2.z * x.z;
+        zr.w = T(0);
+        ((vec4<T> *)z)[node] = zr;
+        bp[node] = x.w;
+    }
+}
+
 // z_p = V-cycle result / sigma, or z_p = v_p on Dirichlet pressure rows
 template <typename T>
 __global__ void schur_merge_kernel(int n, const T *v, const T *xp, const uint8_t *mask,
@@ -1028,7 +1057,10 @@ fsi_status host_scalar(fsi_mesh *mesh, const double *dev, double *out)
 // in and out must not alias (the split writes all of out's records before the
 // merge reads in's pressure slots)
 template <typename T>
-fsi_status apply_precond(fsi_mesh *mesh, const fsi_step_state *st, const T *in, T *out)
+// (presplit: scale_split_kernel has already written out's velocity slots and
+// the V-cycle's right-hand side from `in`)
+fsi_status apply_precond(fsi_mesh *mesh, const fsi_step_state *st, const T *in, T *out,
+                         bool presplit = false)
 {
     Work &W = mesh->newton->w;
     cudaStream_t s = mesh->stream;
@@ -1040,8 +1072,10 @@ fsi_status apply_precond(fsi_mesh *mesh, const fsi_step_state *st, const T *in, 
     const bool amg = uses_amg(mesh);
     T *bp = (T *)(amg ? amg_fine_buffer(mesh, 0) : pmg_fine_buffer(mesh, 0));
     T *xp = (T *)(amg ? amg_fine_buffer(mesh, 1) : pmg_fine_buffer(mesh, 1));
-    schur_split_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, in, out, bp);
-    FSI_TRY(check_launch("Schur split"));
+    if (!presplit) {
+        schur_split_kernel<T><<<grid1d(n), 256, 0, s>>>(n, (const T *)W.inv, in, out, bp);
+        FSI_TRY(check_launch("Schur split"));
+    }
     const double sigma = mesh->alpha_f * mesh->gamma * mesh->phys.dt / (mesh->alpha_m * mesh->phys.rho);
     if (!amg) {
         // the V-cycle's last smoothing step writes z_p itself (no merge pass)
@@ -1081,15 +1115,30 @@ fsi_status gmres(fsi_mesh *mesh, const fsi_step_state *st, int restart, int max_
         return std::isfinite(beta) ? FSI_OK : set_error(FSI_ERR_NAN, "GMRES: non-finite rhs");
     }
     const double target = rtol * beta0;
+    // with the geometric-multigrid Schur preconditioner every basis vector's
+    // scaling also does its Schur split for the next iteration
+    const bool fuse = W.precond != 0 && !uses_amg(mesh);
+    T *bp = nullptr;
+    if (fuse) {
+        FSI_TRY(pmg_ensure(mesh));
+        bp = (T *)pmg_fine_buffer(mesh, 0);
+    }
+    auto scale_basis = [&](const double *den, T *dst) {
+        if (fuse)
+            scale_split_kernel<T><<<grid1d(len / 4), 256, 0, s>>>(
+                (int)(len / 4), den, w, dst, (const T *)W.inv, z, bp);
+        else
+            scale_by_inv_kernel<T><<<grid1d(len), 256, 0, s>>>(len, den, w, dst);
+    };
     while (true) {
-        scale_by_inv_kernel<T><<<grid1d(len), 256, 0, s>>>(len, W.hcol, w, V);
+        scale_basis(W.hcol, V);
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
         int jj = 0;
         bool done = false;
         for (int j = 0; j < restart && its < max_its; ++j) {
             T *Vj = V + (int64_t)j * ld;
-            FSI_TRY(apply_precond<T>(mesh, st, Vj, z));
+            FSI_TRY(apply_precond<T>(mesh, st, Vj, z, fuse));
             FSI_TRY(coupled_jacobian_impl<T>(mesh, st, z, w));
             // classical Gram-Schmidt, h = V^T w (and |w|^2 in the same pass), with
             // a second pass only when Kahan's criterion flags a loss of
@@ -1109,8 +1158,7 @@ fsi_status gmres(fsi_mesh *mesh, const fsi_step_state *st, int restart, int max_
             multi_dot_final_kernel<<<1, kRedThreads, 0, s>>>(1, npart, W.hcol + j + 1, 2, nullptr,
                                                              kAxpyGrid);
             FSI_TRY(check_launch("Gram-Schmidt"));
-            scale_by_inv_kernel<T><<<grid1d(len), 256, 0, s>>>(len, W.hcol + j + 1, w,
-                                                              V + (int64_t)(j + 1) * ld);
+            scale_basis(W.hcol + j + 1, V + (int64_t)(j + 1) * ld);
             FSI_CUDA(cudaMemcpyAsync(W.hhost, W.hcol, (j + 2) * sizeof(double),
                                      cudaMemcpyDeviceToHost, s),
                      "memcpy");
