@@ -545,43 +545,55 @@ template <typename T> __global__ void block_apply_kernel(int n, const T *inv, co
 // Schur-complement block preconditioner, velocity part: inverse of the 3x3
 // velocity sub-block of each nodal block (Gauss-Jordan, partial pivoting,
 // FP64), stored in the upper-left 3x3 of the node's 16 slots.
+// Gauss-Jordan with partial pivoting in the blocks' own precision (an FP32
+// preconditioner's inverse is stored in FP32 anyway; in FP64 the 2.1 M
+// inversions at 128^3 took 366 us on GB300's FP64 unit)
 template <typename T> __global__ void block_invert3_kernel(int n, const T *blocks, T *inv)
 {
     GRID_STRIDE(node, n)
     {
-        double a[3][6];
+        T a[3][6];
+#pragma unroll
         for (int r = 0; r < 3; ++r)
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
-                a[r][c] = (double)blocks[16 * node + 4 * r + c];
-                a[r][3 + c] = r == c ? 1.0 : 0.0;
+                a[r][c] = blocks[16 * node + 4 * r + c];
+                a[r][3 + c] = r == c ? T(1) : T(0);
             }
         bool ok = true;
-        for (int col = 0; col < 3 && ok; ++col) {
+#pragma unroll
+        for (int col = 0; col < 3; ++col) {
+            if (!ok) break;
             int p = col;
+#pragma unroll
             for (int r = col + 1; r < 3; ++r)
                 if (fabs(a[r][col]) > fabs(a[p][col])) p = r;
-            if (!(fabs(a[p][col]) > 0.0)) {
+            if (!(fabs(a[p][col]) > T(0))) {
                 ok = false;
                 break;
             }
             if (p != col)
+#pragma unroll
                 for (int c = 0; c < 6; ++c) {
-                    const double t = a[p][c];
+                    const T t = a[p][c];
                     a[p][c] = a[col][c];
                     a[col][c] = t;
                 }
-            const double piv = 1.0 / a[col][col];
+            const T piv = T(1) / a[col][col];
+#pragma unroll
             for (int c = 0; c < 6; ++c) a[col][c] *= piv;
+#pragma unroll
             for (int r = 0; r < 3; ++r)
                 if (r != col) {
-                    const double f = a[r][col];
+                    const T f = a[r][col];
+#pragma unroll
                     for (int c = 0; c < 6; ++c) a[r][c] -= f * a[col][c];
                 }
         }
         for (int r = 0; r < 4; ++r)
             for (int c = 0; c < 4; ++c)
                 inv[16 * node + 4 * r + c] =
-                    (r < 3 && c < 3) ? (ok ? (T)a[r][3 + c] : (T)(r == c ? 1.0 : 0.0)) : T(0);
+                    (r < 3 && c < 3) ? (ok ? a[r][3 + c] : (r == c ? T(1) : T(0))) : T(0);
     }
 }
 
