@@ -170,6 +170,25 @@ def test_newton_step_matches_direct_newton(fsi, oracle, mixed, precond, rprec):
         (np.linalg.norm(d - d_lin), np.linalg.norm(d), rep)
 
 
+@pytest.mark.parametrize("mixed", [False, True])
+def test_newton_schur_on_a_grid_that_does_not_coarsen(fsi, oracle, mixed):
+    """N = 7: the pressure hierarchy has a single level (its coarse solve is
+    the whole V-cycle), so the Schur preconditioner takes its general path
+    (V-cycle into the level buffer, then the merge pass) after the Krylov
+    loop's basis scaling has split the vector; the step must still reach the
+    oracle's tolerance and its direct-solve neighbourhood."""
+    from oracle import newton
+    mesh, st, dev, P, y0 = setup(fsi, oracle, N=7, m=200, seed=5)
+    code, rep = fsi.fsi_newton_step(mesh, st, mixed=mixed, restart=50, max_newton=12,
+                                    max_krylov=2000, newton_rtol=1e-8, krylov_rtol=1e-3,
+                                    precond=1)
+    assert code == 0 and rep["converged"] == 1
+    y_gpu = H(dev["y"])
+    assert np.linalg.norm(P.residual(y_gpu)) <= 1.01e-8 * rep["r_ref"], rep
+    y_ref, _ = newton.newton(P, y0, rtol=1e-13)
+    assert rel_norm(y_gpu, y_ref) < 1e-3, rep
+
+
 @pytest.mark.parametrize("rprec", [0, 2])
 def test_newton_with_caller_residual_is_bitwise_identical(fsi, oracle, rprec):
     """opts.R0: a caller that already holds R(y_0) (fsi_coupled_residual in
